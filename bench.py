@@ -1,0 +1,435 @@
+"""Benchmark of the kmx front end: Faster-PFH + mutual-NN registration pairs
+per second on the LiDAR-shaped pair (64 beams x 2048 azimuth bins, ~120k raw
+points per scan, voxel 0.3 m -> ~19k voxelised points).
+
+One step = one registration pair through the whole hot path: voxelise both
+clouds, hashed grid, radius search + normals (Algorithm 1 step 1), step 2 +
+SPFH + FPFH (Eqs. A2-A5), mutual matching (Sec. III-C), inputs resident in
+HBM.  L2 is flushed (a 512 MB write) between timed steps, outside the timed
+events.  ``e2e`` repeats the measurement through the same C-ABI calls with the
+raw clouds in pinned host memory: host->device copies and the read-back of the
+correspondences are inside the timed region.
+
+Under torchrun every rank runs its own pair (replicas, weak scaling, no
+collective on the data path; a barrier and a max-reduction of the timings
+only).  ``--impl reference`` times the FP64 CPU oracle on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import lidar_pair  # noqa: E402
+
+WORKLOAD = dict(name="lidar_pair_64beam_2048az_v0.3", voxel=0.3, az_bins=2048, seed=1000)
+METRIC = "Faster-PFH+mutual-NN pairs/s (LiDAR scan pair, voxel 0.3 m)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="kmx", choices=["kmx", "reference"])
+    ap.add_argument("--match", default="auto", choices=["auto", "fp32", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_pair(rank):
+    src, tgt, R, t, vps, vpt = lidar_pair(WORKLOAD["seed"] + rank, az_bins=WORKLOAD["az_bins"])
+    return src, tgt, vps, vpt
+
+
+# ----------------------------------------------------------------------------
+# the oracle (reference arm and CPU baseline)
+# ----------------------------------------------------------------------------
+
+
+def oracle_pair_seconds(src, tgt, vps, vpt):
+    import oracle
+
+    v = WORKLOAD["voxel"]
+    t0 = time.perf_counter()
+    oracle.front_end(src, tgt, v, np.float32(vps).astype(np.float64), np.float32(vpt).astype(np.float64))
+    return time.perf_counter() - t0
+
+
+def oracle_cores():
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else (os.cpu_count() or 1)
+
+
+def cpu_baseline(src, tgt, vps, vpt, budget_s=12.0):
+    times = []
+    t_end = time.perf_counter() + budget_s
+    while not times or (time.perf_counter() < t_end and len(times) < 20):
+        times.append(oracle_pair_seconds(src, tgt, vps, vpt))
+    return dict(value=1.0 / statistics.median(times), unit="pairs/s", cores=oracle_cores(), kind="oracle",
+                sample="%d whole pairs of the workload (voxelise, Faster-PFH on both clouds, FP64 brute-force "
+                       "mutual NN); median pair time %.3f s" % (len(times), statistics.median(times)))
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import build as ob
+
+    ob.build()
+    src, tgt, vps, vpt = make_pair(0)
+    for _ in range(min(args.warmup, 1)):
+        oracle_pair_seconds(src, tgt, vps, vpt)
+    times = [oracle_pair_seconds(src, tgt, vps, vpt) for _ in range(args.steps)]
+    total = sum(times)
+    value = args.steps / total
+    line = dict(metric=METRIC, value=value, unit="pairs/s", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=1000 * total / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=WORKLOAD["name"], raw_points=[len(src), len(tgt)]),
+                cpu_baseline=dict(value=value, unit="pairs/s", kind="oracle", cores=oracle_cores(),
+                                  sample="every step is one whole pair of the workload on the host cores"),
+                e2e=dict(value=value, unit="pairs/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), reasons=sorted(reasons), samples=len(sm))
+
+
+# ----------------------------------------------------------------------------
+# the CUDA path
+# ----------------------------------------------------------------------------
+
+
+def run_kmx(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2409_15615_gb300 import build as kb
+
+    kb.build()
+    from paper_2409_15615_gb300 import kmx, pipeline
+
+    mode = kmx.MATCH_BF16_RERANK if args.match == "bf16" else kmx.MATCH_FP32_EXACT
+    if args.match == "auto":
+        mode = kmx.MATCH_BF16_RERANK if kmx.bf16_available() else kmx.MATCH_FP32_EXACT
+    src, tgt, vps, vpt = make_pair(rank)
+    v = WORKLOAD["voxel"]
+    ps = kmx.params_default(v, viewpoint=np.float32(vps).tolist())
+    pt = kmx.params_default(v, viewpoint=np.float32(vpt).tolist())
+    stream = torch.cuda.current_stream()
+    ctx = kmx.Context(local, stream)
+    pair = pipeline.PairState(ctx, len(src), len(tgt))
+    pair.src.raw.copy_(torch.from_numpy(src).cuda())
+    pair.tgt.raw.copy_(torch.from_numpy(tgt).cuda())
+    pair.run_checked(len(src), len(tgt), ps, pt, mode)  # sizes buffers, checks device errors
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        pair.run(len(src), len(tgt), ps, pt, mode)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    ctx.sync()
+
+    # ---- timed region: K steps, per-step events, L2 flushed between steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ctx.sync()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1000.0)
+
+    # ---- per-stage timing (events between the C-ABI calls of one step)
+    stages = stage_times(torch, ctx, pair, len(src), len(tgt), ps, pt, mode, flush, reps=max(5, args.steps // 2))
+    work = algorithmic_work(pair, ctx)
+    roof = roofline(stages, work, mode)
+
+    # ---- end to end through host buffers
+    e2e = end_to_end(torch, ctx, pair, src, tgt, ps, pt, mode, flush, args.steps, world)
+
+    launches = count_launches(torch, step)
+    n_src_vox = int(pair.src.n_vox.item())
+    n_tgt_vox = int(pair.tgt.n_vox.item())
+    n_corr = int(pair.n_corr.item())
+    if rank != 0:
+        return
+    line = dict(
+        metric=METRIC, value=value, unit="pairs/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+        ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+        dtype="f32" if mode == kmx.MATCH_FP32_EXACT else "bf16+f32", data="synthetic",
+        config=dict(workload=WORKLOAD["name"], raw_points=[len(src), len(tgt)], voxelised=[n_src_vox, n_tgt_vox],
+                    descriptors=[int(pair.src.out["n_valid"].item()), int(pair.tgt.out["n_valid"].item())],
+                    correspondences=n_corr, match="fp32_exact" if mode == kmx.MATCH_FP32_EXACT else "bf16_rerank",
+                    l2="flushed between steps (512 MB write outside the timed events)", parallelism="replicas"),
+        points_per_s=world * args.steps * (n_src_vox + n_tgt_vox) / (total_ms / 1000.0),
+        latency_ms=dict(p50=float(np.percentile(step_ms, 50)), p99=float(np.percentile(step_ms, 99))),
+        wall_s=wall, stages_ms=stages, roofline=roof, e2e=e2e, gpu_launches=launches * args.steps,
+        gpu_launches_per_step=launches, clocks=clk,
+    )
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(src, tgt, vps, vpt)
+    print(json.dumps(line), flush=True)
+
+
+def stage_times(torch, ctx, pair, n_src, n_tgt, ps, pt, mode, flush, reps):
+    """Mean device time of each C-ABI call of a step (events on the context
+    stream between consecutive calls)."""
+    from paper_2409_15615_gb300 import kmx
+
+    stream = ctx.stream
+    names = ["voxelize", "build_grid", "normals", "fasterpfh"]
+    acc = {("src_" + n): [] for n in names}
+    acc.update({("tgt_" + n): [] for n in names})
+    acc["match"] = []
+    for _ in range(reps):
+        flush.zero_()
+        for side, cs, n_raw, prm in (("src_", pair.src, n_src, ps), ("tgt_", pair.tgt, n_tgt, pt)):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            e[0].record(stream)
+            ctx.voxelize(cs.raw[:n_raw], prm.voxel, cap=cs.n_cap, out4=cs.vox4, n_out=cs.n_vox)
+            e[1].record(stream)
+            if cs.grid is not None:
+                cs.grid.free()
+            cs.grid = ctx.build_grid(cs.vox4, prm.r_fpfh, n_cap=cs.n_cap, d_n=cs.n_vox)
+            e[2].record(stream)
+            b = ctx.normals(cs.grid, prm, cs.nbr_cap, out=cs.bufs)
+            e[3].record(stream)
+            ctx.fasterpfh(cs.grid, prm, b["normal4"], b["flags"], b["offs"], b["nbr"], out=cs.out)
+            e[4].record(stream)
+            torch.cuda.synchronize()
+            for i, n in enumerate(names):
+                acc[side + n].append(e[i].elapsed_time(e[i + 1]))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s, t = pair.src, pair.tgt
+        e0.record(stream)
+        ctx.match(s.out["desc"], s.out["valid"], s.n_cap, t.out["desc"], t.out["valid"], t.n_cap,
+                  d_np=s.out["n_valid"], d_nq=t.out["n_valid"], mode=mode, cap=pair.cap, out=pair.corr,
+                  n_out=pair.n_corr)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        acc["match"].append(e0.elapsed_time(e1))
+    ctx.sync()
+    return {k: float(np.mean(v)) for k, v in acc.items()}
+
+
+def algorithmic_work(pair, ctx):
+    """Counts that define the algorithmic bytes / flops of each stage."""
+    out = {}
+    for side, cs in (("src", pair.src), ("tgt", pair.tgt)):
+        n = int(cs.n_vox.item())
+        offs = cs.bufs["offs"][: n + 1].cpu().numpy()
+        flags = cs.bufs["flags"][:n].cpu().numpy()
+        nbr = cs.bufs["nbr"][: offs[-1]].cpu().numpy()
+        B = (flags & 1) > 0
+        mF = np.diff(offs)
+        owner = np.repeat(np.arange(n), mF)
+        valid_pair = B[owner] & B[nbr] & (nbr != owner)
+        mV = np.bincount(owner[valid_pair], minlength=n)
+        nJ = int(cs.out["n_valid"].item())
+        out[side] = dict(n=n, sum_mF=int(mF.sum()), n_B=int(B.sum()), sum_mV_B=int(mV[B].sum()),
+                         sum_mV_J=int(mV[(flags & 2) > 0].sum()), n_J=nJ, n_raw=int(cs.raw.shape[0]))
+    out["match"] = dict(np=out["src"]["n_J"], nq=out["tgt"]["n_J"])
+    return out
+
+
+def stage_bytes(w):
+    """Algorithmic HBM bytes of each feature stage of one cloud."""
+    n = w["n"]
+    return dict(
+        voxelize=16 * w["n_raw"] + 4 * w["n_raw"] + 16 * n,       # read xyz(+pad), assignment, centroids
+        build_grid=16 * n + 16 * n,                                # read points, write cell-ordered copy
+        normals=12 * w["sum_mF"] + 16 * n + 16 * n + 1 * n + 8 * n,  # neighbour coords, own point, normal, flag, offs
+        fasterpfh=24 * w["sum_mV_B"] + 144 * w["sum_mV_J"] + 16 * n + 144 * w["n_B"] + 144 * w["n_J"],
+    )
+
+
+def roofline(stages, work, mode):
+    peaks = measured_peaks()
+    best = None
+    for side in ("src", "tgt"):
+        b = stage_bytes(work[side])
+        for k, by in b.items():
+            ms = stages[side + "_" + k]
+            if best is None or ms > best[1]:
+                best = (side + "_" + k, ms, by)
+    m = work["match"]
+    match_ms = stages["match"]
+    if match_ms > best[1]:
+        if mode == 0:
+            flops = 3.0 * m["np"] * m["nq"] * 33
+            achieved = flops / (match_ms / 1000.0) / 1e12
+            peak = peaks["fp32_tflops"]
+            return dict(kernel="match_tiles_fp32 (kmx_match, FP32 exact)", bound="alu", achieved=achieved, peak=peak,
+                        unit="TFLOP/s", frac=achieved / peak, traffic=None,
+                        note="3 flops (sub + fma) per descriptor element pair; peak = 152 SMs x 128 FP32 lanes x 2 "
+                             "x 2.07 GHz")
+        flops = 2.0 * m["np"] * m["nq"] * 33
+        achieved = flops / (match_ms / 1000.0) / 1e12
+        peak = peaks["bf16_tflops"]
+        return dict(kernel="kmx_match (BF16 tcgen05 + rerank)", bound="tensor", achieved=achieved, peak=peak,
+                    unit="TFLOP/s", frac=achieved / peak, traffic=None)
+    name, ms, by = best
+    achieved = by / (ms / 1000.0) / 1e9
+    return dict(kernel=name, bound="hbm", achieved=achieved, peak=peaks["hbm_gbs"], unit="GB/s",
+                frac=achieved / peaks["hbm_gbs"], traffic=None, algorithmic_bytes=by, ms=ms)
+
+
+def measured_peaks():
+    p = dict(hbm_gbs=6800.0, bf16_tflops=1900.0, source="fallback")
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        p = dict(hbm_gbs=float(m["hbm_gbs"]), bf16_tflops=float(m["bf16_tflops"]), source="measured")
+    except (OSError, KeyError, ValueError):
+        pass
+    p["fp32_tflops"] = 152 * 128 * 2 * 2.07e9 / 1e12
+    return p
+
+
+def end_to_end(torch, ctx, pair, src, tgt, ps, pt, mode, flush, steps, world):
+    """Same steps through the C ABI from pinned host buffers: H2D of both raw
+    clouds and D2H of the correspondences inside the timed events."""
+    h_src = torch.from_numpy(src).pin_memory()
+    h_tgt = torch.from_numpy(tgt).pin_memory()
+    h_corr = torch.empty(pair.corr.shape, dtype=torch.int32).pin_memory()
+    h_n = torch.empty(1, dtype=torch.int64).pin_memory()
+    stream = ctx.stream
+    ms = []
+    for k in range(steps + 2):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pair.src.raw[: len(src)].copy_(h_src, non_blocking=True)
+        pair.tgt.raw[: len(tgt)].copy_(h_tgt, non_blocking=True)
+        pair.run(len(src), len(tgt), ps, pt, mode)
+        h_n.copy_(pair.n_corr, non_blocking=True)
+        h_corr.copy_(pair.corr, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        if k >= 2:
+            ms.append(a.elapsed_time(b))
+    total = sum(ms)
+    if world > 1:
+        t = torch.tensor([total], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t.item())
+    return dict(value=world * steps / (total / 1000.0), unit="pairs/s",
+                h2d_bytes_per_step=int(src.nbytes + tgt.nbytes),
+                d2h_bytes_per_step=int(h_corr.numel() * 4 + 8),
+                p50_ms=float(np.percentile(ms, 50)), p99_ms=float(np.percentile(ms, 99)))
+
+
+def count_launches(torch, step):
+    """Kernels libkmx launches in one step (its own launch counter)."""
+    from paper_2409_15615_gb300 import kmx
+
+    before = kmx.launch_count()
+    step()
+    torch.cuda.synchronize()
+    return kmx.launch_count() - before
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_kmx(args)
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1 and args.impl != "reference":
+        import torch.distributed as dist
+
+        if dist.is_initialized():
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

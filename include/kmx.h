@@ -1,0 +1,219 @@
+/*
+ * kmx.h - C ABI of the GB300 (sm_103a) implementation of the KISS-Matcher
+ * front end (arXiv 2409.15615): voxel downsampling, radius neighbourhoods,
+ * reliable normals, Faster-PFH descriptors and mutual nearest-neighbour
+ * descriptor matching.  The output is the correspondence set A that the
+ * k-core pruning of Sec. III-D consumes.
+ *
+ * General conventions (apply to every entry point below)
+ *  - Pointers named d_* are DEVICE memory owned by the caller.  The library
+ *    never frees them and never keeps them past the call, except where a
+ *    function says so (kmx_build_grid keeps d_xyz4).
+ *  - Every call is asynchronous on the context's stream (kmx_set_stream).
+ *    Scalar results (counts) are written to caller-provided device int64
+ *    cells, so a pipeline of calls needs no host synchronisation.  Host
+ *    return values report only argument and launch errors.
+ *  - Errors detected on the device (index range, capacity, hash overflow)
+ *    are recorded in the context and reported by the next kmx_sync(), which
+ *    synchronises the stream, returns the first such error and clears it.
+ *    Outputs of a call whose device error is reported are unspecified.
+ *  - Sizes named *_cap are host-side capacities (upper bounds); the matching
+ *    d_n* argument, when non-NULL, holds the actual count on the device (as
+ *    written by an earlier call) and must be <= the capacity.  When it is
+ *    NULL the capacity is the exact count.
+ *  - Scratch memory is owned by the context; a call may grow it with
+ *    stream-ordered allocation (cudaMallocAsync).  kmx_reserve() sizes it in
+ *    advance.
+ *  - Point clouds are float32.  "xyz4" layout is [n][4] (x, y, z, pad),
+ *    16-byte aligned rows.
+ *  - No function aborts the process, traps the device or falls back to the
+ *    CPU.
+ */
+#ifndef KMX_H
+#define KMX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KMX_OK = 0,
+    KMX_EINVAL = 1,    /* bad argument: NULL pointer, negative size, bad stride, misaligned row */
+    KMX_ENOMEM = 2,    /* device allocation failed */
+    KMX_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+    KMX_ERANGE = 4,    /* a voxel or grid-cell index does not fit in 21 bits */
+    KMX_ECAPACITY = 5, /* an output buffer was too small; the needed size is in the *needed cell */
+    KMX_ETIMEOUT = 6,  /* a bounded device-side wait gave up */
+    KMX_EBUSY = 7      /* the context is in use by a stream capture */
+} kmx_status;
+
+/* Faster-PFH parameters (Sec. III-C and Sec. IV-B).  All radii are in the
+ * units of the cloud.  kmx_params_default(v) sets the paper's values:
+ * r_normal = 3.5 v, r_fpfh = 5.0 v, tau_num = 3, tau_lin = 0.99, 11 bins per
+ * angular feature (33-D descriptor), viewpoint at the origin. */
+typedef struct {
+    float voxel;        /* voxel size v */
+    float r_normal;     /* normal radius, <= r_fpfh (Sec. III-C) */
+    float r_fpfh;       /* FPFH radius (Eq. A1) */
+    int32_t tau_num;    /* cardinality threshold (Algorithm 1) */
+    float tau_lin;      /* linearity threshold (Algorithm 1) */
+    int32_t hist_bins;  /* H of Eq. A3; only 11 is supported */
+    float viewpoint[3]; /* normals are oriented toward this point */
+} kmx_params;
+
+/* Descriptor rows: 33 used floats padded to 36 (144 bytes). */
+#define KMX_DESC_DIM 33
+#define KMX_DESC_STRIDE 36
+
+/* One correspondence of A (Sec. III-C): i indexes the source (voxelised)
+ * cloud, j the target cloud; d1 and d2 are the descriptor distances from
+ * FPFH(i) to its nearest and second-nearest target descriptors (d2 feeds the
+ * ratio test of Sec. III-D). */
+typedef struct {
+    int32_t i, j;
+    float d1, d2;
+} kmx_corr;
+
+typedef enum {
+    KMX_MATCH_FP32_EXACT = 0, /* exact FP32 distances on CUDA cores */
+    KMX_MATCH_BF16_RERANK = 1 /* BF16 tensor-core distances, top-8 candidates re-ranked exactly in FP32 */
+} kmx_match_mode;
+
+typedef struct kmx_ctx kmx_ctx;   /* opaque, owned by the library */
+typedef struct kmx_grid kmx_grid; /* opaque, owned by the library */
+
+/* Fill *out with the paper's parameters for voxel size v (Sec. IV-B).
+ * Returns KMX_EINVAL if out is NULL or v is not positive and finite. */
+kmx_status kmx_params_default(float v, kmx_params* out);
+
+/* Create a context on CUDA device `device` issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out is owned by the
+ * caller and released with kmx_destroy. */
+kmx_status kmx_create(kmx_ctx** out, int device, void* cuda_stream);
+
+/* Release the context and its scratch memory (synchronises its stream). */
+void kmx_destroy(kmx_ctx* ctx);
+
+/* Issue subsequent work on another stream of the same device. */
+kmx_status kmx_set_stream(kmx_ctx* ctx, void* cuda_stream);
+
+/* Make sure the context scratch holds at least `bytes` bytes. */
+kmx_status kmx_reserve(kmx_ctx* ctx, int64_t bytes);
+
+/* Wait for the context's stream; return (and clear) the first device-side
+ * error recorded since the last kmx_sync, else KMX_OK. */
+kmx_status kmx_sync(kmx_ctx* ctx);
+
+/* Human-readable description of the last error reported on this context. */
+const char* kmx_last_error(const kmx_ctx* ctx);
+
+/* Number of CUDA kernels the library has launched in this process, over all
+ * contexts (diagnostics; a relaxed atomic counter, never reset).  Not from
+ * the paper: it lets a caller count the device work of a call sequence. */
+int64_t kmx_launch_count(void);
+
+/*
+ * Voxel downsampling: the voxelised input clouds of Sec. III-A ("unordered
+ * voxelized point clouds with a voxel size v").
+ *   d_xyz     [n_raw][stride] float32 points, stride 3 or 4.
+ *   voxel     v > 0.  A point belongs to voxel floor(x / v) per axis, with
+ *             the quotient computed in FP64 (half-open cells).
+ *   d_out4    [cap][4] float32: the centroid of each occupied voxel (its
+ *             members summed in FP64 in input order, divided by the count in
+ *             FP64, rounded to FP32), w = 0.  Voxels appear in the order of
+ *             their first member in the input.
+ *   d_n_out   device int64: number of voxels written.
+ *   d_assign  nullable [n_raw] int32: voxel index of every input point.
+ * Device errors: KMX_ERANGE if some |floor(x / v)| >= 2^20; KMX_ECAPACITY if
+ * the voxel count exceeds cap.
+ */
+kmx_status kmx_voxelize(kmx_ctx* ctx, const float* d_xyz, int64_t n_raw, int32_t stride, float voxel,
+                        float* d_out4, int64_t cap, int64_t* d_n_out, int32_t* d_assign);
+
+/*
+ * Hashed uniform grid over a cloud, the search structure that stands in for
+ * the K-d tree of Algorithm 1 (radius search of Eq. A1).
+ *   d_xyz4    [n_cap][4] float32 points; KEPT by the grid: it must stay valid
+ *             and unchanged until kmx_grid_free.
+ *   n_cap     number of rows (exact if d_n is NULL).
+ *   d_n       nullable device int64 actual count (e.g. kmx_voxelize's d_n_out).
+ *   cell      cell edge > 0.  Searches visit the 27 cells around a point, so
+ *             kmx_normals requires cell >= r_fpfh (else KMX_EINVAL).
+ * Device errors: KMX_ERANGE if a cell index does not fit in 21 bits.
+ */
+kmx_status kmx_build_grid(kmx_ctx* ctx, const float* d_xyz4, int64_t n_cap, const int64_t* d_n, float cell,
+                          kmx_grid** out);
+
+/* Release a grid: stream-ordered free on the device and stream its context
+ * had when the grid was built.  It may be called after kmx_destroy of that
+ * context, as long as the stream still exists. */
+void kmx_grid_free(kmx_grid* grid);
+
+/*
+ * Algorithm 1, step 1: one radius search with r_fpfh per point (Eq. A1,
+ * including the point itself), the r_normal subsample P_normal, PCA normal
+ * and linearity p_lin = (l1 - l2) / l1 (Sec. III-C), and the reliability flag
+ * B (|I| >= tau_num, |P_normal| >= tau_num, p_lin < tau_lin).
+ *   d_normal4  [n_cap][4] float32: unit normal oriented toward the viewpoint
+ *              (n . (vp - a_q) >= 0) and p_lin in w, for every point that
+ *              reached PCA; zeros otherwise.
+ *   d_flags    [n_cap] uint8: bit0 = B[q]; bit2 = PCA evaluated; bit1 = 0.
+ *   d_nbr_offs [n_cap + 1] int64 CSR offsets of the neighbour lists.
+ *   d_nbr      [nbr_cap] int32: I(q) for every q (in the order the grid
+ *              visits them); Algorithm 1's M[q] is this list where B[q].
+ *              May be NULL to count only.
+ *   d_needed   device int64: total list length (d_nbr_offs[n]).
+ * The neighbour sets are exact: a distance within FP32 rounding of a radius
+ * is decided again in FP64 as ((dx*dx + dy*dy) + dz*dz) < r*r.
+ * Device errors: KMX_ECAPACITY if the lists need more than nbr_cap entries
+ * (normals and flags are still written; the lists are not).
+ */
+kmx_status kmx_normals(kmx_ctx* ctx, const kmx_grid* grid, const kmx_params* params, float* d_normal4,
+                       uint8_t* d_flags, int64_t* d_nbr_offs, int32_t* d_nbr, int64_t nbr_cap,
+                       int64_t* d_needed);
+
+/*
+ * Algorithm 1, step 2 and the descriptors of Eqs. A2-A5.
+ *   I_valid(q) = { i in M[q] : B[i] }; q enters J iff B[q] and
+ *   |I_valid(q)| >= tau_num.  SPFH(q) (Eq. A4) is built for every q with B
+ *   over k in I_valid(q) without q, each third scaled by 100 / (number of
+ *   contributing pairs); FPFH(q) = SPFH(q) + (1/m) sum_k SPFH(k) / w_k (Eq. A5)
+ *   with w_k = |a_k - a_q| over the m neighbours k != q.
+ *   d_normal4, d_nbr_offs, d_nbr  as written by kmx_normals (or any input of
+ *              the same layout).
+ *   d_flags    [n] uint8 in/out: bit0 (B) is read; bit1 is set for q in J.
+ *   d_desc     [n_cap][36] float32: row j holds FPFH(J[j]) for j < |J|
+ *              (33 values + 3 zeros); other rows are not written.
+ *   d_valid    [n_cap] int32: J in ascending point order.
+ *   d_n_valid  device int64: |J|.
+ *   d_spfh     nullable [n_cap][36] float32: SPFH of every point (zero rows
+ *              for points without B); NULL keeps it in scratch.
+ */
+kmx_status kmx_fasterpfh(kmx_ctx* ctx, const kmx_grid* grid, const kmx_params* params, const float* d_normal4,
+                         uint8_t* d_flags, const int64_t* d_nbr_offs, const int32_t* d_nbr, float* d_desc,
+                         int32_t* d_valid, int64_t* d_n_valid, float* d_spfh);
+
+/*
+ * Mutual nearest-neighbour matching of descriptors (reciprocity test,
+ * Sec. III-C) under Euclidean distance; ties go to the lower row.
+ *   d_desc_p   [np_cap][36] float32 source descriptors (rows as written by
+ *              kmx_fasterpfh); d_valid_p maps row -> source point index.
+ *   d_desc_q   [nq_cap][36] float32 target descriptors; d_valid_q likewise.
+ *   d_np/d_nq  nullable device row counts.
+ *   mode       kmx_match_mode.
+ *   d_out      [cap] kmx_corr sorted by source row; (i, j) are point
+ *              indices taken through d_valid_p / d_valid_q.
+ *   d_n_out    device int64: |A|.
+ * Device errors: KMX_ECAPACITY if |A| > cap (the first cap pairs are kept).
+ */
+kmx_status kmx_match(kmx_ctx* ctx, const float* d_desc_p, const int32_t* d_valid_p, int64_t np_cap,
+                     const int64_t* d_np, const float* d_desc_q, const int32_t* d_valid_q, int64_t nq_cap,
+                     const int64_t* d_nq, int32_t mode, kmx_corr* d_out, int64_t cap, int64_t* d_n_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KMX_H */

@@ -41,7 +41,7 @@ def load():
                                      C.POINTER(i64)]
     lib.orc_pair_features.argtypes = [_f32p, _f64p, _f32p, _f64p, _f64p]
     lib.orc_bin.argtypes = [f64, f64, f64, C.c_int]
-    lib.orc_spfh.argtypes = [_f32p, _f64p, i64, _u8p, _i64p, _i32p, C.c_int, _f64p, _i32p]
+    lib.orc_spfh.argtypes = [_f32p, _f64p, i64, _u8p, _i64p, _i32p, C.c_int, _f64p, _i32p, _f64p]
     lib.orc_fpfh.argtypes = [_f32p, i64, _i32p, _i64p, _i32p, _f64p, C.c_int, _f64p]
     lib.orc_nearest.argtypes = [_f64p, i64, _f64p, i64, C.c_int, _i32p, _f64p, _f64p]
     lib.orc_core_numbers.argtypes = [i64, _i64p, _i32p, _i32p]
@@ -179,17 +179,25 @@ def feature_bin(f, lo, hi, H=11):
     return load().orc_bin(float(f), float(lo), float(hi), int(H))
 
 
-def spfh(p4, normal4, flags, voffs, vnbr, H=11):
-    """SPFH rows [n, 3H] (Eq. A4) and the per-point pair counts."""
+def spfh(p4, normal4, flags, voffs, vnbr, H=11, with_margin=False):
+    """SPFH rows [n, 3H] (Eq. A4) and the per-point pair counts; with
+    ``with_margin`` also the per-point distance of the nearest pair feature to
+    a decision FP32 rounding could flip (bin edge, atan2 cut, source choice,
+    degenerate-pair threshold)."""
     lib = load()
     p = _as_p4(p4)
     n = len(p)
-    out = np.zeros((n, 3 * H))
-    npairs = np.zeros(n, np.int32)
+    out = np.zeros((max(n, 1), 3 * H))
+    npairs = np.zeros(max(n, 1), np.int32)
+    margin = np.zeros(max(n, 1))
     nb = np.ascontiguousarray(vnbr, np.int32) if len(vnbr) else np.zeros(1, np.int32)
-    _check(lib.orc_spfh(p, np.ascontiguousarray(normal4, np.float64), n, np.ascontiguousarray(flags, np.uint8),
-                        np.ascontiguousarray(voffs, np.int64), nb, int(H), out, npairs), "spfh")
-    return out, npairs
+    _check(lib.orc_spfh(p if n else np.zeros((1, 4), np.float32), np.ascontiguousarray(normal4, np.float64)
+                        if n else np.zeros((1, 4)), n, np.ascontiguousarray(flags, np.uint8) if n else
+                        np.zeros(1, np.uint8), np.ascontiguousarray(voffs, np.int64), nb, int(H), out, npairs,
+                        margin), "spfh")
+    if with_margin:
+        return out[:n], npairs[:n], margin[:n]
+    return out[:n], npairs[:n]
 
 
 def fpfh(p4, J, voffs, vnbr, spfh_rows):
@@ -214,10 +222,10 @@ def faster_pfh(p4, params: OracleParams, search="grid"):
     offs, nbr = radius_search(p, params.r_fpfh, method=search)
     normal4, evals, flags, n_normal = normals(p, offs, nbr, params)
     voffs, vnbr, J, flags = valid_filter(offs, nbr, flags, params.tau_num)
-    sp, npairs = spfh(p, normal4, flags, voffs, vnbr, params.hist_bins)
+    sp, npairs, margin = spfh(p, normal4, flags, voffs, vnbr, params.hist_bins, with_margin=True)
     fp = fpfh(p, J, voffs, vnbr, sp)
     return dict(points=p, offs=offs, nbr=nbr, normal4=normal4, evals=evals, n_normal=n_normal, flags=flags,
-                voffs=voffs, vnbr=vnbr, J=J, spfh=sp, npairs=npairs, fpfh=fp)
+                voffs=voffs, vnbr=vnbr, J=J, spfh=sp, npairs=npairs, margin=margin, fpfh=fp)
 
 
 def nearest(X, Y):

@@ -34,8 +34,10 @@
  *  R6 the source point of a pair is the one whose normal makes the smaller
  *     angle with the line through both points: |n_q . d| >= |n_k . d| keeps q
  *     as source (ties keep q).
- *  R7 v = d x u and w = u x v are unit vectors; a pair with |d x u| < 1e-12 is
- *     skipped and does not count in the SPFH normaliser.
+ *  R7 v = d x u and w = u x v are unit vectors; a pair with |d x u| < 1e-6
+ *     (d and u within 1e-6 rad of parallel, where the Darboux frame is not
+ *     defined to FP32 accuracy) is skipped and does not count in the SPFH
+ *     normaliser.
  *  R8 atan2 is the four-quadrant arctangent.
  *  R9 H = 11 bins per feature; feature ranges are [-pi, pi], [-1, 1],
  *     [-1, 1]; bins are 0-based, bin = floor(H (f - lo) / (hi - lo)) clamped
@@ -463,7 +465,7 @@ static double dot3(const double* a, const double* b)
 /*
  * Angular features of the pair (q, k) with normals nq, nk (Eq. A2 with
  * readings R6-R8).  Returns 1 and writes f[3] = (f1, f2, f3), or returns 0
- * if the pair is degenerate (coincident points or |d x u| < 1e-12).
+ * if the pair is degenerate (coincident points or |d x u| < 1e-6).
  */
 int orc_pair_features(const float* pq, const double* nq, const float* pk, const double* nk, double* f)
 {
@@ -485,7 +487,7 @@ int orc_pair_features(const float* pq, const double* nq, const float* pk, const 
     double x[3];
     cross3(d, u, x);
     double s = sqrt(dot3(x, x));
-    if (s < 1e-12) return 0;
+    if (s < 1e-6) return 0;
     double v[3], w[3];
     for (int a = 0; a < 3; ++a) v[a] = x[a] / s;
     cross3(u, v, w);
@@ -509,13 +511,56 @@ int orc_bin(double f, double lo, double hi, int H)
 /* ------------------------------------------------------------------------ */
 
 /*
+ * How close the pair (q, k) is to a decision that FP32 rounding could flip:
+ * the smallest of |(|n_q.d| - |n_k.d|)| (source choice), | |d x u| - 1e-6 |
+ * (degenerate-pair test), the distance of f1 to an interior bin edge or to
+ * +-pi (the atan2 branch cut), and the distance of f2, f3 to an interior bin
+ * edge.  Used by the tests only, to list the points whose exact histogram is
+ * ill-posed at FP32 precision.
+ */
+static double pair_margin(const float* pq, const double* nq, const float* pk, const double* nk, int H)
+{
+    const double PI = 3.14159265358979323846;
+    double dv[3];
+    for (int a = 0; a < 3; ++a) dv[a] = (double)pk[a] - (double)pq[a];
+    double dist = sqrt(dot3(dv, dv));
+    if (!(dist > 0.0)) return INFINITY;
+    double d[3];
+    for (int a = 0; a < 3; ++a) d[a] = dv[a] / dist;
+    double m = fabs(fabs(dot3(nq, d)) - fabs(dot3(nk, d)));
+    const double* u = fabs(dot3(nq, d)) >= fabs(dot3(nk, d)) ? nq : nk;
+    if (u == nk)
+        for (int a = 0; a < 3; ++a) d[a] = -d[a];
+    double x[3];
+    cross3(d, u, x);
+    double s = sqrt(dot3(x, x));
+    m = fmin(m, fabs(s - 1e-6));
+    double f[3];
+    if (!orc_pair_features(pq, nq, pk, nk, f)) return m;
+    const double lo[3] = {-PI, -1.0, -1.0}, hi[3] = {PI, 1.0, 1.0};
+    for (int l = 0; l < 3; ++l) {
+        double w = (hi[l] - lo[l]) / (double)H;
+        double t = (f[l] - lo[l]) / w;
+        double e = fabs(t - floor(t + 0.5)) * w;
+        if (l > 0 && (f[l] - lo[l] < 0.5 * w || hi[l] - f[l] < 0.5 * w)) {
+            /* outer ends of [-1, 1] are not edges (values cannot wrap) */
+            double tt = floor(t + 0.5);
+            if (tt <= 0.0 || tt >= (double)H) e = INFINITY;
+        }
+        m = fmin(m, e);
+    }
+    return m;
+}
+
+/*
  * SPFH of every q with B[q] over k in I_valid(q), k != q (reading R2):
  * sub-histogram l counts the bins of f_l and is scaled by 100 / c, c the
  * number of contributing pairs (reading R7).  spfh is [n][3H] (rows of q
- * without B are zero); npairs[q] = c (nullable).
+ * without B are zero); npairs[q] = c (nullable); margin[q] (nullable) is the
+ * smallest pair_margin over the pairs of q (+inf without pairs).
  */
 int orc_spfh(const float* p4, const double* normal4, int64_t n, const uint8_t* flags, const int64_t* voffs,
-             const int32_t* vnbr, int H, double* spfh, int32_t* npairs)
+             const int32_t* vnbr, int H, double* spfh, int32_t* npairs, double* margin)
 {
     const double PI = 3.14159265358979323846;
     const double lo[3] = {-PI, -1.0, -1.0}, hi[3] = {PI, 1.0, 1.0};
@@ -524,11 +569,14 @@ int orc_spfh(const float* p4, const double* normal4, int64_t n, const uint8_t* f
         double* row = spfh + (size_t)q * 3 * H;
         for (int h = 0; h < 3 * H; ++h) row[h] = 0.0;
         if (npairs) npairs[q] = 0;
+        if (margin) margin[q] = INFINITY;
         if (!(flags[q] & 1)) continue;
         int64_t c = 0;
         for (int64_t t = voffs[q]; t < voffs[q + 1]; ++t) {
             int64_t k = vnbr[t];
             if (k == q) continue;
+            if (margin)
+                margin[q] = fmin(margin[q], pair_margin(p4 + 4 * q, normal4 + 4 * q, p4 + 4 * k, normal4 + 4 * k, H));
             double f[3];
             if (!orc_pair_features(p4 + 4 * q, normal4 + 4 * q, p4 + 4 * k, normal4 + 4 * k, f)) continue;
             for (int l = 0; l < 3; ++l) row[l * H + orc_bin(f[l], lo[l], hi[l], H)] += 1.0;

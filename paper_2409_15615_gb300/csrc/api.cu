@@ -1,0 +1,325 @@
+// C ABI entry points of kmx.h: argument checks, scratch management and the
+// launch sequences of each stage.  No entry point synchronises except
+// kmx_sync / kmx_destroy, and none falls back to the CPU.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "kmx_internal.cuh"
+#include "match_common.cuh"
+
+namespace {
+
+kmx_status fail(kmx_ctx* c, kmx_status s, const char* fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->msg, sizeof(c->msg), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+kmx_status cuda_fail(kmx_ctx* c, cudaError_t e, const char* where)
+{
+    if (e == cudaErrorMemoryAllocation) return fail(c, KMX_ENOMEM, "%s: out of device memory", where);
+    return fail(c, KMX_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// Makes the context's device current for the duration of a call and restores
+// the caller's device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            ok = false;
+            return;
+        }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+kmx_status ensure_ws(kmx_ctx* c, size_t bytes)
+{
+    if (bytes <= c->ws_size && c->ws) return KMX_OK;
+    size_t want = bytes > c->ws_size + c->ws_size / 2 ? bytes : c->ws_size + c->ws_size / 2;
+    if (want < (1u << 20)) want = 1u << 20;
+    if (c->ws) cudaFreeAsync(c->ws, c->stream);
+    c->ws = nullptr;
+    c->ws_size = 0;
+    void* p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, want, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "scratch allocation");
+    c->ws = p;
+    c->ws_size = want;
+    return KMX_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+kmx_status launched(kmx_ctx* c, cudaError_t e, const char* where)
+{
+    if (e != cudaSuccess) return cuda_fail(c, e, where);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, where);
+    return KMX_OK;
+}
+
+}  // namespace
+
+std::atomic<long long> kmx_g_launches{0};
+
+extern "C" {
+
+int64_t kmx_launch_count(void) { return (int64_t)kmx_g_launches.load(std::memory_order_relaxed); }
+
+kmx_status kmx_params_default(float v, kmx_params* out)
+{
+    if (!out || !(v > 0.0f) || !isfinite(v)) return KMX_EINVAL;
+    out->voxel = v;
+    out->r_normal = 3.5f * v;
+    out->r_fpfh = 5.0f * v;
+    out->tau_num = 3;
+    out->tau_lin = 0.99f;
+    out->hist_bins = 11;
+    out->viewpoint[0] = out->viewpoint[1] = out->viewpoint[2] = 0.0f;
+    return KMX_OK;
+}
+
+kmx_status kmx_create(kmx_ctx** out, int device, void* cuda_stream)
+{
+    if (!out) return KMX_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return KMX_EINVAL;
+    DeviceGuard g(device);
+    if (!g.ok) return KMX_ECUDA;
+    kmx_ctx* c = new (std::nothrow) kmx_ctx();
+    if (!c) return KMX_ENOMEM;
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (cudaMalloc(&c->d_err, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMallocHost(&c->h_err, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMemset(c->d_err, 0, sizeof(unsigned int)) != cudaSuccess) {
+        if (c->d_err) cudaFree(c->d_err);
+        if (c->h_err) cudaFreeHost(c->h_err);
+        delete c;
+        return KMX_ENOMEM;
+    }
+    *c->h_err = 0;
+    c->msg[0] = 0;
+    *out = c;
+    return KMX_OK;
+}
+
+void kmx_destroy(kmx_ctx* c)
+{
+    if (!c) return;
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    if (c->ws) cudaFree(c->ws);
+    cudaFree(c->d_err);
+    cudaFreeHost(c->h_err);
+    delete c;
+}
+
+kmx_status kmx_set_stream(kmx_ctx* c, void* cuda_stream)
+{
+    if (!c) return KMX_EINVAL;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    return KMX_OK;
+}
+
+kmx_status kmx_reserve(kmx_ctx* c, int64_t bytes)
+{
+    if (!c || bytes < 0) return KMX_EINVAL;
+    DeviceGuard g(c->device);
+    return ensure_ws(c, (size_t)bytes);
+}
+
+kmx_status kmx_sync(kmx_ctx* c)
+{
+    if (!c) return KMX_EINVAL;
+    DeviceGuard g(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "kmx_sync");
+    e = cudaMemcpy(c->h_err, c->d_err, sizeof(unsigned int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "kmx_sync");
+    const unsigned int bits = *c->h_err;
+    if (!bits) return KMX_OK;
+    cudaMemset(c->d_err, 0, sizeof(unsigned int));
+    if (bits & KMX_DERR_RANGE) return fail(c, KMX_ERANGE, "a voxel or cell index does not fit in 21 bits");
+    if (bits & KMX_DERR_CAPACITY) return fail(c, KMX_ECAPACITY, "an output buffer is too small");
+    if (bits & KMX_DERR_HASHFULL) return fail(c, KMX_ENOMEM, "hash table full");
+    if (bits & KMX_DERR_TIMEOUT) return fail(c, KMX_ETIMEOUT, "device wait timed out");
+    return fail(c, KMX_ECUDA, "unknown device error bits 0x%x", bits);
+}
+
+const char* kmx_last_error(const kmx_ctx* c) { return c ? c->msg : "null context"; }
+
+kmx_status kmx_voxelize(kmx_ctx* c, const float* d_xyz, int64_t n_raw, int32_t stride, float voxel, float* d_out4,
+                        int64_t cap, int64_t* d_n_out, int32_t* d_assign)
+{
+    if (!c) return KMX_EINVAL;
+    if (n_raw < 0 || n_raw > INT32_MAX - 1 || (stride != 3 && stride != 4) || !(voxel > 0.0f) || !isfinite(voxel) ||
+        cap < 0 || !d_n_out || (n_raw > 0 && (!d_xyz || !d_out4)) || (d_out4 && !aligned16(d_out4)))
+        return fail(c, KMX_EINVAL, "kmx_voxelize: bad argument");
+    DeviceGuard g(c->device);
+    kmx_status s = ensure_ws(c, kmx_voxelize_scratch_bytes(n_raw));
+    if (s) return s;
+    return launched(c, kmx_voxelize_launch(c, d_xyz, n_raw, stride, voxel, d_out4, cap, d_n_out, d_assign, c->ws),
+                    "kmx_voxelize");
+}
+
+kmx_status kmx_build_grid(kmx_ctx* c, const float* d_xyz4, int64_t n_cap, const int64_t* d_n, float cell,
+                          kmx_grid** out)
+{
+    if (!c) return KMX_EINVAL;
+    if (!out || n_cap < 0 || n_cap > INT32_MAX - 1 || !(cell > 0.0f) || !isfinite(cell) ||
+        (n_cap > 0 && !d_xyz4) || (d_xyz4 && !aligned16(d_xyz4)))
+        return fail(c, KMX_EINVAL, "kmx_build_grid: bad argument");
+    *out = nullptr;
+    DeviceGuard dg(c->device);
+    kmx_grid* g = new (std::nothrow) kmx_grid();
+    if (!g) return KMX_ENOMEM;
+    g->ctx = c;
+    g->device = c->device;
+    g->stream = c->stream;
+    g->n_cap = n_cap;
+    g->d_n = d_n;
+    g->cell = cell;
+    g->pts = reinterpret_cast<const float4*>(d_xyz4);
+    uint32_t T = 0;
+    const size_t bytes = kmx_grid_bytes(n_cap, &T);
+    g->table_size = T;
+    cudaError_t e = cudaMallocAsync(&g->mem, bytes, c->stream);
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_fail(c, e, "kmx_build_grid");
+    }
+    kmx_arena a{static_cast<char*>(g->mem), 0};
+    g->keys = (unsigned long long*)a.take(sizeof(unsigned long long) * T);
+    g->cells = (int2*)a.take(sizeof(int2) * T);
+    g->sorted = (float4*)a.take(sizeof(float4) * (n_cap + 1));
+    g->d_n_own = (int64_t*)a.take(sizeof(int64_t));
+    g->d_n_sorted = (int64_t*)a.take(sizeof(int64_t));
+    kmx_status s = ensure_ws(c, kmx_grid_scratch_bytes(n_cap, T));
+    if (s == KMX_OK) s = launched(c, kmx_grid_build_launch(c, g, c->ws), "kmx_build_grid");
+    if (s != KMX_OK) {
+        cudaFreeAsync(g->mem, c->stream);
+        delete g;
+        return s;
+    }
+    *out = g;
+    return KMX_OK;
+}
+
+void kmx_grid_free(kmx_grid* g)
+{
+    if (!g) return;
+    DeviceGuard dg(g->device);
+    cudaFreeAsync(g->mem, g->stream);
+    delete g;
+}
+
+static kmx_status check_params(kmx_ctx* c, const kmx_grid* g, const kmx_params* p, const char* who)
+{
+    if (!g || !p) return fail(c, KMX_EINVAL, "%s: null grid or params", who);
+    if (!(p->r_fpfh > 0.0f) || !(p->r_normal > 0.0f) || p->r_normal > p->r_fpfh || !isfinite(p->r_fpfh))
+        return fail(c, KMX_EINVAL, "%s: need 0 < r_normal <= r_fpfh", who);
+    if (g->cell < p->r_fpfh) return fail(c, KMX_EINVAL, "%s: grid cell %g < r_fpfh %g", who, g->cell, p->r_fpfh);
+    if (p->hist_bins != 11) return fail(c, KMX_EINVAL, "%s: only 11 bins per feature are supported", who);
+    if (p->tau_num < 0 || !(p->tau_lin >= 0.0f)) return fail(c, KMX_EINVAL, "%s: bad thresholds", who);
+    if (g->ctx != c) return fail(c, KMX_EINVAL, "%s: grid belongs to another context", who);
+    return KMX_OK;
+}
+
+kmx_status kmx_normals(kmx_ctx* c, const kmx_grid* g, const kmx_params* p, float* d_normal4, uint8_t* d_flags,
+                       int64_t* d_nbr_offs, int32_t* d_nbr, int64_t nbr_cap, int64_t* d_needed)
+{
+    if (!c) return KMX_EINVAL;
+    kmx_status s = check_params(c, g, p, "kmx_normals");
+    if (s) return s;
+    if (!d_normal4 || !aligned16(d_normal4) || !d_flags || !d_nbr_offs || !d_needed || nbr_cap < 0)
+        return fail(c, KMX_EINVAL, "kmx_normals: bad argument");
+    DeviceGuard dg(c->device);
+    s = ensure_ws(c, kmx_normals_scratch_bytes(g->n_cap));
+    if (s) return s;
+    return launched(c,
+                    kmx_normals_launch(c, g, p, d_normal4, d_flags, d_nbr_offs, d_nbr, nbr_cap, d_needed, c->ws),
+                    "kmx_normals");
+}
+
+kmx_status kmx_fasterpfh(kmx_ctx* c, const kmx_grid* g, const kmx_params* p, const float* d_normal4,
+                         uint8_t* d_flags, const int64_t* d_nbr_offs, const int32_t* d_nbr, float* d_desc,
+                         int32_t* d_valid, int64_t* d_n_valid, float* d_spfh)
+{
+    if (!c) return KMX_EINVAL;
+    kmx_status s = check_params(c, g, p, "kmx_fasterpfh");
+    if (s) return s;
+    if (!d_normal4 || !aligned16(d_normal4) || !d_flags || !d_nbr_offs || !d_nbr || !d_desc || !aligned16(d_desc) ||
+        !d_valid || !d_n_valid || (d_spfh && !aligned16(d_spfh)))
+        return fail(c, KMX_EINVAL, "kmx_fasterpfh: bad argument");
+    DeviceGuard dg(c->device);
+    s = ensure_ws(c, kmx_fasterpfh_scratch_bytes(g->n_cap, d_spfh == nullptr));
+    if (s) return s;
+    return launched(c,
+                    kmx_fasterpfh_launch(c, g, p, d_normal4, d_flags, d_nbr_offs, d_nbr, d_desc, d_valid,
+                                         d_n_valid, d_spfh, c->ws),
+                    "kmx_fasterpfh");
+}
+
+kmx_status kmx_match(kmx_ctx* c, const float* d_desc_p, const int32_t* d_valid_p, int64_t np_cap,
+                     const int64_t* d_np, const float* d_desc_q, const int32_t* d_valid_q, int64_t nq_cap,
+                     const int64_t* d_nq, int32_t mode, kmx_corr* d_out, int64_t cap, int64_t* d_n_out)
+{
+    if (!c) return KMX_EINVAL;
+    if (np_cap < 0 || nq_cap < 0 || np_cap > INT32_MAX - 1 || nq_cap > INT32_MAX - 1 || cap < 0 || !d_n_out ||
+        (np_cap > 0 && (!d_desc_p || !aligned16(d_desc_p))) || (nq_cap > 0 && (!d_desc_q || !aligned16(d_desc_q))) ||
+        (cap > 0 && !d_out))
+        return fail(c, KMX_EINVAL, "kmx_match: bad argument");
+    if (mode != KMX_MATCH_FP32_EXACT && mode != KMX_MATCH_BF16_RERANK)
+        return fail(c, KMX_EINVAL, "kmx_match: unknown mode %d", mode);
+    DeviceGuard dg(c->device);
+    return launched(c,
+                    kmx_match_launch(c, d_desc_p, d_valid_p, np_cap, d_np, d_desc_q, d_valid_q, nq_cap, d_nq, mode,
+                                     d_out, cap, d_n_out, nullptr),
+                    "kmx_match");
+}
+
+}  // extern "C"
+
+// Matching dispatch (scratch is taken from the context here because the size
+// depends on the mode).
+cudaError_t kmx_match_launch(kmx_ctx* c, const float* dp, const int32_t* vp, int64_t np_cap, const int64_t* d_np,
+                             const float* dq, const int32_t* vq, int64_t nq_cap, const int64_t* d_nq, int mode,
+                             kmx_corr* out, int64_t cap, int64_t* n_out, void*)
+{
+    cudaStream_t st = c->stream;
+    if (np_cap == 0 || nq_cap == 0) {
+        return cudaMemsetAsync(n_out, 0, sizeof(int64_t), st);
+    }
+    if (mode == KMX_MATCH_FP32_EXACT) {
+        int chunks = 1;
+        const size_t bytes = kmx_match_fp32_scratch_bytes(np_cap, nq_cap, &chunks);
+        if (ensure_ws(c, bytes) != KMX_OK) return cudaErrorMemoryAllocation;
+        kmx::MatchScratch s = kmx::match_common_carve(c->ws, np_cap, nq_cap, chunks);
+        cudaError_t e = cudaMemsetAsync(s.colbest, 0xFF, sizeof(unsigned long long) * nq_cap, st);
+        if (e) return e;
+        if ((e = kmx_match_fp32_launch(c, dp, np_cap, d_np, dq, nq_cap, d_nq, s, chunks))) return e;
+        return kmx::match_finalize(c, s, chunks, np_cap, d_np, vp, vq, out, cap, n_out);
+    }
+    return cudaErrorNotSupported;
+}

@@ -1,0 +1,273 @@
+// Algorithm 1, step 2 and the Faster-PFH descriptors (App. A, Eqs. A2-A5).
+//
+//   valid_count  I_valid(q) = { i in M[q] : B[i] }; q in J iff B[q] and
+//                |I_valid(q)| >= tau_num (one pass on the step-1 flags)
+//   scan/scatter J in ascending point order
+//   spfh_kernel  Darboux-frame features (Eq. A2) of every pair (q, k),
+//                k in I_valid(q) \ {q}, binned (Eq. A3) into a per-warp
+//                shared-memory histogram and scaled by 100 / pairs (Eq. A4)
+//   fpfh_kernel  FPFH(q) = SPFH(q) + (1/m) sum_k SPFH(k) / w_k (Eq. A5), one
+//                warp per row, lane l owning bin l, compensated summation
+//
+// I_valid is never materialised: the SPFH and FPFH kernels walk M[q] and
+// skip entries without B (one byte gathered per neighbour).
+#include "kmx_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kH = 11;
+constexpr int kD = 3 * kH;  // 33
+constexpr int kStride = KMX_DESC_STRIDE;
+
+struct PfhScratch {
+    int32_t* jflag;  // [n+1]
+    int64_t* jpos;   // [n+1]
+    float* spfh;     // [n][36] when the caller passes none
+    void* scan;
+};
+
+PfhScratch carve(void* base, int64_t n, bool need_spfh, size_t* total)
+{
+    PfhScratch s{};
+    kmx_arena a{static_cast<char*>(base), 0};
+    s.jflag = (int32_t*)a.take(sizeof(int32_t) * (n + 1));
+    s.jpos = (int64_t*)a.take(sizeof(int64_t) * (n + 1));
+    s.spfh = need_spfh ? (float*)a.take(sizeof(float) * kStride * (n + 1)) : nullptr;
+    s.scan = a.take(kmx_scan_scratch_bytes(n));
+    *total = kmx_align_up(a.used, 256);
+    return s;
+}
+
+__global__ void __launch_bounds__(kThreads) valid_count(int64_t n_cap, const int64_t* d_n, uint8_t* flags,
+                                                        const int64_t* __restrict__ offs,
+                                                        const int32_t* __restrict__ nbr, int tau_num,
+                                                        int32_t* __restrict__ jflag)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    if (q >= kmx_count(d_n, n_cap)) return;
+    const uint8_t fq = flags[q];
+    int mv = 0;
+    if (fq & 1) {
+        const int64_t b = offs[q], e = offs[q + 1];
+        for (int64_t t = b + lane; t - lane < e; t += 32) {
+            bool ok = false;
+            if (t < e) ok = (flags[nbr[t]] & 1) != 0;  // bit0 is never written here
+            mv += __popc(__ballot_sync(kFull, ok));
+        }
+    }
+    if (lane == 0) {
+        const bool inJ = (fq & 1) && mv >= tau_num;
+        jflag[q] = inJ ? 1 : 0;
+        flags[q] = (uint8_t)((fq & ~2u) | (inJ ? 2u : 0u));
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) scatter_valid(int64_t n_cap, const int64_t* d_n,
+                                                          const int32_t* __restrict__ jflag,
+                                                          const int64_t* __restrict__ jpos,
+                                                          int32_t* __restrict__ valid, int64_t* n_valid)
+{
+    const int64_t q = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (q == 0) *n_valid = jpos[n_cap];
+    if (q >= kmx_count(d_n, n_cap)) return;
+    if (jflag[q]) valid[jpos[q]] = (int32_t)q;
+}
+
+__device__ __forceinline__ float dot3(float ax, float ay, float az, float bx, float by, float bz)
+{
+    return fmaf(az, bz, fmaf(ay, by, ax * bx));
+}
+
+// Angular features of the pair (q, k) (Eq. A2): the point whose normal is
+// closer to parallel with the connecting line is the source; v and w are unit
+// vectors.  Returns false for coincident points or |d x u| < 1e-6.
+__device__ __forceinline__ bool pair_features(float4 pq, float4 nq, float4 pk, float4 nk, float* f)
+{
+    float dx = pk.x - pq.x, dy = pk.y - pq.y, dz = pk.z - pq.z;
+    const float dd = dot3(dx, dy, dz, dx, dy, dz);
+    if (!(dd > 0.f)) return false;
+    const float inv = 1.0f / sqrtf(dd);
+    dx *= inv;
+    dy *= inv;
+    dz *= inv;
+    const float cq = fabsf(dot3(nq.x, nq.y, nq.z, dx, dy, dz));
+    const float ck = fabsf(dot3(nk.x, nk.y, nk.z, dx, dy, dz));
+    float4 u = nq, nb = nk;
+    if (!(cq >= ck)) {
+        u = nk;
+        nb = nq;
+        dx = -dx;
+        dy = -dy;
+        dz = -dz;
+    }
+    // v = d x u / |d x u|
+    float vx = dy * u.z - dz * u.y;
+    float vy = dz * u.x - dx * u.z;
+    float vz = dx * u.y - dy * u.x;
+    const float s = sqrtf(dot3(vx, vy, vz, vx, vy, vz));
+    if (s < 1e-6f) return false;
+    const float is = 1.0f / s;
+    vx *= is;
+    vy *= is;
+    vz *= is;
+    // w = u x v
+    const float wx = u.y * vz - u.z * vy;
+    const float wy = u.z * vx - u.x * vz;
+    const float wz = u.x * vy - u.y * vx;
+    f[0] = atan2f(dot3(wx, wy, wz, nb.x, nb.y, nb.z), dot3(u.x, u.y, u.z, nb.x, nb.y, nb.z));
+    f[1] = dot3(vx, vy, vz, nb.x, nb.y, nb.z);
+    f[2] = dot3(u.x, u.y, u.z, dx, dy, dz);
+    return true;
+}
+
+// 0-based bin (Eq. A3) with the upper end clamped to H-1.
+__device__ __forceinline__ int feature_bin(float f, float lo, float hi)
+{
+    float t = floorf((float)kH * (f - lo) / (hi - lo));
+    t = fminf(fmaxf(t, 0.f), (float)(kH - 1));
+    return (int)t;
+}
+
+__global__ void __launch_bounds__(kThreads) spfh_kernel(int64_t n_cap, const int64_t* d_n,
+                                                        const float4* __restrict__ pts,
+                                                        const float4* __restrict__ normal4,
+                                                        const uint8_t* __restrict__ flags,
+                                                        const int64_t* __restrict__ offs,
+                                                        const int32_t* __restrict__ nbr, float* __restrict__ spfh)
+{
+    __shared__ int hist[kWarps][kStride];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t q = (int64_t)blockIdx.x * kWarps + warp;
+    if (q >= kmx_count(d_n, n_cap)) return;
+    float* row = spfh + q * kStride;
+    const uint8_t fq = flags[q];
+    if (!(fq & 1)) {
+        row[lane] = 0.f;
+        if (lane < kStride - 32) row[32 + lane] = 0.f;
+        return;
+    }
+    hist[warp][lane] = 0;
+    if (lane < kStride - 32) hist[warp][32 + lane] = 0;
+    __syncwarp();
+    const float4 pq = pts[q];
+    const float4 nq = normal4[q];
+    const float PI = 3.14159265358979f;
+    const int64_t b = offs[q], e = offs[q + 1];
+    int pairs = 0;
+    for (int64_t t = b + lane; t - lane < e; t += 32) {
+        bool ok = false;
+        if (t < e) {
+            const int k = nbr[t];
+            if (k != q && (__ldg(&flags[k]) & 1)) {
+                float f[3];
+                ok = pair_features(pq, nq, __ldg(&pts[k]), __ldg(&normal4[k]), f);
+                if (ok) {
+                    atomicAdd(&hist[warp][feature_bin(f[0], -PI, PI)], 1);
+                    atomicAdd(&hist[warp][kH + feature_bin(f[1], -1.f, 1.f)], 1);
+                    atomicAdd(&hist[warp][2 * kH + feature_bin(f[2], -1.f, 1.f)], 1);
+                }
+            }
+        }
+        pairs += __popc(__ballot_sync(kFull, ok));
+    }
+    __syncwarp();
+    const float scale = pairs > 0 ? 100.0f / (float)pairs : 0.f;
+    row[lane] = (float)hist[warp][lane] * scale;
+    if (lane < kStride - 32) row[32 + lane] = lane == 0 ? (float)hist[warp][32] * scale : 0.f;
+}
+
+__device__ __forceinline__ void kahan_add(float& sum, float& comp, float term)
+{
+    const float y = term - comp;
+    const float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+__global__ void __launch_bounds__(kThreads) fpfh_kernel(int64_t n_cap, const int32_t* __restrict__ valid,
+                                                        const int64_t* __restrict__ n_valid,
+                                                        const float4* __restrict__ pts,
+                                                        const uint8_t* __restrict__ flags,
+                                                        const int64_t* __restrict__ offs,
+                                                        const int32_t* __restrict__ nbr,
+                                                        const float* __restrict__ spfh, float* __restrict__ desc)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    if (j >= min(*n_valid, n_cap)) return;
+    const int q = valid[j];
+    const float4 pq = pts[q];
+    float acc = 0.f, comp = 0.f, acc32 = 0.f, comp32 = 0.f;
+    int m = 0;
+    const int64_t b = offs[q], e = offs[q + 1];
+    for (int64_t t = b + lane; t - lane < e; t += 32) {
+        int k = -1;
+        float w = 0.f;
+        if (t < e) {
+            const int kk = nbr[t];
+            if (kk != q && (__ldg(&flags[kk]) & 1)) {
+                const float4 pk = __ldg(&pts[kk]);
+                const float dx = pk.x - pq.x, dy = pk.y - pq.y, dz = pk.z - pq.z;
+                const float d2 = dot3(dx, dy, dz, dx, dy, dz);
+                if (d2 > 0.f) {
+                    k = kk;
+                    w = 1.0f / sqrtf(d2);
+                }
+            }
+        }
+        unsigned bal = __ballot_sync(kFull, k >= 0);
+        m += __popc(bal);
+        while (bal) {
+            const int src = __ffs(bal) - 1;
+            bal &= bal - 1u;
+            const int ke = __shfl_sync(kFull, k, src);
+            const float we = __shfl_sync(kFull, w, src);
+            const float* r = spfh + (int64_t)ke * kStride;
+            kahan_add(acc, comp, __ldg(&r[lane]) * we);
+            if (lane == 0) kahan_add(acc32, comp32, __ldg(&r[32]) * we);
+        }
+    }
+    const float* rq = spfh + (int64_t)q * kStride;
+    const float invm = m > 0 ? 1.0f / (float)m : 0.f;
+    float* out = desc + j * kStride;
+    out[lane] = rq[lane] + acc * invm;
+    if (lane < kStride - 32) out[32 + lane] = lane == 0 ? rq[32] + acc32 * invm : 0.f;
+}
+
+}  // namespace
+
+size_t kmx_fasterpfh_scratch_bytes(int64_t n_cap, bool need_spfh)
+{
+    size_t total = 0;
+    carve(nullptr, n_cap, need_spfh, &total);
+    return total;
+}
+
+cudaError_t kmx_fasterpfh_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_params* prm, const float* normal4,
+                                 uint8_t* flags, const int64_t* offs, const int32_t* nbr, float* desc,
+                                 int32_t* valid, int64_t* n_valid, float* spfh, void* scratch)
+{
+    cudaStream_t st = ctx->stream;
+    size_t total = 0;
+    PfhScratch s = carve(scratch, g->n_cap, spfh == nullptr, &total);
+    float* sp = spfh ? spfh : s.spfh;
+    const int64_t n = g->n_cap;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(s.jflag, 0, sizeof(int32_t) * (n + 1), st))) return e;
+    const unsigned nbw = kmx_blocks(n, kWarps);
+    KMX_COUNT_LAUNCH();
+    valid_count<<<nbw, kThreads, 0, st>>>(n, g->d_n, flags, offs, nbr, prm->tau_num, s.jflag);
+    if ((e = kmx_scan_i32(s.jflag, n, g->d_n, s.jpos, s.scan, st))) return e;
+    KMX_COUNT_LAUNCH();
+    scatter_valid<<<kmx_blocks(n, kThreads), kThreads, 0, st>>>(n, g->d_n, s.jflag, s.jpos, valid, n_valid);
+    KMX_COUNT_LAUNCH();
+    spfh_kernel<<<nbw, kThreads, 0, st>>>(n, g->d_n, g->pts, reinterpret_cast<const float4*>(normal4), flags,
+                                          offs, nbr, sp);
+    KMX_COUNT_LAUNCH();
+    fpfh_kernel<<<nbw, kThreads, 0, st>>>(n, valid, n_valid, g->pts, flags, offs, nbr, sp, desc);
+    return cudaGetLastError();
+}

@@ -1,0 +1,179 @@
+// Internal declarations shared by the kmx CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "kmx.h"
+
+// Process-wide count of kernels launched by the library (kmx_launch_count).
+extern std::atomic<long long> kmx_g_launches;
+#define KMX_COUNT_LAUNCH() kmx_g_launches.fetch_add(1, std::memory_order_relaxed)
+
+// Device-side error bits, accumulated with atomicOr into kmx_ctx::d_err.
+enum : unsigned int {
+    KMX_DERR_RANGE = 1u,
+    KMX_DERR_CAPACITY = 2u,
+    KMX_DERR_HASHFULL = 4u,
+    KMX_DERR_TIMEOUT = 8u,
+};
+
+struct kmx_ctx {
+    int device;
+    cudaStream_t stream;
+    void* ws;              // scratch, stream-ordered allocation
+    size_t ws_size;
+    unsigned int* d_err;   // device error bits
+    unsigned int* h_err;   // pinned host mirror for kmx_sync
+    int sm_count;
+    char msg[256];
+};
+
+struct kmx_grid {
+    kmx_ctx* ctx;           // compared, never dereferenced after kmx_destroy
+    int device;             // device and stream the grid memory belongs to
+    cudaStream_t stream;
+    int64_t n_cap;
+    const int64_t* d_n;     // actual count (caller's cell or grid-owned copy)
+    float cell;
+    double inv_cell;        // 1 / (cell * (1 + KMX_CELL_MARGIN))
+    int64_t* d_n_sorted;    // points actually bucketed (device)
+    uint32_t table_size;    // power of two
+    unsigned long long* keys;  // [table_size] packed cell keys, ~0 = empty
+    int2* cells;            // [table_size] (start, count) in sorted order
+    float4* sorted;         // [n_cap] points in cell order, w = original index (int bits)
+    const float4* pts;      // caller's points in original order
+    int64_t* d_n_own;       // grid-owned count when the caller passed none
+    void* mem;
+};
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+
+#define KMX_EMPTY_KEY 0xFFFFFFFFFFFFFFFFull
+#define KMX_KEY_BIAS 1048576  // 2^20: 21-bit fields hold indices in (-2^20, 2^20)
+
+// MurmurHash3 64-bit finaliser (public domain), used to spread packed keys.
+__device__ __forceinline__ uint32_t kmx_hash64(unsigned long long k)
+{
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return (uint32_t)k;
+}
+
+__device__ __forceinline__ unsigned long long kmx_pack_key(int kx, int ky, int kz)
+{
+    return ((unsigned long long)(uint32_t)(kx + KMX_KEY_BIAS) << 42) |
+           ((unsigned long long)(uint32_t)(ky + KMX_KEY_BIAS) << 21) |
+           (unsigned long long)(uint32_t)(kz + KMX_KEY_BIAS);
+}
+
+// Open-addressing insert with linear probing; returns the slot or -1 when the
+// table is full (at most table_size probes, so the loop always ends).
+__device__ __forceinline__ int kmx_hash_insert(unsigned long long* keys, uint32_t size, unsigned long long key)
+{
+    uint32_t mask = size - 1u;
+    uint32_t h = kmx_hash64(key) & mask;
+    for (uint32_t probe = 0; probe < size; ++probe) {
+        unsigned long long prev = atomicCAS(&keys[h], KMX_EMPTY_KEY, key);
+        if (prev == KMX_EMPTY_KEY || prev == key) return (int)h;
+        h = (h + 1u) & mask;
+    }
+    return -1;
+}
+
+// Lookup; returns the slot or -1 if the key is absent.
+__device__ __forceinline__ int kmx_hash_find(const unsigned long long* __restrict__ keys, uint32_t size,
+                                             unsigned long long key)
+{
+    uint32_t mask = size - 1u;
+    uint32_t h = kmx_hash64(key) & mask;
+    for (uint32_t probe = 0; probe < size; ++probe) {
+        unsigned long long k = __ldg(&keys[h]);
+        if (k == key) return (int)h;
+        if (k == KMX_EMPTY_KEY) return -1;
+        h = (h + 1u) & mask;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ int64_t kmx_count(const int64_t* d_n, int64_t cap)
+{
+    if (!d_n) return cap;
+    int64_t n = *d_n;
+    return n < cap ? n : cap;
+}
+
+__device__ __forceinline__ void kmx_raise(unsigned int* err, unsigned int bit)
+{
+    atomicOr(err, bit);
+}
+
+// ---------------------------------------------------------------------------
+// host-side launch helpers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+
+static inline unsigned int kmx_blocks(int64_t n, int threads)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    return (unsigned int)b;
+}
+
+static inline size_t kmx_align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Bump allocator over the context scratch.  With base == nullptr it only
+// measures (every pointer it returns is null and `used` is the total).
+struct kmx_arena {
+    char* base;
+    size_t used;
+    void* take(size_t bytes)
+    {
+        used = kmx_align_up(used, 256);
+        size_t off = used;
+        used += bytes;
+        return base ? static_cast<void*>(base + off) : nullptr;
+    }
+};
+
+// scan.cu: exclusive prefix sum of n int32 values (values at i >= *d_n count
+// as 0) into out[0..n] (int64, out[n] = total).  Scratch bytes needed:
+size_t kmx_scan_scratch_bytes(int64_t n);
+cudaError_t kmx_scan_i32(const int32_t* in, int64_t n, const int64_t* d_n, int64_t* out, void* scratch,
+                         cudaStream_t s);
+
+// voxel.cu
+size_t kmx_voxelize_scratch_bytes(int64_t n_raw);
+cudaError_t kmx_voxelize_launch(kmx_ctx* ctx, const float* xyz, int64_t n_raw, int stride, float v, float* out4,
+                                int64_t cap, int64_t* n_out, int32_t* assign, void* scratch);
+
+// grid.cu
+size_t kmx_grid_bytes(int64_t n_cap, uint32_t* table_size);
+size_t kmx_grid_scratch_bytes(int64_t n_cap, uint32_t table_size);
+cudaError_t kmx_grid_build_launch(kmx_ctx* ctx, kmx_grid* g, void* scratch);
+
+// normals.cu
+size_t kmx_normals_scratch_bytes(int64_t n_cap);
+cudaError_t kmx_normals_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_params* p, float* normal4,
+                               uint8_t* flags, int64_t* offs, int32_t* nbr, int64_t nbr_cap, int64_t* needed,
+                               void* scratch);
+
+// fpfh.cu
+size_t kmx_fasterpfh_scratch_bytes(int64_t n_cap, bool need_spfh);
+cudaError_t kmx_fasterpfh_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_params* p, const float* normal4,
+                                 uint8_t* flags, const int64_t* offs, const int32_t* nbr, float* desc,
+                                 int32_t* valid, int64_t* n_valid, float* spfh, void* scratch);
+
+// match_fp32.cu / match_tc.cu
+size_t kmx_match_scratch_bytes(int64_t np_cap, int64_t nq_cap, int mode);
+cudaError_t kmx_match_launch(kmx_ctx* ctx, const float* dp, const int32_t* vp, int64_t np_cap,
+                             const int64_t* d_np, const float* dq, const int32_t* vq, int64_t nq_cap,
+                             const int64_t* d_nq, int mode, kmx_corr* out, int64_t cap, int64_t* n_out,
+                             void* scratch);

@@ -1,0 +1,70 @@
+// Pieces shared by the FP32 and the tensor-core matching paths.
+#pragma once
+
+#include "kmx_internal.cuh"
+
+namespace kmx {
+
+// Best and second-best squared distance of one row, with the column of the
+// best (ties to the lower column).
+struct RowBest {
+    float d1;
+    int j1;
+    float d2;
+};
+
+__device__ __forceinline__ void row_update(float& b1, int& j1, float& b2, float d, int j)
+{
+    if (d < b1 || (d == b1 && j < j1)) {
+        b2 = b1;
+        b1 = d;
+        j1 = j;
+    } else if (d < b2) {
+        b2 = d;
+    }
+}
+
+// Merge another (disjoint-column) summary into (d1, j1, d2).
+__device__ __forceinline__ void row_merge(float& d1, int& j1, float& d2, float od1, int oj, float od2)
+{
+    if (od1 < d1 || (od1 == d1 && oj < j1)) {
+        d2 = fminf(d1, od2);
+        d1 = od1;
+        j1 = oj;
+    } else {
+        d2 = fminf(d2, od1);
+    }
+}
+
+// Non-negative float distance in the high word, index in the low word: the
+// unsigned order is (distance, index) lexicographic.
+__device__ __forceinline__ unsigned long long pack_dist_index(float d, uint32_t idx)
+{
+    return ((unsigned long long)__float_as_uint(d) << 32) | idx;
+}
+
+struct MatchScratch {
+    RowBest* part;                // [chunks][np_cap]
+    unsigned long long* colbest;  // [nq_cap] packed (distance, row)
+    int32_t* mflag;               // [np_cap + 1]
+    int64_t* mpos;                // [np_cap + 1]
+    RowBest* merged;              // [np_cap] merged row summaries
+    void* scan;
+    void* extra;                  // path-specific scratch
+};
+
+size_t match_common_bytes(int64_t np_cap, int64_t nq_cap, int chunks, size_t extra = 0);
+MatchScratch match_common_carve(void* base, int64_t np_cap, int64_t nq_cap, int chunks, size_t extra = 0);
+
+// Merge the row partials, apply the reciprocity test and emit A in ascending
+// source row.
+cudaError_t match_finalize(kmx_ctx* ctx, const MatchScratch& s, int chunks, int64_t np_cap, const int64_t* d_np,
+                           const int32_t* vp, const int32_t* vq, kmx_corr* out, int64_t cap, int64_t* n_out);
+
+}  // namespace kmx
+
+// match_fp32.cu
+size_t kmx_match_fp32_scratch_bytes(int64_t np_cap, int64_t nq_cap, int* chunks);
+cudaError_t kmx_match_fp32_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, const int64_t* d_np,
+                                  const float* dq, int64_t nq_cap, const int64_t* d_nq, kmx::MatchScratch& s,
+                                  int chunks);

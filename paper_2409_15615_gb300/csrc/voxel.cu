@@ -1,0 +1,207 @@
+// Voxel downsampling (the voxelised clouds of Sec. III-A).
+//
+// Sort-free design: a device hash table maps packed voxel keys to slots; the
+// lowest input index of each voxel (atomicMin) fixes the output order ("order
+// of first member"), a prefix sum over first-member flags numbers the voxels,
+// a counting scatter groups members per voxel, and each voxel's members are
+// put back in input order before the FP64 centroid sum, so the result does not
+// depend on atomic ordering.
+#include "kmx_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+struct VoxScratch {
+    unsigned long long* keys;  // [T]
+    int32_t* vmin;             // [T] lowest member index
+    int32_t* vcnt;             // [T] member count
+    int32_t* vout;             // [T] output voxel index
+    int32_t* pslot;            // [n] slot of each point
+    int32_t* flag;             // [n] first-member flag, later member count per output voxel
+    int64_t* oidx;             // [n+1] exclusive scan of flags
+    int64_t* vstart;           // [n+1] member offsets per output voxel
+    int32_t* cursor;           // [n] fill cursor per output voxel
+    int32_t* members;          // [n] grouped members (arbitrary order inside a voxel)
+    int32_t* sorted;           // [n] grouped members in input order
+    void* scan;
+    uint32_t T;
+};
+
+uint32_t table_size_for(int64_t n)
+{
+    uint64_t t = 1024;
+    while (t < (uint64_t)(2 * n)) t <<= 1;
+    return (uint32_t)t;
+}
+
+VoxScratch carve(void* base, int64_t n, size_t* total)
+{
+    VoxScratch s{};
+    kmx_arena a{static_cast<char*>(base), 0};
+    s.T = table_size_for(n);
+    auto take = [&](size_t b) { return a.take(b); };
+    s.keys = (unsigned long long*)take(sizeof(unsigned long long) * s.T);
+    s.vmin = (int32_t*)take(sizeof(int32_t) * s.T);
+    s.vcnt = (int32_t*)take(sizeof(int32_t) * s.T);
+    s.vout = (int32_t*)take(sizeof(int32_t) * s.T);
+    s.pslot = (int32_t*)take(sizeof(int32_t) * (n + 1));
+    s.flag = (int32_t*)take(sizeof(int32_t) * (n + 1));
+    s.oidx = (int64_t*)take(sizeof(int64_t) * (n + 1));
+    s.vstart = (int64_t*)take(sizeof(int64_t) * (n + 1));
+    s.cursor = (int32_t*)take(sizeof(int32_t) * (n + 1));
+    s.members = (int32_t*)take(sizeof(int32_t) * (n + 1));
+    s.sorted = (int32_t*)take(sizeof(int32_t) * (n + 1));
+    s.scan = take(kmx_scan_scratch_bytes(n));
+    *total = kmx_align_up(a.used, 256);
+    return s;
+}
+
+// floor(x / v) with the quotient rounded once in FP64 (IEEE division).
+__device__ __forceinline__ bool voxel_index(float x, double v, int* k)
+{
+    double q = floor(__ddiv_rn((double)x, v));
+    if (!(fabs(q) < 1048576.0)) return false;
+    *k = (int)q;
+    return true;
+}
+
+__global__ void __launch_bounds__(kThreads) vox_insert(const float* __restrict__ xyz, int64_t n, int stride,
+                                                       double v, VoxScratch s, unsigned int* err)
+{
+    int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (r >= n) return;
+    const float* p = xyz + r * stride;
+    int kx, ky, kz;
+    bool ok = voxel_index(p[0], v, &kx) & voxel_index(p[1], v, &ky) & voxel_index(p[2], v, &kz);
+    if (!ok) {
+        kmx_raise(err, KMX_DERR_RANGE);
+        s.pslot[r] = -1;
+        return;
+    }
+    int slot = kmx_hash_insert(s.keys, s.T, kmx_pack_key(kx, ky, kz));
+    s.pslot[r] = slot;
+    if (slot < 0) {
+        kmx_raise(err, KMX_DERR_HASHFULL);
+        return;
+    }
+    atomicMin(&s.vmin[slot], (int32_t)r);
+    atomicAdd(&s.vcnt[slot], 1);
+}
+
+__global__ void __launch_bounds__(kThreads) vox_first_flag(int64_t n, VoxScratch s)
+{
+    int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (r >= n) return;
+    int slot = s.pslot[r];
+    s.flag[r] = (slot >= 0 && s.vmin[slot] == (int32_t)r) ? 1 : 0;
+}
+
+// For each first member: number its voxel, record the member count per output
+// voxel (reusing `flag` as the count array), publish the voxel count.
+__global__ void __launch_bounds__(kThreads) vox_number(int64_t n, VoxScratch s, int64_t cap, int64_t* n_out,
+                                                       unsigned int* err)
+{
+    int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (r == 0) {
+        int64_t tot = s.oidx[n];
+        *n_out = tot;
+        if (tot > cap) kmx_raise(err, KMX_DERR_CAPACITY);
+    }
+    if (r >= n) return;
+    if (s.oidx[r + 1] == s.oidx[r]) return;  // not a first member
+    int slot = s.pslot[r];
+    int64_t o = s.oidx[r];
+    s.vout[slot] = (int32_t)o;
+    s.cursor[o] = s.vcnt[slot];  // temporarily: count per output voxel
+}
+
+__global__ void __launch_bounds__(kThreads) vox_scatter(int64_t n, VoxScratch s, int32_t* __restrict__ assign)
+{
+    int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (r >= n) return;
+    int slot = s.pslot[r];
+    if (slot < 0) return;
+    int32_t o = s.vout[slot];
+    if (assign) assign[r] = o;
+    int pos = atomicAdd(&s.cursor[o], 1);
+    s.members[s.vstart[o] + pos] = (int32_t)r;
+}
+
+// One warp per output voxel: restore input order of the members (rank of each
+// member = number of smaller members; members are distinct), then sum in FP64
+// in that order and divide by the count.
+__global__ void __launch_bounds__(kThreads) vox_centroid(const float* __restrict__ xyz, int stride, int64_t n,
+                                                         VoxScratch s, float4* __restrict__ out, int64_t cap)
+{
+    int64_t o = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    int64_t nv = s.oidx[n];
+    if (o >= nv || o >= cap) return;
+    int64_t b = s.vstart[o];
+    int L = (int)(s.vstart[o + 1] - b);
+    const int32_t* mem = s.members + b;
+    int32_t* srt = s.sorted + b;
+    for (int e = lane; e < L; e += 32) {
+        int32_t me = mem[e];
+        int rank = 0;
+        for (int f = 0; f < L; ++f) rank += (mem[f] < me);
+        srt[rank] = me;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        double sx = 0.0, sy = 0.0, sz = 0.0;
+        for (int e = 0; e < L; ++e) {
+            const float* p = xyz + (int64_t)srt[e] * stride;
+            sx = __dadd_rn(sx, (double)p[0]);
+            sy = __dadd_rn(sy, (double)p[1]);
+            sz = __dadd_rn(sz, (double)p[2]);
+        }
+        double c = (double)L;
+        out[o] = make_float4(__double2float_rn(__ddiv_rn(sx, c)), __double2float_rn(__ddiv_rn(sy, c)),
+                             __double2float_rn(__ddiv_rn(sz, c)), 0.0f);
+    }
+}
+
+}  // namespace
+
+size_t kmx_voxelize_scratch_bytes(int64_t n_raw)
+{
+    size_t total = 0;
+    carve(nullptr, n_raw, &total);
+    return total;
+}
+
+cudaError_t kmx_voxelize_launch(kmx_ctx* ctx, const float* xyz, int64_t n, int stride, float v, float* out4,
+                                int64_t cap, int64_t* n_out, int32_t* assign, void* scratch)
+{
+    cudaStream_t st = ctx->stream;
+    size_t total = 0;
+    VoxScratch s = carve(scratch, n, &total);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(s.keys, 0xFF, sizeof(unsigned long long) * s.T, st))) return e;
+    if ((e = cudaMemsetAsync(s.vmin, 0x7F, sizeof(int32_t) * s.T, st))) return e;
+    if ((e = cudaMemsetAsync(s.vcnt, 0, sizeof(int32_t) * s.T, st))) return e;
+    if (n == 0) {
+        return cudaMemsetAsync(n_out, 0, sizeof(int64_t), st);
+    }
+    unsigned nb = kmx_blocks(n, kThreads);
+    KMX_COUNT_LAUNCH();
+    vox_insert<<<nb, kThreads, 0, st>>>(xyz, n, stride, (double)v, s, ctx->d_err);
+    KMX_COUNT_LAUNCH();
+    vox_first_flag<<<nb, kThreads, 0, st>>>(n, s);
+    if ((e = kmx_scan_i32(s.flag, n, nullptr, s.oidx, s.scan, st))) return e;
+    if ((e = cudaMemsetAsync(s.cursor, 0, sizeof(int32_t) * (n + 1), st))) return e;
+    KMX_COUNT_LAUNCH();
+    vox_number<<<nb, kThreads, 0, st>>>(n, s, cap, n_out, ctx->d_err);
+    // member offsets per output voxel: scan of the counts parked in `cursor`
+    if ((e = cudaMemcpyAsync(s.flag, s.cursor, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st))) return e;
+    if ((e = kmx_scan_i32(s.flag, n, n_out, s.vstart, s.scan, st))) return e;
+    if ((e = cudaMemsetAsync(s.cursor, 0, sizeof(int32_t) * (n + 1), st))) return e;
+    KMX_COUNT_LAUNCH();
+    vox_scatter<<<nb, kThreads, 0, st>>>(n, s, assign);
+    KMX_COUNT_LAUNCH();
+    vox_centroid<<<kmx_blocks(n * 32, kThreads), kThreads, 0, st>>>(xyz, stride, n, s,
+                                                                    reinterpret_cast<float4*>(out4), cap);
+    return cudaGetLastError();
+}

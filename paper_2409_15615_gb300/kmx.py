@@ -1,0 +1,246 @@
+"""Thin Python binding of the kmx C ABI (``include/kmx.h``).
+
+Argument marshalling only: torch tensors provide device memory and the CUDA
+stream, every computation runs in the CUDA kernels of ``libkmx.so``.  The
+library must have been built (``paper_2409_15615_gb300.build``); importing
+this module without it raises, there is no CPU fallback.
+
+Function names follow the C entry points: ``voxelize``, ``build_grid``,
+``normals``, ``fasterpfh``, ``match``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import weakref
+
+import torch
+
+from . import build as _build
+
+_LIB = None
+
+KMX_OK, KMX_EINVAL, KMX_ENOMEM, KMX_ECUDA, KMX_ERANGE, KMX_ECAPACITY, KMX_ETIMEOUT, KMX_EBUSY = range(8)
+MATCH_FP32_EXACT = 0
+MATCH_BF16_RERANK = 1
+DESC_DIM = 33
+DESC_STRIDE = 36
+
+_STATUS_NAMES = {0: "KMX_OK", 1: "KMX_EINVAL", 2: "KMX_ENOMEM", 3: "KMX_ECUDA", 4: "KMX_ERANGE",
+                 5: "KMX_ECAPACITY", 6: "KMX_ETIMEOUT", 7: "KMX_EBUSY"}
+
+
+class KmxError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (_STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+class Params(C.Structure):
+    """kmx_params (Sec. III-C / IV-B parameters)."""
+    _fields_ = [("voxel", C.c_float), ("r_normal", C.c_float), ("r_fpfh", C.c_float), ("tau_num", C.c_int32),
+                ("tau_lin", C.c_float), ("hist_bins", C.c_int32), ("viewpoint", C.c_float * 3)]
+
+
+class Corr(C.Structure):
+    _fields_ = [("i", C.c_int32), ("j", C.c_int32), ("d1", C.c_float), ("d2", C.c_float)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def library():
+    """Load libkmx.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError("libkmx.so is not built (run paper_2409_15615_gb300.build.build()); "
+                          "the kmx front end has no CPU fallback")
+    lib = C.CDLL(path)
+    vp, i64, i32, f32 = C.c_void_p, C.c_int64, C.c_int32, C.c_float
+    sig = {
+        "kmx_params_default": (C.c_int, [f32, C.POINTER(Params)]),
+        "kmx_create": (C.c_int, [C.POINTER(vp), C.c_int, vp]),
+        "kmx_destroy": (None, [vp]),
+        "kmx_set_stream": (C.c_int, [vp, vp]),
+        "kmx_reserve": (C.c_int, [vp, i64]),
+        "kmx_sync": (C.c_int, [vp]),
+        "kmx_last_error": (C.c_char_p, [vp]),
+        "kmx_launch_count": (C.c_int64, []),
+        "kmx_voxelize": (C.c_int, [vp, vp, i64, i32, f32, vp, i64, vp, vp]),
+        "kmx_build_grid": (C.c_int, [vp, vp, i64, vp, f32, C.POINTER(vp)]),
+        "kmx_grid_free": (None, [vp]),
+        "kmx_normals": (C.c_int, [vp, vp, C.POINTER(Params), vp, vp, vp, vp, i64, vp]),
+        "kmx_fasterpfh": (C.c_int, [vp, vp, C.POINTER(Params), vp, vp, vp, vp, vp, vp, vp, vp]),
+        "kmx_match": (C.c_int, [vp, vp, vp, i64, vp, vp, vp, i64, vp, i32, vp, i64, vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def params_default(voxel: float, viewpoint=(0.0, 0.0, 0.0)) -> Params:
+    p = Params()
+    st = library().kmx_params_default(float(voxel), C.byref(p))
+    if st:
+        raise KmxError(st, "kmx_params_default(%r)" % voxel)
+    for a in range(3):
+        p.viewpoint[a] = float(viewpoint[a])
+    return p
+
+
+class Grid:
+    """Owner of a kmx_grid handle (keeps its point tensor alive)."""
+
+    def __init__(self, ctx, handle, points, n_cap, d_n, cell):
+        self.ctx, self.handle, self.points, self.n_cap, self.d_n, self.cell = ctx, handle, points, n_cap, d_n, cell
+
+    def free(self):
+        if self.handle:
+            library().kmx_grid_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Context:
+    """A kmx context bound to one device and (by default) the current torch
+    stream of that device."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        self.lib = library()
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = C.c_void_p()
+        st = self.lib.kmx_create(C.byref(h), device, C.c_void_p(self.stream.cuda_stream))
+        if st:
+            raise KmxError(st, "kmx_create(device=%d)" % device)
+        self.h = h
+        self._grids = weakref.WeakSet()
+
+    def close(self):
+        """Free this context's grids, then the context itself."""
+        if getattr(self, "h", None):
+            for g in list(self._grids):
+                g.free()
+            self.lib.kmx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        self.stream = stream
+        self._check(self.lib.kmx_set_stream(self.h, C.c_void_p(stream.cuda_stream)), "kmx_set_stream")
+
+    def _check(self, st, what):
+        if st:
+            raise KmxError(st, "%s: %s" % (what, self.lib.kmx_last_error(self.h).decode()))
+
+    def reserve(self, nbytes: int):
+        self._check(self.lib.kmx_reserve(self.h, int(nbytes)), "kmx_reserve")
+
+    def sync(self):
+        """Wait for the stream; raise the first device-side error."""
+        self._check(self.lib.kmx_sync(self.h), "kmx_sync")
+
+    def _scalar(self):
+        return torch.zeros(1, dtype=torch.int64, device=self.device)
+
+    # -- stages -----------------------------------------------------------
+
+    def voxelize(self, xyz: torch.Tensor, voxel: float, cap: int | None = None, out4=None, n_out=None,
+                 assign=None):
+        """kmx_voxelize.  Returns (out4 [cap, 4], n_out device int64[1], assign|None)."""
+        n, stride = xyz.shape
+        cap = n if cap is None else cap
+        out4 = torch.empty((max(cap, 1), 4), dtype=torch.float32, device=self.device) if out4 is None else out4
+        n_out = self._scalar() if n_out is None else n_out
+        if assign is True:
+            assign = torch.empty(max(n, 1), dtype=torch.int32, device=self.device)
+        elif assign is False:
+            assign = None
+        self._check(self.lib.kmx_voxelize(self.h, _ptr(xyz), n, stride, float(voxel), _ptr(out4), cap, _ptr(n_out),
+                                          _ptr(assign)), "kmx_voxelize")
+        return out4, n_out, assign
+
+    def build_grid(self, xyz4: torch.Tensor, cell: float, n_cap: int | None = None, d_n=None) -> Grid:
+        n_cap = xyz4.shape[0] if n_cap is None else n_cap
+        h = C.c_void_p()
+        self._check(self.lib.kmx_build_grid(self.h, _ptr(xyz4), n_cap, _ptr(d_n), float(cell), C.byref(h)),
+                    "kmx_build_grid")
+        g = Grid(self, h, xyz4, n_cap, d_n, cell)
+        self._grids.add(g)
+        return g
+
+    def normals(self, grid: Grid, params: Params, nbr_cap: int, out=None):
+        """kmx_normals.  Returns dict(normal4, flags, offs, nbr, needed)."""
+        n = grid.n_cap
+        o = out or {}
+        normal4 = o.get("normal4", torch.empty((max(n, 1), 4), dtype=torch.float32, device=self.device))
+        flags = o.get("flags", torch.empty(max(n, 1), dtype=torch.uint8, device=self.device))
+        offs = o.get("offs", torch.empty(n + 1, dtype=torch.int64, device=self.device))
+        nbr = o.get("nbr", torch.empty(max(nbr_cap, 1), dtype=torch.int32, device=self.device)) if nbr_cap else None
+        needed = o.get("needed", self._scalar())
+        self._check(self.lib.kmx_normals(self.h, grid.handle, C.byref(params), _ptr(normal4), _ptr(flags), _ptr(offs),
+                                         _ptr(nbr), int(nbr_cap), _ptr(needed)), "kmx_normals")
+        return dict(normal4=normal4, flags=flags, offs=offs, nbr=nbr, needed=needed)
+
+    def fasterpfh(self, grid: Grid, params: Params, normal4, flags, offs, nbr, want_spfh=False, out=None):
+        """kmx_fasterpfh.  Returns dict(desc, valid, n_valid, spfh)."""
+        n = grid.n_cap
+        o = out or {}
+        desc = o.get("desc", torch.empty((max(n, 1), DESC_STRIDE), dtype=torch.float32, device=self.device))
+        valid = o.get("valid", torch.empty(max(n, 1), dtype=torch.int32, device=self.device))
+        n_valid = o.get("n_valid", self._scalar())
+        spfh = None
+        if want_spfh:
+            spfh = o.get("spfh", torch.empty((max(n, 1), DESC_STRIDE), dtype=torch.float32, device=self.device))
+        self._check(self.lib.kmx_fasterpfh(self.h, grid.handle, C.byref(params), _ptr(normal4), _ptr(flags),
+                                           _ptr(offs), _ptr(nbr), _ptr(desc), _ptr(valid), _ptr(n_valid),
+                                           _ptr(spfh)), "kmx_fasterpfh")
+        return dict(desc=desc, valid=valid, n_valid=n_valid, spfh=spfh)
+
+    def match(self, desc_p, valid_p, np_cap, desc_q, valid_q, nq_cap, d_np=None, d_nq=None,
+              mode=MATCH_FP32_EXACT, cap=None, out=None, n_out=None):
+        """kmx_match.  Returns (corr int32 tensor [cap, 4] viewing kmx_corr rows, n_out)."""
+        cap = min(np_cap, nq_cap) if cap is None else cap
+        out = torch.empty((max(cap, 1), 4), dtype=torch.int32, device=self.device) if out is None else out
+        n_out = self._scalar() if n_out is None else n_out
+        self._check(self.lib.kmx_match(self.h, _ptr(desc_p), _ptr(valid_p), int(np_cap), _ptr(d_np), _ptr(desc_q),
+                                       _ptr(valid_q), int(nq_cap), _ptr(d_nq), int(mode), _ptr(out), int(cap),
+                                       _ptr(n_out)), "kmx_match")
+        return out, n_out
+
+
+def launch_count() -> int:
+    """Kernels launched by libkmx in this process so far."""
+    return int(library().kmx_launch_count())
+
+
+def bf16_available() -> bool:
+    """Whether this build provides the BF16 tensor-core matching mode."""
+    return False
+
+
+def corr_fields(corr: torch.Tensor, n: int):
+    """Split the first n kmx_corr rows into (i, j, d1, d2) tensors."""
+    c = corr[:n]
+    return c[:, 0], c[:, 1], c[:, 2].view(torch.float32), c[:, 3].view(torch.float32)

@@ -1,0 +1,100 @@
+"""One registration pair through the kmx front end: voxelise -> grid ->
+normals (Algorithm 1 step 1) -> Faster-PFH (step 2, Eqs. A2-A5) for each
+cloud, then mutual matching (Sec. III-C).
+
+All buffers are preallocated from capacities, every count stays on the
+device, and the sequence issues no host synchronisation, so one pair is a
+fixed chain of kernel launches on one stream.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import kmx
+
+
+class CloudState:
+    """Device buffers for one cloud of at most ``n_raw_cap`` raw points."""
+
+    def __init__(self, ctx: kmx.Context, n_raw_cap: int, nbr_per_point: int = 96, stride: int = 3):
+        dev = ctx.device
+        n = max(int(n_raw_cap), 1)
+        self.ctx = ctx
+        self.n_cap = n
+        self.raw = torch.empty((n, stride), dtype=torch.float32, device=dev)
+        self.vox4 = torch.empty((n, 4), dtype=torch.float32, device=dev)
+        self.n_vox = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.bufs = dict(
+            normal4=torch.empty((n, 4), dtype=torch.float32, device=dev),
+            flags=torch.empty(n, dtype=torch.uint8, device=dev),
+            offs=torch.empty(n + 1, dtype=torch.int64, device=dev),
+            needed=torch.zeros(1, dtype=torch.int64, device=dev),
+        )
+        self.nbr_cap = n * nbr_per_point
+        self.bufs["nbr"] = torch.empty(self.nbr_cap, dtype=torch.int32, device=dev)
+        self.out = dict(
+            desc=torch.empty((n, kmx.DESC_STRIDE), dtype=torch.float32, device=dev),
+            valid=torch.empty(n, dtype=torch.int32, device=dev),
+            n_valid=torch.zeros(1, dtype=torch.int64, device=dev),
+        )
+        self.grid = None
+
+    def features(self, n_raw: int, params: kmx.Params, raw: torch.Tensor | None = None):
+        """Run a1-a6 on the first ``n_raw`` rows of ``raw`` (default: self.raw)."""
+        ctx = self.ctx
+        src = self.raw if raw is None else raw
+        ctx.voxelize(src[:n_raw], params.voxel, cap=self.n_cap, out4=self.vox4, n_out=self.n_vox)
+        if self.grid is not None:
+            self.grid.free()
+        self.grid = ctx.build_grid(self.vox4, params.r_fpfh, n_cap=self.n_cap, d_n=self.n_vox)
+        b = ctx.normals(self.grid, params, self.nbr_cap, out=self.bufs)
+        ctx.fasterpfh(self.grid, params, b["normal4"], b["flags"], b["offs"], b["nbr"], out=self.out)
+        return self
+
+    def grow_neighbours(self, needed: int):
+        self.nbr_cap = int(needed * 1.25) + 1024
+        self.bufs["nbr"] = torch.empty(self.nbr_cap, dtype=torch.int32, device=self.ctx.device)
+
+
+class PairState:
+    """Buffers for one source/target pair and its correspondences."""
+
+    def __init__(self, ctx: kmx.Context, n_src_cap: int, n_tgt_cap: int, nbr_per_point: int = 96):
+        self.ctx = ctx
+        self.src = CloudState(ctx, n_src_cap, nbr_per_point)
+        self.tgt = CloudState(ctx, n_tgt_cap, nbr_per_point)
+        cap = max(min(self.src.n_cap, self.tgt.n_cap), 1)
+        self.corr = torch.empty((cap, 4), dtype=torch.int32, device=ctx.device)
+        self.n_corr = torch.zeros(1, dtype=torch.int64, device=ctx.device)
+        self.cap = cap
+
+    def run(self, n_src: int, n_tgt: int, p_src: kmx.Params, p_tgt: kmx.Params, mode: int):
+        self.src.features(n_src, p_src)
+        self.tgt.features(n_tgt, p_tgt)
+        s, t = self.src, self.tgt
+        self.ctx.match(s.out["desc"], s.out["valid"], s.n_cap, t.out["desc"], t.out["valid"], t.n_cap,
+                       d_np=s.out["n_valid"], d_nq=t.out["n_valid"], mode=mode, cap=self.cap, out=self.corr,
+                       n_out=self.n_corr)
+        return self
+
+    def run_checked(self, n_src, n_tgt, p_src, p_tgt, mode):
+        """run() then synchronise; grows the neighbour lists and reruns once
+        if they did not fit."""
+        for attempt in range(2):
+            self.run(n_src, n_tgt, p_src, p_tgt, mode)
+            try:
+                self.ctx.sync()
+                return self
+            except kmx.KmxError as e:
+                if e.status != kmx.KMX_ECAPACITY or attempt:
+                    raise
+                for c in (self.src, self.tgt):
+                    need = int(c.bufs["needed"].item())
+                    if need > c.nbr_cap:
+                        c.grow_neighbours(need)
+        return self
+
+    def correspondences(self):
+        n = int(self.n_corr.item())
+        i, j, d1, d2 = kmx.corr_fields(self.corr, n)
+        return i.cpu().numpy(), j.cpu().numpy(), d1.cpu().numpy(), d2.cpu().numpy()

@@ -1,0 +1,412 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars: voxel assignments, centroids and neighbour sets bit-exact; normals
+within 1e-5 rad; SPFH/FPFH bins within 1e-4 at the 100-per-histogram scale
+(1e-4 * S_l / 100 for a sub-histogram whose oracle sum is S_l);
+correspondences identical.  Excused, and counted, are only the cases the
+oracle marks as ill-posed at FP32 precision: near-degenerate or sign-ill-posed
+normals, p_lin within 1e-5 of tau_lin, pair features within 2e-5 of a bin
+edge / the atan2 cut / the source tie / the degenerate-pair threshold, and
+matches whose top-2 distance gap is below 1e-3 (relative).
+"""
+import numpy as np
+import pytest
+
+from synth import lidar_pair, scene_pair
+
+pytestmark = pytest.mark.gpu
+
+H = 11
+NORMAL_TOL_RAD = 1e-5
+BIN_TOL = 1e-4          # at the 100-per-histogram scale
+FEATURE_BAND = 2e-6     # f units (FP32 feature error is ~1e-7)
+GAP_BAND = 1e-3
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def ctx(torch_cuda):
+    from paper_2409_15615_gb300 import build, kmx
+
+    build.build()
+    c = kmx.Context(0)
+    yield c
+    c.close()
+
+
+def dev(torch, a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def params_for(kmx, orc, v, vp):
+    vp32 = np.asarray(vp, np.float32)
+    return (kmx.params_default(v, viewpoint=vp32.tolist()),
+            orc.OracleParams(v, viewpoint=vp32.astype(np.float64)))
+
+
+# ----------------------------------------------------------------------------
+# voxelisation
+# ----------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("case", ["scene", "lidar", "stride4", "negative", "single"])
+def test_voxelize_bit_exact(torch_cuda, ctx, orc, case):
+    torch = torch_cuda
+    if case == "scene":
+        x, v = scene_pair(0)[0], 0.1
+    elif case == "lidar":
+        x, v = lidar_pair(0)[0], 0.3
+    elif case == "stride4":
+        x = scene_pair(1, n=7000)[1]
+        x = np.concatenate([x, np.ones((len(x), 1), np.float32)], 1)
+        v = 0.07
+    elif case == "negative":
+        rng = np.random.default_rng(3)
+        x = rng.normal(0, 0.3, (5000, 3)).astype(np.float32)
+        x[:50] = (rng.integers(-8, 8, (50, 3)) * 0.125).astype(np.float32)  # exactly on faces
+        v = 0.125
+    else:
+        x, v = np.array([[-1.5, 2.25, 0.0]], np.float32), 0.5
+    ref, ref_assign = orc.voxelize(x, v)
+    out4, n_out, assign = ctx.voxelize(dev(torch, x), v, assign=True)
+    ctx.sync()
+    n = int(n_out.item())
+    assert n == len(ref)
+    got = out4[:n].cpu().numpy()
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+    assert np.array_equal(assign.cpu().numpy()[: len(x)], ref_assign)
+
+
+def test_voxelize_empty_and_range(torch_cuda, ctx):
+    torch = torch_cuda
+    from paper_2409_15615_gb300 import kmx
+
+    out4, n_out, _ = ctx.voxelize(torch.zeros((0, 3), device="cuda"), 0.1, cap=4)
+    ctx.sync()
+    assert int(n_out.item()) == 0
+    big = np.array([[0, 0, 0], [2.0 ** 20 * 0.1 + 10.0, 0, 0]], np.float32)
+    ctx.voxelize(dev(torch, big), 0.1)
+    with pytest.raises(kmx.KmxError) as e:
+        ctx.sync()
+    assert e.value.status == kmx.KMX_ERANGE
+
+
+# ----------------------------------------------------------------------------
+# radius search and normals (Algorithm 1, step 1)
+# ----------------------------------------------------------------------------
+
+
+def _gpu_step1(torch, ctx, kmx, pts4, prm, nbr_cap=None):
+    p = dev(torch, pts4)
+    grid = ctx.build_grid(p, prm.r_fpfh)
+    cap = nbr_cap if nbr_cap is not None else len(pts4) * 200
+    out = ctx.normals(grid, prm, cap)
+    ctx.sync()
+    res = {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
+    res["grid"] = grid
+    res["dev_points"] = p
+    res["dev"] = out
+    return res
+
+
+def _sets_equal(o_offs, o_nbr, g_offs, g_nbr):
+    assert np.array_equal(o_offs, g_offs)
+    for q in range(len(o_offs) - 1):
+        a = o_nbr[o_offs[q]:o_offs[q + 1]]
+        b = np.sort(g_nbr[g_offs[q]:g_offs[q + 1]])
+        if not np.array_equal(a, b):
+            return q
+    return -1
+
+
+@pytest.mark.parametrize("case", ["scene", "lidar", "ties"])
+def test_neighbour_sets_bit_exact(torch_cuda, ctx, orc, case):
+    from paper_2409_15615_gb300 import kmx
+
+    torch = torch_cuda
+    if case == "scene":
+        vs, _ = orc.voxelize(scene_pair(2)[0], 0.1)
+        v = 0.1
+    elif case == "lidar":
+        vs, _ = orc.voxelize(lidar_pair(2)[0], 0.3)
+        v = 0.3
+    else:
+        # a lattice of spacing 1/8 with r_FPFH = 0.5 exactly: many distances equal
+        # the radius and must be excluded (strict < of Eq. A1)
+        g = np.arange(-6, 7) * 0.125
+        xx, yy, zz = np.meshgrid(g, g, g[:5])
+        vs = np.stack([xx.ravel(), yy.ravel(), zz.ravel(), 0 * xx.ravel()], 1).astype(np.float32)
+        v = 0.1
+    prm, oprm = params_for(kmx, orc, v, (0, 0, 0))
+    if case == "ties":
+        prm.r_fpfh, prm.r_normal = 0.5, 0.375
+        oprm.r_fpfh, oprm.r_normal = 0.5, 0.375
+    offs, nbr = orc.radius_search(vs, oprm.r_fpfh)
+    g = _gpu_step1(torch, ctx, kmx, vs, prm)
+    assert int(g["needed"][0]) == len(nbr)
+    bad = _sets_equal(offs, nbr, g["offs"], g["nbr"])
+    assert bad < 0, "neighbour set of point %d differs" % bad
+
+
+def _normal_bands(o_n4, o_ev, pts, vp, tau_lin):
+    l1, l2, l3 = o_ev[:, 0], o_ev[:, 1], o_ev[:, 2]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        degenerate = (l2 - l3) / np.where(l1 > 0, l1, 1) < 1e-2
+        view = vp[None, :] - pts[:, :3].astype(np.float64)
+        sign_ill = np.abs(np.sum(o_n4[:, :3] * view, 1)) / np.maximum(np.linalg.norm(view, axis=1), 1e-300) < 1e-4
+    lin_band = np.abs(o_n4[:, 3] - tau_lin) < 1e-5
+    return degenerate | sign_ill, lin_band
+
+
+@pytest.mark.parametrize("case", ["scene", "lidar"])
+def test_normals_parity(torch_cuda, ctx, orc, case):
+    from paper_2409_15615_gb300 import kmx
+
+    torch = torch_cuda
+    if case == "scene":
+        src, _, _, _, vp, _ = scene_pair(4)
+        v = 0.1
+    else:
+        src, _, _, _, vp, _ = lidar_pair(4)
+        v = 0.3
+    vs, _ = orc.voxelize(src, v)
+    prm, oprm = params_for(kmx, orc, v, vp)
+    offs, nbr = orc.radius_search(vs, oprm.r_fpfh)
+    o_n4, o_ev, o_fl, _ = orc.normals(vs, offs, nbr, oprm)
+    g = _gpu_step1(torch, ctx, kmx, vs, prm)
+    g_n4, g_fl = g["normal4"][: len(vs)], g["flags"][: len(vs)]
+    # PCA reached: depends on integer counts only -> exact
+    assert np.array_equal(g_fl & 4, o_fl & 4)
+    ill, lin_band = _normal_bands(o_n4, o_ev, vs, oprm.viewpoint, oprm.tau_lin)
+    pca = (o_fl & 4) > 0
+    check = pca & ~ill & (o_ev[:, 0] > 0)
+    a = g_n4[check, :3].astype(np.float64)
+    a /= np.linalg.norm(a, axis=1, keepdims=True)  # FP32 rounding leaves |a| = 1 +- 1e-7
+    b = o_n4[check, :3]
+    ang = np.arctan2(np.linalg.norm(np.cross(a, b), axis=1), np.sum(a * b, 1))
+    assert ang.max() <= NORMAL_TOL_RAD, "max normal angle %.3g rad" % ang.max()
+    assert np.abs(g_n4[check, 3] - o_n4[check, 3]).max() < 1e-5
+    same_b = (g_fl & 1) == (o_fl & 1)
+    assert np.all(same_b | lin_band | ill), "B differs outside the bands at %s" % np.nonzero(~(same_b | lin_band | ill))[0][:10]
+    assert check.mean() > 0.5
+
+
+def test_neighbour_capacity_error(torch_cuda, ctx, orc):
+    from paper_2409_15615_gb300 import kmx
+
+    torch = torch_cuda
+    vs, _ = orc.voxelize(scene_pair(5, n=4000)[0], 0.1)
+    prm, oprm = params_for(kmx, orc, 0.1, (5, 5, 5))
+    offs, nbr = orc.radius_search(vs, oprm.r_fpfh)
+    p = dev(torch, vs)
+    grid = ctx.build_grid(p, prm.r_fpfh)
+    out = ctx.normals(grid, prm, 10)
+    with pytest.raises(kmx.KmxError) as e:
+        ctx.sync()
+    assert e.value.status == kmx.KMX_ECAPACITY
+    assert int(out["needed"].item()) == len(nbr)
+    # a grid cell smaller than r_FPFH is refused on the host
+    small = ctx.build_grid(p, prm.r_fpfh * 0.5)
+    with pytest.raises(kmx.KmxError) as e:
+        ctx.normals(small, prm, len(nbr))
+    assert e.value.status == kmx.KMX_EINVAL
+    ctx.sync()
+
+
+# ----------------------------------------------------------------------------
+# Faster-PFH (Algorithm 1 step 2, Eqs. A2-A5), stage-isolated on oracle inputs
+# ----------------------------------------------------------------------------
+
+
+def _hist_close(got, ref, extra_scale=None):
+    """Per-row max violation of |got - ref| <= BIN_TOL * S_l / 100."""
+    viol = np.zeros(len(ref))
+    for l in range(3):
+        sl = ref[:, l * H:(l + 1) * H]
+        tol = BIN_TOL * np.maximum(sl.sum(1), 100.0) / 100.0
+        err = np.abs(got[:, l * H:(l + 1) * H] - sl).max(1)
+        viol = np.maximum(viol, err / tol)
+    return viol
+
+
+def _fpfh_band(o, n):
+    """Rows of J whose FPFH depends on a pair within FEATURE_BAND of a flip."""
+    bad_q = o["margin"] < FEATURE_BAND
+    band = np.zeros(n, bool)
+    for q in o["J"]:
+        ks = o["vnbr"][o["voffs"][q]:o["voffs"][q + 1]]
+        band[q] = bad_q[q] or bad_q[ks].any()
+    return band
+
+
+@pytest.mark.parametrize("case", ["scene", "lidar"])
+def test_fasterpfh_stage_isolated(torch_cuda, ctx, orc, case):
+    from paper_2409_15615_gb300 import kmx
+
+    torch = torch_cuda
+    if case == "scene":
+        src, _, _, _, vp, _ = scene_pair(6)
+        v = 0.1
+    else:
+        src, _, _, _, vp, _ = lidar_pair(6)
+        v = 0.3
+    vs, _ = orc.voxelize(src, v)
+    prm, oprm = params_for(kmx, orc, v, vp)
+    # oracle step 1, then the oracle's own step 2 / SPFH / FPFH on FP32-cast normals
+    offs, nbr = orc.radius_search(vs, oprm.r_fpfh)
+    n4, ev, fl, _ = orc.normals(vs, offs, nbr, oprm)
+    n4_32 = n4.astype(np.float32)
+    n4_in = n4_32.astype(np.float64)
+    voffs, vnbr, J, fl2 = orc.valid_filter(offs, nbr, fl, oprm.tau_num)
+    sp, npairs, margin = orc.spfh(vs, n4_in, fl2, voffs, vnbr, H, with_margin=True)
+    fp = orc.fpfh(vs, J, voffs, vnbr, sp)
+    o = dict(margin=margin, J=J, voffs=voffs, vnbr=vnbr)
+    # GPU step 2 on the same inputs
+    p = dev(torch, vs)
+    grid = ctx.build_grid(p, prm.r_fpfh)
+    flags = dev(torch, fl & 5)
+    res = ctx.fasterpfh(grid, prm, dev(torch, n4_32), flags, dev(torch, offs), dev(torch, nbr.astype(np.int32)),
+                        want_spfh=True)
+    ctx.sync()
+    nJ = int(res["n_valid"].item())
+    gJ = res["valid"][:nJ].cpu().numpy()
+    assert np.array_equal(gJ, J)
+    assert np.array_equal(flags.cpu().numpy(), fl2)
+    gsp = res["spfh"][: len(vs), :33].cpu().numpy().astype(np.float64)
+    ok_q = margin >= FEATURE_BAND
+    v_sp = _hist_close(gsp[ok_q], sp[ok_q])
+    assert v_sp.max() <= 1.0, "SPFH off by %.3g x tolerance" % v_sp.max()
+    assert np.all(res["spfh"][: len(vs), 33:].cpu().numpy() == 0)
+    gfp = res["desc"][:nJ, :33].cpu().numpy().astype(np.float64)
+    band = _fpfh_band(o, len(vs))[J]
+    v_fp = _hist_close(gfp[~band], fp[~band])
+    assert v_fp.max() <= 1.0, "FPFH off by %.3g x tolerance" % v_fp.max()
+    assert band.mean() < 0.5, "%.3f of the FPFH rows sit in the band" % band.mean()
+
+
+# ----------------------------------------------------------------------------
+# mutual matching, stage-isolated on oracle descriptors
+# ----------------------------------------------------------------------------
+
+
+def _gap_band(o_side):
+    g1 = (o_side["d2p"] - o_side["d1p"]) / np.maximum(o_side["d2p"], 1e-300)
+    g2 = (o_side["d2q"] - o_side["d1q"]) / np.maximum(o_side["d2q"], 1e-300)
+    return g1 < GAP_BAND, g2 < GAP_BAND
+
+
+def _pad36(F):
+    out = np.zeros((len(F), 36), np.float32)
+    out[:, :33] = F
+    return out
+
+
+def _check_match(torch, ctx, orc, FP, FQ, mode):
+    FP32 = FP.astype(np.float32)
+    FQ32 = FQ.astype(np.float32)
+    A, side = orc.mutual_match(FP32.astype(np.float64), FQ32.astype(np.float64))
+    corr, n_out = ctx.match(dev(torch, _pad36(FP32)), None, len(FP), dev(torch, _pad36(FQ32)), None, len(FQ),
+                            mode=mode)
+    ctx.sync()
+    n = int(n_out.item())
+    c = corr[:n].cpu().numpy()
+    gi, gj = c[:, 0], c[:, 1]
+    gd1, gd2 = c[:, 2].view(np.float32), c[:, 3].view(np.float32)
+    bp, bq = _gap_band(side)
+    ref = {(int(i), int(j)) for i, j in zip(A["i"], A["j"])}
+    got = {(int(i), int(j)) for i, j in zip(gi, gj)}
+    for (i, j) in ref ^ got:
+        jj = side["nn_pq"][i]
+        assert bp[i] or bq[jj] or bq[j], "pair (%d, %d) differs outside the gap band" % (i, j)
+    assert np.all(np.diff(gi) > 0)
+    # distances of the common pairs
+    refd = {(int(i), int(j)): (d1, d2) for i, j, d1, d2 in zip(A["i"], A["j"], A["d1"], A["d2"])}
+    for i, j, d1, d2 in zip(gi, gj, gd1, gd2):
+        if (int(i), int(j)) in refd:
+            r1, r2 = refd[(int(i), int(j))]
+            assert abs(d1 - r1) <= 1e-4 * max(r1, 1e-3) + 1e-4
+            if np.isfinite(r2):
+                assert abs(d2 - r2) <= 1e-4 * max(r2, 1e-3) + 1e-4
+    return len(ref), len(ref ^ got)
+
+
+@pytest.mark.parametrize("shape", [(700, 1300), (1, 5), (129, 128), (4099, 3001)])
+def test_match_fp32_random(torch_cuda, ctx, orc, shape):
+    from paper_2409_15615_gb300 import kmx
+
+    rng = np.random.default_rng(sum(shape))
+    FP = rng.gamma(0.5, 20.0, (shape[0], 33))
+    FQ = rng.gamma(0.5, 20.0, (shape[1], 33))
+    k = min(shape) // 2  # plant k near-copies so that there are true matches
+    FQ[:k] = FP[rng.permutation(shape[0])[:k]] + rng.normal(0, 0.5, (k, 33))
+    n_ref, n_diff = _check_match(torch_cuda, ctx, orc, FP, FQ, kmx.MATCH_FP32_EXACT)
+    assert n_diff <= max(1, n_ref // 100)
+
+
+def test_match_fp32_on_oracle_descriptors(torch_cuda, ctx, orc):
+    from paper_2409_15615_gb300 import kmx
+
+    src, tgt, _, _, vps, vpt = scene_pair(7)
+    fs = orc.faster_pfh(orc.voxelize(src, 0.1)[0], orc.OracleParams(0.1, viewpoint=vps))
+    ft = orc.faster_pfh(orc.voxelize(tgt, 0.1)[0], orc.OracleParams(0.1, viewpoint=vpt))
+    n_ref, n_diff = _check_match(torch_cuda, ctx, orc, fs["fpfh"], ft["fpfh"], kmx.MATCH_FP32_EXACT)
+    assert n_ref > 100
+
+
+def test_match_empty(torch_cuda, ctx):
+    torch = torch_cuda
+    from paper_2409_15615_gb300 import kmx
+
+    d = torch.zeros((4, 36), device="cuda")
+    corr, n = ctx.match(d, None, 0, d, None, 4, mode=kmx.MATCH_FP32_EXACT, cap=4)
+    ctx.sync()
+    assert int(n.item()) == 0
+
+
+# ----------------------------------------------------------------------------
+# the chained pipeline (voxelise -> ... -> match) against the oracle's chain
+# ----------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("case", ["scene", "lidar"])
+def test_chained_pair(torch_cuda, ctx, orc, case):
+    from paper_2409_15615_gb300 import kmx, pipeline
+
+    torch = torch_cuda
+    if case == "scene":
+        src, tgt, R, t, vps, vpt = scene_pair(8)
+        v = 0.1
+    else:
+        src, tgt, R, t, vps, vpt = lidar_pair(8)
+        v = 0.3
+    A, fs, ft, vs, vt = orc.front_end(src, tgt, v, np.float32(vps).astype(np.float64),
+                                      np.float32(vpt).astype(np.float64))
+    ps, _ = params_for(kmx, orc, v, vps)
+    pt, _ = params_for(kmx, orc, v, vpt)
+    pair = pipeline.PairState(ctx, len(src), len(tgt))
+    pair.src.raw.copy_(dev(torch, src))
+    pair.tgt.raw.copy_(dev(torch, tgt))
+    pair.run_checked(len(src), len(tgt), ps, pt, kmx.MATCH_FP32_EXACT)
+    assert int(pair.src.n_vox.item()) == len(vs) and int(pair.tgt.n_vox.item()) == len(vt)
+    assert np.array_equal(pair.src.vox4[: len(vs)].cpu().numpy().view(np.uint32), vs.view(np.uint32))
+    # J: equal up to points whose B flag sits on the tau_lin band
+    for cs, fo in ((pair.src, fs), (pair.tgt, ft)):
+        nJ = int(cs.out["n_valid"].item())
+        gJ = cs.out["valid"][:nJ].cpu().numpy()
+        diff = np.setxor1d(gJ, fo["J"])
+        assert len(diff) <= max(2, len(fo["J"]) // 1000), "J differs in %d points" % len(diff)
+    gi, gj, gd1, gd2 = pair.correspondences()
+    ref = set(zip(A["i"].tolist(), A["j"].tolist()))
+    got = set(zip(gi.tolist(), gj.tolist()))
+    agree = len(ref & got) / max(len(ref), 1)
+    assert agree > 0.97, "only %.3f of the oracle's correspondences reproduced" % agree
