@@ -41,7 +41,7 @@ def load():
                                      C.POINTER(i64)]
     lib.orc_pair_features.argtypes = [_f32p, _f64p, _f32p, _f64p, _f64p]
     lib.orc_bin.argtypes = [f64, f64, f64, C.c_int]
-    lib.orc_spfh.argtypes = [_f32p, _f64p, i64, _u8p, _i64p, _i32p, C.c_int, _f64p, _i32p, _f64p]
+    lib.orc_spfh.argtypes = [_f32p, _f64p, i64, _u8p, _i64p, _i32p, C.c_int, _f64p, _i32p, _f64p, f64, _i32p]
     lib.orc_fpfh.argtypes = [_f32p, i64, _i32p, _i64p, _i32p, _f64p, C.c_int, _f64p]
     lib.orc_nearest.argtypes = [_f64p, i64, _f64p, i64, C.c_int, _i32p, _f64p, _f64p]
     lib.orc_core_numbers.argtypes = [i64, _i64p, _i32p, _i32p]
@@ -179,24 +179,26 @@ def feature_bin(f, lo, hi, H=11):
     return load().orc_bin(float(f), float(lo), float(hi), int(H))
 
 
-def spfh(p4, normal4, flags, voffs, vnbr, H=11, with_margin=False):
+def spfh(p4, normal4, flags, voffs, vnbr, H=11, with_margin=False, band=2e-6):
     """SPFH rows [n, 3H] (Eq. A4) and the per-point pair counts; with
-    ``with_margin`` also the per-point distance of the nearest pair feature to
-    a decision FP32 rounding could flip (bin edge, atan2 cut, source choice,
-    degenerate-pair threshold)."""
+    ``with_margin`` also, per point, the distance of the nearest pair feature
+    to a decision FP32 rounding could flip (bin edge, atan2 cut, source
+    choice, degenerate-pair threshold) and the number of its pairs closer
+    than ``band`` to such a decision."""
     lib = load()
     p = _as_p4(p4)
     n = len(p)
     out = np.zeros((max(n, 1), 3 * H))
     npairs = np.zeros(max(n, 1), np.int32)
     margin = np.zeros(max(n, 1))
+    n_marg = np.zeros(max(n, 1), np.int32)
     nb = np.ascontiguousarray(vnbr, np.int32) if len(vnbr) else np.zeros(1, np.int32)
     _check(lib.orc_spfh(p if n else np.zeros((1, 4), np.float32), np.ascontiguousarray(normal4, np.float64)
                         if n else np.zeros((1, 4)), n, np.ascontiguousarray(flags, np.uint8) if n else
                         np.zeros(1, np.uint8), np.ascontiguousarray(voffs, np.int64), nb, int(H), out, npairs,
-                        margin), "spfh")
+                        margin, float(band), n_marg), "spfh")
     if with_margin:
-        return out[:n], npairs[:n], margin[:n]
+        return out[:n], npairs[:n], margin[:n], n_marg[:n]
     return out[:n], npairs[:n]
 
 
@@ -222,10 +224,10 @@ def faster_pfh(p4, params: OracleParams, search="grid"):
     offs, nbr = radius_search(p, params.r_fpfh, method=search)
     normal4, evals, flags, n_normal = normals(p, offs, nbr, params)
     voffs, vnbr, J, flags = valid_filter(offs, nbr, flags, params.tau_num)
-    sp, npairs, margin = spfh(p, normal4, flags, voffs, vnbr, params.hist_bins, with_margin=True)
+    sp, npairs, margin, n_marg = spfh(p, normal4, flags, voffs, vnbr, params.hist_bins, with_margin=True)
     fp = fpfh(p, J, voffs, vnbr, sp)
     return dict(points=p, offs=offs, nbr=nbr, normal4=normal4, evals=evals, n_normal=n_normal, flags=flags,
-                voffs=voffs, vnbr=vnbr, J=J, spfh=sp, npairs=npairs, margin=margin, fpfh=fp)
+                voffs=voffs, vnbr=vnbr, J=J, spfh=sp, npairs=npairs, margin=margin, n_marg=n_marg, fpfh=fp)
 
 
 def nearest(X, Y):

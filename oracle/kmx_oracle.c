@@ -557,10 +557,12 @@ static double pair_margin(const float* pq, const double* nq, const float* pk, co
  * sub-histogram l counts the bins of f_l and is scaled by 100 / c, c the
  * number of contributing pairs (reading R7).  spfh is [n][3H] (rows of q
  * without B are zero); npairs[q] = c (nullable); margin[q] (nullable) is the
- * smallest pair_margin over the pairs of q (+inf without pairs).
+ * smallest pair_margin over the pairs of q (+inf without pairs); n_marg[q]
+ * (nullable) counts the pairs of q whose pair_margin is below `band`.
  */
 int orc_spfh(const float* p4, const double* normal4, int64_t n, const uint8_t* flags, const int64_t* voffs,
-             const int32_t* vnbr, int H, double* spfh, int32_t* npairs, double* margin)
+             const int32_t* vnbr, int H, double* spfh, int32_t* npairs, double* margin, double band,
+             int32_t* n_marg)
 {
     const double PI = 3.14159265358979323846;
     const double lo[3] = {-PI, -1.0, -1.0}, hi[3] = {PI, 1.0, 1.0};
@@ -570,13 +572,17 @@ int orc_spfh(const float* p4, const double* normal4, int64_t n, const uint8_t* f
         for (int h = 0; h < 3 * H; ++h) row[h] = 0.0;
         if (npairs) npairs[q] = 0;
         if (margin) margin[q] = INFINITY;
+        if (n_marg) n_marg[q] = 0;
         if (!(flags[q] & 1)) continue;
         int64_t c = 0;
         for (int64_t t = voffs[q]; t < voffs[q + 1]; ++t) {
             int64_t k = vnbr[t];
             if (k == q) continue;
-            if (margin)
-                margin[q] = fmin(margin[q], pair_margin(p4 + 4 * q, normal4 + 4 * q, p4 + 4 * k, normal4 + 4 * k, H));
+            if (margin || n_marg) {
+                double pm = pair_margin(p4 + 4 * q, normal4 + 4 * q, p4 + 4 * k, normal4 + 4 * k, H);
+                if (margin) margin[q] = fmin(margin[q], pm);
+                if (n_marg && pm < band) n_marg[q] += 1;
+            }
             double f[3];
             if (!orc_pair_features(p4 + 4 * q, normal4 + 4 * q, p4 + 4 * k, normal4 + 4 * k, f)) continue;
             for (int l = 0; l < 3; ++l) row[l * H + orc_bin(f[l], lo[l], hi[l], H)] += 1.0;

@@ -63,6 +63,11 @@ cudaError_t match_finalize(kmx_ctx* ctx, const MatchScratch& s, int chunks, int6
 
 }  // namespace kmx
 
+// match_tc.cu
+size_t kmx_match_tc_extra_bytes(int64_t np_cap, int64_t nq_cap, int sm_count);
+cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, const int64_t* d_np, const float* dq,
+                                int64_t nq_cap, const int64_t* d_nq, kmx::MatchScratch& s);
+
 // match_fp32.cu
 size_t kmx_match_fp32_scratch_bytes(int64_t np_cap, int64_t nq_cap, int* chunks);
 cudaError_t kmx_match_fp32_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, const int64_t* d_np,

@@ -8,10 +8,14 @@
 // space, so all 32 lanes test candidates regardless of how the points are
 // spread over the cells.  Two passes: the first counts |I| and accumulates the
 // P_normal mean; after a prefix sum of the counts the second writes the CSR
-// lists and accumulates the covariance centred on that mean.  The 3x3
-// eigen-problem is solved in FP64 (closed form, Smith 1961: trigonometric
-// eigenvalues, eigenvector of the smallest one from the best-conditioned cross
-// product of two rows of A - l3 I).
+// lists and accumulates the covariance centred on that mean.
+//
+// The 3x3 eigen-problem is solved in FP64 (closed form, Smith 1961:
+// trigonometric eigenvalues, eigenvector of the smallest one from the
+// best-conditioned cross product of two rows of A - l3 I).  GB300 issues FP64
+// at a small fraction of the FP32 rate and a warp instruction costs the same
+// with 1 or 32 active lanes, so each block first gathers the covariances of
+// its 32 queries in shared memory and then solves them one per lane.
 #include "kmx_internal.cuh"
 #include "grid_common.cuh"
 
@@ -19,6 +23,8 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+constexpr int kQPerWarp = 4;                    // queries per warp in the fill pass
+constexpr int kQPerBlock = kWarps * kQPerWarp;  // = 32, one per lane of the solving warp
 constexpr unsigned kFull = 0xffffffffu;
 
 struct NormScratch {
@@ -168,8 +174,8 @@ __device__ __forceinline__ void cross3(const double* a, const double* b, double*
 
 // Eigenvalues l1 >= l2 >= l3 of a symmetric 3x3 matrix and a unit eigenvector
 // of l3.  Returns false if the matrix is a multiple of the identity.
-__device__ bool eig_sym3(double a00, double a01, double a02, double a11, double a12, double a22, double* l,
-                         double* nv)
+__device__ __forceinline__ bool eig_sym3(double a00, double a01, double a02, double a11, double a12, double a22,
+                                         double* l, double* nv)
 {
     const double p1 = a01 * a01 + a02 * a02 + a12 * a12;
     const double q = (a00 + a11 + a22) / 3.0;
@@ -200,14 +206,17 @@ __device__ bool eig_sym3(double a00, double a01, double a02, double a11, double 
     const double n0 = c0[0] * c0[0] + c0[1] * c0[1] + c0[2] * c0[2];
     const double n1 = c1[0] * c1[0] + c1[1] * c1[1] + c1[2] * c1[2];
     const double n2 = c2[0] * c2[0] + c2[1] * c2[1] + c2[2] * c2[2];
-    const double* c = c0;
-    double nb = n0;
+    double cx = c0[0], cy = c0[1], cz = c0[2], nb = n0;
     if (n1 > nb) {
-        c = c1;
+        cx = c1[0];
+        cy = c1[1];
+        cz = c1[2];
         nb = n1;
     }
     if (n2 > nb) {
-        c = c2;
+        cx = c2[0];
+        cy = c2[1];
+        cz = c2[2];
         nb = n2;
     }
     if (!(nb > 0.0)) {
@@ -217,9 +226,9 @@ __device__ bool eig_sym3(double a00, double a01, double a02, double a11, double 
         return true;
     }
     const double inv = 1.0 / sqrt(nb);
-    nv[0] = c[0] * inv;
-    nv[1] = c[1] * inv;
-    nv[2] = c[2] * inv;
+    nv[0] = cx * inv;
+    nv[1] = cy * inv;
+    nv[2] = cz * inv;
     return true;
 }
 
@@ -236,87 +245,118 @@ struct NormOut {
     float vp[3];
 };
 
-// Pass 2: CSR lists, centred covariance over P_normal, FP64 eigen-solve,
-// orientation, linearity test.
+// Pass 2: CSR lists and centred second moments over P_normal (a warp per
+// query, kQPerWarp queries per warp), then the FP64 eigen-solve, orientation
+// and linearity test with one query per lane of warp 0.
 __global__ void __launch_bounds__(kThreads) search_fill(GridView g, Radii R, NormScratch s, NormOut o,
                                                         unsigned int* err)
 {
-    const int lane = threadIdx.x & 31;
+    __shared__ float sm_mom[9][kQPerBlock];  // s1x s1y s1z sxx sxy sxz syy syz szz
+    __shared__ float sm_q[3][kQPerBlock];
+    __shared__ int sm_qi[kQPerBlock], sm_nN[kQPerBlock];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t total_list = o.offs[o.n_cap];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *o.needed = total_list;
         if (o.nbr && total_list > o.nbr_cap) kmx_raise(err, KMX_DERR_CAPACITY);
     }
     const bool write = o.nbr && total_list <= o.nbr_cap;
-    const int64_t p = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-    if (p >= *g.n_sorted) return;
-    const float4 q = g.sorted[p];
-    const int qi = __float_as_int(q.w);
-    const float4 mq = s.mean[qi];
-    const int nN = __float_as_int(mq.w);
-    int start, excl;
-    const int total = stencil(g, q, lane, &start, &excl);
-    int64_t out = o.offs[qi];
-    // centred sums over P_normal: first moments (should be ~0) and second moments
-    float s1x = 0.f, s1y = 0.f, s1z = 0.f;
-    float sxx = 0.f, sxy = 0.f, sxz = 0.f, syy = 0.f, syz = 0.f, szz = 0.f;
-    for (int base = 0; base < total; base += 32) {
-        const int t = base + lane;
-        const int pos = candidate(t, start, excl);
-        bool inF = false, inN = false;
-        float dx = 0.f, dy = 0.f, dz = 0.f;
-        int idx = 0;
-        if (t < total) {
-            const float4 a = g.sorted[pos];
-            idx = __float_as_int(a.w);
-            dx = a.x - q.x;
-            dy = a.y - q.y;
-            dz = a.z - q.z;
-            const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            inF = within(a, q, d2, R.rf2, R.rf2d);
-            inN = inF && within(a, q, d2, R.rn2, R.rn2d);
+    const int64_t n_sorted = *g.n_sorted;
+    for (int k = 0; k < kQPerWarp; ++k) {
+        const int slot = warp * kQPerWarp + k;
+        const int64_t p = (int64_t)blockIdx.x * kQPerBlock + slot;
+        if (p >= n_sorted) {
+            if (lane == 0) sm_qi[slot] = -1;
+            continue;
         }
-        const unsigned bal = __ballot_sync(kFull, inF);
-        if (inF && write) o.nbr[out + __popc(bal & ((1u << lane) - 1u))] = idx;
-        out += __popc(bal);
-        if (inN) {
-            const float ex = dx - mq.x, ey = dy - mq.y, ez = dz - mq.z;
-            s1x += ex;
-            s1y += ey;
-            s1z += ez;
-            sxx = fmaf(ex, ex, sxx);
-            sxy = fmaf(ex, ey, sxy);
-            sxz = fmaf(ex, ez, sxz);
-            syy = fmaf(ey, ey, syy);
-            syz = fmaf(ey, ez, syz);
-            szz = fmaf(ez, ez, szz);
+        const float4 q = g.sorted[p];
+        const int qi = __float_as_int(q.w);
+        const float4 mq = s.mean[qi];
+        int start, excl;
+        const int total = stencil(g, q, lane, &start, &excl);
+        int64_t out = o.offs[qi];
+        float s1x = 0.f, s1y = 0.f, s1z = 0.f;
+        float sxx = 0.f, sxy = 0.f, sxz = 0.f, syy = 0.f, syz = 0.f, szz = 0.f;
+        for (int base = 0; base < total; base += 32) {
+            const int t = base + lane;
+            const int pos = candidate(t, start, excl);
+            bool inF = false, inN = false;
+            float dx = 0.f, dy = 0.f, dz = 0.f;
+            int idx = 0;
+            if (t < total) {
+                const float4 a = g.sorted[pos];
+                idx = __float_as_int(a.w);
+                dx = a.x - q.x;
+                dy = a.y - q.y;
+                dz = a.z - q.z;
+                const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                inF = within(a, q, d2, R.rf2, R.rf2d);
+                inN = inF && within(a, q, d2, R.rn2, R.rn2d);
+            }
+            const unsigned bal = __ballot_sync(kFull, inF);
+            if (inF && write) o.nbr[out + __popc(bal & ((1u << lane) - 1u))] = idx;
+            out += __popc(bal);
+            if (inN) {
+                const float ex = dx - mq.x, ey = dy - mq.y, ez = dz - mq.z;
+                s1x += ex;
+                s1y += ey;
+                s1z += ez;
+                sxx = fmaf(ex, ex, sxx);
+                sxy = fmaf(ex, ey, sxy);
+                sxz = fmaf(ex, ez, sxz);
+                syy = fmaf(ey, ey, syy);
+                syz = fmaf(ey, ez, syz);
+                szz = fmaf(ez, ez, szz);
+            }
+        }
+        s1x = warp_sum(s1x);
+        s1y = warp_sum(s1y);
+        s1z = warp_sum(s1z);
+        sxx = warp_sum(sxx);
+        sxy = warp_sum(sxy);
+        sxz = warp_sum(sxz);
+        syy = warp_sum(syy);
+        syz = warp_sum(syz);
+        szz = warp_sum(szz);
+        if (lane == 0) {
+            sm_mom[0][slot] = s1x;
+            sm_mom[1][slot] = s1y;
+            sm_mom[2][slot] = s1z;
+            sm_mom[3][slot] = sxx;
+            sm_mom[4][slot] = sxy;
+            sm_mom[5][slot] = sxz;
+            sm_mom[6][slot] = syy;
+            sm_mom[7][slot] = syz;
+            sm_mom[8][slot] = szz;
+            sm_q[0][slot] = q.x;
+            sm_q[1][slot] = q.y;
+            sm_q[2][slot] = q.z;
+            sm_qi[slot] = qi;
+            sm_nN[slot] = __float_as_int(mq.w);
         }
     }
-    s1x = warp_sum(s1x);
-    s1y = warp_sum(s1y);
-    s1z = warp_sum(s1z);
-    sxx = warp_sum(sxx);
-    sxy = warp_sum(sxy);
-    sxz = warp_sum(sxz);
-    syy = warp_sum(syy);
-    syz = warp_sum(syz);
-    szz = warp_sum(szz);
-    if (lane != 0) return;
+    __syncthreads();
+    if (warp != 0) return;
+    const int qi = sm_qi[lane];
+    if (qi < 0) return;
+    const int nN = sm_nN[lane];
     const int mF = (int)(o.offs[qi + 1] - o.offs[qi]);
     uint8_t flag = 0;
     float4 nout = make_float4(0.f, 0.f, 0.f, 0.f);
     if (mF >= o.tau_num && nN >= o.tau_num) {
         const double inv = 1.0 / (double)nN;
-        const double m0 = (double)s1x * inv, m1 = (double)s1y * inv, m2 = (double)s1z * inv;
-        const double c00 = (double)sxx * inv - m0 * m0, c01 = (double)sxy * inv - m0 * m1;
-        const double c02 = (double)sxz * inv - m0 * m2, c11 = (double)syy * inv - m1 * m1;
-        const double c12 = (double)syz * inv - m1 * m2, c22 = (double)szz * inv - m2 * m2;
+        const double m0 = (double)sm_mom[0][lane] * inv, m1 = (double)sm_mom[1][lane] * inv;
+        const double m2 = (double)sm_mom[2][lane] * inv;
+        const double c00 = (double)sm_mom[3][lane] * inv - m0 * m0, c01 = (double)sm_mom[4][lane] * inv - m0 * m1;
+        const double c02 = (double)sm_mom[5][lane] * inv - m0 * m2, c11 = (double)sm_mom[6][lane] * inv - m1 * m1;
+        const double c12 = (double)sm_mom[7][lane] * inv - m1 * m2, c22 = (double)sm_mom[8][lane] * inv - m2 * m2;
         double l[3], nv[3];
         eig_sym3(c00, c01, c02, c11, c12, c22, l, nv);
         flag |= 4;
         if (l[0] > 0.0) {
-            const double view = nv[0] * ((double)o.vp[0] - (double)q.x) + nv[1] * ((double)o.vp[1] - (double)q.y) +
-                                nv[2] * ((double)o.vp[2] - (double)q.z);
+            const double view = nv[0] * ((double)o.vp[0] - (double)sm_q[0][lane]) +
+                                nv[1] * ((double)o.vp[1] - (double)sm_q[1][lane]) +
+                                nv[2] * ((double)o.vp[2] - (double)sm_q[2][lane]);
             bool flip = view < 0.0;
             if (view == 0.0) flip = nv[0] != 0.0 ? nv[0] < 0.0 : (nv[1] != 0.0 ? nv[1] < 0.0 : nv[2] < 0.0);
             const double sgn = flip ? -1.0 : 1.0;
@@ -364,13 +404,12 @@ cudaError_t kmx_normals_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_params
     if ((e = cudaMemsetAsync(flags, 0, n, st))) return e;
     KMX_COUNT_LAUNCH();
     clear_counts<<<kmx_blocks(n + 1, 256), 256, 0, st>>>(s.cnt, n);
-    const unsigned nb = kmx_blocks(n, kWarps);
     KMX_COUNT_LAUNCH();
-    search_count<<<nb, kThreads, 0, st>>>(gv, R, s);
+    search_count<<<kmx_blocks(n, kWarps), kThreads, 0, st>>>(gv, R, s);
     if ((e = kmx_scan_i32(s.cnt, n, g->d_n, offs, s.scan, st))) return e;
     NormOut o{reinterpret_cast<float4*>(normal4), flags, offs, nbr, nbr_cap, n, needed, prm->tau_num,
               prm->tau_lin, {prm->viewpoint[0], prm->viewpoint[1], prm->viewpoint[2]}};
     KMX_COUNT_LAUNCH();
-    search_fill<<<nb, kThreads, 0, st>>>(gv, R, s, o, ctx->d_err);
+    search_fill<<<kmx_blocks(n, kQPerBlock), kThreads, 0, st>>>(gv, R, s, o, ctx->d_err);
     return cudaGetLastError();
 }

@@ -23,7 +23,7 @@ struct VoxScratch {
     int64_t* vstart;           // [n+1] member offsets per output voxel
     int32_t* cursor;           // [n] fill cursor per output voxel
     int32_t* members;          // [n] grouped members (arbitrary order inside a voxel)
-    int32_t* sorted;           // [n] grouped members in input order
+    float4* run;               // [n] member coordinates per voxel, in input order
     void* scan;
     uint32_t T;
 };
@@ -51,7 +51,7 @@ VoxScratch carve(void* base, int64_t n, size_t* total)
     s.vstart = (int64_t*)take(sizeof(int64_t) * (n + 1));
     s.cursor = (int32_t*)take(sizeof(int32_t) * (n + 1));
     s.members = (int32_t*)take(sizeof(int32_t) * (n + 1));
-    s.sorted = (int32_t*)take(sizeof(int32_t) * (n + 1));
+    s.run = (float4*)take(sizeof(float4) * (n + 1));
     s.scan = take(kmx_scan_scratch_bytes(n));
     *total = kmx_align_up(a.used, 256);
     return s;
@@ -128,39 +128,38 @@ __global__ void __launch_bounds__(kThreads) vox_scatter(int64_t n, VoxScratch s,
     s.members[s.vstart[o] + pos] = (int32_t)r;
 }
 
-// One warp per output voxel: restore input order of the members (rank of each
-// member = number of smaller members; members are distinct), then sum in FP64
-// in that order and divide by the count.
+// One thread per output voxel (so FP64 instructions run with every lane
+// busy).  Each member's rank in input order (the number of smaller member
+// indices) places its coordinates in a per-voxel run, which is then summed in
+// FP64 in that order and divided by the count.  All loads are independent of
+// one another, so their latencies overlap.
 __global__ void __launch_bounds__(kThreads) vox_centroid(const float* __restrict__ xyz, int stride, int64_t n,
                                                          VoxScratch s, float4* __restrict__ out, int64_t cap)
 {
-    int64_t o = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    int64_t nv = s.oidx[n];
+    const int64_t o = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int64_t nv = s.oidx[n];
     if (o >= nv || o >= cap) return;
-    int64_t b = s.vstart[o];
-    int L = (int)(s.vstart[o + 1] - b);
-    const int32_t* mem = s.members + b;
-    int32_t* srt = s.sorted + b;
-    for (int e = lane; e < L; e += 32) {
-        int32_t me = mem[e];
+    const int64_t b = s.vstart[o];
+    const int L = (int)(s.vstart[o + 1] - b);
+    const int32_t* m = s.members + b;
+    float4* run = s.run + b;
+    for (int e = 0; e < L; ++e) {
+        const int32_t me = m[e];
         int rank = 0;
-        for (int f = 0; f < L; ++f) rank += (mem[f] < me);
-        srt[rank] = me;
+        for (int f = 0; f < L; ++f) rank += (m[f] < me);
+        const float* p = xyz + (int64_t)me * stride;
+        run[rank] = make_float4(p[0], p[1], p[2], 0.f);
     }
-    __syncwarp();
-    if (lane == 0) {
-        double sx = 0.0, sy = 0.0, sz = 0.0;
-        for (int e = 0; e < L; ++e) {
-            const float* p = xyz + (int64_t)srt[e] * stride;
-            sx = __dadd_rn(sx, (double)p[0]);
-            sy = __dadd_rn(sy, (double)p[1]);
-            sz = __dadd_rn(sz, (double)p[2]);
-        }
-        double c = (double)L;
-        out[o] = make_float4(__double2float_rn(__ddiv_rn(sx, c)), __double2float_rn(__ddiv_rn(sy, c)),
-                             __double2float_rn(__ddiv_rn(sz, c)), 0.0f);
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int e = 0; e < L; ++e) {
+        const float4 p = run[e];
+        sx = __dadd_rn(sx, (double)p.x);
+        sy = __dadd_rn(sy, (double)p.y);
+        sz = __dadd_rn(sz, (double)p.z);
     }
+    const double c = (double)L;
+    out[o] = make_float4(__double2float_rn(__ddiv_rn(sx, c)), __double2float_rn(__ddiv_rn(sy, c)),
+                         __double2float_rn(__ddiv_rn(sz, c)), 0.0f);
 }
 
 }  // namespace
@@ -201,7 +200,7 @@ cudaError_t kmx_voxelize_launch(kmx_ctx* ctx, const float* xyz, int64_t n, int s
     KMX_COUNT_LAUNCH();
     vox_scatter<<<nb, kThreads, 0, st>>>(n, s, assign);
     KMX_COUNT_LAUNCH();
-    vox_centroid<<<kmx_blocks(n * 32, kThreads), kThreads, 0, st>>>(xyz, stride, n, s,
+    vox_centroid<<<kmx_blocks(n, kThreads), kThreads, 0, st>>>(xyz, stride, n, s,
                                                                     reinterpret_cast<float4*>(out4), cap);
     return cudaGetLastError();
 }

@@ -237,7 +237,7 @@ def launch_count() -> int:
 
 def bf16_available() -> bool:
     """Whether this build provides the BF16 tensor-core matching mode."""
-    return False
+    return True
 
 
 def corr_fields(corr: torch.Tensor, n: int):
