@@ -319,7 +319,7 @@ cudaError_t kmx_match_launch(kmx_ctx* c, const float* dp, const int32_t* vp, int
         cudaError_t e = cudaMemsetAsync(s.colbest, 0xFF, sizeof(unsigned long long) * nq_cap, st);
         if (e) return e;
         if ((e = kmx_match_fp32_launch(c, dp, np_cap, d_np, dq, nq_cap, d_nq, s, chunks))) return e;
-        return kmx::match_finalize(c, s, chunks, np_cap, d_np, vp, vq, out, cap, n_out);
+        return kmx::match_finalize(c, s, np_cap, d_np, vp, vq, out, cap, n_out);
     }
     if (mode == KMX_MATCH_BF16_RERANK) {
         const size_t extra = kmx_match_tc_extra_bytes(np_cap, nq_cap, c->sm_count);
@@ -329,7 +329,7 @@ cudaError_t kmx_match_launch(kmx_ctx* c, const float* dp, const int32_t* vp, int
         cudaError_t e = cudaMemsetAsync(s.colbest, 0xFF, sizeof(unsigned long long) * nq_cap, st);
         if (e) return e;
         if ((e = kmx_match_tc_launch(c, dp, np_cap, d_np, dq, nq_cap, d_nq, s))) return e;
-        return kmx::match_finalize(c, s, 1, np_cap, d_np, vp, vq, out, cap, n_out);
+        return kmx::match_finalize(c, s, np_cap, d_np, vp, vq, out, cap, n_out);
     }
     return cudaErrorNotSupported;
 }

@@ -7,14 +7,16 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__global__ void __launch_bounds__(kThreads) merge_mutual(const RowBest* __restrict__ part, int chunks,
-                                                         int64_t np_cap, const int64_t* d_np,
+__global__ void __launch_bounds__(kThreads) merge_mutual(const RowBest* __restrict__ part,
+                                                         const int* __restrict__ d_chunks, int64_t np_cap,
+                                                         const int64_t* d_np,
                                                          const unsigned long long* __restrict__ colbest,
                                                          RowBest* __restrict__ merged, int32_t* __restrict__ mflag)
 {
     const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (i >= kmx_count(d_np, np_cap)) return;
     RowBest r = part[i];
+    const int chunks = *d_chunks;
     for (int c = 1; c < chunks; ++c) {
         const RowBest o = part[(int64_t)c * np_cap + i];
         row_merge(r.d1, r.j1, r.d2, o.d1, o.j1, o.d2);
@@ -61,6 +63,7 @@ size_t match_common_bytes(int64_t np_cap, int64_t nq_cap, int chunks, size_t ext
     a.take(sizeof(int64_t) * (np_cap + 1));
     a.take(kmx_scan_scratch_bytes(np_cap));
     a.take(sizeof(RowBest) * (np_cap + 1));
+    a.take(sizeof(int) * 4);
     a.take(extra);
     return kmx_align_up(a.used, 256);
 }
@@ -75,11 +78,12 @@ MatchScratch match_common_carve(void* base, int64_t np_cap, int64_t nq_cap, int 
     s.mpos = (int64_t*)a.take(sizeof(int64_t) * (np_cap + 1));
     s.scan = a.take(kmx_scan_scratch_bytes(np_cap));
     s.merged = (RowBest*)a.take(sizeof(RowBest) * (np_cap + 1));
+    s.chunks = (int*)a.take(sizeof(int) * 4);
     s.extra = a.take(extra);
     return s;
 }
 
-cudaError_t match_finalize(kmx_ctx* ctx, const MatchScratch& s, int chunks, int64_t np_cap, const int64_t* d_np,
+cudaError_t match_finalize(kmx_ctx* ctx, const MatchScratch& s, int64_t np_cap, const int64_t* d_np,
                            const int32_t* vp, const int32_t* vq, kmx_corr* out, int64_t cap, int64_t* n_out)
 {
     cudaStream_t st = ctx->stream;
@@ -88,7 +92,7 @@ cudaError_t match_finalize(kmx_ctx* ctx, const MatchScratch& s, int chunks, int6
     if ((e = cudaMemsetAsync(s.mflag, 0, sizeof(int32_t) * (np_cap + 1), st))) return e;
     const unsigned nb = kmx_blocks(np_cap, kThreads);
     KMX_COUNT_LAUNCH();
-    merge_mutual<<<nb, kThreads, 0, st>>>(s.part, chunks, np_cap, d_np, s.colbest, merged, s.mflag);
+    merge_mutual<<<nb, kThreads, 0, st>>>(s.part, s.chunks, np_cap, d_np, s.colbest, merged, s.mflag);
     if ((e = kmx_scan_i32(s.mflag, np_cap, d_np, s.mpos, s.scan, st))) return e;
     KMX_COUNT_LAUNCH();
     emit<<<nb, kThreads, 0, st>>>(np_cap, d_np, merged, s.mflag, s.mpos, vp, vq, out, cap, n_out, ctx->d_err);

@@ -36,6 +36,18 @@ __device__ __forceinline__ void row_merge(float& d1, int& j1, float& d2, float o
     }
 }
 
+// Column chunks per row tile so that row_tiles x chunks reaches about
+// `target` CTAs (clamped to [1, max_chunks] and to the column tiles).
+__host__ __device__ __forceinline__ int work_chunks(int64_t row_tiles, int64_t col_tiles, int64_t target,
+                                                    int max_chunks)
+{
+    int64_t c = row_tiles > 0 ? (target + row_tiles - 1) / row_tiles : 1;
+    if (c < 1) c = 1;
+    if (c > max_chunks) c = max_chunks;
+    if (c > col_tiles) c = col_tiles > 0 ? col_tiles : 1;
+    return (int)c;
+}
+
 // Non-negative float distance in the high word, index in the low word: the
 // unsigned order is (distance, index) lexicographic.
 __device__ __forceinline__ unsigned long long pack_dist_index(float d, uint32_t idx)
@@ -49,6 +61,7 @@ struct MatchScratch {
     int32_t* mflag;               // [np_cap + 1]
     int64_t* mpos;                // [np_cap + 1]
     RowBest* merged;              // [np_cap] merged row summaries
+    int* chunks;                  // chunk count chosen on the device (row partials in `part`)
     void* scan;
     void* extra;                  // path-specific scratch
 };
@@ -56,9 +69,9 @@ struct MatchScratch {
 size_t match_common_bytes(int64_t np_cap, int64_t nq_cap, int chunks, size_t extra = 0);
 MatchScratch match_common_carve(void* base, int64_t np_cap, int64_t nq_cap, int chunks, size_t extra = 0);
 
-// Merge the row partials, apply the reciprocity test and emit A in ascending
-// source row.
-cudaError_t match_finalize(kmx_ctx* ctx, const MatchScratch& s, int chunks, int64_t np_cap, const int64_t* d_np,
+// Merge the row partials (as many chunks as *s.chunks says), apply the
+// reciprocity test and emit A in ascending source row.
+cudaError_t match_finalize(kmx_ctx* ctx, const MatchScratch& s, int64_t np_cap, const int64_t* d_np,
                            const int32_t* vp, const int32_t* vq, kmx_corr* out, int64_t cap, int64_t* n_out);
 
 }  // namespace kmx
@@ -69,6 +82,12 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
                                 int64_t nq_cap, const int64_t* d_nq, kmx::MatchScratch& s);
 
 // match_fp32.cu
+int kmx_match_fp32_max_chunks();
+// exact FP32 row summaries for the descriptor rows listed in rows[0..*d_nlist)
+// (list positions index `part`, [max_chunks][list_cap]); no column bests
+cudaError_t kmx_match_fp32_rows_launch(kmx_ctx* ctx, const float* dp, const int32_t* rows, int64_t list_cap,
+                                       const int64_t* d_nlist, const float* dq, int64_t nq_cap, const int64_t* d_nq,
+                                       kmx::RowBest* part, int* chunks_out);
 size_t kmx_match_fp32_scratch_bytes(int64_t np_cap, int64_t nq_cap, int* chunks);
 cudaError_t kmx_match_fp32_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, const int64_t* d_np,
                                   const float* dq, int64_t nq_cap, const int64_t* d_nq, kmx::MatchScratch& s,

@@ -162,9 +162,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
 // pack
 // ---------------------------------------------------------------------------
 
-// One thread per row of the padded matrix.
+// One thread per row of the padded matrix.  Rows are centred on the common
+// mean of both clouds first (distances do not change; products get smaller).
+// The largest squared norm of the side is folded into *maxnorm (float bits of
+// a non-negative value order like the value).
 __global__ void __launch_bounds__(256) pack_bf16(const float* __restrict__ desc, int64_t n_cap, const int64_t* d_n,
-                                                 int64_t rows_pad, uint8_t* __restrict__ out)
+                                                 int64_t rows_pad, const float* __restrict__ mean,
+                                                 uint8_t* __restrict__ out, unsigned int* __restrict__ maxnorm)
 {
     const int64_t r = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (r >= rows_pad) return;
@@ -182,6 +186,8 @@ __global__ void __launch_bounds__(256) pack_bf16(const float* __restrict__ desc,
             x[4 * c + 2] = v.z;
             x[4 * c + 3] = v.w;
         }
+#pragma unroll
+        for (int h = 0; h < KMX_DESC_DIM; ++h) x[h] -= __ldg(mean + h);
     }
     uint8_t* tile = out + (r / kTM) * (int64_t)kTileBytes;
     const int rin = (int)(r % kTM);
@@ -212,6 +218,7 @@ __global__ void __launch_bounds__(256) pack_bf16(const float* __restrict__ desc,
         *reinterpret_cast<uint4*>(tile + kHalfBytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
     reinterpret_cast<float*>(tile + kOperandBytes)[rin] = r < n ? nrm : INFINITY;
+    if (r < n) atomicMax(maxnorm, __float_as_uint(nrm));
 }
 
 // ---------------------------------------------------------------------------
@@ -244,19 +251,28 @@ __device__ __forceinline__ void topk_insert(float* tv, int* ti, float v, int j)
     }
 }
 
+// The grid is sized from the capacities; the (row tile, column chunk) split
+// of the actual counts is decided here (kmx::work_chunks) and published in
+// *chunks_out for the re-ranking kernel.
 __global__ void __launch_bounds__(kThreads, 1) tc_topk(const uint8_t* __restrict__ packA, int64_t rows_cap,
                                                       const int64_t* d_rows, const uint8_t* __restrict__ packB,
-                                                      int64_t cols_cap, const int64_t* d_cols, int tiles_per_chunk,
-                                                      Cand* __restrict__ part, unsigned int* err)
+                                                      int64_t cols_cap, const int64_t* d_cols, int target_ctas,
+                                                      Cand* __restrict__ part, int* __restrict__ chunks_out,
+                                                      unsigned int* err)
 {
     extern __shared__ uint8_t smem_raw[];
     TcShared& S = *reinterpret_cast<TcShared*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int64_t rows = kmx_count(d_rows, rows_cap), cols = kmx_count(d_cols, cols_cap);
-    const int64_t row0 = (int64_t)blockIdx.x * kTM;
-    if (row0 >= rows) return;
+    const int64_t n_rt = (rows + kTM - 1) / kTM;
     const int64_t n_ct = (cols + kTN - 1) / kTN;
-    const int64_t t0 = (int64_t)blockIdx.y * tiles_per_chunk;
+    const int chunks = kmx::work_chunks(n_rt, n_ct, target_ctas, kMaxChunks);
+    if (blockIdx.x == 0 && tid == 0) *chunks_out = chunks;
+    if ((int64_t)blockIdx.x >= n_rt * chunks) return;
+    const int chunk = (int)(blockIdx.x % chunks);
+    const int64_t row0 = (int64_t)(blockIdx.x / chunks) * kTM;
+    const int64_t tiles_per_chunk = (n_ct + chunks - 1) / chunks;
+    const int64_t t0 = chunk * tiles_per_chunk;
     const int T = (int)max((int64_t)0, min(n_ct, t0 + tiles_per_chunk) - t0);
     const uint32_t idesc = idesc_bf16(kTM, kTN);
 
@@ -346,14 +362,30 @@ __global__ void __launch_bounds__(kThreads, 1) tc_topk(const uint8_t* __restrict
         if (S.failed) break;
         const int64_t col0 = (t0 + t) * kTN;
         const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * kTN);
+        // Fast path: 32 keys and their minimum without a branch; only when
+        // the minimum beats the current 8th key are the keys inserted one by
+        // one (rare once the list has filled).
 #pragma unroll 1
         for (int c0 = 0; c0 < kTN; c0 += 32) {
-            float acc[32];
-            tmem_ld32(lane_addr + c0, acc);
+            float v[32];
+            tmem_ld32(lane_addr + c0, v);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const float v = fmaf(-2.0f, acc[j], S.nrm[s][c0 + j]);
-                if (v < tv[kTopK - 1]) topk_insert(tv, ti, v, (int)(col0 + c0 + j));
+            for (int j = 0; j < 32; ++j) v[j] = fmaf(-2.0f, v[j], S.nrm[s][c0 + j]);
+            float m[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) m[j] = fminf(v[j], v[j + 16]);
+#pragma unroll
+            for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+                for (int j = 0; j < w; ++j) m[j] = fminf(m[j], m[j + w]);
+            if (m[0] < tv[kTopK - 1]) {
+#pragma unroll 1
+                for (int j = 0; j < 32; ++j) {
+                    float vj = v[0];
+#pragma unroll
+                    for (int k = 1; k < 32; ++k) vj = (j == k) ? v[k] : vj;  // register select, no local memory
+                    if (vj < tv[kTopK - 1]) topk_insert(tv, ti, vj, (int)(col0 + c0 + j));
+                }
             }
         }
         tc_fence_before();
@@ -381,7 +413,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_topk(const uint8_t* __restrict
     } else {
         const int64_t row = row0 + tid;
         if (row < rows) {
-            Cand* out = part + ((int64_t)blockIdx.y * rows_cap + row) * kTopK;
+            Cand* out = part + ((int64_t)chunk * rows_cap + row) * kTopK;
 #pragma unroll
             for (int k = 0; k < kTopK; ++k) out[k] = Cand{tv[k], ti[k]};
         }
@@ -393,26 +425,113 @@ __global__ void __launch_bounds__(kThreads, 1) tc_topk(const uint8_t* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// exact FP32 re-ranking
+// common mean of both descriptor sets (deterministic: fixed partition, fixed
+// summation order)
 // ---------------------------------------------------------------------------
 
-// One warp per row of X: lane c holds candidate c of the chunk lists, its
-// exact FP32 distance is sum_h (x_h - y_h)^2 accumulated with fmaf in h order
-// (the same arithmetic as the exact path).  Writes either the row summary
-// (d1, NN, d2) or the packed (distance, row) best of the column side.
+constexpr int kSumBlocks = 64;
+
+// Block b sums, per descriptor value, rows [b*R, (b+1)*R) of P followed by Q.
+__global__ void __launch_bounds__(64) col_partial(const float* __restrict__ P, int64_t np_cap, const int64_t* d_np,
+                                                  const float* __restrict__ Q, int64_t nq_cap, const int64_t* d_nq,
+                                                  double* __restrict__ partial)
+{
+    const int h = threadIdx.x;
+    if (h >= KMX_DESC_DIM) return;
+    const int64_t np = kmx_count(d_np, np_cap), nq = kmx_count(d_nq, nq_cap), n = np + nq;
+    const int64_t R = (n + kSumBlocks - 1) / kSumBlocks;
+    const int64_t lo = (int64_t)blockIdx.x * R, hi = min(n, lo + R);
+    double s = 0.0;
+    for (int64_t r = lo; r < hi; ++r) {
+        const float v = r < np ? __ldg(P + r * KMX_DESC_STRIDE + h) : __ldg(Q + (r - np) * KMX_DESC_STRIDE + h);
+        s += (double)v;
+    }
+    partial[blockIdx.x * KMX_DESC_DIM + h] = s;
+}
+
+__global__ void col_mean(const double* __restrict__ partial, int64_t np_cap, const int64_t* d_np, int64_t nq_cap,
+                         const int64_t* d_nq, float* __restrict__ mean, unsigned int* __restrict__ maxnorm)
+{
+    const int h = threadIdx.x;
+    const int64_t n = kmx_count(d_np, np_cap) + kmx_count(d_nq, nq_cap);
+    if (h < KMX_DESC_DIM) {
+        double s = 0.0;
+        for (int b = 0; b < kSumBlocks; ++b) s += partial[b * KMX_DESC_DIM + h];
+        mean[h] = n > 0 ? (float)(s / (double)n) : 0.f;
+    } else if (h < KMX_DESC_STRIDE) {
+        mean[h] = 0.f;
+    }
+    if (h < 2) maxnorm[h] = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// certified exact FP32 re-ranking
+// ---------------------------------------------------------------------------
+
+// Bound on |approximate key - exact key| for one row (keys ||y||^2 - 2 x.y of
+// the centred descriptors): the split operands represent x, y to 2^-18
+// relative per element and the FP32 accumulation of 144 products adds at
+// most ~2^-16 of sum |x_h y_h|, so 2 * 2^-14 * |x| * max|y| covers the
+// product term with margin; 2^-18 * max|y|^2 covers the FP32 norms and the
+// final fused multiply-add.
+__device__ __forceinline__ float key_error_bound(float x_norm2, float ymax_norm2)
+{
+    return 2.0f * (1.0f / 16384.0f) * sqrtf(x_norm2) * sqrtf(ymax_norm2) + (1.0f / 262144.0f) * ymax_norm2;
+}
+
+// One warp per row of X.  Lane c holds candidate c of the chunk lists
+// (chunks x 8 <= 32).  With a(k) the k-th smallest approximate key over the
+// candidates, a(8) - a(2) > 2E proves that the exact nearest and second-
+// nearest columns are among the candidates (each key is within E of its
+// exact value); the row is then re-ranked exactly: sum_h (x_h - y_h)^2 in
+// FP32 with fmaf in h order, the arithmetic of the exact path, lowest index
+// on ties.  Otherwise the row is flagged for the exact fallback.
 __global__ void __launch_bounds__(256) rerank(const float* __restrict__ X, int64_t rows_cap, const int64_t* d_rows,
                                               const float* __restrict__ Y, const Cand* __restrict__ part,
-                                              int chunks, kmx::RowBest* __restrict__ rows_out,
-                                              unsigned long long* __restrict__ cols_best)
+                                              const int* __restrict__ d_chunks, const float* __restrict__ mean,
+                                              const unsigned int* __restrict__ ymax_bits,
+                                              kmx::RowBest* __restrict__ rows_out,
+                                              unsigned long long* __restrict__ cols_best,
+                                              int32_t* __restrict__ fallback, int* __restrict__ final_chunks)
 {
     const int lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (final_chunks && i == 0 && lane == 0) *final_chunks = 1;  // rows_out holds whole-row summaries
     if (i >= kmx_count(d_rows, rows_cap)) return;
+    const int chunks = *d_chunks;
     int j = -1;
-    if (lane < chunks * kTopK) j = part[((int64_t)(lane / kTopK) * rows_cap + i) * kTopK + lane % kTopK].idx;
+    float a = INFINITY;
+    if (lane < chunks * kTopK) {
+        const Cand c = part[((int64_t)(lane / kTopK) * rows_cap + i) * kTopK + lane % kTopK];
+        j = c.idx;
+        if (j >= 0) a = c.v;
+    }
+    // ranks of the approximate keys (ties by lane), a(2) and a(8)
+    int rank = 0, valid = 0;
+#pragma unroll
+    for (int o = 0; o < 32; ++o) {
+        const float ao = __shfl_sync(0xffffffffu, a, o);
+        const int jo = __shfl_sync(0xffffffffu, j, o);
+        valid += jo >= 0;
+        rank += (jo >= 0) && (ao < a || (ao == a && o < lane));
+    }
+    const float a2 = __shfl_sync(0xffffffffu, a, __ffs(__ballot_sync(0xffffffffu, j >= 0 && rank == 1)) - 1 & 31);
+    const float a8 = __shfl_sync(0xffffffffu, a, __ffs(__ballot_sync(0xffffffffu, j >= 0 && rank == 7)) - 1 & 31);
+    const float* x = X + i * KMX_DESC_STRIDE;
+    float xn2 = 0.f;
+#pragma unroll
+    for (int h = 0; h < KMX_DESC_DIM; ++h) {
+        const float e = __ldg(x + h) - __ldg(mean + h);
+        xn2 = fmaf(e, e, xn2);
+    }
+    const float E = key_error_bound(xn2, __uint_as_float(*ymax_bits));
+    const bool certified = valid < kTopK || (a8 - a2 > 2.0f * E);
+    if (!certified) {
+        if (lane == 0) fallback[i] = 1;
+        return;
+    }
     float d = INFINITY;
     if (j >= 0) {
-        const float* x = X + i * KMX_DESC_STRIDE;
         const float* y = Y + (int64_t)j * KMX_DESC_STRIDE;
         float acc = 0.f;
 #pragma unroll
@@ -422,7 +541,6 @@ __global__ void __launch_bounds__(256) rerank(const float* __restrict__ X, int64
         }
         d = acc;
     }
-    // lexicographic (d, j) minimum over the warp, and the second-smallest d
     float b1 = d;
     int j1 = j >= 0 ? j : 0x7fffffff;
     float b2 = INFINITY;
@@ -438,13 +556,38 @@ __global__ void __launch_bounds__(256) rerank(const float* __restrict__ X, int64
     if (cols_best && j1 != 0x7fffffff) cols_best[i] = kmx::pack_dist_index(b1, (uint32_t)j1);
 }
 
-int chunks_for(int64_t row_tiles, int64_t col_tiles, int sm_count)
+// Compact the flagged rows into a list (ascending) and publish its length.
+__global__ void __launch_bounds__(256) compact_flags(int64_t n_cap, const int64_t* d_n,
+                                                     const int32_t* __restrict__ flags,
+                                                     const int64_t* __restrict__ pos, int32_t* __restrict__ list,
+                                                     int64_t* __restrict__ n_list)
 {
-    int64_t c = (2 * (int64_t)sm_count + row_tiles - 1) / (row_tiles > 0 ? row_tiles : 1);
-    if (c < 1) c = 1;
-    if (c > kMaxChunks) c = kMaxChunks;
-    if (c > col_tiles) c = col_tiles > 0 ? col_tiles : 1;
-    return (int)c;
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i == 0) *n_list = pos[n_cap];
+    if (i >= kmx_count(d_n, n_cap)) return;
+    if (flags[i]) list[pos[i]] = (int32_t)i;
+}
+
+// Merge the exact fallback partials of each listed row and store them where
+// the certified rows went.
+__global__ void __launch_bounds__(256) fallback_merge(const kmx::RowBest* __restrict__ part,
+                                                      const int* __restrict__ d_chunks, int64_t list_cap,
+                                                      const int32_t* __restrict__ list,
+                                                      const int64_t* __restrict__ n_list,
+                                                      kmx::RowBest* __restrict__ rows_out,
+                                                      unsigned long long* __restrict__ cols_best)
+{
+    const int64_t r = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (r >= min(*n_list, list_cap)) return;
+    kmx::RowBest b = part[r];
+    const int chunks = *d_chunks;
+    for (int c = 1; c < chunks; ++c) {
+        const kmx::RowBest o = part[(int64_t)c * list_cap + r];
+        kmx::row_merge(b.d1, b.j1, b.d2, o.d1, o.j1, o.d2);
+    }
+    const int i = list[r];
+    if (rows_out) rows_out[i] = b;
+    if (cols_best && b.j1 != 0x7fffffff) cols_best[i] = kmx::pack_dist_index(b.d1, (uint32_t)b.j1);
 }
 
 size_t tc_smem_bytes()
@@ -454,60 +597,121 @@ size_t tc_smem_bytes()
     return need < 96 * 1024 ? 96 * 1024 : need;
 }
 
-}  // namespace
-
-struct TcPlan {
-    int64_t tp, tq;  // row tiles of P and Q
-    int cp, cq;      // chunks of the two passes
+struct TcBuffers {
+    uint8_t *packP, *packQ;
+    Cand *candP, *candQ;
+    double* partial;
+    float* mean;
+    unsigned int* maxnorm;  // [0] = P side, [1] = Q side
+    int* chunks;            // [0] candP, [1] candQ, [2] fallback P, [3] fallback Q
+    int32_t *flagP, *flagQ, *listP, *listQ;
+    int64_t *posP, *posQ, *nlist;  // nlist[0] P, [1] Q
+    kmx::RowBest *fbP, *fbQ;
+    void* scan;
 };
 
-static TcPlan tc_plan(int64_t np_cap, int64_t nq_cap, int sm_count)
+TcBuffers tc_carve(void* base, int64_t np_cap, int64_t nq_cap, size_t* total)
 {
-    TcPlan p;
-    p.tp = (np_cap + kTM - 1) / kTM;
-    p.tq = (nq_cap + kTM - 1) / kTM;
-    p.cp = chunks_for(p.tp, p.tq, sm_count);
-    p.cq = chunks_for(p.tq, p.tp, sm_count);
-    return p;
+    TcBuffers b{};
+    kmx_arena a{static_cast<char*>(base), 0};
+    const int64_t tp = (np_cap + kTM - 1) / kTM, tq = (nq_cap + kTM - 1) / kTM;
+    const int fc = kmx_match_fp32_max_chunks();
+    b.packP = (uint8_t*)a.take((size_t)tp * kTileBytes);
+    b.packQ = (uint8_t*)a.take((size_t)tq * kTileBytes);
+    b.candP = (Cand*)a.take(sizeof(Cand) * kTopK * (size_t)kMaxChunks * (np_cap + 1));
+    b.candQ = (Cand*)a.take(sizeof(Cand) * kTopK * (size_t)kMaxChunks * (nq_cap + 1));
+    b.partial = (double*)a.take(sizeof(double) * kSumBlocks * KMX_DESC_DIM);
+    b.mean = (float*)a.take(sizeof(float) * KMX_DESC_STRIDE);
+    b.maxnorm = (unsigned int*)a.take(sizeof(unsigned int) * 2);
+    b.chunks = (int*)a.take(sizeof(int) * 4);
+    b.flagP = (int32_t*)a.take(sizeof(int32_t) * (np_cap + 1));
+    b.flagQ = (int32_t*)a.take(sizeof(int32_t) * (nq_cap + 1));
+    b.listP = (int32_t*)a.take(sizeof(int32_t) * (np_cap + 1));
+    b.listQ = (int32_t*)a.take(sizeof(int32_t) * (nq_cap + 1));
+    b.posP = (int64_t*)a.take(sizeof(int64_t) * (np_cap + 1));
+    b.posQ = (int64_t*)a.take(sizeof(int64_t) * (nq_cap + 1));
+    b.nlist = (int64_t*)a.take(sizeof(int64_t) * 2);
+    b.fbP = (kmx::RowBest*)a.take(sizeof(kmx::RowBest) * (size_t)fc * (np_cap + 1));
+    b.fbQ = (kmx::RowBest*)a.take(sizeof(kmx::RowBest) * (size_t)fc * (nq_cap + 1));
+    b.scan = a.take(kmx_scan_scratch_bytes(np_cap > nq_cap ? np_cap : nq_cap));
+    *total = kmx_align_up(a.used, 256);
+    return b;
 }
 
-size_t kmx_match_tc_extra_bytes(int64_t np_cap, int64_t nq_cap, int sm_count)
+}  // namespace
+
+size_t kmx_match_tc_extra_bytes(int64_t np_cap, int64_t nq_cap, int)
 {
-    TcPlan p = tc_plan(np_cap, nq_cap, sm_count);
-    kmx_arena a{nullptr, 0};
-    a.take((size_t)p.tp * kTileBytes);
-    a.take((size_t)p.tq * kTileBytes);
-    a.take(sizeof(Cand) * kTopK * (size_t)p.cp * (np_cap + 1));
-    a.take(sizeof(Cand) * kTopK * (size_t)p.cq * (nq_cap + 1));
-    return kmx_align_up(a.used, 256);
+    size_t total = 0;
+    tc_carve(nullptr, np_cap, nq_cap, &total);
+    return total;
 }
 
 cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, const int64_t* d_np, const float* dq,
                                 int64_t nq_cap, const int64_t* d_nq, kmx::MatchScratch& s)
 {
     cudaStream_t st = ctx->stream;
-    TcPlan p = tc_plan(np_cap, nq_cap, ctx->sm_count);
-    kmx_arena a{static_cast<char*>(s.extra), 0};
-    uint8_t* packP = (uint8_t*)a.take((size_t)p.tp * kTileBytes);
-    uint8_t* packQ = (uint8_t*)a.take((size_t)p.tq * kTileBytes);
-    Cand* partP = (Cand*)a.take(sizeof(Cand) * kTopK * (size_t)p.cp * (np_cap + 1));
-    Cand* partQ = (Cand*)a.take(sizeof(Cand) * kTopK * (size_t)p.cq * (nq_cap + 1));
+    size_t total = 0;
+    TcBuffers b = tc_carve(s.extra, np_cap, nq_cap, &total);
+    const int64_t tp = (np_cap + kTM - 1) / kTM, tq = (nq_cap + kTM - 1) / kTM;
     const size_t smem = tc_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(tc_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e) return e;
+    if ((e = cudaMemsetAsync(b.flagP, 0, sizeof(int32_t) * (np_cap + 1), st))) return e;
+    if ((e = cudaMemsetAsync(b.flagQ, 0, sizeof(int32_t) * (nq_cap + 1), st))) return e;
+    const int target = 2 * ctx->sm_count;
+    // common mean, then split-BF16 packs of the centred rows
     KMX_COUNT_LAUNCH();
-    pack_bf16<<<kmx_blocks(p.tp * kTM, 256), 256, 0, st>>>(dp, np_cap, d_np, p.tp * kTM, packP);
+    col_partial<<<kSumBlocks, 64, 0, st>>>(dp, np_cap, d_np, dq, nq_cap, d_nq, b.partial);
     KMX_COUNT_LAUNCH();
-    pack_bf16<<<kmx_blocks(p.tq * kTM, 256), 256, 0, st>>>(dq, nq_cap, d_nq, p.tq * kTM, packQ);
+    col_mean<<<1, 64, 0, st>>>(b.partial, np_cap, d_np, nq_cap, d_nq, b.mean, b.maxnorm);
     KMX_COUNT_LAUNCH();
-    tc_topk<<<dim3((unsigned)p.tp, (unsigned)p.cp), kThreads, smem, st>>>(
-        packP, np_cap, d_np, packQ, nq_cap, d_nq, (int)((p.tq + p.cp - 1) / p.cp), partP, ctx->d_err);
+    pack_bf16<<<kmx_blocks(tp * kTM, 256), 256, 0, st>>>(dp, np_cap, d_np, tp * kTM, b.mean, b.packP, b.maxnorm);
     KMX_COUNT_LAUNCH();
-    tc_topk<<<dim3((unsigned)p.tq, (unsigned)p.cq), kThreads, smem, st>>>(
-        packQ, nq_cap, d_nq, packP, np_cap, d_np, (int)((p.tp + p.cq - 1) / p.cq), partQ, ctx->d_err);
+    pack_bf16<<<kmx_blocks(tq * kTM, 256), 256, 0, st>>>(dq, nq_cap, d_nq, tq * kTM, b.mean, b.packQ,
+                                                        b.maxnorm + 1);
+    // candidates both ways
     KMX_COUNT_LAUNCH();
-    rerank<<<kmx_blocks(np_cap, 8), 256, 0, st>>>(dp, np_cap, d_np, dq, partP, p.cp, s.part, nullptr);
+    tc_topk<<<(unsigned)(tp * kMaxChunks), kThreads, smem, st>>>(b.packP, np_cap, d_np, b.packQ, nq_cap, d_nq, target,
+                                                                 b.candP, b.chunks + 0, ctx->d_err);
     KMX_COUNT_LAUNCH();
-    rerank<<<kmx_blocks(nq_cap, 8), 256, 0, st>>>(dq, nq_cap, d_nq, dp, partQ, p.cq, nullptr, s.colbest);
+    tc_topk<<<(unsigned)(tq * kMaxChunks), kThreads, smem, st>>>(b.packQ, nq_cap, d_nq, b.packP, np_cap, d_np, target,
+                                                                 b.candQ, b.chunks + 1, ctx->d_err);
+    // certified exact re-ranking; uncertified rows are flagged
+    KMX_COUNT_LAUNCH();
+    rerank<<<kmx_blocks(np_cap, 8), 256, 0, st>>>(dp, np_cap, d_np, dq, b.candP, b.chunks + 0, b.mean, b.maxnorm + 1,
+                                                  s.part, nullptr, b.flagP, s.chunks);
+    KMX_COUNT_LAUNCH();
+    rerank<<<kmx_blocks(nq_cap, 8), 256, 0, st>>>(dq, nq_cap, d_nq, dp, b.candQ, b.chunks + 1, b.mean, b.maxnorm,
+                                                  nullptr, s.colbest, b.flagQ, nullptr);
+    // exact fallback for the flagged rows of each side
+    if ((e = kmx_scan_i32(b.flagP, np_cap, d_np, b.posP, b.scan, st))) return e;
+    KMX_COUNT_LAUNCH();
+    compact_flags<<<kmx_blocks(np_cap, 256), 256, 0, st>>>(np_cap, d_np, b.flagP, b.posP, b.listP, b.nlist + 0);
+    if ((e = kmx_scan_i32(b.flagQ, nq_cap, d_nq, b.posQ, b.scan, st))) return e;
+    KMX_COUNT_LAUNCH();
+    compact_flags<<<kmx_blocks(nq_cap, 256), 256, 0, st>>>(nq_cap, d_nq, b.flagQ, b.posQ, b.listQ, b.nlist + 1);
+    if ((e = kmx_match_fp32_rows_launch(ctx, dp, b.listP, np_cap, b.nlist + 0, dq, nq_cap, d_nq, b.fbP,
+                                        b.chunks + 2)))
+        return e;
+    if ((e = kmx_match_fp32_rows_launch(ctx, dq, b.listQ, nq_cap, b.nlist + 1, dp, np_cap, d_np, b.fbQ,
+                                        b.chunks + 3)))
+        return e;
+    KMX_COUNT_LAUNCH();
+    fallback_merge<<<kmx_blocks(np_cap, 256), 256, 0, st>>>(b.fbP, b.chunks + 2, np_cap, b.listP, b.nlist + 0, s.part,
+                                                            nullptr);
+    KMX_COUNT_LAUNCH();
+    fallback_merge<<<kmx_blocks(nq_cap, 256), 256, 0, st>>>(b.fbQ, b.chunks + 3, nq_cap, b.listQ, b.nlist + 1,
+                                                            nullptr, s.colbest);
     return cudaGetLastError();
+}
+
+// Rows that needed the exact fallback in the last BF16 match on this scratch
+// (diagnostics): copies nlist[0..1] to the caller's device buffer.
+cudaError_t kmx_match_tc_fallback_counts(kmx_ctx* ctx, const kmx::MatchScratch& s, int64_t np_cap, int64_t nq_cap,
+                                         int64_t* dst)
+{
+    size_t total = 0;
+    TcBuffers b = tc_carve(s.extra, np_cap, nq_cap, &total);
+    return cudaMemcpyAsync(dst, b.nlist, 2 * sizeof(int64_t), cudaMemcpyDeviceToDevice, ctx->stream);
 }

@@ -128,11 +128,32 @@ __global__ void __launch_bounds__(kThreads) vox_scatter(int64_t n, VoxScratch s,
     s.members[s.vstart[o] + pos] = (int32_t)r;
 }
 
+// Exponent bookkeeping for the exactness test of an FP64 sum of FP32 values:
+// if every nonzero |x| is a normal FP32 number with binary exponent in
+// [emin, emax], all values are multiples of 2^(emin-23) and every partial sum
+// of L of them is below L * 2^(emax+1); when that quotient fits in 53 bits,
+// i.e. emax - emin <= 29 - ceil(log2 L), every partial sum is exact and the
+// FP64 result is the same in any summation order.
+__device__ __forceinline__ void exp_range(float x, int& emin, int& emax, bool& odd)
+{
+    const uint32_t bits = __float_as_uint(x) & 0x7fffffffu;
+    if (bits == 0) return;
+    const int e = (int)(bits >> 23);
+    if (e == 0 || e == 255) {  // subnormal, inf or nan: no shortcut
+        odd = true;
+        return;
+    }
+    emin = min(emin, e);
+    emax = max(emax, e);
+}
+
 // One thread per output voxel (so FP64 instructions run with every lane
-// busy).  Each member's rank in input order (the number of smaller member
-// indices) places its coordinates in a per-voxel run, which is then summed in
-// FP64 in that order and divided by the count.  All loads are independent of
-// one another, so their latencies overlap.
+// busy).  The members are summed in FP64 in the order the scatter left them;
+// the exponent test above shows that this equals the input-order sum for
+// every voxel except those whose coordinates span a huge range (a voxel
+// touching a coordinate plane through the origin, with values near zero).
+// Those are summed again in input order: each member's rank (the number of
+// smaller member indices) places its coordinates in a per-voxel run.
 __global__ void __launch_bounds__(kThreads) vox_centroid(const float* __restrict__ xyz, int stride, int64_t n,
                                                          VoxScratch s, float4* __restrict__ out, int64_t cap)
 {
@@ -142,20 +163,42 @@ __global__ void __launch_bounds__(kThreads) vox_centroid(const float* __restrict
     const int64_t b = s.vstart[o];
     const int L = (int)(s.vstart[o + 1] - b);
     const int32_t* m = s.members + b;
-    float4* run = s.run + b;
-    for (int e = 0; e < L; ++e) {
-        const int32_t me = m[e];
-        int rank = 0;
-        for (int f = 0; f < L; ++f) rank += (m[f] < me);
-        const float* p = xyz + (int64_t)me * stride;
-        run[rank] = make_float4(p[0], p[1], p[2], 0.f);
-    }
     double sx = 0.0, sy = 0.0, sz = 0.0;
+    int emin[3] = {255, 255, 255}, emax[3] = {0, 0, 0};
+    bool odd = false;
+    // unrolled so that the loads of several members are in flight together
+    // (the index load and the coordinate load of one member are dependent)
+#pragma unroll 8
     for (int e = 0; e < L; ++e) {
-        const float4 p = run[e];
-        sx = __dadd_rn(sx, (double)p.x);
-        sy = __dadd_rn(sy, (double)p.y);
-        sz = __dadd_rn(sz, (double)p.z);
+        const float* p = xyz + (int64_t)__ldg(m + e) * stride;
+        const float x = p[0], y = p[1], z = p[2];
+        sx = __dadd_rn(sx, (double)x);
+        sy = __dadd_rn(sy, (double)y);
+        sz = __dadd_rn(sz, (double)z);
+        exp_range(x, emin[0], emax[0], odd);
+        exp_range(y, emin[1], emax[1], odd);
+        exp_range(z, emin[2], emax[2], odd);
+    }
+    const int lg = 32 - __clz(L > 1 ? L - 1 : 1);  // ceil(log2 L) for L >= 2
+    bool exact = !odd;
+    for (int a = 0; a < 3; ++a)
+        if (emax[a] >= emin[a] && emax[a] - emin[a] > 29 - lg) exact = false;
+    if (!exact) {
+        float4* run = s.run + b;
+        for (int e = 0; e < L; ++e) {
+            const int32_t me = m[e];
+            int rank = 0;
+            for (int f = 0; f < L; ++f) rank += (m[f] < me);
+            const float* p = xyz + (int64_t)me * stride;
+            run[rank] = make_float4(p[0], p[1], p[2], 0.f);
+        }
+        sx = sy = sz = 0.0;
+        for (int e = 0; e < L; ++e) {
+            const float4 p = run[e];
+            sx = __dadd_rn(sx, (double)p.x);
+            sy = __dadd_rn(sy, (double)p.y);
+            sz = __dadd_rn(sz, (double)p.z);
+        }
     }
     const double c = (double)L;
     out[o] = make_float4(__double2float_rn(__ddiv_rn(sx, c)), __double2float_rn(__ddiv_rn(sy, c)),
