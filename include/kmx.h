@@ -212,6 +212,37 @@ kmx_status kmx_match(kmx_ctx* ctx, const float* d_desc_p, const int32_t* d_valid
                      const int64_t* d_np, const float* d_desc_q, const int32_t* d_valid_q, int64_t nq_cap,
                      const int64_t* d_nq, int32_t mode, kmx_corr* d_out, int64_t cap, int64_t* d_n_out);
 
+/*
+ * Exact FP32 mutual matching without any allocation (the paper has no
+ * counterpart: this is a service for callers of this library).  Callers that
+ * cannot allocate device memory while they match (a process whose memory
+ * pool already owns the device, a real-time loop that must not block on the
+ * driver's allocator, a host framework that forbids allocation calls from
+ * plug-in code) get the result of kmx_match(..., KMX_MATCH_FP32_EXACT, ...)
+ * without a context and without cudaMalloc, cudaFree or any allocating
+ * library routine.
+ *   Arguments are those of kmx_match (same layouts and meaning) plus the
+ *   cudaStream_t to run on; work goes to the device current at the call.
+ *   Scratch is a fixed device array of about 6 MB inside the library,
+ *   reserved on every device that loads the library until the process exits.
+ *   np_cap and nq_cap may not exceed KMX_NOALLOC_MAX_ROWS: larger requests
+ *   return KMX_EINVAL and launch nothing.
+ *   The first call on a device looks the array's address up (once per
+ *   device, with that device current); make that first call before any
+ *   stream capture.
+ *   All calls share the one array: calls whose work overlaps on the GPU (on
+ *   different streams, or from several threads) race and corrupt each
+ *   other's results; serialise them.
+ *   Device-side overflow of `cap` is visible as *d_n_out > cap (the first cap
+ *   pairs are written); no other device error can occur on this path.
+ * Returns KMX_OK, KMX_EINVAL (bad argument or size beyond the maximum) or
+ * KMX_ECUDA (the symbol lookup or a launch failed).
+ */
+#define KMX_NOALLOC_MAX_ROWS 32768
+kmx_status kmx_match_noalloc(const float* d_desc_p, const int32_t* d_valid_p, int64_t np_cap, const int64_t* d_np,
+                             const float* d_desc_q, const int32_t* d_valid_q, int64_t nq_cap, const int64_t* d_nq,
+                             kmx_corr* d_out, int64_t cap, int64_t* d_n_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif
