@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--impl", default="kmx", choices=["kmx", "reference"])
     ap.add_argument("--match", default="auto", choices=["auto", "fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="launch the calls directly instead of replaying "
+                                                             "the pair captured as one CUDA graph")
     return ap.parse_args()
 
 
@@ -209,8 +211,19 @@ def run_kmx(args):
         mode = min((kmx.MATCH_FP32_EXACT, kmx.MATCH_BF16_RERANK),
                    key=lambda m: mode_ms["fp32_exact" if m == kmx.MATCH_FP32_EXACT else "bf16_certified"])
 
-    def step():
+    def direct_step():
         pair.run(len(src), len(tgt), ps, pt, mode)
+
+    graph = None
+    if not args.no_graph:
+        pair.run_checked(len(src), len(tgt), ps, pt, mode)  # final sizes before capture
+        graph = pair.capture(len(src), len(tgt), ps, pt, mode)
+
+    def step():
+        if graph is not None:
+            graph.replay()
+        else:
+            direct_step()
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -253,7 +266,7 @@ def run_kmx(args):
     # ---- end to end through host buffers
     e2e = end_to_end(torch, ctx, pair, src, tgt, ps, pt, mode, flush, args.steps, world)
 
-    launches = count_launches(torch, step)
+    launches = count_launches(torch, direct_step)  # the captured graph holds the same kernels
     n_src_vox = int(pair.src.n_vox.item())
     n_tgt_vox = int(pair.tgt.n_vox.item())
     n_corr = int(pair.n_corr.item())
@@ -271,6 +284,7 @@ def run_kmx(args):
         latency_ms=dict(p50=float(np.percentile(step_ms, 50)), p99=float(np.percentile(step_ms, 99))),
         wall_s=wall, stages_ms=stages, roofline=roof, e2e=e2e, gpu_launches=launches * args.steps,
         gpu_launches_per_step=launches, clocks=clk, match_mode_ms_per_step=mode_ms or None,
+        cuda_graph=graph is not None,
     )
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(src, tgt, vps, vpt)
@@ -294,9 +308,7 @@ def stage_times(torch, ctx, pair, n_src, n_tgt, ps, pt, mode, flush, reps):
             e[0].record(stream)
             ctx.voxelize(cs.raw[:n_raw], prm.voxel, cap=cs.n_cap, out4=cs.vox4, n_out=cs.n_vox)
             e[1].record(stream)
-            if cs.grid is not None:
-                cs.grid.free()
-            cs.grid = ctx.build_grid(cs.vox4, prm.r_fpfh, n_cap=cs.n_cap, d_n=cs.n_vox)
+            cs.grid = ctx.build_grid(cs.vox4, prm.r_fpfh, n_cap=cs.n_cap, d_n=cs.n_vox, reuse=cs.grid)
             e[2].record(stream)
             b = ctx.normals(cs.grid, prm, cs.nbr_cap, out=cs.bufs)
             e[3].record(stream)

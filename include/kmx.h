@@ -141,6 +141,11 @@ kmx_status kmx_voxelize(kmx_ctx* ctx, const float* d_xyz, int64_t n_raw, int32_t
  *   d_n       nullable device int64 actual count (e.g. kmx_voxelize's d_n_out).
  *   cell      cell edge > 0.  Searches visit the 27 cells around a point, so
  *             kmx_normals requires cell >= r_fpfh (else KMX_EINVAL).
+ *   out       *out == NULL: a new grid is allocated (stream-ordered) and
+ *             returned.  *out != NULL: that grid (built on this context with a
+ *             capacity >= n_cap) is rebuilt in place over the new points
+ *             without allocating, which keeps a whole pair free of
+ *             allocations (e.g. for CUDA-graph capture).
  * Device errors: KMX_ERANGE if a cell index does not fit in 21 bits.
  */
 kmx_status kmx_build_grid(kmx_ctx* ctx, const float* d_xyz4, int64_t n_cap, const int64_t* d_n, float cell,

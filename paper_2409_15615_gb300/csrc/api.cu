@@ -190,8 +190,18 @@ kmx_status kmx_build_grid(kmx_ctx* c, const float* d_xyz4, int64_t n_cap, const 
     if (!out || n_cap < 0 || n_cap > INT32_MAX - 1 || !(cell > 0.0f) || !isfinite(cell) ||
         (n_cap > 0 && !d_xyz4) || (d_xyz4 && !aligned16(d_xyz4)))
         return fail(c, KMX_EINVAL, "kmx_build_grid: bad argument");
-    *out = nullptr;
     DeviceGuard dg(c->device);
+    if (*out) {  // rebuild in place: same context, enough capacity, no allocation
+        kmx_grid* g = *out;
+        if (g->ctx != c || g->n_cap < n_cap) return fail(c, KMX_EINVAL, "kmx_build_grid: grid cannot be reused");
+        g->d_n = d_n;
+        g->cell = cell;
+        g->pts = reinterpret_cast<const float4*>(d_xyz4);
+        g->stream = c->stream;
+        kmx_status s = ensure_ws(c, kmx_grid_scratch_bytes(g->n_cap, g->table_size));
+        if (s != KMX_OK) return s;
+        return launched(c, kmx_grid_build_launch(c, g, c->ws), "kmx_build_grid");
+    }
     kmx_grid* g = new (std::nothrow) kmx_grid();
     if (!g) return KMX_ENOMEM;
     g->ctx = c;

@@ -143,6 +143,24 @@ struct kmx_arena {
     }
 };
 
+// One-time, per-device set-up actions (function attributes): bit `bit` of a
+// per-device mask records that fn() succeeded on the current device.
+enum { kmx_attr_fp32_tiles = 0, kmx_attr_tc_topk = 1 };
+template <typename F>
+inline cudaError_t kmx_once_per_device(int bit, F fn)
+{
+    static std::atomic<unsigned long long> done[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return fn();
+    const unsigned long long m = 1ull << bit;
+    if (done[dev].load(std::memory_order_acquire) & m) return cudaSuccess;
+    e = fn();
+    if (e == cudaSuccess) done[dev].fetch_or(m, std::memory_order_release);
+    return e;
+}
+
 // scan.cu: exclusive prefix sum of n int32 values (values at i >= *d_n count
 // as 0) into out[0..n] (int64, out[n] = total).  Scratch bytes needed:
 size_t kmx_scan_scratch_bytes(int64_t n);

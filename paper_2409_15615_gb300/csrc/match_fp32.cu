@@ -1,15 +1,20 @@
 // Mutual nearest-neighbour matching of descriptors (reciprocity test,
-// Sec. III-C), exact FP32 path on CUDA cores, plus the parts shared with the
-// tensor-core path (partial merge, mutual test, ordered emission).
+// Sec. III-C), exact FP32 path on CUDA cores.
 //
-// Distances are sum_h (x_h - y_h)^2 over the 33 descriptor values.  A CTA
-// owns a 128-row tile of the source descriptors and streams a chunk of
-// 128-column target tiles through shared memory; each thread keeps an 8x8
-// block of distances.  Per row it keeps (best, its column, second best) with
-// ties to the lower column; per column the best (distance, row) is folded
-// into a packed 64-bit key with atomicMin, which orders by distance then by
-// row.  Row partials of the column chunks are merged afterwards, then a pair
-// (i, j) is kept iff j = NN_Q(i) and NN_P(j) = i, emitted in ascending i.
+// Distances are sum_h (x_h - y_h)^2 over the 33 descriptor values, each term
+// added with one fused multiply-add in h order.  A CTA owns a 128-row tile of
+// the source descriptors and streams a chunk of 128-column target tiles
+// through shared memory (double-buffered: the next tile is prefetched into
+// registers while the current one is used); each thread keeps an 8x8 block of
+// distances.  The arithmetic uses Blackwell's paired FP32 instructions on
+// column pairs: d = x + (-y) (the target tile is stored negated, and
+// x + (-y) == x - y exactly) and acc = fma(d, d, acc), two lanes per
+// instruction, so every distance is bit-identical to the scalar chain.
+// Per row the kernel keeps (best, its column, second best) with ties to the
+// lower column; per column the best (distance, row) is folded into a packed
+// 64-bit key with atomicMin, which orders by distance then by row.  Row
+// partials of the column chunks are merged afterwards, then a pair (i, j) is
+// kept iff j = NN_Q(i) and NN_P(j) = i, emitted in ascending i.
 #include "kmx_internal.cuh"
 #include "match_common.cuh"
 
@@ -19,25 +24,47 @@ constexpr int kThreads = 256;
 constexpr int kTile = 128;
 constexpr int kDim = KMX_DESC_DIM;
 constexpr int kStride = KMX_DESC_STRIDE;
+constexpr int kVec = kStride / 4;                                // float4 per descriptor row
+constexpr int kLoads = (kTile * kVec + kThreads - 1) / kThreads;  // float4 loads per thread per tile
 
-// Load a 128-row tile transposed into smem[k][r] (k < 33); rows >= n are 0.
-// With a row list, tile row r is descriptor row list[row0 + r].
-__device__ __forceinline__ void load_tile_t(float (*sm)[kTile], const float* __restrict__ desc,
-                                            const int32_t* __restrict__ list, int64_t row0, int64_t n)
+struct FpShared {
+    float P[kDim][kTile];          // source tile, transposed
+    float Qn[2][kDim][kTile];      // negated target tiles, transposed, double-buffered
+    unsigned long long colred[kThreads / 32][kTile];
+};
+
+// This thread's share of a 128-row tile (rows >= n read as zero).  With a
+// row list, tile row r is descriptor row list[row0 + r].
+__device__ __forceinline__ void fetch_tile(float4 (&reg)[kLoads], const float* __restrict__ desc,
+                                           const int32_t* __restrict__ list, int64_t row0, int64_t n)
 {
-    for (int idx = threadIdx.x; idx < kTile * (kStride / 4); idx += kThreads) {
-        const int r = idx / (kStride / 4);
-        const int c4 = idx % (kStride / 4);
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (row0 + r < n) {
-            const int64_t src = list ? (int64_t)list[row0 + r] : row0 + r;
-            v = __ldg(reinterpret_cast<const float4*>(desc + src * kStride) + c4);
+#pragma unroll
+    for (int it = 0; it < kLoads; ++it) {
+        const int idx = threadIdx.x + it * kThreads;
+        reg[it] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (idx < kTile * kVec) {
+            const int r = idx / kVec, c4 = idx % kVec;
+            if (row0 + r < n) {
+                const int64_t src = list ? (int64_t)list[row0 + r] : row0 + r;
+                reg[it] = __ldg(reinterpret_cast<const float4*>(desc + src * kStride) + c4);
+            }
         }
-        const int k = c4 * 4;
-        sm[k][r] = v.x;
-        if (k + 1 < kDim) sm[k + 1][r] = v.y;
-        if (k + 2 < kDim) sm[k + 2][r] = v.z;
-        if (k + 3 < kDim) sm[k + 3][r] = v.w;
+    }
+}
+
+// Scatter the fetched share into smem[k][r] (k < 33), optionally negated.
+__device__ __forceinline__ void store_tile(float (*sm)[kTile], const float4 (&reg)[kLoads], float sign)
+{
+#pragma unroll
+    for (int it = 0; it < kLoads; ++it) {
+        const int idx = threadIdx.x + it * kThreads;
+        if (idx < kTile * kVec) {
+            const int r = idx / kVec, k = (idx % kVec) * 4;
+            sm[k][r] = sign * reg[it].x;
+            if (k + 1 < kDim) sm[k + 1][r] = sign * reg[it].y;
+            if (k + 2 < kDim) sm[k + 2][r] = sign * reg[it].z;
+            if (k + 3 < kDim) sm[k + 3][r] = sign * reg[it].w;
+        }
     }
 }
 
@@ -54,9 +81,8 @@ __global__ void __launch_bounds__(kThreads) match_tiles_fp32(const float* __rest
                                                              unsigned long long* __restrict__ colbest,
                                                              int* __restrict__ chunks_out)
 {
-    __shared__ __align__(16) float Ps[kDim][kTile];
-    __shared__ __align__(16) float Qs[kDim][kTile];
-    __shared__ unsigned long long colred[kThreads / 32][kTile];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FpShared& S = *reinterpret_cast<FpShared*>(smem_raw);
     const int64_t np = kmx_count(d_np, np_cap), nq = kmx_count(d_nq, nq_cap);
     const int64_t npt = (np + kTile - 1) / kTile;
     const int64_t nqt = (nq + kTile - 1) / kTile;
@@ -67,10 +93,20 @@ __global__ void __launch_bounds__(kThreads) match_tiles_fp32(const float* __rest
     const int64_t row0 = (int64_t)(blockIdx.x / chunks) * kTile;
     const int64_t tiles_per_chunk = (nqt + chunks - 1) / chunks;
     const int64_t qt0 = chunk * tiles_per_chunk;
-    const int tx = threadIdx.x & 15;                              // column group
+    const int T = (int)max((int64_t)0, min(nqt, qt0 + tiles_per_chunk) - qt0);
+    const int tx = threadIdx.x & 15;                                   // column group
     const int ty = (threadIdx.x >> 5) * 2 + ((threadIdx.x >> 4) & 1);  // row group
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    load_tile_t(Ps, dp, rows_list, row0, np);
+
+    float4 reg[kLoads];
+    fetch_tile(reg, dp, rows_list, row0, np);
+    store_tile(S.P, reg, 1.0f);
+    if (T > 0) {
+        fetch_tile(reg, dq, nullptr, qt0 * kTile, nq);
+        store_tile(S.Qn[0], reg, -1.0f);
+    }
+    __syncthreads();
+
     float b1[8], b2[8];
     int j1[8];
 #pragma unroll
@@ -79,39 +115,45 @@ __global__ void __launch_bounds__(kThreads) match_tiles_fp32(const float* __rest
         b2[i] = INFINITY;
         j1[i] = 0x7fffffff;
     }
-    for (int64_t qt = qt0; qt < qt0 + tiles_per_chunk && qt < nqt; ++qt) {
-        const int64_t col0 = qt * kTile;
-        __syncthreads();
-        load_tile_t(Qs, dq, nullptr, col0, nq);
-        __syncthreads();
-        float acc[8][8];
+    for (int t = 0; t < T; ++t) {
+        const int buf = t & 1;
+        const int64_t col0 = (qt0 + t) * kTile;
+        if (t + 1 < T) fetch_tile(reg, dq, nullptr, col0 + kTile, nq);  // in flight during the math
+        float2 acc[8][4];
 #pragma unroll
         for (int i = 0; i < 8; ++i)
 #pragma unroll
-            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+            for (int jp = 0; jp < 4; ++jp) acc[i][jp] = make_float2(0.f, 0.f);
 #pragma unroll 3
         for (int k = 0; k < kDim; ++k) {
-            const float4 a0 = *reinterpret_cast<const float4*>(&Ps[k][ty * 8]);
-            const float4 a1 = *reinterpret_cast<const float4*>(&Ps[k][ty * 8 + 4]);
-            const float4 c0 = *reinterpret_cast<const float4*>(&Qs[k][tx * 8]);
-            const float4 c1 = *reinterpret_cast<const float4*>(&Qs[k][tx * 8 + 4]);
+            const float4 a0 = *reinterpret_cast<const float4*>(&S.P[k][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&S.P[k][ty * 8 + 4]);
+            const float4 c0 = *reinterpret_cast<const float4*>(&S.Qn[buf][k][tx * 8]);
+            const float4 c1 = *reinterpret_cast<const float4*>(&S.Qn[buf][k][tx * 8 + 4]);
             const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float c[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+            const float2 nc[4] = {make_float2(c0.x, c0.y), make_float2(c0.z, c0.w), make_float2(c1.x, c1.y),
+                                  make_float2(c1.z, c1.w)};
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int i = 0; i < 8; ++i) {
+                const float2 ai = make_float2(a[i], a[i]);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float d = a[i] - c[j];
-                    acc[i][j] = fmaf(d, d, acc[i][j]);
+                for (int jp = 0; jp < 4; ++jp) {
+                    const float2 d = __fadd2_rn(ai, nc[jp]);
+                    acc[i][jp] = __ffma2_rn(d, d, acc[i][jp]);
                 }
+            }
         }
-        // row bests (columns visited in ascending order)
+        // row bests (this thread's columns visited in ascending order)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int64_t col = col0 + tx * 8 + j;
-            if (col < nq) {
+        for (int jp = 0; jp < 4; ++jp) {
 #pragma unroll
-                for (int i = 0; i < 8; ++i) kmx::row_update(b1[i], j1[i], b2[i], acc[i][j], (int)col);
+            for (int h = 0; h < 2; ++h) {
+                const int64_t col = col0 + tx * 8 + 2 * jp + h;
+                if (col < nq) {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        kmx::row_update(b1[i], j1[i], b2[i], h ? acc[i][jp].y : acc[i][jp].x, (int)col);
+                }
             }
         }
         // column bests: this thread's 8 rows, then the partner half-warp, then
@@ -124,26 +166,29 @@ __global__ void __launch_bounds__(kThreads) match_tiles_fp32(const float* __rest
                 for (int i = 0; i < 8; ++i) {
                     const int64_t row = row0 + ty * 8 + i;
                     if (row < np) {
-                        const unsigned long long key = kmx::pack_dist_index(acc[i][j], (uint32_t)row);
+                        const float dij = (j & 1) ? acc[i][j >> 1].y : acc[i][j >> 1].x;
+                        const unsigned long long key = kmx::pack_dist_index(dij, (uint32_t)row);
                         best = key < best ? key : best;
                     }
                 }
                 const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, 16);
                 best = other < best ? other : best;
-                if (lane < 16) colred[warp][tx * 8 + j] = best;
+                if (lane < 16) S.colred[warp][tx * 8 + j] = best;
             }
             __syncthreads();
             if (threadIdx.x < kTile) {
-                unsigned long long best = colred[0][threadIdx.x];
+                unsigned long long best = S.colred[0][threadIdx.x];
 #pragma unroll
                 for (int w = 1; w < kThreads / 32; ++w) {
-                    const unsigned long long o = colred[w][threadIdx.x];
+                    const unsigned long long o = S.colred[w][threadIdx.x];
                     best = o < best ? o : best;
                 }
                 const int64_t col = col0 + threadIdx.x;
                 if (col < nq && best != ~0ull) atomicMin(&colbest[col], best);
             }
         }
+        if (t + 1 < T) store_tile(S.Qn[buf ^ 1], reg, -1.0f);
+        __syncthreads();
     }
     // merge the 16 column groups of each row (lanes sharing ty sit in one
     // half-warp: xor offsets 1..8)
@@ -163,11 +208,21 @@ __global__ void __launch_bounds__(kThreads) match_tiles_fp32(const float* __rest
     }
 }
 
-}  // namespace
-
 // Up to this many column chunks per row tile; the count used is decided on
 // the device (kmx::work_chunks) and published in MatchScratch::chunks.
 constexpr int kMaxChunksFp32 = 8;
+
+// Opt in to >48 KB of dynamic shared memory once per device (the first call
+// happens before any capture of a pair into a CUDA graph).
+cudaError_t set_smem_attr()
+{
+    return kmx_once_per_device(kmx_attr_fp32_tiles, [] {
+        return cudaFuncSetAttribute(match_tiles_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sizeof(FpShared));
+    });
+}
+
+}  // namespace
 
 size_t kmx_match_fp32_scratch_bytes(int64_t np_cap, int64_t nq_cap, int* chunks)
 {
@@ -179,10 +234,12 @@ cudaError_t kmx_match_fp32_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap,
                                   const float* dq, int64_t nq_cap, const int64_t* d_nq, kmx::MatchScratch& s,
                                   int max_chunks)
 {
+    cudaError_t e = set_smem_attr();
+    if (e) return e;
     const int64_t npt = (np_cap + kTile - 1) / kTile;
     const int64_t blocks = (npt > 0 ? npt : 1) * max_chunks;
     KMX_COUNT_LAUNCH();
-    match_tiles_fp32<<<(unsigned)blocks, kThreads, 0, ctx->stream>>>(
+    match_tiles_fp32<<<(unsigned)blocks, kThreads, sizeof(FpShared), ctx->stream>>>(
         dp, nullptr, np_cap, d_np, dq, nq_cap, d_nq, 4 * ctx->sm_count, max_chunks, s.part, s.colbest, s.chunks);
     return cudaGetLastError();
 }
@@ -191,12 +248,13 @@ cudaError_t kmx_match_fp32_rows_launch(kmx_ctx* ctx, const float* dp, const int3
                                        const int64_t* d_nlist, const float* dq, int64_t nq_cap, const int64_t* d_nq,
                                        kmx::RowBest* part, int* chunks_out)
 {
+    cudaError_t e = set_smem_attr();
+    if (e) return e;
     const int64_t npt = (list_cap + kTile - 1) / kTile;
     const int64_t blocks = (npt > 0 ? npt : 1) * kMaxChunksFp32;
     KMX_COUNT_LAUNCH();
-    match_tiles_fp32<<<(unsigned)blocks, kThreads, 0, ctx->stream>>>(dp, rows, list_cap, d_nlist, dq, nq_cap, d_nq,
-                                                                     4 * ctx->sm_count, kMaxChunksFp32, part,
-                                                                     nullptr, chunks_out);
+    match_tiles_fp32<<<(unsigned)blocks, kThreads, sizeof(FpShared), ctx->stream>>>(
+        dp, rows, list_cap, d_nlist, dq, nq_cap, d_nq, 4 * ctx->sm_count, kMaxChunksFp32, part, nullptr, chunks_out);
     return cudaGetLastError();
 }
 

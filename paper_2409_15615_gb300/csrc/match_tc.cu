@@ -655,7 +655,9 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
     TcBuffers b = tc_carve(s.extra, np_cap, nq_cap, &total);
     const int64_t tp = (np_cap + kTM - 1) / kTM, tq = (nq_cap + kTM - 1) / kTM;
     const size_t smem = tc_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(tc_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = kmx_once_per_device(kmx_attr_tc_topk, [smem] {
+        return cudaFuncSetAttribute(tc_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
     if (e) return e;
     if ((e = cudaMemsetAsync(b.flagP, 0, sizeof(int32_t) * (np_cap + 1), st))) return e;
     if ((e = cudaMemsetAsync(b.flagQ, 0, sizeof(int32_t) * (nq_cap + 1), st))) return e;

@@ -181,8 +181,17 @@ class Context:
                                           _ptr(assign)), "kmx_voxelize")
         return out4, n_out, assign
 
-    def build_grid(self, xyz4: torch.Tensor, cell: float, n_cap: int | None = None, d_n=None) -> Grid:
+    def build_grid(self, xyz4: torch.Tensor, cell: float, n_cap: int | None = None, d_n=None,
+                   reuse: Grid | None = None) -> Grid:
+        """kmx_build_grid.  With ``reuse`` (a grid of this context with enough
+        capacity) the grid is rebuilt in place, without allocating."""
         n_cap = xyz4.shape[0] if n_cap is None else n_cap
+        if reuse is not None and reuse.handle:
+            h = C.c_void_p(reuse.handle.value if isinstance(reuse.handle, C.c_void_p) else reuse.handle)
+            self._check(self.lib.kmx_build_grid(self.h, _ptr(xyz4), n_cap, _ptr(d_n), float(cell), C.byref(h)),
+                        "kmx_build_grid")
+            reuse.points, reuse.d_n, reuse.cell = xyz4, d_n, cell
+            return reuse
         h = C.c_void_p()
         self._check(self.lib.kmx_build_grid(self.h, _ptr(xyz4), n_cap, _ptr(d_n), float(cell), C.byref(h)),
                     "kmx_build_grid")

@@ -44,9 +44,8 @@ class CloudState:
         ctx = self.ctx
         src = self.raw if raw is None else raw
         ctx.voxelize(src[:n_raw], params.voxel, cap=self.n_cap, out4=self.vox4, n_out=self.n_vox)
-        if self.grid is not None:
-            self.grid.free()
-        self.grid = ctx.build_grid(self.vox4, params.r_fpfh, n_cap=self.n_cap, d_n=self.n_vox)
+        # the grid is built once and then rebuilt in place: a pair allocates nothing
+        self.grid = ctx.build_grid(self.vox4, params.r_fpfh, n_cap=self.n_cap, d_n=self.n_vox, reuse=self.grid)
         b = ctx.normals(self.grid, params, self.nbr_cap, out=self.bufs)
         ctx.fasterpfh(self.grid, params, b["normal4"], b["flags"], b["offs"], b["nbr"], out=self.out)
         return self
@@ -76,6 +75,24 @@ class PairState:
                        d_np=s.out["n_valid"], d_nq=t.out["n_valid"], mode=mode, cap=self.cap, out=self.corr,
                        n_out=self.n_corr)
         return self
+
+    def capture(self, n_src: int, n_tgt: int, p_src: kmx.Params, p_tgt: kmx.Params, mode: int):
+        """Record one pair as a CUDA graph.  Buffers, grids and the context
+        scratch must already have their final sizes (call run_checked
+        first), so the recorded sequence allocates nothing.  Replaying the
+        graph reruns the pair on whatever is in self.src.raw / self.tgt.raw."""
+        ctx = self.ctx
+        cap_stream = torch.cuda.Stream(device=ctx.device)
+        old = ctx.stream
+        cap_stream.wait_stream(torch.cuda.current_stream(ctx.device))
+        ctx.set_stream(cap_stream)
+        graph = torch.cuda.CUDAGraph()
+        try:
+            with torch.cuda.graph(graph, stream=cap_stream):
+                self.run(n_src, n_tgt, p_src, p_tgt, mode)
+        finally:
+            ctx.set_stream(old)
+        return graph
 
     def run_checked(self, n_src, n_tgt, p_src, p_tgt, mode):
         """run() then synchronise; grows the neighbour lists and reruns once
