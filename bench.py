@@ -32,6 +32,10 @@ sys.path.insert(0, ROOT)
 from synth import lidar_pair  # noqa: E402
 
 WORKLOAD = dict(name="lidar_pair_64beam_2048az_v0.3", voxel=0.3, az_bins=2048, seed=1000)
+
+# DRAM bytes (read + write) of one launch, from the ncu captures summarised in
+# profiles/; an entry is removed whenever its kernel changes.
+PROFILED_TRAFFIC = {"match_tiles_fp32": 3848448}
 METRIC = "Faster-PFH+mutual-NN pairs/s (LiDAR scan pair, voxel 0.3 m)"
 
 
@@ -378,9 +382,10 @@ def roofline(stages, work, mode):
             achieved = flops / (match_ms / 1000.0) / 1e12
             peak = peaks["fp32_tflops"]
             return dict(kernel="match_tiles_fp32 (kmx_match, FP32 exact)", bound="alu", achieved=achieved, peak=peak,
-                        unit="TFLOP/s", frac=achieved / peak, traffic=None,
+                        unit="TFLOP/s", frac=achieved / peak, traffic=PROFILED_TRAFFIC.get("match_tiles_fp32"),
                         note="3 flops (sub + fma) per descriptor element pair; peak = 152 SMs x 128 FP32 lanes x 2 "
-                             "x 2.07 GHz")
+                             "x 2.07 GHz (derived, no measured FP32 peak); traffic = DRAM read+write bytes of one "
+                             "launch from ncu (profiles/match_tiles_fp32_lidar_pair.md)")
         flops = 2.0 * m["np"] * m["nq"] * 33
         achieved = flops / (match_ms / 1000.0) / 1e12
         peak = peaks["bf16_tflops"]
