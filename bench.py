@@ -49,6 +49,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch the calls directly instead of replaying "
                                                              "the pair captured as one CUDA graph")
+    ap.add_argument("--batch-pairs", type=int, default=32,
+                    help="also time a batch of this many uneven pairs in one graph launch (0 = skip)")
+    ap.add_argument("--serve-requests", type=int, default=64,
+                    help="also run the serving loop with this many requests per rate (0 = skip)")
+    ap.add_argument("--serve-rates", default="100,1000", help="request rates (req/s) for the serving loop")
     return ap.parse_args()
 
 
@@ -290,9 +295,72 @@ def run_kmx(args):
         gpu_launches_per_step=launches, clocks=clk, match_mode_ms_per_step=mode_ms or None,
         cuda_graph=graph is not None,
     )
+    if args.batch_pairs > 0:
+        line["batched"] = bench_batched(torch, args.batch_pairs, rank)
+    if args.serve_requests > 0:
+        line["serving"] = bench_serving(torch, args.serve_requests, [float(x) for x in args.serve_rates.split(",")],
+                                        rank)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(src, tgt, vps, vpt)
     print(json.dumps(line), flush=True)
+
+
+def bench_batched(torch, n_pairs, rank):
+    """Uneven pairs (raw size log-uniform in [5k, 300k], scene and LiDAR
+    generators, voxel in {0.05, 0.1, 0.3}) in one graph launch, lanes and
+    match mode autotuned, against the same pairs run one at a time."""
+    from synth import batch_pairs
+
+    from paper_2409_15615_gb300 import batch
+
+    specs = [batch.PairSpec(p["src"], p["tgt"], p["voxel"], tuple(p["vp_src"]), tuple(p["vp_tgt"]))
+             for p in batch_pairs(7000 + rank, n_pairs=n_pairs)]
+    runner, table = batch.autotune(specs, lane_options=(1, 4, 8, 16))
+    best = min(table, key=lambda r: r["batch_s"])
+    sec = batch.time_batch(runner, reps=5, graph=True)
+    # the plain path: the same pairs one at a time, direct launches, one stream
+    plain = batch.BatchRunner(specs, lanes=1, mode=best["mode"]).prepare()
+    plain_sec = batch.time_batch(plain, reps=3, graph=False)
+    n_corr = int(runner.n_corr.sum().item())
+    same = bool(torch.equal(runner.n_corr, plain.n_corr))
+    runner.close()
+    plain.close()
+    return dict(pairs=n_pairs, lanes=best["lanes"], mode="fp32_exact" if best["mode"] == 0 else "bf16_certified",
+                batch_ms=sec * 1e3, pairs_per_s=n_pairs / sec, plain_pairs_per_s=n_pairs / plain_sec,
+                speedup_vs_plain=plain_sec / sec, raw_points=int(sum(len(s.src) + len(s.tgt) for s in specs)),
+                correspondences=n_corr, same_counts_as_plain=same, autotune=table)
+
+
+def bench_serving(torch, n_req, rates, rank):
+    """Poisson request streams against resident maps (one indoor room map
+    and one LiDAR map), queries log-uniform in [5k, 300k] raw points."""
+    from synth import lidar_pair, scene_pair
+    from synth.scenes import map_cloud
+
+    from paper_2409_15615_gb300 import kmx, serve
+
+    ctx = kmx.Context(0)
+    maps = []
+    for k, n in enumerate((400_000, 200_000)):
+        xyz, vp, kind = map_cloud(9000 + k, n)
+        maps.append(serve.ResidentMap(ctx, xyz, 0.1 if kind == "indoor" else 0.3, vp))
+    rng = np.random.default_rng(11 + rank)
+    out = []
+    for rate in rates:
+        arr = serve.poisson_arrivals(rate, n_req, seed=int(rate) + rank)
+        reqs = []
+        for i in range(n_req):
+            n = int(round(np.exp(rng.uniform(np.log(5000), np.log(300000)))))
+            q, _, _, _, vpq, _ = scene_pair(int(rng.integers(1 << 30)), n=n)
+            reqs.append(serve.Request(i, i % len(maps), q, maps[i % len(maps)].voxel, tuple(vpq), float(arr[i])))
+        srv = serve.Server(maps, slots=8)
+        done = srv.run(reqs, realtime=True)
+        st = serve.latency_stats(done)
+        st["rate_req_s"] = rate
+        out.append(st)
+    ctx.close()
+    return dict(requests_per_rate=n_req, slots=8, budget_gb=60, maps=[int(len(m.desc)) for m in maps],
+                per_rate=out)
 
 
 def stage_times(torch, ctx, pair, n_src, n_tgt, ps, pt, mode, flush, reps):

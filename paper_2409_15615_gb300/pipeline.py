@@ -67,13 +67,18 @@ class PairState:
         self.n_corr = torch.zeros(1, dtype=torch.int64, device=ctx.device)
         self.cap = cap
 
-    def run(self, n_src: int, n_tgt: int, p_src: kmx.Params, p_tgt: kmx.Params, mode: int):
-        self.src.features(n_src, p_src)
-        self.tgt.features(n_tgt, p_tgt)
+    def run(self, n_src: int, n_tgt: int, p_src: kmx.Params, p_tgt: kmx.Params, mode: int, raw_src=None,
+            raw_tgt=None, corr_out=None, n_out=None):
+        """One pair: features of both clouds, then matching.  raw_* default to
+        the state's own input buffers; corr_out / n_out (a [cap, 4] int32
+        slot and a device int64 cell) default to the state's own."""
+        self.src.features(n_src, p_src, raw=raw_src)
+        self.tgt.features(n_tgt, p_tgt, raw=raw_tgt)
         s, t = self.src, self.tgt
+        out = self.corr if corr_out is None else corr_out
         self.ctx.match(s.out["desc"], s.out["valid"], s.n_cap, t.out["desc"], t.out["valid"], t.n_cap,
-                       d_np=s.out["n_valid"], d_nq=t.out["n_valid"], mode=mode, cap=self.cap, out=self.corr,
-                       n_out=self.n_corr)
+                       d_np=s.out["n_valid"], d_nq=t.out["n_valid"], mode=mode, cap=out.shape[0], out=out,
+                       n_out=self.n_corr if n_out is None else n_out)
         return self
 
     def capture(self, n_src: int, n_tgt: int, p_src: kmx.Params, p_tgt: kmx.Params, mode: int):
