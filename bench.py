@@ -58,14 +58,15 @@ def parse():
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_2409_15615_gb300 import replicas
+
+    return replicas.dist_env()
 
 
 def make_pair(rank):
-    src, tgt, R, t, vps, vpt = lidar_pair(WORKLOAD["seed"] + rank, az_bins=WORKLOAD["az_bins"])
+    from paper_2409_15615_gb300 import replicas
+
+    src, tgt, R, t, vps, vpt = lidar_pair(replicas.pair_seed(WORKLOAD["seed"], rank), az_bins=WORKLOAD["az_bins"])
     return src, tgt, vps, vpt
 
 
@@ -260,12 +261,10 @@ def run_kmx(args):
     clk = clocks.stop()
     ctx.sync()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1000.0)
+    from paper_2409_15615_gb300 import replicas
+
+    total_ms = replicas.max_over_ranks(sum(step_ms), device="cuda")
+    value = replicas.whole_job_throughput(args.steps, world, total_ms / 1000.0)
 
     # ---- per-stage timing (events between the C-ABI calls of one step)
     stages = stage_times(torch, ctx, pair, len(src), len(tgt), ps, pt, mode, flush, reps=max(5, args.steps // 2))
@@ -499,11 +498,9 @@ def end_to_end(torch, ctx, pair, src, tgt, ps, pt, mode, flush, steps, world):
         b.synchronize()
         if k >= 2:
             ms.append(a.elapsed_time(b))
-    total = sum(ms)
-    if world > 1:
-        t = torch.tensor([total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = float(t.item())
+    from paper_2409_15615_gb300 import replicas
+
+    total = replicas.max_over_ranks(sum(ms), device="cuda")
     return dict(value=world * steps / (total / 1000.0), unit="pairs/s",
                 h2d_bytes_per_step=int(src.nbytes + tgt.nbytes),
                 d2h_bytes_per_step=int(h_corr.numel() * 4 + 8),

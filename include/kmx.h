@@ -114,6 +114,14 @@ const char* kmx_last_error(const kmx_ctx* ctx);
  * the paper: it lets a caller count the device work of a call sequence. */
 int64_t kmx_launch_count(void);
 
+/* Failure-path check (not from the paper): launch one block that polls a
+ * device flag nothing sets, at most `polls` times, the
+ * same bounded-wait pattern the tensor-core matcher uses on its mbarriers
+ * (polls <= 2^24, a few seconds at most).
+ * When the polls run out the kernel records KMX_ETIMEOUT and returns, so the
+ * next kmx_sync reports KMX_ETIMEOUT and the context stays usable. */
+kmx_status kmx_check_timeout(kmx_ctx* ctx, int64_t polls);
+
 /*
  * Voxel downsampling: the voxelised input clouds of Sec. III-A ("unordered
  * voxelized point clouds with a voxel size v").

@@ -76,6 +76,16 @@ kmx_status launched(kmx_ctx* c, cudaError_t e, const char* where)
     return KMX_OK;
 }
 
+// Polls a flag that nothing sets, a bounded number of times, then records a
+// timeout: the bounded-wait pattern, exercised without any fault.
+__global__ void bounded_wait(const volatile unsigned int* flag, long long polls, unsigned int* err)
+{
+    if (threadIdx.x != 0) return;
+    for (long long i = 0; i < polls; ++i)
+        if (*flag) return;
+    atomicOr(err, KMX_DERR_TIMEOUT);
+}
+
 }  // namespace
 
 std::atomic<long long> kmx_g_launches{0};
@@ -168,6 +178,21 @@ kmx_status kmx_sync(kmx_ctx* c)
 }
 
 const char* kmx_last_error(const kmx_ctx* c) { return c ? c->msg : "null context"; }
+
+kmx_status kmx_check_timeout(kmx_ctx* c, int64_t polls)
+{
+    if (!c) return KMX_EINVAL;
+    if (polls < 1 || polls > (1ll << 24)) return fail(c, KMX_EINVAL, "kmx_check_timeout: polls out of range");
+    DeviceGuard g(c->device);
+    kmx_status s = ensure_ws(c, 256);
+    if (s) return s;
+    unsigned int* flag = static_cast<unsigned int*>(c->ws);
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(unsigned int), c->stream);
+    if (e) return cuda_fail(c, e, "kmx_check_timeout");
+    KMX_COUNT_LAUNCH();
+    bounded_wait<<<1, 32, 0, c->stream>>>(flag, (long long)polls, c->d_err);
+    return launched(c, cudaGetLastError(), "kmx_check_timeout");
+}
 
 kmx_status kmx_voxelize(kmx_ctx* c, const float* d_xyz, int64_t n_raw, int32_t stride, float voxel, float* d_out4,
                         int64_t cap, int64_t* d_n_out, int32_t* d_assign)

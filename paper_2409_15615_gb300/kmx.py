@@ -70,6 +70,7 @@ def library():
         "kmx_sync": (C.c_int, [vp]),
         "kmx_last_error": (C.c_char_p, [vp]),
         "kmx_launch_count": (C.c_int64, []),
+        "kmx_check_timeout": (C.c_int, [vp, i64]),
         "kmx_voxelize": (C.c_int, [vp, vp, i64, i32, f32, vp, i64, vp, vp]),
         "kmx_build_grid": (C.c_int, [vp, vp, i64, vp, f32, C.POINTER(vp)]),
         "kmx_grid_free": (None, [vp]),
@@ -153,6 +154,10 @@ class Context:
     def _check(self, st, what):
         if st:
             raise KmxError(st, "%s: %s" % (what, self.lib.kmx_last_error(self.h).decode()))
+
+    def check_timeout(self, polls: int):
+        """kmx_check_timeout: a bounded wait on a flag nothing sets."""
+        self._check(self.lib.kmx_check_timeout(self.h, int(polls)), "kmx_check_timeout")
 
     def reserve(self, nbytes: int):
         self._check(self.lib.kmx_reserve(self.h, int(nbytes)), "kmx_reserve")

@@ -1,0 +1,131 @@
+"""End-to-end and full-size checks on the GPU.
+
+* Registration success (Sec. IV-A criterion) computed by the oracle's own
+  ratio filter, k-core pruning and GNC-TLS (Secs. III-D, III-E) on the GPU's
+  correspondences equals the success on the oracle's correspondences, pair by
+  pair, on object-rich scene pairs.
+* The large dense indoor pair (2M raw points per cloud, voxel 0.02 m,
+  ~300k voxels): voxelisation is checked bit-exactly in full; descriptors and
+  matches on sampled rows, against the oracle run on the whole cloud.
+"""
+import numpy as np
+import pytest
+
+from synth import indoor_pair, scene_pair
+
+pytestmark = pytest.mark.gpu
+
+H = 11
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2409_15615_gb300 import build, kmx
+
+    build.build()
+    ctx = kmx.Context(0)
+    yield torch, kmx, ctx
+    ctx.close()
+
+
+def _gpu_pair(torch, kmx, ctx, src, tgt, v, vps, vpt, mode):
+    from paper_2409_15615_gb300 import pipeline
+
+    pair = pipeline.PairState(ctx, len(src), len(tgt))
+    pair.src.raw.copy_(torch.from_numpy(src).cuda())
+    pair.tgt.raw.copy_(torch.from_numpy(tgt).cuda())
+    ps = kmx.params_default(v, viewpoint=np.float32(vps).tolist())
+    pt = kmx.params_default(v, viewpoint=np.float32(vpt).tolist())
+    pair.run_checked(len(src), len(tgt), ps, pt, mode)
+    return pair
+
+
+def test_registration_success_parity(env, orc):
+    torch, kmx, ctx = env
+    flags_o, flags_g = [], []
+    for seed in range(500, 512):
+        src, tgt, R, t, vps, vpt = scene_pair(seed, n=10000, clutter=True)
+        vp_s, vp_t = np.float32(vps).astype(np.float64), np.float32(vpt).astype(np.float64)
+        A, fs, ft, vs, vt = orc.front_end(src, tgt, 0.1, vp_s, vp_t)
+        Ro, to, _ = orc.register(A, vs, vt, 0.1)
+        pair = _gpu_pair(torch, kmx, ctx, src, tgt, 0.1, vps, vpt, kmx.MATCH_FP32_EXACT)
+        gi, gj, gd1, gd2 = pair.correspondences()
+        G = np.zeros(len(gi), dtype=A.dtype)
+        G["i"], G["j"], G["d1"], G["d2"] = gi, gj, gd1, gd2
+        vs_g = pair.src.vox4[: int(pair.src.n_vox.item())].cpu().numpy()
+        vt_g = pair.tgt.vox4[: int(pair.tgt.n_vox.item())].cpu().numpy()
+        Rg, tg, _ = orc.register(G, vs_g, vt_g, 0.1)
+        flags_o.append(orc.is_success(Ro, to, R, t))
+        flags_g.append(orc.is_success(Rg, tg, R, t))
+    assert flags_o == flags_g
+    assert sum(flags_o) >= len(flags_o) // 2  # the workload does register
+
+
+@pytest.mark.slow
+def test_indoor_2m_pair_sampled(env, orc):
+    torch, kmx, ctx = env
+    src, tgt, R, t, vps, vpt = indoor_pair(31)
+    v = 0.02
+    pair = _gpu_pair(torch, kmx, ctx, src, tgt, v, vps, vpt, kmx.MATCH_FP32_EXACT)
+    # voxelisation: bit-exact, whole clouds
+    vs, _ = orc.voxelize(src, v)
+    vt, _ = orc.voxelize(tgt, v)
+    ns, nt = int(pair.src.n_vox.item()), int(pair.tgt.n_vox.item())
+    assert (ns, nt) == (len(vs), len(vt)) and ns > 200000
+    assert np.array_equal(pair.src.vox4[:ns].cpu().numpy().view(np.uint32), vs.view(np.uint32))
+    assert np.array_equal(pair.tgt.vox4[:nt].cpu().numpy().view(np.uint32), vt.view(np.uint32))
+    # the oracle's chain on both whole clouds
+    ps = orc.OracleParams(v, viewpoint=np.float32(vps).astype(np.float64))
+    pt = orc.OracleParams(v, viewpoint=np.float32(vpt).astype(np.float64))
+    fs = orc.faster_pfh(vs, ps)
+    ft = orc.faster_pfh(vt, pt)
+    # neighbour counts are exact integers
+    g_offs = pair.src.bufs["offs"][: ns + 1].cpu().numpy()
+    assert np.array_equal(g_offs, fs["offs"])
+    # J: equal up to points whose reliability sits on the tau_lin band
+    g_J = pair.src.out["valid"][: int(pair.src.out["n_valid"].item())].cpu().numpy()
+    diff = np.setxor1d(g_J, fs["J"])
+    assert len(diff) <= max(3, len(fs["J"]) // 2000)
+    # sampled FPFH rows (those whose neighbourhood has no J/B difference),
+    # each within tolerance plus the exact allowance of its flip-prone pairs
+    from parity_helpers import fpfh_allowance, hist_violation, spfh_allowance
+
+    rng = np.random.default_rng(0)
+    row_of = {q: r for r, q in enumerate(g_J)}
+    flagged = set(diff.tolist())
+    a_fp = fpfh_allowance(vs, fs["J"], fs["voffs"], fs["vnbr"], spfh_allowance(fs["n_marg"], fs["npairs"]))
+    g_desc = pair.src.out["desc"]
+    sel = []
+    for r in rng.choice(len(fs["J"]), 2000, replace=False):
+        q = int(fs["J"][r])
+        nb = fs["nbr"][fs["offs"][q]:fs["offs"][q + 1]]
+        if q in row_of and not flagged.intersection(nb.tolist()):
+            sel.append(r)
+    sel = np.array(sel)
+    assert len(sel) > 1500
+    got = g_desc[torch.as_tensor([row_of[int(fs["J"][r])] for r in sel], device="cuda"), :33].cpu().numpy()
+    v = hist_violation(got.astype(np.float64), fs["fpfh"][sel], a_fp[sel])
+    assert v.max() <= 1.0, "FPFH off by %.3g x tolerance" % v.max()
+    # sampled matches: exact nearest target row of sampled source rows, and
+    # their reciprocity, against the GPU's correspondence set
+    if len(diff) == 0:
+        gi, gj, _, _ = pair.correspondences()
+        got = dict(zip(gi.tolist(), gj.tolist()))
+        rows = rng.choice(len(fs["J"]), 300, replace=False)
+        nn, d1, d2 = orc.nearest(fs["fpfh"][rows], ft["fpfh"])
+        back, e1, e2 = orc.nearest(ft["fpfh"][nn], fs["fpfh"])
+        # rows whose descriptors carry a bin flip (chained FP32 vs FP64) may
+        # legitimately differ; they are rare, so require 97 % agreement
+        agree = checked_m = 0
+        for k, r in enumerate(rows):
+            if (d2[k] - d1[k]) / max(d2[k], 1e-300) < 1e-3 or (e2[k] - e1[k]) / max(e2[k], 1e-300) < 1e-3:
+                continue
+            q = int(fs["J"][r])
+            mutual = back[k] == r
+            ok = got.get(q) == int(ft["J"][nn[k]]) if mutual else q not in got
+            agree += ok
+            checked_m += 1
+        assert checked_m > 150 and agree >= 0.97 * checked_m

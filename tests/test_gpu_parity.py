@@ -229,42 +229,9 @@ def test_neighbour_capacity_error(torch_cuda, ctx, orc):
 # ----------------------------------------------------------------------------
 
 
-def _hist_close(got, ref, allowance=None):
-    """Per-row max of |got - ref| / (BIN_TOL * S_l / 100 + allowance), over the
-    three sub-histograms (S_l = the oracle's sum of sub-histogram l)."""
-    viol = np.zeros(len(ref))
-    extra = np.zeros(len(ref)) if allowance is None else allowance
-    for l in range(3):
-        sl = ref[:, l * H:(l + 1) * H]
-        tol = BIN_TOL * np.maximum(sl.sum(1), 100.0) / 100.0 + extra
-        err = np.abs(got[:, l * H:(l + 1) * H] - sl).max(1)
-        viol = np.maximum(viol, err / tol)
-    return viol
-
-
-def _spfh_allowance(n_marg, npairs):
-    """Largest per-bin change of SPFH(q) that FP32 rounding can cause: each
-    pair within FEATURE_BAND of a flip may move one count (or change the pair
-    count), worth 2 * 100 / c per flip-prone pair."""
-    a = np.zeros(len(n_marg))
-    ok = npairs > 0
-    a[ok] = 2.0 * n_marg[ok] * 100.0 / npairs[ok]
-    return a
-
-
-def _fpfh_allowance(pts, J, voffs, vnbr, a_sp):
-    """The same allowance carried through Eq. A5: SPFH(q)'s own plus
-    (1/m) sum_k a_k / w_k over the neighbours k."""
-    p = pts[:, :3].astype(np.float64)
-    cnt = np.diff(voffs)
-    owner = np.repeat(np.arange(len(cnt)), cnt)
-    k = np.asarray(vnbr, np.int64)
-    keep = k != owner
-    owner, k = owner[keep], k[keep]
-    w = 1.0 / np.linalg.norm(p[k] - p[owner], axis=1)
-    m = np.bincount(owner, minlength=len(cnt))
-    s = np.bincount(owner, weights=w * a_sp[k], minlength=len(cnt))
-    return (a_sp + np.where(m > 0, s / np.maximum(m, 1), 0.0))[J]
+from parity_helpers import fpfh_allowance as _fpfh_allowance  # noqa: E402
+from parity_helpers import hist_violation as _hist_close  # noqa: E402
+from parity_helpers import spfh_allowance as _spfh_allowance  # noqa: E402
 
 
 @pytest.mark.parametrize("case", ["scene", "lidar"])
