@@ -239,7 +239,7 @@ def run_kmx(args):
         flush.zero_()
         step()
     torch.cuda.synchronize()
-    ctx.sync()
+    pair.sync()
 
     # ---- timed region: K steps, per-step events, L2 flushed between steps
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -259,7 +259,7 @@ def run_kmx(args):
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    ctx.sync()
+    pair.sync()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     from paper_2409_15615_gb300 import replicas
 
@@ -367,7 +367,6 @@ def stage_times(torch, ctx, pair, n_src, n_tgt, ps, pt, mode, flush, reps):
     stream between consecutive calls)."""
     from paper_2409_15615_gb300 import kmx
 
-    stream = ctx.stream
     names = ["voxelize", "build_grid", "normals", "fasterpfh"]
     acc = {("src_" + n): [] for n in names}
     acc.update({("tgt_" + n): [] for n in names})
@@ -375,21 +374,23 @@ def stage_times(torch, ctx, pair, n_src, n_tgt, ps, pt, mode, flush, reps):
     for _ in range(reps):
         flush.zero_()
         for side, cs, n_raw, prm in (("src_", pair.src, n_src, ps), ("tgt_", pair.tgt, n_tgt, pt)):
+            c, stream = cs.ctx, cs.ctx.stream
             e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
             e[0].record(stream)
-            ctx.voxelize(cs.raw[:n_raw], prm.voxel, cap=cs.n_cap, out4=cs.vox4, n_out=cs.n_vox)
+            c.voxelize(cs.raw[:n_raw], prm.voxel, cap=cs.n_cap, out4=cs.vox4, n_out=cs.n_vox)
             e[1].record(stream)
-            cs.grid = ctx.build_grid(cs.vox4, prm.r_fpfh, n_cap=cs.n_cap, d_n=cs.n_vox, reuse=cs.grid)
+            cs.grid = c.build_grid(cs.vox4, prm.r_fpfh, n_cap=cs.n_cap, d_n=cs.n_vox, reuse=cs.grid)
             e[2].record(stream)
-            b = ctx.normals(cs.grid, prm, cs.nbr_cap, out=cs.bufs)
+            b = c.normals(cs.grid, prm, cs.nbr_cap, out=cs.bufs)
             e[3].record(stream)
-            ctx.fasterpfh(cs.grid, prm, b["normal4"], b["flags"], b["offs"], b["nbr"], out=cs.out)
+            c.fasterpfh(cs.grid, prm, b["normal4"], b["flags"], b["offs"], b["nbr"], out=cs.out)
             e[4].record(stream)
             torch.cuda.synchronize()
             for i, n in enumerate(names):
                 acc[side + n].append(e[i].elapsed_time(e[i + 1]))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s, t = pair.src, pair.tgt
+        stream = ctx.stream
         e0.record(stream)
         ctx.match(s.out["desc"], s.out["valid"], s.n_cap, t.out["desc"], t.out["valid"], t.n_cap,
                   d_np=s.out["n_valid"], d_nq=t.out["n_valid"], mode=mode, cap=pair.cap, out=pair.corr,
@@ -397,7 +398,7 @@ def stage_times(torch, ctx, pair, n_src, n_tgt, ps, pt, mode, flush, reps):
         e1.record(stream)
         torch.cuda.synchronize()
         acc["match"].append(e0.elapsed_time(e1))
-    ctx.sync()
+    pair.sync()
     return {k: float(np.mean(v)) for k, v in acc.items()}
 
 

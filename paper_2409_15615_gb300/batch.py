@@ -87,7 +87,8 @@ class BatchRunner:
             ctx = kmx.Context(device, stream)
             ms = int(max(self.n_src[q])) if q else 1
             mt = int(max(self.n_tgt[q])) if q else 1
-            self.lanes.append((stream, ctx, pipeline.PairState(ctx, ms, mt, nbr_per_point)))
+            # lanes already run concurrently, so each lane's pair stays on one stream
+            self.lanes.append((stream, ctx, pipeline.PairState(ctx, ms, mt, nbr_per_point, overlap=False)))
         self.graph = None
 
     def _run_lane(self, lane_idx):

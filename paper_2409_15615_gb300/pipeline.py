@@ -4,7 +4,10 @@ cloud, then mutual matching (Sec. III-C).
 
 All buffers are preallocated from capacities, every count stays on the
 device, and the sequence issues no host synchronisation, so one pair is a
-fixed chain of kernel launches on one stream.
+fixed chain of kernel launches.  The two clouds' feature chains are
+independent; with ``overlap`` the target's runs on a second context (its own
+stream and scratch) concurrently with the source's, forked from and joined
+back to the caller's stream, so the pair still orders like one stream.
 """
 from __future__ import annotations
 
@@ -56,12 +59,19 @@ class CloudState:
 
 
 class PairState:
-    """Buffers for one source/target pair and its correspondences."""
+    """Buffers for one source/target pair and its correspondences.
 
-    def __init__(self, ctx: kmx.Context, n_src_cap: int, n_tgt_cap: int, nbr_per_point: int = 96):
+    With ``overlap`` (the default) the pair owns a second context for the
+    target cloud on a stream of its own; ``close()`` releases it."""
+
+    def __init__(self, ctx: kmx.Context, n_src_cap: int, n_tgt_cap: int, nbr_per_point: int = 96,
+                 overlap: bool = True):
         self.ctx = ctx
+        self.side_ctx = None
+        if overlap:
+            self.side_ctx = kmx.Context(ctx.device.index, torch.cuda.Stream(device=ctx.device))
         self.src = CloudState(ctx, n_src_cap, nbr_per_point)
-        self.tgt = CloudState(ctx, n_tgt_cap, nbr_per_point)
+        self.tgt = CloudState(self.side_ctx or ctx, n_tgt_cap, nbr_per_point)
         cap = max(min(self.src.n_cap, self.tgt.n_cap), 1)
         self.corr = torch.empty((cap, 4), dtype=torch.int32, device=ctx.device)
         self.n_corr = torch.zeros(1, dtype=torch.int64, device=ctx.device)
@@ -72,8 +82,13 @@ class PairState:
         """One pair: features of both clouds, then matching.  raw_* default to
         the state's own input buffers; corr_out / n_out (a [cap, 4] int32
         slot and a device int64 cell) default to the state's own."""
+        side = self.side_ctx
+        if side is not None:
+            side.stream.wait_stream(self.ctx.stream)  # fork
         self.src.features(n_src, p_src, raw=raw_src)
         self.tgt.features(n_tgt, p_tgt, raw=raw_tgt)
+        if side is not None:
+            self.ctx.stream.wait_stream(side.stream)  # join
         s, t = self.src, self.tgt
         out = self.corr if corr_out is None else corr_out
         self.ctx.match(s.out["desc"], s.out["valid"], s.n_cap, t.out["desc"], t.out["valid"], t.n_cap,
@@ -105,7 +120,7 @@ class PairState:
         for attempt in range(2):
             self.run(n_src, n_tgt, p_src, p_tgt, mode)
             try:
-                self.ctx.sync()
+                self.sync()
                 return self
             except kmx.KmxError as e:
                 if e.status != kmx.KMX_ECAPACITY or attempt:
@@ -115,6 +130,27 @@ class PairState:
                     if need > c.nbr_cap:
                         c.grow_neighbours(need)
         return self
+
+    def sync(self):
+        """Wait for the pair; raise the first device-side error of either
+        context (both are synchronised, so both errors are cleared)."""
+        err = None
+        for c in (self.side_ctx, self.ctx):
+            if c is None:
+                continue
+            try:
+                c.sync()
+            except kmx.KmxError as e:
+                err = err or e
+        if err is not None:
+            raise err
+
+    def close(self):
+        """Release the target cloud's context (and the grid built on it)."""
+        if self.side_ctx is not None:
+            self.tgt.grid = None
+            self.side_ctx.close()
+            self.side_ctx = None
 
     def correspondences(self):
         n = int(self.n_corr.item())

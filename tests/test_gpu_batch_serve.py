@@ -31,6 +31,7 @@ def _single(torch, spec, mode):
     pt = kmx.params_default(spec.voxel, viewpoint=np.float32(spec.vp_tgt).tolist())
     st.run_checked(len(spec.src), len(spec.tgt), ps, pt, mode)
     out = st.correspondences()
+    st.close()
     ctx.close()
     return out
 

@@ -57,6 +57,7 @@ def test_registration_success_parity(env, orc):
         G["i"], G["j"], G["d1"], G["d2"] = gi, gj, gd1, gd2
         vs_g = pair.src.vox4[: int(pair.src.n_vox.item())].cpu().numpy()
         vt_g = pair.tgt.vox4[: int(pair.tgt.n_vox.item())].cpu().numpy()
+        pair.close()
         Rg, tg, _ = orc.register(G, vs_g, vt_g, 0.1)
         flags_o.append(orc.is_success(Ro, to, R, t))
         flags_g.append(orc.is_success(Rg, tg, R, t))
@@ -129,3 +130,4 @@ def test_indoor_2m_pair_sampled(env, orc):
             agree += ok
             checked_m += 1
         assert checked_m > 150 and agree >= 0.97 * checked_m
+    pair.close()

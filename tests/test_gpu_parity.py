@@ -397,6 +397,7 @@ def test_chained_pair(torch_cuda, ctx, orc, case):
     ref = set(zip(A["i"].tolist(), A["j"].tolist()))
     got = set(zip(gi.tolist(), gj.tolist()))
     agree = len(ref & got) / max(len(ref), 1)
+    pair.close()
     assert agree > 0.97, "only %.3f of the oracle's correspondences reproduced" % agree
 
 
