@@ -35,7 +35,7 @@ WORKLOAD = dict(name="lidar_pair_64beam_2048az_v0.3", voxel=0.3, az_bins=2048, s
 
 # DRAM bytes (read + write) of one launch, from the ncu captures summarised in
 # profiles/; an entry is removed whenever its kernel changes.
-PROFILED_TRAFFIC = {"match_tiles_fp32": 3848448}
+PROFILED_TRAFFIC = {}  # kernel -> DRAM read+write bytes per launch (ncu); none yet for the current kernels
 METRIC = "Faster-PFH+mutual-NN pairs/s (LiDAR scan pair, voxel 0.3 m)"
 
 
@@ -449,11 +449,13 @@ def roofline(stages, work, mode):
             flops = 3.0 * m["np"] * m["nq"] * 33
             achieved = flops / (match_ms / 1000.0) / 1e12
             peak = peaks["fp32_tflops"]
-            return dict(kernel="match_tiles_fp32 (kmx_match, FP32 exact)", bound="alu", achieved=achieved, peak=peak,
-                        unit="TFLOP/s", frac=achieved / peak, traffic=PROFILED_TRAFFIC.get("match_tiles_fp32"),
-                        note="3 flops (sub + fma) per descriptor element pair; peak = 152 SMs x 128 FP32 lanes x 2 "
-                             "x 2.07 GHz (derived, no measured FP32 peak); traffic = DRAM read+write bytes of one "
-                             "launch from ncu (profiles/match_tiles_fp32_lidar_pair.md)")
+            return dict(kernel="match_tiles_fp32_bulk (kmx_match, FP32 exact)", bound="alu", achieved=achieved,
+                        peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                        traffic=PROFILED_TRAFFIC.get("match_tiles_fp32_bulk"),
+                        note="3 flops (sub + fma) per descriptor element pair; duration = the whole kmx_match call "
+                             "(pack, tiles, merge, emit) from CUDA events, so the tile kernel alone runs faster; "
+                             "peak = 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived, no measured FP32 peak); "
+                             "traffic = DRAM read+write bytes of one launch from ncu")
         flops = 2.0 * m["np"] * m["nq"] * 33
         achieved = flops / (match_ms / 1000.0) / 1e12
         peak = peaks["bf16_tflops"]

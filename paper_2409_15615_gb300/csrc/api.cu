@@ -347,14 +347,11 @@ cudaError_t kmx_match_launch(kmx_ctx* c, const float* dp, const int32_t* vp, int
         return cudaMemsetAsync(n_out, 0, sizeof(int64_t), st);
     }
     if (mode == KMX_MATCH_FP32_EXACT) {
-        int chunks = 1;
-        const size_t bytes = kmx_match_fp32_scratch_bytes(np_cap, nq_cap, &chunks);
+        const size_t extra = kmx_match_fp32_bulk_extra_bytes(np_cap, nq_cap, c->sm_count);
+        const size_t bytes = kmx::match_common_bytes(np_cap, nq_cap, 1, extra);
         if (ensure_ws(c, bytes) != KMX_OK) return cudaErrorMemoryAllocation;
-        kmx::MatchScratch s = kmx::match_common_carve(c->ws, np_cap, nq_cap, chunks);
-        cudaError_t e = cudaMemsetAsync(s.colbest, 0xFF, sizeof(unsigned long long) * nq_cap, st);
-        if (e) return e;
-        if ((e = kmx_match_fp32_launch(c, dp, np_cap, d_np, dq, nq_cap, d_nq, s, chunks))) return e;
-        return kmx::match_finalize(c, s, np_cap, d_np, vp, vq, out, cap, n_out);
+        kmx::MatchScratch s = kmx::match_common_carve(c->ws, np_cap, nq_cap, 1, extra);
+        return kmx_match_fp32_bulk_launch(c, dp, vp, np_cap, d_np, dq, vq, nq_cap, d_nq, s, out, cap, n_out);
     }
     if (mode == KMX_MATCH_BF16_RERANK) {
         const size_t extra = kmx_match_tc_extra_bytes(np_cap, nq_cap, c->sm_count);

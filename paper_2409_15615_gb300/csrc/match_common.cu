@@ -93,9 +93,19 @@ cudaError_t match_finalize(kmx_ctx* ctx, const MatchScratch& s, int64_t np_cap, 
     const unsigned nb = kmx_blocks(np_cap, kThreads);
     KMX_COUNT_LAUNCH();
     merge_mutual<<<nb, kThreads, 0, st>>>(s.part, s.chunks, np_cap, d_np, s.colbest, merged, s.mflag);
+    if ((e = cudaGetLastError())) return e;
+    return match_emit(ctx, s, np_cap, d_np, vp, vq, out, cap, n_out);
+}
+
+cudaError_t match_emit(kmx_ctx* ctx, const MatchScratch& s, int64_t np_cap, const int64_t* d_np,
+                       const int32_t* vp, const int32_t* vq, kmx_corr* out, int64_t cap, int64_t* n_out)
+{
+    cudaStream_t st = ctx->stream;
+    cudaError_t e;
     if ((e = kmx_scan_i32(s.mflag, np_cap, d_np, s.mpos, s.scan, st))) return e;
     KMX_COUNT_LAUNCH();
-    emit<<<nb, kThreads, 0, st>>>(np_cap, d_np, merged, s.mflag, s.mpos, vp, vq, out, cap, n_out, ctx->d_err);
+    emit<<<kmx_blocks(np_cap, kThreads), kThreads, 0, st>>>(np_cap, d_np, s.merged, s.mflag, s.mpos, vp, vq, out,
+                                                            cap, n_out, ctx->d_err);
     return cudaGetLastError();
 }
 

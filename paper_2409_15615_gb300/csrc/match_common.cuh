@@ -74,12 +74,26 @@ MatchScratch match_common_carve(void* base, int64_t np_cap, int64_t nq_cap, int 
 cudaError_t match_finalize(kmx_ctx* ctx, const MatchScratch& s, int64_t np_cap, const int64_t* d_np,
                            const int32_t* vp, const int32_t* vq, kmx_corr* out, int64_t cap, int64_t* n_out);
 
+// The tail of match_finalize for paths that merge their own partials: given
+// s.merged and s.mflag (1 = mutual, every row < n_p written), number the
+// mutual rows and emit A in ascending source row.
+cudaError_t match_emit(kmx_ctx* ctx, const MatchScratch& s, int64_t np_cap, const int64_t* d_np,
+                       const int32_t* vp, const int32_t* vq, kmx_corr* out, int64_t cap, int64_t* n_out);
+
 }  // namespace kmx
 
 // match_tc.cu
 size_t kmx_match_tc_extra_bytes(int64_t np_cap, int64_t nq_cap, int sm_count);
 cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, const int64_t* d_np, const float* dq,
                                 int64_t nq_cap, const int64_t* d_nq, kmx::MatchScratch& s);
+
+// match_fp32_bulk.cu: the exact FP32 path of kmx_match (packs both sides,
+// matches, merges and emits A)
+size_t kmx_match_fp32_bulk_extra_bytes(int64_t np_cap, int64_t nq_cap, int sm_count);
+cudaError_t kmx_match_fp32_bulk_launch(kmx_ctx* ctx, const float* dp, const int32_t* vp, int64_t np_cap,
+                                       const int64_t* d_np, const float* dq, const int32_t* vq, int64_t nq_cap,
+                                       const int64_t* d_nq, kmx::MatchScratch& s, kmx_corr* out, int64_t cap,
+                                       int64_t* n_out);
 
 // match_fp32.cu
 int kmx_match_fp32_max_chunks();

@@ -24,11 +24,19 @@
 // swapped.  Every wait on an mbarrier is bounded; on timeout the kernel
 // records KMX_DERR_TIMEOUT, drains what it issued and frees its TMEM.
 #include "kmx_internal.cuh"
+#include "bulk_copy.cuh"
 #include "match_common.cuh"
 
 #include <cuda_bf16.h>
 
 namespace {
+
+using kmx::bulk_g2s;
+using kmx::mbar_expect_tx;
+using kmx::mbar_fence_init;
+using kmx::mbar_init;
+using kmx::mbar_wait;
+using kmx::smem_u32;
 
 constexpr int kTM = 128;                       // rows per tile (UMMA M)
 constexpr int kTN = 128;                       // columns per tile (UMMA N)
@@ -43,7 +51,6 @@ constexpr int kTopK = 8;
 constexpr int kMaxChunks = 4;                  // 4 x 8 candidates = one warp in rerank
 constexpr int kThreads = 128;
 constexpr int kTmemCols = 256;                 // two 128-column FP32 accumulators
-constexpr uint32_t kWaitLimit = 1u << 22;
 
 struct __align__(8) Cand {
     float v;
@@ -51,50 +58,8 @@ struct __align__(8) Cand {
 };
 
 // ---------------------------------------------------------------------------
-// PTX wrappers (tcgen05, mbarrier, bulk copy)
+// PTX wrappers (tcgen05; mbarrier and bulk copy in bulk_copy.cuh)
 // ---------------------------------------------------------------------------
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-// Bounded wait for the phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
-{
-    const uint32_t a = smem_u32(bar);
-    for (uint32_t it = 0; it < kWaitLimit; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
