@@ -76,25 +76,23 @@ __global__ void __launch_bounds__(kThreads) grid_scatter(int64_t n_cap, const in
     s.tmp[s.start[slot] + pos] = (int32_t)i;
 }
 
-// One warp per slot: write the cell's points in ascending index order (rank =
-// number of smaller indices in the cell), with the index in w.
-__global__ void __launch_bounds__(kThreads) grid_fill(const float4* __restrict__ pts, uint32_t T, GridScratch s,
-                                                      float4* __restrict__ sorted)
+// One thread per point: its rank in the cell (the number of smaller point
+// indices there) places it, so each cell holds its points in ascending index
+// order, with the index in w.
+__global__ void __launch_bounds__(kThreads) grid_fill(const float4* __restrict__ pts, int64_t n_cap,
+                                                      const int64_t* d_n, GridScratch s, float4* __restrict__ sorted)
 {
-    int64_t t = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (t >= T) return;
-    int L = s.cnt[t];
-    if (L == 0) return;
-    int64_t b = s.start[t];
+    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i >= kmx_count(d_n, n_cap)) return;
+    const int slot = s.pslot[i];
+    if (slot < 0) return;
+    const int L = s.cnt[slot];
+    const int64_t b = s.start[slot];
     const int32_t* seg = s.tmp + b;
-    for (int e = lane; e < L; e += 32) {
-        int32_t me = seg[e];
-        int rank = 0;
-        for (int f = 0; f < L; ++f) rank += (seg[f] < me);
-        float4 p = pts[me];
-        sorted[b + rank] = make_float4(p.x, p.y, p.z, __int_as_float(me));
-    }
+    int rank = 0;
+    for (int f = 0; f < L; ++f) rank += (seg[f] < (int32_t)i);
+    const float4 p = pts[i];
+    sorted[b + rank] = make_float4(p.x, p.y, p.z, __int_as_float((int32_t)i));
 }
 
 }  // namespace
@@ -140,6 +138,6 @@ cudaError_t kmx_grid_build_launch(kmx_ctx* ctx, kmx_grid* g, void* scratch)
     KMX_COUNT_LAUNCH();
     grid_scatter<<<nb, kThreads, 0, st>>>(g->n_cap, g->d_n, s);
     KMX_COUNT_LAUNCH();
-    grid_fill<<<kmx_blocks((int64_t)T * 32, kThreads), kThreads, 0, st>>>(g->pts, T, s, g->sorted);
+    grid_fill<<<nb, kThreads, 0, st>>>(g->pts, g->n_cap, g->d_n, s, g->sorted);
     return cudaGetLastError();
 }

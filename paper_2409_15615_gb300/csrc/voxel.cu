@@ -3,9 +3,10 @@
 // Sort-free design: a device hash table maps packed voxel keys to slots; the
 // lowest input index of each voxel (atomicMin) fixes the output order ("order
 // of first member"), a prefix sum over first-member flags numbers the voxels,
-// a counting scatter groups members per voxel, and each voxel's members are
-// put back in input order before the FP64 centroid sum, so the result does not
-// depend on atomic ordering.
+// a counting scatter groups members per voxel, and the centroid is the FP64
+// input-order sum (computed exactly in integers when an exponent test shows
+// that sum is exact, else in input order), so the result does not depend on
+// atomic ordering.
 #include "kmx_internal.cuh"
 
 namespace {
@@ -147,23 +148,48 @@ __device__ __forceinline__ void exp_range(float x, int& emin, int& emax, bool& o
     emax = max(emax, e);
 }
 
-// One thread per output voxel (so FP64 instructions run with every lane
-// busy).  The members are summed in FP64 in the order the scatter left them;
-// the exponent test above shows that this equals the input-order sum for
-// every voxel except those whose coordinates span a huge range (a voxel
-// touching a coordinate plane through the origin, with values near zero).
-// Those are summed again in input order: each member's rank (the number of
-// smaller member indices) places its coordinates in a per-voxel run.
-__global__ void __launch_bounds__(kThreads) vox_centroid(const float* __restrict__ xyz, int stride, int64_t n,
-                                                         VoxScratch s, float4* __restrict__ out, int64_t cap)
+// When the exponent test passes, the exact sum is computed in integers: every
+// value is m * 2^(e - 150) with a 24-bit integer m (normal number, biased
+// exponent e), so it is the integer m << (e - emin) times 2^(emin - 150); the
+// shift is at most 29 - ceil(log2 L) and the sum of L such integers stays
+// below 2^53, so it converts to FP64 exactly.
+__device__ __forceinline__ long long scaled_int(float x, int emin)
 {
-    const int64_t o = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const uint32_t bits = __float_as_uint(x);
+    const uint32_t mag = bits & 0x7fffffffu;
+    if (mag == 0) return 0;
+    const long long m = (long long)((mag & 0x7fffffu) | 0x800000u) << ((int)(mag >> 23) - emin);
+    return (bits >> 31) ? -m : m;
+}
+
+// isum * 2^(emin - 150) in FP64 (exact: |isum| < 2^53 and the power of two is
+// a normal FP64 number for every emin in [1, 255]).
+__device__ __forceinline__ double scaled_sum(long long isum, int emin)
+{
+    const double p2 = __longlong_as_double((long long)(emin - 150 + 1023) << 52);
+    return __dmul_rn(__ll2double_rn(isum), p2);
+}
+
+constexpr int kCentroidThreads = 128;  // small blocks spread a few thousand voxels over every SM
+
+// One thread per output voxel.  A first pass over the members finds each
+// axis's exponent range; if the exponent test passes, the FP64 input-order sum
+// equals the exact sum, which a second pass accumulates in 64-bit integers
+// (integer pipe; GB300's FP64 rate made the FP64 adds the bottleneck).
+// Otherwise (a voxel whose coordinates span a huge range, e.g. values near
+// zero next to larger ones) the members are summed in FP64 in input order:
+// each member's rank (the number of smaller member indices) places its
+// coordinates in a per-voxel run.
+__global__ void __launch_bounds__(kCentroidThreads) vox_centroid(const float* __restrict__ xyz, int stride,
+                                                                 int64_t n, VoxScratch s,
+                                                                 float4* __restrict__ out, int64_t cap)
+{
+    const int64_t o = (int64_t)blockIdx.x * kCentroidThreads + threadIdx.x;
     const int64_t nv = s.oidx[n];
     if (o >= nv || o >= cap) return;
     const int64_t b = s.vstart[o];
     const int L = (int)(s.vstart[o + 1] - b);
     const int32_t* m = s.members + b;
-    double sx = 0.0, sy = 0.0, sz = 0.0;
     int emin[3] = {255, 255, 255}, emax[3] = {0, 0, 0};
     bool odd = false;
     // unrolled so that the loads of several members are in flight together
@@ -171,19 +197,28 @@ __global__ void __launch_bounds__(kThreads) vox_centroid(const float* __restrict
 #pragma unroll 8
     for (int e = 0; e < L; ++e) {
         const float* p = xyz + (int64_t)__ldg(m + e) * stride;
-        const float x = p[0], y = p[1], z = p[2];
-        sx = __dadd_rn(sx, (double)x);
-        sy = __dadd_rn(sy, (double)y);
-        sz = __dadd_rn(sz, (double)z);
-        exp_range(x, emin[0], emax[0], odd);
-        exp_range(y, emin[1], emax[1], odd);
-        exp_range(z, emin[2], emax[2], odd);
+        exp_range(p[0], emin[0], emax[0], odd);
+        exp_range(p[1], emin[1], emax[1], odd);
+        exp_range(p[2], emin[2], emax[2], odd);
     }
     const int lg = 32 - __clz(L > 1 ? L - 1 : 1);  // ceil(log2 L) for L >= 2
     bool exact = !odd;
     for (int a = 0; a < 3; ++a)
         if (emax[a] >= emin[a] && emax[a] - emin[a] > 29 - lg) exact = false;
-    if (!exact) {
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    if (exact) {
+        long long ix = 0, iy = 0, iz = 0;
+#pragma unroll 8
+        for (int e = 0; e < L; ++e) {
+            const float* p = xyz + (int64_t)__ldg(m + e) * stride;
+            ix += scaled_int(p[0], emin[0]);
+            iy += scaled_int(p[1], emin[1]);
+            iz += scaled_int(p[2], emin[2]);
+        }
+        sx = scaled_sum(ix, emin[0]);
+        sy = scaled_sum(iy, emin[1]);
+        sz = scaled_sum(iz, emin[2]);
+    } else {
         float4* run = s.run + b;
         for (int e = 0; e < L; ++e) {
             const int32_t me = m[e];
@@ -192,7 +227,6 @@ __global__ void __launch_bounds__(kThreads) vox_centroid(const float* __restrict
             const float* p = xyz + (int64_t)me * stride;
             run[rank] = make_float4(p[0], p[1], p[2], 0.f);
         }
-        sx = sy = sz = 0.0;
         for (int e = 0; e < L; ++e) {
             const float4 p = run[e];
             sx = __dadd_rn(sx, (double)p.x);
@@ -243,7 +277,7 @@ cudaError_t kmx_voxelize_launch(kmx_ctx* ctx, const float* xyz, int64_t n, int s
     KMX_COUNT_LAUNCH();
     vox_scatter<<<nb, kThreads, 0, st>>>(n, s, assign);
     KMX_COUNT_LAUNCH();
-    vox_centroid<<<kmx_blocks(n, kThreads), kThreads, 0, st>>>(xyz, stride, n, s,
-                                                                    reinterpret_cast<float4*>(out4), cap);
+    vox_centroid<<<kmx_blocks(n, kCentroidThreads), kCentroidThreads, 0, st>>>(xyz, stride, n, s,
+                                                                                    reinterpret_cast<float4*>(out4), cap);
     return cudaGetLastError();
 }

@@ -60,7 +60,22 @@ def params_for(kmx, orc, v, vp):
 # ----------------------------------------------------------------------------
 
 
-@pytest.mark.parametrize("case", ["scene", "lidar", "stride4", "negative", "single"])
+def _exponent_mix():
+    """Voxels of ~60 members (integer path near its shift limit), voxels
+    mixing magnitudes from 1e-30 to 0.5 and subnormals, zeros and -0.0 (FP64
+    input-order path), on both sides of the origin."""
+    rng = np.random.default_rng(4)
+    a = rng.random((4000, 3)) * 2.0
+    b = rng.random((300, 3)) * 0.5 * 10.0 ** rng.uniform(-30, 0, (300, 3))
+    c = rng.random((40, 3)) * 0.25
+    c[:10, 0] = 1e-40  # subnormal in FP32
+    c[10:20, 1] = 0.0
+    c[20:30, 2] = -0.0
+    x = np.concatenate([a, b, c, -a[:500], -b[:100]]).astype(np.float32)
+    return x[rng.permutation(len(x))]
+
+
+@pytest.mark.parametrize("case", ["scene", "lidar", "stride4", "negative", "single", "exponents"])
 def test_voxelize_bit_exact(torch_cuda, ctx, orc, case):
     torch = torch_cuda
     if case == "scene":
@@ -76,6 +91,8 @@ def test_voxelize_bit_exact(torch_cuda, ctx, orc, case):
         x = rng.normal(0, 0.3, (5000, 3)).astype(np.float32)
         x[:50] = (rng.integers(-8, 8, (50, 3)) * 0.125).astype(np.float32)  # exactly on faces
         v = 0.125
+    elif case == "exponents":
+        x, v = _exponent_mix(), 0.5
     else:
         x, v = np.array([[-1.5, 2.25, 0.0]], np.float32), 0.5
     ref, ref_assign = orc.voxelize(x, v)
