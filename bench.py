@@ -35,7 +35,7 @@ WORKLOAD = dict(name="lidar_pair_64beam_2048az_v0.3", voxel=0.3, az_bins=2048, s
 
 # DRAM bytes (read + write) of one launch, from the ncu captures summarised in
 # profiles/; an entry is removed whenever its kernel changes.
-PROFILED_TRAFFIC = {}  # kernel -> DRAM read+write bytes per launch (ncu); none yet for the current kernels
+PROFILED_TRAFFIC = {"match_tiles_fp32_bulk": 5237248}  # DRAM read+write bytes of one launch (ncu, LiDAR pair)
 METRIC = "Faster-PFH+mutual-NN pairs/s (LiDAR scan pair, voxel 0.3 m)"
 
 
@@ -455,7 +455,8 @@ def roofline(stages, work, mode):
                         note="3 flops (sub + fma) per descriptor element pair; duration = the whole kmx_match call "
                              "(pack, tiles, merge, emit) from CUDA events, so the tile kernel alone runs faster; "
                              "peak = 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived, no measured FP32 peak); "
-                             "traffic = DRAM read+write bytes of one launch from ncu")
+                             "traffic = DRAM read+write bytes of one launch from ncu "
+                             "(profiles/match_tiles_fp32_bulk_lidar_pair.md)")
         flops = 2.0 * m["np"] * m["nq"] * 33
         achieved = flops / (match_ms / 1000.0) / 1e12
         peak = peaks["bf16_tflops"]

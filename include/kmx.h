@@ -78,7 +78,13 @@ typedef struct {
 
 typedef enum {
     KMX_MATCH_FP32_EXACT = 0, /* exact FP32 distances on CUDA cores */
-    KMX_MATCH_BF16_RERANK = 1 /* BF16 tensor-core distances, top-8 candidates re-ranked exactly in FP32 */
+    /* split-BF16 (hi + lo) tensor-core distances on centred descriptors give
+     * top-8 candidates per row; a row whose candidates provably contain its
+     * exact nearest and second-nearest columns (a(8) - a(2) > 2E, E the bound
+     * on the approximate key's error) is re-ranked exactly in FP32, every
+     * other row goes through the exact FP32 tiles.  The result equals
+     * KMX_MATCH_FP32_EXACT's. */
+    KMX_MATCH_BF16_RERANK = 1
 } kmx_match_mode;
 
 typedef struct kmx_ctx kmx_ctx;   /* opaque, owned by the library */
