@@ -261,7 +261,7 @@ cudaError_t kmx_fasterpfh_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_para
     const unsigned nbw = kmx_blocks(n, kWarps);
     KMX_COUNT_LAUNCH();
     valid_count<<<nbw, kThreads, 0, st>>>(n, g->d_n, flags, offs, nbr, prm->tau_num, s.jflag);
-    if ((e = kmx_scan_i32(s.jflag, n, g->d_n, s.jpos, s.scan, st))) return e;
+    if ((e = kmx_scan_i32(s.jflag, n, g->d_n, s.jpos, s.scan, st, ctx->d_err))) return e;
     KMX_COUNT_LAUNCH();
     scatter_valid<<<kmx_blocks(n, kThreads), kThreads, 0, st>>>(n, g->d_n, s.jflag, s.jpos, valid, n_valid);
     KMX_COUNT_LAUNCH();

@@ -132,7 +132,7 @@ cudaError_t kmx_grid_build_launch(kmx_ctx* ctx, kmx_grid* g, void* scratch)
     unsigned nb = kmx_blocks(g->n_cap, kThreads);
     KMX_COUNT_LAUNCH();
     grid_insert<<<nb, kThreads, 0, st>>>(g->pts, g->n_cap, g->d_n, g->inv_cell, g->keys, T, s, ctx->d_err);
-    if ((e = kmx_scan_i32(s.cnt, T, nullptr, s.start, s.scan, st))) return e;
+    if ((e = kmx_scan_i32(s.cnt, T, nullptr, s.start, s.scan, st, ctx->d_err))) return e;
     KMX_COUNT_LAUNCH();
     grid_cells<<<kmx_blocks(T, kThreads), kThreads, 0, st>>>(T, s, g->cells, g->d_n_sorted);
     KMX_COUNT_LAUNCH();

@@ -164,8 +164,10 @@ inline cudaError_t kmx_once_per_device(int bit, F fn)
 // scan.cu: exclusive prefix sum of n int32 values (values at i >= *d_n count
 // as 0) into out[0..n] (int64, out[n] = total).  Scratch bytes needed:
 size_t kmx_scan_scratch_bytes(int64_t n);
+// One launch (plus a memset of the scratch); a look-back wait that runs out
+// raises KMX_DERR_TIMEOUT in *err (a valid device word).
 cudaError_t kmx_scan_i32(const int32_t* in, int64_t n, const int64_t* d_n, int64_t* out, void* scratch,
-                         cudaStream_t s);
+                         cudaStream_t s, unsigned int* err);
 
 // voxel.cu
 size_t kmx_voxelize_scratch_bytes(int64_t n_raw);

@@ -102,7 +102,7 @@ cudaError_t match_emit(kmx_ctx* ctx, const MatchScratch& s, int64_t np_cap, cons
 {
     cudaStream_t st = ctx->stream;
     cudaError_t e;
-    if ((e = kmx_scan_i32(s.mflag, np_cap, d_np, s.mpos, s.scan, st))) return e;
+    if ((e = kmx_scan_i32(s.mflag, np_cap, d_np, s.mpos, s.scan, st, ctx->d_err))) return e;
     KMX_COUNT_LAUNCH();
     emit<<<kmx_blocks(np_cap, kThreads), kThreads, 0, st>>>(np_cap, d_np, s.merged, s.mflag, s.mpos, vp, vq, out,
                                                             cap, n_out, ctx->d_err);

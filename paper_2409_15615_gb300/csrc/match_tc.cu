@@ -652,10 +652,10 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
     rerank<<<kmx_blocks(nq_cap, 8), 256, 0, st>>>(dq, nq_cap, d_nq, dp, b.candQ, b.chunks + 1, b.mean, b.maxnorm,
                                                   nullptr, s.colbest, b.flagQ, nullptr);
     // exact fallback for the flagged rows of each side
-    if ((e = kmx_scan_i32(b.flagP, np_cap, d_np, b.posP, b.scan, st))) return e;
+    if ((e = kmx_scan_i32(b.flagP, np_cap, d_np, b.posP, b.scan, st, ctx->d_err))) return e;
     KMX_COUNT_LAUNCH();
     compact_flags<<<kmx_blocks(np_cap, 256), 256, 0, st>>>(np_cap, d_np, b.flagP, b.posP, b.listP, b.nlist + 0);
-    if ((e = kmx_scan_i32(b.flagQ, nq_cap, d_nq, b.posQ, b.scan, st))) return e;
+    if ((e = kmx_scan_i32(b.flagQ, nq_cap, d_nq, b.posQ, b.scan, st, ctx->d_err))) return e;
     KMX_COUNT_LAUNCH();
     compact_flags<<<kmx_blocks(nq_cap, 256), 256, 0, st>>>(nq_cap, d_nq, b.flagQ, b.posQ, b.listQ, b.nlist + 1);
     if ((e = kmx_match_fp32_rows_launch(ctx, dp, b.listP, np_cap, b.nlist + 0, dq, nq_cap, d_nq, b.fbP,

@@ -406,7 +406,7 @@ cudaError_t kmx_normals_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_params
     clear_counts<<<kmx_blocks(n + 1, 256), 256, 0, st>>>(s.cnt, n);
     KMX_COUNT_LAUNCH();
     search_count<<<kmx_blocks(n, kWarps), kThreads, 0, st>>>(gv, R, s);
-    if ((e = kmx_scan_i32(s.cnt, n, g->d_n, offs, s.scan, st))) return e;
+    if ((e = kmx_scan_i32(s.cnt, n, g->d_n, offs, s.scan, st, ctx->d_err))) return e;
     NormOut o{reinterpret_cast<float4*>(normal4), flags, offs, nbr, nbr_cap, n, needed, prm->tau_num,
               prm->tau_lin, {prm->viewpoint[0], prm->viewpoint[1], prm->viewpoint[2]}};
     KMX_COUNT_LAUNCH();

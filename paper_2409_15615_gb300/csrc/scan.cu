@@ -1,6 +1,16 @@
-// Device-wide exclusive prefix sum (three-phase: tile scans, a recursive scan
-// of the tile totals, then a uniform add).  Used to turn per-point counts into
-// CSR offsets and to compact flagged points in order.
+// Device-wide exclusive prefix sum in one pass (decoupled look-back, after
+// Merrill and Garland, "Single-pass Parallel Prefix Scan with Decoupled
+// Look-back", 2016).  Used to turn per-point counts into CSR offsets and to
+// compact flagged points in order.
+//
+// Each CTA claims the next tile id from a counter (so a tile only ever waits
+// for tiles claimed before it, by CTAs already running), scans its tile,
+// publishes the tile total as an "aggregate", then looks back over the
+// predecessors' status words, summing aggregates until it meets an
+// "inclusive prefix", and publishes its own inclusive prefix.  A status word
+// holds the flag in its top two bits and the value below, so one 64-bit load
+// sees both.  Every spin is bounded: when it runs out the CTA records
+// KMX_DERR_TIMEOUT and finishes with a wrong prefix instead of waiting on.
 #include "kmx_internal.cuh"
 
 namespace {
@@ -8,21 +18,44 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kItems = 8;
 constexpr int64_t kTile = kThreads * kItems;
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagIncl = 2ull << 62;
+constexpr unsigned long long kValueMask = (1ull << 62) - 1;
+constexpr uint32_t kPollLimit = 1u << 22;
 
-// Scan one tile of `len` entries; entries at i >= count read as 0.  Writes the
-// tile-local exclusive prefix for i < len and the tile total.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) scan_tiles(const T* __restrict__ in, int64_t len, int64_t count_cap,
-                                                       const int64_t* __restrict__ d_count,
-                                                       int64_t* __restrict__ out, int64_t* __restrict__ tile_sums)
+__device__ __forceinline__ unsigned long long load_status(const unsigned long long* p)
 {
-    int64_t count = d_count ? min(*d_count, count_cap) : count_cap;
-    int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kItems;
+    return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+
+__device__ __forceinline__ void store_status(unsigned long long* p, unsigned long long v)
+{
+    *reinterpret_cast<volatile unsigned long long*>(p) = v;
+}
+
+// status[0] is the tile counter, status[1 + t] the status word of tile t; all
+// zero before the launch.  Entries at i >= count read as 0; out[i] is written
+// for i < len.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) scan_onepass(const T* __restrict__ in, int64_t len, int64_t count_cap,
+                                                         const int64_t* __restrict__ d_count,
+                                                         int64_t* __restrict__ out,
+                                                         unsigned long long* __restrict__ status,
+                                                         unsigned int* __restrict__ err)
+{
+    __shared__ int64_t wsum[kThreads / 32];
+    __shared__ int64_t tile_prefix;
+    __shared__ int64_t tile_id;
+    if (threadIdx.x == 0) tile_id = (int64_t)atomicAdd(status, 1ull);
+    __syncthreads();
+    const int64_t tile = tile_id;
+    const int64_t count = d_count ? min(*d_count, count_cap) : count_cap;
+    const int64_t base = tile * kTile + (int64_t)threadIdx.x * kItems;
     int64_t v[kItems];
     int64_t s = 0;
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
-        int64_t idx = base + i;
+        const int64_t idx = base + i;
         v[i] = idx < count ? (int64_t)in[idx] : 0;
         s += v[i];
     }
@@ -30,77 +63,82 @@ __global__ void __launch_bounds__(kThreads) scan_tiles(const T* __restrict__ in,
     int64_t x = s;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
-    __shared__ int64_t wsum[kThreads / 32];
     if (lane == 31) wsum[warp] = x;
     __syncthreads();
     if (warp == 0) {
         int64_t w = lane < kThreads / 32 ? wsum[lane] : 0;
 #pragma unroll
         for (int o = 1; o < kThreads / 32; o <<= 1) {
-            int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+            const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
             if (lane >= o) w += y;
         }
         if (lane < kThreads / 32) wsum[lane] = w;
+        const int64_t total = __shfl_sync(0xffffffffu, w, kThreads / 32 - 1);
+        unsigned long long* st = status + 1;
+        int64_t excl = 0;
+        if (tile == 0) {
+            if (lane == 0) store_status(&st[0], kFlagIncl | ((unsigned long long)total & kValueMask));
+        } else {
+            if (lane == 0) store_status(&st[tile], kFlagAgg | ((unsigned long long)total & kValueMask));
+            int64_t pred = tile - 1;
+            uint32_t polls = 0;
+            bool timed_out = false;
+            while (true) {
+                const int64_t t = pred - lane;
+                // before tile 0 there is nothing: an inclusive prefix of 0
+                unsigned long long w_st = t >= 0 ? load_status(&st[t]) : kFlagIncl;
+                while (__any_sync(0xffffffffu, (w_st >> 62) == 0)) {
+                    if (++polls > kPollLimit) {
+                        timed_out = true;
+                        break;
+                    }
+                    if ((w_st >> 62) == 0) w_st = load_status(&st[t]);
+                }
+                if (timed_out) break;
+                const unsigned incl = __ballot_sync(0xffffffffu, (w_st >> 62) == 2);
+                const int stop = incl ? __ffs(incl) - 1 : 32;  // nearest inclusive predecessor
+                int64_t c = lane <= stop ? (int64_t)(w_st & kValueMask) : 0;
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+                excl += c;
+                if (incl) break;
+                pred -= 32;
+            }
+            if (lane == 0) {
+                if (timed_out) kmx_raise(err, KMX_DERR_TIMEOUT);
+                store_status(&st[tile], kFlagIncl | ((unsigned long long)(excl + total) & kValueMask));
+            }
+        }
+        if (lane == 0) tile_prefix = excl;
     }
     __syncthreads();
-    int64_t excl = x - s + (warp ? wsum[warp - 1] : 0);
+    int64_t e = tile_prefix + x - s + (warp ? wsum[warp - 1] : 0);
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
-        int64_t idx = base + i;
-        if (idx < len) out[idx] = excl;
-        excl += v[i];
-    }
-    if (threadIdx.x == kThreads - 1) tile_sums[blockIdx.x] = excl;
-}
-
-__global__ void __launch_bounds__(kThreads) add_tile_offsets(int64_t* __restrict__ out, int64_t len,
-                                                             const int64_t* __restrict__ tile_offs)
-{
-    int64_t base = (int64_t)blockIdx.x * kTile;
-    int64_t add = tile_offs[blockIdx.x];
-    if (add == 0) return;
-    for (int i = threadIdx.x; i < kTile; i += kThreads) {
-        int64_t idx = base + i;
-        if (idx < len) out[idx] += add;
+        const int64_t idx = base + i;
+        if (idx < len) out[idx] = e;
+        e += v[i];
     }
 }
 
-size_t level_bytes(int64_t len)
-{
-    int64_t nb = (len + kTile - 1) / kTile;
-    if (nb <= 1) return 256;
-    // tile sums (nb) + their exclusive scan (nb + 1), then the next level
-    return kmx_align_up((size_t)(2 * nb + 1) * sizeof(int64_t), 256) + level_bytes(nb + 1);
-}
-
-template <typename T>
-cudaError_t scan_level(const T* in, int64_t len, int64_t count_cap, const int64_t* d_count, int64_t* out,
-                       char* scratch, cudaStream_t s)
-{
-    int64_t nb = (len + kTile - 1) / kTile;
-    if (nb < 1) nb = 1;
-    int64_t* sums = reinterpret_cast<int64_t*>(scratch);
-    int64_t* offs = sums + nb;
-    KMX_COUNT_LAUNCH();
-    scan_tiles<T><<<(unsigned)nb, kThreads, 0, s>>>(in, len, count_cap, d_count, out, sums);
-    if (nb == 1) return cudaGetLastError();
-    char* next = scratch + kmx_align_up((size_t)(2 * nb + 1) * sizeof(int64_t), 256);
-    cudaError_t e = scan_level<int64_t>(sums, nb + 1, nb, nullptr, offs, next, s);
-    if (e != cudaSuccess) return e;
-    KMX_COUNT_LAUNCH();
-    add_tile_offsets<<<(unsigned)nb, kThreads, 0, s>>>(out, len, offs);
-    return cudaGetLastError();
-}
+int64_t tiles_for(int64_t len) { return len > 0 ? (len + kTile - 1) / kTile : 1; }
 
 }  // namespace
 
-size_t kmx_scan_scratch_bytes(int64_t n) { return level_bytes(n + 1); }
+size_t kmx_scan_scratch_bytes(int64_t n) { return kmx_align_up((size_t)(tiles_for(n + 1) + 1) * 8, 256); }
 
 cudaError_t kmx_scan_i32(const int32_t* in, int64_t n, const int64_t* d_n, int64_t* out, void* scratch,
-                         cudaStream_t s)
+                         cudaStream_t s, unsigned int* err)
 {
-    return scan_level<int32_t>(in, n + 1, n, d_n, out, static_cast<char*>(scratch), s);
+    const int64_t len = n + 1;
+    const int64_t tiles = tiles_for(len);
+    unsigned long long* status = static_cast<unsigned long long*>(scratch);
+    cudaError_t e = cudaMemsetAsync(status, 0, (size_t)(tiles + 1) * 8, s);
+    if (e) return e;
+    KMX_COUNT_LAUNCH();
+    scan_onepass<int32_t><<<(unsigned)tiles, kThreads, 0, s>>>(in, len, n, d_n, out, status, err);
+    return cudaGetLastError();
 }

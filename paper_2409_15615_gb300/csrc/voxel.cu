@@ -266,13 +266,13 @@ cudaError_t kmx_voxelize_launch(kmx_ctx* ctx, const float* xyz, int64_t n, int s
     vox_insert<<<nb, kThreads, 0, st>>>(xyz, n, stride, (double)v, s, ctx->d_err);
     KMX_COUNT_LAUNCH();
     vox_first_flag<<<nb, kThreads, 0, st>>>(n, s);
-    if ((e = kmx_scan_i32(s.flag, n, nullptr, s.oidx, s.scan, st))) return e;
+    if ((e = kmx_scan_i32(s.flag, n, nullptr, s.oidx, s.scan, st, ctx->d_err))) return e;
     if ((e = cudaMemsetAsync(s.cursor, 0, sizeof(int32_t) * (n + 1), st))) return e;
     KMX_COUNT_LAUNCH();
     vox_number<<<nb, kThreads, 0, st>>>(n, s, cap, n_out, ctx->d_err);
     // member offsets per output voxel: scan of the counts parked in `cursor`
     if ((e = cudaMemcpyAsync(s.flag, s.cursor, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st))) return e;
-    if ((e = kmx_scan_i32(s.flag, n, n_out, s.vstart, s.scan, st))) return e;
+    if ((e = kmx_scan_i32(s.flag, n, n_out, s.vstart, s.scan, st, ctx->d_err))) return e;
     if ((e = cudaMemsetAsync(s.cursor, 0, sizeof(int32_t) * (n + 1), st))) return e;
     KMX_COUNT_LAUNCH();
     vox_scatter<<<nb, kThreads, 0, st>>>(n, s, assign);
