@@ -225,7 +225,9 @@ kmx_status kmx_fasterpfh(kmx_ctx* ctx, const kmx_grid* grid, const kmx_params* p
  *   d_out      [cap] kmx_corr sorted by source row; (i, j) are point
  *              indices taken through d_valid_p / d_valid_q.
  *   d_n_out    device int64: |A|.
- * Device errors: KMX_ECAPACITY if |A| > cap (the first cap pairs are kept).
+ * Device errors: KMX_ECAPACITY if |A| > cap (the first cap pairs are kept);
+ * in KMX_MATCH_FP32_EXACT mode KMX_ERANGE if a descriptor value among the
+ * first n_p / n_q rows is NaN or infinite (A is then unspecified).
  */
 kmx_status kmx_match(kmx_ctx* ctx, const float* d_desc_p, const int32_t* d_valid_p, int64_t np_cap,
                      const int64_t* d_np, const float* d_desc_q, const int32_t* d_valid_q, int64_t nq_cap,

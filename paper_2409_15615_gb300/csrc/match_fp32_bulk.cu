@@ -1,33 +1,45 @@
 // Mutual nearest-neighbour matching of descriptors (reciprocity test,
 // Sec. III-C), exact FP32 path of kmx_match: the tiled matcher with its
-// operands staged by bulk copies.
+// operands staged by bulk copies and the all-zero dimensions of a tile pair
+// skipped.
 //
 // Every distance is sum_h (x_h - y_h)^2 over the 33 descriptor values, each
 // term added with one fused multiply-add in h order, exactly the arithmetic of
-// match_fp32.cu (so both give identical bits):
+// match_fp32.cu.  A term whose x_h and y_h are both zero is fma(+-0, +-0,
+// acc) = acc, so leaving it out gives the same bits; FPFH histograms are
+// mostly zeros (about 70 % of the entries on LiDAR scans), and rows with
+// similar zero patterns are grouped into the same tiles so that whole
+// dimensions of a 128 x 128 tile pair are zero on both sides:
 //
-//   pack_tiles        descriptor rows -> 128-row tiles stored transposed
-//                     ([33][128]); source values as (x, x) pairs, so a pair
-//                     loads straight into a paired FP32 instruction, target
-//                     values negated (x + (-y) == x - y exactly).  Rows past
-//                     the count are zero and ignored later.
+//   mask_insert    per row: the nonzero mask of its 33 values, counted in a
+//                  hash table of (side, mask); the first row of a mask lists it.
+//   mask_rank      per distinct mask: the rows with a smaller mask on its side
+//                  (masks compared with dimension 0 as the most significant
+//                  bit), i.e. where its group starts.  A few hundred to a
+//                  thousand distinct masks occur per cloud, so this is cheap.
+//   place_pack     each row at the next free position of its group (rows with
+//                  one mask are interchangeable: their order inside a group
+//                  changes neither a tile's mask nor any result), written into
+//                  the packed tiles: transposed [33][128]; source values as
+//                  (x, x) pairs (one load per paired FP32 instruction), target
+//                  values negated (x + (-y) == x - y exactly); the original
+//                  row index beside each tile; the tile's nonzero mask (OR of
+//                  its rows).
 //   match_tiles_fp32_bulk
-//                     the (row tile x column tile) grid, flattened row-major,
-//                     is split into equal contiguous ranges, one per CTA, with
-//                     as many CTAs as fit on the GPU at once (every CTA gets
-//                     the same number of tiles, +-1).  The source tile stays
-//                     in shared memory; target tiles stream through a 3-stage
-//                     ring filled by cp.async.bulk (one contiguous 16.5 KB
-//                     copy per tile, mbarrier completion), so no register
-//                     holds a prefetched tile.  Each thread keeps an 8 x 8
-//                     block of distances (paired instructions on column
-//                     pairs).  Per row: (best, its column, second best), ties
-//                     to the lower column; per column: the best (distance,
-//                     row) packed into 64 bits and folded with atomicMin.
-//                     When a CTA leaves a row tile (or its range ends) it
-//                     writes the rows' summaries as one "segment".
-//   merge_segments    per source row, the segments of its row tile in column
-//                     order, then the reciprocity test.
+//                  the (row tile x column tile) grid, flattened row-major, is
+//                  split into equal contiguous ranges, one per CTA, with as
+//                  many CTAs as fit on the GPU at once.  The source tile stays
+//                  in shared memory; target tiles stream through a 3-stage
+//                  ring filled by cp.async.bulk (mbarrier completion).  For a
+//                  tile pair only the dimensions set in either tile's mask are
+//                  visited, in ascending order.  Each thread keeps an 8 x 8
+//                  block of distances.  Per row: (best, its column, second
+//                  best), ties to the lower original column; per column: the
+//                  best (distance, original row) packed into 64 bits and folded
+//                  with atomicMin.  When a CTA leaves a row tile (or its range
+//                  ends) it writes the rows' summaries as one "segment".
+//   merge_segments per source row, the segments of its row tile, then the
+//                  reciprocity test; results land at the original row.
 //
 // Every mbarrier wait is bounded; on timeout the kernel records
 // KMX_DERR_TIMEOUT, waits (bounded) for the copies it issued and returns.
@@ -50,83 +62,286 @@ constexpr int kStride = KMX_DESC_STRIDE;
 constexpr int kStages = 3;
 constexpr uint32_t kPBytes = kDim * kTile * sizeof(float2);  // 33792
 constexpr uint32_t kQBytes = kDim * kTile * sizeof(float);   // 16896
+constexpr uint32_t kPermBytes = kTile * sizeof(int32_t);     // 512
 constexpr int kCtasPerSm = 2;
+constexpr int kChunksPerCta = 16;  // chunks of the tile sequence per resident CTA (load balance)
+constexpr int kMinChunk = 4;       // tile pairs per chunk at least (more than kStages - 1)
+
+// Thread 0's position in its own stream of tile pairs (kept in shared memory:
+// only thread 0 uses it): the chunk being produced, the offset in it, the tile
+// index and column tile of the next item, its ring stage.
+struct Producer {
+    int64_t x;
+    int c;
+    int o;
+    int ct;
+    int par;
+    int st;
+};
 
 struct __align__(16) BulkShared {
     float2 P[kDim][kTile];                              // source tile, (x, x) pairs
     float Q[kStages][kDim][kTile];                      // negated target tiles
     unsigned long long colred[kThreads / 32][kTile];    // per-warp column bests
+    int32_t pperm[kTile];                               // original row of each tile row
+    int32_t qperm[kStages][kTile];                      // original column of each tile column
     uint64_t bar_p;
     uint64_t bar_q[kStages];
+    Producer prod;
+    int chunk[2];                                       // chunk ids of the current and next local chunk
+    int end_item;                                       // first local item past the stream (INT_MAX = unknown)
     int failed;
 };
-static_assert(kPBytes % 16 == 0 && kQBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
-static_assert(offsetof(BulkShared, Q) % 16 == 0, "bulk copy destinations are 16-byte aligned");
+static_assert(kPBytes % 16 == 0 && kQBytes % 16 == 0 && kPermBytes % 16 == 0, "bulk copies move 16-byte units");
+static_assert(offsetof(BulkShared, Q) % 16 == 0 && offsetof(BulkShared, pperm) % 16 == 0 &&
+                  offsetof(BulkShared, qperm) % 16 == 0,
+              "bulk copy destinations are 16-byte aligned");
 
-// One thread per row of the padded matrix (rows up to the count rounded up to
-// a whole tile).
-template <bool kPairs>
-__global__ void __launch_bounds__(256) pack_tiles(const float* __restrict__ desc, int64_t n_cap,
-                                                  const int64_t* d_n, void* __restrict__ out)
+__host__ __device__ __forceinline__ int64_t tiles_of(int64_t n) { return (n + kTile - 1) / kTile; }
+
+// Both sides of one matching call (side 0 = source rows, side 1 = target).
+struct SortSides {
+    const float* desc[2];
+    int64_t cap[2];
+    const int64_t* d_n[2];
+    int32_t* rowslot[2];           // [cap] hash slot of each row's mask
+    unsigned long long* keys;      // [T] (side << 33) | mask, ~0 = empty
+    int32_t* count;                // [T] rows per mask
+    int32_t* cursor;               // [T] placement cursor per mask
+    int64_t* gstart;               // [T] first position of each mask's group
+    int32_t* distinct;             // [T] slots in use
+    int32_t* n_distinct;           // [1]
+    unsigned long long* dorder;    // [T] per distinct mask: (side << 40) | mask order
+    int32_t* dcount;               // [T] per distinct mask: its rows
+    uint32_t T;                    // power of two >= 2 (cap0 + cap1)
+    void* packed[2];               // side 0: float2 pairs, side 1: negated floats
+    int32_t* perm[2];              // [tiles * 128] original row per packed position, -1 = padding
+    unsigned long long* mask[2];   // [tiles] nonzero dimensions of each packed tile
+    unsigned long long* colbest;   // [cap1] reset here
+};
+
+__device__ __forceinline__ unsigned long long row_mask(const float* __restrict__ row, float (&v)[kStride])
 {
-    const int64_t n = kmx_count(d_n, n_cap);
-    const int64_t n_pad = (n + kTile - 1) / kTile * kTile;
-    const int64_t r = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    if (r >= n_pad) return;
-    float v[kStride];
-    if (r < n) {
-        const float4* row = reinterpret_cast<const float4*>(desc + r * kStride);
+    const float4* r4 = reinterpret_cast<const float4*>(row);
 #pragma unroll
-        for (int c = 0; c < kStride / 4; ++c) {
-            const float4 x = __ldg(row + c);
-            v[4 * c] = x.x;
-            v[4 * c + 1] = x.y;
-            v[4 * c + 2] = x.z;
-            v[4 * c + 3] = x.w;
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < kStride; ++k) v[k] = 0.f;
+    for (int c = 0; c < kStride / 4; ++c) {
+        const float4 x = __ldg(r4 + c);
+        v[4 * c] = x.x;
+        v[4 * c + 1] = x.y;
+        v[4 * c + 2] = x.z;
+        v[4 * c + 3] = x.w;
     }
-    const int64_t base = (r / kTile) * kDim * kTile + (r % kTile);
-    if (kPairs) {
-        float2* o = static_cast<float2*>(out) + base;
+    unsigned long long m = 0;
 #pragma unroll
-        for (int k = 0; k < kDim; ++k) o[k * kTile] = make_float2(v[k], v[k]);
-    } else {
-        float* o = static_cast<float*>(out) + base;
+    for (int k = 0; k < kDim; ++k) m |= (unsigned long long)(v[k] != 0.f) << k;
+    return m;  // bit k = dimension k
+}
+
+__device__ __forceinline__ bool row_finite(const float (&v)[kStride])
+{
+    bool ok = true;
 #pragma unroll
-        for (int k = 0; k < kDim; ++k) o[k * kTile] = -v[k];
+    for (int k = 0; k < kDim; ++k) ok &= fabsf(v[k]) <= 3.402823466e38f;  // false for NaN and +-inf
+    return ok;
+}
+
+// Order of masks: dimension 0 is the most significant bit.
+__device__ __forceinline__ unsigned long long mask_order(unsigned long long m) { return __brevll(m) >> (64 - kDim); }
+
+__global__ void __launch_bounds__(256) mask_insert(SortSides S, unsigned int* err)
+{
+    const int64_t n0 = kmx_count(S.d_n[0], S.cap[0]), n1 = kmx_count(S.d_n[1], S.cap[1]);
+    const int64_t t0 = tiles_of(n0), t1 = tiles_of(n1);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n0 + n1; t += stride) {
+        const int s = t < n0 ? 0 : 1;
+        const int64_t i = s ? t - n0 : t;
+        float v[kStride];
+        const unsigned long long key = ((unsigned long long)s << kDim) | row_mask(S.desc[s] + i * kStride, v);
+        if (!row_finite(v)) kmx_raise(err, KMX_DERR_RANGE);
+        if (s == 1) S.colbest[i] = ~0ull;
+        const int slot = kmx_hash_insert(S.keys, S.T, key);
+        S.rowslot[s][i] = slot;
+        if (slot < 0) {  // cannot happen at load <= 1/2; reported, never written past
+            kmx_raise(err, KMX_DERR_HASHFULL);
+            continue;
+        }
+        // one atomic per distinct slot in the warp (a few masks hold most rows)
+        const unsigned same = __match_any_sync(__activemask(), slot);
+        if ((threadIdx.x & 31) == __ffs(same) - 1 &&
+            atomicAdd(&S.count[slot], __popc(same)) == 0)
+            S.distinct[atomicAdd(S.n_distinct, 1)] = slot;
+    }
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < t0 + t1; t += stride) {
+        if (t < t0)
+            S.mask[0][t] = 0;
+        else
+            S.mask[1][t - t0] = 0;
     }
 }
 
-__device__ __forceinline__ void row_step(float& b1, int& j1, float& b2, float d, int j)
+__global__ void __launch_bounds__(256) mask_compact(SortSides S)
 {
-    // columns arrive in ascending order, so an equal distance keeps the
-    // earlier (lower) column; NaN compares false and is ignored
-    const bool lt1 = d < b1, lt2 = d < b2;
-    b2 = lt1 ? b1 : (lt2 ? d : b2);
-    j1 = lt1 ? j : j1;
-    b1 = lt1 ? d : b1;
+    const int nd = *S.n_distinct;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nd; e += stride) {
+        const int slot = S.distinct[e];
+        const unsigned long long key = S.keys[slot];
+        S.dorder[e] = ((key >> kDim) << 40) | mask_order(key);
+        S.dcount[e] = S.count[slot];
+    }
+}
+
+// One warp per distinct mask: the rows of the smaller masks on its side (the
+// lanes stride over the compact list) give where its group starts.
+__global__ void __launch_bounds__(256) mask_rank(SortSides S)
+{
+    const int nd = *S.n_distinct;
+    const int lane = threadIdx.x & 31;
+    const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < nd; e += wstride) {
+        const unsigned long long me = S.dorder[e];
+        const unsigned long long lo = me & ~((1ull << 40) - 1);  // same side, any mask
+        int64_t start = 0;
+        for (int f = lane; f < nd; f += 32) {
+            const unsigned long long o = S.dorder[f];
+            if (o >= lo && o < me) start += S.dcount[f];
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) start += __shfl_xor_sync(0xffffffffu, start, o);
+        if (lane == 0) S.gstart[S.distinct[e]] = start;
+    }
+}
+
+// Slots cover each side's padded rows: slot < n is row `slot`, placed and
+// packed; n <= slot < tiles * 128 is a padding position, zeroed.
+__global__ void __launch_bounds__(256) place_pack(SortSides S)
+{
+    const int64_t n0 = kmx_count(S.d_n[0], S.cap[0]), n1 = kmx_count(S.d_n[1], S.cap[1]);
+    const int64_t pad0 = tiles_of(n0) * kTile, pad1 = tiles_of(n1) * kTile;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < pad0 + pad1; t += stride) {
+        const int s = t < pad0 ? 0 : 1;
+        const int64_t slot = s ? t - pad0 : t;
+        float v[kStride];
+        int64_t pos;
+        int32_t orig;
+        if (slot < (s ? n1 : n0)) {
+            const int hs = S.rowslot[s][slot];
+            if (hs < 0) continue;  // table overflow, already reported
+            const unsigned long long m = row_mask(S.desc[s] + slot * kStride, v);
+            // one atomic per distinct slot in the warp; lanes take consecutive places
+            const unsigned same = __match_any_sync(__activemask(), hs);
+            const int lane = threadIdx.x & 31, leader = __ffs(same) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(&S.cursor[hs], __popc(same));
+            base = __shfl_sync(same, base, leader);
+            pos = S.gstart[hs] + base + __popc(same & ((1u << lane) - 1u));
+            orig = (int32_t)slot;
+            if (m) atomicOr(&S.mask[s][pos / kTile], m);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kStride; ++k) v[k] = 0.f;
+            pos = slot;
+            orig = -1;
+        }
+        S.perm[s][pos] = orig;
+        const int64_t base = (pos / kTile) * kDim * kTile + (pos % kTile);
+        if (s == 0) {
+            float2* o = static_cast<float2*>(S.packed[0]) + base;
+#pragma unroll
+            for (int k = 0; k < kDim; ++k) o[k * kTile] = make_float2(v[k], v[k]);
+        } else {
+            float* o = static_cast<float*>(S.packed[1]) + base;
+#pragma unroll
+            for (int k = 0; k < kDim; ++k) o[k * kTile] = -v[k];
+        }
+    }
+}
+
+// Row best as one key: distance bits (non-negative floats order like their
+// bits) above the original column, so the minimum key is the best distance
+// with ties to the lower column, in any visiting order; the second best is the
+// second smallest of {b1, b2, d} = min(b2, max(b1, d)).  Needs finite
+// distances (descriptors are checked when they are packed).
+__device__ __forceinline__ void row_step(unsigned long long& k1, float& b2, float d, uint32_t j)
+{
+    const float b1 = __uint_as_float((uint32_t)(k1 >> 32));
+    b2 = fminf(b2, fmaxf(b1, d));
+    const unsigned long long kd = ((unsigned long long)__float_as_uint(d) << 32) | j;
+    k1 = kd < k1 ? kd : k1;
+}
+
+constexpr unsigned long long kNoBest = (0x7f800000ull << 32) | 0x7fffffffull;  // (+inf, no column)
+
+// The flattened tile sequence (row-major over packed row tiles x column
+// tiles) is cut into NC chunks of L consecutive tile pairs; CTAs take chunks
+// from a counter, so a CTA whose tile pairs need many dimensions simply takes
+// fewer chunks.  The chunk holding tile x is x / L; the segment of chunk c in
+// row tile rt lives in slot c + rt (chunks are contiguous, so slots are
+// unique and below NC + npt).
+struct ChunkGeo {
+    int L, NC;
+};
+
+__device__ __forceinline__ ChunkGeo chunk_geo(int64_t W, int ctas)
+{
+    const int64_t per = (int64_t)kChunksPerCta * ctas;
+    int64_t L = (W + per - 1) / per;
+    if (L < kMinChunk) L = kMinChunk;
+    return ChunkGeo{(int)L, (int)((W + L - 1) / L)};
+}
+
+__device__ __forceinline__ int read_end(const BulkShared& S) { return *reinterpret_cast<const volatile int*>(&S.end_item); }
+
+// Thread 0 only, for consecutive local items u: take a new chunk when the
+// current one is used up, stop (recording the end of the stream) when the
+// counter has run out or the tile sequence has ended, else issue the copies
+// of the item's column tile into its ring stage.
+__device__ __forceinline__ bool produce(BulkShared& S, int u, const ChunkGeo& cg, int64_t W, int nqt,
+                                        int32_t* counter, const float* __restrict__ qn,
+                                        const int32_t* __restrict__ qperm, int& issued)
+{
+    Producer& P = S.prod;
+    if (P.o == cg.L) {
+        P.par ^= 1;
+        P.o = 0;
+        P.c = atomicAdd(counter, 1);
+        S.chunk[P.par] = P.c;
+        P.x = (int64_t)P.c * cg.L;
+        P.ct = (int)(P.x % nqt);
+    }
+    if (P.c >= cg.NC || P.x >= W) {
+        S.end_item = u;
+        return false;
+    }
+    mbar_expect_tx(&S.bar_q[P.st], kQBytes + kPermBytes);
+    bulk_g2s(S.Q[P.st], qn + (int64_t)P.ct * kDim * kTile, kQBytes, &S.bar_q[P.st]);
+    bulk_g2s(S.qperm[P.st], qperm + (int64_t)P.ct * kTile, kPermBytes, &S.bar_q[P.st]);
+    issued = u + 1;
+    ++P.o;
+    ++P.x;
+    if (++P.ct == nqt) P.ct = 0;
+    if (++P.st == kStages) P.st = 0;
+    return true;
 }
 
 __global__ void __launch_bounds__(kThreads, kCtasPerSm)
-    match_tiles_fp32_bulk(const float2* __restrict__ pp, int64_t np_cap, const int64_t* d_np,
-                          const float* __restrict__ qn, int64_t nq_cap, const int64_t* d_nq, int ctas,
-                          kmx::RowBest* __restrict__ seg, unsigned long long* __restrict__ colbest,
-                          unsigned int* __restrict__ err)
+    match_tiles_fp32_bulk(const float2* __restrict__ pp, const int32_t* __restrict__ pperm,
+                          const unsigned long long* __restrict__ pmask, int64_t np_cap, const int64_t* d_np,
+                          const float* __restrict__ qn, const int32_t* __restrict__ qperm,
+                          const unsigned long long* __restrict__ qmask, int64_t nq_cap, const int64_t* d_nq,
+                          int ctas, int32_t* __restrict__ counter, kmx::RowBest* __restrict__ seg,
+                          unsigned long long* __restrict__ colbest, unsigned int* __restrict__ err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     BulkShared& S = *reinterpret_cast<BulkShared*>(smem_raw);
     const int64_t np = kmx_count(d_np, np_cap), nq = kmx_count(d_nq, nq_cap);
-    const int64_t npt = (np + kTile - 1) / kTile;
-    const int64_t nqt = (nq + kTile - 1) / kTile;
-    const int64_t W = npt * nqt;
-    const int64_t G = min((int64_t)ctas, W);
-    const int64_t b = blockIdx.x;
-    if (b >= G) return;
-    const int64_t w0 = b * W / G;
-    const int T = (int)((b + 1) * W / G - w0);  // >= 1 because G <= W
+    const int npt = (int)tiles_of(np);
+    const int nqt = (int)tiles_of(nq);
+    const int64_t W = (int64_t)npt * nqt;
+    if (W == 0) return;
+    const ChunkGeo cg = chunk_geo(W, ctas);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tx = tid & 15;                     // column group: columns 4tx..4tx+3 and 64+4tx..64+4tx+3
     const int ty = warp * 2 + ((tid >> 4) & 1);  // row group: rows 8ty..8ty+7
@@ -136,55 +351,74 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
         for (int s = 0; s < kStages; ++s) mbar_init(&S.bar_q[s], 1);
         mbar_fence_init();
         S.failed = 0;
+        S.end_item = INT_MAX;
     }
     __syncthreads();
-    int64_t rt = w0 / nqt;
+    int issued = 0;  // meaningful in thread 0: local items whose copies were issued
     if (tid == 0) {
-        mbar_expect_tx(&S.bar_p, kPBytes);
-        bulk_g2s(S.P, pp + rt * kDim * kTile, kPBytes, &S.bar_p);
-        for (int s = 0; s < kStages && s < T; ++s) {
-            mbar_expect_tx(&S.bar_q[s], kQBytes);
-            bulk_g2s(S.Q[s], qn + ((w0 + s) % nqt) * kDim * kTile, kQBytes, &S.bar_q[s]);
+        const int c0 = atomicAdd(counter, 1);
+        S.chunk[0] = c0;
+        if (c0 >= cg.NC) {
+            S.end_item = 0;
+        } else {
+            const int64_t x0 = (int64_t)c0 * cg.L;
+            S.prod = Producer{x0, c0, 0, (int)(x0 % nqt), 0, 0};
+            const int64_t rt0 = x0 / nqt;
+            mbar_expect_tx(&S.bar_p, kPBytes + kPermBytes);
+            bulk_g2s(S.P, pp + rt0 * kDim * kTile, kPBytes, &S.bar_p);
+            bulk_g2s(S.pperm, pperm + rt0 * kTile, kPermBytes, &S.bar_p);
+            for (int u = 0; u < kStages; ++u)
+                if (!produce(S, u, cg, W, nqt, counter, qn, qperm, issued)) break;
         }
     }
-    int issued = min(T, kStages);  // column tiles whose copy has been issued
+    __syncthreads();
+    if (read_end(S) == 0) return;
+    // this thread's view of the current item: chunk id and parity, offset in
+    // the chunk, row and column tile, ring stage and its phase
+    int cid = S.chunk[0];
+    int kpar = 0;
+    int o = 0;
+    int rt = (int)(((int64_t)cid * cg.L) / nqt);
+    int ct = (int)(((int64_t)cid * cg.L) - (int64_t)rt * nqt);
+    int s = 0;
+    uint32_t qphase = 0;
     uint32_t p_phase = 0;
     bool p_ready = false;
+    unsigned long long mrow = __ldg(pmask + rt);
 
-    float b1[8], b2[8];
-    int j1[8];
+    unsigned long long k1[8];
+    float b2[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        b1[i] = INFINITY;
+        k1[i] = kNoBest;
         b2[i] = INFINITY;
-        j1[i] = 0x7fffffff;
     }
     bool failed = false;
     int t = 0;
-    for (; t < T; ++t) {
-        const int64_t w = w0 + t;
-        const int64_t col0 = (w % nqt) * kTile;
-        const int s = t % kStages;
+    for (; t < read_end(S); ++t) {
+        const int64_t col0 = (int64_t)ct * kTile;
         if (!p_ready) {
             if (!mbar_wait(&S.bar_p, p_phase)) S.failed = 1;
             p_ready = true;
         }
-        if (!mbar_wait(&S.bar_q[s], (uint32_t)(t / kStages) & 1u)) S.failed = 1;
+        if (!mbar_wait(&S.bar_q[s], qphase)) S.failed = 1;
 
         float2 acc[8][4];
 #pragma unroll
         for (int i = 0; i < 8; ++i)
 #pragma unroll
             for (int jp = 0; jp < 4; ++jp) acc[i][jp] = make_float2(0.f, 0.f);
-#pragma unroll 1
-        for (int k = 0; k < kDim; ++k) {
-            const float4 c0 = *reinterpret_cast<const float4*>(&S.Q[s][k][tx * 4]);
-            const float4 c1 = *reinterpret_cast<const float4*>(&S.Q[s][k][64 + tx * 4]);
+        // dimensions that are zero in every row of both tiles add exactly
+        // nothing; the others are visited in ascending order
+        for (unsigned long long m = mrow | __ldg(qmask + ct); m; m &= m - 1) {
+            const int kk = __ffsll((long long)m) - 1;
+            const float4 c0 = *reinterpret_cast<const float4*>(&S.Q[s][kk][tx * 4]);
+            const float4 c1 = *reinterpret_cast<const float4*>(&S.Q[s][kk][64 + tx * 4]);
             const float2 nc[4] = {make_float2(c0.x, c0.y), make_float2(c0.z, c0.w), make_float2(c1.x, c1.y),
                                   make_float2(c1.z, c1.w)};
 #pragma unroll
             for (int ih = 0; ih < 4; ++ih) {
-                const float4 a2 = *reinterpret_cast<const float4*>(&S.P[k][ty * 8 + 2 * ih]);
+                const float4 a2 = *reinterpret_cast<const float4*>(&S.P[kk][ty * 8 + 2 * ih]);
                 const float2 ai[2] = {make_float2(a2.x, a2.y), make_float2(a2.z, a2.w)};
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -196,36 +430,40 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
                 }
             }
         }
-        // row bests, this thread's columns in ascending order
+        // row bests over this thread's columns (padding columns skipped)
 #pragma unroll
         for (int jp = 0; jp < 4; ++jp) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int c = (jp < 2 ? 0 : 64) + tx * 4 + 2 * (jp & 1) + h;
-                const int64_t col = col0 + c;
-                if (col < nq) {
+                if (col0 + c < nq) {
+                    const uint32_t jo = (uint32_t)S.qperm[s][c];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) row_step(b1[i], j1[i], b2[i], h ? acc[i][jp].y : acc[i][jp].x, (int)col);
+                    for (int i = 0; i < 8; ++i) row_step(k1[i], b2[i], h ? acc[i][jp].y : acc[i][jp].x, jo);
                 }
             }
         }
-        // column bests: this thread's 8 rows (ascending, ties to the lower
-        // row), the partner half-warp, then the 8 warps through shared memory
-        const int64_t rowbase = rt * kTile + ty * 8;
+        // column bests: over this thread's 8 rows the smallest distance and
+        // the lowest original row reaching it (padding rows count as +inf),
+        // then the partner half-warp, then the 8 warps through shared memory
+        const int64_t rowbase = (int64_t)rt * kTile + ty * 8;
+        uint32_t ro[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) ro[i] = rowbase + i < np ? (uint32_t)S.pperm[ty * 8 + i] : 0xffffffffu;
 #pragma unroll
         for (int jp = 0; jp < 4; ++jp) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                float m = INFINITY;
-                int mi = -1;
+                float dv[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const float dij = h ? acc[i][jp].y : acc[i][jp].x;
-                    const bool take = rowbase + i < np && (mi < 0 || dij < m);
-                    m = take ? dij : m;
-                    mi = take ? i : mi;
-                }
-                unsigned long long best = mi < 0 ? ~0ull : kmx::pack_dist_index(m, (uint32_t)(rowbase + mi));
+                for (int i = 0; i < 8; ++i) dv[i] = ro[i] != 0xffffffffu ? (h ? acc[i][jp].y : acc[i][jp].x) : INFINITY;
+                float m = dv[0];
+#pragma unroll
+                for (int i = 1; i < 8; ++i) m = fminf(m, dv[i]);
+                uint32_t r = 0xffffffffu;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) r = dv[i] == m ? min(r, ro[i]) : r;
+                unsigned long long best = r == 0xffffffffu ? ~0ull : kmx::pack_dist_index(m, r);
                 const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, 16);
                 best = other < best ? other : best;
                 const int c = (jp < 2 ? 0 : 64) + tx * 4 + 2 * (jp & 1) + h;
@@ -238,49 +476,69 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
             unsigned long long best = S.colred[0][tid];
 #pragma unroll
             for (int v = 1; v < kThreads / 32; ++v) {
-                const unsigned long long o = S.colred[v][tid];
-                best = o < best ? o : best;
+                const unsigned long long ov = S.colred[v][tid];
+                best = ov < best ? ov : best;
             }
-            const int64_t col = col0 + tid;
-            if (col < nq && best != ~0ull) atomicMin(&colbest[col], best);
+            if (col0 + tid < nq && best != ~0ull) atomicMin(&colbest[S.qperm[s][tid]], best);
         }
-        const bool seg_end = (t + 1 == T) || ((w + 1) % nqt == 0);
+        const bool seg_end = (o == cg.L - 1) || (ct + 1 == nqt);  // row tile, chunk or sequence ends
         if (seg_end && !failed) {
             // merge the 16 column groups of each row (one half-warp), write
-            // the segment, restart the row bests
+            // the segment of (chunk, row tile), restart the row bests
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                float d1 = b1[i], d2 = b2[i];
-                int jj = j1[i];
+                float d1 = __uint_as_float((uint32_t)(k1[i] >> 32)), d2 = b2[i];
+                int jj = (int)(uint32_t)k1[i];
 #pragma unroll
-                for (int o = 1; o < 16; o <<= 1) {
-                    const float od1 = __shfl_xor_sync(0xffffffffu, d1, o);
-                    const float od2 = __shfl_xor_sync(0xffffffffu, d2, o);
-                    const int oj = __shfl_xor_sync(0xffffffffu, jj, o);
+                for (int sh = 1; sh < 16; sh <<= 1) {
+                    const float od1 = __shfl_xor_sync(0xffffffffu, d1, sh);
+                    const float od2 = __shfl_xor_sync(0xffffffffu, d2, sh);
+                    const int oj = __shfl_xor_sync(0xffffffffu, jj, sh);
                     kmx::row_merge(d1, jj, d2, od1, oj, od2);
                 }
                 if (tx == 0 && rowbase + i < np)
-                    seg[(b + rt) * kTile + ty * 8 + i] = kmx::RowBest{d1, jj, d2};
-                b1[i] = INFINITY;
+                    seg[((int64_t)cid + rt) * kTile + ty * 8 + i] = kmx::RowBest{d1, jj, d2};
+                k1[i] = kNoBest;
                 b2[i] = INFINITY;
-                j1[i] = 0x7fffffff;
             }
         }
         __syncthreads();  // (2) stage s, the source tile and colred are free
         if (failed) break;
-        if (tid == 0 && t + kStages < T) {
-            mbar_expect_tx(&S.bar_q[s], kQBytes);
-            bulk_g2s(S.Q[s], qn + ((w0 + t + kStages) % nqt) * kDim * kTile, kQBytes, &S.bar_q[s]);
-        }
-        issued = min(T, t + 1 + kStages);
-        if (seg_end && t + 1 < T) {
-            ++rt;
-            if (tid == 0) {
-                mbar_expect_tx(&S.bar_p, kPBytes);
-                bulk_g2s(S.P, pp + rt * kDim * kTile, kPBytes, &S.bar_p);
+        if (tid == 0 && read_end(S) == INT_MAX) produce(S, t + kStages, cg, W, nqt, counter, qn, qperm, issued);
+        // advance to the next item (its chunk id is known: it was produced
+        // kStages items ago); a new row tile reloads the source tile
+        if (t + 1 < read_end(S)) {
+            int rt1;
+            if (o + 1 < cg.L) {
+                ++o;
+                rt1 = rt;
+                if (++ct == nqt) {
+                    ct = 0;
+                    rt1 = rt + 1;
+                }
+            } else {
+                kpar ^= 1;
+                cid = S.chunk[kpar];
+                o = 0;
+                const int64_t x1 = (int64_t)cid * cg.L;
+                rt1 = (int)(x1 / nqt);
+                ct = (int)(x1 - (int64_t)rt1 * nqt);
             }
-            p_phase ^= 1u;
-            p_ready = false;
+            if (rt1 != rt) {
+                if (tid == 0) {
+                    mbar_expect_tx(&S.bar_p, kPBytes + kPermBytes);
+                    bulk_g2s(S.P, pp + (int64_t)rt1 * kDim * kTile, kPBytes, &S.bar_p);
+                    bulk_g2s(S.pperm, pperm + (int64_t)rt1 * kTile, kPermBytes, &S.bar_p);
+                }
+                rt = rt1;
+                mrow = __ldg(pmask + rt);
+                p_phase ^= 1u;
+                p_ready = false;
+            }
+        }
+        if (++s == kStages) {
+            s = 0;
+            qphase ^= 1u;
         }
     }
     if (failed && tid == 0) {
@@ -292,54 +550,80 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     }
 }
 
-// One thread per source row: the segments of its row tile, in column order,
-// then the reciprocity test against the packed column bests.
-__global__ void __launch_bounds__(256) merge_segments(const kmx::RowBest* __restrict__ seg, int ctas,
-                                                      int64_t np_cap, const int64_t* d_np, int64_t nq_cap,
-                                                      const int64_t* d_nq,
+// One thread per packed source position: the segments of its row tile (one
+// per chunk that touched it, in ascending column order; row_merge resolves
+// ties by original column), then the reciprocity test; results go to the
+// original row.
+__global__ void __launch_bounds__(256) merge_segments(const kmx::RowBest* __restrict__ seg,
+                                                      const int32_t* __restrict__ pperm, int ctas, int64_t np_cap,
+                                                      const int64_t* d_np, int64_t nq_cap, const int64_t* d_nq,
                                                       const unsigned long long* __restrict__ colbest,
                                                       kmx::RowBest* __restrict__ merged, int32_t* __restrict__ mflag)
 {
     const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
     const int64_t np = kmx_count(d_np, np_cap), nq = kmx_count(d_nq, nq_cap);
     if (i >= np) return;
-    const int64_t npt = (np + kTile - 1) / kTile;
-    const int64_t nqt = (nq + kTile - 1) / kTile;
+    const int64_t npt = tiles_of(np);
+    const int64_t nqt = tiles_of(nq);
     const int64_t W = npt * nqt;
     kmx::RowBest r{INFINITY, 0x7fffffff, INFINITY};
     if (W > 0) {
-        const int64_t G = min((int64_t)ctas, W);
+        const ChunkGeo cg = chunk_geo(W, ctas);
         const int64_t rt = i / kTile;
-        // the CTA whose range holds flattened tile x is floor(((x + 1) G - 1) / W)
-        const int64_t x0 = rt * nqt, x1 = x0 + nqt - 1;
-        const int64_t bf = ((x0 + 1) * G - 1) / W, bl = ((x1 + 1) * G - 1) / W;
-        r = seg[(bf + rt) * kTile + (i % kTile)];
-        for (int64_t bb = bf + 1; bb <= bl; ++bb) {
-            const kmx::RowBest o = seg[(bb + rt) * kTile + (i % kTile)];
+        const int64_t cf = (rt * nqt) / cg.L, cl = (rt * nqt + nqt - 1) / cg.L;
+        r = seg[(cf + rt) * kTile + (i % kTile)];
+        for (int64_t c = cf + 1; c <= cl; ++c) {
+            const kmx::RowBest o = seg[(c + rt) * kTile + (i % kTile)];
             kmx::row_merge(r.d1, r.j1, r.d2, o.d1, o.j1, o.d2);
         }
     }
-    merged[i] = r;
+    const int32_t orig = pperm[i];
+    merged[orig] = r;
     bool mutual = false;
-    if (r.j1 >= 0 && r.j1 != 0x7fffffff) mutual = (uint32_t)(colbest[r.j1] & 0xffffffffull) == (uint32_t)i;
-    mflag[i] = mutual ? 1 : 0;
+    if (r.j1 >= 0 && r.j1 != 0x7fffffff) mutual = (uint32_t)(colbest[r.j1] & 0xffffffffull) == (uint32_t)orig;
+    mflag[orig] = mutual ? 1 : 0;
 }
 
-int64_t tiles_of(int64_t n) { return (n + kTile - 1) / kTile; }
-
 struct BulkScratch {
-    float2* pp;
-    float* qn;
+    SortSides sort;
     kmx::RowBest* seg;
+    int32_t* chunk_counter;
 };
+
+uint32_t mask_table_size(int64_t np_cap, int64_t nq_cap)
+{
+    uint64_t t = 1024;
+    while (t < (uint64_t)(2 * (np_cap + nq_cap + 1))) t <<= 1;
+    return (uint32_t)t;
+}
 
 BulkScratch carve(void* base, int64_t np_cap, int64_t nq_cap, int max_ctas, size_t* total)
 {
     kmx_arena a{static_cast<char*>(base), 0};
-    BulkScratch s;
-    s.pp = static_cast<float2*>(a.take((size_t)tiles_of(np_cap) * kPBytes));
-    s.qn = static_cast<float*>(a.take((size_t)tiles_of(nq_cap) * kQBytes));
-    s.seg = static_cast<kmx::RowBest*>(a.take(sizeof(kmx::RowBest) * kTile * (size_t)(max_ctas + tiles_of(np_cap))));
+    BulkScratch s{};
+    const int64_t cap[2] = {np_cap, nq_cap};
+    for (int side = 0; side < 2; ++side) {
+        const int64_t tiles = tiles_of(cap[side]);
+        s.sort.packed[side] = a.take((size_t)tiles * (side ? kQBytes : kPBytes));
+        s.sort.perm[side] = static_cast<int32_t*>(a.take((size_t)tiles * kPermBytes));
+        s.sort.mask[side] = static_cast<unsigned long long*>(a.take(sizeof(unsigned long long) * (tiles + 1)));
+        s.sort.rowslot[side] = static_cast<int32_t*>(a.take(sizeof(int32_t) * (cap[side] + 1)));
+    }
+    const uint32_t T = mask_table_size(np_cap, nq_cap);
+    s.sort.T = T;
+    s.sort.keys = static_cast<unsigned long long*>(a.take(sizeof(unsigned long long) * T));
+    // count, cursor, the distinct counter and the chunk counter are adjacent:
+    // one memset clears them
+    s.sort.count = static_cast<int32_t*>(a.take(sizeof(int32_t) * (2 * (size_t)T + 2)));
+    s.sort.cursor = s.sort.count + T;
+    s.sort.n_distinct = s.sort.count + 2 * (size_t)T;
+    s.chunk_counter = s.sort.count + 2 * (size_t)T + 1;
+    s.sort.dorder = static_cast<unsigned long long*>(a.take(sizeof(unsigned long long) * T));
+    s.sort.dcount = static_cast<int32_t*>(a.take(sizeof(int32_t) * T));
+    s.sort.gstart = static_cast<int64_t*>(a.take(sizeof(int64_t) * T));
+    s.sort.distinct = static_cast<int32_t*>(a.take(sizeof(int32_t) * T));
+    s.seg = static_cast<kmx::RowBest*>(
+        a.take(sizeof(kmx::RowBest) * kTile * (size_t)(kChunksPerCta * max_ctas + 1 + tiles_of(np_cap))));
     *total = kmx_align_up(a.used, 256);
     return s;
 }
@@ -370,7 +654,14 @@ cudaError_t kmx_match_fp32_bulk_launch(kmx_ctx* ctx, const float* dp, const int3
 {
     cudaStream_t st = ctx->stream;
     size_t total = 0;
-    const BulkScratch b = carve(s.extra, np_cap, nq_cap, max_ctas(ctx->sm_count), &total);
+    BulkScratch b = carve(s.extra, np_cap, nq_cap, max_ctas(ctx->sm_count), &total);
+    b.sort.desc[0] = dp;
+    b.sort.desc[1] = dq;
+    b.sort.cap[0] = np_cap;
+    b.sort.cap[1] = nq_cap;
+    b.sort.d_n[0] = d_np;
+    b.sort.d_n[1] = d_nq;
+    b.sort.colbest = s.colbest;
     cudaError_t e = set_smem_attr();
     if (e) return e;
     int per_sm = 0;
@@ -378,18 +669,25 @@ cudaError_t kmx_match_fp32_bulk_launch(kmx_ctx* ctx, const float* dp, const int3
                                                            sizeof(BulkShared))))
         return e;
     const int ctas = max(1, min(per_sm, kCtasPerSm)) * ctx->sm_count;
+    const unsigned small_grid = 4u * (unsigned)ctx->sm_count;  // grid-stride over the actual rows
+    if ((e = cudaMemsetAsync(b.sort.keys, 0xFF, sizeof(unsigned long long) * b.sort.T, st))) return e;
+    if ((e = cudaMemsetAsync(b.sort.count, 0, sizeof(int32_t) * (2 * (size_t)b.sort.T + 2), st))) return e;
     KMX_COUNT_LAUNCH();
-    pack_tiles<true><<<kmx_blocks(tiles_of(np_cap) * kTile, 256), 256, 0, st>>>(dp, np_cap, d_np, b.pp);
+    mask_insert<<<small_grid, 256, 0, st>>>(b.sort, ctx->d_err);
     KMX_COUNT_LAUNCH();
-    pack_tiles<false><<<kmx_blocks(tiles_of(nq_cap) * kTile, 256), 256, 0, st>>>(dq, nq_cap, d_nq, b.qn);
-    if ((e = cudaMemsetAsync(s.colbest, 0xFF, sizeof(unsigned long long) * nq_cap, st))) return e;
+    mask_compact<<<small_grid, 256, 0, st>>>(b.sort);
     KMX_COUNT_LAUNCH();
-    match_tiles_fp32_bulk<<<ctas, kThreads, sizeof(BulkShared), st>>>(b.pp, np_cap, d_np, b.qn, nq_cap, d_nq, ctas,
-                                                                      b.seg, s.colbest, ctx->d_err);
-    if ((e = cudaMemsetAsync(s.mflag, 0, sizeof(int32_t) * (np_cap + 1), st))) return e;
+    mask_rank<<<small_grid, 256, 0, st>>>(b.sort);
     KMX_COUNT_LAUNCH();
-    merge_segments<<<kmx_blocks(np_cap, 256), 256, 0, st>>>(b.seg, ctas, np_cap, d_np, nq_cap, d_nq, s.colbest,
-                                                            s.merged, s.mflag);
+    place_pack<<<small_grid, 256, 0, st>>>(b.sort);
+    KMX_COUNT_LAUNCH();
+    match_tiles_fp32_bulk<<<ctas, kThreads, sizeof(BulkShared), st>>>(
+        static_cast<const float2*>(b.sort.packed[0]), b.sort.perm[0], b.sort.mask[0], np_cap, d_np,
+        static_cast<const float*>(b.sort.packed[1]), b.sort.perm[1], b.sort.mask[1], nq_cap, d_nq, ctas,
+        b.chunk_counter, b.seg, s.colbest, ctx->d_err);
+    KMX_COUNT_LAUNCH();
+    merge_segments<<<kmx_blocks(np_cap, 256), 256, 0, st>>>(b.seg, b.sort.perm[0], ctas, np_cap, d_np, nq_cap, d_nq,
+                                                            s.colbest, s.merged, s.mflag);
     if ((e = cudaGetLastError())) return e;
     return kmx::match_emit(ctx, s, np_cap, d_np, vp, vq, out, cap, n_out);
 }

@@ -86,3 +86,22 @@ def test_match_capacity_overflow_is_reported(env):
         ctx.sync()
     assert e.value.status == kmx.KMX_ECAPACITY
     assert int(n.item()) == 200  # identical sets: every row is its own mutual neighbour
+
+
+def test_match_non_finite_descriptor_is_reported(env):
+    torch, kmx, ctx = env
+    rng = np.random.default_rng(1)
+    for bad in (np.nan, np.inf, -np.inf):
+        F = rng.random((300, 36)).astype(np.float32)
+        F[:, 33:] = 0
+        G = F.copy()
+        G[123, 7] = bad
+        dp, dq = torch.from_numpy(F).cuda(), torch.from_numpy(G).cuda()
+        ctx.match(dp, None, 300, dq, None, 300, mode=kmx.MATCH_FP32_EXACT)
+        with pytest.raises(kmx.KmxError) as e:
+            ctx.sync()
+        assert e.value.status == kmx.KMX_ERANGE
+    # the context is still usable
+    corr, n = ctx.match(dp, None, 300, dp, None, 300, mode=kmx.MATCH_FP32_EXACT)
+    ctx.sync()
+    assert int(n.item()) == 300

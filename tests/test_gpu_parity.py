@@ -368,6 +368,64 @@ def test_match_fp32_on_oracle_descriptors(torch_cuda, ctx, orc):
     assert n_ref > 100
 
 
+def _noalloc_match(torch, kmx, FP32, FQ32):
+    """kmx_match_noalloc: the register-prefetch tiled kernel, no sorting, no
+    dimension skipping; same FP32 arithmetic per distance."""
+    import ctypes
+
+    lib = kmx.library()
+    fn = lib.kmx_match_noalloc
+    vp, i64 = ctypes.c_void_p, ctypes.c_int64
+    fn.restype = ctypes.c_int
+    fn.argtypes = [vp, vp, i64, vp, vp, vp, i64, vp, vp, i64, vp, vp]
+    dp, dq = dev(torch, _pad36(FP32)), dev(torch, _pad36(FQ32))
+    cap = min(len(FP32), len(FQ32))
+    out = torch.zeros((cap, 4), dtype=torch.int32, device="cuda")
+    n_out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    st = fn(vp(dp.data_ptr()), None, len(FP32), None, vp(dq.data_ptr()), None, len(FQ32), None, vp(out.data_ptr()),
+            cap, vp(n_out.data_ptr()), vp(stream.cuda_stream))
+    assert st == kmx.KMX_OK
+    torch.cuda.synchronize()
+    return out[: int(n_out.item())].cpu().numpy()
+
+
+def test_match_fp32_sparse_ties_equals_dense_kernel(torch_cuda, ctx, orc):
+    """Rows drawn from a few zero patterns (so the exact path regroups rows and
+    skips all-zero dimensions of tile pairs), exact duplicate rows and columns
+    and all-zero rows (ties in both directions, resolved by the original
+    index): the exact path equals the unsorted dense kernel byte for byte,
+    and the oracle up to the gap band."""
+    from paper_2409_15615_gb300 import kmx
+
+    torch = torch_cuda
+    rng = np.random.default_rng(11)
+    patterns = rng.random((40, 33)) < 0.3
+    patterns[:, [5, 16, 27]] = True
+
+    def rows(n):
+        return rng.gamma(0.5, 20.0, (n, 33)) * patterns[rng.integers(0, len(patterns), n)]
+
+    FP, FQ = rows(3000), rows(2600)
+    k = 800
+    src = rng.permutation(3000)[:k]
+    FQ[1000:1000 + k] = FP[src] + rng.normal(0, 0.3, (k, 33)) * (FP[src] != 0)
+    FQ[100:160] = FQ[40:100]  # duplicate columns
+    FP[200:260] = FP[10:70]  # duplicate rows
+    FP[5] = 0.0
+    FQ[7] = 0.0
+    FQ[8] = 0.0
+    FP32, FQ32 = FP.astype(np.float32), FQ.astype(np.float32)
+    corr, n_out = ctx.match(dev(torch, _pad36(FP32)), None, len(FP32), dev(torch, _pad36(FQ32)), None, len(FQ32),
+                            mode=kmx.MATCH_FP32_EXACT)
+    ctx.sync()
+    got = corr[: int(n_out.item())].cpu().numpy()
+    ref = _noalloc_match(torch, kmx, FP32, FQ32)
+    assert len(got) > k // 2
+    assert got.shape == ref.shape and np.array_equal(got, ref)
+    _check_match(torch, ctx, orc, FP, FQ, kmx.MATCH_FP32_EXACT)
+
+
 def test_match_empty(torch_cuda, ctx):
     torch = torch_cuda
     from paper_2409_15615_gb300 import kmx

@@ -1,17 +1,26 @@
 """Host model of the exact matcher's work split (match_fp32_bulk.cu).
 
-The (row tile x column tile) grid, W = npt * nqt tiles flattened row-major,
-is split over G = min(ctas, W) CTAs: CTA b takes tiles [b W / G, (b+1) W / G).
-A CTA writes one row-summary segment per row tile it touches, in slot b + rt;
-merge_segments finds the CTAs that touched row tile rt in closed form,
-b = floor(((x + 1) G - 1) / W) for the first and last tile x of the row tile.
-These checks pin that arithmetic: every tile is covered exactly once, slots
-are unique and inside the (ctas + npt) * 128 segment array, and the merge
-visits exactly the CTAs that touched each row tile, in column order.
+The (row tile x column tile) grid, W = npt * nqt tile pairs flattened
+row-major, is cut into NC chunks of L consecutive pairs, with
+L = max(4, ceil(W / (16 * ctas))); CTAs take chunks from a counter.  The
+segment of chunk c in row tile rt sits in slot c + rt of a
+(16 * ctas + 1 + npt) * 128 array, and merge_segments reads the chunks
+floor(rt * nqt / L) .. floor((rt * nqt + nqt - 1) / L) of row tile rt.
+These checks pin that arithmetic for any order in which the CTAs take the
+chunks: every tile pair is covered exactly once, slots are unique and in
+bounds, and the merge reads exactly the segments written for its row tile.
 """
 import random
 
 TILE = 128
+CHUNKS_PER_CTA = 16
+MIN_CHUNK = 4
+
+
+def chunk_geo(W, ctas):
+    per = CHUNKS_PER_CTA * ctas
+    L = max(MIN_CHUNK, -(-W // per))
+    return L, -(-W // L)
 
 
 def _check(n_p, n_q, ctas):
@@ -19,36 +28,33 @@ def _check(n_p, n_q, ctas):
     W = npt * nqt
     if W == 0:
         return
-    G = min(ctas, W)
+    L, NC = chunk_geo(W, ctas)
+    assert NC <= CHUNKS_PER_CTA * ctas and L > 3
     slots = {}
     covered = [0] * W
-    for b in range(G):
-        w0, w1 = b * W // G, (b + 1) * W // G
-        assert w1 - w0 >= 1
-        rt = w0 // nqt
-        for t in range(w1 - w0):
-            w = w0 + t
-            covered[w] += 1
-            assert w // nqt == rt
-            if t + 1 == w1 - w0 or (w + 1) % nqt == 0:
-                key = b + rt
-                assert key not in slots and key < ctas + npt
-                slots[key] = (b, rt)
-                rt += 1
+    for c in range(NC):  # the CTA that takes a chunk does not change what it writes
+        for o in range(L):
+            x = c * L + o
+            if x >= W:
+                break
+            covered[x] += 1
+            rt, ct = divmod(x, nqt)
+            if o == L - 1 or ct + 1 == nqt:  # segment end, as in the kernel
+                key = c + rt
+                assert key not in slots and key < CHUNKS_PER_CTA * ctas + 1 + npt
+                slots[key] = (c, rt)
     assert covered == [1] * W
     for rt in range(npt):
-        x0, x1 = rt * nqt, rt * nqt + nqt - 1
-        bf, bl = ((x0 + 1) * G - 1) // W, ((x1 + 1) * G - 1) // W
-        touched = [b for b in range(G) if max(b * W // G, x0) < min((b + 1) * W // G, x1 + 1)]
-        assert touched == list(range(bf, bl + 1))
-        assert [slots[b + rt] for b in touched] == [(b, rt) for b in touched]
+        cf, cl = rt * nqt // L, (rt * nqt + nqt - 1) // L
+        assert [slots[c + rt] for c in range(cf, cl + 1)] == [(c, rt) for c in range(cf, cl + 1)]
 
 
-def test_split_covers_every_tile_once():
+def test_chunks_cover_every_tile_once():
     cases = [(1, 1, 304), (1, 5, 304), (129, 128, 304), (4099, 3001, 304), (12778, 12776, 304),
-             (128, 121000, 304), (121000, 128, 304), (700, 1300, 152), (5, 5, 1), (0, 10, 304)]
+             (128, 121000, 304), (121000, 128, 304), (700, 1300, 152), (5, 5, 1), (0, 10, 304),
+             (300000, 300000, 304)]
     rng = random.Random(0)
     cases += [(rng.randint(1, 30000), rng.randint(1, 30000), rng.choice([1, 2, 7, 152, 304, 456]))
-              for _ in range(300)]
+              for _ in range(200)]
     for n_p, n_q, ctas in cases:
         _check(n_p, n_q, ctas)
