@@ -160,7 +160,12 @@ __global__ void __launch_bounds__(256) mask_insert(SortSides S, unsigned int* er
         const unsigned long long key = ((unsigned long long)s << kDim) | row_mask(S.desc[s] + i * kStride, v);
         if (!row_finite(v)) kmx_raise(err, KMX_DERR_RANGE);
         if (s == 1) S.colbest[i] = ~0ull;
-        const int slot = kmx_hash_insert(S.keys, S.T, key);
+        // lanes with the same key share one insert (a few masks hold most rows)
+        const unsigned same_key = __match_any_sync(__activemask(), key);
+        const int key_leader = __ffs(same_key) - 1;
+        int slot = 0;
+        if ((int)(threadIdx.x & 31) == key_leader) slot = kmx_hash_insert(S.keys, S.T, key);
+        slot = __shfl_sync(same_key, slot, key_leader);
         S.rowslot[s][i] = slot;
         if (slot < 0) {  // cannot happen at load <= 1/2; reported, never written past
             kmx_raise(err, KMX_DERR_HASHFULL);
@@ -192,24 +197,40 @@ __global__ void __launch_bounds__(256) mask_compact(SortSides S)
     }
 }
 
-// One warp per distinct mask: the rows of the smaller masks on its side (the
-// lanes stride over the compact list) give where its group starts.
+constexpr int kRankChunk = 2048;
+
+// One warp per distinct mask: the rows of the smaller masks on its side give
+// where its group starts.  The compact list is staged through shared memory
+// in chunks; the lanes of a warp stride over a chunk.
 __global__ void __launch_bounds__(256) mask_rank(SortSides S)
 {
+    __shared__ unsigned long long so[kRankChunk];
+    __shared__ int32_t sc[kRankChunk];
     const int nd = *S.n_distinct;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < nd; e += wstride) {
-        const unsigned long long me = S.dorder[e];
+    // uniform over the block so that every thread reaches the barriers
+    for (int64_t e0 = (int64_t)blockIdx.x * (blockDim.x >> 5); e0 < nd; e0 += wstride) {
+        const int64_t e = e0 + warp;
+        const unsigned long long me = e < nd ? S.dorder[e] : 0ull;
         const unsigned long long lo = me & ~((1ull << 40) - 1);  // same side, any mask
         int64_t start = 0;
-        for (int f = lane; f < nd; f += 32) {
-            const unsigned long long o = S.dorder[f];
-            if (o >= lo && o < me) start += S.dcount[f];
+        for (int f0 = 0; f0 < nd; f0 += kRankChunk) {
+            const int len = min(kRankChunk, nd - f0);
+            __syncthreads();
+            for (int f = threadIdx.x; f < len; f += blockDim.x) {
+                so[f] = S.dorder[f0 + f];
+                sc[f] = S.dcount[f0 + f];
+            }
+            __syncthreads();
+            for (int f = lane; f < len; f += 32) {
+                const unsigned long long o = so[f];
+                if (o >= lo && o < me) start += sc[f];
+            }
         }
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) start += __shfl_xor_sync(0xffffffffu, start, o);
-        if (lane == 0) S.gstart[S.distinct[e]] = start;
+        if (lane == 0 && e < nd) S.gstart[S.distinct[e]] = start;
     }
 }
 
@@ -240,8 +261,12 @@ __global__ void __launch_bounds__(256) place_pack(SortSides S)
             orig = (int32_t)slot;
             if (m) atomicOr(&S.mask[s][pos / kTile], m);
         } else {
+            // source padding rows hold +inf, so their distances are +inf (or 0
+            // in a tile pair with no dimension to visit, where the index
+            // 0xffffffff still loses every tie); target padding columns are
+            // skipped by index
 #pragma unroll
-            for (int k = 0; k < kStride; ++k) v[k] = 0.f;
+            for (int k = 0; k < kStride; ++k) v[k] = s == 0 ? INFINITY : 0.f;
             pos = slot;
             orig = -1;
         }
@@ -447,36 +472,37 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
         // the lowest original row reaching it (padding rows count as +inf),
         // then the partner half-warp, then the 8 warps through shared memory
         const int64_t rowbase = (int64_t)rt * kTile + ty * 8;
-        uint32_t ro[8];
+        uint32_t ro[8];  // padding rows: 0xffffffff (perm -1), distance +inf
 #pragma unroll
-        for (int i = 0; i < 8; ++i) ro[i] = rowbase + i < np ? (uint32_t)S.pperm[ty * 8 + i] : 0xffffffffu;
+        for (int i = 0; i < 8; ++i) ro[i] = (uint32_t)S.pperm[ty * 8 + i];
 #pragma unroll
         for (int jp = 0; jp < 4; ++jp) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                float dv[8];
+                float m = h ? acc[0][jp].y : acc[0][jp].x;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) dv[i] = ro[i] != 0xffffffffu ? (h ? acc[i][jp].y : acc[i][jp].x) : INFINITY;
-                float m = dv[0];
-#pragma unroll
-                for (int i = 1; i < 8; ++i) m = fminf(m, dv[i]);
+                for (int i = 1; i < 8; ++i) m = fminf(m, h ? acc[i][jp].y : acc[i][jp].x);
                 uint32_t r = 0xffffffffu;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) r = dv[i] == m ? min(r, ro[i]) : r;
+                for (int i = 0; i < 8; ++i) r = (h ? acc[i][jp].y : acc[i][jp].x) == m ? min(r, ro[i]) : r;
                 unsigned long long best = r == 0xffffffffu ? ~0ull : kmx::pack_dist_index(m, r);
                 const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, 16);
                 best = other < best ? other : best;
-                const int c = (jp < 2 ? 0 : 64) + tx * 4 + 2 * (jp & 1) + h;
-                if (lane < 16) S.colred[warp][c] = best;
+                // stored at (2 jp + h) * 16 + tx: lanes write consecutive words
+                if (lane < 16) S.colred[warp][(2 * jp + h) * 16 + tx] = best;
             }
         }
         __syncthreads();  // (1) all waits of this tile are behind every thread
         failed = S.failed != 0;  // uniform: S.failed is written only before (1)
         if (!failed && tid < kTile) {
-            unsigned long long best = S.colred[0][tid];
+            // column tid of the tile was stored at (2 jp + h) * 16 + tx
+            const int q = tid & 63;
+            const int jp = (tid >> 6) * 2 + ((q & 3) >> 1), h = q & 1, ctx = q >> 2;
+            const int p = (2 * jp + h) * 16 + ctx;
+            unsigned long long best = S.colred[0][p];
 #pragma unroll
             for (int v = 1; v < kThreads / 32; ++v) {
-                const unsigned long long ov = S.colred[v][tid];
+                const unsigned long long ov = S.colred[v][p];
                 best = ov < best ? ov : best;
             }
             if (col0 + tid < nq && best != ~0ull) atomicMin(&colbest[S.qperm[s][tid]], best);
