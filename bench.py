@@ -35,7 +35,7 @@ WORKLOAD = dict(name="lidar_pair_64beam_2048az_v0.3", voxel=0.3, az_bins=2048, s
 
 # DRAM bytes (read + write) of one launch, from the ncu captures summarised in
 # profiles/; an entry is removed whenever its kernel changes.
-PROFILED_TRAFFIC = {"match_tiles_fp32_bulk": 5237248}  # DRAM read+write bytes of one launch (ncu, LiDAR pair)
+PROFILED_TRAFFIC = {}  # kernel -> DRAM read+write bytes of one launch (ncu, LiDAR pair); none for the current build
 METRIC = "Faster-PFH+mutual-NN pairs/s (LiDAR scan pair, voxel 0.3 m)"
 
 
@@ -402,6 +402,27 @@ def stage_times(torch, ctx, pair, n_src, n_tgt, ps, pt, mode, flush, reps):
     return {k: float(np.mean(v)) for k, v in acc.items()}
 
 
+def executed_dims(P, Q, tile=128):
+    """Mean number of the 33 dimensions the exact matcher visits per tile
+    pair: rows grouped by nonzero mask (masks ordered with dimension 0 most
+    significant), 128-row tiles, a dimension visited when any row of either
+    tile is nonzero there.  Rows with one mask are interchangeable, so this
+    reproduces the kernel's tile masks exactly."""
+    def tile_masks(X):
+        nz = X != 0
+        bits = (nz.astype(np.uint64) << np.arange(33, dtype=np.uint64)).sum(1)
+        order_key = np.zeros(len(X), np.uint64)
+        for d in range(33):
+            order_key = (order_key << np.uint64(1)) | nz[:, d].astype(np.uint64)
+        srt = bits[np.argsort(order_key, kind="stable")]
+        n_t = (len(X) + tile - 1) // tile
+        return np.array([np.bitwise_or.reduce(srt[t * tile:(t + 1) * tile]) for t in range(n_t)], np.uint64)
+    mp, mq = tile_masks(P), tile_masks(Q)
+    pop = np.vectorize(lambda v: bin(int(v)).count("1"))
+    both = mp[:, None] | mq[None, :]
+    return float(pop(both).mean())
+
+
 def algorithmic_work(pair, ctx):
     """Counts that define the algorithmic bytes / flops of each stage."""
     out = {}
@@ -418,7 +439,9 @@ def algorithmic_work(pair, ctx):
         nJ = int(cs.out["n_valid"].item())
         out[side] = dict(n=n, sum_mF=int(mF.sum()), n_B=int(B.sum()), sum_mV_B=int(mV[B].sum()),
                          sum_mV_J=int(mV[(flags & 2) > 0].sum()), n_J=nJ, n_raw=int(cs.raw.shape[0]))
-    out["match"] = dict(np=out["src"]["n_J"], nq=out["tgt"]["n_J"])
+    out["match"] = dict(np=out["src"]["n_J"], nq=out["tgt"]["n_J"],
+                        executed_dims=executed_dims(pair.src.out["desc"][: out["src"]["n_J"], :33].cpu().numpy(),
+                                                    pair.tgt.out["desc"][: out["tgt"]["n_J"], :33].cpu().numpy()))
     return out
 
 
@@ -449,13 +472,18 @@ def roofline(stages, work, mode):
             flops = 3.0 * m["np"] * m["nq"] * 33
             achieved = flops / (match_ms / 1000.0) / 1e12
             peak = peaks["fp32_tflops"]
+            executed = achieved * m["executed_dims"] / 33.0
             return dict(kernel="match_tiles_fp32_bulk (kmx_match, FP32 exact)", bound="alu", achieved=achieved,
                         peak=peak, unit="TFLOP/s", frac=achieved / peak,
                         traffic=PROFILED_TRAFFIC.get("match_tiles_fp32_bulk"),
-                        note="3 flops (sub + fma) per descriptor element pair; duration = the whole kmx_match call "
-                             "(pack, tiles, merge, emit) from CUDA events, so the tile kernel alone runs faster; "
-                             "peak = 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived, no measured FP32 peak); "
-                             "traffic = DRAM read+write bytes of one launch from ncu "
+                        executed_dims_per_tile_pair=m["executed_dims"], executed_tflops=executed,
+                        executed_frac=executed / peak,
+                        note="achieved counts the algorithmic 3 flops (sub + fma) for all 33 values of every "
+                             "descriptor pair; the kernel skips dimensions that are zero across a whole 128 x 128 "
+                             "tile pair (exact), so it executes executed_dims_per_tile_pair / 33 of them "
+                             "(executed_tflops); duration = the whole kmx_match call (sort, pack, tiles, merge, "
+                             "emit) from CUDA events; peak = 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived, no "
+                             "measured FP32 peak); traffic = DRAM read+write bytes of one launch from ncu "
                              "(profiles/match_tiles_fp32_bulk_lidar_pair.md)")
         flops = 2.0 * m["np"] * m["nq"] * 33
         achieved = flops / (match_ms / 1000.0) / 1e12

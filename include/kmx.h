@@ -234,6 +234,33 @@ kmx_status kmx_match(kmx_ctx* ctx, const float* d_desc_p, const int32_t* d_valid
                      const int64_t* d_nq, int32_t mode, kmx_corr* d_out, int64_t cap, int64_t* d_n_out);
 
 /*
+ * Correspondence pruning of Sec. III-D, the step after matching: the ratio
+ * filter keeps the n_tau correspondences with the lowest d1 / d2 (Lowe's
+ * ratio; FP64 division, 1 when d2 = 0; ties to the lower i), the pairwise
+ * invariant of Eq. 3 joins selected correspondences k and k' when
+ * | |b_k - b_k'| - |a_k - a_k'| | <= 2 beta (norms in FP64 of the FP32 end
+ * points, as ((dx dx + dy dy) + dz dz)), and the maximum k-core of that graph
+ * holds the candidate inliers passed on to the solver (Sec. III-E).
+ *   d_corr     [corr_cap] kmx_corr as written by kmx_match; d_n_corr nullable
+ *              device count.  (i, j) index d_src4 / d_tgt4.
+ *   d_src4, d_tgt4  voxelised end points [.][4] float32 (a = source, b = target).
+ *   n_tau      1 .. 65536 (the paper uses 3000); beta > 0 (the paper: 1.5 v).
+ *   d_sel      [n_tau] int32: indices into d_corr, ascending (ratio, i).
+ *   d_n_sel    device int64: min(n_corr, n_tau).
+ *   d_core     [n_tau] int32: core number of each selected correspondence
+ *              (position p of d_sel) in the compatibility graph.
+ *   d_kmax     device int32: the largest core number (0 without edges).
+ *   d_inlier   [n_tau] int32: positions p with core number kmax, ascending.
+ *   d_n_inlier device int64: their count.
+ * The core numbers come from a cooperative launch (its blocks wait on one
+ * another through a bounded grid barrier): do not capture this call into a
+ * CUDA graph.  Device errors: KMX_ETIMEOUT if a barrier wait ran out.
+ */
+kmx_status kmx_prune(kmx_ctx* ctx, const kmx_corr* d_corr, int64_t corr_cap, const int64_t* d_n_corr,
+                     const float* d_src4, const float* d_tgt4, int32_t n_tau, double beta, int32_t* d_sel,
+                     int64_t* d_n_sel, int32_t* d_core, int32_t* d_kmax, int32_t* d_inlier, int64_t* d_n_inlier);
+
+/*
  * Exact FP32 mutual matching without any allocation (the paper has no
  * counterpart: this is a service for callers of this library).  Callers that
  * cannot allocate device memory while they match (a process whose memory

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <cmath>
 #include <new>
 
 #include "kmx_internal.cuh"
@@ -314,6 +315,25 @@ kmx_status kmx_fasterpfh(kmx_ctx* c, const kmx_grid* g, const kmx_params* p, con
                     kmx_fasterpfh_launch(c, g, p, d_normal4, d_flags, d_nbr_offs, d_nbr, d_desc, d_valid,
                                          d_n_valid, d_spfh, c->ws),
                     "kmx_fasterpfh");
+}
+
+kmx_status kmx_prune(kmx_ctx* c, const kmx_corr* d_corr, int64_t corr_cap, const int64_t* d_n_corr,
+                     const float* d_src4, const float* d_tgt4, int32_t n_tau, double beta, int32_t* d_sel,
+                     int64_t* d_n_sel, int32_t* d_core, int32_t* d_kmax, int32_t* d_inlier, int64_t* d_n_inlier)
+{
+    if (!c) return KMX_EINVAL;
+    if (corr_cap < 0 || corr_cap > INT32_MAX - 1 || (corr_cap > 0 && !d_corr) || !d_src4 || !aligned16(d_src4) ||
+        !d_tgt4 || !aligned16(d_tgt4) || n_tau < 1 || n_tau > 65536 || !(beta > 0.0) || !std::isfinite(beta) ||
+        !d_sel || !d_n_sel || !d_core || !d_kmax || !d_inlier || !d_n_inlier)
+        return fail(c, KMX_EINVAL, "kmx_prune: bad argument");
+    DeviceGuard dg(c->device);
+    kmx_status s = ensure_ws(c, kmx_prune_scratch_bytes(corr_cap, n_tau));
+    if (s) return s;
+    return launched(c,
+                    kmx_prune_launch(c, d_corr, corr_cap, d_n_corr, reinterpret_cast<const float4*>(d_src4),
+                                     reinterpret_cast<const float4*>(d_tgt4), n_tau, beta, d_sel, d_n_sel, d_core,
+                                     d_kmax, d_inlier, d_n_inlier, c->ws),
+                    "kmx_prune");
 }
 
 kmx_status kmx_match(kmx_ctx* c, const float* d_desc_p, const int32_t* d_valid_p, int64_t np_cap,

@@ -145,7 +145,7 @@ struct kmx_arena {
 
 // One-time, per-device set-up actions (function attributes): bit `bit` of a
 // per-device mask records that fn() succeeded on the current device.
-enum { kmx_attr_fp32_tiles = 0, kmx_attr_tc_topk = 1, kmx_attr_fp32_bulk = 2 };
+enum { kmx_attr_fp32_tiles = 0, kmx_attr_tc_topk = 1, kmx_attr_fp32_bulk = 2, kmx_attr_kcore = 3 };
 template <typename F>
 inline cudaError_t kmx_once_per_device(int bit, F fn)
 {
@@ -190,6 +190,13 @@ size_t kmx_fasterpfh_scratch_bytes(int64_t n_cap, bool need_spfh);
 cudaError_t kmx_fasterpfh_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_params* p, const float* normal4,
                                  uint8_t* flags, const int64_t* offs, const int32_t* nbr, float* desc,
                                  int32_t* valid, int64_t* n_valid, float* spfh, void* scratch);
+
+// prune.cu
+size_t kmx_prune_scratch_bytes(int64_t corr_cap, int32_t n_tau);
+cudaError_t kmx_prune_launch(kmx_ctx* ctx, const kmx_corr* corr, int64_t cap, const int64_t* d_n,
+                             const float4* src4, const float4* tgt4, int32_t n_tau, double beta, int32_t* sel,
+                             int64_t* n_sel, int32_t* core_out, int32_t* kmax, int32_t* inlier, int64_t* n_inlier,
+                             void* scratch);
 
 // match_fp32.cu / match_tc.cu
 size_t kmx_match_scratch_bytes(int64_t np_cap, int64_t nq_cap, int mode);

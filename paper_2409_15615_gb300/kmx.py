@@ -77,6 +77,7 @@ def library():
         "kmx_normals": (C.c_int, [vp, vp, C.POINTER(Params), vp, vp, vp, vp, i64, vp]),
         "kmx_fasterpfh": (C.c_int, [vp, vp, C.POINTER(Params), vp, vp, vp, vp, vp, vp, vp, vp]),
         "kmx_match": (C.c_int, [vp, vp, vp, i64, vp, vp, vp, i64, vp, i32, vp, i64, vp]),
+        "kmx_prune": (C.c_int, [vp, vp, i64, vp, vp, vp, i32, C.c_double, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -242,6 +243,26 @@ class Context:
                                        _ptr(valid_q), int(nq_cap), _ptr(d_nq), int(mode), _ptr(out), int(cap),
                                        _ptr(n_out)), "kmx_match")
         return out, n_out
+
+
+    def prune(self, corr, corr_cap, src4, tgt4, beta, n_tau=3000, d_n_corr=None, out=None):
+        """kmx_prune (Sec. III-D): ratio filter, pairwise-invariant graph, max
+        k-core.  Returns dict(sel, n_sel, core, kmax, inlier, n_inlier) of
+        device tensors; sel indexes the rows of ``corr``."""
+        o = out or {}
+        dev = self.device
+        r = dict(
+            sel=o.get("sel", torch.empty(n_tau, dtype=torch.int32, device=dev)),
+            n_sel=o.get("n_sel", self._scalar()),
+            core=o.get("core", torch.empty(n_tau, dtype=torch.int32, device=dev)),
+            kmax=o.get("kmax", torch.zeros(1, dtype=torch.int32, device=dev)),
+            inlier=o.get("inlier", torch.empty(n_tau, dtype=torch.int32, device=dev)),
+            n_inlier=o.get("n_inlier", self._scalar()),
+        )
+        self._check(self.lib.kmx_prune(self.h, _ptr(corr), int(corr_cap), _ptr(d_n_corr), _ptr(src4), _ptr(tgt4),
+                                       int(n_tau), float(beta), _ptr(r["sel"]), _ptr(r["n_sel"]), _ptr(r["core"]),
+                                       _ptr(r["kmax"]), _ptr(r["inlier"]), _ptr(r["n_inlier"])), "kmx_prune")
+        return r
 
 
 def launch_count() -> int:
