@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=64,
                     help="also run the serving loop with this many requests per rate (0 = skip)")
     ap.add_argument("--serve-rates", default="100,1000", help="request rates (req/s) for the serving loop")
+    ap.add_argument("--no-prune", action="store_true", help="skip timing kmx_prune (ratio filter, invariant "
+                    "graph, max k-core) on the pair's correspondences")
     return ap.parse_args()
 
 
@@ -294,6 +296,9 @@ def run_kmx(args):
         gpu_launches_per_step=launches, clocks=clk, match_mode_ms_per_step=mode_ms or None,
         cuda_graph=graph is not None,
     )
+    if not args.no_prune:
+        line["prune"] = bench_prune(torch, ctx, pair, WORKLOAD["voxel"], reps=max(5, args.steps // 4),
+                                    with_oracle=world == 1 and not args.no_cpu_baseline)
     if args.batch_pairs > 0:
         line["batched"] = bench_batched(torch, args.batch_pairs, rank)
     if args.serve_requests > 0:
@@ -328,6 +333,44 @@ def bench_batched(torch, n_pairs, rank):
                 batch_ms=sec * 1e3, pairs_per_s=n_pairs / sec, plain_pairs_per_s=n_pairs / plain_sec,
                 speedup_vs_plain=plain_sec / sec, raw_points=int(sum(len(s.src) + len(s.tgt) for s in specs)),
                 correspondences=n_corr, same_counts_as_plain=same, autotune=table)
+
+
+def bench_prune(torch, ctx, pair, voxel, reps, with_oracle):
+    """kmx_prune (Sec. III-D: ratio filter N_tau = 3000, invariant graph with
+    beta = 1.5 v, max k-core) on the pair's correspondences, resident in HBM:
+    median device time of the call (CUDA events); beside it, once, the
+    oracle's ratio filter, graph and core numbers on the same input."""
+    n_corr = int(pair.n_corr.item())
+    beta = 1.5 * voxel
+    out = ctx.prune(pair.corr, n_corr, pair.src.vox4, pair.tgt.vox4, beta)
+    ctx.sync()
+    stream = ctx.stream
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.prune(pair.corr, n_corr, pair.src.vox4, pair.tgt.vox4, beta, out=out)
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    ctx.sync()
+    res = dict(ms=float(np.median(ts)), correspondences=n_corr, selected=int(out["n_sel"].item()),
+               kmax=int(out["kmax"].item()), max_core=int(out["n_inlier"].item()), n_tau=3000, beta=beta)
+    if with_oracle:
+        from oracle import registration as reg
+
+        i, j, d1, d2 = pair.correspondences()
+        A = np.zeros(len(i), dtype=[("i", np.int64), ("j", np.int64), ("d1", np.float64), ("d2", np.float64)])
+        A["i"], A["j"], A["d1"], A["d2"] = i, j, d1, d2
+        vs = pair.src.vox4[: int(pair.src.n_vox.item())].cpu().numpy().astype(np.float64)
+        vt = pair.tgt.vox4[: int(pair.tgt.n_vox.item())].cpu().numpy().astype(np.float64)
+        t0 = time.perf_counter()
+        sel = reg.ratio_filter(A, 3000)
+        offs, adj = reg.invariant_graph(vs[sel["i"], :3], vt[sel["j"], :3], beta)
+        keep = reg.max_kcore(offs, adj)
+        res["oracle_ms"] = (time.perf_counter() - t0) * 1e3
+        res["oracle_max_core"] = int(len(keep))
+    return res
 
 
 def bench_serving(torch, n_req, rates, rank):
