@@ -244,7 +244,7 @@ kmx_status kmx_match(kmx_ctx* ctx, const float* d_desc_p, const int32_t* d_valid
  *   d_corr     [corr_cap] kmx_corr as written by kmx_match; d_n_corr nullable
  *              device count.  (i, j) index d_src4 / d_tgt4.
  *   d_src4, d_tgt4  voxelised end points [.][4] float32 (a = source, b = target).
- *   n_tau      1 .. 65536 (the paper uses 3000); beta > 0 (the paper: 1.5 v).
+ *   n_tau      1 .. 16384 (the paper uses 3000); beta > 0 (the paper: 1.5 v).
  *   d_sel      [n_tau] int32: indices into d_corr, ascending (ratio, i).
  *   d_n_sel    device int64: min(n_corr, n_tau).
  *   d_core     [n_tau] int32: core number of each selected correspondence

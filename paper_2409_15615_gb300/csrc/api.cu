@@ -323,7 +323,7 @@ kmx_status kmx_prune(kmx_ctx* c, const kmx_corr* d_corr, int64_t corr_cap, const
 {
     if (!c) return KMX_EINVAL;
     if (corr_cap < 0 || corr_cap > INT32_MAX - 1 || (corr_cap > 0 && !d_corr) || !d_src4 || !aligned16(d_src4) ||
-        !d_tgt4 || !aligned16(d_tgt4) || n_tau < 1 || n_tau > 65536 || !(beta > 0.0) || !std::isfinite(beta) ||
+        !d_tgt4 || !aligned16(d_tgt4) || n_tau < 1 || n_tau > 16384 || !(beta > 0.0) || !std::isfinite(beta) ||
         !d_sel || !d_n_sel || !d_core || !d_kmax || !d_inlier || !d_n_inlier)
         return fail(c, KMX_EINVAL, "kmx_prune: bad argument");
     DeviceGuard dg(c->device);

@@ -145,7 +145,7 @@ struct kmx_arena {
 
 // One-time, per-device set-up actions (function attributes): bit `bit` of a
 // per-device mask records that fn() succeeded on the current device.
-enum { kmx_attr_fp32_tiles = 0, kmx_attr_tc_topk = 1, kmx_attr_fp32_bulk = 2, kmx_attr_kcore = 3 };
+enum { kmx_attr_fp32_tiles = 0, kmx_attr_tc_topk = 1, kmx_attr_fp32_bulk = 2 };
 template <typename F>
 inline cudaError_t kmx_once_per_device(int bit, F fn)
 {

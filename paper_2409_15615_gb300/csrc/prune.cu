@@ -36,19 +36,22 @@ constexpr int kBuckets = 4096;
 constexpr int kThreads = 256;
 constexpr uint32_t kSpinLimit = 1u << 24;
 constexpr int kMaxSweeps = 1 << 16;
+constexpr int kHistCap = 2048;  // per-warp histogram of capped neighbour values (values below it)
 
 struct PruneScratch {
     double* ratio;            // [n_cap]
     int32_t* bucket;          // [n_cap]
     int32_t* hist;            // [kBuckets]
     int32_t* cand;            // [n_cap]
+    unsigned long long* ckey; // [n_cap] candidate ratio bits
+    int32_t* ci;              // [n_cap] candidate source index i
     int32_t* n_cand;          // [1]
     int32_t* thr;             // [1] threshold bucket
     float4* pa;               // [n_tau] source end point of each selected correspondence
     float4* pb;               // [n_tau] target end point
     uint32_t* adj;            // [n_tau][words]
     int32_t* core;            // [n_tau] working values (copied to the caller)
-    uint32_t* sync;           // [8] barrier count, barrier generation, change counters x3
+    uint32_t* sync;           // [8] barrier count, barrier generation, change counters x3, work counters x3
 };
 
 __device__ __forceinline__ int64_t corr_count(const int64_t* d_n, int64_t cap)
@@ -102,12 +105,18 @@ __global__ void __launch_bounds__(1024) ratio_threshold(int32_t n_tau, PruneScra
     }
 }
 
-__global__ void __launch_bounds__(kThreads) ratio_candidates(int64_t cap, const int64_t* d_n, PruneScratch s)
+__global__ void __launch_bounds__(kThreads) ratio_candidates(const kmx_corr* __restrict__ corr, int64_t cap,
+                                                            const int64_t* d_n, PruneScratch s)
 {
     const int64_t n = corr_count(d_n, cap);
     const int32_t thr = *s.thr;
     for (int64_t k = (int64_t)blockIdx.x * kThreads + threadIdx.x; k < n; k += (int64_t)gridDim.x * kThreads)
-        if (s.bucket[k] <= thr) s.cand[atomicAdd(s.n_cand, 1)] = (int32_t)k;
+        if (s.bucket[k] <= thr) {
+            const int c = atomicAdd(s.n_cand, 1);
+            s.cand[c] = (int32_t)k;
+            s.ckey[c] = (unsigned long long)__double_as_longlong(s.ratio[k]);
+            s.ci[c] = corr[k].i;
+        }
 }
 
 // (ratio, i) lexicographic: a non-negative double orders like its bits.
@@ -116,40 +125,25 @@ __device__ __forceinline__ bool key_less(unsigned long long ra, int32_t ia, unsi
     return ra < rb || (ra == rb && ia < ib);
 }
 
-constexpr int kRankTile = 1024;
-
+// One warp per candidate: its rank among the candidates (the lanes stride
+// over the compact keys).
 __global__ void __launch_bounds__(kThreads) ratio_rank(const kmx_corr* __restrict__ corr, int32_t n_tau,
                                                       const float4* __restrict__ src4,
                                                       const float4* __restrict__ tgt4, PruneScratch s,
                                                       int32_t* __restrict__ sel)
 {
-    __shared__ unsigned long long tr[kRankTile];
-    __shared__ int32_t ti[kRankTile];
     const int m = *s.n_cand;
-    // uniform over the block so that every thread reaches the barriers
-    for (int c0 = blockIdx.x * kThreads; c0 < m; c0 += gridDim.x * kThreads) {
-        const int c = c0 + threadIdx.x;
-        int32_t k = -1, ik = 0;
-        unsigned long long rk = 0;
-        if (c < m) {
-            k = s.cand[c];
-            rk = (unsigned long long)__double_as_longlong(s.ratio[k]);
-            ik = corr[k].i;
-        }
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (kThreads / 32);
+    for (int c = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); c < m; c += warps) {
+        const unsigned long long rk = s.ckey[c];
+        const int32_t ik = s.ci[c];
         int rank = 0;
-        for (int f0 = 0; f0 < m; f0 += kRankTile) {
-            const int len = min(kRankTile, m - f0);
-            __syncthreads();
-            for (int f = threadIdx.x; f < len; f += kThreads) {
-                const int kf = s.cand[f0 + f];
-                tr[f] = (unsigned long long)__double_as_longlong(s.ratio[kf]);
-                ti[f] = corr[kf].i;
-            }
-            __syncthreads();
-            if (k >= 0)
-                for (int f = 0; f < len; ++f) rank += key_less(tr[f], ti[f], rk, ik);
-        }
-        if (k >= 0 && rank < n_tau) {
+        for (int f = lane; f < m; f += 32) rank += key_less(s.ckey[f], s.ci[f], rk, ik);
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
+        if (lane == 0 && rank < n_tau) {
+            const int32_t k = s.cand[c];
             sel[rank] = k;
             const kmx_corr e = corr[k];
             s.pa[rank] = src4[e.i];
@@ -261,35 +255,75 @@ __global__ void __launch_bounds__(kThreads) kcore(const int64_t* d_n_sel, int32_
     const int nsel = (int)*d_n_sel;
     const uint32_t nblocks = gridDim.x;
     const int lane = threadIdx.x & 31;
-    const int warps = (int)(gridDim.x * (kThreads / 32));
-    const int gw = (int)(blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5));
     int32_t* c = s.core;
     uint32_t* bar_count = s.sync;
     uint32_t* bar_gen = s.sync + 1;
     uint32_t* changed = s.sync + 2;  // three rotating counters
-    extern __shared__ int32_t snap[];  // [nsel] values at the start of the sweep
+    // dynamic shared memory: per-warp histograms of kHistCap ints, then the
+    // snapshot of c taken at the start of each sweep
+    extern __shared__ int32_t dyn[];
+    int32_t* hist = dyn + (threadIdx.x >> 5) * kHistCap;
+    int32_t* snap = dyn + (kThreads / 32) * kHistCap;
+    uint32_t* work = s.sync + 5;  // three rotating per-sweep vertex counters
     __shared__ uint32_t block_changed;
     bool ok = true;
     for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
         if (threadIdx.x == 0) block_changed = 0;
         for (int v = threadIdx.x; v < nsel; v += kThreads) snap[v] = *reinterpret_cast<const volatile int32_t*>(&c[v]);
         __syncthreads();
-        for (int v = gw; v < nsel; v += warps) {
+        while (true) {
+            int v = 0;
+            if (lane == 0) v = (int)atomicAdd(&work[sweep % 3], 1u);
+            v = __shfl_sync(0xffffffffu, v, 0);
+            if (v >= nsel) break;
             const int cv = snap[v];
             if (cv == 0) continue;
             const uint32_t* row = s.adj + (int64_t)v * words;
             int h = cv;
             if (count_ge(row, words, snap, cv) < cv) {
-                // the largest h < cv with count_ge(h) >= h (count_ge falls as h grows)
-                int lo = 0, hi = cv - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (count_ge(row, words, snap, mid) >= mid)
-                        lo = mid;
-                    else
-                        hi = mid - 1;
+                if (cv < kHistCap) {
+                    // histogram of min(c(u), cv), then the largest h with at
+                    // least h values >= h, scanning 32 h's at a time from cv down
+                    for (int e = lane; e <= cv; e += 32) hist[e] = 0;
+                    __syncwarp();
+                    for (int w = lane; w < words; w += 32) {
+                        uint32_t bits = row[w];
+                        while (bits) {
+                            const int b = __ffs(bits) - 1;
+                            bits &= bits - 1;
+                            atomicAdd(&hist[min(snap[w * 32 + b], cv)], 1);
+                        }
+                    }
+                    __syncwarp();
+                    int suffix = 0;
+                    for (int top = cv;; top -= 32) {
+                        const int hh = top - lane;
+                        int x = hh >= 0 ? hist[hh] : 0;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int y = __shfl_up_sync(0xffffffffu, x, o);
+                            if (lane >= o) x += y;
+                        }
+                        const unsigned hit = __ballot_sync(0xffffffffu, hh >= 0 && suffix + x >= hh);
+                        if (hit) {
+                            h = top - (__ffs(hit) - 1);
+                            break;
+                        }
+                        suffix += __shfl_sync(0xffffffffu, x, 31);
+                    }
+                    __syncwarp();
+                } else {
+                    // the largest h < cv with count_ge(h) >= h (count_ge falls as h grows)
+                    int lo = 0, hi = cv - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (count_ge(row, words, snap, mid) >= mid)
+                            lo = mid;
+                        else
+                            hi = mid - 1;
+                    }
+                    h = lo;
                 }
-                h = lo;
             }
             if (h != cv) {
                 if (lane == 0) {
@@ -301,7 +335,10 @@ __global__ void __launch_bounds__(kThreads) kcore(const int64_t* d_n_sel, int32_
         __syncthreads();
         if (threadIdx.x == 0) {
             if (block_changed) atomicAdd(&changed[sweep % 3], block_changed);
-            if (blockIdx.x == 0) changed[(sweep + 1) % 3] = 0;
+            if (blockIdx.x == 0) {
+                changed[(sweep + 1) % 3] = 0;
+                work[(sweep + 1) % 3] = 0;
+            }
         }
         if (!grid_barrier(bar_count, bar_gen, nblocks)) {
             ok = false;
@@ -371,6 +408,8 @@ PruneScratch carve(void* base, int64_t cap, int32_t n_tau, size_t* total)
     s.ratio = static_cast<double*>(a.take(sizeof(double) * (cap + 1)));
     s.bucket = static_cast<int32_t*>(a.take(sizeof(int32_t) * (cap + 1)));
     s.cand = static_cast<int32_t*>(a.take(sizeof(int32_t) * (cap + 1)));
+    s.ckey = static_cast<unsigned long long*>(a.take(sizeof(unsigned long long) * (cap + 1)));
+    s.ci = static_cast<int32_t*>(a.take(sizeof(int32_t) * (cap + 1)));
     s.pa = static_cast<float4*>(a.take(sizeof(float4) * (n_tau + 1)));
     s.pb = static_cast<float4*>(a.take(sizeof(float4) * (n_tau + 1)));
     s.adj = static_cast<uint32_t*>(a.take(sizeof(uint32_t) * ((size_t)n_tau * words_for(n_tau) + 1)));
@@ -415,7 +454,7 @@ cudaError_t kmx_prune_launch(kmx_ctx* ctx, const kmx_corr* corr, int64_t cap, co
     KMX_COUNT_LAUNCH();
     ratio_threshold<<<1, 1024, 0, st>>>(n_tau, s);
     KMX_COUNT_LAUNCH();
-    ratio_candidates<<<grid, kThreads, 0, st>>>(cap, d_n, s);
+    ratio_candidates<<<grid, kThreads, 0, st>>>(corr, cap, d_n, s);
     KMX_COUNT_LAUNCH();
     ratio_rank<<<grid, kThreads, 0, st>>>(corr, n_tau, src4, tgt4, s, sel);
     const int32_t words = words_for(n_tau);
@@ -423,13 +462,12 @@ cudaError_t kmx_prune_launch(kmx_ctx* ctx, const kmx_corr* corr, int64_t cap, co
     graph_build<<<grid, kThreads, 0, st>>>(n_tau, n_sel, 2.0 * beta, s, words);
     // one CTA per SM (co-resident under a cooperative launch: the sweeps wait
     // on one another through the grid barrier)
-    const size_t snap_bytes = sizeof(int32_t) * (size_t)n_tau;
-    if (snap_bytes > 48 * 1024) {
-        if ((e = kmx_once_per_device(kmx_attr_kcore, [] {
-                 return cudaFuncSetAttribute(kcore, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-             })))
-            return e;
-    }
+    const size_t snap_bytes = sizeof(int32_t) * ((size_t)n_tau + (size_t)(kThreads / 32) * kHistCap);
+    // this call is never captured (cooperative launch), so the opt-in is set
+    // to the exact size on every call
+    if (snap_bytes > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(kcore, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)snap_bytes)))
+        return e;
     int per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kcore, kThreads, snap_bytes))) return e;
     if (per_sm < 1) return cudaErrorLaunchOutOfResources;
