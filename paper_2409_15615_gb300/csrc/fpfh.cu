@@ -221,14 +221,41 @@ __global__ void __launch_bounds__(kThreads) fpfh_kernel(int64_t n_cap, const int
         }
         unsigned bal = __ballot_sync(kFull, k >= 0);
         m += __popc(bal);
+        // neighbours in ballot order, 8 rows loaded at a time (the loads of
+        // one batch are in flight together; the sums keep their order)
         while (bal) {
-            const int src = __ffs(bal) - 1;
-            bal &= bal - 1u;
-            const int ke = __shfl_sync(kFull, k, src);
-            const float we = __shfl_sync(kFull, w, src);
-            const float* r = spfh + (int64_t)ke * kStride;
-            kahan_add(acc, comp, __ldg(&r[lane]) * we);
-            if (lane == 0) kahan_add(acc32, comp32, __ldg(&r[32]) * we);
+            constexpr int kBatch = 8;
+            int ks[kBatch];
+            float ws[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                ks[u] = -1;
+                ws[u] = 0.f;
+                if (bal) {  // warp-uniform
+                    const int src = __ffs(bal) - 1;
+                    bal &= bal - 1u;
+                    ks[u] = __shfl_sync(kFull, k, src);
+                    ws[u] = __shfl_sync(kFull, w, src);
+                }
+            }
+            float v[kBatch], v32[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                v[u] = 0.f;
+                v32[u] = 0.f;
+                if (ks[u] >= 0) {
+                    const float* r = spfh + (int64_t)ks[u] * kStride;
+                    v[u] = __ldg(&r[lane]);
+                    if (lane == 0) v32[u] = __ldg(&r[32]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                if (ks[u] >= 0) {
+                    kahan_add(acc, comp, v[u] * ws[u]);
+                    if (lane == 0) kahan_add(acc32, comp32, v32[u] * ws[u]);
+                }
+            }
         }
     }
     const float* rq = spfh + (int64_t)q * kStride;

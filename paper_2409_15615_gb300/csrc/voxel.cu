@@ -148,6 +148,27 @@ __device__ __forceinline__ void exp_range(float x, int& emin, int& emax, bool& o
     emax = max(emax, e);
 }
 
+// The FP64 sum of a voxel's members in input order: each member's rank (the
+// number of smaller member indices) places its coordinates in a per-voxel run.
+__device__ void ordered_sum(const float* __restrict__ xyz, int stride, const int32_t* m, int L, float4* run,
+                            double& sx, double& sy, double& sz)
+{
+    for (int e = 0; e < L; ++e) {
+        const int32_t me = m[e];
+        int rank = 0;
+        for (int f = 0; f < L; ++f) rank += (m[f] < me);
+        const float* p = xyz + (int64_t)me * stride;
+        run[rank] = make_float4(p[0], p[1], p[2], 0.f);
+    }
+    sx = sy = sz = 0.0;
+    for (int e = 0; e < L; ++e) {
+        const float4 p = run[e];
+        sx = __dadd_rn(sx, (double)p.x);
+        sy = __dadd_rn(sy, (double)p.y);
+        sz = __dadd_rn(sz, (double)p.z);
+    }
+}
+
 // When the exponent test passes, the exact sum is computed in integers: every
 // value is m * 2^(e - 150) with a 24-bit integer m (normal number, biased
 // exponent e), so it is the integer m << (e - emin) times 2^(emin - 150); the
@@ -171,15 +192,15 @@ __device__ __forceinline__ double scaled_sum(long long isum, int emin)
 }
 
 constexpr int kCentroidThreads = 128;  // small blocks spread a few thousand voxels over every SM
+constexpr int kBigVoxel = 32;          // members above which a whole warp sums the voxel (vox_centroid_big)
 
-// One thread per output voxel.  A first pass over the members finds each
-// axis's exponent range; if the exponent test passes, the FP64 input-order sum
-// equals the exact sum, which a second pass accumulates in 64-bit integers
-// (integer pipe; GB300's FP64 rate made the FP64 adds the bottleneck).
-// Otherwise (a voxel whose coordinates span a huge range, e.g. values near
-// zero next to larger ones) the members are summed in FP64 in input order:
-// each member's rank (the number of smaller member indices) places its
-// coordinates in a per-voxel run.
+// One thread per output voxel of at most kBigVoxel members.  A first pass
+// over the members finds each axis's exponent range; if the exponent test
+// passes, the FP64 input-order sum equals the exact sum, which a second pass
+// accumulates in 64-bit integers (integer pipe; GB300's FP64 rate made the
+// FP64 adds the bottleneck).  Otherwise (a voxel whose coordinates span a huge
+// range, e.g. values near zero next to larger ones) the members are summed in
+// FP64 in input order.
 __global__ void __launch_bounds__(kCentroidThreads) vox_centroid(const float* __restrict__ xyz, int stride,
                                                                  int64_t n, VoxScratch s,
                                                                  float4* __restrict__ out, int64_t cap)
@@ -189,6 +210,7 @@ __global__ void __launch_bounds__(kCentroidThreads) vox_centroid(const float* __
     if (o >= nv || o >= cap) return;
     const int64_t b = s.vstart[o];
     const int L = (int)(s.vstart[o + 1] - b);
+    if (L > kBigVoxel) return;  // vox_centroid_big
     const int32_t* m = s.members + b;
     int emin[3] = {255, 255, 255}, emax[3] = {0, 0, 0};
     bool odd = false;
@@ -219,24 +241,77 @@ __global__ void __launch_bounds__(kCentroidThreads) vox_centroid(const float* __
         sy = scaled_sum(iy, emin[1]);
         sz = scaled_sum(iz, emin[2]);
     } else {
-        float4* run = s.run + b;
-        for (int e = 0; e < L; ++e) {
-            const int32_t me = m[e];
-            int rank = 0;
-            for (int f = 0; f < L; ++f) rank += (m[f] < me);
-            const float* p = xyz + (int64_t)me * stride;
-            run[rank] = make_float4(p[0], p[1], p[2], 0.f);
-        }
-        for (int e = 0; e < L; ++e) {
-            const float4 p = run[e];
-            sx = __dadd_rn(sx, (double)p.x);
-            sy = __dadd_rn(sy, (double)p.y);
-            sz = __dadd_rn(sz, (double)p.z);
-        }
+        ordered_sum(xyz, stride, m, L, s.run + b, sx, sy, sz);
     }
     const double c = (double)L;
     out[o] = make_float4(__double2float_rn(__ddiv_rn(sx, c)), __double2float_rn(__ddiv_rn(sy, c)),
                          __double2float_rn(__ddiv_rn(sz, c)), 0.0f);
+}
+
+// One warp per voxel with more than kBigVoxel members (dense cells near a
+// scanner): the lanes split the members, the exponent ranges and the integer
+// sums are combined with shuffles (integer addition is exact in any order);
+// a voxel that fails the exponent test is summed in input order by lane 0.
+__global__ void __launch_bounds__(kThreads) vox_centroid_big(const float* __restrict__ xyz, int stride, int64_t n,
+                                                            VoxScratch s, float4* __restrict__ out, int64_t cap)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nv = min(s.oidx[n], cap);
+    const int64_t warps = (int64_t)gridDim.x * (kThreads / 32);
+    for (int64_t o = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5; o < nv; o += warps) {
+        const int64_t b = s.vstart[o];
+        const int L = (int)(s.vstart[o + 1] - b);
+        if (L <= kBigVoxel) continue;
+        const int32_t* m = s.members + b;
+        int emin[3] = {255, 255, 255}, emax[3] = {0, 0, 0};
+        bool odd = false;
+        for (int e = lane; e < L; e += 32) {
+            const float* p = xyz + (int64_t)__ldg(m + e) * stride;
+            exp_range(p[0], emin[0], emax[0], odd);
+            exp_range(p[1], emin[1], emax[1], odd);
+            exp_range(p[2], emin[2], emax[2], odd);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+#pragma unroll
+            for (int sh = 16; sh >= 1; sh >>= 1) {
+                emin[a] = min(emin[a], __shfl_xor_sync(0xffffffffu, emin[a], sh));
+                emax[a] = max(emax[a], __shfl_xor_sync(0xffffffffu, emax[a], sh));
+            }
+        }
+        odd = __any_sync(0xffffffffu, odd);
+        const int lg = 32 - __clz(L - 1);  // ceil(log2 L), L > 32
+        bool exact = !odd;
+        for (int a = 0; a < 3; ++a)
+            if (emax[a] >= emin[a] && emax[a] - emin[a] > 29 - lg) exact = false;
+        double sx = 0.0, sy = 0.0, sz = 0.0;
+        if (exact) {
+            long long ix = 0, iy = 0, iz = 0;
+            for (int e = lane; e < L; e += 32) {
+                const float* p = xyz + (int64_t)__ldg(m + e) * stride;
+                ix += scaled_int(p[0], emin[0]);
+                iy += scaled_int(p[1], emin[1]);
+                iz += scaled_int(p[2], emin[2]);
+            }
+#pragma unroll
+            for (int sh = 16; sh >= 1; sh >>= 1) {
+                ix += __shfl_xor_sync(0xffffffffu, ix, sh);
+                iy += __shfl_xor_sync(0xffffffffu, iy, sh);
+                iz += __shfl_xor_sync(0xffffffffu, iz, sh);
+            }
+            sx = scaled_sum(ix, emin[0]);
+            sy = scaled_sum(iy, emin[1]);
+            sz = scaled_sum(iz, emin[2]);
+        } else if (lane == 0) {
+            ordered_sum(xyz, stride, m, L, s.run + b, sx, sy, sz);
+        }
+        if (lane == 0) {
+            const double c = (double)L;
+            out[o] = make_float4(__double2float_rn(__ddiv_rn(sx, c)), __double2float_rn(__ddiv_rn(sy, c)),
+                                 __double2float_rn(__ddiv_rn(sz, c)), 0.0f);
+        }
+        __syncwarp();
+    }
 }
 
 }  // namespace
@@ -279,5 +354,8 @@ cudaError_t kmx_voxelize_launch(kmx_ctx* ctx, const float* xyz, int64_t n, int s
     KMX_COUNT_LAUNCH();
     vox_centroid<<<kmx_blocks(n, kCentroidThreads), kCentroidThreads, 0, st>>>(xyz, stride, n, s,
                                                                                     reinterpret_cast<float4*>(out4), cap);
+    KMX_COUNT_LAUNCH();
+    vox_centroid_big<<<4u * (unsigned)ctx->sm_count, kThreads, 0, st>>>(xyz, stride, n, s,
+                                                                         reinterpret_cast<float4*>(out4), cap);
     return cudaGetLastError();
 }
