@@ -21,6 +21,7 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kH = 11;
 constexpr int kD = 3 * kH;  // 33
 constexpr int kStride = KMX_DESC_STRIDE;
+static_assert(kD == KMX_DESC_DIM, "three sub-histograms of H bins");
 
 struct PfhScratch {
     int32_t* jflag;  // [n+1]
@@ -47,8 +48,8 @@ __global__ void __launch_bounds__(kThreads) valid_count(int64_t n_cap, const int
                                                         int32_t* __restrict__ jflag)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t q = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-    if (q >= kmx_count(d_n, n_cap)) return;
+    const int64_t n = kmx_count(d_n, n_cap);
+    for (int64_t q = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); q < n; q += (int64_t)gridDim.x * kWarps) {
     const uint8_t fq = flags[q];
     int mv = 0;
     if (fq & 1) {
@@ -64,6 +65,7 @@ __global__ void __launch_bounds__(kThreads) valid_count(int64_t n_cap, const int
         jflag[q] = inJ ? 1 : 0;
         flags[q] = (uint8_t)((fq & ~2u) | (inJ ? 2u : 0u));
     }
+    }
 }
 
 __global__ void __launch_bounds__(kThreads) scatter_valid(int64_t n_cap, const int64_t* d_n,
@@ -71,10 +73,10 @@ __global__ void __launch_bounds__(kThreads) scatter_valid(int64_t n_cap, const i
                                                           const int64_t* __restrict__ jpos,
                                                           int32_t* __restrict__ valid, int64_t* n_valid)
 {
-    const int64_t q = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (q == 0) *n_valid = jpos[n_cap];
-    if (q >= kmx_count(d_n, n_cap)) return;
-    if (jflag[q]) valid[jpos[q]] = (int32_t)q;
+    const int64_t n = kmx_count(d_n, n_cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *n_valid = jpos[n_cap];
+    for (int64_t q = (int64_t)blockIdx.x * kThreads + threadIdx.x; q < n; q += (int64_t)gridDim.x * kThreads)
+        if (jflag[q]) valid[jpos[q]] = (int32_t)q;
 }
 
 __device__ __forceinline__ float dot3(float ax, float ay, float az, float bx, float by, float bz)
@@ -141,14 +143,14 @@ __global__ void __launch_bounds__(kThreads) spfh_kernel(int64_t n_cap, const int
 {
     __shared__ int hist[kWarps][kStride];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t q = (int64_t)blockIdx.x * kWarps + warp;
-    if (q >= kmx_count(d_n, n_cap)) return;
+    const int64_t n = kmx_count(d_n, n_cap);
+    for (int64_t q = (int64_t)blockIdx.x * kWarps + warp; q < n; q += (int64_t)gridDim.x * kWarps) {
     float* row = spfh + q * kStride;
     const uint8_t fq = flags[q];
     if (!(fq & 1)) {
         row[lane] = 0.f;
         if (lane < kStride - 32) row[32 + lane] = 0.f;
-        return;
+        continue;
     }
     hist[warp][lane] = 0;
     if (lane < kStride - 32) hist[warp][32 + lane] = 0;
@@ -178,6 +180,8 @@ __global__ void __launch_bounds__(kThreads) spfh_kernel(int64_t n_cap, const int
     const float scale = pairs > 0 ? 100.0f / (float)pairs : 0.f;
     row[lane] = (float)hist[warp][lane] * scale;
     if (lane < kStride - 32) row[32 + lane] = lane == 0 ? (float)hist[warp][32] * scale : 0.f;
+    __syncwarp();  // the histogram is cleared for the next query
+    }
 }
 
 __device__ __forceinline__ void kahan_add(float& sum, float& comp, float term)
@@ -196,73 +200,59 @@ __global__ void __launch_bounds__(kThreads) fpfh_kernel(int64_t n_cap, const int
                                                         const int32_t* __restrict__ nbr,
                                                         const float* __restrict__ spfh, float* __restrict__ desc)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t j = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-    if (j >= min(*n_valid, n_cap)) return;
-    const int q = valid[j];
-    const float4 pq = pts[q];
-    float acc = 0.f, comp = 0.f, acc32 = 0.f, comp32 = 0.f;
-    int m = 0;
-    const int64_t b = offs[q], e = offs[q + 1];
-    for (int64_t t = b + lane; t - lane < e; t += 32) {
-        int k = -1;
-        float w = 0.f;
-        if (t < e) {
-            const int kk = nbr[t];
-            if (kk != q && (__ldg(&flags[kk]) & 1)) {
-                const float4 pk = __ldg(&pts[kk]);
-                const float dx = pk.x - pq.x, dy = pk.y - pq.y, dz = pk.z - pq.z;
-                const float d2 = dot3(dx, dy, dz, dx, dy, dz);
-                if (d2 > 0.f) {
-                    k = kk;
-                    w = 1.0f / sqrtf(d2);
+    // per warp, the valid neighbours of one 32-entry chunk of the list, in
+    // list order: their index and weight 1 / w_k
+    __shared__ int32_t sk[kWarps][32];
+    __shared__ float sw[kWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t nv = min(*n_valid, n_cap);
+    for (int64_t j = (int64_t)blockIdx.x * kWarps + warp; j < nv; j += (int64_t)gridDim.x * kWarps) {
+        const int q = valid[j];
+        const float4 pq = pts[q];
+        float acc = 0.f, comp = 0.f, acc32 = 0.f, comp32 = 0.f;
+        int m = 0;
+        const int64_t b = offs[q], e = offs[q + 1];
+        for (int64_t t = b + lane; t - lane < e; t += 32) {
+            int k = -1;
+            float w = 0.f;
+            if (t < e) {
+                const int kk = nbr[t];
+                if (kk != q && (__ldg(&flags[kk]) & 1)) {
+                    const float4 pk = __ldg(&pts[kk]);
+                    const float dx = pk.x - pq.x, dy = pk.y - pq.y, dz = pk.z - pq.z;
+                    const float d2 = dot3(dx, dy, dz, dx, dy, dz);
+                    if (d2 > 0.f) {
+                        k = kk;
+                        w = 1.0f / sqrtf(d2);
+                    }
                 }
             }
+            const unsigned bal = __ballot_sync(kFull, k >= 0);
+            const int cnt = __popc(bal);
+            if (k >= 0) {
+                const int slot = __popc(bal & ((1u << lane) - 1u));
+                sk[warp][slot] = k;
+                sw[warp][slot] = w;
+            }
+            __syncwarp();
+            m += cnt;
+            // lanes are the bins; the rows of the chunk's neighbours are added
+            // in list order, four loads in flight
+#pragma unroll 4
+            for (int i = 0; i < cnt; ++i) {
+                const float* r = spfh + (int64_t)sk[warp][i] * kStride;
+                const float we = sw[warp][i];
+                kahan_add(acc, comp, __ldg(&r[lane]) * we);
+                if (lane == 0) kahan_add(acc32, comp32, __ldg(&r[32]) * we);
+            }
+            __syncwarp();
         }
-        unsigned bal = __ballot_sync(kFull, k >= 0);
-        m += __popc(bal);
-        // neighbours in ballot order, 8 rows loaded at a time (the loads of
-        // one batch are in flight together; the sums keep their order)
-        while (bal) {
-            constexpr int kBatch = 8;
-            int ks[kBatch];
-            float ws[kBatch];
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                ks[u] = -1;
-                ws[u] = 0.f;
-                if (bal) {  // warp-uniform
-                    const int src = __ffs(bal) - 1;
-                    bal &= bal - 1u;
-                    ks[u] = __shfl_sync(kFull, k, src);
-                    ws[u] = __shfl_sync(kFull, w, src);
-                }
-            }
-            float v[kBatch], v32[kBatch];
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                v[u] = 0.f;
-                v32[u] = 0.f;
-                if (ks[u] >= 0) {
-                    const float* r = spfh + (int64_t)ks[u] * kStride;
-                    v[u] = __ldg(&r[lane]);
-                    if (lane == 0) v32[u] = __ldg(&r[32]);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                if (ks[u] >= 0) {
-                    kahan_add(acc, comp, v[u] * ws[u]);
-                    if (lane == 0) kahan_add(acc32, comp32, v32[u] * ws[u]);
-                }
-            }
-        }
+        const float* rq = spfh + (int64_t)q * kStride;
+        const float invm = m > 0 ? 1.0f / (float)m : 0.f;
+        float* out = desc + j * kStride;
+        out[lane] = rq[lane] + acc * invm;
+        if (lane < kStride - 32) out[32 + lane] = lane == 0 ? rq[32] + acc32 * invm : 0.f;
     }
-    const float* rq = spfh + (int64_t)q * kStride;
-    const float invm = m > 0 ? 1.0f / (float)m : 0.f;
-    float* out = desc + j * kStride;
-    out[lane] = rq[lane] + acc * invm;
-    if (lane < kStride - 32) out[32 + lane] = lane == 0 ? rq[32] + acc32 * invm : 0.f;
 }
 
 }  // namespace
@@ -283,14 +273,16 @@ cudaError_t kmx_fasterpfh_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_para
     PfhScratch s = carve(scratch, g->n_cap, spfh == nullptr, &total);
     float* sp = spfh ? spfh : s.spfh;
     const int64_t n = g->n_cap;
-    cudaError_t e;
-    if ((e = cudaMemsetAsync(s.jflag, 0, sizeof(int32_t) * (n + 1), st))) return e;
-    const unsigned nbw = kmx_blocks(n, kWarps);
+    cudaError_t e = cudaSuccess;
+    // valid_count writes the flag of every point below the count; the scan
+    // reads no other entry
+    const unsigned nbw = kmx_stride_blocks(n, kWarps, ctx->sm_count);
     KMX_COUNT_LAUNCH();
     valid_count<<<nbw, kThreads, 0, st>>>(n, g->d_n, flags, offs, nbr, prm->tau_num, s.jflag);
     if ((e = kmx_scan_i32(s.jflag, n, g->d_n, s.jpos, s.scan, st, ctx->d_err))) return e;
     KMX_COUNT_LAUNCH();
-    scatter_valid<<<kmx_blocks(n, kThreads), kThreads, 0, st>>>(n, g->d_n, s.jflag, s.jpos, valid, n_valid);
+    scatter_valid<<<kmx_stride_blocks(n, kThreads, ctx->sm_count), kThreads, 0, st>>>(n, g->d_n, s.jflag, s.jpos,
+                                                                                       valid, n_valid);
     KMX_COUNT_LAUNCH();
     spfh_kernel<<<nbw, kThreads, 0, st>>>(n, g->d_n, g->pts, reinterpret_cast<const float4*>(normal4), flags,
                                           offs, nbr, sp);

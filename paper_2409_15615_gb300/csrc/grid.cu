@@ -37,24 +37,25 @@ __global__ void __launch_bounds__(kThreads) grid_insert(const float4* __restrict
                                                         unsigned long long* keys, uint32_t T, GridScratch s,
                                                         unsigned int* err)
 {
-    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (i >= kmx_count(d_n, n_cap)) return;
-    float4 p = pts[i];
-    int cx, cy, cz;
-    bool ok = kmx_cell_index(p.x, inv_cell, &cx) & kmx_cell_index(p.y, inv_cell, &cy) &
-              kmx_cell_index(p.z, inv_cell, &cz);
-    if (!ok) {
-        kmx_raise(err, KMX_DERR_RANGE);
-        s.pslot[i] = -1;
-        return;
+    const int64_t n = kmx_count(d_n, n_cap);
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        float4 p = pts[i];
+        int cx, cy, cz;
+        bool ok = kmx_cell_index(p.x, inv_cell, &cx) & kmx_cell_index(p.y, inv_cell, &cy) &
+                  kmx_cell_index(p.z, inv_cell, &cz);
+        if (!ok) {
+            kmx_raise(err, KMX_DERR_RANGE);
+            s.pslot[i] = -1;
+            continue;
+        }
+        int slot = kmx_hash_insert(keys, T, kmx_pack_key(cx, cy, cz));
+        s.pslot[i] = slot;
+        if (slot < 0) {
+            kmx_raise(err, KMX_DERR_HASHFULL);
+            continue;
+        }
+        atomicAdd(&s.cnt[slot], 1);
     }
-    int slot = kmx_hash_insert(keys, T, kmx_pack_key(cx, cy, cz));
-    s.pslot[i] = slot;
-    if (slot < 0) {
-        kmx_raise(err, KMX_DERR_HASHFULL);
-        return;
-    }
-    atomicAdd(&s.cnt[slot], 1);
 }
 
 __global__ void __launch_bounds__(kThreads) grid_cells(uint32_t T, GridScratch s, int2* __restrict__ cells,
@@ -68,12 +69,13 @@ __global__ void __launch_bounds__(kThreads) grid_cells(uint32_t T, GridScratch s
 
 __global__ void __launch_bounds__(kThreads) grid_scatter(int64_t n_cap, const int64_t* d_n, GridScratch s)
 {
-    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (i >= kmx_count(d_n, n_cap)) return;
-    int slot = s.pslot[i];
-    if (slot < 0) return;
-    int pos = atomicAdd(&s.cursor[slot], 1);
-    s.tmp[s.start[slot] + pos] = (int32_t)i;
+    const int64_t n = kmx_count(d_n, n_cap);
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        const int slot = s.pslot[i];
+        if (slot < 0) continue;
+        const int pos = atomicAdd(&s.cursor[slot], 1);
+        s.tmp[s.start[slot] + pos] = (int32_t)i;
+    }
 }
 
 // One thread per point: its rank in the cell (the number of smaller point
@@ -82,17 +84,18 @@ __global__ void __launch_bounds__(kThreads) grid_scatter(int64_t n_cap, const in
 __global__ void __launch_bounds__(kThreads) grid_fill(const float4* __restrict__ pts, int64_t n_cap,
                                                       const int64_t* d_n, GridScratch s, float4* __restrict__ sorted)
 {
-    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (i >= kmx_count(d_n, n_cap)) return;
-    const int slot = s.pslot[i];
-    if (slot < 0) return;
-    const int L = s.cnt[slot];
-    const int64_t b = s.start[slot];
-    const int32_t* seg = s.tmp + b;
-    int rank = 0;
-    for (int f = 0; f < L; ++f) rank += (seg[f] < (int32_t)i);
-    const float4 p = pts[i];
-    sorted[b + rank] = make_float4(p.x, p.y, p.z, __int_as_float((int32_t)i));
+    const int64_t n = kmx_count(d_n, n_cap);
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        const int slot = s.pslot[i];
+        if (slot < 0) continue;
+        const int L = s.cnt[slot];
+        const int64_t b = s.start[slot];
+        const int32_t* seg = s.tmp + b;
+        int rank = 0;
+        for (int f = 0; f < L; ++f) rank += (seg[f] < (int32_t)i);
+        const float4 p = pts[i];
+        sorted[b + rank] = make_float4(p.x, p.y, p.z, __int_as_float((int32_t)i));
+    }
 }
 
 }  // namespace
@@ -129,7 +132,7 @@ cudaError_t kmx_grid_build_launch(kmx_ctx* ctx, kmx_grid* g, void* scratch)
     if ((e = cudaMemsetAsync(s.cnt, 0, sizeof(int32_t) * T, st))) return e;
     if ((e = cudaMemsetAsync(s.cursor, 0, sizeof(int32_t) * T, st))) return e;
     g->inv_cell = 1.0 / ((double)g->cell * (1.0 + KMX_CELL_MARGIN));
-    unsigned nb = kmx_blocks(g->n_cap, kThreads);
+    const unsigned nb = kmx_stride_blocks(g->n_cap, kThreads, ctx->sm_count);
     KMX_COUNT_LAUNCH();
     grid_insert<<<nb, kThreads, 0, st>>>(g->pts, g->n_cap, g->d_n, g->inv_cell, g->keys, T, s, ctx->d_err);
     if ((e = kmx_scan_i32(s.cnt, T, nullptr, s.start, s.scan, st, ctx->d_err))) return e;

@@ -129,6 +129,16 @@ static inline unsigned int kmx_blocks(int64_t n, int threads)
 
 static inline size_t kmx_align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Blocks for a grid-stride kernel over at most `cap_items` items of which only
+// a device-side count are real: enough for the capacity, but never more than
+// `per_sm` resident blocks per SM (the rest would only be scheduled to exit).
+static inline unsigned int kmx_stride_blocks(int64_t cap_items, int items_per_block, int sm_count, int per_sm = 8)
+{
+    const unsigned int b = kmx_blocks(cap_items, items_per_block);
+    const unsigned int lim = (unsigned int)(per_sm * (sm_count > 0 ? sm_count : 1));
+    return b < lim ? b : lim;
+}
+
 // Bump allocator over the context scratch.  With base == nullptr it only
 // measures (every pointer it returns is null and `used` is the total).
 struct kmx_arena {

@@ -34,22 +34,24 @@ __global__ void __launch_bounds__(kThreads) emit(int64_t np_cap, const int64_t* 
                                                  kmx_corr* __restrict__ out, int64_t cap, int64_t* n_out,
                                                  unsigned int* err)
 {
-    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (i == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         const int64_t tot = mpos[np_cap];
         *n_out = tot;
         if (tot > cap) kmx_raise(err, KMX_DERR_CAPACITY);
     }
-    if (i >= kmx_count(d_np, np_cap) || !mflag[i]) return;
-    const int64_t p = mpos[i];
-    if (p >= cap) return;
-    const RowBest r = merged[i];
-    kmx_corr c;
-    c.i = vp ? vp[i] : (int32_t)i;
-    c.j = vq ? vq[r.j1] : r.j1;
-    c.d1 = sqrtf(r.d1);
-    c.d2 = sqrtf(r.d2);
-    out[p] = c;
+    const int64_t n = kmx_count(d_np, np_cap);
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        if (!mflag[i]) continue;
+        const int64_t p = mpos[i];
+        if (p >= cap) continue;
+        const RowBest r = merged[i];
+        kmx_corr c;
+        c.i = vp ? vp[i] : (int32_t)i;
+        c.j = vq ? vq[r.j1] : r.j1;
+        c.d1 = sqrtf(r.d1);
+        c.d2 = sqrtf(r.d2);
+        out[p] = c;
+    }
 }
 
 }  // namespace
@@ -104,8 +106,9 @@ cudaError_t match_emit(kmx_ctx* ctx, const MatchScratch& s, int64_t np_cap, cons
     cudaError_t e;
     if ((e = kmx_scan_i32(s.mflag, np_cap, d_np, s.mpos, s.scan, st, ctx->d_err))) return e;
     KMX_COUNT_LAUNCH();
-    emit<<<kmx_blocks(np_cap, kThreads), kThreads, 0, st>>>(np_cap, d_np, s.merged, s.mflag, s.mpos, vp, vq, out,
-                                                            cap, n_out, ctx->d_err);
+    emit<<<kmx_stride_blocks(np_cap, kThreads, ctx->sm_count), kThreads, 0, st>>>(np_cap, d_np, s.merged, s.mflag,
+                                                                                   s.mpos, vp, vq, out, cap, n_out,
+                                                                                   ctx->d_err);
     return cudaGetLastError();
 }
 

@@ -586,12 +586,11 @@ __global__ void __launch_bounds__(256) merge_segments(const kmx::RowBest* __rest
                                                       const unsigned long long* __restrict__ colbest,
                                                       kmx::RowBest* __restrict__ merged, int32_t* __restrict__ mflag)
 {
-    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
     const int64_t np = kmx_count(d_np, np_cap), nq = kmx_count(d_nq, nq_cap);
-    if (i >= np) return;
     const int64_t npt = tiles_of(np);
     const int64_t nqt = tiles_of(nq);
     const int64_t W = npt * nqt;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < np; i += (int64_t)gridDim.x * 256) {
     kmx::RowBest r{INFINITY, 0x7fffffff, INFINITY};
     if (W > 0) {
         const ChunkGeo cg = chunk_geo(W, ctas);
@@ -608,6 +607,7 @@ __global__ void __launch_bounds__(256) merge_segments(const kmx::RowBest* __rest
     bool mutual = false;
     if (r.j1 >= 0 && r.j1 != 0x7fffffff) mutual = (uint32_t)(colbest[r.j1] & 0xffffffffull) == (uint32_t)orig;
     mflag[orig] = mutual ? 1 : 0;
+    }
 }
 
 struct BulkScratch {
@@ -712,8 +712,8 @@ cudaError_t kmx_match_fp32_bulk_launch(kmx_ctx* ctx, const float* dp, const int3
         static_cast<const float*>(b.sort.packed[1]), b.sort.perm[1], b.sort.mask[1], nq_cap, d_nq, ctas,
         b.chunk_counter, b.seg, s.colbest, ctx->d_err);
     KMX_COUNT_LAUNCH();
-    merge_segments<<<kmx_blocks(np_cap, 256), 256, 0, st>>>(b.seg, b.sort.perm[0], ctas, np_cap, d_np, nq_cap, d_nq,
-                                                            s.colbest, s.merged, s.mflag);
+    merge_segments<<<kmx_stride_blocks(np_cap, 256, ctx->sm_count), 256, 0, st>>>(
+        b.seg, b.sort.perm[0], ctas, np_cap, d_np, nq_cap, d_nq, s.colbest, s.merged, s.mflag);
     if ((e = cudaGetLastError())) return e;
     return kmx::match_emit(ctx, s, np_cap, d_np, vp, vq, out, cap, n_out);
 }

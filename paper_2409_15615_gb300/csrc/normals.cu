@@ -125,8 +125,8 @@ __device__ __forceinline__ float warp_sum(float v)
 __global__ void __launch_bounds__(kThreads) search_count(GridView g, Radii R, NormScratch s)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t p = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-    if (p >= *g.n_sorted) return;
+    const int64_t n_sorted = *g.n_sorted;
+    for (int64_t p = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); p < n_sorted; p += (int64_t)gridDim.x * kWarps) {
     const float4 q = g.sorted[p];
     const int qi = __float_as_int(q.w);
     int start, excl;
@@ -162,6 +162,7 @@ __global__ void __launch_bounds__(kThreads) search_count(GridView g, Radii R, No
         s.cnt[qi] = nf;
         const float inv = nn > 0 ? 1.0f / (float)nn : 0.0f;
         s.mean[qi] = make_float4(sx * inv, sy * inv, sz * inv, __int_as_float(nn));
+    }
     }
 }
 
@@ -262,9 +263,11 @@ __global__ void __launch_bounds__(kThreads) search_fill(GridView g, Radii R, Nor
     }
     const bool write = o.nbr && total_list <= o.nbr_cap;
     const int64_t n_sorted = *g.n_sorted;
+    // uniform over the block: every thread reaches the barriers
+    for (int64_t chunk = blockIdx.x; chunk * kQPerBlock < n_sorted; chunk += gridDim.x) {
     for (int k = 0; k < kQPerWarp; ++k) {
         const int slot = warp * kQPerWarp + k;
-        const int64_t p = (int64_t)blockIdx.x * kQPerBlock + slot;
+        const int64_t p = chunk * kQPerBlock + slot;
         if (p >= n_sorted) {
             if (lane == 0) sm_qi[slot] = -1;
             continue;
@@ -336,9 +339,8 @@ __global__ void __launch_bounds__(kThreads) search_fill(GridView g, Radii R, Nor
         }
     }
     __syncthreads();
-    if (warp != 0) return;
+    if (warp == 0 && sm_qi[lane] >= 0) {
     const int qi = sm_qi[lane];
-    if (qi < 0) return;
     const int nN = sm_nN[lane];
     const int mF = (int)(o.offs[qi + 1] - o.offs[qi]);
     uint8_t flag = 0;
@@ -367,12 +369,17 @@ __global__ void __launch_bounds__(kThreads) search_fill(GridView g, Radii R, Nor
     }
     o.normal4[qi] = nout;
     o.flags[qi] = flag;
+    }
+    __syncthreads();  // the shared moments are rewritten by the next chunk
+    }
 }
 
-__global__ void clear_counts(int32_t* cnt, int64_t n)
+// |I(q)| of points that a range error kept out of the grid stays 0.
+__global__ void clear_counts(int32_t* cnt, const int64_t* d_n, int64_t n_cap)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i <= n) cnt[i] = 0;
+    const int64_t n = kmx_count(d_n, n_cap);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        cnt[i] = 0;
 }
 
 }  // namespace
@@ -403,13 +410,13 @@ cudaError_t kmx_normals_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_params
     if ((e = cudaMemsetAsync(normal4, 0, sizeof(float4) * n, st))) return e;
     if ((e = cudaMemsetAsync(flags, 0, n, st))) return e;
     KMX_COUNT_LAUNCH();
-    clear_counts<<<kmx_blocks(n + 1, 256), 256, 0, st>>>(s.cnt, n);
+    clear_counts<<<kmx_stride_blocks(n, 256, ctx->sm_count), 256, 0, st>>>(s.cnt, g->d_n, n);
     KMX_COUNT_LAUNCH();
-    search_count<<<kmx_blocks(n, kWarps), kThreads, 0, st>>>(gv, R, s);
+    search_count<<<kmx_stride_blocks(n, kWarps, ctx->sm_count), kThreads, 0, st>>>(gv, R, s);
     if ((e = kmx_scan_i32(s.cnt, n, g->d_n, offs, s.scan, st, ctx->d_err))) return e;
     NormOut o{reinterpret_cast<float4*>(normal4), flags, offs, nbr, nbr_cap, n, needed, prm->tau_num,
               prm->tau_lin, {prm->viewpoint[0], prm->viewpoint[1], prm->viewpoint[2]}};
     KMX_COUNT_LAUNCH();
-    search_fill<<<kmx_blocks(n, kQPerBlock), kThreads, 0, st>>>(gv, R, s, o, ctx->d_err);
+    search_fill<<<kmx_stride_blocks(n, kQPerBlock, ctx->sm_count), kThreads, 0, st>>>(gv, R, s, o, ctx->d_err);
     return cudaGetLastError();
 }
