@@ -261,6 +261,29 @@ kmx_status kmx_prune(kmx_ctx* ctx, const kmx_corr* d_corr, int64_t corr_cap, con
                      int64_t* d_n_sel, int32_t* d_core, int32_t* d_kmax, int32_t* d_inlier, int64_t* d_n_inlier);
 
 /*
+ * Robust pose (Sec. III-E): GNC with the truncated-least-squares loss (the
+ * paper's solver, Yang et al. 2020) on the correspondences of the maximum
+ * k-core, around a weighted rigid alignment (Horn's unit-quaternion closed
+ * form).  Point k < *d_n_inlier is a_k = d_src4[c.i], b_k = d_tgt4[c.j] with
+ * c = d_corr[d_sel[d_inlier[k]]] (the outputs of kmx_prune).
+ *   noise_bound  c of the TLS loss (the paper: beta); max_iters (100),
+ *              mu_factor (1.4) and tol (1e-12, on the weighted cost) set the
+ *              GNC schedule.
+ *   d_R        [9] float64, row-major, and d_t [3] float64: b ~ R a + t.
+ *   d_w        [inlier_cap] float32: the final weight of each point.
+ *   d_stats    [4] int32: iterations, points with weight > 0.5, points,
+ *              status (0, or 1 with fewer than 3 points: R = I, t = 0).
+ * inlier_cap <= 4096 (one block holds the points); more points on the device
+ * raise KMX_ECAPACITY.  Residuals and moments are FP32 on coordinates centred
+ * on their FP64 centroids, so the pose agrees with an FP64 solver to about
+ * 1e-5 relative.
+ */
+kmx_status kmx_gnc(kmx_ctx* ctx, const kmx_corr* d_corr, const int32_t* d_sel, const int32_t* d_inlier,
+                   const int64_t* d_n_inlier, int64_t inlier_cap, const float* d_src4, const float* d_tgt4,
+                   double noise_bound, int32_t max_iters, double mu_factor, double tol, double* d_R, double* d_t,
+                   float* d_w, int32_t* d_stats);
+
+/*
  * Exact FP32 mutual matching without any allocation (the paper has no
  * counterpart: this is a service for callers of this library).  Callers that
  * cannot allocate device memory while they match (a process whose memory

@@ -336,6 +336,25 @@ kmx_status kmx_prune(kmx_ctx* c, const kmx_corr* d_corr, int64_t corr_cap, const
                     "kmx_prune");
 }
 
+kmx_status kmx_gnc(kmx_ctx* c, const kmx_corr* d_corr, const int32_t* d_sel, const int32_t* d_inlier,
+                   const int64_t* d_n_inlier, int64_t inlier_cap, const float* d_src4, const float* d_tgt4,
+                   double noise_bound, int32_t max_iters, double mu_factor, double tol, double* d_R, double* d_t,
+                   float* d_w, int32_t* d_stats)
+{
+    if (!c) return KMX_EINVAL;
+    if (!d_corr || !d_sel || !d_inlier || inlier_cap < 0 || inlier_cap > kmx_gnc_max_points() || !d_src4 ||
+        !aligned16(d_src4) || !d_tgt4 || !aligned16(d_tgt4) || !(noise_bound > 0.0) || !std::isfinite(noise_bound) ||
+        max_iters < 0 || !(mu_factor > 1.0) || !std::isfinite(mu_factor) || !(tol >= 0.0) || !d_R || !d_t ||
+        (inlier_cap > 0 && !d_w) || !d_stats)
+        return fail(c, KMX_EINVAL, "kmx_gnc: bad argument");
+    DeviceGuard dg(c->device);
+    return launched(c,
+                    kmx_gnc_launch(c, d_corr, d_sel, d_inlier, d_n_inlier, inlier_cap,
+                                   reinterpret_cast<const float4*>(d_src4), reinterpret_cast<const float4*>(d_tgt4),
+                                   noise_bound, max_iters, mu_factor, tol, d_R, d_t, d_w, d_stats),
+                    "kmx_gnc");
+}
+
 kmx_status kmx_match(kmx_ctx* c, const float* d_desc_p, const int32_t* d_valid_p, int64_t np_cap,
                      const int64_t* d_np, const float* d_desc_q, const int32_t* d_valid_q, int64_t nq_cap,
                      const int64_t* d_nq, int32_t mode, kmx_corr* d_out, int64_t cap, int64_t* d_n_out)

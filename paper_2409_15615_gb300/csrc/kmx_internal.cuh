@@ -208,6 +208,13 @@ cudaError_t kmx_prune_launch(kmx_ctx* ctx, const kmx_corr* corr, int64_t cap, co
                              int64_t* n_sel, int32_t* core_out, int32_t* kmax, int32_t* inlier, int64_t* n_inlier,
                              void* scratch);
 
+// gnc.cu
+int64_t kmx_gnc_max_points();
+cudaError_t kmx_gnc_launch(kmx_ctx* ctx, const kmx_corr* corr, const int32_t* sel, const int32_t* inlier,
+                           const int64_t* d_n, int64_t cap, const float4* src4, const float4* tgt4, double noise_bound,
+                           int max_iters, double mu_factor, double tol, double* R, double* t, float* w,
+                           int32_t* stats);
+
 // match_fp32.cu / match_tc.cu
 size_t kmx_match_scratch_bytes(int64_t np_cap, int64_t nq_cap, int mode);
 cudaError_t kmx_match_launch(kmx_ctx* ctx, const float* dp, const int32_t* vp, int64_t np_cap,

@@ -78,6 +78,8 @@ def library():
         "kmx_fasterpfh": (C.c_int, [vp, vp, C.POINTER(Params), vp, vp, vp, vp, vp, vp, vp, vp]),
         "kmx_match": (C.c_int, [vp, vp, vp, i64, vp, vp, vp, i64, vp, i32, vp, i64, vp]),
         "kmx_prune": (C.c_int, [vp, vp, i64, vp, vp, vp, i32, C.c_double, vp, vp, vp, vp, vp, vp]),
+        "kmx_gnc": (C.c_int, [vp, vp, vp, vp, vp, i64, vp, vp, C.c_double, i32, C.c_double, C.c_double, vp, vp,
+                              vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -262,6 +264,27 @@ class Context:
         self._check(self.lib.kmx_prune(self.h, _ptr(corr), int(corr_cap), _ptr(d_n_corr), _ptr(src4), _ptr(tgt4),
                                        int(n_tau), float(beta), _ptr(r["sel"]), _ptr(r["n_sel"]), _ptr(r["core"]),
                                        _ptr(r["kmax"]), _ptr(r["inlier"]), _ptr(r["n_inlier"])), "kmx_prune")
+        return r
+
+
+    def gnc(self, corr, pruned, src4, tgt4, noise_bound, inlier_cap=None, max_iters=100, mu_factor=1.4,
+            tol=1e-12, out=None):
+        """kmx_gnc (Sec. III-E) on the maximum k-core of ``pruned`` (the dict
+        kmx_prune / Context.prune returns).  Returns dict(R [9] f64, t [3] f64,
+        w, stats [4] int32) of device tensors."""
+        o = out or {}
+        cap = int(pruned["inlier"].shape[0]) if inlier_cap is None else int(inlier_cap)
+        dev = self.device
+        r = dict(
+            R=o.get("R", torch.zeros(9, dtype=torch.float64, device=dev)),
+            t=o.get("t", torch.zeros(3, dtype=torch.float64, device=dev)),
+            w=o.get("w", torch.zeros(max(cap, 1), dtype=torch.float32, device=dev)),
+            stats=o.get("stats", torch.zeros(4, dtype=torch.int32, device=dev)),
+        )
+        self._check(self.lib.kmx_gnc(self.h, _ptr(corr), _ptr(pruned["sel"]), _ptr(pruned["inlier"]),
+                                     _ptr(pruned["n_inlier"]), cap, _ptr(src4), _ptr(tgt4), float(noise_bound),
+                                     int(max_iters), float(mu_factor), float(tol), _ptr(r["R"]), _ptr(r["t"]),
+                                     _ptr(r["w"]), _ptr(r["stats"])), "kmx_gnc")
         return r
 
 
