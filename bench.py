@@ -54,8 +54,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=64,
                     help="also run the serving loop with this many requests per rate (0 = skip)")
     ap.add_argument("--serve-rates", default="100,1000", help="request rates (req/s) for the serving loop")
-    ap.add_argument("--no-prune", action="store_true", help="skip timing kmx_prune (ratio filter, invariant "
-                    "graph, max k-core) on the pair's correspondences")
+    ap.add_argument("--no-register", action="store_true", help="skip timing kmx_prune + kmx_gnc (ratio filter, "
+                    "invariant graph, max k-core, GNC-TLS pose) on the pair's correspondences")
     return ap.parse_args()
 
 
@@ -69,7 +69,7 @@ def make_pair(rank):
     from paper_2409_15615_gb300 import replicas
 
     src, tgt, R, t, vps, vpt = lidar_pair(replicas.pair_seed(WORKLOAD["seed"], rank), az_bins=WORKLOAD["az_bins"])
-    return src, tgt, vps, vpt
+    return src, tgt, vps, vpt, R, t
 
 
 # ----------------------------------------------------------------------------
@@ -108,7 +108,7 @@ def run_reference(args):
     from oracle import build as ob
 
     ob.build()
-    src, tgt, vps, vpt = make_pair(0)
+    src, tgt, vps, vpt, _, _ = make_pair(0)
     for _ in range(min(args.warmup, 1)):
         oracle_pair_seconds(src, tgt, vps, vpt)
     times = [oracle_pair_seconds(src, tgt, vps, vpt) for _ in range(args.steps)]
@@ -192,7 +192,7 @@ def run_kmx(args):
     from paper_2409_15615_gb300 import kmx, pipeline
 
     mode = kmx.MATCH_BF16_RERANK if args.match == "bf16" else kmx.MATCH_FP32_EXACT
-    src, tgt, vps, vpt = make_pair(rank)
+    src, tgt, vps, vpt, R_gt, t_gt = make_pair(rank)
     v = WORKLOAD["voxel"]
     ps = kmx.params_default(v, viewpoint=np.float32(vps).tolist())
     pt = kmx.params_default(v, viewpoint=np.float32(vpt).tolist())
@@ -296,9 +296,10 @@ def run_kmx(args):
         gpu_launches_per_step=launches, clocks=clk, match_mode_ms_per_step=mode_ms or None,
         cuda_graph=graph is not None,
     )
-    if not args.no_prune:
-        line["prune"] = bench_prune(torch, ctx, pair, WORKLOAD["voxel"], reps=max(5, args.steps // 4),
-                                    with_oracle=world == 1 and not args.no_cpu_baseline)
+    if not args.no_register:
+        line["register"] = bench_register(torch, ctx, pair, WORKLOAD["voxel"], R_gt, t_gt,
+                                          reps=max(5, args.steps // 4),
+                                          with_oracle=world == 1 and not args.no_cpu_baseline)
     if args.batch_pairs > 0:
         line["batched"] = bench_batched(torch, args.batch_pairs, rank)
     if args.serve_requests > 0:
@@ -335,30 +336,43 @@ def bench_batched(torch, n_pairs, rank):
                 correspondences=n_corr, same_counts_as_plain=same, autotune=table)
 
 
-def bench_prune(torch, ctx, pair, voxel, reps, with_oracle):
-    """kmx_prune (Sec. III-D: ratio filter N_tau = 3000, invariant graph with
-    beta = 1.5 v, max k-core) on the pair's correspondences, resident in HBM:
-    median device time of the call (CUDA events); beside it, once, the
-    oracle's ratio filter, graph and core numbers on the same input."""
+def bench_register(torch, ctx, pair, voxel, R_gt, t_gt, reps, with_oracle):
+    """Registration after matching, on the device: kmx_prune (Sec. III-D:
+    ratio filter N_tau = 3000, invariant graph with beta = 1.5 v, max k-core)
+    then kmx_gnc (Sec. III-E: GNC-TLS), on the pair's correspondences resident
+    in HBM.  Median device time of each call and of both (CUDA events), the
+    pose errors against the generator's ground truth, and beside it, once,
+    the oracle's same two stages on the same input."""
+    from oracle import registration as reg
+
     n_corr = int(pair.n_corr.item())
     beta = 1.5 * voxel
-    out = ctx.prune(pair.corr, n_corr, pair.src.vox4, pair.tgt.vox4, beta)
+    pr = ctx.prune(pair.corr, n_corr, pair.src.vox4, pair.tgt.vox4, beta)
+    g = ctx.gnc(pair.corr, pr, pair.src.vox4, pair.tgt.vox4, beta)
     ctx.sync()
     stream = ctx.stream
-    ts = []
+    t_prune, t_gnc = [], []
     for _ in range(reps):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        ctx.prune(pair.corr, n_corr, pair.src.vox4, pair.tgt.vox4, beta, out=out)
-        b.record(stream)
-        b.synchronize()
-        ts.append(a.elapsed_time(b))
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        ctx.prune(pair.corr, n_corr, pair.src.vox4, pair.tgt.vox4, beta, out=pr)
+        e[1].record(stream)
+        ctx.gnc(pair.corr, pr, pair.src.vox4, pair.tgt.vox4, beta, out=g)
+        e[2].record(stream)
+        e[2].synchronize()
+        t_prune.append(e[0].elapsed_time(e[1]))
+        t_gnc.append(e[1].elapsed_time(e[2]))
     ctx.sync()
-    res = dict(ms=float(np.median(ts)), correspondences=n_corr, selected=int(out["n_sel"].item()),
-               kmax=int(out["kmax"].item()), max_core=int(out["n_inlier"].item()), n_tau=3000, beta=beta)
+    R = g["R"].cpu().numpy().reshape(3, 3)
+    t = g["t"].cpu().numpy()
+    rot, tr = reg.pose_errors(R, t, R_gt, t_gt)
+    st = g["stats"].cpu().numpy()
+    res = dict(prune_ms=float(np.median(t_prune)), gnc_ms=float(np.median(t_gnc)),
+               ms=float(np.median(np.add(t_prune, t_gnc))), correspondences=n_corr,
+               selected=int(pr["n_sel"].item()), kmax=int(pr["kmax"].item()), max_core=int(pr["n_inlier"].item()),
+               gnc_iterations=int(st[0]), gnc_inliers=int(st[1]), rot_err_deg=rot, trans_err_m=tr,
+               success=bool(reg.is_success(R, t, R_gt, t_gt)), n_tau=3000, beta=beta)
     if with_oracle:
-        from oracle import registration as reg
-
         i, j, d1, d2 = pair.correspondences()
         A = np.zeros(len(i), dtype=[("i", np.int64), ("j", np.int64), ("d1", np.float64), ("d2", np.float64)])
         A["i"], A["j"], A["d1"], A["d2"] = i, j, d1, d2
@@ -366,10 +380,16 @@ def bench_prune(torch, ctx, pair, voxel, reps, with_oracle):
         vt = pair.tgt.vox4[: int(pair.tgt.n_vox.item())].cpu().numpy().astype(np.float64)
         t0 = time.perf_counter()
         sel = reg.ratio_filter(A, 3000)
-        offs, adj = reg.invariant_graph(vs[sel["i"], :3], vt[sel["j"], :3], beta)
+        a, b = vs[sel["i"], :3], vt[sel["j"], :3]
+        offs, adj = reg.invariant_graph(a, b, beta)
         keep = reg.max_kcore(offs, adj)
-        res["oracle_ms"] = (time.perf_counter() - t0) * 1e3
+        t1 = time.perf_counter()
+        Ro, to, _ = reg.gnc_tls(a[keep], b[keep], beta)
+        t2 = time.perf_counter()
+        res["oracle_prune_ms"] = (t1 - t0) * 1e3
+        res["oracle_gnc_ms"] = (t2 - t1) * 1e3
         res["oracle_max_core"] = int(len(keep))
+        res["oracle_success"] = bool(reg.is_success(Ro, to, R_gt, t_gt))
     return res
 
 

@@ -135,3 +135,36 @@ def test_gnc_too_few_points(env):
     ctx.sync()
     assert np.array_equal(got["R"].cpu().numpy(), np.eye(3).ravel())
     assert got["stats"].cpu().numpy()[3] == 1
+
+
+def test_device_registration_success_parity(env):
+    """Features, matching, pruning and GNC all on the device: the success
+    verdict of Sec. IV-A equals the oracle's whole chain, pair by pair."""
+    torch, kmx, ctx = env
+    from oracle import core as orc
+    from oracle import registration as reg
+    from paper_2409_15615_gb300 import pipeline
+
+    flags_o, flags_g = [], []
+    for seed in range(500, 512):
+        src, tgt, Rgt, tgt_t, vps, vpt = scene_pair(seed, n=10000, clutter=True)
+        v = 0.1
+        A, fs, ft, vs, vt = orc.front_end(src, tgt, v, np.float32(vps).astype(np.float64),
+                                          np.float32(vpt).astype(np.float64))
+        Ro, to, _ = reg.register(A, vs, vt, v)
+        flags_o.append(reg.is_success(Ro, to, Rgt, tgt_t))
+        pair = pipeline.PairState(ctx, len(src), len(tgt))
+        pair.src.raw.copy_(torch.from_numpy(src).cuda())
+        pair.tgt.raw.copy_(torch.from_numpy(tgt).cuda())
+        ps = kmx.params_default(v, viewpoint=np.float32(vps).tolist())
+        pt = kmx.params_default(v, viewpoint=np.float32(vpt).tolist())
+        pair.run_checked(len(src), len(tgt), ps, pt, kmx.MATCH_FP32_EXACT)
+        pr = ctx.prune(pair.corr, int(pair.n_corr.item()), pair.src.vox4, pair.tgt.vox4, 1.5 * v)
+        got = ctx.gnc(pair.corr, pr, pair.src.vox4, pair.tgt.vox4, 1.5 * v)
+        ctx.sync()
+        Rg = got["R"].cpu().numpy().reshape(3, 3)
+        ok = got["stats"].cpu().numpy()[3] == 0 and reg.is_success(Rg, got["t"].cpu().numpy(), Rgt, tgt_t)
+        flags_g.append(bool(ok))
+        pair.close()
+    assert flags_g == flags_o
+    assert sum(flags_o) >= len(flags_o) // 2
