@@ -49,11 +49,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch the calls directly instead of replaying "
                                                              "the pair captured as one CUDA graph")
-    ap.add_argument("--batch-pairs", type=int, default=32,
+    ap.add_argument("--batch-pairs", type=int, default=256,
                     help="also time a batch of this many uneven pairs in one graph launch (0 = skip)")
     ap.add_argument("--serve-requests", type=int, default=64,
                     help="also run the serving loop with this many requests per rate (0 = skip)")
-    ap.add_argument("--serve-rates", default="100,1000", help="request rates (req/s) for the serving loop")
+    ap.add_argument("--serve-rates", default="50,100,200,500,1000,2000",
+                    help="request rates (req/s) for the serving loop")
     ap.add_argument("--no-register", action="store_true", help="skip timing kmx_prune + kmx_gnc (ratio filter, "
                     "invariant graph, max k-core, GNC-TLS pose) on the pair's correspondences")
     return ap.parse_args()
@@ -393,36 +394,44 @@ def bench_register(torch, ctx, pair, voxel, R_gt, t_gt, reps, with_oracle):
     return res
 
 
-def bench_serving(torch, n_req, rates, rank):
-    """Poisson request streams against resident maps (one indoor room map
-    and one LiDAR map), queries log-uniform in [5k, 300k] raw points."""
-    from synth import lidar_pair, scene_pair
-    from synth.scenes import map_cloud
+def bench_serving(torch, n_req, rates, rank, n_maps=32):
+    """Poisson request streams against ``n_maps`` device-resident maps (raw
+    size log-uniform in [100k, 1M], LiDAR and indoor generators, voxelised
+    and described once), query scans log-uniform in [5k, 300k] raw points
+    drawn from a pool of 64; HBM admission budget 60 GB; p50 / p99 latency
+    and completed pairs/s per rate."""
+    from synth.scenes import map_cloud, query_scan
 
     from paper_2409_15615_gb300 import kmx, serve
 
     ctx = kmx.Context(0)
-    maps = []
-    for k, n in enumerate((400_000, 200_000)):
-        xyz, vp, kind = map_cloud(9000 + k, n)
-        maps.append(serve.ResidentMap(ctx, xyz, 0.1 if kind == "indoor" else 0.3, vp))
     rng = np.random.default_rng(11 + rank)
+    maps = []
+    for k in range(n_maps):
+        n = int(round(np.exp(rng.uniform(np.log(100_000), np.log(1_000_000)))))
+        xyz, vp, kind = map_cloud(9000 + 97 * rank + k, n)
+        maps.append(serve.ResidentMap(ctx, xyz, 0.1 if kind == "indoor" else 0.3, vp))
+    pool = []
+    for k in range(64):
+        n = int(round(np.exp(rng.uniform(np.log(5000), np.log(300000)))))
+        pool.append(query_scan(int(rng.integers(1 << 30)), n))
     out = []
     for rate in rates:
         arr = serve.poisson_arrivals(rate, n_req, seed=int(rate) + rank)
         reqs = []
         for i in range(n_req):
-            n = int(round(np.exp(rng.uniform(np.log(5000), np.log(300000)))))
-            q, _, _, _, vpq, _ = scene_pair(int(rng.integers(1 << 30)), n=n)
-            reqs.append(serve.Request(i, i % len(maps), q, maps[i % len(maps)].voxel, tuple(vpq), float(arr[i])))
+            q, vpq = pool[int(rng.integers(len(pool)))]
+            m = int(rng.integers(len(maps)))
+            reqs.append(serve.Request(i, m, q, maps[m].voxel, tuple(vpq), float(arr[i])))
         srv = serve.Server(maps, slots=8)
         done = srv.run(reqs, realtime=True)
         st = serve.latency_stats(done)
         st["rate_req_s"] = rate
         out.append(st)
+    resident = [int(len(m.desc)) for m in maps]
     ctx.close()
-    return dict(requests_per_rate=n_req, slots=8, budget_gb=60, maps=[int(len(m.desc)) for m in maps],
-                per_rate=out)
+    return dict(requests_per_rate=n_req, slots=8, budget_gb=60, maps=len(maps),
+                map_descriptors=dict(min=min(resident), max=max(resident), total=sum(resident)), per_rate=out)
 
 
 def stage_times(torch, ctx, pair, n_src, n_tgt, ps, pt, mode, flush, reps):
