@@ -55,6 +55,8 @@ def parse():
                     help="also run the serving loop with this many requests per rate (0 = skip)")
     ap.add_argument("--serve-rates", default="50,100,200,500,1000,2000",
                     help="request rates (req/s) for the serving loop")
+    ap.add_argument("--no-indoor", action="store_true", help="skip the 2M-point indoor pair (voxel 0.02 m, "
+                    "full ~300k x 300k matching in both modes)")
     ap.add_argument("--no-register", action="store_true", help="skip timing kmx_prune + kmx_gnc (ratio filter, "
                     "invariant graph, max k-core, GNC-TLS pose) on the pair's correspondences")
     return ap.parse_args()
@@ -301,6 +303,8 @@ def run_kmx(args):
         line["register"] = bench_register(torch, ctx, pair, WORKLOAD["voxel"], R_gt, t_gt,
                                           reps=max(5, args.steps // 4),
                                           with_oracle=world == 1 and not args.no_cpu_baseline)
+    if not args.no_indoor:
+        line["indoor"] = bench_indoor(torch, rank, reps=3)
     if args.batch_pairs > 0:
         line["batched"] = bench_batched(torch, args.batch_pairs, rank)
     if args.serve_requests > 0:
@@ -335,6 +339,58 @@ def bench_batched(torch, n_pairs, rank):
                 batch_ms=sec * 1e3, pairs_per_s=n_pairs / sec, plain_pairs_per_s=n_pairs / plain_sec,
                 speedup_vs_plain=plain_sec / sec, raw_points=int(sum(len(s.src) + len(s.tgt) for s in specs)),
                 correspondences=n_corr, same_counts_as_plain=same, autotune=table)
+
+
+def bench_indoor(torch, rank, reps):
+    """The large dense pair: 2M raw points per cloud from the indoor-room
+    generator, voxel 0.02 m (~300k points), full mutual matching of all
+    descriptors.  One pair per step, graph replay, inputs resident in HBM;
+    exact FP32 and BF16 tensor-core + certified FP32 rerank timed on the same
+    pair, with their correspondence sets compared."""
+    from synth import indoor_pair
+
+    from paper_2409_15615_gb300 import kmx, pipeline
+
+    src, tgt, R, t, vps, vpt = indoor_pair(31 + rank)
+    v = 0.02
+    ctx = kmx.Context(0)
+    pair = pipeline.PairState(ctx, len(src), len(tgt))
+    pair.src.raw.copy_(torch.from_numpy(src).cuda())
+    pair.tgt.raw.copy_(torch.from_numpy(tgt).cuda())
+    ps = kmx.params_default(v, viewpoint=np.float32(vps).tolist())
+    pt = kmx.params_default(v, viewpoint=np.float32(vpt).tolist())
+    out = dict(raw_points=[len(src), len(tgt)])
+    stream = torch.cuda.current_stream()
+    sets = {}
+    for mode, name in ((kmx.MATCH_FP32_EXACT, "fp32_exact"), (kmx.MATCH_BF16_RERANK, "bf16_certified")):
+        pair.run_checked(len(src), len(tgt), ps, pt, mode)
+        graph = pair.capture(len(src), len(tgt), ps, pt, mode)
+        graph.replay()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            graph.replay()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        pair.sync()
+        n = int(pair.n_corr.item())
+        sets[name] = pair.corr[:n].cpu().numpy()
+        out[name] = dict(ms_per_pair=float(np.median(ts)), pairs_per_s=1e3 / float(np.median(ts)), correspondences=n)
+        del graph
+    # feature stages alone (both clouds, graph replay) give the match share
+    out["voxelised"] = [int(pair.src.n_vox.item()), int(pair.tgt.n_vox.item())]
+    out["descriptors"] = [int(pair.src.out["n_valid"].item()), int(pair.tgt.out["n_valid"].item())]
+    np_, nq_ = out["descriptors"]
+    fp = out["fp32_exact"]["ms_per_pair"]
+    out["points_per_s"] = (out["voxelised"][0] + out["voxelised"][1]) / (fp / 1e3)
+    out["identical_sets"] = bool(np.array_equal(sets["fp32_exact"], sets["bf16_certified"]))
+    out["match_flops_dense"] = 3.0 * np_ * nq_ * 33
+    pair.close()
+    ctx.close()
+    return out
 
 
 def bench_register(torch, ctx, pair, voxel, R_gt, t_gt, reps, with_oracle):
