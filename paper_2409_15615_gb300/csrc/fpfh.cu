@@ -50,21 +50,21 @@ __global__ void __launch_bounds__(kThreads) valid_count(int64_t n_cap, const int
     const int lane = threadIdx.x & 31;
     const int64_t n = kmx_count(d_n, n_cap);
     for (int64_t q = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); q < n; q += (int64_t)gridDim.x * kWarps) {
-    const uint8_t fq = flags[q];
-    int mv = 0;
-    if (fq & 1) {
-        const int64_t b = offs[q], e = offs[q + 1];
-        for (int64_t t = b + lane; t - lane < e; t += 32) {
-            bool ok = false;
-            if (t < e) ok = (flags[nbr[t]] & 1) != 0;  // bit0 is never written here
-            mv += __popc(__ballot_sync(kFull, ok));
+        const uint8_t fq = flags[q];
+        int mv = 0;
+        if (fq & 1) {
+            const int64_t b = offs[q], e = offs[q + 1];
+            for (int64_t t = b + lane; t - lane < e; t += 32) {
+                bool ok = false;
+                if (t < e) ok = (flags[nbr[t]] & 1) != 0;  // bit0 is never written here
+                mv += __popc(__ballot_sync(kFull, ok));
+            }
         }
-    }
-    if (lane == 0) {
-        const bool inJ = (fq & 1) && mv >= tau_num;
-        jflag[q] = inJ ? 1 : 0;
-        flags[q] = (uint8_t)((fq & ~2u) | (inJ ? 2u : 0u));
-    }
+        if (lane == 0) {
+            const bool inJ = (fq & 1) && mv >= tau_num;
+            jflag[q] = inJ ? 1 : 0;
+            flags[q] = (uint8_t)((fq & ~2u) | (inJ ? 2u : 0u));
+        }
     }
 }
 
@@ -145,42 +145,42 @@ __global__ void __launch_bounds__(kThreads) spfh_kernel(int64_t n_cap, const int
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t n = kmx_count(d_n, n_cap);
     for (int64_t q = (int64_t)blockIdx.x * kWarps + warp; q < n; q += (int64_t)gridDim.x * kWarps) {
-    float* row = spfh + q * kStride;
-    const uint8_t fq = flags[q];
-    if (!(fq & 1)) {
-        row[lane] = 0.f;
-        if (lane < kStride - 32) row[32 + lane] = 0.f;
-        continue;
-    }
-    hist[warp][lane] = 0;
-    if (lane < kStride - 32) hist[warp][32 + lane] = 0;
-    __syncwarp();
-    const float4 pq = pts[q];
-    const float4 nq = normal4[q];
-    const float PI = 3.14159265358979f;
-    const int64_t b = offs[q], e = offs[q + 1];
-    int pairs = 0;
-    for (int64_t t = b + lane; t - lane < e; t += 32) {
-        bool ok = false;
-        if (t < e) {
-            const int k = nbr[t];
-            if (k != q && (__ldg(&flags[k]) & 1)) {
-                float f[3];
-                ok = pair_features(pq, nq, __ldg(&pts[k]), __ldg(&normal4[k]), f);
-                if (ok) {
-                    atomicAdd(&hist[warp][feature_bin(f[0], -PI, PI)], 1);
-                    atomicAdd(&hist[warp][kH + feature_bin(f[1], -1.f, 1.f)], 1);
-                    atomicAdd(&hist[warp][2 * kH + feature_bin(f[2], -1.f, 1.f)], 1);
+        float* row = spfh + q * kStride;
+        const uint8_t fq = flags[q];
+        if (!(fq & 1)) {
+            row[lane] = 0.f;
+            if (lane < kStride - 32) row[32 + lane] = 0.f;
+            continue;
+        }
+        hist[warp][lane] = 0;
+        if (lane < kStride - 32) hist[warp][32 + lane] = 0;
+        __syncwarp();
+        const float4 pq = pts[q];
+        const float4 nq = normal4[q];
+        const float PI = 3.14159265358979f;
+        const int64_t b = offs[q], e = offs[q + 1];
+        int pairs = 0;
+        for (int64_t t = b + lane; t - lane < e; t += 32) {
+            bool ok = false;
+            if (t < e) {
+                const int k = nbr[t];
+                if (k != q && (__ldg(&flags[k]) & 1)) {
+                    float f[3];
+                    ok = pair_features(pq, nq, __ldg(&pts[k]), __ldg(&normal4[k]), f);
+                    if (ok) {
+                        atomicAdd(&hist[warp][feature_bin(f[0], -PI, PI)], 1);
+                        atomicAdd(&hist[warp][kH + feature_bin(f[1], -1.f, 1.f)], 1);
+                        atomicAdd(&hist[warp][2 * kH + feature_bin(f[2], -1.f, 1.f)], 1);
+                    }
                 }
             }
+            pairs += __popc(__ballot_sync(kFull, ok));
         }
-        pairs += __popc(__ballot_sync(kFull, ok));
-    }
-    __syncwarp();
-    const float scale = pairs > 0 ? 100.0f / (float)pairs : 0.f;
-    row[lane] = (float)hist[warp][lane] * scale;
-    if (lane < kStride - 32) row[32 + lane] = lane == 0 ? (float)hist[warp][32] * scale : 0.f;
-    __syncwarp();  // the histogram is cleared for the next query
+        __syncwarp();
+        const float scale = pairs > 0 ? 100.0f / (float)pairs : 0.f;
+        row[lane] = (float)hist[warp][lane] * scale;
+        if (lane < kStride - 32) row[32 + lane] = lane == 0 ? (float)hist[warp][32] * scale : 0.f;
+        __syncwarp();  // the histogram is cleared for the next query
     }
 }
 

@@ -591,22 +591,22 @@ __global__ void __launch_bounds__(256) merge_segments(const kmx::RowBest* __rest
     const int64_t nqt = tiles_of(nq);
     const int64_t W = npt * nqt;
     for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < np; i += (int64_t)gridDim.x * 256) {
-    kmx::RowBest r{INFINITY, 0x7fffffff, INFINITY};
-    if (W > 0) {
-        const ChunkGeo cg = chunk_geo(W, ctas);
-        const int64_t rt = i / kTile;
-        const int64_t cf = (rt * nqt) / cg.L, cl = (rt * nqt + nqt - 1) / cg.L;
-        r = seg[(cf + rt) * kTile + (i % kTile)];
-        for (int64_t c = cf + 1; c <= cl; ++c) {
-            const kmx::RowBest o = seg[(c + rt) * kTile + (i % kTile)];
-            kmx::row_merge(r.d1, r.j1, r.d2, o.d1, o.j1, o.d2);
+        kmx::RowBest r{INFINITY, 0x7fffffff, INFINITY};
+        if (W > 0) {
+            const ChunkGeo cg = chunk_geo(W, ctas);
+            const int64_t rt = i / kTile;
+            const int64_t cf = (rt * nqt) / cg.L, cl = (rt * nqt + nqt - 1) / cg.L;
+            r = seg[(cf + rt) * kTile + (i % kTile)];
+            for (int64_t c = cf + 1; c <= cl; ++c) {
+                const kmx::RowBest o = seg[(c + rt) * kTile + (i % kTile)];
+                kmx::row_merge(r.d1, r.j1, r.d2, o.d1, o.j1, o.d2);
+            }
         }
-    }
-    const int32_t orig = pperm[i];
-    merged[orig] = r;
-    bool mutual = false;
-    if (r.j1 >= 0 && r.j1 != 0x7fffffff) mutual = (uint32_t)(colbest[r.j1] & 0xffffffffull) == (uint32_t)orig;
-    mflag[orig] = mutual ? 1 : 0;
+        const int32_t orig = pperm[i];
+        merged[orig] = r;
+        bool mutual = false;
+        if (r.j1 >= 0 && r.j1 != 0x7fffffff) mutual = (uint32_t)(colbest[r.j1] & 0xffffffffull) == (uint32_t)orig;
+        mflag[orig] = mutual ? 1 : 0;
     }
 }
 

@@ -127,42 +127,42 @@ __global__ void __launch_bounds__(kThreads) search_count(GridView g, Radii R, No
     const int lane = threadIdx.x & 31;
     const int64_t n_sorted = *g.n_sorted;
     for (int64_t p = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); p < n_sorted; p += (int64_t)gridDim.x * kWarps) {
-    const float4 q = g.sorted[p];
-    const int qi = __float_as_int(q.w);
-    int start, excl;
-    const int total = stencil(g, q, lane, &start, &excl);
-    int nf = 0, nn = 0;
-    float sx = 0.f, sy = 0.f, sz = 0.f;
-    for (int base = 0; base < total; base += 32) {
-        const int t = base + lane;
-        const int pos = candidate(t, start, excl);
-        bool inF = false, inN = false;
-        float dx = 0.f, dy = 0.f, dz = 0.f;
-        if (t < total) {
-            const float4 a = g.sorted[pos];
-            dx = a.x - q.x;
-            dy = a.y - q.y;
-            dz = a.z - q.z;
-            const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            inF = within(a, q, d2, R.rf2, R.rf2d);
-            inN = inF && within(a, q, d2, R.rn2, R.rn2d);
+        const float4 q = g.sorted[p];
+        const int qi = __float_as_int(q.w);
+        int start, excl;
+        const int total = stencil(g, q, lane, &start, &excl);
+        int nf = 0, nn = 0;
+        float sx = 0.f, sy = 0.f, sz = 0.f;
+        for (int base = 0; base < total; base += 32) {
+            const int t = base + lane;
+            const int pos = candidate(t, start, excl);
+            bool inF = false, inN = false;
+            float dx = 0.f, dy = 0.f, dz = 0.f;
+            if (t < total) {
+                const float4 a = g.sorted[pos];
+                dx = a.x - q.x;
+                dy = a.y - q.y;
+                dz = a.z - q.z;
+                const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                inF = within(a, q, d2, R.rf2, R.rf2d);
+                inN = inF && within(a, q, d2, R.rn2, R.rn2d);
+            }
+            nf += __popc(__ballot_sync(kFull, inF));
+            nn += __popc(__ballot_sync(kFull, inN));
+            if (inN) {
+                sx += dx;
+                sy += dy;
+                sz += dz;
+            }
         }
-        nf += __popc(__ballot_sync(kFull, inF));
-        nn += __popc(__ballot_sync(kFull, inN));
-        if (inN) {
-            sx += dx;
-            sy += dy;
-            sz += dz;
+        sx = warp_sum(sx);
+        sy = warp_sum(sy);
+        sz = warp_sum(sz);
+        if (lane == 0) {
+            s.cnt[qi] = nf;
+            const float inv = nn > 0 ? 1.0f / (float)nn : 0.0f;
+            s.mean[qi] = make_float4(sx * inv, sy * inv, sz * inv, __int_as_float(nn));
         }
-    }
-    sx = warp_sum(sx);
-    sy = warp_sum(sy);
-    sz = warp_sum(sz);
-    if (lane == 0) {
-        s.cnt[qi] = nf;
-        const float inv = nn > 0 ? 1.0f / (float)nn : 0.0f;
-        s.mean[qi] = make_float4(sx * inv, sy * inv, sz * inv, __int_as_float(nn));
-    }
     }
 }
 
@@ -265,112 +265,112 @@ __global__ void __launch_bounds__(kThreads) search_fill(GridView g, Radii R, Nor
     const int64_t n_sorted = *g.n_sorted;
     // uniform over the block: every thread reaches the barriers
     for (int64_t chunk = blockIdx.x; chunk * kQPerBlock < n_sorted; chunk += gridDim.x) {
-    for (int k = 0; k < kQPerWarp; ++k) {
-        const int slot = warp * kQPerWarp + k;
-        const int64_t p = chunk * kQPerBlock + slot;
-        if (p >= n_sorted) {
-            if (lane == 0) sm_qi[slot] = -1;
-            continue;
-        }
-        const float4 q = g.sorted[p];
-        const int qi = __float_as_int(q.w);
-        const float4 mq = s.mean[qi];
-        int start, excl;
-        const int total = stencil(g, q, lane, &start, &excl);
-        int64_t out = o.offs[qi];
-        float s1x = 0.f, s1y = 0.f, s1z = 0.f;
-        float sxx = 0.f, sxy = 0.f, sxz = 0.f, syy = 0.f, syz = 0.f, szz = 0.f;
-        for (int base = 0; base < total; base += 32) {
-            const int t = base + lane;
-            const int pos = candidate(t, start, excl);
-            bool inF = false, inN = false;
-            float dx = 0.f, dy = 0.f, dz = 0.f;
-            int idx = 0;
-            if (t < total) {
-                const float4 a = g.sorted[pos];
-                idx = __float_as_int(a.w);
-                dx = a.x - q.x;
-                dy = a.y - q.y;
-                dz = a.z - q.z;
-                const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                inF = within(a, q, d2, R.rf2, R.rf2d);
-                inN = inF && within(a, q, d2, R.rn2, R.rn2d);
+        for (int k = 0; k < kQPerWarp; ++k) {
+            const int slot = warp * kQPerWarp + k;
+            const int64_t p = chunk * kQPerBlock + slot;
+            if (p >= n_sorted) {
+                if (lane == 0) sm_qi[slot] = -1;
+                continue;
             }
-            const unsigned bal = __ballot_sync(kFull, inF);
-            if (inF && write) o.nbr[out + __popc(bal & ((1u << lane) - 1u))] = idx;
-            out += __popc(bal);
-            if (inN) {
-                const float ex = dx - mq.x, ey = dy - mq.y, ez = dz - mq.z;
-                s1x += ex;
-                s1y += ey;
-                s1z += ez;
-                sxx = fmaf(ex, ex, sxx);
-                sxy = fmaf(ex, ey, sxy);
-                sxz = fmaf(ex, ez, sxz);
-                syy = fmaf(ey, ey, syy);
-                syz = fmaf(ey, ez, syz);
-                szz = fmaf(ez, ez, szz);
+            const float4 q = g.sorted[p];
+            const int qi = __float_as_int(q.w);
+            const float4 mq = s.mean[qi];
+            int start, excl;
+            const int total = stencil(g, q, lane, &start, &excl);
+            int64_t out = o.offs[qi];
+            float s1x = 0.f, s1y = 0.f, s1z = 0.f;
+            float sxx = 0.f, sxy = 0.f, sxz = 0.f, syy = 0.f, syz = 0.f, szz = 0.f;
+            for (int base = 0; base < total; base += 32) {
+                const int t = base + lane;
+                const int pos = candidate(t, start, excl);
+                bool inF = false, inN = false;
+                float dx = 0.f, dy = 0.f, dz = 0.f;
+                int idx = 0;
+                if (t < total) {
+                    const float4 a = g.sorted[pos];
+                    idx = __float_as_int(a.w);
+                    dx = a.x - q.x;
+                    dy = a.y - q.y;
+                    dz = a.z - q.z;
+                    const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    inF = within(a, q, d2, R.rf2, R.rf2d);
+                    inN = inF && within(a, q, d2, R.rn2, R.rn2d);
+                }
+                const unsigned bal = __ballot_sync(kFull, inF);
+                if (inF && write) o.nbr[out + __popc(bal & ((1u << lane) - 1u))] = idx;
+                out += __popc(bal);
+                if (inN) {
+                    const float ex = dx - mq.x, ey = dy - mq.y, ez = dz - mq.z;
+                    s1x += ex;
+                    s1y += ey;
+                    s1z += ez;
+                    sxx = fmaf(ex, ex, sxx);
+                    sxy = fmaf(ex, ey, sxy);
+                    sxz = fmaf(ex, ez, sxz);
+                    syy = fmaf(ey, ey, syy);
+                    syz = fmaf(ey, ez, syz);
+                    szz = fmaf(ez, ez, szz);
+                }
+            }
+            s1x = warp_sum(s1x);
+            s1y = warp_sum(s1y);
+            s1z = warp_sum(s1z);
+            sxx = warp_sum(sxx);
+            sxy = warp_sum(sxy);
+            sxz = warp_sum(sxz);
+            syy = warp_sum(syy);
+            syz = warp_sum(syz);
+            szz = warp_sum(szz);
+            if (lane == 0) {
+                sm_mom[0][slot] = s1x;
+                sm_mom[1][slot] = s1y;
+                sm_mom[2][slot] = s1z;
+                sm_mom[3][slot] = sxx;
+                sm_mom[4][slot] = sxy;
+                sm_mom[5][slot] = sxz;
+                sm_mom[6][slot] = syy;
+                sm_mom[7][slot] = syz;
+                sm_mom[8][slot] = szz;
+                sm_q[0][slot] = q.x;
+                sm_q[1][slot] = q.y;
+                sm_q[2][slot] = q.z;
+                sm_qi[slot] = qi;
+                sm_nN[slot] = __float_as_int(mq.w);
             }
         }
-        s1x = warp_sum(s1x);
-        s1y = warp_sum(s1y);
-        s1z = warp_sum(s1z);
-        sxx = warp_sum(sxx);
-        sxy = warp_sum(sxy);
-        sxz = warp_sum(sxz);
-        syy = warp_sum(syy);
-        syz = warp_sum(syz);
-        szz = warp_sum(szz);
-        if (lane == 0) {
-            sm_mom[0][slot] = s1x;
-            sm_mom[1][slot] = s1y;
-            sm_mom[2][slot] = s1z;
-            sm_mom[3][slot] = sxx;
-            sm_mom[4][slot] = sxy;
-            sm_mom[5][slot] = sxz;
-            sm_mom[6][slot] = syy;
-            sm_mom[7][slot] = syz;
-            sm_mom[8][slot] = szz;
-            sm_q[0][slot] = q.x;
-            sm_q[1][slot] = q.y;
-            sm_q[2][slot] = q.z;
-            sm_qi[slot] = qi;
-            sm_nN[slot] = __float_as_int(mq.w);
+        __syncthreads();
+        if (warp == 0 && sm_qi[lane] >= 0) {
+            const int qi = sm_qi[lane];
+            const int nN = sm_nN[lane];
+            const int mF = (int)(o.offs[qi + 1] - o.offs[qi]);
+            uint8_t flag = 0;
+            float4 nout = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (mF >= o.tau_num && nN >= o.tau_num) {
+                const double inv = 1.0 / (double)nN;
+                const double m0 = (double)sm_mom[0][lane] * inv, m1 = (double)sm_mom[1][lane] * inv;
+                const double m2 = (double)sm_mom[2][lane] * inv;
+                const double c00 = (double)sm_mom[3][lane] * inv - m0 * m0, c01 = (double)sm_mom[4][lane] * inv - m0 * m1;
+                const double c02 = (double)sm_mom[5][lane] * inv - m0 * m2, c11 = (double)sm_mom[6][lane] * inv - m1 * m1;
+                const double c12 = (double)sm_mom[7][lane] * inv - m1 * m2, c22 = (double)sm_mom[8][lane] * inv - m2 * m2;
+                double l[3], nv[3];
+                eig_sym3(c00, c01, c02, c11, c12, c22, l, nv);
+                flag |= 4;
+                if (l[0] > 0.0) {
+                    const double view = nv[0] * ((double)o.vp[0] - (double)sm_q[0][lane]) +
+                                        nv[1] * ((double)o.vp[1] - (double)sm_q[1][lane]) +
+                                        nv[2] * ((double)o.vp[2] - (double)sm_q[2][lane]);
+                    bool flip = view < 0.0;
+                    if (view == 0.0) flip = nv[0] != 0.0 ? nv[0] < 0.0 : (nv[1] != 0.0 ? nv[1] < 0.0 : nv[2] < 0.0);
+                    const double sgn = flip ? -1.0 : 1.0;
+                    const double plin = (l[0] - l[1]) / l[0];
+                    nout = make_float4((float)(sgn * nv[0]), (float)(sgn * nv[1]), (float)(sgn * nv[2]), (float)plin);
+                    if (plin < (double)o.tau_lin) flag |= 1;
+                }
+            }
+            o.normal4[qi] = nout;
+            o.flags[qi] = flag;
         }
-    }
-    __syncthreads();
-    if (warp == 0 && sm_qi[lane] >= 0) {
-    const int qi = sm_qi[lane];
-    const int nN = sm_nN[lane];
-    const int mF = (int)(o.offs[qi + 1] - o.offs[qi]);
-    uint8_t flag = 0;
-    float4 nout = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (mF >= o.tau_num && nN >= o.tau_num) {
-        const double inv = 1.0 / (double)nN;
-        const double m0 = (double)sm_mom[0][lane] * inv, m1 = (double)sm_mom[1][lane] * inv;
-        const double m2 = (double)sm_mom[2][lane] * inv;
-        const double c00 = (double)sm_mom[3][lane] * inv - m0 * m0, c01 = (double)sm_mom[4][lane] * inv - m0 * m1;
-        const double c02 = (double)sm_mom[5][lane] * inv - m0 * m2, c11 = (double)sm_mom[6][lane] * inv - m1 * m1;
-        const double c12 = (double)sm_mom[7][lane] * inv - m1 * m2, c22 = (double)sm_mom[8][lane] * inv - m2 * m2;
-        double l[3], nv[3];
-        eig_sym3(c00, c01, c02, c11, c12, c22, l, nv);
-        flag |= 4;
-        if (l[0] > 0.0) {
-            const double view = nv[0] * ((double)o.vp[0] - (double)sm_q[0][lane]) +
-                                nv[1] * ((double)o.vp[1] - (double)sm_q[1][lane]) +
-                                nv[2] * ((double)o.vp[2] - (double)sm_q[2][lane]);
-            bool flip = view < 0.0;
-            if (view == 0.0) flip = nv[0] != 0.0 ? nv[0] < 0.0 : (nv[1] != 0.0 ? nv[1] < 0.0 : nv[2] < 0.0);
-            const double sgn = flip ? -1.0 : 1.0;
-            const double plin = (l[0] - l[1]) / l[0];
-            nout = make_float4((float)(sgn * nv[0]), (float)(sgn * nv[1]), (float)(sgn * nv[2]), (float)plin);
-            if (plin < (double)o.tau_lin) flag |= 1;
-        }
-    }
-    o.normal4[qi] = nout;
-    o.flags[qi] = flag;
-    }
-    __syncthreads();  // the shared moments are rewritten by the next chunk
+        __syncthreads();  // the shared moments are rewritten by the next chunk
     }
 }
 
