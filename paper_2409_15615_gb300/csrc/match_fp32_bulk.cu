@@ -64,7 +64,7 @@ constexpr uint32_t kPBytes = kDim * kTile * sizeof(float2);  // 33792
 constexpr uint32_t kQBytes = kDim * kTile * sizeof(float);   // 16896
 constexpr uint32_t kPermBytes = kTile * sizeof(int32_t);     // 512
 constexpr int kCtasPerSm = 2;
-constexpr int kChunksPerCta = 16;  // chunks of the tile sequence per resident CTA (load balance)
+constexpr int kChunksPerCta = 8;  // chunks of the tile sequence per resident CTA (load balance)
 constexpr int kMinChunk = 4;       // tile pairs per chunk at least (more than kStages - 1)
 
 // Thread 0's position in its own stream of tile pairs (kept in shared memory:

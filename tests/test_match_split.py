@@ -2,9 +2,9 @@
 
 The (row tile x column tile) grid, W = npt * nqt tile pairs flattened
 row-major, is cut into NC chunks of L consecutive pairs, with
-L = max(4, ceil(W / (16 * ctas))); CTAs take chunks from a counter.  The
+L = max(4, ceil(W / (8 * ctas))); CTAs take chunks from a counter.  The
 segment of chunk c in row tile rt sits in slot c + rt of a
-(16 * ctas + 1 + npt) * 128 array, and merge_segments reads the chunks
+(8 * ctas + 1 + npt) * 128 array, and merge_segments reads the chunks
 floor(rt * nqt / L) .. floor((rt * nqt + nqt - 1) / L) of row tile rt.
 These checks pin that arithmetic for any order in which the CTAs take the
 chunks: every tile pair is covered exactly once, slots are unique and in
@@ -13,7 +13,7 @@ bounds, and the merge reads exactly the segments written for its row tile.
 import random
 
 TILE = 128
-CHUNKS_PER_CTA = 16
+CHUNKS_PER_CTA = 8
 MIN_CHUNK = 4
 
 
