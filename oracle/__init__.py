@@ -26,6 +26,7 @@ from .core import (  # noqa: F401
     spfh,
     fpfh,
     faster_pfh,
+    classic_fpfh,
     nearest,
     mutual_match,
     front_end,

@@ -230,6 +230,36 @@ def faster_pfh(p4, params: OracleParams, search="grid"):
                 voffs=voffs, vnbr=vnbr, J=J, spfh=sp, npairs=npairs, margin=margin, n_marg=n_marg, fpfh=fp)
 
 
+def classic_fpfh(p4, params: OracleParams, search="grid"):
+    """Classic FPFH (Rusu et al. 2009), the baseline Faster-PFH is compared
+    with in Sec. III-C (Fig. 2(a)): (i) a radius search with r_normal and a
+    PCA normal for every point, (ii) a second search with r_FPFH and the SPFH
+    of every point, (iii) a third search with r_FPFH and the weighted FPFH sum
+    (Eq. A5), with no reliability test anywhere.
+
+    Readings (the paper describes the steps, not their edge cases): a point
+    has a normal when |P_normal| >= 3 and l1 > 0 (fewer than three points fix
+    no plane); the normal is oriented and the pair features, bins and weights
+    are those of Faster-PFH; SPFH and FPFH run over the neighbours that have
+    a normal; every point with a normal gets a descriptor.  These are the
+    Faster-PFH stages with the linearity test switched off (tau_lin above
+    any p_lin) and tau_num = 1 in step 2, so the returned J is the set of
+    points with a normal.  Returns the same dict as ``faster_pfh`` plus
+    offs_n, nbr_n (the r_normal lists)."""
+    p = _as_p4(p4)
+    offs_n, nbr_n = radius_search(p, params.r_normal, method=search)
+    cp = OracleParams(params.voxel, r_normal=params.r_normal, r_fpfh=params.r_fpfh, tau_num=3, tau_lin=2.0,
+                      hist_bins=params.hist_bins, viewpoint=params.viewpoint)
+    normal4, evals, flags, n_normal = normals(p, offs_n, nbr_n, cp)
+    offs, nbr = radius_search(p, params.r_fpfh, method=search)
+    voffs, vnbr, J, flags = valid_filter(offs, nbr, flags, 1)
+    sp, npairs, margin, n_marg = spfh(p, normal4, flags, voffs, vnbr, params.hist_bins, with_margin=True)
+    fp = fpfh(p, J, voffs, vnbr, sp)
+    return dict(points=p, offs_n=offs_n, nbr_n=nbr_n, offs=offs, nbr=nbr, normal4=normal4, evals=evals,
+                n_normal=n_normal, flags=flags, voffs=voffs, vnbr=vnbr, J=J, spfh=sp, npairs=npairs, margin=margin,
+                n_marg=n_marg, fpfh=fp)
+
+
 def nearest(X, Y):
     """Row-wise nearest row of Y for every row of X: (nn, d1, d2) with ties to
     the lower index and d2 the second-smallest distance."""
