@@ -57,6 +57,7 @@ def parse():
                     help="request rates (req/s) for the serving loop")
     ap.add_argument("--no-indoor", action="store_true", help="skip the 2M-point indoor pair (voxel 0.02 m, "
                     "full ~300k x 300k matching in both modes)")
+    ap.add_argument("--no-ablation", action="store_true", help="skip the classic-FPFH vs Faster-PFH comparison")
     ap.add_argument("--no-register", action="store_true", help="skip timing kmx_prune + kmx_gnc (ratio filter, "
                     "invariant graph, max k-core, GNC-TLS pose) on the pair's correspondences")
     return ap.parse_args()
@@ -303,6 +304,8 @@ def run_kmx(args):
         line["register"] = bench_register(torch, ctx, pair, WORKLOAD["voxel"], R_gt, t_gt,
                                           reps=max(5, args.steps // 4),
                                           with_oracle=world == 1 and not args.no_cpu_baseline)
+    if not args.no_ablation:
+        line["ablation_classic_fpfh"] = bench_ablation(torch, rank, reps=max(5, args.steps // 3))
     if not args.no_indoor:
         line["indoor"] = bench_indoor(torch, rank, reps=3)
     if args.batch_pairs > 0:
@@ -448,6 +451,76 @@ def bench_register(torch, ctx, pair, voxel, R_gt, t_gt, reps, with_oracle):
         res["oracle_max_core"] = int(len(keep))
         res["oracle_success"] = bool(reg.is_success(Ro, to, R_gt, t_gt))
     return res
+
+
+def bench_ablation(torch, rank, reps):
+    """Classic FPFH (three radius searches, no reliability filtering) against
+    Faster-PFH on the same clouds, the comparison of Sec. III-C.  Per method:
+    device time of the feature stage alone (normals and descriptors;
+    voxelisation and the grid are the same for both and left out) and of the
+    whole pair (both clouds one after the other, then exact FP32 matching),
+    L2 flushed before each repetition; the descriptors; and the mutual
+    correspondences with the share that are inliers (ground-truth-aligned
+    points within 3 v of each other)."""
+    from paper_2409_15615_gb300 import kmx, pipeline
+    from paper_2409_15615_gb300 import replicas
+    from synth import scene_pair
+
+    seed = replicas.pair_seed(WORKLOAD["seed"], rank)
+    cases = [("lidar_64beam_2048az_v0.3", lidar_pair(seed, az_bins=WORKLOAD["az_bins"]), 0.3),
+             ("scene_20k_v0.1", scene_pair(seed, n=20000), 0.1)]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = {}
+    for name, (src, tgt, R, t, vps, vpt), v in cases:
+        ctx = kmx.Context(torch.cuda.current_device())
+        pair = pipeline.PairState(ctx, len(src), len(tgt), overlap=False)
+        pair.src.raw.copy_(torch.from_numpy(src).cuda())
+        pair.tgt.raw.copy_(torch.from_numpy(tgt).cuda())
+        ps = kmx.params_default(v, viewpoint=np.float32(vps).tolist())
+        pt = kmx.params_default(v, viewpoint=np.float32(vpt).tolist())
+        res = {}
+        for method in ("faster", "classic"):
+            pair.src.method = pair.tgt.method = method
+            pair.run_checked(len(src), len(tgt), ps, pt, kmx.MATCH_FP32_EXACT)
+            cs = pair.src
+            times = []
+            for _ in range(reps + 3):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(ctx.stream)
+                if method == "classic":
+                    ctx.fpfh_classic(cs.grid, ps, out=dict(normal4=cs.bufs["normal4"], flags=cs.bufs["flags"],
+                                                           **cs.out))
+                else:
+                    b = ctx.normals(cs.grid, ps, cs.nbr_cap, out=cs.bufs)
+                    ctx.fasterpfh(cs.grid, ps, b["normal4"], b["flags"], b["offs"], b["nbr"], out=cs.out)
+                e1.record(ctx.stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            pair_t = []
+            for _ in range(reps + 3):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(ctx.stream)
+                pair.run(len(src), len(tgt), ps, pt, kmx.MATCH_FP32_EXACT)
+                e1.record(ctx.stream)
+                e1.synchronize()
+                pair_t.append(e0.elapsed_time(e1))
+            ctx.sync()
+            i, j, _, _ = pair.correspondences()
+            vs = pair.src.vox4[: int(pair.src.n_vox.item())].cpu().numpy().astype(np.float64)
+            vt = pair.tgt.vox4[: int(pair.tgt.n_vox.item())].cpu().numpy().astype(np.float64)
+            err = np.linalg.norm(vs[i, :3] @ np.asarray(R).T + np.asarray(t) - vt[j, :3], axis=1)
+            res[method] = dict(feature_ms=float(np.median(times[3:])), pair_ms=float(np.median(pair_t[3:])),
+                               voxelised=int(vs.shape[0]),
+                               descriptors=int(cs.out["n_valid"].item()), correspondences=int(len(i)),
+                               inlier_ratio=float(np.mean(err < 3 * v)) if len(i) else 0.0)
+        pair.close()
+        ctx.close()
+        res["feature_speedup"] = res["classic"]["feature_ms"] / res["faster"]["feature_ms"]
+        res["pair_speedup"] = res["classic"]["pair_ms"] / res["faster"]["pair_ms"]
+        out[name] = res
+    return out
 
 
 def bench_serving(torch, n_req, rates, rank, n_maps=32):

@@ -215,6 +215,32 @@ kmx_status kmx_fasterpfh(kmx_ctx* ctx, const kmx_grid* grid, const kmx_params* p
                          int32_t* d_valid, int64_t* d_n_valid, float* d_spfh);
 
 /*
+ * Classic FPFH (Rusu et al. 2009), the baseline Faster-PFH is compared with
+ * in Sec. III-C (Fig. 2(a)): three radius searches on the grid and no
+ * reliability test (tau_num and tau_lin are not read).
+ *   (i)   r_normal search; a point has a normal when |P_normal| >= 3 and
+ *         l1 > 0 (PCA, FP64 solve, oriented toward params->viewpoint);
+ *   (ii)  r_fpfh search; SPFH (Eqs. A2-A4) of every point with a normal over
+ *         its neighbours with a normal (itself excluded);
+ *   (iii) r_fpfh search; FPFH (Eq. A5) over the same neighbours.
+ * J is the set of points with a normal.  Radius tests are exact as in
+ * kmx_normals.  No neighbour lists are written.
+ *   d_normal4  [n_cap][4] float32 out: normal and p_lin for points with a
+ *              normal, zeros otherwise.
+ *   d_flags    [n_cap] uint8 out: bit0 = has a normal, bit1 = in J (the
+ *              same), bit2 = PCA evaluated.
+ *   d_desc     [n_cap][36] float32 out: row j holds FPFH(J[j]) for j < |J|.
+ *   d_valid    [n_cap] int32 out: J in ascending point order.
+ *   d_n_valid  device int64 out: |J|.
+ *   d_spfh     nullable [n_cap][36] float32 out: SPFH of every point the
+ *              grid holds (zero rows for points without a normal).
+ * Host errors: KMX_EINVAL as kmx_normals (grid cell below r_fpfh, radii,
+ * misaligned buffers).  All outputs are device memory owned by the caller.
+ */
+kmx_status kmx_fpfh_classic(kmx_ctx* ctx, const kmx_grid* grid, const kmx_params* params, float* d_normal4,
+                            uint8_t* d_flags, float* d_desc, int32_t* d_valid, int64_t* d_n_valid, float* d_spfh);
+
+/*
  * Mutual nearest-neighbour matching of descriptors (reciprocity test,
  * Sec. III-C) under Euclidean distance; ties go to the lower row.
  *   d_desc_p   [np_cap][36] float32 source descriptors (rows as written by

@@ -317,6 +317,23 @@ kmx_status kmx_fasterpfh(kmx_ctx* c, const kmx_grid* g, const kmx_params* p, con
                     "kmx_fasterpfh");
 }
 
+kmx_status kmx_fpfh_classic(kmx_ctx* c, const kmx_grid* g, const kmx_params* p, float* d_normal4, uint8_t* d_flags,
+                            float* d_desc, int32_t* d_valid, int64_t* d_n_valid, float* d_spfh)
+{
+    if (!c) return KMX_EINVAL;
+    kmx_status s = check_params(c, g, p, "kmx_fpfh_classic");
+    if (s) return s;
+    if (!d_normal4 || !aligned16(d_normal4) || !d_flags || !d_desc || !aligned16(d_desc) || !d_valid || !d_n_valid ||
+        (d_spfh && !aligned16(d_spfh)))
+        return fail(c, KMX_EINVAL, "kmx_fpfh_classic: bad argument");
+    DeviceGuard dg(c->device);
+    s = ensure_ws(c, kmx_fpfh_classic_scratch_bytes(g->n_cap, d_spfh == nullptr));
+    if (s) return s;
+    return launched(c,
+                    kmx_fpfh_classic_launch(c, g, p, d_normal4, d_flags, d_desc, d_valid, d_n_valid, d_spfh, c->ws),
+                    "kmx_fpfh_classic");
+}
+
 kmx_status kmx_prune(kmx_ctx* c, const kmx_corr* d_corr, int64_t corr_cap, const int64_t* d_n_corr,
                      const float* d_src4, const float* d_tgt4, int32_t n_tau, double beta, int32_t* d_sel,
                      int64_t* d_n_sel, int32_t* d_core, int32_t* d_kmax, int32_t* d_inlier, int64_t* d_n_inlier)

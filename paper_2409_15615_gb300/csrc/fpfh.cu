@@ -11,17 +11,15 @@
 //
 // I_valid is never materialised: the SPFH and FPFH kernels walk M[q] and
 // skip entries without B (one byte gathered per neighbour).
-#include "kmx_internal.cuh"
+#include "pfh_common.cuh"
+
+using namespace kmxp;
 
 namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kH = 11;
-constexpr int kD = 3 * kH;  // 33
-constexpr int kStride = KMX_DESC_STRIDE;
-static_assert(kD == KMX_DESC_DIM, "three sub-histograms of H bins");
 
 struct PfhScratch {
     int32_t* jflag;  // [n+1]
@@ -79,61 +77,6 @@ __global__ void __launch_bounds__(kThreads) scatter_valid(int64_t n_cap, const i
         if (jflag[q]) valid[jpos[q]] = (int32_t)q;
 }
 
-__device__ __forceinline__ float dot3(float ax, float ay, float az, float bx, float by, float bz)
-{
-    return fmaf(az, bz, fmaf(ay, by, ax * bx));
-}
-
-// Angular features of the pair (q, k) (Eq. A2): the point whose normal is
-// closer to parallel with the connecting line is the source; v and w are unit
-// vectors.  Returns false for coincident points or |d x u| < 1e-6.
-__device__ __forceinline__ bool pair_features(float4 pq, float4 nq, float4 pk, float4 nk, float* f)
-{
-    float dx = pk.x - pq.x, dy = pk.y - pq.y, dz = pk.z - pq.z;
-    const float dd = dot3(dx, dy, dz, dx, dy, dz);
-    if (!(dd > 0.f)) return false;
-    const float inv = 1.0f / sqrtf(dd);
-    dx *= inv;
-    dy *= inv;
-    dz *= inv;
-    const float cq = fabsf(dot3(nq.x, nq.y, nq.z, dx, dy, dz));
-    const float ck = fabsf(dot3(nk.x, nk.y, nk.z, dx, dy, dz));
-    float4 u = nq, nb = nk;
-    if (!(cq >= ck)) {
-        u = nk;
-        nb = nq;
-        dx = -dx;
-        dy = -dy;
-        dz = -dz;
-    }
-    // v = d x u / |d x u|
-    float vx = dy * u.z - dz * u.y;
-    float vy = dz * u.x - dx * u.z;
-    float vz = dx * u.y - dy * u.x;
-    const float s = sqrtf(dot3(vx, vy, vz, vx, vy, vz));
-    if (s < 1e-6f) return false;
-    const float is = 1.0f / s;
-    vx *= is;
-    vy *= is;
-    vz *= is;
-    // w = u x v
-    const float wx = u.y * vz - u.z * vy;
-    const float wy = u.z * vx - u.x * vz;
-    const float wz = u.x * vy - u.y * vx;
-    f[0] = atan2f(dot3(wx, wy, wz, nb.x, nb.y, nb.z), dot3(u.x, u.y, u.z, nb.x, nb.y, nb.z));
-    f[1] = dot3(vx, vy, vz, nb.x, nb.y, nb.z);
-    f[2] = dot3(u.x, u.y, u.z, dx, dy, dz);
-    return true;
-}
-
-// 0-based bin (Eq. A3) with the upper end clamped to H-1.
-__device__ __forceinline__ int feature_bin(float f, float lo, float hi)
-{
-    float t = floorf((float)kH * (f - lo) / (hi - lo));
-    t = fminf(fmaxf(t, 0.f), (float)(kH - 1));
-    return (int)t;
-}
-
 __global__ void __launch_bounds__(kThreads) spfh_kernel(int64_t n_cap, const int64_t* d_n,
                                                         const float4* __restrict__ pts,
                                                         const float4* __restrict__ normal4,
@@ -182,14 +125,6 @@ __global__ void __launch_bounds__(kThreads) spfh_kernel(int64_t n_cap, const int
         if (lane < kStride - 32) row[32 + lane] = lane == 0 ? (float)hist[warp][32] * scale : 0.f;
         __syncwarp();  // the histogram is cleared for the next query
     }
-}
-
-__device__ __forceinline__ void kahan_add(float& sum, float& comp, float term)
-{
-    const float y = term - comp;
-    const float t = sum + y;
-    comp = (t - sum) - y;
-    sum = t;
 }
 
 __global__ void __launch_bounds__(kThreads) fpfh_kernel(int64_t n_cap, const int32_t* __restrict__ valid,

@@ -16,8 +16,9 @@
 // at a small fraction of the FP32 rate and a warp instruction costs the same
 // with 1 or 32 active lanes, so each block first gathers the covariances of
 // its 32 queries in shared memory and then solves them one per lane.
-#include "kmx_internal.cuh"
-#include "grid_common.cuh"
+#include "search_common.cuh"
+
+using namespace kmxs;
 
 namespace {
 
@@ -25,7 +26,6 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kQPerWarp = 4;                    // queries per warp in the fill pass
 constexpr int kQPerBlock = kWarps * kQPerWarp;  // = 32, one per lane of the solving warp
-constexpr unsigned kFull = 0xffffffffu;
 
 struct NormScratch {
     int32_t* cnt;    // [n+1] |I(q)|
@@ -42,83 +42,6 @@ NormScratch carve(void* base, int64_t n, size_t* total)
     s.scan = a.take(kmx_scan_scratch_bytes(n));
     *total = kmx_align_up(a.used, 256);
     return s;
-}
-
-struct GridView {
-    const float4* __restrict__ sorted;
-    const int2* __restrict__ cells;
-    const unsigned long long* __restrict__ keys;
-    uint32_t T;
-    double inv_cell;
-    const int64_t* n_sorted;
-};
-
-struct Radii {
-    float rf2, rn2;     // FP32 squared radii
-    double rf2d, rn2d;  // FP64 squared radii, (double)r * (double)r
-};
-
-// Is a within radius of q?  FP32 unless the FP32 distance lies within 1e-5
-// (relative) of r^2, where the FP64 expression ((dx*dx + dy*dy) + dz*dz) <
-// r*r decides; FP32 error is far below that band, so the set is exact.
-__device__ __forceinline__ bool within(float4 a, float4 q, float d2, float r2, double r2d)
-{
-    if (fabsf(d2 - r2) > 1e-5f * r2) return d2 < r2;
-    double dx = __dsub_rn((double)a.x, (double)q.x);
-    double dy = __dsub_rn((double)a.y, (double)q.y);
-    double dz = __dsub_rn((double)a.z, (double)q.z);
-    double e = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-    return e < r2d;
-}
-
-// Lane l < 27 gets (start, count) of stencil cell l; returns the candidate
-// total and leaves each lane's exclusive prefix in *excl.
-__device__ __forceinline__ int stencil(const GridView& g, float4 q, int lane, int* start, int* excl)
-{
-    int cx, cy, cz;
-    kmx_cell_index(q.x, g.inv_cell, &cx);
-    kmx_cell_index(q.y, g.inv_cell, &cy);
-    kmx_cell_index(q.z, g.inv_cell, &cz);
-    int st = 0, ct = 0;
-    if (lane < 27) {
-        int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
-        int slot = kmx_hash_find(g.keys, g.T, kmx_pack_key(cx + dx, cy + dy, cz + dz));
-        if (slot >= 0) {
-            int2 c = g.cells[slot];
-            st = c.x;
-            ct = c.y;
-        }
-    }
-    int incl = ct;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += y;
-    }
-    *start = st;
-    *excl = incl - ct;
-    return __shfl_sync(kFull, incl, 31);
-}
-
-// Candidate number t -> position in the sorted point array.
-__device__ __forceinline__ int candidate(int t, int start, int excl)
-{
-    int lo = 0;
-#pragma unroll
-    for (int step = 16; step >= 1; step >>= 1) {
-        int e = __shfl_sync(kFull, excl, lo + step);
-        if (e <= t) lo += step;
-    }
-    int cs = __shfl_sync(kFull, start, lo);
-    int ce = __shfl_sync(kFull, excl, lo);
-    return cs + (t - ce);
-}
-
-__device__ __forceinline__ float warp_sum(float v)
-{
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
 }
 
 // Pass 1: |I(q)|, |P_normal| and the P_normal mean (relative to q).
@@ -164,73 +87,6 @@ __global__ void __launch_bounds__(kThreads) search_count(GridView g, Radii R, No
             s.mean[qi] = make_float4(sx * inv, sy * inv, sz * inv, __int_as_float(nn));
         }
     }
-}
-
-__device__ __forceinline__ void cross3(const double* a, const double* b, double* c)
-{
-    c[0] = a[1] * b[2] - a[2] * b[1];
-    c[1] = a[2] * b[0] - a[0] * b[2];
-    c[2] = a[0] * b[1] - a[1] * b[0];
-}
-
-// Eigenvalues l1 >= l2 >= l3 of a symmetric 3x3 matrix and a unit eigenvector
-// of l3.  Returns false if the matrix is a multiple of the identity.
-__device__ __forceinline__ bool eig_sym3(double a00, double a01, double a02, double a11, double a12, double a22,
-                                         double* l, double* nv)
-{
-    const double p1 = a01 * a01 + a02 * a02 + a12 * a12;
-    const double q = (a00 + a11 + a22) / 3.0;
-    const double b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
-    const double p2 = b00 * b00 + b11 * b11 + b22 * b22 + 2.0 * p1;
-    if (!(p2 > 0.0)) {
-        l[0] = l[1] = l[2] = q;
-        nv[0] = 0.0;
-        nv[1] = 0.0;
-        nv[2] = 1.0;
-        return false;
-    }
-    const double p = sqrt(p2 / 6.0);
-    const double det = b00 * (b11 * b22 - a12 * a12) - a01 * (a01 * b22 - a12 * a02) + a02 * (a01 * a12 - b11 * a02);
-    double r = det / (2.0 * p * p * p);
-    r = fmin(1.0, fmax(-1.0, r));
-    const double phi = acos(r) / 3.0;
-    l[0] = q + 2.0 * p * cos(phi);
-    l[2] = q + 2.0 * p * cos(phi + 2.0943951023931957);  // + 2 pi / 3
-    l[1] = 3.0 * q - l[0] - l[2];
-    const double r0[3] = {a00 - l[2], a01, a02};
-    const double r1[3] = {a01, a11 - l[2], a12};
-    const double r2[3] = {a02, a12, a22 - l[2]};
-    double c0[3], c1[3], c2[3];
-    cross3(r0, r1, c0);
-    cross3(r0, r2, c1);
-    cross3(r1, r2, c2);
-    const double n0 = c0[0] * c0[0] + c0[1] * c0[1] + c0[2] * c0[2];
-    const double n1 = c1[0] * c1[0] + c1[1] * c1[1] + c1[2] * c1[2];
-    const double n2 = c2[0] * c2[0] + c2[1] * c2[1] + c2[2] * c2[2];
-    double cx = c0[0], cy = c0[1], cz = c0[2], nb = n0;
-    if (n1 > nb) {
-        cx = c1[0];
-        cy = c1[1];
-        cz = c1[2];
-        nb = n1;
-    }
-    if (n2 > nb) {
-        cx = c2[0];
-        cy = c2[1];
-        cz = c2[2];
-        nb = n2;
-    }
-    if (!(nb > 0.0)) {
-        nv[0] = 0.0;
-        nv[1] = 0.0;
-        nv[2] = 1.0;
-        return true;
-    }
-    const double inv = 1.0 / sqrt(nb);
-    nv[0] = cx * inv;
-    nv[1] = cy * inv;
-    nv[2] = cz * inv;
-    return true;
 }
 
 struct NormOut {
@@ -346,26 +202,14 @@ __global__ void __launch_bounds__(kThreads) search_fill(GridView g, Radii R, Nor
             uint8_t flag = 0;
             float4 nout = make_float4(0.f, 0.f, 0.f, 0.f);
             if (mF >= o.tau_num && nN >= o.tau_num) {
-                const double inv = 1.0 / (double)nN;
-                const double m0 = (double)sm_mom[0][lane] * inv, m1 = (double)sm_mom[1][lane] * inv;
-                const double m2 = (double)sm_mom[2][lane] * inv;
-                const double c00 = (double)sm_mom[3][lane] * inv - m0 * m0, c01 = (double)sm_mom[4][lane] * inv - m0 * m1;
-                const double c02 = (double)sm_mom[5][lane] * inv - m0 * m2, c11 = (double)sm_mom[6][lane] * inv - m1 * m1;
-                const double c12 = (double)sm_mom[7][lane] * inv - m1 * m2, c22 = (double)sm_mom[8][lane] * inv - m2 * m2;
-                double l[3], nv[3];
-                eig_sym3(c00, c01, c02, c11, c12, c22, l, nv);
+                float mom[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) mom[i] = sm_mom[i][lane];
+                double plin;
                 flag |= 4;
-                if (l[0] > 0.0) {
-                    const double view = nv[0] * ((double)o.vp[0] - (double)sm_q[0][lane]) +
-                                        nv[1] * ((double)o.vp[1] - (double)sm_q[1][lane]) +
-                                        nv[2] * ((double)o.vp[2] - (double)sm_q[2][lane]);
-                    bool flip = view < 0.0;
-                    if (view == 0.0) flip = nv[0] != 0.0 ? nv[0] < 0.0 : (nv[1] != 0.0 ? nv[1] < 0.0 : nv[2] < 0.0);
-                    const double sgn = flip ? -1.0 : 1.0;
-                    const double plin = (l[0] - l[1]) / l[0];
-                    nout = make_float4((float)(sgn * nv[0]), (float)(sgn * nv[1]), (float)(sgn * nv[2]), (float)plin);
-                    if (plin < (double)o.tau_lin) flag |= 1;
-                }
+                if (normal_from_moments(mom, nN, sm_q[0][lane], sm_q[1][lane], sm_q[2][lane], o.vp, &nout, &plin) &&
+                    plin < (double)o.tau_lin)
+                    flag |= 1;
             }
             o.normal4[qi] = nout;
             o.flags[qi] = flag;

@@ -76,6 +76,7 @@ def library():
         "kmx_grid_free": (None, [vp]),
         "kmx_normals": (C.c_int, [vp, vp, C.POINTER(Params), vp, vp, vp, vp, i64, vp]),
         "kmx_fasterpfh": (C.c_int, [vp, vp, C.POINTER(Params), vp, vp, vp, vp, vp, vp, vp, vp]),
+        "kmx_fpfh_classic": (C.c_int, [vp, vp, C.POINTER(Params), vp, vp, vp, vp, vp, vp]),
         "kmx_match": (C.c_int, [vp, vp, vp, i64, vp, vp, vp, i64, vp, i32, vp, i64, vp]),
         "kmx_prune": (C.c_int, [vp, vp, i64, vp, vp, vp, i32, C.c_double, vp, vp, vp, vp, vp, vp]),
         "kmx_gnc": (C.c_int, [vp, vp, vp, vp, vp, i64, vp, vp, C.c_double, i32, C.c_double, C.c_double, vp, vp,
@@ -234,6 +235,27 @@ class Context:
                                            _ptr(offs), _ptr(nbr), _ptr(desc), _ptr(valid), _ptr(n_valid),
                                            _ptr(spfh)), "kmx_fasterpfh")
         return dict(desc=desc, valid=valid, n_valid=n_valid, spfh=spfh)
+
+    def fpfh_classic(self, grid: Grid, params: Params, want_spfh=False, out=None):
+        """kmx_fpfh_classic (the classic FPFH baseline of Sec. III-C).
+        Returns dict(normal4, flags, desc, valid, n_valid, spfh)."""
+        n = grid.n_cap
+        o = out or {}
+        dev = self.device
+        r = dict(
+            normal4=o.get("normal4", torch.empty((max(n, 1), 4), dtype=torch.float32, device=dev)),
+            flags=o.get("flags", torch.empty(max(n, 1), dtype=torch.uint8, device=dev)),
+            desc=o.get("desc", torch.empty((max(n, 1), DESC_STRIDE), dtype=torch.float32, device=dev)),
+            valid=o.get("valid", torch.empty(max(n, 1), dtype=torch.int32, device=dev)),
+            n_valid=o.get("n_valid", self._scalar()),
+            spfh=None,
+        )
+        if want_spfh:
+            r["spfh"] = o.get("spfh", torch.empty((max(n, 1), DESC_STRIDE), dtype=torch.float32, device=dev))
+        self._check(self.lib.kmx_fpfh_classic(self.h, grid.handle, C.byref(params), _ptr(r["normal4"]),
+                                              _ptr(r["flags"]), _ptr(r["desc"]), _ptr(r["valid"]),
+                                              _ptr(r["n_valid"]), _ptr(r["spfh"])), "kmx_fpfh_classic")
+        return r
 
     def match(self, desc_p, valid_p, np_cap, desc_q, valid_q, nq_cap, d_np=None, d_nq=None,
               mode=MATCH_FP32_EXACT, cap=None, out=None, n_out=None):

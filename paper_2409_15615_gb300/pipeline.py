@@ -41,6 +41,9 @@ class CloudState:
             n_valid=torch.zeros(1, dtype=torch.int64, device=dev),
         )
         self.grid = None
+        # "classic": the classic FPFH baseline (three searches, no filtering)
+        # in place of Faster-PFH; same outputs, so matching is unchanged
+        self.method = "faster"
 
     def features(self, n_raw: int, params: kmx.Params, raw: torch.Tensor | None = None):
         """Run a1-a6 on the first ``n_raw`` rows of ``raw`` (default: self.raw)."""
@@ -49,6 +52,10 @@ class CloudState:
         ctx.voxelize(src[:n_raw], params.voxel, cap=self.n_cap, out4=self.vox4, n_out=self.n_vox)
         # the grid is built once and then rebuilt in place: a pair allocates nothing
         self.grid = ctx.build_grid(self.vox4, params.r_fpfh, n_cap=self.n_cap, d_n=self.n_vox, reuse=self.grid)
+        if self.method == "classic":
+            b = self.bufs
+            ctx.fpfh_classic(self.grid, params, out=dict(normal4=b["normal4"], flags=b["flags"], **self.out))
+            return self
         b = ctx.normals(self.grid, params, self.nbr_cap, out=self.bufs)
         ctx.fasterpfh(self.grid, params, b["normal4"], b["flags"], b["offs"], b["nbr"], out=self.out)
         return self
