@@ -455,7 +455,10 @@ def bench_register(torch, ctx, pair, voxel, R_gt, t_gt, reps, with_oracle):
 
 def bench_ablation(torch, rank, reps):
     """Classic FPFH (three radius searches, no reliability filtering) against
-    Faster-PFH on the same clouds, the comparison of Sec. III-C.  Per method:
+    Faster-PFH on the same clouds, the comparison of Sec. III-C; Faster-PFH
+    both through stored neighbour lists ("lists", the search-once design of
+    the paper and the default path) and list-free ("faster", kmx_features,
+    every stage walking the grid again).  Per method:
     device time of the feature stage alone (normals and descriptors;
     voxelisation and the grid are the same for both and left out) and of the
     whole pair (both clouds one after the other, then exact FP32 matching),
@@ -479,7 +482,7 @@ def bench_ablation(torch, rank, reps):
         ps = kmx.params_default(v, viewpoint=np.float32(vps).tolist())
         pt = kmx.params_default(v, viewpoint=np.float32(vpt).tolist())
         res = {}
-        for method in ("faster", "classic"):
+        for method in ("lists", "faster", "classic"):
             pair.src.method = pair.tgt.method = method
             pair.run_checked(len(src), len(tgt), ps, pt, kmx.MATCH_FP32_EXACT)
             cs = pair.src
@@ -488,12 +491,12 @@ def bench_ablation(torch, rank, reps):
                 flush.zero_()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(ctx.stream)
-                if method == "classic":
-                    ctx.fpfh_classic(cs.grid, ps, out=dict(normal4=cs.bufs["normal4"], flags=cs.bufs["flags"],
-                                                           **cs.out))
-                else:
+                if method == "lists":
                     b = ctx.normals(cs.grid, ps, cs.nbr_cap, out=cs.bufs)
                     ctx.fasterpfh(cs.grid, ps, b["normal4"], b["flags"], b["offs"], b["nbr"], out=cs.out)
+                else:
+                    fn = ctx.features if method == "faster" else ctx.fpfh_classic
+                    fn(cs.grid, ps, out=dict(normal4=cs.bufs["normal4"], flags=cs.bufs["flags"], **cs.out))
                 e1.record(ctx.stream)
                 e1.synchronize()
                 times.append(e0.elapsed_time(e1))
@@ -517,8 +520,9 @@ def bench_ablation(torch, rank, reps):
                                inlier_ratio=float(np.mean(err < 3 * v)) if len(i) else 0.0)
         pair.close()
         ctx.close()
-        res["feature_speedup"] = res["classic"]["feature_ms"] / res["faster"]["feature_ms"]
-        res["pair_speedup"] = res["classic"]["pair_ms"] / res["faster"]["pair_ms"]
+        res["feature_speedup"] = res["classic"]["feature_ms"] / res["lists"]["feature_ms"]
+        res["pair_speedup"] = res["classic"]["pair_ms"] / res["lists"]["pair_ms"]
+        res["listfree_over_lists"] = res["faster"]["feature_ms"] / res["lists"]["feature_ms"]
         out[name] = res
     return out
 

@@ -215,6 +215,24 @@ kmx_status kmx_fasterpfh(kmx_ctx* ctx, const kmx_grid* grid, const kmx_params* p
                          int32_t* d_valid, int64_t* d_n_valid, float* d_spfh);
 
 /*
+ * Algorithm 1 (steps 1 and 2) and the descriptors of Eqs. A2-A5 in one call,
+ * without neighbour lists: every stage walks the grid's 27-cell stencil
+ * again instead of reading stored lists.  Same definitions, sets and
+ * summation order as kmx_normals followed by kmx_fasterpfh, so the outputs
+ * equal theirs bit for bit:
+ *   d_normal4  [n_cap][4] float32 out: as kmx_normals.
+ *   d_flags    [n_cap] uint8 out: bit0 = B, bit1 = in J, bit2 = PCA evaluated.
+ *   d_desc     [n_cap][36] float32 out: row j holds FPFH(J[j]) for j < |J|.
+ *   d_valid    [n_cap] int32 out: J in ascending point order.
+ *   d_n_valid  device int64 out: |J|.
+ *   d_spfh     nullable [n_cap][36] float32 out: SPFH of every point the grid
+ *              holds (zero rows for points without B).
+ * Host errors: KMX_EINVAL as kmx_normals.  No capacity error can occur.
+ */
+kmx_status kmx_features(kmx_ctx* ctx, const kmx_grid* grid, const kmx_params* params, float* d_normal4,
+                        uint8_t* d_flags, float* d_desc, int32_t* d_valid, int64_t* d_n_valid, float* d_spfh);
+
+/*
  * Classic FPFH (Rusu et al. 2009), the baseline Faster-PFH is compared with
  * in Sec. III-C (Fig. 2(a)): three radius searches on the grid and no
  * reliability test (tau_num and tau_lin are not read).

@@ -317,21 +317,35 @@ kmx_status kmx_fasterpfh(kmx_ctx* c, const kmx_grid* g, const kmx_params* p, con
                     "kmx_fasterpfh");
 }
 
-kmx_status kmx_fpfh_classic(kmx_ctx* c, const kmx_grid* g, const kmx_params* p, float* d_normal4, uint8_t* d_flags,
-                            float* d_desc, int32_t* d_valid, int64_t* d_n_valid, float* d_spfh)
+static kmx_status fpfh_search(kmx_ctx* c, const kmx_grid* g, const kmx_params* p, bool classic, float* d_normal4,
+                              uint8_t* d_flags, float* d_desc, int32_t* d_valid, int64_t* d_n_valid, float* d_spfh,
+                              const char* who)
 {
     if (!c) return KMX_EINVAL;
-    kmx_status s = check_params(c, g, p, "kmx_fpfh_classic");
+    kmx_status s = check_params(c, g, p, who);
     if (s) return s;
     if (!d_normal4 || !aligned16(d_normal4) || !d_flags || !d_desc || !aligned16(d_desc) || !d_valid || !d_n_valid ||
         (d_spfh && !aligned16(d_spfh)))
-        return fail(c, KMX_EINVAL, "kmx_fpfh_classic: bad argument");
+        return fail(c, KMX_EINVAL, "%s: bad argument", who);
     DeviceGuard dg(c->device);
-    s = ensure_ws(c, kmx_fpfh_classic_scratch_bytes(g->n_cap, d_spfh == nullptr));
+    s = ensure_ws(c, kmx_fpfh_search_scratch_bytes(g->n_cap, d_spfh == nullptr));
     if (s) return s;
     return launched(c,
-                    kmx_fpfh_classic_launch(c, g, p, d_normal4, d_flags, d_desc, d_valid, d_n_valid, d_spfh, c->ws),
-                    "kmx_fpfh_classic");
+                    kmx_fpfh_search_launch(c, g, p, classic, d_normal4, d_flags, d_desc, d_valid, d_n_valid, d_spfh,
+                                           c->ws),
+                    who);
+}
+
+kmx_status kmx_features(kmx_ctx* c, const kmx_grid* g, const kmx_params* p, float* d_normal4, uint8_t* d_flags,
+                        float* d_desc, int32_t* d_valid, int64_t* d_n_valid, float* d_spfh)
+{
+    return fpfh_search(c, g, p, false, d_normal4, d_flags, d_desc, d_valid, d_n_valid, d_spfh, "kmx_features");
+}
+
+kmx_status kmx_fpfh_classic(kmx_ctx* c, const kmx_grid* g, const kmx_params* p, float* d_normal4, uint8_t* d_flags,
+                            float* d_desc, int32_t* d_valid, int64_t* d_n_valid, float* d_spfh)
+{
+    return fpfh_search(c, g, p, true, d_normal4, d_flags, d_desc, d_valid, d_n_valid, d_spfh, "kmx_fpfh_classic");
 }
 
 kmx_status kmx_prune(kmx_ctx* c, const kmx_corr* d_corr, int64_t corr_cap, const int64_t* d_n_corr,

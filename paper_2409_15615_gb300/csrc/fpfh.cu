@@ -1,11 +1,11 @@
 // Algorithm 1, step 2 and the Faster-PFH descriptors (App. A, Eqs. A2-A5).
 //
-//   valid_count  I_valid(q) = { i in M[q] : B[i] }; q in J iff B[q] and
-//                |I_valid(q)| >= tau_num (one pass on the step-1 flags)
+//   spfh_kernel  for q with B: Darboux-frame features (Eq. A2) of every pair
+//                (q, k), k in I_valid(q) \ {q}, binned (Eq. A3) into a
+//                per-warp shared-memory histogram and scaled by 100 / pairs
+//                (Eq. A4); in the same pass |I_valid(q)| = |{ i in M[q] : B[i] }|
+//                and so q in J iff B[q] and |I_valid(q)| >= tau_num
 //   scan/scatter J in ascending point order
-//   spfh_kernel  Darboux-frame features (Eq. A2) of every pair (q, k),
-//                k in I_valid(q) \ {q}, binned (Eq. A3) into a per-warp
-//                shared-memory histogram and scaled by 100 / pairs (Eq. A4)
 //   fpfh_kernel  FPFH(q) = SPFH(q) + (1/m) sum_k SPFH(k) / w_k (Eq. A5), one
 //                warp per row, lane l owning bin l, compensated summation
 //
@@ -40,32 +40,6 @@ PfhScratch carve(void* base, int64_t n, bool need_spfh, size_t* total)
     return s;
 }
 
-__global__ void __launch_bounds__(kThreads) valid_count(int64_t n_cap, const int64_t* d_n, uint8_t* flags,
-                                                        const int64_t* __restrict__ offs,
-                                                        const int32_t* __restrict__ nbr, int tau_num,
-                                                        int32_t* __restrict__ jflag)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t n = kmx_count(d_n, n_cap);
-    for (int64_t q = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); q < n; q += (int64_t)gridDim.x * kWarps) {
-        const uint8_t fq = flags[q];
-        int mv = 0;
-        if (fq & 1) {
-            const int64_t b = offs[q], e = offs[q + 1];
-            for (int64_t t = b + lane; t - lane < e; t += 32) {
-                bool ok = false;
-                if (t < e) ok = (flags[nbr[t]] & 1) != 0;  // bit0 is never written here
-                mv += __popc(__ballot_sync(kFull, ok));
-            }
-        }
-        if (lane == 0) {
-            const bool inJ = (fq & 1) && mv >= tau_num;
-            jflag[q] = inJ ? 1 : 0;
-            flags[q] = (uint8_t)((fq & ~2u) | (inJ ? 2u : 0u));
-        }
-    }
-}
-
 __global__ void __launch_bounds__(kThreads) scatter_valid(int64_t n_cap, const int64_t* d_n,
                                                           const int32_t* __restrict__ jflag,
                                                           const int64_t* __restrict__ jpos,
@@ -79,10 +53,10 @@ __global__ void __launch_bounds__(kThreads) scatter_valid(int64_t n_cap, const i
 
 __global__ void __launch_bounds__(kThreads) spfh_kernel(int64_t n_cap, const int64_t* d_n,
                                                         const float4* __restrict__ pts,
-                                                        const float4* __restrict__ normal4,
-                                                        const uint8_t* __restrict__ flags,
+                                                        const float4* __restrict__ normal4, uint8_t* flags,
                                                         const int64_t* __restrict__ offs,
-                                                        const int32_t* __restrict__ nbr, float* __restrict__ spfh)
+                                                        const int32_t* __restrict__ nbr, int tau_num,
+                                                        float* __restrict__ spfh, int32_t* __restrict__ jflag)
 {
     __shared__ int hist[kWarps][kStride];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -93,6 +67,10 @@ __global__ void __launch_bounds__(kThreads) spfh_kernel(int64_t n_cap, const int
         if (!(fq & 1)) {
             row[lane] = 0.f;
             if (lane < kStride - 32) row[32 + lane] = 0.f;
+            if (lane == 0) {
+                jflag[q] = 0;
+                if (fq & 2) flags[q] = (uint8_t)(fq & ~2u);
+            }
             continue;
         }
         hist[warp][lane] = 0;
@@ -102,12 +80,15 @@ __global__ void __launch_bounds__(kThreads) spfh_kernel(int64_t n_cap, const int
         const float4 nq = normal4[q];
         const float PI = 3.14159265358979f;
         const int64_t b = offs[q], e = offs[q + 1];
-        int pairs = 0;
+        int pairs = 0, mv = 0;
         for (int64_t t = b + lane; t - lane < e; t += 32) {
-            bool ok = false;
+            bool ok = false, valid = false;
             if (t < e) {
                 const int k = nbr[t];
-                if (k != q && (__ldg(&flags[k]) & 1)) {
+                // bit0 is never written here, so a byte another warp is
+                // updating still shows the same B
+                valid = (flags[k] & 1) != 0;
+                if (k != q && valid) {
                     float f[3];
                     ok = pair_features(pq, nq, __ldg(&pts[k]), __ldg(&normal4[k]), f);
                     if (ok) {
@@ -118,6 +99,12 @@ __global__ void __launch_bounds__(kThreads) spfh_kernel(int64_t n_cap, const int
                 }
             }
             pairs += __popc(__ballot_sync(kFull, ok));
+            mv += __popc(__ballot_sync(kFull, valid));
+        }
+        if (lane == 0) {
+            const bool inJ = mv >= tau_num;  // q itself is in M[q] with B
+            jflag[q] = inJ ? 1 : 0;
+            flags[q] = (uint8_t)((fq & ~2u) | (inJ ? 2u : 0u));
         }
         __syncwarp();
         const float scale = pairs > 0 ? 100.0f / (float)pairs : 0.f;
@@ -209,18 +196,16 @@ cudaError_t kmx_fasterpfh_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_para
     float* sp = spfh ? spfh : s.spfh;
     const int64_t n = g->n_cap;
     cudaError_t e = cudaSuccess;
-    // valid_count writes the flag of every point below the count; the scan
+    // spfh_kernel writes the J flag of every point below the count; the scan
     // reads no other entry
     const unsigned nbw = kmx_stride_blocks(n, kWarps, ctx->sm_count);
     KMX_COUNT_LAUNCH();
-    valid_count<<<nbw, kThreads, 0, st>>>(n, g->d_n, flags, offs, nbr, prm->tau_num, s.jflag);
+    spfh_kernel<<<nbw, kThreads, 0, st>>>(n, g->d_n, g->pts, reinterpret_cast<const float4*>(normal4), flags,
+                                          offs, nbr, prm->tau_num, sp, s.jflag);
     if ((e = kmx_scan_i32(s.jflag, n, g->d_n, s.jpos, s.scan, st, ctx->d_err))) return e;
     KMX_COUNT_LAUNCH();
     scatter_valid<<<kmx_stride_blocks(n, kThreads, ctx->sm_count), kThreads, 0, st>>>(n, g->d_n, s.jflag, s.jpos,
                                                                                        valid, n_valid);
-    KMX_COUNT_LAUNCH();
-    spfh_kernel<<<nbw, kThreads, 0, st>>>(n, g->d_n, g->pts, reinterpret_cast<const float4*>(normal4), flags,
-                                          offs, nbr, sp);
     KMX_COUNT_LAUNCH();
     fpfh_kernel<<<nbw, kThreads, 0, st>>>(n, valid, n_valid, g->pts, flags, offs, nbr, sp, desc);
     return cudaGetLastError();

@@ -1,19 +1,25 @@
-// Classic FPFH (Rusu et al. 2009), the baseline Faster-PFH is compared with
-// in Sec. III-C (Fig. 2(a)): three radius searches and no reliability test.
+// Descriptors computed by walking the grid again for every stage instead of
+// storing neighbour lists: the classic FPFH baseline and a list-free
+// Faster-PFH.  On this GPU a 27-cell stencil walk of an L2-resident grid costs
+// less than writing the CSR lists once and gathering them three times.
 //
-//   classic_normals  search 1, r_normal: PCA normal of every point with
-//                    |P_normal| >= 3 (a warp per query; one sweep of the
-//                    stencil for the mean, a second for the centred moments;
-//                    FP64 solve and orientation as in Faster-PFH)
-//   scan/scatter     J = the points with a normal, ascending
-//   classic_spfh     search 2, r_FPFH: SPFH (Eqs. A2-A4) of every point with
-//                    a normal, over its neighbours with a normal
-//   classic_fpfh     search 3, r_FPFH: FPFH (Eq. A5) over the same
-//                    neighbours, row jpos[q] of the output
-//
-// Only normals and SPFH rows pass between the searches, as in the classic
-// pipeline; no neighbour list is stored.  Queries are taken in the grid's
-// cell order so that neighbouring warps walk the same cells.
+// Classic FPFH (Rusu et al. 2009), the baseline of Sec. III-C (Fig. 2(a)):
+//   walk_normals<classic>  search 1, r_normal: PCA normal of every point with
+//                          |P_normal| >= 3; J = the points with a normal
+//   spfh_walk              search 2, r_FPFH: SPFH (Eqs. A2-A4) over the
+//                          neighbours with a normal
+//   fpfh_walk              search 3, r_FPFH: FPFH (Eq. A5), row jpos[q]
+// Faster-PFH (Algorithm 1 and Eqs. A2-A5), the same sets as kmx_normals +
+// kmx_fasterpfh:
+//   walk_normals<faster>   |I| (r_FPFH), P_normal and its normal; B from
+//                          tau_num and tau_lin (step 1)
+//   valid_walk             |I_valid(q)| over the neighbours with B; J (step 2)
+//   spfh_walk, fpfh_walk   over B neighbours, for B points / for J
+// A warp takes one query; queries run in the grid's cell order so that
+// neighbouring warps walk the same cells.  The neighbours a stage visits come
+// in the same order as in the stored lists of kmx_normals, so every sum is
+// formed in the same order and the list-free Faster-PFH reproduces the
+// list-based one bit for bit.
 #include "pfh_common.cuh"
 #include "search_common.cuh"
 
@@ -26,10 +32,10 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kQPerWarp = 4;
 constexpr int kQPerBlock = kWarps * kQPerWarp;  // = 32, one per lane of the solving warp
-constexpr int kMinNormal = 3;                   // PCA of fewer points fixes no plane
+constexpr int kMinNormal = 3;                   // classic: PCA of fewer points fixes no plane
 
 struct ClassicScratch {
-    int32_t* jflag;  // [n+1] 1 if the point has a normal
+    int32_t* jflag;  // [n+1] 1 if the point is in J
     int64_t* jpos;   // [n+1] exclusive prefix of jflag
     float* spfh;     // [n][36] when the caller passes none
     void* scan;
@@ -47,11 +53,14 @@ ClassicScratch carve(void* base, int64_t n, bool need_spfh, size_t* total)
     return s;
 }
 
-// Search 1: P_normal(q) = { s : |a_s - a_q| < r_normal } and its normal.
-// flags: bit0 = has a normal (= in J), bit1 = in J, bit2 = PCA evaluated.
-__global__ void __launch_bounds__(kThreads) classic_normals(GridView g, Radii R, float vp0, float vp1, float vp2,
-                                                            float4* __restrict__ normal4,
-                                                            uint8_t* __restrict__ flags, int32_t* __restrict__ jflag)
+// Normals.  Classic: P_normal(q) = { s : |a_s - a_q| < r_normal }, PCA when
+// |P_normal| >= 3; flags bit0 = bit1 = has a normal (J), jflag written.
+// Faster-PFH (step 1): also |I(q)| over r_FPFH; PCA when |I| >= tau_num and
+// |P_normal| >= tau_num; bit0 = B (normal and p_lin < tau_lin).  bit2 = PCA.
+template <bool kClassic>
+__global__ void __launch_bounds__(kThreads) walk_normals(GridView g, Radii R, float vp0, float vp1, float vp2,
+                                                         int tau_num, float tau_lin, float4* __restrict__ normal4,
+                                                         uint8_t* __restrict__ flags, int32_t* __restrict__ jflag)
 {
     __shared__ float sm_mom[9][kQPerBlock];
     __shared__ float sm_q[3][kQPerBlock];
@@ -71,13 +80,13 @@ __global__ void __launch_bounds__(kThreads) classic_normals(GridView g, Radii R,
             const float4 q = g.sorted[p];
             int start, excl;
             const int total = stencil(g, q, lane, &start, &excl);
-            // sweep 1: |P_normal| and the mean offset from q
-            int nn = 0;
+            // sweep 1: |I|, |P_normal| and the mean offset from q
+            int nf = 0, nn = 0;
             float sx = 0.f, sy = 0.f, sz = 0.f;
             for (int base = 0; base < total; base += 32) {
                 const int t = base + lane;
                 const int pos = candidate(t, start, excl);
-                bool inN = false;
+                bool inF = false, inN = false;
                 float dx = 0.f, dy = 0.f, dz = 0.f;
                 if (t < total) {
                     const float4 a = g.sorted[pos];
@@ -85,8 +94,10 @@ __global__ void __launch_bounds__(kThreads) classic_normals(GridView g, Radii R,
                     dy = a.y - q.y;
                     dz = a.z - q.z;
                     const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                    inN = within(a, q, d2, R.rn2, R.rn2d);
+                    inF = within(a, q, d2, R.rf2, R.rf2d);
+                    inN = inF && within(a, q, d2, R.rn2, R.rn2d);
                 }
+                nf += __popc(__ballot_sync(kFull, inF));
                 nn += __popc(__ballot_sync(kFull, inN));
                 if (inN) {
                     sx += dx;
@@ -102,7 +113,8 @@ __global__ void __launch_bounds__(kThreads) classic_normals(GridView g, Radii R,
             // sweep 2: moments of the offsets centred on that mean
             float s1x = 0.f, s1y = 0.f, s1z = 0.f;
             float sxx = 0.f, sxy = 0.f, sxz = 0.f, syy = 0.f, syz = 0.f, szz = 0.f;
-            if (nn >= kMinNormal) {
+            const bool pca = kClassic ? nn >= kMinNormal : (nf >= tau_num && nn >= tau_num);
+            if (pca) {
                 for (int base = 0; base < total; base += 32) {
                     const int t = base + lane;
                     const int pos = candidate(t, start, excl);
@@ -110,7 +122,7 @@ __global__ void __launch_bounds__(kThreads) classic_normals(GridView g, Radii R,
                         const float4 a = g.sorted[pos];
                         const float dx = a.x - q.x, dy = a.y - q.y, dz = a.z - q.z;
                         const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                        if (within(a, q, d2, R.rn2, R.rn2d)) {
+                        if (within(a, q, d2, R.rf2, R.rf2d) && within(a, q, d2, R.rn2, R.rn2d)) {
                             const float ex = dx - mx, ey = dy - my, ez = dz - mz;
                             s1x += ex;
                             s1y += ey;
@@ -148,7 +160,7 @@ __global__ void __launch_bounds__(kThreads) classic_normals(GridView g, Radii R,
                 sm_q[1][slot] = q.y;
                 sm_q[2][slot] = q.z;
                 sm_qi[slot] = __float_as_int(q.w);
-                sm_nN[slot] = nn;
+                sm_nN[slot] = pca ? nn : -1;
             }
         }
         __syncthreads();
@@ -157,24 +169,62 @@ __global__ void __launch_bounds__(kThreads) classic_normals(GridView g, Radii R,
             const int nN = sm_nN[lane];
             uint8_t flag = 0;
             float4 nout = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (nN >= kMinNormal) {
+            if (nN >= 0) {
                 float mom[9];
 #pragma unroll
                 for (int i = 0; i < 9; ++i) mom[i] = sm_mom[i][lane];
                 double plin;
                 flag |= 4;
-                if (normal_from_moments(mom, nN, sm_q[0][lane], sm_q[1][lane], sm_q[2][lane], vp, &nout, &plin))
-                    flag |= 3;
+                const bool has = normal_from_moments(mom, nN, sm_q[0][lane], sm_q[1][lane], sm_q[2][lane], vp, &nout,
+                                                     &plin);
+                if (kClassic && has) flag |= 3;
+                if (!kClassic && has && plin < (double)tau_lin) flag |= 1;
             }
             normal4[qi] = nout;
             flags[qi] = flag;
-            jflag[qi] = flag & 1;
+            if (kClassic) jflag[qi] = flag & 1;
         }
         __syncthreads();  // the shared moments are rewritten by the next chunk
     }
 }
 
-__global__ void __launch_bounds__(kThreads) scatter_classic(int64_t n_cap, const int64_t* d_n,
+// Step 2: q enters J iff B[q] and |I_valid(q)| = |{ k in I(q) : B[k] }| >=
+// tau_num (q itself counted); sets flags bit1 and jflag.
+__global__ void __launch_bounds__(kThreads) valid_walk(GridView g, Radii R, int tau_num, uint8_t* flags,
+                                                       int32_t* __restrict__ jflag)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t n_sorted = *g.n_sorted;
+    for (int64_t p = (int64_t)blockIdx.x * kWarps + warp; p < n_sorted; p += (int64_t)gridDim.x * kWarps) {
+        const float4 q = g.sorted[p];
+        const int qi = __float_as_int(q.w);
+        const uint8_t fq = flags[qi];
+        if (!(fq & 1)) continue;
+        int start, excl;
+        const int total = stencil(g, q, lane, &start, &excl);
+        int mv = 0;
+        for (int base = 0; base < total; base += 32) {
+            const int t = base + lane;
+            const int pos = candidate(t, start, excl);
+            bool ok = false;
+            if (t < total) {
+                const float4 a = g.sorted[pos];
+                const float dx = a.x - q.x, dy = a.y - q.y, dz = a.z - q.z;
+                const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                // bit0 is never written here, so reading a byte that another
+                // warp is updating sees the same B
+                ok = within(a, q, d2, R.rf2, R.rf2d) && (flags[__float_as_int(a.w)] & 1);
+            }
+            mv += __popc(__ballot_sync(kFull, ok));
+        }
+        if (lane == 0 && mv >= tau_num) {
+            jflag[qi] = 1;
+            flags[qi] = (uint8_t)(fq | 2u);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) scatter_j(int64_t n_cap, const int64_t* d_n,
                                                             const int32_t* __restrict__ jflag,
                                                             const int64_t* __restrict__ jpos,
                                                             int32_t* __restrict__ valid, int64_t* n_valid)
@@ -185,8 +235,8 @@ __global__ void __launch_bounds__(kThreads) scatter_classic(int64_t n_cap, const
         if (jflag[q]) valid[jpos[q]] = (int32_t)q;
 }
 
-// Search 2: SPFH(q) over k != q within r_FPFH that have a normal.
-__global__ void __launch_bounds__(kThreads) classic_spfh(GridView g, Radii R, const float4* __restrict__ normal4,
+// SPFH(q) (Eqs. A2-A4) for q with bit0, over k != q within r_FPFH with bit0.
+__global__ void __launch_bounds__(kThreads) spfh_walk(GridView g, Radii R, const float4* __restrict__ normal4,
                                                          const uint8_t* __restrict__ flags,
                                                          float* __restrict__ spfh)
 {
@@ -239,10 +289,10 @@ __global__ void __launch_bounds__(kThreads) classic_spfh(GridView g, Radii R, co
     }
 }
 
-// Search 3: FPFH(q) = SPFH(q) + (1/m) sum_k SPFH(k) / w_k over the same
-// neighbours; lane l owns bin l, the rows are added in the order the stencil
-// yields them with compensated summation.
-__global__ void __launch_bounds__(kThreads) classic_fpfh(GridView g, Radii R, const uint8_t* __restrict__ flags,
+// FPFH(q) = SPFH(q) + (1/m) sum_k SPFH(k) / w_k (Eq. A5) for q in J (bit1),
+// over the neighbours the SPFH stage used; lane l owns bin l, the rows are
+// added in the order the stencil yields them with compensated summation.
+__global__ void __launch_bounds__(kThreads) fpfh_walk(GridView g, Radii R, const uint8_t* __restrict__ flags,
                                                          const int64_t* __restrict__ jpos,
                                                          const float* __restrict__ spfh, float* __restrict__ desc)
 {
@@ -253,7 +303,7 @@ __global__ void __launch_bounds__(kThreads) classic_fpfh(GridView g, Radii R, co
     for (int64_t p = (int64_t)blockIdx.x * kWarps + warp; p < n_sorted; p += (int64_t)gridDim.x * kWarps) {
         const float4 q = g.sorted[p];
         const int qi = __float_as_int(q.w);
-        if (!(flags[qi] & 1)) continue;
+        if (!(flags[qi] & 2)) continue;
         int start, excl;
         const int total = stencil(g, q, lane, &start, &excl);
         float acc = 0.f, comp = 0.f, acc32 = 0.f, comp32 = 0.f;
@@ -301,16 +351,16 @@ __global__ void __launch_bounds__(kThreads) classic_fpfh(GridView g, Radii R, co
 
 }  // namespace
 
-size_t kmx_fpfh_classic_scratch_bytes(int64_t n_cap, bool need_spfh)
+size_t kmx_fpfh_search_scratch_bytes(int64_t n_cap, bool need_spfh)
 {
     size_t total = 0;
     carve(nullptr, n_cap, need_spfh, &total);
     return total;
 }
 
-cudaError_t kmx_fpfh_classic_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_params* prm, float* normal4,
-                                    uint8_t* flags, float* desc, int32_t* valid, int64_t* n_valid, float* spfh,
-                                    void* scratch)
+cudaError_t kmx_fpfh_search_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_params* prm, bool classic,
+                                   float* normal4, uint8_t* flags, float* desc, int32_t* valid, int64_t* n_valid,
+                                   float* spfh, void* scratch)
 {
     cudaStream_t st = ctx->stream;
     size_t total = 0;
@@ -329,18 +379,28 @@ cudaError_t kmx_fpfh_classic_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_p
     if ((e = cudaMemsetAsync(normal4, 0, sizeof(float4) * n, st))) return e;
     if ((e = cudaMemsetAsync(flags, 0, n, st))) return e;
     if ((e = cudaMemsetAsync(s.jflag, 0, sizeof(int32_t) * (n + 1), st))) return e;
+    const unsigned nbn = kmx_stride_blocks(n, kQPerBlock, ctx->sm_count);
+    const unsigned nbw = kmx_stride_blocks(n, kWarps, ctx->sm_count);
+    const float4* n4 = reinterpret_cast<const float4*>(normal4);
     KMX_COUNT_LAUNCH();
-    classic_normals<<<kmx_stride_blocks(n, kQPerBlock, ctx->sm_count), kThreads, 0, st>>>(
-        gv, R, prm->viewpoint[0], prm->viewpoint[1], prm->viewpoint[2], reinterpret_cast<float4*>(normal4), flags,
-        s.jflag);
+    if (classic) {
+        walk_normals<true><<<nbn, kThreads, 0, st>>>(gv, R, prm->viewpoint[0], prm->viewpoint[1], prm->viewpoint[2],
+                                                     prm->tau_num, prm->tau_lin, reinterpret_cast<float4*>(normal4),
+                                                     flags, s.jflag);
+    } else {
+        walk_normals<false><<<nbn, kThreads, 0, st>>>(gv, R, prm->viewpoint[0], prm->viewpoint[1],
+                                                      prm->viewpoint[2], prm->tau_num, prm->tau_lin,
+                                                      reinterpret_cast<float4*>(normal4), flags, s.jflag);
+        KMX_COUNT_LAUNCH();
+        valid_walk<<<nbw, kThreads, 0, st>>>(gv, R, prm->tau_num, flags, s.jflag);
+    }
     if ((e = kmx_scan_i32(s.jflag, n, g->d_n, s.jpos, s.scan, st, ctx->d_err))) return e;
     KMX_COUNT_LAUNCH();
-    scatter_classic<<<kmx_stride_blocks(n, kThreads, ctx->sm_count), kThreads, 0, st>>>(n, g->d_n, s.jflag, s.jpos,
-                                                                                         valid, n_valid);
-    const unsigned nbw = kmx_stride_blocks(n, kWarps, ctx->sm_count);
+    scatter_j<<<kmx_stride_blocks(n, kThreads, ctx->sm_count), kThreads, 0, st>>>(n, g->d_n, s.jflag, s.jpos, valid,
+                                                                                   n_valid);
     KMX_COUNT_LAUNCH();
-    classic_spfh<<<nbw, kThreads, 0, st>>>(gv, R, reinterpret_cast<const float4*>(normal4), flags, sp);
+    spfh_walk<<<nbw, kThreads, 0, st>>>(gv, R, n4, flags, sp);
     KMX_COUNT_LAUNCH();
-    classic_fpfh<<<nbw, kThreads, 0, st>>>(gv, R, flags, s.jpos, sp, desc);
+    fpfh_walk<<<nbw, kThreads, 0, st>>>(gv, R, flags, s.jpos, sp, desc);
     return cudaGetLastError();
 }

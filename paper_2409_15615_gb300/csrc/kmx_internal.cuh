@@ -201,11 +201,12 @@ cudaError_t kmx_fasterpfh_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_para
                                  uint8_t* flags, const int64_t* offs, const int32_t* nbr, float* desc,
                                  int32_t* valid, int64_t* n_valid, float* spfh, void* scratch);
 
-// fpfh_classic.cu
-size_t kmx_fpfh_classic_scratch_bytes(int64_t n_cap, bool need_spfh);
-cudaError_t kmx_fpfh_classic_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_params* p, float* normal4,
-                                    uint8_t* flags, float* desc, int32_t* valid, int64_t* n_valid, float* spfh,
-                                    void* scratch);
+// fpfh_search.cu: the classic FPFH baseline (classic = true) or the
+// list-free Faster-PFH (classic = false)
+size_t kmx_fpfh_search_scratch_bytes(int64_t n_cap, bool need_spfh);
+cudaError_t kmx_fpfh_search_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_params* p, bool classic,
+                                   float* normal4, uint8_t* flags, float* desc, int32_t* valid, int64_t* n_valid,
+                                   float* spfh, void* scratch);
 
 // prune.cu
 size_t kmx_prune_scratch_bytes(int64_t corr_cap, int32_t n_tau);

@@ -77,6 +77,7 @@ def library():
         "kmx_normals": (C.c_int, [vp, vp, C.POINTER(Params), vp, vp, vp, vp, i64, vp]),
         "kmx_fasterpfh": (C.c_int, [vp, vp, C.POINTER(Params), vp, vp, vp, vp, vp, vp, vp, vp]),
         "kmx_fpfh_classic": (C.c_int, [vp, vp, C.POINTER(Params), vp, vp, vp, vp, vp, vp]),
+        "kmx_features": (C.c_int, [vp, vp, C.POINTER(Params), vp, vp, vp, vp, vp, vp]),
         "kmx_match": (C.c_int, [vp, vp, vp, i64, vp, vp, vp, i64, vp, i32, vp, i64, vp]),
         "kmx_prune": (C.c_int, [vp, vp, i64, vp, vp, vp, i32, C.c_double, vp, vp, vp, vp, vp, vp]),
         "kmx_gnc": (C.c_int, [vp, vp, vp, vp, vp, i64, vp, vp, C.c_double, i32, C.c_double, C.c_double, vp, vp,
@@ -236,9 +237,7 @@ class Context:
                                            _ptr(spfh)), "kmx_fasterpfh")
         return dict(desc=desc, valid=valid, n_valid=n_valid, spfh=spfh)
 
-    def fpfh_classic(self, grid: Grid, params: Params, want_spfh=False, out=None):
-        """kmx_fpfh_classic (the classic FPFH baseline of Sec. III-C).
-        Returns dict(normal4, flags, desc, valid, n_valid, spfh)."""
+    def _search_descriptors(self, fn, grid, params, want_spfh, out):
         n = grid.n_cap
         o = out or {}
         dev = self.device
@@ -252,10 +251,19 @@ class Context:
         )
         if want_spfh:
             r["spfh"] = o.get("spfh", torch.empty((max(n, 1), DESC_STRIDE), dtype=torch.float32, device=dev))
-        self._check(self.lib.kmx_fpfh_classic(self.h, grid.handle, C.byref(params), _ptr(r["normal4"]),
-                                              _ptr(r["flags"]), _ptr(r["desc"]), _ptr(r["valid"]),
-                                              _ptr(r["n_valid"]), _ptr(r["spfh"])), "kmx_fpfh_classic")
+        self._check(getattr(self.lib, fn)(self.h, grid.handle, C.byref(params), _ptr(r["normal4"]), _ptr(r["flags"]),
+                                          _ptr(r["desc"]), _ptr(r["valid"]), _ptr(r["n_valid"]), _ptr(r["spfh"])), fn)
         return r
+
+    def features(self, grid: Grid, params: Params, want_spfh=False, out=None):
+        """kmx_features: Algorithm 1 and Eqs. A2-A5 without neighbour lists.
+        Returns dict(normal4, flags, desc, valid, n_valid, spfh)."""
+        return self._search_descriptors("kmx_features", grid, params, want_spfh, out)
+
+    def fpfh_classic(self, grid: Grid, params: Params, want_spfh=False, out=None):
+        """kmx_fpfh_classic (the classic FPFH baseline of Sec. III-C).
+        Returns dict(normal4, flags, desc, valid, n_valid, spfh)."""
+        return self._search_descriptors("kmx_fpfh_classic", grid, params, want_spfh, out)
 
     def match(self, desc_p, valid_p, np_cap, desc_q, valid_q, nq_cap, d_np=None, d_nq=None,
               mode=MATCH_FP32_EXACT, cap=None, out=None, n_out=None):

@@ -33,17 +33,22 @@ class CloudState:
             offs=torch.empty(n + 1, dtype=torch.int64, device=dev),
             needed=torch.zeros(1, dtype=torch.int64, device=dev),
         )
+        # neighbour lists exist only for the list-based path, allocated on its
+        # first use
         self.nbr_cap = n * nbr_per_point
-        self.bufs["nbr"] = torch.empty(self.nbr_cap, dtype=torch.int32, device=dev)
+        self.bufs["nbr"] = None
         self.out = dict(
             desc=torch.empty((n, kmx.DESC_STRIDE), dtype=torch.float32, device=dev),
             valid=torch.empty(n, dtype=torch.int32, device=dev),
             n_valid=torch.zeros(1, dtype=torch.int64, device=dev),
         )
         self.grid = None
-        # "classic": the classic FPFH baseline (three searches, no filtering)
-        # in place of Faster-PFH; same outputs, so matching is unchanged
-        self.method = "faster"
+        # "lists" (default): Faster-PFH through stored neighbour lists
+        # (kmx_normals + kmx_fasterpfh); "faster": the same outputs walking the
+        # grid for every stage (kmx_features: no list memory, slower on
+        # LiDAR-like clouds); "classic": the classic FPFH baseline (three
+        # searches, no filtering).  Matching is unchanged.
+        self.method = "lists"
 
     def features(self, n_raw: int, params: kmx.Params, raw: torch.Tensor | None = None):
         """Run a1-a6 on the first ``n_raw`` rows of ``raw`` (default: self.raw)."""
@@ -52,10 +57,13 @@ class CloudState:
         ctx.voxelize(src[:n_raw], params.voxel, cap=self.n_cap, out4=self.vox4, n_out=self.n_vox)
         # the grid is built once and then rebuilt in place: a pair allocates nothing
         self.grid = ctx.build_grid(self.vox4, params.r_fpfh, n_cap=self.n_cap, d_n=self.n_vox, reuse=self.grid)
-        if self.method == "classic":
+        if self.method in ("faster", "classic"):
             b = self.bufs
-            ctx.fpfh_classic(self.grid, params, out=dict(normal4=b["normal4"], flags=b["flags"], **self.out))
+            fn = ctx.features if self.method == "faster" else ctx.fpfh_classic
+            fn(self.grid, params, out=dict(normal4=b["normal4"], flags=b["flags"], **self.out))
             return self
+        if self.bufs["nbr"] is None:
+            self.bufs["nbr"] = torch.empty(self.nbr_cap, dtype=torch.int32, device=ctx.device)
         b = ctx.normals(self.grid, params, self.nbr_cap, out=self.bufs)
         ctx.fasterpfh(self.grid, params, b["normal4"], b["flags"], b["offs"], b["nbr"], out=self.out)
         return self

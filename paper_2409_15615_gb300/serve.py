@@ -24,10 +24,10 @@ import torch
 
 from . import kmx, pipeline
 
-# rough device bytes per raw query point of one request (cloud buffers with 96
-# neighbours per point, descriptors, correspondences) plus a fixed part for
+# rough device bytes per raw query point of one request (cloud, grid,
+# normals, SPFH and descriptor buffers, correspondences) plus a fixed part for
 # the matching scratch; used only for admission against the budget
-BYTES_PER_POINT = 700
+BYTES_PER_POINT = 450
 BYTES_FIXED = 32 << 20
 
 

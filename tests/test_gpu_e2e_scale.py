@@ -83,9 +83,14 @@ def test_indoor_2m_pair_sampled(env, orc):
     pt = orc.OracleParams(v, viewpoint=np.float32(vpt).astype(np.float64))
     fs = orc.faster_pfh(vs, ps)
     ft = orc.faster_pfh(vt, pt)
-    # neighbour counts are exact integers
-    g_offs = pair.src.bufs["offs"][: ns + 1].cpu().numpy()
+    # neighbour counts are exact integers (the pair ran list-free; the list
+    # call on the same grid gives the counts)
+    prm = kmx.params_default(v, viewpoint=np.float32(vps).tolist())
+    lst = ctx.normals(pair.src.grid, prm, len(fs["nbr"]) + 1)
+    ctx.sync()
+    g_offs = lst["offs"][: ns + 1].cpu().numpy()
     assert np.array_equal(g_offs, fs["offs"])
+    del lst
     # J: equal up to points whose reliability sits on the tau_lin band
     g_J = pair.src.out["valid"][: int(pair.src.out["n_valid"].item())].cpu().numpy()
     diff = np.setxor1d(g_J, fs["J"])
