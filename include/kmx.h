@@ -63,6 +63,31 @@ typedef struct {
     float viewpoint[3]; /* normals are oriented toward this point */
 } kmx_params;
 
+/* Geometric suppression (Sec. III-B): ground removal before the descriptors.
+ * The paper uses Patchwork (Lim et al., RA-L 2021) without restating it;
+ * kmx_suppress_ground implements a stand-in with Patchwork's concentric zone
+ * model and region-wise ground plane fitting.  Sensor frame, z up; lengths in
+ * the cloud's units.  kmx_ground_params_default() sets: zone edges 2.7, 12.3,
+ * 22.1, 41.1, 80 m; rings 2, 4, 4, 4 and sectors 16, 32, 54, 32 per zone;
+ * quant_log2 8; z_limit 80; n_lpr 20; th_seeds = th_dist = 0.125; n_iter 3;
+ * max_slope 1 (45 degrees); max_ground_z -0.8 (a sensor ~1.7 m above the
+ * road); min_points 10; max_bin_points 65536. */
+typedef struct {
+    float zone_r[5];          /* zone edges, increasing, > 0 */
+    int32_t zone_rings[4];    /* equal-width rings per zone, 1..1024 */
+    int32_t zone_sectors[4];  /* sectors per zone (equal steps of the pseudo-angle), 1..1024 */
+    int32_t quant_log2;       /* the fit works on coordinates rounded to 2^-quant_log2, 0..12 */
+    float z_limit;            /* points with |z| >= z_limit are never ground */
+    int32_t n_lpr;            /* lowest points averaged into the seed height, 1..1024 */
+    float th_seeds;           /* seeds lie below that height + th_seeds */
+    float th_dist;            /* ground points lie within th_dist of the plane (orthogonally) */
+    int32_t n_iter;           /* refits, 0..64 */
+    float max_slope;          /* accept a plane with a^2 + b^2 <= max_slope^2 */
+    float max_ground_z;       /* accept a plane whose ground points' mean height is below this */
+    int32_t min_points;       /* bins with fewer members are not fitted (>= 3) */
+    int32_t max_bin_points;   /* bins with more members are not fitted (<= 65536) */
+} kmx_ground_params;
+
 /* Descriptor rows: 33 used floats padded to 36 (144 bytes). */
 #define KMX_DESC_DIM 33
 #define KMX_DESC_STRIDE 36
@@ -145,6 +170,53 @@ kmx_status kmx_check_timeout(kmx_ctx* ctx, int64_t polls);
  */
 kmx_status kmx_voxelize(kmx_ctx* ctx, const float* d_xyz, int64_t n_raw, int32_t stride, float voxel,
                         float* d_out4, int64_t cap, int64_t* d_n_out, int32_t* d_assign);
+
+/* kmx_voxelize with the number of input points in device memory, for a
+ * chain without host synchronisation (e.g. after kmx_suppress_ground):
+ * d_xyz holds n_cap rows of which the first *d_n_raw (clamped to n_cap) are
+ * voxelised; otherwise identical to kmx_voxelize (same output, order and
+ * errors).  d_n_raw is required. */
+kmx_status kmx_voxelize_count(kmx_ctx* ctx, const float* d_xyz, int64_t n_cap, const int64_t* d_n_raw,
+                              int32_t stride, float voxel, float* d_out4, int64_t cap, int64_t* d_n_out,
+                              int32_t* d_assign);
+
+/* Fill *out with the default suppression parameters (see kmx_ground_params).
+ * KMX_EINVAL if out is NULL. */
+kmx_status kmx_ground_params_default(kmx_ground_params* out);
+
+/* Number of bins of the zone model, or -1 if the parameters are invalid. */
+int32_t kmx_ground_bins(const kmx_ground_params* params);
+
+/*
+ * Geometric suppression (Sec. III-B): removes ground points before the
+ * descriptors, so that the many mutually consistent but wrong matches on the
+ * ground plane do not dominate pruning, and fewer points reach the later
+ * steps.  The stand-in for the paper's Patchwork, per point and per bin of
+ * the zone model:
+ *   bin       zone by x^2 + y^2 against the zone edges, ring by the radius,
+ *             sector by the pseudo-angle (quadrant + |y| / (|x| + |y|)).
+ *   seeds     members below (sum of the n_lpr lowest quantised heights) / k
+ *             + th_seeds, decided in integers.
+ *   plane     least-squares height field z = a x + b y + c over the seeds
+ *             (exact integer moments, FP64 Cramer's rule), refitted n_iter
+ *             times over the members within th_dist of the plane.
+ *   accept    a^2 + b^2 <= max_slope^2 and the ground members' mean height
+ *             below max_ground_z; those members are removed.
+ * Every decision is exact or a fixed sequence of IEEE FP64 operations, so the
+ * result is independent of thread order (and equals the CPU oracle's).
+ *   d_xyz     [n][stride] float32 points (stride 3 or 4), sensor frame.
+ *   d_out     [n][stride] float32 out, distinct from d_xyz: the kept points
+ *             in input order, d_n_out of them.
+ *   d_n_out   device int64 out: number of kept points.
+ *   d_ground  nullable [n] uint8 out: 1 for removed (ground) points.
+ *   d_planes  nullable [kmx_ground_bins()][4] double out per bin: a, b, c
+ *             (quantised units) and a status: 0 too few or too many members,
+ *             1 no fit, 2 too steep, 3 too high, 4 ground.
+ * Host errors: KMX_EINVAL for invalid parameters or arguments.
+ */
+kmx_status kmx_suppress_ground(kmx_ctx* ctx, const float* d_xyz, int64_t n, int32_t stride,
+                               const kmx_ground_params* params, float* d_out, int64_t* d_n_out, uint8_t* d_ground,
+                               double* d_planes);
 
 /*
  * Hashed uniform grid over a cloud, the search structure that stands in for

@@ -205,8 +205,67 @@ kmx_status kmx_voxelize(kmx_ctx* c, const float* d_xyz, int64_t n_raw, int32_t s
     DeviceGuard g(c->device);
     kmx_status s = ensure_ws(c, kmx_voxelize_scratch_bytes(n_raw));
     if (s) return s;
-    return launched(c, kmx_voxelize_launch(c, d_xyz, n_raw, stride, voxel, d_out4, cap, d_n_out, d_assign, c->ws),
+    return launched(c,
+                    kmx_voxelize_launch(c, d_xyz, n_raw, nullptr, stride, voxel, d_out4, cap, d_n_out, d_assign,
+                                        c->ws),
                     "kmx_voxelize");
+}
+
+kmx_status kmx_voxelize_count(kmx_ctx* c, const float* d_xyz, int64_t n_cap, const int64_t* d_n_raw, int32_t stride,
+                              float voxel, float* d_out4, int64_t cap, int64_t* d_n_out, int32_t* d_assign)
+{
+    if (!c) return KMX_EINVAL;
+    if (n_cap < 0 || n_cap > INT32_MAX - 1 || !d_n_raw || (stride != 3 && stride != 4) || !(voxel > 0.0f) ||
+        !isfinite(voxel) || cap < 0 || !d_n_out || (n_cap > 0 && (!d_xyz || !d_out4)) || (d_out4 && !aligned16(d_out4)))
+        return fail(c, KMX_EINVAL, "kmx_voxelize_count: bad argument");
+    DeviceGuard g(c->device);
+    kmx_status s = ensure_ws(c, kmx_voxelize_scratch_bytes(n_cap));
+    if (s) return s;
+    return launched(c,
+                    kmx_voxelize_launch(c, d_xyz, n_cap, d_n_raw, stride, voxel, d_out4, cap, d_n_out, d_assign,
+                                        c->ws),
+                    "kmx_voxelize_count");
+}
+
+kmx_status kmx_ground_params_default(kmx_ground_params* out)
+{
+    if (!out) return KMX_EINVAL;
+    const float zr[5] = {2.7f, 12.3f, 22.1f, 41.1f, 80.0f};
+    const int32_t rings[4] = {2, 4, 4, 4}, sectors[4] = {16, 32, 54, 32};
+    for (int k = 0; k < 5; ++k) out->zone_r[k] = zr[k];
+    for (int k = 0; k < 4; ++k) {
+        out->zone_rings[k] = rings[k];
+        out->zone_sectors[k] = sectors[k];
+    }
+    out->quant_log2 = 8;
+    out->z_limit = 80.0f;
+    out->n_lpr = 20;
+    out->th_seeds = 0.125f;
+    out->th_dist = 0.125f;
+    out->n_iter = 3;
+    out->max_slope = 1.0f;
+    out->max_ground_z = -0.8f;
+    out->min_points = 10;
+    out->max_bin_points = 65536;
+    return KMX_OK;
+}
+
+int32_t kmx_ground_bins(const kmx_ground_params* p) { return kmx_ground_bins_of(p); }
+
+kmx_status kmx_suppress_ground(kmx_ctx* c, const float* d_xyz, int64_t n, int32_t stride, const kmx_ground_params* p,
+                               float* d_out, int64_t* d_n_out, uint8_t* d_ground, double* d_planes)
+{
+    if (!c) return KMX_EINVAL;
+    const int nb = kmx_ground_bins_of(p);
+    if (nb < 0) return fail(c, KMX_EINVAL, "kmx_suppress_ground: bad parameters");
+    if (n < 0 || n > INT32_MAX - 1 || (stride != 3 && stride != 4) || !d_n_out || (n > 0 && (!d_xyz || !d_out)) ||
+        (n > 0 && d_out == d_xyz))
+        return fail(c, KMX_EINVAL, "kmx_suppress_ground: bad argument");
+    DeviceGuard g(c->device);
+    kmx_status s = ensure_ws(c, kmx_ground_scratch_bytes(n, nb));
+    if (s) return s;
+    return launched(c, kmx_ground_launch(c, d_xyz, n, stride, p, d_out, d_n_out, d_ground, d_planes, c->ws),
+                    "kmx_suppress_ground");
 }
 
 kmx_status kmx_build_grid(kmx_ctx* c, const float* d_xyz4, int64_t n_cap, const int64_t* d_n, float cell,

@@ -181,8 +181,9 @@ cudaError_t kmx_scan_i32(const int32_t* in, int64_t n, const int64_t* d_n, int64
 
 // voxel.cu
 size_t kmx_voxelize_scratch_bytes(int64_t n_raw);
-cudaError_t kmx_voxelize_launch(kmx_ctx* ctx, const float* xyz, int64_t n_raw, int stride, float v, float* out4,
-                                int64_t cap, int64_t* n_out, int32_t* assign, void* scratch);
+// d_n: nullable device count of the points actually present (<= n_raw)
+cudaError_t kmx_voxelize_launch(kmx_ctx* ctx, const float* xyz, int64_t n_raw, const int64_t* d_n, int stride, float v,
+                                float* out4, int64_t cap, int64_t* n_out, int32_t* assign, void* scratch);
 
 // grid.cu
 size_t kmx_grid_bytes(int64_t n_cap, uint32_t* table_size);
@@ -200,6 +201,13 @@ size_t kmx_fasterpfh_scratch_bytes(int64_t n_cap, bool need_spfh);
 cudaError_t kmx_fasterpfh_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_params* p, const float* normal4,
                                  uint8_t* flags, const int64_t* offs, const int32_t* nbr, float* desc,
                                  int32_t* valid, int64_t* n_valid, float* spfh, void* scratch);
+
+// ground.cu: geometric suppression; kmx_ground_bins_of is -1 for invalid
+// parameters
+int kmx_ground_bins_of(const kmx_ground_params* p);
+size_t kmx_ground_scratch_bytes(int64_t n, int nb);
+cudaError_t kmx_ground_launch(kmx_ctx* ctx, const float* xyz, int64_t n, int stride, const kmx_ground_params* prm,
+                              float* out, int64_t* n_out, uint8_t* ground, double* planes, void* scratch);
 
 // fpfh_search.cu: the classic FPFH baseline (classic = true) or the
 // list-free Faster-PFH (classic = false)

@@ -67,11 +67,12 @@ __device__ __forceinline__ bool voxel_index(float x, double v, int* k)
     return true;
 }
 
-__global__ void __launch_bounds__(kThreads) vox_insert(const float* __restrict__ xyz, int64_t n, int stride,
-                                                       double v, VoxScratch s, unsigned int* err)
+__global__ void __launch_bounds__(kThreads) vox_insert(const float* __restrict__ xyz, int64_t n_cap,
+                                                       const int64_t* d_n, int stride, double v, VoxScratch s,
+                                                       unsigned int* err)
 {
     int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (r >= n) return;
+    if (r >= kmx_count(d_n, n_cap)) return;
     const float* p = xyz + r * stride;
     int kx, ky, kz;
     bool ok = voxel_index(p[0], v, &kx) & voxel_index(p[1], v, &ky) & voxel_index(p[2], v, &kz);
@@ -90,18 +91,18 @@ __global__ void __launch_bounds__(kThreads) vox_insert(const float* __restrict__
     atomicAdd(&s.vcnt[slot], 1);
 }
 
-__global__ void __launch_bounds__(kThreads) vox_first_flag(int64_t n, VoxScratch s)
+__global__ void __launch_bounds__(kThreads) vox_first_flag(int64_t n_cap, const int64_t* d_n, VoxScratch s)
 {
     int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (r >= n) return;
+    if (r >= kmx_count(d_n, n_cap)) return;
     int slot = s.pslot[r];
     s.flag[r] = (slot >= 0 && s.vmin[slot] == (int32_t)r) ? 1 : 0;
 }
 
 // For each first member: number its voxel, record the member count per output
 // voxel (reusing `flag` as the count array), publish the voxel count.
-__global__ void __launch_bounds__(kThreads) vox_number(int64_t n, VoxScratch s, int64_t cap, int64_t* n_out,
-                                                       unsigned int* err)
+__global__ void __launch_bounds__(kThreads) vox_number(int64_t n, const int64_t* d_n, VoxScratch s, int64_t cap,
+                                                       int64_t* n_out, unsigned int* err)
 {
     int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (r == 0) {
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(kThreads) vox_number(int64_t n, VoxScratch s, 
         *n_out = tot;
         if (tot > cap) kmx_raise(err, KMX_DERR_CAPACITY);
     }
-    if (r >= n) return;
+    if (r >= kmx_count(d_n, n)) return;
     if (s.oidx[r + 1] == s.oidx[r]) return;  // not a first member
     int slot = s.pslot[r];
     int64_t o = s.oidx[r];
@@ -117,10 +118,11 @@ __global__ void __launch_bounds__(kThreads) vox_number(int64_t n, VoxScratch s, 
     s.cursor[o] = s.vcnt[slot];  // temporarily: count per output voxel
 }
 
-__global__ void __launch_bounds__(kThreads) vox_scatter(int64_t n, VoxScratch s, int32_t* __restrict__ assign)
+__global__ void __launch_bounds__(kThreads) vox_scatter(int64_t n, const int64_t* d_n, VoxScratch s,
+                                                        int32_t* __restrict__ assign)
 {
     int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (r >= n) return;
+    if (r >= kmx_count(d_n, n)) return;
     int slot = s.pslot[r];
     if (slot < 0) return;
     int32_t o = s.vout[slot];
@@ -323,8 +325,8 @@ size_t kmx_voxelize_scratch_bytes(int64_t n_raw)
     return total;
 }
 
-cudaError_t kmx_voxelize_launch(kmx_ctx* ctx, const float* xyz, int64_t n, int stride, float v, float* out4,
-                                int64_t cap, int64_t* n_out, int32_t* assign, void* scratch)
+cudaError_t kmx_voxelize_launch(kmx_ctx* ctx, const float* xyz, int64_t n, const int64_t* d_n, int stride, float v,
+                                float* out4, int64_t cap, int64_t* n_out, int32_t* assign, void* scratch)
 {
     cudaStream_t st = ctx->stream;
     size_t total = 0;
@@ -338,19 +340,19 @@ cudaError_t kmx_voxelize_launch(kmx_ctx* ctx, const float* xyz, int64_t n, int s
     }
     unsigned nb = kmx_blocks(n, kThreads);
     KMX_COUNT_LAUNCH();
-    vox_insert<<<nb, kThreads, 0, st>>>(xyz, n, stride, (double)v, s, ctx->d_err);
+    vox_insert<<<nb, kThreads, 0, st>>>(xyz, n, d_n, stride, (double)v, s, ctx->d_err);
     KMX_COUNT_LAUNCH();
-    vox_first_flag<<<nb, kThreads, 0, st>>>(n, s);
-    if ((e = kmx_scan_i32(s.flag, n, nullptr, s.oidx, s.scan, st, ctx->d_err))) return e;
+    vox_first_flag<<<nb, kThreads, 0, st>>>(n, d_n, s);
+    if ((e = kmx_scan_i32(s.flag, n, d_n, s.oidx, s.scan, st, ctx->d_err))) return e;
     if ((e = cudaMemsetAsync(s.cursor, 0, sizeof(int32_t) * (n + 1), st))) return e;
     KMX_COUNT_LAUNCH();
-    vox_number<<<nb, kThreads, 0, st>>>(n, s, cap, n_out, ctx->d_err);
+    vox_number<<<nb, kThreads, 0, st>>>(n, d_n, s, cap, n_out, ctx->d_err);
     // member offsets per output voxel: scan of the counts parked in `cursor`
     if ((e = cudaMemcpyAsync(s.flag, s.cursor, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st))) return e;
     if ((e = kmx_scan_i32(s.flag, n, n_out, s.vstart, s.scan, st, ctx->d_err))) return e;
     if ((e = cudaMemsetAsync(s.cursor, 0, sizeof(int32_t) * (n + 1), st))) return e;
     KMX_COUNT_LAUNCH();
-    vox_scatter<<<nb, kThreads, 0, st>>>(n, s, assign);
+    vox_scatter<<<nb, kThreads, 0, st>>>(n, d_n, s, assign);
     KMX_COUNT_LAUNCH();
     vox_centroid<<<kmx_blocks(n, kCentroidThreads), kCentroidThreads, 0, st>>>(xyz, stride, n, s,
                                                                                     reinterpret_cast<float4*>(out4), cap);

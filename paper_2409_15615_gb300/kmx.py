@@ -42,6 +42,14 @@ class Params(C.Structure):
                 ("tau_lin", C.c_float), ("hist_bins", C.c_int32), ("viewpoint", C.c_float * 3)]
 
 
+class GroundParams(C.Structure):
+    """kmx_ground_params (geometric suppression stand-in, Sec. III-B)."""
+    _fields_ = [("zone_r", C.c_float * 5), ("zone_rings", C.c_int32 * 4), ("zone_sectors", C.c_int32 * 4),
+                ("quant_log2", C.c_int32), ("z_limit", C.c_float), ("n_lpr", C.c_int32), ("th_seeds", C.c_float),
+                ("th_dist", C.c_float), ("n_iter", C.c_int32), ("max_slope", C.c_float),
+                ("max_ground_z", C.c_float), ("min_points", C.c_int32), ("max_bin_points", C.c_int32)]
+
+
 class Corr(C.Structure):
     _fields_ = [("i", C.c_int32), ("j", C.c_int32), ("d1", C.c_float), ("d2", C.c_float)]
 
@@ -78,6 +86,10 @@ def library():
         "kmx_fasterpfh": (C.c_int, [vp, vp, C.POINTER(Params), vp, vp, vp, vp, vp, vp, vp, vp]),
         "kmx_fpfh_classic": (C.c_int, [vp, vp, C.POINTER(Params), vp, vp, vp, vp, vp, vp]),
         "kmx_features": (C.c_int, [vp, vp, C.POINTER(Params), vp, vp, vp, vp, vp, vp]),
+        "kmx_voxelize_count": (C.c_int, [vp, vp, i64, vp, i32, f32, vp, i64, vp, vp]),
+        "kmx_ground_params_default": (C.c_int, [C.POINTER(GroundParams)]),
+        "kmx_ground_bins": (C.c_int32, [C.POINTER(GroundParams)]),
+        "kmx_suppress_ground": (C.c_int, [vp, vp, i64, i32, C.POINTER(GroundParams), vp, vp, vp, vp]),
         "kmx_match": (C.c_int, [vp, vp, vp, i64, vp, vp, vp, i64, vp, i32, vp, i64, vp]),
         "kmx_prune": (C.c_int, [vp, vp, i64, vp, vp, vp, i32, C.c_double, vp, vp, vp, vp, vp, vp]),
         "kmx_gnc": (C.c_int, [vp, vp, vp, vp, vp, i64, vp, vp, C.c_double, i32, C.c_double, C.c_double, vp, vp,
@@ -93,6 +105,21 @@ def library():
 
 def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def ground_params_default(**overrides) -> GroundParams:
+    """kmx_ground_params_default, then the given fields replaced."""
+    p = GroundParams()
+    st = library().kmx_ground_params_default(C.byref(p))
+    if st:
+        raise KmxError(st, "kmx_ground_params_default")
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def ground_bins(p: GroundParams) -> int:
+    return int(library().kmx_ground_bins(C.byref(p)))
 
 
 def params_default(voxel: float, viewpoint=(0.0, 0.0, 0.0)) -> Params:
@@ -175,6 +202,34 @@ class Context:
         return torch.zeros(1, dtype=torch.int64, device=self.device)
 
     # -- stages -----------------------------------------------------------
+
+    def suppress_ground(self, xyz: torch.Tensor, params: GroundParams | None = None, out=None, n_out=None,
+                        want_ground=False, want_planes=False):
+        """kmx_suppress_ground.  Returns dict(out [n, stride] (kept points
+        first), n_out device int64[1], ground uint8[n] | None, planes
+        float64[bins, 4] | None)."""
+        params = params if params is not None else ground_params_default()
+        n, stride = xyz.shape
+        out = torch.empty((max(n, 1), stride), dtype=torch.float32, device=self.device) if out is None else out
+        n_out = self._scalar() if n_out is None else n_out
+        ground = torch.empty(max(n, 1), dtype=torch.uint8, device=self.device) if want_ground else None
+        planes = None
+        if want_planes:
+            planes = torch.empty((max(ground_bins(params), 1), 4), dtype=torch.float64, device=self.device)
+        self._check(self.lib.kmx_suppress_ground(self.h, _ptr(xyz), n, stride, C.byref(params), _ptr(out),
+                                                 _ptr(n_out), _ptr(ground), _ptr(planes)), "kmx_suppress_ground")
+        return dict(out=out, n_out=n_out, ground=ground, planes=planes)
+
+    def voxelize_count(self, xyz: torch.Tensor, d_n, voxel: float, cap: int | None = None, out4=None, n_out=None):
+        """kmx_voxelize_count: the first d_n (device int64) rows of xyz.
+        Returns (out4 [cap, 4], n_out device int64[1])."""
+        n, stride = xyz.shape
+        cap = n if cap is None else cap
+        out4 = torch.empty((max(cap, 1), 4), dtype=torch.float32, device=self.device) if out4 is None else out4
+        n_out = self._scalar() if n_out is None else n_out
+        self._check(self.lib.kmx_voxelize_count(self.h, _ptr(xyz), n, _ptr(d_n), stride, float(voxel), _ptr(out4),
+                                                cap, _ptr(n_out), None), "kmx_voxelize_count")
+        return out4, n_out
 
     def voxelize(self, xyz: torch.Tensor, voxel: float, cap: int | None = None, out4=None, n_out=None,
                  assign=None):

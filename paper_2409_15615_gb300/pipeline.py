@@ -49,12 +49,25 @@ class CloudState:
         # LiDAR-like clouds); "classic": the classic FPFH baseline (three
         # searches, no filtering).  Matching is unchanged.
         self.method = "lists"
+        # geometric suppression (Sec. III-B) before voxelisation when set to
+        # a kmx.GroundParams: ground points are removed on the device and the
+        # voxeliser reads the kept count from device memory
+        self.suppress = None
+        self.kept = None
+        self.n_kept = torch.zeros(1, dtype=torch.int64, device=dev)
 
     def features(self, n_raw: int, params: kmx.Params, raw: torch.Tensor | None = None):
         """Run a1-a6 on the first ``n_raw`` rows of ``raw`` (default: self.raw)."""
         ctx = self.ctx
         src = self.raw if raw is None else raw
-        ctx.voxelize(src[:n_raw], params.voxel, cap=self.n_cap, out4=self.vox4, n_out=self.n_vox)
+        if self.suppress is not None:
+            if self.kept is None or self.kept.shape[1] != src.shape[1]:
+                self.kept = torch.empty((self.n_cap, src.shape[1]), dtype=torch.float32, device=ctx.device)
+            ctx.suppress_ground(src[:n_raw], self.suppress, out=self.kept, n_out=self.n_kept)
+            ctx.voxelize_count(self.kept[:n_raw], self.n_kept, params.voxel, cap=self.n_cap, out4=self.vox4,
+                               n_out=self.n_vox)
+        else:
+            ctx.voxelize(src[:n_raw], params.voxel, cap=self.n_cap, out4=self.vox4, n_out=self.n_vox)
         # the grid is built once and then rebuilt in place: a pair allocates nothing
         self.grid = ctx.build_grid(self.vox4, params.r_fpfh, n_cap=self.n_cap, d_n=self.n_vox, reuse=self.grid)
         if self.method in ("faster", "classic"):
