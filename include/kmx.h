@@ -76,7 +76,8 @@ typedef struct {
     float zone_r[5];          /* zone edges, increasing, > 0 */
     int32_t zone_rings[4];    /* equal-width rings per zone, 1..1024 */
     int32_t zone_sectors[4];  /* sectors per zone (equal steps of the pseudo-angle), 1..1024 */
-    int32_t quant_log2;       /* the fit works on coordinates rounded to 2^-quant_log2, 0..12 */
+    int32_t quant_log2;       /* the fit works on coordinates rounded to 2^-quant_log2, 0..12;
+                                 zone_r[4] and z_limit times 2^quant_log2 must not exceed 32767 */
     float z_limit;            /* points with |z| >= z_limit are never ground */
     int32_t n_lpr;            /* lowest points averaged into the seed height, 1..1024 */
     float th_seeds;           /* seeds lie below that height + th_seeds */

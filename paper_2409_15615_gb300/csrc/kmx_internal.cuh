@@ -155,7 +155,7 @@ struct kmx_arena {
 
 // One-time, per-device set-up actions (function attributes): bit `bit` of a
 // per-device mask records that fn() succeeded on the current device.
-enum { kmx_attr_fp32_tiles = 0, kmx_attr_tc_topk = 1, kmx_attr_fp32_bulk = 2, kmx_attr_gnc = 3 };
+enum { kmx_attr_fp32_tiles = 0, kmx_attr_tc_topk = 1, kmx_attr_fp32_bulk = 2, kmx_attr_gnc = 3, kmx_attr_ground = 4 };
 template <typename F>
 inline cudaError_t kmx_once_per_device(int bit, F fn)
 {

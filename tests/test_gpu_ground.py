@@ -36,6 +36,25 @@ def _disc(rmax=30.0, step=0.3, z=-1.73, f=None):
     return np.stack([x, y, zz], 1).astype(np.float32)
 
 
+def _edges():
+    """Points on and next to every ring edge and on the sector edges that are
+    exact in both precisions (axes, diagonals): the index decisions the GPU
+    takes in FP32 must fall back to the FP64 definition there."""
+    zr = (2.7, 12.3, 22.1, 41.1, 80.0)
+    rings = (2, 4, 4, 4)
+    radii = []
+    for k in range(4):
+        for j in range(rings[k] + 1):
+            r = np.float32(zr[k] + j * (zr[k + 1] - zr[k]) / rings[k])
+            radii += [np.nextafter(r, np.float32(0)), r, np.nextafter(r, np.float32(100))]
+    ang = np.concatenate([np.arange(8) * np.pi / 4, np.random.default_rng(2).uniform(0, 2 * np.pi, 40)])
+    pts = np.array([[r * np.cos(a), r * np.sin(a), -1.73] for r in radii for a in ang], np.float32)
+    d = np.float32(7.0)
+    exact = np.array([[d, d, -1.73], [-d, d, -1.73], [-d, -d, -1.73], [d, -d, -1.73], [d, 0, -1.73], [0, d, -1.73],
+                      [-d, 0, -1.73], [0, -d, -1.73], [-0.0, d, -1.73], [d, -0.0, -1.73]], np.float32)
+    return np.concatenate([pts, exact, _disc(step=0.5)])
+
+
 def _cases():
     rng = np.random.default_rng(5)
     walls = np.concatenate([np.stack([8 + 2 * np.linspace(0, 1, 40), np.full(40, 5.0), np.full(40, zc)], 1)
@@ -53,6 +72,10 @@ def _cases():
         "lidar_a": lidar_pair(1000)[0],
         "lidar_b": lidar_pair(1003, az_bins=1024)[1],
         "tiny": np.array([[5.0, 0.3, -1.7], [5.1, 0.4, -1.7]], np.float32),
+        # points 10 m below the ground: the GPU's lowest-point window (8 m)
+        # no longer holds the n_lpr lowest, so it takes its other path
+        "deep_outliers": np.concatenate([_disc(), np.array([[5.0, 0.5, -11.73], [10.0, -3.0, -12.5]], np.float32)]),
+        "edges": _edges(),
     }
 
 
@@ -78,7 +101,7 @@ def _check(torch, kmx, ctx, pts, stride=3, prm=None, oprm=None):
 
 
 @pytest.mark.parametrize("case", ["flat_walls", "tilted", "steep", "roof", "slope35", "noisy", "lidar_a",
-                                  "lidar_b", "tiny"])
+                                  "lidar_b", "tiny", "deep_outliers", "edges"])
 def test_suppression_bit_exact(env, case):
     torch, kmx, ctx = env
     o = _check(torch, kmx, ctx, _cases()[case])
