@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-indoor", action="store_true", help="skip the 2M-point indoor pair (voxel 0.02 m, "
                     "full ~300k x 300k matching in both modes)")
     ap.add_argument("--no-ablation", action="store_true", help="skip the classic-FPFH vs Faster-PFH comparison")
+    ap.add_argument("--no-suppressed", action="store_true", help="skip the LiDAR pair with geometric suppression "
+                    "(ground removal) and device-side registration")
     ap.add_argument("--no-register", action="store_true", help="skip timing kmx_prune + kmx_gnc (ratio filter, "
                     "invariant graph, max k-core, GNC-TLS pose) on the pair's correspondences")
     return ap.parse_args()
@@ -304,6 +306,8 @@ def run_kmx(args):
         line["register"] = bench_register(torch, ctx, pair, WORKLOAD["voxel"], R_gt, t_gt,
                                           reps=max(5, args.steps // 4),
                                           with_oracle=world == 1 and not args.no_cpu_baseline)
+    if not args.no_suppressed:
+        line["suppressed"] = bench_suppressed(torch, rank, steps=max(10, args.steps), warmup=max(3, args.warmup))
     if not args.no_ablation:
         line["ablation_classic_fpfh"] = bench_ablation(torch, rank, reps=max(5, args.steps // 3))
     if not args.no_indoor:
@@ -450,6 +454,87 @@ def bench_register(torch, ctx, pair, voxel, R_gt, t_gt, reps, with_oracle):
         res["oracle_gnc_ms"] = (t2 - t1) * 1e3
         res["oracle_max_core"] = int(len(keep))
         res["oracle_success"] = bool(reg.is_success(Ro, to, R_gt, t_gt))
+    return res
+
+
+def bench_suppressed(torch, rank, steps, warmup):
+    """The bench's LiDAR pair with geometric suppression (Sec. III-B) in
+    front: kmx_suppress_ground removes the ground of each raw scan, the
+    voxeliser reads the kept count on the device, then Faster-PFH and exact
+    matching as in the headline step (graph replay, each cloud on its own
+    stream, L2 flushed between steps).  Then kmx_prune and kmx_gnc on the
+    correspondences (CUDA events), the pose error against the generator's
+    ground truth, and the whole registration time (pair + prune + GNC)."""
+    from oracle import registration as reg
+    from paper_2409_15615_gb300 import kmx, pipeline, replicas
+
+    src, tgt, R, t, vps, vpt = lidar_pair(replicas.pair_seed(WORKLOAD["seed"], rank), az_bins=WORKLOAD["az_bins"])
+    v = WORKLOAD["voxel"]
+    ctx = kmx.Context(torch.cuda.current_device(), torch.cuda.current_stream())
+    pair = pipeline.PairState(ctx, len(src), len(tgt))
+    gp = kmx.ground_params_default()
+    pair.src.suppress = pair.tgt.suppress = gp
+    pair.src.raw.copy_(torch.from_numpy(src).cuda())
+    pair.tgt.raw.copy_(torch.from_numpy(tgt).cuda())
+    ps = kmx.params_default(v, viewpoint=np.float32(vps).tolist())
+    pt = kmx.params_default(v, viewpoint=np.float32(vpt).tolist())
+    mode = kmx.MATCH_FP32_EXACT
+    pair.run_checked(len(src), len(tgt), ps, pt, mode)
+    graph = pair.capture(len(src), len(tgt), ps, pt, mode)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = ctx.stream
+    for _ in range(warmup):
+        flush.zero_()
+        graph.replay()
+    torch.cuda.synchronize()
+    pair.sync()
+
+    def timed(fn, reps):
+        out = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            out.append(a.elapsed_time(b))
+        return out
+
+    times = timed(graph.replay, steps)
+    pair.sync()
+    sup = timed(lambda: ctx.suppress_ground(pair.src.raw[: len(src)], gp, out=pair.src.kept,
+                                            n_out=pair.src.n_kept), steps)
+    n_corr = int(pair.n_corr.item())
+    beta = 1.5 * v
+    reg_t = []
+    pr = g = None
+    for _ in range(max(3, steps // 2)):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        pr = ctx.prune(pair.corr, n_corr, pair.src.vox4, pair.tgt.vox4, beta, out=pr)
+        e[1].record(stream)
+        g = ctx.gnc(pair.corr, pr, pair.src.vox4, pair.tgt.vox4, beta, out=g)
+        e[2].record(stream)
+        e[2].synchronize()
+        reg_t.append((e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])))
+    ctx.sync()
+    Rg = g["R"].cpu().numpy().reshape(3, 3)
+    tg = g["t"].cpu().numpy()
+    rot, tr = reg.pose_errors(Rg, tg, R, t)
+    pair_ms = float(np.median(times))
+    prune_ms = float(np.median([x[0] for x in reg_t]))
+    gnc_ms = float(np.median([x[1] for x in reg_t]))
+    res = dict(pairs_per_s=1000.0 / pair_ms, pair_ms=pair_ms, suppress_ms_per_cloud=float(np.median(sup)),
+               raw_points=[len(src), len(tgt)], kept_points=[int(pair.src.n_kept.item()), int(pair.tgt.n_kept.item())],
+               voxelised=[int(pair.src.n_vox.item()), int(pair.tgt.n_vox.item())],
+               descriptors=[int(pair.src.out["n_valid"].item()), int(pair.tgt.out["n_valid"].item())],
+               correspondences=n_corr, prune_ms=prune_ms, gnc_ms=gnc_ms,
+               registration_ms=pair_ms + prune_ms + gnc_ms, max_core=int(pr["n_inlier"].item()),
+               rot_err_deg=rot, trans_err_m=tr, success=bool(reg.is_success(Rg, tg, R, t)),
+               ground_params="kmx_ground_params_default (4 zones, 504 bins, th 0.125 m, 3 refits)")
+    pair.close()
+    ctx.close()
     return res
 
 

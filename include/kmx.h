@@ -260,7 +260,9 @@ void kmx_grid_free(kmx_grid* grid);
  * The neighbour sets are exact: a distance within FP32 rounding of a radius
  * is decided again in FP64 as ((dx*dx + dy*dy) + dz*dz) < r*r.
  * Device errors: KMX_ECAPACITY if the lists need more than nbr_cap entries
- * (normals and flags are still written; the lists are not).
+ * (normals and flags are still written; the lists are not, and every offset
+ * is set to 0 so that a following kmx_fasterpfh reads empty lists; d_needed
+ * holds the length to allocate).
  */
 kmx_status kmx_normals(kmx_ctx* ctx, const kmx_grid* grid, const kmx_params* params, float* d_normal4,
                        uint8_t* d_flags, int64_t* d_nbr_offs, int32_t* d_nbr, int64_t nbr_cap,

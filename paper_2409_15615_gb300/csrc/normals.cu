@@ -226,6 +226,17 @@ __global__ void clear_counts(int32_t* cnt, const int64_t* d_n, int64_t n_cap)
         cnt[i] = 0;
 }
 
+// When the lists did not fit (search_fill wrote none of them), every offset
+// becomes 0: a later stage then reads empty lists instead of entries past
+// the end of the list buffer.  `needed` (the full length) is left for the
+// caller to size the buffer.
+__global__ void empty_lists_on_overflow(int64_t* offs, int64_t n_cap, const int64_t* needed, int64_t nbr_cap)
+{
+    if (*needed <= nbr_cap) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n_cap; i += (int64_t)gridDim.x * blockDim.x)
+        offs[i] = 0;
+}
+
 }  // namespace
 
 size_t kmx_normals_scratch_bytes(int64_t n_cap)
@@ -262,5 +273,10 @@ cudaError_t kmx_normals_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_params
               prm->tau_lin, {prm->viewpoint[0], prm->viewpoint[1], prm->viewpoint[2]}};
     KMX_COUNT_LAUNCH();
     search_fill<<<kmx_stride_blocks(n, kQPerBlock, ctx->sm_count), kThreads, 0, st>>>(gv, R, s, o, ctx->d_err);
+    if (nbr) {
+        KMX_COUNT_LAUNCH();
+        empty_lists_on_overflow<<<kmx_stride_blocks(n + 1, 256, ctx->sm_count), 256, 0, st>>>(offs, n, needed,
+                                                                                             nbr_cap);
+    }
     return cudaGetLastError();
 }

@@ -85,10 +85,12 @@ def _run_request(slot: _Slot, req: Request, m: ResidentMap, mode: int, nbr_per_p
     matching against the resident map, D2H of the correspondences."""
     ctx = slot.ctx
     n = len(req.xyz)
-    st = pipeline.CloudState(ctx, n, nbr_per_point)
     params = kmx.params_default(req.voxel, viewpoint=np.float32(req.viewpoint).tolist())
     host = torch.from_numpy(np.ascontiguousarray(req.xyz, np.float32)).pin_memory()
     with torch.cuda.stream(slot.stream):
+        # allocated (and zero-filled) on the slot's stream, so the caching
+        # allocator orders their reuse and their fills with this request's work
+        st = pipeline.CloudState(ctx, n, nbr_per_point)
         st.raw.copy_(host, non_blocking=True)
         st.features(n, params)
         cap = max(min(n, m.n_valid), 1)

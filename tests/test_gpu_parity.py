@@ -233,6 +233,12 @@ def test_neighbour_capacity_error(torch_cuda, ctx, orc):
         ctx.sync()
     assert e.value.status == kmx.KMX_ECAPACITY
     assert int(out["needed"].item()) == len(nbr)
+    # the lists were not written: every offset is 0, so the next stage reads
+    # empty lists (no entry past the 10-entry buffer) and describes nothing
+    assert np.all(out["offs"].cpu().numpy() == 0)
+    res = ctx.fasterpfh(grid, prm, out["normal4"], out["flags"], out["offs"], out["nbr"])
+    ctx.sync()
+    assert int(res["n_valid"].item()) == 0
     # a grid cell smaller than r_FPFH is refused on the host
     small = ctx.build_grid(p, prm.r_fpfh * 0.5)
     with pytest.raises(kmx.KmxError) as e:
