@@ -302,23 +302,32 @@ def run_kmx(args):
         gpu_launches_per_step=launches, clocks=clk, match_mode_ms_per_step=mode_ms or None,
         cuda_graph=graph is not None,
     )
+    # the sections after the headline each run guarded: a failure is recorded
+    # in its entry ({"error": ...}) and the line is still printed
+    def section(name, fn):
+        try:
+            line[name] = fn()
+        except Exception as e:  # reported in the JSON line, not hidden
+            line[name] = {"error": "%s: %s" % (type(e).__name__, str(e).splitlines()[0] if str(e) else "")}
+
     if not args.no_register:
-        line["register"] = bench_register(torch, ctx, pair, WORKLOAD["voxel"], R_gt, t_gt,
-                                          reps=max(5, args.steps // 4),
-                                          with_oracle=world == 1 and not args.no_cpu_baseline)
+        section("register", lambda: bench_register(torch, ctx, pair, WORKLOAD["voxel"], R_gt, t_gt,
+                                                   reps=max(5, args.steps // 4),
+                                                   with_oracle=world == 1 and not args.no_cpu_baseline))
     if not args.no_suppressed:
-        line["suppressed"] = bench_suppressed(torch, rank, steps=max(10, args.steps), warmup=max(3, args.warmup))
+        section("suppressed", lambda: bench_suppressed(torch, rank, steps=max(10, args.steps),
+                                                       warmup=max(3, args.warmup)))
     if not args.no_ablation:
-        line["ablation_classic_fpfh"] = bench_ablation(torch, rank, reps=max(5, args.steps // 3))
+        section("ablation_classic_fpfh", lambda: bench_ablation(torch, rank, reps=max(5, args.steps // 3)))
     if not args.no_indoor:
-        line["indoor"] = bench_indoor(torch, rank, reps=3)
+        section("indoor", lambda: bench_indoor(torch, rank, reps=3))
     if args.batch_pairs > 0:
-        line["batched"] = bench_batched(torch, args.batch_pairs, rank)
+        section("batched", lambda: bench_batched(torch, args.batch_pairs, rank))
     if args.serve_requests > 0:
-        line["serving"] = bench_serving(torch, args.serve_requests, [float(x) for x in args.serve_rates.split(",")],
-                                        rank)
+        section("serving", lambda: bench_serving(torch, args.serve_requests,
+                                                 [float(x) for x in args.serve_rates.split(",")], rank))
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(src, tgt, vps, vpt)
+        section("cpu_baseline", lambda: cpu_baseline(src, tgt, vps, vpt))
     print(json.dumps(line), flush=True)
 
 
