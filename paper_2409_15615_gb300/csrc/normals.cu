@@ -10,9 +10,11 @@
 // P_normal mean; after a prefix sum of the counts the second writes the CSR
 // lists and accumulates the covariance centred on that mean.
 //
-// The 3x3 eigen-problem is solved in FP64 (closed form, Smith 1961:
-// trigonometric eigenvalues, eigenvector of the smallest one from the
-// best-conditioned cross product of two rows of A - l3 I).  GB300 issues FP64
+// The 3x3 eigen-problem starts from the closed form (Smith 1961:
+// trigonometric eigenvalues) in FP32, refines the well-separated extreme
+// eigenvalue by FP64 Newton steps on the characteristic polynomial and takes
+// the other two from a quadratic in FP64; the normal is the best-conditioned
+// cross product of two rows of A - l3 I in FP64 (search_common.cuh).  GB300 issues FP64
 // at a small fraction of the FP32 rate and a warp instruction costs the same
 // with 1 or 32 active lanes, so each block first gathers the covariances of
 // its 32 queries in shared memory and then solves them one per lane.

@@ -112,14 +112,45 @@ __device__ __forceinline__ bool eig_sym3(double a00, double a01, double a02, dou
         nv[2] = 1.0;
         return false;
     }
-    const double p = sqrt(p2 / 6.0);
+    // Eigenvalues of the traceless B = A - qI are the roots of
+    // g(mu) = mu^3 - (p2 / 2) mu - det(B), i.e. 2p cos(phi + 2 pi k / 3) with
+    // p = sqrt(p2 / 6), phi = acos(r) / 3, r = det(B) / (2 p^3).  GB300 issues
+    // FP64 slowly and acos / cos in FP64 dominated this solve, so: the
+    // trigonometric form in FP32 for a start, two FP64 Newton steps on the
+    // extreme root that is well separated (the largest when r >= 0, i.e. when
+    // the two smaller roots are the closer pair; else the smallest), and the
+    // other two in FP64 from the quadratic mu^2 + m mu + (m^2 - p2 / 2) = 0
+    // (sum of the roots 0, sum of their pairwise products -p2 / 2), whose
+    // square root resolves a close pair to ~1e-8 p.  Beyond p (below -p) g is
+    // increasing and convex (concave), so Newton started there (the start is
+    // clamped; pf is within 2^-23 of p) moves monotonically to that extreme
+    // root.  Eigenvalues come out to ~1e-8 relative or better, the smallest
+    // one to FP64 accuracy where the normal is well posed.
     const double det = b00 * (b11 * b22 - a12 * a12) - a01 * (a01 * b22 - a12 * a02) + a02 * (a01 * a12 - b11 * a02);
-    double r = det / (2.0 * p * p * p);
-    r = fmin(1.0, fmax(-1.0, r));
-    const double phi = acos(r) / 3.0;
-    l[0] = q + 2.0 * p * cos(phi);
-    l[2] = q + 2.0 * p * cos(phi + 2.0943951023931957);  // + 2 pi / 3
-    l[1] = 3.0 * q - l[0] - l[2];
+    const float pf = sqrtf((float)p2 / 6.0f);
+    const float rf = fminf(1.0f, fmaxf(-1.0f, (float)det / (2.0f * pf * pf * pf)));
+    const float phi = acosf(rf) / 3.0f;
+    const double edge = (double)pf * (1.0 + 0x1p-20);
+    const bool top = rf >= 0.0f;
+    double mu = top ? fmax((double)(2.0f * pf * cosf(phi)), edge)
+                    : fmin((double)(2.0f * pf * cosf(phi + 2.0943951f)), -edge);
+    const double h = 0.5 * p2;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const double g = mu * (mu * mu - h) - det;
+        const double dg = 3.0 * mu * mu - h;
+        if (dg > 0.0) mu -= g / dg;  // dg > 0 beyond +-p
+    }
+    const double sd = sqrt(fmax(0.0, 2.0 * p2 - 3.0 * mu * mu));
+    if (top) {
+        l[0] = q + mu;
+        l[1] = q + 0.5 * (-mu + sd);
+        l[2] = q + 0.5 * (-mu - sd);
+    } else {
+        l[0] = q + 0.5 * (-mu + sd);
+        l[1] = q + 0.5 * (-mu - sd);
+        l[2] = q + mu;
+    }
     const double r0[3] = {a00 - l[2], a01, a02};
     const double r1[3] = {a01, a11 - l[2], a12};
     const double r2[3] = {a02, a12, a22 - l[2]};
