@@ -184,3 +184,85 @@ class PairState:
         n = int(self.n_corr.item())
         i, j, d1, d2 = kmx.corr_fields(self.corr, n)
         return i.cpu().numpy(), j.cpu().numpy(), d1.cpu().numpy(), d2.cpu().numpy()
+
+
+class PairStream:
+    """Registration pairs streamed from pinned host memory, overlapped.
+
+    Two PairStates take turns.  Pair k's raw clouds are uploaded on an H2D
+    stream, its features and matching run on the context's stream (a CUDA
+    graph per slot when ``graph`` is set), and its correspondences are
+    downloaded on a D2H stream, so the upload of pair k+1 and the download of
+    pair k-1 overlap pair k's kernels.  A slot is reused only after its
+    previous pair's compute has read its inputs and its previous download
+    has read its outputs (events order the three streams)."""
+
+    def __init__(self, ctx: kmx.Context, n_src_cap: int, n_tgt_cap: int, nbr_per_point: int = 96):
+        self.ctx = ctx
+        self.slots = [PairState(ctx, n_src_cap, n_tgt_cap, nbr_per_point) for _ in range(2)]
+        self.h2d = torch.cuda.Stream(device=ctx.device)
+        self.d2h = torch.cuda.Stream(device=ctx.device)
+        self.done = [None, None]   # compute of the slot's last pair finished
+        self.down = [None, None]   # download of the slot's last pair finished
+        self.graphs = [None, None]
+        self.k = 0
+
+    def prepare(self, n_src, n_tgt, p_src, p_tgt, mode, graph: bool = True):
+        """Size every buffer (a checked run per slot) and, with ``graph``,
+        record each slot's pair as a CUDA graph for these sizes."""
+        for i, s in enumerate(self.slots):
+            s.run_checked(n_src, n_tgt, p_src, p_tgt, mode)
+            self.graphs[i] = s.capture(n_src, n_tgt, p_src, p_tgt, mode) if graph else None
+        torch.cuda.synchronize(self.ctx.device)
+        self.sizes = (n_src, n_tgt, p_src, p_tgt, mode)
+        return self
+
+    def submit(self, h_src: torch.Tensor, h_tgt: torch.Tensor, h_corr: torch.Tensor, h_n: torch.Tensor,
+               timing: bool = False):
+        """Enqueue one pair: h_src / h_tgt pinned [n, 3] clouds of the prepared
+        sizes, h_corr ([cap, 4] int32) / h_n ([1] int64) pinned outputs.
+        Returns the event after which h_corr / h_n hold the result (the host
+        buffers must stay untouched until then); with ``timing``, (start,
+        end) timing events around the pair's upload and download."""
+        n_src, n_tgt, p_src, p_tgt, mode = self.sizes
+        i = self.k % 2
+        s = self.slots[i]
+        compute = self.ctx.stream
+        if self.done[i] is not None:
+            self.h2d.wait_event(self.done[i])
+        start = torch.cuda.Event(enable_timing=True) if timing else None
+        with torch.cuda.stream(self.h2d):
+            if start is not None:
+                start.record(self.h2d)
+            s.src.raw[:n_src].copy_(h_src, non_blocking=True)
+            s.tgt.raw[:n_tgt].copy_(h_tgt, non_blocking=True)
+            up = torch.cuda.Event()
+            up.record(self.h2d)
+        compute.wait_event(up)
+        if self.down[i] is not None:
+            compute.wait_event(self.down[i])
+        with torch.cuda.stream(compute):
+            if self.graphs[i] is not None:
+                self.graphs[i].replay()
+            else:
+                s.run(n_src, n_tgt, p_src, p_tgt, mode)
+            done = torch.cuda.Event()
+            done.record(compute)
+        self.d2h.wait_event(done)
+        with torch.cuda.stream(self.d2h):
+            h_n.copy_(s.n_corr, non_blocking=True)
+            h_corr.copy_(s.corr, non_blocking=True)
+            down = torch.cuda.Event(enable_timing=timing)
+            down.record(self.d2h)
+        self.done[i], self.down[i] = done, down
+        self.k += 1
+        return (start, down) if timing else down
+
+    def sync(self):
+        torch.cuda.synchronize(self.ctx.device)
+        for s in self.slots:
+            s.sync()
+
+    def close(self):
+        for s in self.slots:
+            s.close()
