@@ -812,10 +812,10 @@ def end_to_end(torch, ctx, pair, src, tgt, ps, pt, mode, flush, steps, world):
     """The same pairs through the public streaming API (pipeline.PairStream)
     from pinned host buffers: every pair's H2D upload of both raw clouds and
     D2H download of its correspondences (the whole [cap, 4] buffer and the
-    count) are inside the timed region; uploads and downloads of neighbouring
-    pairs overlap the current pair's kernels (two slots, graph replay).
-    Timed with CUDA events from the first upload to the last download; each
-    pair's inputs arrive by copy, so no L2 flush is added."""
+    count) are inside the timed region; uploads and downloads overlap the
+    kernels, and two pairs are in flight on two compute streams (two slots,
+    graph replay).  Timed with CUDA events from the first upload to the last
+    download; each pair's inputs arrive by copy, so no L2 flush is added."""
     from paper_2409_15615_gb300 import pipeline, replicas
 
     h_src = torch.from_numpy(src).pin_memory()
@@ -838,7 +838,7 @@ def end_to_end(torch, ctx, pair, src, tgt, ps, pt, mode, flush, steps, world):
                 h2d_bytes_per_step=int(src.nbytes + tgt.nbytes),
                 d2h_bytes_per_step=int(h_corr.numel() * 4 + 8),
                 p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
-                correspondences=n_corr, overlapped=True)
+                correspondences=n_corr, overlapped=True, pairs_in_flight=2)
 
 
 def count_launches(torch, step):

@@ -190,16 +190,24 @@ class PairStream:
     """Registration pairs streamed from pinned host memory, overlapped.
 
     Two PairStates take turns.  Pair k's raw clouds are uploaded on an H2D
-    stream, its features and matching run on the context's stream (a CUDA
-    graph per slot when ``graph`` is set), and its correspondences are
+    stream, its features and matching run on its slot's compute stream (a
+    CUDA graph per slot when ``graph`` is set), and its correspondences are
     downloaded on a D2H stream, so the upload of pair k+1 and the download of
-    pair k-1 overlap pair k's kernels.  A slot is reused only after its
-    previous pair's compute has read its inputs and its previous download
-    has read its outputs (events order the three streams)."""
+    pair k-1 overlap pair k's kernels; by default the two slots also compute
+    on separate contexts, so consecutive pairs overlap each other's kernels
+    (the feature chain leaves most of the GPU idle).  A slot is reused only
+    after its previous pair's compute has read its inputs and its previous
+    download has read its outputs (events order the streams)."""
 
-    def __init__(self, ctx: kmx.Context, n_src_cap: int, n_tgt_cap: int, nbr_per_point: int = 96):
+    def __init__(self, ctx: kmx.Context, n_src_cap: int, n_tgt_cap: int, nbr_per_point: int = 96,
+                 concurrent: bool = True):
         self.ctx = ctx
-        self.slots = [PairState(ctx, n_src_cap, n_tgt_cap, nbr_per_point) for _ in range(2)]
+        # with ``concurrent`` the second slot computes on a context (stream and
+        # scratch) of its own, so consecutive pairs may also overlap each
+        # other's kernels; otherwise both slots compute on ctx's stream
+        self.own_ctx = kmx.Context(ctx.device.index, torch.cuda.Stream(device=ctx.device)) if concurrent else None
+        self.ctxs = [ctx, self.own_ctx or ctx]
+        self.slots = [PairState(c, n_src_cap, n_tgt_cap, nbr_per_point) for c in self.ctxs]
         self.h2d = torch.cuda.Stream(device=ctx.device)
         self.d2h = torch.cuda.Stream(device=ctx.device)
         self.done = [None, None]   # compute of the slot's last pair finished
@@ -227,7 +235,7 @@ class PairStream:
         n_src, n_tgt, p_src, p_tgt, mode = self.sizes
         i = self.k % 2
         s = self.slots[i]
-        compute = self.ctx.stream
+        compute = self.ctxs[i].stream
         if self.done[i] is not None:
             self.h2d.wait_event(self.done[i])
         start = torch.cuda.Event(enable_timing=True) if timing else None
@@ -266,3 +274,6 @@ class PairStream:
     def close(self):
         for s in self.slots:
             s.close()
+        if self.own_ctx is not None:
+            self.own_ctx.close()
+            self.own_ctx = None

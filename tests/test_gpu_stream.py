@@ -18,8 +18,8 @@ def _pairs(k, n=8000):
     return out
 
 
-@pytest.mark.parametrize("graph", [True, False])
-def test_stream_equals_plain_runs(graph):
+@pytest.mark.parametrize("graph,concurrent", [(True, False), (False, False), (True, True)])
+def test_stream_equals_plain_runs(graph, concurrent):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -41,7 +41,7 @@ def test_stream_equals_plain_runs(graph):
         i, j, _, _ = plain.correspondences()
         ref.append(set(zip(i.tolist(), j.tolist())))
     plain.close()
-    st = pipeline.PairStream(ctx, n, n)
+    st = pipeline.PairStream(ctx, n, n, concurrent=concurrent)
     st.prepare(n, n, prm, prm, kmx.MATCH_FP32_EXACT, graph=graph)
     hosts = [(torch.from_numpy(s).pin_memory(), torch.from_numpy(t).pin_memory()) for s, t, _, _ in pairs]
     outs = [(torch.empty(st.slots[0].corr.shape, dtype=torch.int32).pin_memory(),
