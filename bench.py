@@ -103,9 +103,22 @@ def cpu_baseline(src, tgt, vps, vpt, budget_s=12.0):
     t_end = time.perf_counter() + budget_s
     while not times or (time.perf_counter() < t_end and len(times) < 20):
         times.append(oracle_pair_seconds(src, tgt, vps, vpt))
-    return dict(value=1.0 / statistics.median(times), unit="pairs/s", cores=oracle_cores(), kind="oracle",
-                sample="%d whole pairs of the workload (voxelise, Faster-PFH on both clouds, FP64 brute-force "
-                       "mutual NN); median pair time %.3f s" % (len(times), statistics.median(times)))
+    out = dict(value=1.0 / statistics.median(times), unit="pairs/s", cores=oracle_cores(), kind="oracle",
+               sample="%d whole pairs of the workload (voxelise, Faster-PFH on both clouds, FP64 brute-force "
+                      "mutual NN); median pair time %.3f s" % (len(times), statistics.median(times)))
+    # the same pair once on one host thread (a child process with OMP_NUM_THREADS=1)
+    code = ("import sys, time, numpy as np; sys.path.insert(0, %r); import bench; "
+            "from synth import lidar_pair; "
+            "s, t, R, tr, a, b = lidar_pair(%d, az_bins=%d); "
+            "print(bench.oracle_pair_seconds(s, t, a, b))" % (ROOT, WORKLOAD["seed"], WORKLOAD["az_bins"]))
+    try:
+        env = dict(os.environ, OMP_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+        sec = float(r.stdout.strip().splitlines()[-1])
+        out["one_thread"] = dict(value=1.0 / sec, unit="pairs/s", cores=1, sample="one whole pair of the workload")
+    except (subprocess.SubprocessError, ValueError, IndexError, OSError) as e:
+        out["one_thread"] = dict(error=type(e).__name__)
+    return out
 
 
 def run_reference(args):
@@ -279,6 +292,7 @@ def run_kmx(args):
     stages = stage_times(torch, ctx, pair, len(src), len(tgt), ps, pt, mode, flush, reps=max(5, args.steps // 2))
     work = algorithmic_work(pair, ctx)
     roof = roofline(stages, work, mode)
+    roof["feature_stages"] = stage_roofline(stages, work)
 
     # ---- end to end through host buffers
     e2e = end_to_end(torch, ctx, pair, src, tgt, ps, pt, mode, flush, args.steps, world)
@@ -754,6 +768,21 @@ def stage_bytes(w):
         normals=12 * w["sum_mF"] + 16 * n + 16 * n + 1 * n + 8 * n,  # neighbour coords, own point, normal, flag, offs
         fasterpfh=24 * w["sum_mV_B"] + 144 * w["sum_mV_J"] + 16 * n + 144 * w["n_B"] + 144 * w["n_J"],
     )
+
+
+def stage_roofline(stages, work):
+    """Each feature stage of each cloud: algorithmic bytes, its device time
+    (CUDA events between the C-ABI calls), achieved GB/s and the fraction of
+    the measured HBM copy bandwidth.  The stages are short and their working
+    sets (a few MB) stay in L2, so these fractions are low by nature."""
+    peak = measured_peaks()["hbm_gbs"]
+    out = {}
+    for side in ("src", "tgt"):
+        for k, by in stage_bytes(work[side]).items():
+            ms = stages[side + "_" + k]
+            gbs = by / (ms / 1000.0) / 1e9 if ms > 0 else 0.0
+            out[side + "_" + k] = dict(bytes=int(by), ms=ms, gbs=gbs, frac=gbs / peak)
+    return out
 
 
 def roofline(stages, work, mode):
