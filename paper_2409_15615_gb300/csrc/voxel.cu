@@ -58,37 +58,60 @@ VoxScratch carve(void* base, int64_t n, size_t* total)
     return s;
 }
 
-// floor(x / v) with the quotient rounded once in FP64 (IEEE division).
-__device__ __forceinline__ bool voxel_index(float x, double v, int* k)
+// floor(x / v) with the quotient rounded once in FP64 (IEEE division).  The
+// FP32 quotient is within one FP32 ulp of the FP64 one; when no integer lies
+// within four ulps of it (plus a tiny absolute term for quotients near 0),
+// its floor is the FP64 floor, else the FP64 division decides.  GB300 issues
+// FP64 slowly; the result is exactly the FP64 definition's.
+__device__ __forceinline__ bool voxel_index(float x, float vf, double v, int* k)
 {
-    double q = floor(__ddiv_rn((double)x, v));
+    const float qf = __fdiv_rn(x, vf);
+    const float m = fmaf(fabsf(qf), 0x1p-22f, 0x1p-100f);
+    const float lo = floorf(__fsub_rn(qf, m)), hi = floorf(__fadd_rn(qf, m));
+    const double q = lo == hi ? (double)lo : floor(__ddiv_rn((double)x, v));
     if (!(fabs(q) < 1048576.0)) return false;
     *k = (int)q;
     return true;
 }
 
+// Consecutive scan points often fall into one voxel, so the lanes of a warp
+// with the same key share one insert and one update of the voxel's count and
+// lowest member (the group's lowest lane holds its lowest index).
 __global__ void __launch_bounds__(kThreads) vox_insert(const float* __restrict__ xyz, int64_t n_cap,
-                                                       const int64_t* d_n, int stride, double v, VoxScratch s,
-                                                       unsigned int* err)
+                                                       const int64_t* d_n, int stride, float vf, double v,
+                                                       VoxScratch s, unsigned int* err)
 {
-    int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (r >= kmx_count(d_n, n_cap)) return;
-    const float* p = xyz + r * stride;
-    int kx, ky, kz;
-    bool ok = voxel_index(p[0], v, &kx) & voxel_index(p[1], v, &ky) & voxel_index(p[2], v, &kz);
-    if (!ok) {
-        kmx_raise(err, KMX_DERR_RANGE);
-        s.pslot[r] = -1;
-        return;
+    const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    bool ok = false;
+    unsigned long long key = 0;
+    if (r < kmx_count(d_n, n_cap)) {
+        const float* p = xyz + r * stride;
+        int kx, ky, kz;
+        ok = voxel_index(p[0], vf, v, &kx) & voxel_index(p[1], vf, v, &ky) & voxel_index(p[2], vf, v, &kz);
+        if (ok) {
+            key = kmx_pack_key(kx, ky, kz);
+        } else {
+            kmx_raise(err, KMX_DERR_RANGE);
+            s.pslot[r] = -1;
+        }
     }
-    int slot = kmx_hash_insert(s.keys, s.T, kmx_pack_key(kx, ky, kz));
+    const unsigned act = __ballot_sync(0xffffffffu, ok);  // every lane of the (full) warp gets here
+    if (!ok) return;
+    const unsigned grp = __match_any_sync(act, key);
+    const int leader = __ffs(grp) - 1;
+    int slot = 0;
+    if (lane == leader) {
+        slot = kmx_hash_insert(s.keys, s.T, key);
+        if (slot >= 0) {
+            atomicMin(&s.vmin[slot], (int32_t)r);
+            atomicAdd(&s.vcnt[slot], __popc(grp));
+        } else {
+            kmx_raise(err, KMX_DERR_HASHFULL);
+        }
+    }
+    slot = __shfl_sync(grp, slot, leader);
     s.pslot[r] = slot;
-    if (slot < 0) {
-        kmx_raise(err, KMX_DERR_HASHFULL);
-        return;
-    }
-    atomicMin(&s.vmin[slot], (int32_t)r);
-    atomicAdd(&s.vcnt[slot], 1);
 }
 
 __global__ void __launch_bounds__(kThreads) vox_first_flag(int64_t n_cap, const int64_t* d_n, VoxScratch s)
@@ -340,7 +363,7 @@ cudaError_t kmx_voxelize_launch(kmx_ctx* ctx, const float* xyz, int64_t n, const
     }
     unsigned nb = kmx_blocks(n, kThreads);
     KMX_COUNT_LAUNCH();
-    vox_insert<<<nb, kThreads, 0, st>>>(xyz, n, d_n, stride, (double)v, s, ctx->d_err);
+    vox_insert<<<nb, kThreads, 0, st>>>(xyz, n, d_n, stride, v, (double)v, s, ctx->d_err);
     KMX_COUNT_LAUNCH();
     vox_first_flag<<<nb, kThreads, 0, st>>>(n, d_n, s);
     if ((e = kmx_scan_i32(s.flag, n, d_n, s.oidx, s.scan, st, ctx->d_err))) return e;
@@ -348,8 +371,7 @@ cudaError_t kmx_voxelize_launch(kmx_ctx* ctx, const float* xyz, int64_t n, const
     KMX_COUNT_LAUNCH();
     vox_number<<<nb, kThreads, 0, st>>>(n, d_n, s, cap, n_out, ctx->d_err);
     // member offsets per output voxel: scan of the counts parked in `cursor`
-    if ((e = cudaMemcpyAsync(s.flag, s.cursor, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st))) return e;
-    if ((e = kmx_scan_i32(s.flag, n, n_out, s.vstart, s.scan, st, ctx->d_err))) return e;
+    if ((e = kmx_scan_i32(s.cursor, n, n_out, s.vstart, s.scan, st, ctx->d_err))) return e;
     if ((e = cudaMemsetAsync(s.cursor, 0, sizeof(int32_t) * (n + 1), st))) return e;
     KMX_COUNT_LAUNCH();
     vox_scatter<<<nb, kThreads, 0, st>>>(n, d_n, s, assign);
