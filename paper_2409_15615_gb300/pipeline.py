@@ -189,30 +189,36 @@ class PairState:
 class PairStream:
     """Registration pairs streamed from pinned host memory, overlapped.
 
-    Two PairStates take turns.  Pair k's raw clouds are uploaded on an H2D
-    stream, its features and matching run on its slot's compute stream (a
-    CUDA graph per slot when ``graph`` is set), and its correspondences are
-    downloaded on a D2H stream, so the upload of pair k+1 and the download of
-    pair k-1 overlap pair k's kernels; by default the two slots also compute
-    on separate contexts, so consecutive pairs overlap each other's kernels
-    (the feature chain leaves most of the GPU idle).  A slot is reused only
+    ``slots`` PairStates take turns (pair k runs on slot k mod slots).  Pair
+    k's raw clouds are uploaded on an H2D stream, its features and matching
+    run on its slot's compute stream (a CUDA graph per slot when ``graph`` is
+    set), and its correspondences are downloaded on a D2H stream, so the
+    upload of pair k+1 and the download of pair k-1 overlap pair k's kernels;
+    by default every slot also computes on a context of its own, so up to
+    ``slots`` consecutive pairs overlap each other's kernels (the feature
+    chain of one pair leaves most of the GPU idle).  A slot is reused only
     after its previous pair's compute has read its inputs and its previous
     download has read its outputs (events order the streams)."""
 
     def __init__(self, ctx: kmx.Context, n_src_cap: int, n_tgt_cap: int, nbr_per_point: int = 96,
-                 concurrent: bool = True):
+                 concurrent: bool = True, slots: int = 2):
+        if slots < 1:
+            raise ValueError("slots must be >= 1")
         self.ctx = ctx
-        # with ``concurrent`` the second slot computes on a context (stream and
-        # scratch) of its own, so consecutive pairs may also overlap each
-        # other's kernels; otherwise both slots compute on ctx's stream
-        self.own_ctx = kmx.Context(ctx.device.index, torch.cuda.Stream(device=ctx.device)) if concurrent else None
-        self.ctxs = [ctx, self.own_ctx or ctx]
+        # with ``concurrent`` every slot after the first computes on a context
+        # (stream and scratch) of its own, so consecutive pairs may also
+        # overlap each other's kernels; otherwise all slots compute on ctx's
+        # stream
+        self.own_ctxs = [kmx.Context(ctx.device.index, torch.cuda.Stream(device=ctx.device))
+                         for _ in range(slots - 1)] if concurrent else []
+        self.ctxs = [ctx] + (self.own_ctxs or [ctx] * (slots - 1))
         self.slots = [PairState(c, n_src_cap, n_tgt_cap, nbr_per_point) for c in self.ctxs]
+        self.n = slots
         self.h2d = torch.cuda.Stream(device=ctx.device)
         self.d2h = torch.cuda.Stream(device=ctx.device)
-        self.done = [None, None]   # compute of the slot's last pair finished
-        self.down = [None, None]   # download of the slot's last pair finished
-        self.graphs = [None, None]
+        self.done = [None] * slots   # compute of the slot's last pair finished
+        self.down = [None] * slots   # download of the slot's last pair finished
+        self.graphs = [None] * slots
         self.k = 0
 
     def prepare(self, n_src, n_tgt, p_src, p_tgt, mode, graph: bool = True):
@@ -233,7 +239,7 @@ class PairStream:
         buffers must stay untouched until then); with ``timing``, (start,
         end) timing events around the pair's upload and download."""
         n_src, n_tgt, p_src, p_tgt, mode = self.sizes
-        i = self.k % 2
+        i = self.k % self.n
         s = self.slots[i]
         compute = self.ctxs[i].stream
         if self.done[i] is not None:
@@ -274,6 +280,6 @@ class PairStream:
     def close(self):
         for s in self.slots:
             s.close()
-        if self.own_ctx is not None:
-            self.own_ctx.close()
-            self.own_ctx = None
+        for c in self.own_ctxs:
+            c.close()
+        self.own_ctxs = []

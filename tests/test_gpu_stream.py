@@ -18,8 +18,9 @@ def _pairs(k, n=8000):
     return out
 
 
-@pytest.mark.parametrize("graph,concurrent", [(True, False), (False, False), (True, True)])
-def test_stream_equals_plain_runs(graph, concurrent):
+@pytest.mark.parametrize("graph,concurrent,slots", [(True, False, 2), (False, False, 2), (True, True, 2),
+                                                   (True, True, 3), (False, True, 4)])
+def test_stream_equals_plain_runs(graph, concurrent, slots):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -41,13 +42,13 @@ def test_stream_equals_plain_runs(graph, concurrent):
         i, j, _, _ = plain.correspondences()
         ref.append(set(zip(i.tolist(), j.tolist())))
     plain.close()
-    st = pipeline.PairStream(ctx, n, n, concurrent=concurrent)
+    st = pipeline.PairStream(ctx, n, n, concurrent=concurrent, slots=slots)
     st.prepare(n, n, prm, prm, kmx.MATCH_FP32_EXACT, graph=graph)
     hosts = [(torch.from_numpy(s).pin_memory(), torch.from_numpy(t).pin_memory()) for s, t, _, _ in pairs]
     outs = [(torch.empty(st.slots[0].corr.shape, dtype=torch.int32).pin_memory(),
              torch.empty(1, dtype=torch.int64).pin_memory()) for _ in range(8)]
     evs = []
-    for k in range(8):  # each pair twice, back to back, so both slots serve every pair
+    for k in range(8):  # each pair twice; with 2 or 3 slots every pair lands on two slots
         hs, ht = hosts[k % 4]
         evs.append(st.submit(hs, ht, outs[k][0], outs[k][1]))
     for ev in evs:
