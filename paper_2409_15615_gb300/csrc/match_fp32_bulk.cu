@@ -85,6 +85,8 @@ struct __align__(16) BulkShared {
     unsigned long long colred[kThreads / 32][kTile];    // per-warp column bests
     int32_t pperm[kTile];                               // original row of each tile row
     int32_t qperm[kStages][kTile];                      // original column of each tile column
+    unsigned long long pm[2];                           // nonzero masks of row tiles rt & ~1, rt | 1
+    unsigned long long qm[kStages][2];                  // the same for each stage's column tile
     uint64_t bar_p;
     uint64_t bar_q[kStages];
     Producer prod;
@@ -94,7 +96,8 @@ struct __align__(16) BulkShared {
 };
 static_assert(kPBytes % 16 == 0 && kQBytes % 16 == 0 && kPermBytes % 16 == 0, "bulk copies move 16-byte units");
 static_assert(offsetof(BulkShared, Q) % 16 == 0 && offsetof(BulkShared, pperm) % 16 == 0 &&
-                  offsetof(BulkShared, qperm) % 16 == 0,
+                  offsetof(BulkShared, qperm) % 16 == 0 && offsetof(BulkShared, pm) % 16 == 0 &&
+                  offsetof(BulkShared, qm) % 16 == 0,
               "bulk copy destinations are 16-byte aligned");
 
 __host__ __device__ __forceinline__ int64_t tiles_of(int64_t n) { return (n + kTile - 1) / kTile; }
@@ -325,7 +328,8 @@ __device__ __forceinline__ int read_end(const BulkShared& S) { return *reinterpr
 // of the item's column tile into its ring stage.
 __device__ __forceinline__ bool produce(BulkShared& S, int u, const ChunkGeo& cg, int64_t W, int nqt,
                                         int32_t* counter, const float* __restrict__ qn,
-                                        const int32_t* __restrict__ qperm, int& issued)
+                                        const int32_t* __restrict__ qperm,
+                                        const unsigned long long* __restrict__ qmask, int& issued)
 {
     Producer& P = S.prod;
     if (P.o == cg.L) {
@@ -340,9 +344,12 @@ __device__ __forceinline__ bool produce(BulkShared& S, int u, const ChunkGeo& cg
         S.end_item = u;
         return false;
     }
-    mbar_expect_tx(&S.bar_q[P.st], kQBytes + kPermBytes);
+    // the tile's nonzero mask travels with it, in the 16-byte pair holding it
+    // (the mask arrays have tiles + 1 entries and start 16-byte aligned)
+    mbar_expect_tx(&S.bar_q[P.st], kQBytes + kPermBytes + 16);
     bulk_g2s(S.Q[P.st], qn + (int64_t)P.ct * kDim * kTile, kQBytes, &S.bar_q[P.st]);
     bulk_g2s(S.qperm[P.st], qperm + (int64_t)P.ct * kTile, kPermBytes, &S.bar_q[P.st]);
+    bulk_g2s(S.qm[P.st], qmask + (P.ct & ~1), 16, &S.bar_q[P.st]);
     issued = u + 1;
     ++P.o;
     ++P.x;
@@ -389,11 +396,12 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
             const int64_t x0 = (int64_t)c0 * cg.L;
             S.prod = Producer{x0, c0, 0, (int)(x0 % nqt), 0, 0};
             const int64_t rt0 = x0 / nqt;
-            mbar_expect_tx(&S.bar_p, kPBytes + kPermBytes);
+            mbar_expect_tx(&S.bar_p, kPBytes + kPermBytes + 16);
             bulk_g2s(S.P, pp + rt0 * kDim * kTile, kPBytes, &S.bar_p);
             bulk_g2s(S.pperm, pperm + rt0 * kTile, kPermBytes, &S.bar_p);
+            bulk_g2s(S.pm, pmask + (rt0 & ~1), 16, &S.bar_p);
             for (int u = 0; u < kStages; ++u)
-                if (!produce(S, u, cg, W, nqt, counter, qn, qperm, issued)) break;
+                if (!produce(S, u, cg, W, nqt, counter, qn, qperm, qmask, issued)) break;
         }
     }
     __syncthreads();
@@ -409,7 +417,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     uint32_t qphase = 0;
     uint32_t p_phase = 0;
     bool p_ready = false;
-    unsigned long long mrow = __ldg(pmask + rt);
+    unsigned long long mrow = 0;
 
     unsigned long long k1[8];
     float b2[8];
@@ -425,6 +433,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
         if (!p_ready) {
             if (!mbar_wait(&S.bar_p, p_phase)) S.failed = 1;
             p_ready = true;
+            mrow = S.pm[rt & 1];
         }
         if (!mbar_wait(&S.bar_q[s], qphase)) S.failed = 1;
 
@@ -435,7 +444,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
             for (int jp = 0; jp < 4; ++jp) acc[i][jp] = make_float2(0.f, 0.f);
         // dimensions that are zero in every row of both tiles add exactly
         // nothing; the others are visited in ascending order
-        for (unsigned long long m = mrow | __ldg(qmask + ct); m; m &= m - 1) {
+        for (unsigned long long m = mrow | S.qm[s][ct & 1]; m; m &= m - 1) {
             const int kk = __ffsll((long long)m) - 1;
             const float4 c0 = *reinterpret_cast<const float4*>(&S.Q[s][kk][tx * 4]);
             const float4 c1 = *reinterpret_cast<const float4*>(&S.Q[s][kk][64 + tx * 4]);
@@ -530,7 +539,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
         }
         __syncthreads();  // (2) stage s, the source tile and colred are free
         if (failed) break;
-        if (tid == 0 && read_end(S) == INT_MAX) produce(S, t + kStages, cg, W, nqt, counter, qn, qperm, issued);
+        if (tid == 0 && read_end(S) == INT_MAX) produce(S, t + kStages, cg, W, nqt, counter, qn, qperm, qmask, issued);
         // advance to the next item (its chunk id is known: it was produced
         // kStages items ago); a new row tile reloads the source tile
         if (t + 1 < read_end(S)) {
@@ -552,12 +561,12 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
             }
             if (rt1 != rt) {
                 if (tid == 0) {
-                    mbar_expect_tx(&S.bar_p, kPBytes + kPermBytes);
+                    mbar_expect_tx(&S.bar_p, kPBytes + kPermBytes + 16);
                     bulk_g2s(S.P, pp + (int64_t)rt1 * kDim * kTile, kPBytes, &S.bar_p);
                     bulk_g2s(S.pperm, pperm + (int64_t)rt1 * kTile, kPermBytes, &S.bar_p);
+                    bulk_g2s(S.pm, pmask + (rt1 & ~1), 16, &S.bar_p);
                 }
                 rt = rt1;
-                mrow = __ldg(pmask + rt);
                 p_phase ^= 1u;
                 p_ready = false;
             }
