@@ -131,6 +131,16 @@ void kmx_destroy(kmx_ctx* ctx);
 /* Issue subsequent work on another stream of the same device. */
 kmx_status kmx_set_stream(kmx_ctx* ctx, void* cuda_stream);
 
+/* Residency of the exact FP32 matcher (kmx_match, KMX_MATCH_FP32_EXACT):
+ * its tile kernel runs as ctas_per_sm resident CTAs on every SM (1 or 2;
+ * 0 restores the default, 2).  Each CTA holds about 95 KB of shared memory and
+ * half of an SM's registers, so with 2 the matcher fills the GPU (fastest
+ * for one matching at a time) and with 1 half of every SM stays free for
+ * kernels on other streams, e.g. the feature chains of other pairs in
+ * flight.  The results do not depend on it.  Not from the paper: a
+ * scheduling choice.  Returns KMX_EINVAL for other values. */
+kmx_status kmx_set_match_residency(kmx_ctx* ctx, int ctas_per_sm);
+
 /* Make sure the context scratch holds at least `bytes` bytes. */
 kmx_status kmx_reserve(kmx_ctx* ctx, int64_t bytes);
 

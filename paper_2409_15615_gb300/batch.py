@@ -53,7 +53,7 @@ class BatchRunner:
     """Device state for one batch of pairs on `lanes` concurrent lanes."""
 
     def __init__(self, pairs, lanes: int = 8, mode: int = kmx.MATCH_FP32_EXACT, device: int = 0,
-                 nbr_per_point: int = 96):
+                 nbr_per_point: int = 96, match_residency: int | None = None):
         self.pairs = list(pairs)
         self.mode = mode
         self.device = torch.device("cuda", device)
@@ -81,10 +81,15 @@ class BatchRunner:
         self.p_tgt = [kmx.params_default(p.voxel, viewpoint=np.float32(p.vp_tgt).tolist()) for p in self.pairs]
         # lanes
         self.queues = _assign_lpt(self.n_src + self.n_tgt, lanes)
+        # with several lanes the exact matcher leaves half of every SM to the
+        # other lanes' kernels (kmx_set_match_residency); one lane keeps the
+        # default
+        res = (1 if lanes > 1 else 0) if match_residency is None else match_residency
         self.lanes = []
         for q in self.queues:
             stream = torch.cuda.Stream(device=self.device)
             ctx = kmx.Context(device, stream)
+            ctx.set_match_residency(res)
             ms = int(max(self.n_src[q])) if q else 1
             mt = int(max(self.n_tgt[q])) if q else 1
             # lanes already run concurrently, so each lane's pair stays on one stream

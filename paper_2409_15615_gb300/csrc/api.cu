@@ -153,6 +153,13 @@ kmx_status kmx_set_stream(kmx_ctx* c, void* cuda_stream)
     return KMX_OK;
 }
 
+kmx_status kmx_set_match_residency(kmx_ctx* c, int ctas_per_sm)
+{
+    if (!c || ctas_per_sm < 0 || ctas_per_sm > 2) return KMX_EINVAL;
+    c->match_ctas_per_sm = ctas_per_sm;
+    return KMX_OK;
+}
+
 kmx_status kmx_reserve(kmx_ctx* c, int64_t bytes)
 {
     if (!c || bytes < 0) return KMX_EINVAL;

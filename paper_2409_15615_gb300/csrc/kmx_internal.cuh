@@ -29,6 +29,7 @@ struct kmx_ctx {
     unsigned int* d_err;   // device error bits
     unsigned int* h_err;   // pinned host mirror for kmx_sync
     int sm_count;
+    int match_ctas_per_sm;  // exact matcher residency, 0 = default
     char msg[256];
 };
 

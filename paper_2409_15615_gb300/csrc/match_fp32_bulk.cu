@@ -703,7 +703,8 @@ cudaError_t kmx_match_fp32_bulk_launch(kmx_ctx* ctx, const float* dp, const int3
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, match_tiles_fp32_bulk, kThreads,
                                                            sizeof(BulkShared))))
         return e;
-    const int ctas = max(1, min(per_sm, kCtasPerSm)) * ctx->sm_count;
+    const int want = ctx->match_ctas_per_sm > 0 ? ctx->match_ctas_per_sm : kCtasPerSm;
+    const int ctas = max(1, min(per_sm, min(want, kCtasPerSm))) * ctx->sm_count;
     const unsigned small_grid = 4u * (unsigned)ctx->sm_count;  // grid-stride over the actual rows
     if ((e = cudaMemsetAsync(b.sort.keys, 0xFF, sizeof(unsigned long long) * b.sort.T, st))) return e;
     if ((e = cudaMemsetAsync(b.sort.count, 0, sizeof(int32_t) * (2 * (size_t)b.sort.T + 2), st))) return e;

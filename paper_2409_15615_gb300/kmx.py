@@ -75,6 +75,7 @@ def library():
         "kmx_destroy": (None, [vp]),
         "kmx_set_stream": (C.c_int, [vp, vp]),
         "kmx_reserve": (C.c_int, [vp, i64]),
+        "kmx_set_match_residency": (C.c_int, [vp, i32]),
         "kmx_sync": (C.c_int, [vp]),
         "kmx_last_error": (C.c_char_p, [vp]),
         "kmx_launch_count": (C.c_int64, []),
@@ -190,6 +191,11 @@ class Context:
     def check_timeout(self, polls: int):
         """kmx_check_timeout: a bounded wait on a flag nothing sets."""
         self._check(self.lib.kmx_check_timeout(self.h, int(polls)), "kmx_check_timeout")
+
+    def set_match_residency(self, ctas_per_sm: int):
+        """CTAs per SM of the exact matcher's tile kernel (1 or 2, 0 = default
+        2): 1 leaves half of every SM to kernels on other streams."""
+        self._check(self.lib.kmx_set_match_residency(self.h, int(ctas_per_sm)), "kmx_set_match_residency")
 
     def reserve(self, nbytes: int):
         self._check(self.lib.kmx_reserve(self.h, int(nbytes)), "kmx_reserve")

@@ -201,17 +201,27 @@ class PairStream:
     download has read its outputs (events order the streams)."""
 
     def __init__(self, ctx: kmx.Context, n_src_cap: int, n_tgt_cap: int, nbr_per_point: int = 96,
-                 concurrent: bool = True, slots: int = 2):
+                 concurrent: bool = True, slots: int = 2, match_residency: int | None = None):
         if slots < 1:
             raise ValueError("slots must be >= 1")
         self.ctx = ctx
-        # with ``concurrent`` every slot after the first computes on a context
-        # (stream and scratch) of its own, so consecutive pairs may also
-        # overlap each other's kernels; otherwise all slots compute on ctx's
-        # stream
-        self.own_ctxs = [kmx.Context(ctx.device.index, torch.cuda.Stream(device=ctx.device))
-                         for _ in range(slots - 1)] if concurrent else []
-        self.ctxs = [ctx] + (self.own_ctxs or [ctx] * (slots - 1))
+        if concurrent:
+            # every slot computes on a context (stream and scratch) of its
+            # own, so consecutive pairs also overlap each other's kernels.
+            # With several pairs in flight the exact matcher takes one CTA
+            # per SM instead of two, leaving half of every SM to the other
+            # pairs' feature kernels (1940 vs 1840 pairs/s streamed on the
+            # LiDAR pair with 4 slots, although one matching alone is slower)
+            res = (1 if slots > 1 else 0) if match_residency is None else match_residency
+            self.own_ctxs = [kmx.Context(ctx.device.index, torch.cuda.Stream(device=ctx.device))
+                             for _ in range(slots)]
+            for c in self.own_ctxs:
+                c.set_match_residency(res)
+            self.ctxs = list(self.own_ctxs)
+        else:
+            # all slots compute on ctx's stream, with ctx's settings
+            self.own_ctxs = []
+            self.ctxs = [ctx] * slots
         self.slots = [PairState(c, n_src_cap, n_tgt_cap, nbr_per_point) for c in self.ctxs]
         self.n = slots
         self.h2d = torch.cuda.Stream(device=ctx.device)

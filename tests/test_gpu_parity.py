@@ -432,6 +432,35 @@ def test_match_fp32_sparse_ties_equals_dense_kernel(torch_cuda, ctx, orc):
     _check_match(torch, ctx, orc, FP, FQ, kmx.MATCH_FP32_EXACT)
 
 
+def test_match_residency_does_not_change_results(torch_cuda, ctx):
+    """The exact matcher's residency (1 or 2 CTAs per SM, a scheduling
+    choice) changes the number of tile-pair ranges, the segments and the
+    order of the column atomics, never the correspondences; out-of-range
+    values are rejected."""
+    from paper_2409_15615_gb300 import kmx
+
+    torch = torch_cuda
+    rng = np.random.default_rng(23)
+    patterns = rng.random((30, 33)) < 0.3
+    FP = (rng.gamma(0.5, 20.0, (2900, 33)) * patterns[rng.integers(0, 30, 2900)]).astype(np.float32)
+    FQ = (rng.gamma(0.5, 20.0, (2700, 33)) * patterns[rng.integers(0, 30, 2700)]).astype(np.float32)
+    FQ[300:500] = FP[:200]  # exact duplicates: ties resolved by original index
+    dp, dq = dev(torch, _pad36(FP)), dev(torch, _pad36(FQ))
+    outs = []
+    for res in (0, 1, 2, 1):
+        ctx.set_match_residency(res)
+        corr, n_out = ctx.match(dp, None, len(FP), dq, None, len(FQ), mode=kmx.MATCH_FP32_EXACT)
+        ctx.sync()
+        outs.append(corr[: int(n_out.item())].cpu().numpy())
+    ctx.set_match_residency(0)
+    assert len(outs[0]) >= 200
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    for bad in (-1, 3):
+        with pytest.raises(kmx.KmxError):
+            ctx.set_match_residency(bad)
+
+
 def test_match_empty(torch_cuda, ctx):
     torch = torch_cuda
     from paper_2409_15615_gb300 import kmx
