@@ -23,9 +23,9 @@ GridScratch carve(void* base, int64_t n, uint32_t T, size_t* total)
     GridScratch s{};
     kmx_arena a{static_cast<char*>(base), 0};
     s.pslot = (int32_t*)a.take(sizeof(int32_t) * (n + 1));
-    s.cnt = (int32_t*)a.take(sizeof(int32_t) * T);
+    s.cnt = (int32_t*)a.take(2 * sizeof(int32_t) * T);  // cnt and cursor, cleared together
+    s.cursor = s.cnt ? s.cnt + T : nullptr;
     s.start = (int64_t*)a.take(sizeof(int64_t) * (T + 1));
-    s.cursor = (int32_t*)a.take(sizeof(int32_t) * T);
     s.tmp = (int32_t*)a.take(sizeof(int32_t) * (n + 1));
     s.scan = a.take(kmx_scan_scratch_bytes(T));
     *total = kmx_align_up(a.used, 256);
@@ -129,8 +129,7 @@ cudaError_t kmx_grid_build_launch(kmx_ctx* ctx, kmx_grid* g, void* scratch)
     GridScratch s = carve(scratch, g->n_cap, T, &total);
     cudaError_t e;
     if ((e = cudaMemsetAsync(g->keys, 0xFF, sizeof(unsigned long long) * T, st))) return e;
-    if ((e = cudaMemsetAsync(s.cnt, 0, sizeof(int32_t) * T, st))) return e;
-    if ((e = cudaMemsetAsync(s.cursor, 0, sizeof(int32_t) * T, st))) return e;
+    if ((e = cudaMemsetAsync(s.cnt, 0, 2 * sizeof(int32_t) * T, st))) return e;  // cnt and cursor
     g->inv_cell = 1.0 / ((double)g->cell * (1.0 + KMX_CELL_MARGIN));
     const unsigned nb = kmx_stride_blocks(g->n_cap, kThreads, ctx->sm_count);
     KMX_COUNT_LAUNCH();

@@ -114,8 +114,6 @@ struct SortSides {
     int64_t* gstart;               // [T] first position of each mask's group
     int32_t* distinct;             // [T] slots in use
     int32_t* n_distinct;           // [1]
-    unsigned long long* dorder;    // [T] per distinct mask: (side << 40) | mask order
-    int32_t* dcount;               // [T] per distinct mask: its rows
     uint32_t T;                    // power of two >= 2 (cap0 + cap1)
     void* packed[2];               // side 0: float2 pairs, side 1: negated floats
     int32_t* perm[2];              // [tiles * 128] original row per packed position, -1 = padding
@@ -188,16 +186,11 @@ __global__ void __launch_bounds__(256) mask_insert(SortSides S, unsigned int* er
     }
 }
 
-__global__ void __launch_bounds__(256) mask_compact(SortSides S)
+// Sort key of distinct mask e: (side << 40) | mask order.
+__device__ __forceinline__ unsigned long long distinct_order(const SortSides& S, int64_t e)
 {
-    const int nd = *S.n_distinct;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nd; e += stride) {
-        const int slot = S.distinct[e];
-        const unsigned long long key = S.keys[slot];
-        S.dorder[e] = ((key >> kDim) << 40) | mask_order(key);
-        S.dcount[e] = S.count[slot];
-    }
+    const unsigned long long key = S.keys[S.distinct[e]];
+    return ((key >> kDim) << 40) | mask_order(key);
 }
 
 constexpr int kRankChunk = 2048;
@@ -215,15 +208,15 @@ __global__ void __launch_bounds__(256) mask_rank(SortSides S)
     // uniform over the block so that every thread reaches the barriers
     for (int64_t e0 = (int64_t)blockIdx.x * (blockDim.x >> 5); e0 < nd; e0 += wstride) {
         const int64_t e = e0 + warp;
-        const unsigned long long me = e < nd ? S.dorder[e] : 0ull;
+        const unsigned long long me = e < nd ? distinct_order(S, e) : 0ull;
         const unsigned long long lo = me & ~((1ull << 40) - 1);  // same side, any mask
         int64_t start = 0;
         for (int f0 = 0; f0 < nd; f0 += kRankChunk) {
             const int len = min(kRankChunk, nd - f0);
             __syncthreads();
             for (int f = threadIdx.x; f < len; f += blockDim.x) {
-                so[f] = S.dorder[f0 + f];
-                sc[f] = S.dcount[f0 + f];
+                so[f] = distinct_order(S, f0 + f);
+                sc[f] = S.count[S.distinct[f0 + f]];
             }
             __syncthreads();
             for (int f = lane; f < len; f += 32) {
@@ -653,8 +646,6 @@ BulkScratch carve(void* base, int64_t np_cap, int64_t nq_cap, int max_ctas, size
     s.sort.cursor = s.sort.count + T;
     s.sort.n_distinct = s.sort.count + 2 * (size_t)T;
     s.chunk_counter = s.sort.count + 2 * (size_t)T + 1;
-    s.sort.dorder = static_cast<unsigned long long*>(a.take(sizeof(unsigned long long) * T));
-    s.sort.dcount = static_cast<int32_t*>(a.take(sizeof(int32_t) * T));
     s.sort.gstart = static_cast<int64_t*>(a.take(sizeof(int64_t) * T));
     s.sort.distinct = static_cast<int32_t*>(a.take(sizeof(int32_t) * T));
     s.seg = static_cast<kmx::RowBest*>(
@@ -710,8 +701,6 @@ cudaError_t kmx_match_fp32_bulk_launch(kmx_ctx* ctx, const float* dp, const int3
     if ((e = cudaMemsetAsync(b.sort.count, 0, sizeof(int32_t) * (2 * (size_t)b.sort.T + 2), st))) return e;
     KMX_COUNT_LAUNCH();
     mask_insert<<<small_grid, 256, 0, st>>>(b.sort, ctx->d_err);
-    KMX_COUNT_LAUNCH();
-    mask_compact<<<small_grid, 256, 0, st>>>(b.sort);
     KMX_COUNT_LAUNCH();
     mask_rank<<<small_grid, 256, 0, st>>>(b.sort);
     KMX_COUNT_LAUNCH();

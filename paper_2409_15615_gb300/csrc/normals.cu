@@ -220,12 +220,17 @@ __global__ void __launch_bounds__(kThreads) search_fill(GridView g, Radii R, Nor
     }
 }
 
-// |I(q)| of points that a range error kept out of the grid stays 0.
-__global__ void clear_counts(int32_t* cnt, const int64_t* d_n, int64_t n_cap)
+// Zero the counts |I(q)| of the actual points, and the normals and flags of
+// the whole capacity: points that a range error kept out of the grid keep
+// zeros, the others are written by search_fill.
+__global__ void clear_counts(int32_t* cnt, float4* normal4, uint8_t* flags, const int64_t* d_n, int64_t n_cap)
 {
     const int64_t n = kmx_count(d_n, n_cap);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        cnt[i] = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_cap; i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < n) cnt[i] = 0;
+        normal4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        flags[i] = 0;
+    }
 }
 
 // When the lists did not fit (search_fill wrote none of them), every offset
@@ -263,11 +268,9 @@ cudaError_t kmx_normals_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_params
     R.rn2d = (double)prm->r_normal * (double)prm->r_normal;
     const int64_t n = g->n_cap;
     cudaError_t e;
-    // points outside the bucketed set (only after a range error) keep zeros
-    if ((e = cudaMemsetAsync(normal4, 0, sizeof(float4) * n, st))) return e;
-    if ((e = cudaMemsetAsync(flags, 0, n, st))) return e;
     KMX_COUNT_LAUNCH();
-    clear_counts<<<kmx_stride_blocks(n, 256, ctx->sm_count), 256, 0, st>>>(s.cnt, g->d_n, n);
+    clear_counts<<<kmx_stride_blocks(n, 256, ctx->sm_count), 256, 0, st>>>(
+        s.cnt, reinterpret_cast<float4*>(normal4), flags, g->d_n, n);
     KMX_COUNT_LAUNCH();
     search_count<<<kmx_stride_blocks(n, kWarps, ctx->sm_count), kThreads, 0, st>>>(gv, R, s);
     if ((e = kmx_scan_i32(s.cnt, n, g->d_n, offs, s.scan, st, ctx->d_err))) return e;

@@ -14,9 +14,9 @@ namespace {
 constexpr int kThreads = 256;
 
 struct VoxScratch {
-    unsigned long long* keys;  // [T]
-    int32_t* vmin;             // [T] lowest member index
-    int32_t* vcnt;             // [T] member count
+    unsigned long long* keys;  // [T]   \ one allocation, cleared by one
+    uint32_t* vmin;            // [T]    > all-ones memset: empty key, no
+    uint32_t* vcnt;            // [T]   /  member yet, member count - 1
     int32_t* vout;             // [T] output voxel index
     int32_t* pslot;            // [n] slot of each point
     int32_t* flag;             // [n] first-member flag, later member count per output voxel
@@ -36,15 +36,18 @@ uint32_t table_size_for(int64_t n)
     return (uint32_t)t;
 }
 
+// keys, lowest member and member count of every table slot
+size_t table_bytes(uint32_t T) { return (sizeof(unsigned long long) + 2 * sizeof(uint32_t)) * (size_t)T; }
+
 VoxScratch carve(void* base, int64_t n, size_t* total)
 {
     VoxScratch s{};
     kmx_arena a{static_cast<char*>(base), 0};
     s.T = table_size_for(n);
     auto take = [&](size_t b) { return a.take(b); };
-    s.keys = (unsigned long long*)take(sizeof(unsigned long long) * s.T);
-    s.vmin = (int32_t*)take(sizeof(int32_t) * s.T);
-    s.vcnt = (int32_t*)take(sizeof(int32_t) * s.T);
+    s.keys = (unsigned long long*)take(table_bytes(s.T));
+    s.vmin = reinterpret_cast<uint32_t*>(s.keys + s.T);
+    s.vcnt = s.vmin + s.T;
     s.vout = (int32_t*)take(sizeof(int32_t) * s.T);
     s.pslot = (int32_t*)take(sizeof(int32_t) * (n + 1));
     s.flag = (int32_t*)take(sizeof(int32_t) * (n + 1));
@@ -104,8 +107,8 @@ __global__ void __launch_bounds__(kThreads) vox_insert(const float* __restrict__
     if (lane == leader) {
         slot = kmx_hash_insert(s.keys, s.T, key);
         if (slot >= 0) {
-            atomicMin(&s.vmin[slot], (int32_t)r);
-            atomicAdd(&s.vcnt[slot], __popc(grp));
+            atomicMin(&s.vmin[slot], (uint32_t)r);
+            atomicAdd(&s.vcnt[slot], (uint32_t)__popc(grp));  // from all-ones: count - 1
         } else {
             kmx_raise(err, KMX_DERR_HASHFULL);
         }
@@ -119,11 +122,14 @@ __global__ void __launch_bounds__(kThreads) vox_first_flag(int64_t n_cap, const 
     int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (r >= kmx_count(d_n, n_cap)) return;
     int slot = s.pslot[r];
-    s.flag[r] = (slot >= 0 && s.vmin[slot] == (int32_t)r) ? 1 : 0;
+    s.flag[r] = (slot >= 0 && s.vmin[slot] == (uint32_t)r) ? 1 : 0;
 }
 
 // For each first member: number its voxel, record the member count per output
-// voxel (reusing `flag` as the count array), publish the voxel count.
+// voxel (in `flag`, whose first-member flags the scan has consumed), zero the
+// voxel's fill cursor for vox_scatter, publish the voxel count.  Every output
+// voxel o < count is written here, and the scan of the counts reads no entry
+// past the count, so neither array needs clearing beforehand.
 __global__ void __launch_bounds__(kThreads) vox_number(int64_t n, const int64_t* d_n, VoxScratch s, int64_t cap,
                                                        int64_t* n_out, unsigned int* err)
 {
@@ -138,7 +144,8 @@ __global__ void __launch_bounds__(kThreads) vox_number(int64_t n, const int64_t*
     int slot = s.pslot[r];
     int64_t o = s.oidx[r];
     s.vout[slot] = (int32_t)o;
-    s.cursor[o] = s.vcnt[slot];  // temporarily: count per output voxel
+    s.flag[o] = (int32_t)(s.vcnt[slot] + 1u);
+    s.cursor[o] = 0;
 }
 
 __global__ void __launch_bounds__(kThreads) vox_scatter(int64_t n, const int64_t* d_n, VoxScratch s,
@@ -355,9 +362,7 @@ cudaError_t kmx_voxelize_launch(kmx_ctx* ctx, const float* xyz, int64_t n, const
     size_t total = 0;
     VoxScratch s = carve(scratch, n, &total);
     cudaError_t e;
-    if ((e = cudaMemsetAsync(s.keys, 0xFF, sizeof(unsigned long long) * s.T, st))) return e;
-    if ((e = cudaMemsetAsync(s.vmin, 0x7F, sizeof(int32_t) * s.T, st))) return e;
-    if ((e = cudaMemsetAsync(s.vcnt, 0, sizeof(int32_t) * s.T, st))) return e;
+    if ((e = cudaMemsetAsync(s.keys, 0xFF, table_bytes(s.T), st))) return e;
     if (n == 0) {
         return cudaMemsetAsync(n_out, 0, sizeof(int64_t), st);
     }
@@ -367,12 +372,10 @@ cudaError_t kmx_voxelize_launch(kmx_ctx* ctx, const float* xyz, int64_t n, const
     KMX_COUNT_LAUNCH();
     vox_first_flag<<<nb, kThreads, 0, st>>>(n, d_n, s);
     if ((e = kmx_scan_i32(s.flag, n, d_n, s.oidx, s.scan, st, ctx->d_err))) return e;
-    if ((e = cudaMemsetAsync(s.cursor, 0, sizeof(int32_t) * (n + 1), st))) return e;
     KMX_COUNT_LAUNCH();
     vox_number<<<nb, kThreads, 0, st>>>(n, d_n, s, cap, n_out, ctx->d_err);
-    // member offsets per output voxel: scan of the counts parked in `cursor`
-    if ((e = kmx_scan_i32(s.cursor, n, n_out, s.vstart, s.scan, st, ctx->d_err))) return e;
-    if ((e = cudaMemsetAsync(s.cursor, 0, sizeof(int32_t) * (n + 1), st))) return e;
+    // member offsets per output voxel: scan of the counts vox_number left in `flag`
+    if ((e = kmx_scan_i32(s.flag, n, n_out, s.vstart, s.scan, st, ctx->d_err))) return e;
     KMX_COUNT_LAUNCH();
     vox_scatter<<<nb, kThreads, 0, st>>>(n, d_n, s, assign);
     KMX_COUNT_LAUNCH();
