@@ -141,6 +141,7 @@ void kmx_destroy(kmx_ctx* c)
     DeviceGuard g(c->device);
     cudaStreamSynchronize(c->stream);
     if (c->ws) cudaFree(c->ws);
+    if (c->scan_status) cudaFree(c->scan_status);
     cudaFree(c->d_err);
     cudaFreeHost(c->h_err);
     delete c;
@@ -178,6 +179,8 @@ kmx_status kmx_sync(kmx_ctx* c)
     const unsigned int bits = *c->h_err;
     if (!bits) return KMX_OK;
     cudaMemset(c->d_err, 0, sizeof(unsigned int));
+    // a scan that gave up may have left its status words set: start clean
+    if (c->scan_status) cudaMemset(c->scan_status, 0, sizeof(unsigned long long) * (size_t)c->scan_words);
     if (bits & KMX_DERR_RANGE) return fail(c, KMX_ERANGE, "a voxel or cell index does not fit in 21 bits");
     if (bits & KMX_DERR_CAPACITY) return fail(c, KMX_ECAPACITY, "an output buffer is too small");
     if (bits & KMX_DERR_HASHFULL) return fail(c, KMX_ENOMEM, "hash table full");

@@ -25,7 +25,6 @@ struct PfhScratch {
     int32_t* jflag;  // [n+1]
     int64_t* jpos;   // [n+1]
     float* spfh;     // [n][36] when the caller passes none
-    void* scan;
 };
 
 PfhScratch carve(void* base, int64_t n, bool need_spfh, size_t* total)
@@ -35,7 +34,6 @@ PfhScratch carve(void* base, int64_t n, bool need_spfh, size_t* total)
     s.jflag = (int32_t*)a.take(sizeof(int32_t) * (n + 1));
     s.jpos = (int64_t*)a.take(sizeof(int64_t) * (n + 1));
     s.spfh = need_spfh ? (float*)a.take(sizeof(float) * kStride * (n + 1)) : nullptr;
-    s.scan = a.take(kmx_scan_scratch_bytes(n));
     *total = kmx_align_up(a.used, 256);
     return s;
 }
@@ -202,7 +200,7 @@ cudaError_t kmx_fasterpfh_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_para
     KMX_COUNT_LAUNCH();
     spfh_kernel<<<nbw, kThreads, 0, st>>>(n, g->d_n, g->pts, reinterpret_cast<const float4*>(normal4), flags,
                                           offs, nbr, prm->tau_num, sp, s.jflag);
-    if ((e = kmx_scan_i32(s.jflag, n, g->d_n, s.jpos, s.scan, st, ctx->d_err))) return e;
+    if ((e = kmx_scan_i32(ctx, s.jflag, n, g->d_n, s.jpos))) return e;
     KMX_COUNT_LAUNCH();
     scatter_valid<<<kmx_stride_blocks(n, kThreads, ctx->sm_count), kThreads, 0, st>>>(n, g->d_n, s.jflag, s.jpos,
                                                                                        valid, n_valid);

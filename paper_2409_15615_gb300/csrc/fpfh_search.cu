@@ -38,7 +38,6 @@ struct ClassicScratch {
     int32_t* jflag;  // [n+1] 1 if the point is in J
     int64_t* jpos;   // [n+1] exclusive prefix of jflag
     float* spfh;     // [n][36] when the caller passes none
-    void* scan;
 };
 
 ClassicScratch carve(void* base, int64_t n, bool need_spfh, size_t* total)
@@ -48,7 +47,6 @@ ClassicScratch carve(void* base, int64_t n, bool need_spfh, size_t* total)
     s.jflag = (int32_t*)a.take(sizeof(int32_t) * (n + 1));
     s.jpos = (int64_t*)a.take(sizeof(int64_t) * (n + 1));
     s.spfh = need_spfh ? (float*)a.take(sizeof(float) * kStride * (n + 1)) : nullptr;
-    s.scan = a.take(kmx_scan_scratch_bytes(n));
     *total = kmx_align_up(a.used, 256);
     return s;
 }
@@ -394,7 +392,7 @@ cudaError_t kmx_fpfh_search_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_pa
         KMX_COUNT_LAUNCH();
         valid_walk<<<nbw, kThreads, 0, st>>>(gv, R, prm->tau_num, flags, s.jflag);
     }
-    if ((e = kmx_scan_i32(s.jflag, n, g->d_n, s.jpos, s.scan, st, ctx->d_err))) return e;
+    if ((e = kmx_scan_i32(ctx, s.jflag, n, g->d_n, s.jpos))) return e;
     KMX_COUNT_LAUNCH();
     scatter_j<<<kmx_stride_blocks(n, kThreads, ctx->sm_count), kThreads, 0, st>>>(n, g->d_n, s.jflag, s.jpos, valid,
                                                                                    n_valid);

@@ -15,7 +15,6 @@ struct GridScratch {
     int64_t* start;   // [T+1] exclusive scan of cnt
     int32_t* cursor;  // [T] fill cursor
     int32_t* tmp;     // [n] point indices grouped by cell
-    void* scan;
 };
 
 GridScratch carve(void* base, int64_t n, uint32_t T, size_t* total)
@@ -27,7 +26,6 @@ GridScratch carve(void* base, int64_t n, uint32_t T, size_t* total)
     s.cursor = s.cnt ? s.cnt + T : nullptr;
     s.start = (int64_t*)a.take(sizeof(int64_t) * (T + 1));
     s.tmp = (int32_t*)a.take(sizeof(int32_t) * (n + 1));
-    s.scan = a.take(kmx_scan_scratch_bytes(T));
     *total = kmx_align_up(a.used, 256);
     return s;
 }
@@ -134,7 +132,7 @@ cudaError_t kmx_grid_build_launch(kmx_ctx* ctx, kmx_grid* g, void* scratch)
     const unsigned nb = kmx_stride_blocks(g->n_cap, kThreads, ctx->sm_count);
     KMX_COUNT_LAUNCH();
     grid_insert<<<nb, kThreads, 0, st>>>(g->pts, g->n_cap, g->d_n, g->inv_cell, g->keys, T, s, ctx->d_err);
-    if ((e = kmx_scan_i32(s.cnt, T, nullptr, s.start, s.scan, st, ctx->d_err))) return e;
+    if ((e = kmx_scan_i32(ctx, s.cnt, T, nullptr, s.start))) return e;
     KMX_COUNT_LAUNCH();
     grid_cells<<<kmx_blocks(T, kThreads), kThreads, 0, st>>>(T, s, g->cells, g->d_n_sorted);
     KMX_COUNT_LAUNCH();

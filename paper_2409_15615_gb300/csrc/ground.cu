@@ -47,7 +47,6 @@ struct GroundScratch {
     int32_t* cnt;      // [nb+1] members per bin
     int64_t* bstart;   // [nb+1] first member of each bin
     int32_t* cursor;   // [nb+1] fill cursor per bin
-    void* scan;
 };
 
 GroundScratch carve(void* base, int64_t n, int nb, size_t* total)
@@ -62,7 +61,6 @@ GroundScratch carve(void* base, int64_t n, int nb, size_t* total)
     s.cnt = (int32_t*)a.take(sizeof(int32_t) * (nb + 1));
     s.bstart = (int64_t*)a.take(sizeof(int64_t) * (nb + 1));
     s.cursor = (int32_t*)a.take(sizeof(int32_t) * (nb + 1));
-    s.scan = a.take(kmx_scan_scratch_bytes(n > nb ? n : nb));
     *total = kmx_align_up(a.used, 256);
     return s;
 }
@@ -589,7 +587,7 @@ cudaError_t kmx_ground_launch(kmx_ctx* ctx, const float* xyz, int64_t n, int str
     const unsigned nbp = kmx_stride_blocks(n, kThreads, ctx->sm_count);
     KMX_COUNT_LAUNCH();
     gs_bin<<<nbp, kThreads, 0, st>>>(xyz, n, stride, P, s);
-    if ((e = kmx_scan_i32(s.cnt, P.nb, nullptr, s.bstart, s.scan, st, ctx->d_err))) return e;
+    if ((e = kmx_scan_i32(ctx, s.cnt, P.nb, nullptr, s.bstart))) return e;
     KMX_COUNT_LAUNCH();
     gs_scatter<<<nbp, kThreads, 0, st>>>(n, s);
     if ((e = kmx_once_per_device(kmx_attr_ground, [] {
@@ -599,7 +597,7 @@ cudaError_t kmx_ground_launch(kmx_ctx* ctx, const float* xyz, int64_t n, int str
         return e;
     KMX_COUNT_LAUNCH();
     gs_fit<<<(unsigned)P.nb, kThreads, kStage * sizeof(short4), st>>>(P, s, planes);
-    if ((e = kmx_scan_i32(s.keep, n, nullptr, s.pos, s.scan, st, ctx->d_err))) return e;
+    if ((e = kmx_scan_i32(ctx, s.keep, n, nullptr, s.pos))) return e;
     KMX_COUNT_LAUNCH();
     gs_compact<<<nbp, kThreads, 0, st>>>(xyz, n, stride, s, out, n_out, ground);
     return cudaGetLastError();

@@ -30,6 +30,8 @@ struct kmx_ctx {
     unsigned int* h_err;   // pinned host mirror for kmx_sync
     int sm_count;
     int match_ctas_per_sm;  // exact matcher residency, 0 = default
+    unsigned long long* scan_status;  // zeroed look-back area of the scans (scan.cu)
+    int64_t scan_words;
     char msg[256];
 };
 
@@ -173,12 +175,15 @@ inline cudaError_t kmx_once_per_device(int bit, F fn)
 }
 
 // scan.cu: exclusive prefix sum of n int32 values (values at i >= *d_n count
-// as 0) into out[0..n] (int64, out[n] = total).  Scratch bytes needed:
-size_t kmx_scan_scratch_bytes(int64_t n);
-// One launch (plus a memset of the scratch); a look-back wait that runs out
-// raises KMX_DERR_TIMEOUT in *err (a valid device word).
-cudaError_t kmx_scan_i32(const int32_t* in, int64_t n, const int64_t* d_n, int64_t* out, void* scratch,
-                         cudaStream_t s, unsigned int* err);
+// as 0) into out[0..n] (int64, out[n] = total), on the context stream.  One
+// launch; its look-back status words come from the context's zeroed area,
+// grown here when needed (so a first call of a size must not be inside a
+// graph capture).  A look-back wait that runs out raises KMX_DERR_TIMEOUT.
+cudaError_t kmx_scan_i32(kmx_ctx* ctx, const int32_t* in, int64_t n, const int64_t* d_n, int64_t* out);
+// Status words a scan of n values uses.
+int64_t kmx_scan_words(int64_t n);
+// Make the context's zeroed status area hold at least `words` words.
+cudaError_t kmx_scan_reserve(kmx_ctx* ctx, int64_t words);
 
 // voxel.cu
 size_t kmx_voxelize_scratch_bytes(int64_t n_raw);

@@ -63,7 +63,6 @@ size_t match_common_bytes(int64_t np_cap, int64_t nq_cap, int chunks, size_t ext
     a.take(sizeof(unsigned long long) * (nq_cap + 1));
     a.take(sizeof(int32_t) * (np_cap + 1));
     a.take(sizeof(int64_t) * (np_cap + 1));
-    a.take(kmx_scan_scratch_bytes(np_cap));
     a.take(sizeof(RowBest) * (np_cap + 1));
     a.take(sizeof(int) * 4);
     a.take(extra);
@@ -78,7 +77,6 @@ MatchScratch match_common_carve(void* base, int64_t np_cap, int64_t nq_cap, int 
     s.colbest = (unsigned long long*)a.take(sizeof(unsigned long long) * (nq_cap + 1));
     s.mflag = (int32_t*)a.take(sizeof(int32_t) * (np_cap + 1));
     s.mpos = (int64_t*)a.take(sizeof(int64_t) * (np_cap + 1));
-    s.scan = a.take(kmx_scan_scratch_bytes(np_cap));
     s.merged = (RowBest*)a.take(sizeof(RowBest) * (np_cap + 1));
     s.chunks = (int*)a.take(sizeof(int) * 4);
     s.extra = a.take(extra);
@@ -104,7 +102,7 @@ cudaError_t match_emit(kmx_ctx* ctx, const MatchScratch& s, int64_t np_cap, cons
 {
     cudaStream_t st = ctx->stream;
     cudaError_t e;
-    if ((e = kmx_scan_i32(s.mflag, np_cap, d_np, s.mpos, s.scan, st, ctx->d_err))) return e;
+    if ((e = kmx_scan_i32(ctx, s.mflag, np_cap, d_np, s.mpos))) return e;
     KMX_COUNT_LAUNCH();
     emit<<<kmx_stride_blocks(np_cap, kThreads, ctx->sm_count), kThreads, 0, st>>>(np_cap, d_np, s.merged, s.mflag,
                                                                                    s.mpos, vp, vq, out, cap, n_out,

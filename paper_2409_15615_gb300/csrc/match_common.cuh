@@ -62,7 +62,6 @@ struct MatchScratch {
     int64_t* mpos;                // [np_cap + 1]
     RowBest* merged;              // [np_cap] merged row summaries
     int* chunks;                  // chunk count chosen on the device (row partials in `part`)
-    void* scan;
     void* extra;                  // path-specific scratch
 };
 

@@ -16,6 +16,7 @@ namespace {
 
 constexpr int64_t kMaxRows = KMX_NOALLOC_MAX_ROWS;
 constexpr size_t kErrBytes = 256;                 // device error word, own 256-byte slot
+constexpr size_t kStatusBytes = 256;              // the scan's look-back words (32 words)
 constexpr size_t kScratchBytes = 6u << 20;        // >= error slot + match scratch for kMaxRows x kMaxRows
 
 // The scratch.  In host code this name is only a stand-in for the symbol:
@@ -63,8 +64,12 @@ extern "C" kmx_status kmx_match_noalloc(const float* d_desc_p, const int32_t* d_
     c.device = device;
     c.stream = static_cast<cudaStream_t>(cuda_stream);
     c.d_err = static_cast<unsigned int*>(base);
-    c.ws = static_cast<char*>(base) + kErrBytes;
-    c.ws_size = kScratchBytes - kErrBytes;
+    // the scan's status words sit in the array too, so it never grows them
+    c.scan_status = reinterpret_cast<unsigned long long*>(static_cast<char*>(base) + kErrBytes);
+    c.scan_words = kStatusBytes / sizeof(unsigned long long);
+    c.ws = static_cast<char*>(base) + kErrBytes + kStatusBytes;
+    c.ws_size = kScratchBytes - kErrBytes - kStatusBytes;
+    if (kmx_scan_words(np_cap) > c.scan_words) return KMX_EINVAL;  // cannot happen for np_cap <= kMaxRows
     if (cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return KMX_ECUDA;
     if (np_cap == 0 || nq_cap == 0)
         return cudaMemsetAsync(d_n_out, 0, sizeof(int64_t), c.stream) == cudaSuccess ? KMX_OK : KMX_ECUDA;
@@ -74,6 +79,7 @@ extern "C" kmx_status kmx_match_noalloc(const float* d_desc_p, const int32_t* d_
     kmx::MatchScratch s = kmx::match_common_carve(c.ws, np_cap, nq_cap, chunks);
     // the array keeps the previous call's contents: reset what must start fresh
     cudaError_t e = cudaMemsetAsync(c.d_err, 0, sizeof(unsigned int), c.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c.scan_status, 0, kStatusBytes, c.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s.colbest, 0xFF, sizeof(unsigned long long) * nq_cap, c.stream);
     if (e == cudaSuccess) e = kmx_match_fp32_launch(&c, d_desc_p, np_cap, d_np, d_desc_q, nq_cap, d_nq, s, chunks);
     if (e == cudaSuccess) e = kmx::match_finalize(&c, s, np_cap, d_np, d_valid_p, d_valid_q, d_out, cap, d_n_out);

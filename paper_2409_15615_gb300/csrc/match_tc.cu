@@ -572,7 +572,6 @@ struct TcBuffers {
     int32_t *flagP, *flagQ, *listP, *listQ;
     int64_t *posP, *posQ, *nlist;  // nlist[0] P, [1] Q
     kmx::RowBest *fbP, *fbQ;
-    void* scan;
 };
 
 TcBuffers tc_carve(void* base, int64_t np_cap, int64_t nq_cap, size_t* total)
@@ -598,7 +597,6 @@ TcBuffers tc_carve(void* base, int64_t np_cap, int64_t nq_cap, size_t* total)
     b.nlist = (int64_t*)a.take(sizeof(int64_t) * 2);
     b.fbP = (kmx::RowBest*)a.take(sizeof(kmx::RowBest) * (size_t)fc * (np_cap + 1));
     b.fbQ = (kmx::RowBest*)a.take(sizeof(kmx::RowBest) * (size_t)fc * (nq_cap + 1));
-    b.scan = a.take(kmx_scan_scratch_bytes(np_cap > nq_cap ? np_cap : nq_cap));
     *total = kmx_align_up(a.used, 256);
     return b;
 }
@@ -652,10 +650,10 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
     rerank<<<kmx_blocks(nq_cap, 8), 256, 0, st>>>(dq, nq_cap, d_nq, dp, b.candQ, b.chunks + 1, b.mean, b.maxnorm,
                                                   nullptr, s.colbest, b.flagQ, nullptr);
     // exact fallback for the flagged rows of each side
-    if ((e = kmx_scan_i32(b.flagP, np_cap, d_np, b.posP, b.scan, st, ctx->d_err))) return e;
+    if ((e = kmx_scan_i32(ctx, b.flagP, np_cap, d_np, b.posP))) return e;
     KMX_COUNT_LAUNCH();
     compact_flags<<<kmx_blocks(np_cap, 256), 256, 0, st>>>(np_cap, d_np, b.flagP, b.posP, b.listP, b.nlist + 0);
-    if ((e = kmx_scan_i32(b.flagQ, nq_cap, d_nq, b.posQ, b.scan, st, ctx->d_err))) return e;
+    if ((e = kmx_scan_i32(ctx, b.flagQ, nq_cap, d_nq, b.posQ))) return e;
     KMX_COUNT_LAUNCH();
     compact_flags<<<kmx_blocks(nq_cap, 256), 256, 0, st>>>(nq_cap, d_nq, b.flagQ, b.posQ, b.listQ, b.nlist + 1);
     if ((e = kmx_match_fp32_rows_launch(ctx, dp, b.listP, np_cap, b.nlist + 0, dq, nq_cap, d_nq, b.fbP,

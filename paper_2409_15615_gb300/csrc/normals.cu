@@ -32,7 +32,6 @@ constexpr int kQPerBlock = kWarps * kQPerWarp;  // = 32, one per lane of the sol
 struct NormScratch {
     int32_t* cnt;    // [n+1] |I(q)|
     float4* mean;    // [n] P_normal mean minus the query point; w = |P_normal| (int bits)
-    void* scan;
 };
 
 NormScratch carve(void* base, int64_t n, size_t* total)
@@ -41,7 +40,6 @@ NormScratch carve(void* base, int64_t n, size_t* total)
     kmx_arena a{static_cast<char*>(base), 0};
     s.cnt = (int32_t*)a.take(sizeof(int32_t) * (n + 1));
     s.mean = (float4*)a.take(sizeof(float4) * (n + 1));
-    s.scan = a.take(kmx_scan_scratch_bytes(n));
     *total = kmx_align_up(a.used, 256);
     return s;
 }
@@ -273,7 +271,7 @@ cudaError_t kmx_normals_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_params
         s.cnt, reinterpret_cast<float4*>(normal4), flags, g->d_n, n);
     KMX_COUNT_LAUNCH();
     search_count<<<kmx_stride_blocks(n, kWarps, ctx->sm_count), kThreads, 0, st>>>(gv, R, s);
-    if ((e = kmx_scan_i32(s.cnt, n, g->d_n, offs, s.scan, st, ctx->d_err))) return e;
+    if ((e = kmx_scan_i32(ctx, s.cnt, n, g->d_n, offs))) return e;
     NormOut o{reinterpret_cast<float4*>(normal4), flags, offs, nbr, nbr_cap, n, needed, prm->tau_num,
               prm->tau_lin, {prm->viewpoint[0], prm->viewpoint[1], prm->viewpoint[2]}};
     KMX_COUNT_LAUNCH();

@@ -11,6 +11,12 @@
 // holds the flag in its top two bits and the value below, so one 64-bit load
 // sees both.  Every spin is bounded: when it runs out the CTA records
 // KMX_DERR_TIMEOUT and finishes with a wrong prefix instead of waiting on.
+//
+// The status words live in one zeroed area per context.  Each CTA counts
+// itself finished after its last status access, and the last one zeroes the
+// words the scan used, so the next scan on the context starts from zeros
+// without a memset (one graph node less per scan).  kmx_sync zeroes the area
+// again whenever a device error was recorded.
 #include "kmx_internal.cuh"
 
 namespace {
@@ -33,22 +39,28 @@ __device__ __forceinline__ void store_status(unsigned long long* p, unsigned lon
     *reinterpret_cast<volatile unsigned long long*>(p) = v;
 }
 
-// status[0] is the tile counter, status[1 + t] the status word of tile t; all
-// zero before the launch.  Entries at i >= count read as 0; out[i] is written
-// for i < len.
+// status[0] is the tile counter, status[1] the count of finished CTAs,
+// status[2 + t] the status word of tile t; all zero before the launch and
+// zeroed again by the last CTA.  Entries at i >= count read as 0; out[i] is
+// written for i < len.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) scan_onepass(const T* __restrict__ in, int64_t len, int64_t count_cap,
                                                          const int64_t* __restrict__ d_count,
                                                          int64_t* __restrict__ out,
-                                                         unsigned long long* __restrict__ status,
+                                                         unsigned long long* __restrict__ status, int64_t tiles,
                                                          unsigned int* __restrict__ err)
 {
     __shared__ int64_t wsum[kThreads / 32];
     __shared__ int64_t tile_prefix;
+    __shared__ int last;
     __shared__ int64_t tile_id;
     if (threadIdx.x == 0) tile_id = (int64_t)atomicAdd(status, 1ull);
     __syncthreads();
     const int64_t tile = tile_id;
+    if (tile >= tiles) {  // the area was not zero at launch: an earlier scan did not finish
+        if (threadIdx.x == 0) kmx_raise(err, KMX_DERR_TIMEOUT);
+        return;
+    }
     const int64_t count = d_count ? min(*d_count, count_cap) : count_cap;
     const int64_t base = tile * kTile + (int64_t)threadIdx.x * kItems;
     int64_t v[kItems];
@@ -77,7 +89,7 @@ __global__ void __launch_bounds__(kThreads) scan_onepass(const T* __restrict__ i
         }
         if (lane < kThreads / 32) wsum[lane] = w;
         const int64_t total = __shfl_sync(0xffffffffu, w, kThreads / 32 - 1);
-        unsigned long long* st = status + 1;
+        unsigned long long* st = status + 2;
         int64_t excl = 0;
         if (tile == 0) {
             if (lane == 0) store_status(&st[0], kFlagIncl | ((unsigned long long)total & kValueMask));
@@ -112,9 +124,19 @@ __global__ void __launch_bounds__(kThreads) scan_onepass(const T* __restrict__ i
                 store_status(&st[tile], kFlagIncl | ((unsigned long long)(excl + total) & kValueMask));
             }
         }
-        if (lane == 0) tile_prefix = excl;
+        if (lane == 0) {
+            tile_prefix = excl;
+            // this CTA's status accesses are done (the look-back's loads were
+            // consumed by the warp before lane 0 got here)
+            __threadfence();
+            last = atomicAdd(status + 1, 1ull) == (unsigned long long)(tiles - 1);
+        }
     }
     __syncthreads();
+    if (last) {
+        // every CTA has finished with the status words: leave them zero
+        for (int64_t i = threadIdx.x; i < tiles + 2; i += kThreads) store_status(&status[i], 0ull);
+    }
     int64_t e = tile_prefix + x - s + (warp ? wsum[warp - 1] : 0);
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
@@ -128,17 +150,37 @@ int64_t tiles_for(int64_t len) { return len > 0 ? (len + kTile - 1) / kTile : 1;
 
 }  // namespace
 
-size_t kmx_scan_scratch_bytes(int64_t n) { return kmx_align_up((size_t)(tiles_for(n + 1) + 1) * 8, 256); }
+int64_t kmx_scan_words(int64_t n) { return tiles_for(n + 1) + 2; }
 
-cudaError_t kmx_scan_i32(const int32_t* in, int64_t n, const int64_t* d_n, int64_t* out, void* scratch,
-                         cudaStream_t s, unsigned int* err)
+cudaError_t kmx_scan_reserve(kmx_ctx* ctx, int64_t words)
+{
+    if (ctx->scan_status && words <= ctx->scan_words) return cudaSuccess;
+    int64_t want = ctx->scan_words + ctx->scan_words / 2;
+    if (want < words) want = words;
+    if (want < 4096) want = 4096;
+    if (ctx->scan_status) cudaFreeAsync(ctx->scan_status, ctx->stream);
+    ctx->scan_status = nullptr;
+    ctx->scan_words = 0;
+    void* p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, (size_t)want * 8, ctx->stream);
+    if (e) return e;
+    if ((e = cudaMemsetAsync(p, 0, (size_t)want * 8, ctx->stream))) {
+        cudaFreeAsync(p, ctx->stream);
+        return e;
+    }
+    ctx->scan_status = static_cast<unsigned long long*>(p);
+    ctx->scan_words = want;
+    return cudaSuccess;
+}
+
+cudaError_t kmx_scan_i32(kmx_ctx* ctx, const int32_t* in, int64_t n, const int64_t* d_n, int64_t* out)
 {
     const int64_t len = n + 1;
     const int64_t tiles = tiles_for(len);
-    unsigned long long* status = static_cast<unsigned long long*>(scratch);
-    cudaError_t e = cudaMemsetAsync(status, 0, (size_t)(tiles + 1) * 8, s);
+    cudaError_t e = kmx_scan_reserve(ctx, kmx_scan_words(n));
     if (e) return e;
     KMX_COUNT_LAUNCH();
-    scan_onepass<int32_t><<<(unsigned)tiles, kThreads, 0, s>>>(in, len, n, d_n, out, status, err);
+    scan_onepass<int32_t><<<(unsigned)tiles, kThreads, 0, ctx->stream>>>(in, len, n, d_n, out, ctx->scan_status,
+                                                                          tiles, ctx->d_err);
     return cudaGetLastError();
 }

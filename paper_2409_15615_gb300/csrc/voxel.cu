@@ -25,7 +25,6 @@ struct VoxScratch {
     int32_t* cursor;           // [n] fill cursor per output voxel
     int32_t* members;          // [n] grouped members (arbitrary order inside a voxel)
     float4* run;               // [n] member coordinates per voxel, in input order
-    void* scan;
     uint32_t T;
 };
 
@@ -56,7 +55,6 @@ VoxScratch carve(void* base, int64_t n, size_t* total)
     s.cursor = (int32_t*)take(sizeof(int32_t) * (n + 1));
     s.members = (int32_t*)take(sizeof(int32_t) * (n + 1));
     s.run = (float4*)take(sizeof(float4) * (n + 1));
-    s.scan = take(kmx_scan_scratch_bytes(n));
     *total = kmx_align_up(a.used, 256);
     return s;
 }
@@ -371,11 +369,11 @@ cudaError_t kmx_voxelize_launch(kmx_ctx* ctx, const float* xyz, int64_t n, const
     vox_insert<<<nb, kThreads, 0, st>>>(xyz, n, d_n, stride, v, (double)v, s, ctx->d_err);
     KMX_COUNT_LAUNCH();
     vox_first_flag<<<nb, kThreads, 0, st>>>(n, d_n, s);
-    if ((e = kmx_scan_i32(s.flag, n, d_n, s.oidx, s.scan, st, ctx->d_err))) return e;
+    if ((e = kmx_scan_i32(ctx, s.flag, n, d_n, s.oidx))) return e;
     KMX_COUNT_LAUNCH();
     vox_number<<<nb, kThreads, 0, st>>>(n, d_n, s, cap, n_out, ctx->d_err);
     // member offsets per output voxel: scan of the counts vox_number left in `flag`
-    if ((e = kmx_scan_i32(s.flag, n, n_out, s.vstart, s.scan, st, ctx->d_err))) return e;
+    if ((e = kmx_scan_i32(ctx, s.flag, n, n_out, s.vstart))) return e;
     KMX_COUNT_LAUNCH();
     vox_scatter<<<nb, kThreads, 0, st>>>(n, d_n, s, assign);
     KMX_COUNT_LAUNCH();
