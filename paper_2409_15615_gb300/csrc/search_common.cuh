@@ -98,11 +98,42 @@ __device__ __forceinline__ void cross3(const double* a, const double* b, double*
 
 // Eigenvalues l1 >= l2 >= l3 of a symmetric 3x3 matrix and a unit eigenvector
 // of l3.  Returns false if the matrix is a multiple of the identity.
+//
+// GB300 issues FP64 at a small fraction of the FP32 rate, and an FP64 divide
+// or square root is a long instruction sequence, so the reciprocals and
+// reciprocal square roots below start from the FP32 intrinsic and take one
+// FP64 Newton-Raphson step (r <- r (2 - x r) for 1/x, r <- r (3 - x r^2) / 2
+// for 1/sqrt(x)), which squares the FP32 start's relative error (about 1e-7)
+// to about 1e-14: far below the 1e-8 the eigenvalues are accurate to.
+// Arguments outside [2^-100, 2^100] take the FP64 operation itself.
+__device__ __forceinline__ bool fp32_range(double x) { return x > 0x1p-100 && x < 0x1p100; }
+
+__device__ __forceinline__ double recip64(double x)
+{
+    if (!fp32_range(x)) return 1.0 / x;
+    const double r = (double)__frcp_rn((float)x);
+    return r * fma(-x, r, 2.0);
+}
+
+__device__ __forceinline__ double rsqrt64(double x)
+{
+    if (!fp32_range(x)) return 1.0 / sqrt(x);
+    const double r = (double)rsqrtf((float)x);
+    return r * fma(-0.5 * x, r * r, 1.5);
+}
+
+// sqrt(x) = x / sqrt(x) for x > 0, 0 for x <= 0
+__device__ __forceinline__ double sqrt64(double x)
+{
+    if (!(x > 0.0)) return 0.0;
+    return fp32_range(x) ? x * rsqrt64(x) : sqrt(x);
+}
+
 __device__ __forceinline__ bool eig_sym3(double a00, double a01, double a02, double a11, double a12, double a22,
                                          double* l, double* nv)
 {
     const double p1 = a01 * a01 + a02 * a02 + a12 * a12;
-    const double q = (a00 + a11 + a22) / 3.0;
+    const double q = (a00 + a11 + a22) * (1.0 / 3.0);
     const double b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
     const double p2 = b00 * b00 + b11 * b11 + b22 * b22 + 2.0 * p1;
     if (!(p2 > 0.0)) {
@@ -139,9 +170,9 @@ __device__ __forceinline__ bool eig_sym3(double a00, double a01, double a02, dou
     for (int it = 0; it < 2; ++it) {
         const double g = mu * (mu * mu - h) - det;
         const double dg = 3.0 * mu * mu - h;
-        if (dg > 0.0) mu -= g / dg;  // dg > 0 beyond +-p
+        if (dg > 0.0) mu -= g * recip64(dg);  // dg > 0 beyond +-p
     }
-    const double sd = sqrt(fmax(0.0, 2.0 * p2 - 3.0 * mu * mu));
+    const double sd = sqrt64(2.0 * p2 - 3.0 * mu * mu);
     if (top) {
         l[0] = q + mu;
         l[1] = q + 0.5 * (-mu + sd);
@@ -180,7 +211,7 @@ __device__ __forceinline__ bool eig_sym3(double a00, double a01, double a02, dou
         nv[2] = 1.0;
         return true;
     }
-    const double inv = 1.0 / sqrt(nb);
+    const double inv = rsqrt64(nb);
     nv[0] = cx * inv;
     nv[1] = cy * inv;
     nv[2] = cz * inv;
@@ -196,7 +227,7 @@ __device__ __forceinline__ bool eig_sym3(double a00, double a01, double a02, dou
 __device__ __forceinline__ bool normal_from_moments(const float* mom, int nN, float qx, float qy, float qz,
                                                     const float* vp, float4* nout, double* plin_out)
 {
-    const double inv = 1.0 / (double)nN;
+    const double inv = recip64((double)nN);
     const double m0 = (double)mom[0] * inv, m1 = (double)mom[1] * inv, m2 = (double)mom[2] * inv;
     const double c00 = (double)mom[3] * inv - m0 * m0, c01 = (double)mom[4] * inv - m0 * m1;
     const double c02 = (double)mom[5] * inv - m0 * m2, c11 = (double)mom[6] * inv - m1 * m1;
