@@ -52,3 +52,21 @@ def test_params_default_is_host_only(lib):
     assert list(p.viewpoint) == [1.0, 2.0, 3.0]
     bad = kmx.Params()
     assert kmx.library().kmx_params_default(-1.0, ctypes.byref(bad)) == kmx.KMX_EINVAL
+
+
+def test_context_setters_refuse_a_null_context_without_a_device(lib):
+    # argument checks come before any CUDA call, so they run without a GPU
+    from paper_2409_15615_gb300 import kmx
+
+    L = kmx.library()
+    assert L.kmx_set_match_residency(None, 1) == kmx.KMX_EINVAL
+    assert L.kmx_set_stream(None, None) == kmx.KMX_EINVAL
+    assert L.kmx_reserve(None, 0) == kmx.KMX_EINVAL
+    assert L.kmx_sync(None) == kmx.KMX_EINVAL
+
+
+def test_pair_stream_needs_a_slot():
+    from paper_2409_15615_gb300 import pipeline
+
+    with pytest.raises(ValueError):
+        pipeline.PairStream(None, 1, 1, slots=0)
