@@ -64,7 +64,8 @@ constexpr uint32_t kPBytes = kDim * kTile * sizeof(float2);  // 33792
 constexpr uint32_t kQBytes = kDim * kTile * sizeof(float);   // 16896
 constexpr uint32_t kPermBytes = kTile * sizeof(int32_t);     // 512
 constexpr int kCtasPerSm = 2;
-constexpr int kChunksPerCta = 8;  // chunks of the tile sequence per resident CTA (load balance)
+constexpr int kChunksPerCta = 8;      // chunks of the tile sequence per resident CTA (load balance)
+constexpr int kTailChunksPerCta = 4;  // smaller chunks per CTA for the end of the sequence
 constexpr int kMinChunk = 4;       // tile pairs per chunk at least (more than kStages - 1)
 
 // Thread 0's position in its own stream of tile pairs (kept in shared memory:
@@ -77,6 +78,20 @@ struct Producer {
     int ct;
     int par;
     int st;
+    int len;  // length of chunk c
+};
+
+// The flattened tile sequence (row-major over packed row tiles x column
+// tiles) is cut into chunks that CTAs take from a counter, so a CTA whose
+// tile pairs need many dimensions simply takes fewer chunks: NA chunks of
+// LA pairs, then the last W - WA pairs (about one large chunk per CTA) in
+// chunks of LB <= LA pairs, so that the CTAs finish within a small chunk of
+// each other.  Chunks are contiguous and only the last one may be short, so
+// the segment of chunk c in row tile rt can live in slot c + rt (unique,
+// below NC + npt).
+struct ChunkGeo {
+    int LA, NA, LB, NC;
+    int64_t WA;
 };
 
 struct __align__(16) BulkShared {
@@ -90,6 +105,7 @@ struct __align__(16) BulkShared {
     uint64_t bar_p;
     uint64_t bar_q[kStages];
     Producer prod;
+    ChunkGeo cg;                                        // the chunk geometry (thread 0 writes it once)
     int chunk[2];                                       // chunk ids of the current and next local chunk
     int end_item;                                       // first local item past the stream (INT_MAX = unknown)
     int failed;
@@ -295,22 +311,31 @@ __device__ __forceinline__ void row_step(unsigned long long& k1, float& b2, floa
 
 constexpr unsigned long long kNoBest = (0x7f800000ull << 32) | 0x7fffffffull;  // (+inf, no column)
 
-// The flattened tile sequence (row-major over packed row tiles x column
-// tiles) is cut into NC chunks of L consecutive tile pairs; CTAs take chunks
-// from a counter, so a CTA whose tile pairs need many dimensions simply takes
-// fewer chunks.  The chunk holding tile x is x / L; the segment of chunk c in
-// row tile rt lives in slot c + rt (chunks are contiguous, so slots are
-// unique and below NC + npt).
-struct ChunkGeo {
-    int L, NC;
-};
-
 __device__ __forceinline__ ChunkGeo chunk_geo(int64_t W, int ctas)
 {
     const int64_t per = (int64_t)kChunksPerCta * ctas;
-    int64_t L = (W + per - 1) / per;
-    if (L < kMinChunk) L = kMinChunk;
-    return ChunkGeo{(int)L, (int)((W + L - 1) / L)};
+    int64_t LA = (W + per - 1) / per;
+    if (LA < kMinChunk) LA = kMinChunk;
+    const int64_t tail = W < ctas * LA ? W : ctas * LA;
+    const int64_t NA = (W - tail) / LA;
+    const int64_t WA = NA * LA;
+    const int64_t tper = (int64_t)kTailChunksPerCta * ctas;
+    int64_t LB = (W - WA + tper - 1) / tper;
+    if (LB < kMinChunk) LB = kMinChunk;
+    const int64_t NB = (W - WA + LB - 1) / LB;
+    return ChunkGeo{(int)LA, (int)NA, (int)LB, (int)(NA + NB), WA};
+}
+
+__device__ __forceinline__ int64_t chunk_start(const ChunkGeo& g, int c)
+{
+    return c < g.NA ? (int64_t)c * g.LA : g.WA + (int64_t)(c - g.NA) * g.LB;
+}
+
+__device__ __forceinline__ int chunk_len(const ChunkGeo& g, int c) { return c < g.NA ? g.LA : g.LB; }
+
+__device__ __forceinline__ int64_t chunk_of(const ChunkGeo& g, int64_t x)
+{
+    return x < g.WA ? x / g.LA : g.NA + (x - g.WA) / g.LB;
 }
 
 __device__ __forceinline__ int read_end(const BulkShared& S) { return *reinterpret_cast<const volatile int*>(&S.end_item); }
@@ -325,12 +350,13 @@ __device__ __forceinline__ bool produce(BulkShared& S, int u, const ChunkGeo& cg
                                         const unsigned long long* __restrict__ qmask, int& issued)
 {
     Producer& P = S.prod;
-    if (P.o == cg.L) {
+    if (P.o == P.len) {
         P.par ^= 1;
         P.o = 0;
         P.c = atomicAdd(counter, 1);
         S.chunk[P.par] = P.c;
-        P.x = (int64_t)P.c * cg.L;
+        P.x = chunk_start(cg, P.c);
+        P.len = chunk_len(cg, P.c);
         P.ct = (int)(P.x % nqt);
     }
     if (P.c >= cg.NC || P.x >= W) {
@@ -366,7 +392,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     const int nqt = (int)tiles_of(nq);
     const int64_t W = (int64_t)npt * nqt;
     if (W == 0) return;
-    const ChunkGeo cg = chunk_geo(W, ctas);
+    const ChunkGeo& cg = S.cg;  // read from shared memory where needed (registers are full)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tx = tid & 15;                     // column group: columns 4tx..4tx+3 and 64+4tx..64+4tx+3
     const int ty = warp * 2 + ((tid >> 4) & 1);  // row group: rows 8ty..8ty+7
@@ -377,6 +403,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
         mbar_fence_init();
         S.failed = 0;
         S.end_item = INT_MAX;
+        S.cg = chunk_geo(W, ctas);
     }
     __syncthreads();
     int issued = 0;  // meaningful in thread 0: local items whose copies were issued
@@ -386,8 +413,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
         if (c0 >= cg.NC) {
             S.end_item = 0;
         } else {
-            const int64_t x0 = (int64_t)c0 * cg.L;
-            S.prod = Producer{x0, c0, 0, (int)(x0 % nqt), 0, 0};
+            const int64_t x0 = chunk_start(cg, c0);
+            S.prod = Producer{x0, c0, 0, (int)(x0 % nqt), 0, 0, chunk_len(cg, c0)};
             const int64_t rt0 = x0 / nqt;
             mbar_expect_tx(&S.bar_p, kPBytes + kPermBytes + 16);
             bulk_g2s(S.P, pp + rt0 * kDim * kTile, kPBytes, &S.bar_p);
@@ -399,13 +426,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     }
     __syncthreads();
     if (read_end(S) == 0) return;
-    // this thread's view of the current item: chunk id and parity, offset in
-    // the chunk, row and column tile, ring stage and its phase
+    // this thread's view of the current item: chunk id and parity, items
+    // left in the chunk after it, row and column tile, ring stage and phase
     int cid = S.chunk[0];
     int kpar = 0;
-    int o = 0;
-    int rt = (int)(((int64_t)cid * cg.L) / nqt);
-    int ct = (int)(((int64_t)cid * cg.L) - (int64_t)rt * nqt);
+    int left = chunk_len(cg, cid) - 1;
+    int rt = (int)(chunk_start(cg, cid) / nqt);
+    int ct = (int)(chunk_start(cg, cid) - (int64_t)rt * nqt);
     int s = 0;
     uint32_t qphase = 0;
     uint32_t p_phase = 0;
@@ -509,7 +536,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
             }
             if (col0 + tid < nq && best != ~0ull) atomicMin(&colbest[S.qperm[s][tid]], best);
         }
-        const bool seg_end = (o == cg.L - 1) || (ct + 1 == nqt);  // row tile, chunk or sequence ends
+        const bool seg_end = (left == 0) || (ct + 1 == nqt);  // row tile, chunk or sequence ends
         if (seg_end && !failed) {
             // merge the 16 column groups of each row (one half-warp), write
             // the segment of (chunk, row tile), restart the row bests
@@ -537,8 +564,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
         // kStages items ago); a new row tile reloads the source tile
         if (t + 1 < read_end(S)) {
             int rt1;
-            if (o + 1 < cg.L) {
-                ++o;
+            if (left > 0) {
+                --left;
                 rt1 = rt;
                 if (++ct == nqt) {
                     ct = 0;
@@ -547,8 +574,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
             } else {
                 kpar ^= 1;
                 cid = S.chunk[kpar];
-                o = 0;
-                const int64_t x1 = (int64_t)cid * cg.L;
+                left = chunk_len(cg, cid) - 1;
+                const int64_t x1 = chunk_start(cg, cid);
                 rt1 = (int)(x1 / nqt);
                 ct = (int)(x1 - (int64_t)rt1 * nqt);
             }
@@ -597,7 +624,7 @@ __global__ void __launch_bounds__(256) merge_segments(const kmx::RowBest* __rest
         if (W > 0) {
             const ChunkGeo cg = chunk_geo(W, ctas);
             const int64_t rt = i / kTile;
-            const int64_t cf = (rt * nqt) / cg.L, cl = (rt * nqt + nqt - 1) / cg.L;
+            const int64_t cf = chunk_of(cg, rt * nqt), cl = chunk_of(cg, rt * nqt + nqt - 1);
             r = seg[(cf + rt) * kTile + (i % kTile)];
             for (int64_t c = cf + 1; c <= cl; ++c) {
                 const kmx::RowBest o = seg[(c + rt) * kTile + (i % kTile)];
@@ -649,7 +676,8 @@ BulkScratch carve(void* base, int64_t np_cap, int64_t nq_cap, int max_ctas, size
     s.sort.gstart = static_cast<int64_t*>(a.take(sizeof(int64_t) * T));
     s.sort.distinct = static_cast<int32_t*>(a.take(sizeof(int32_t) * T));
     s.seg = static_cast<kmx::RowBest*>(
-        a.take(sizeof(kmx::RowBest) * kTile * (size_t)(kChunksPerCta * max_ctas + 1 + tiles_of(np_cap))));
+        a.take(sizeof(kmx::RowBest) * kTile *
+               (size_t)((kChunksPerCta + kTailChunksPerCta) * max_ctas + 1 + tiles_of(np_cap))));
     *total = kmx_align_up(a.used, 256);
     return s;
 }

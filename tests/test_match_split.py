@@ -1,26 +1,46 @@
 """Host model of the exact matcher's work split (match_fp32_bulk.cu).
 
 The (row tile x column tile) grid, W = npt * nqt tile pairs flattened
-row-major, is cut into NC chunks of L consecutive pairs, with
-L = max(4, ceil(W / (8 * ctas))); CTAs take chunks from a counter.  The
-segment of chunk c in row tile rt sits in slot c + rt of a
-(8 * ctas + 1 + npt) * 128 array, and merge_segments reads the chunks
-floor(rt * nqt / L) .. floor((rt * nqt + nqt - 1) / L) of row tile rt.
-These checks pin that arithmetic for any order in which the CTAs take the
-chunks: every tile pair is covered exactly once, slots are unique and in
-bounds, and the merge reads exactly the segments written for its row tile.
+row-major, is cut into chunks of consecutive pairs that CTAs take from a
+counter: NA chunks of LA = max(4, ceil(W / (8 * ctas))) pairs, then the
+last W - NA * LA pairs (about one large chunk per CTA) in chunks of
+LB = max(4, ceil(that / (4 * ctas))) pairs, so that the CTAs finish
+within a small chunk of each other.  The segment of chunk c in row tile rt
+sits in slot c + rt of a ((8 + 4) * ctas + 1 + npt) * 128 array, and
+merge_segments reads the chunks chunk_of(rt * nqt) .. chunk_of(rt * nqt +
+nqt - 1) of row tile rt.  These checks pin that arithmetic for any order in
+which the CTAs take the chunks: every tile pair is covered exactly once,
+slots are unique and in bounds, and the merge reads exactly the segments
+written for its row tile.
 """
 import random
 
 TILE = 128
 CHUNKS_PER_CTA = 8
+TAIL_CHUNKS_PER_CTA = 4
 MIN_CHUNK = 4
 
 
 def chunk_geo(W, ctas):
     per = CHUNKS_PER_CTA * ctas
-    L = max(MIN_CHUNK, -(-W // per))
-    return L, -(-W // L)
+    LA = max(MIN_CHUNK, -(-W // per))
+    NA = (W - min(W, ctas * LA)) // LA
+    WA = NA * LA
+    LB = max(MIN_CHUNK, -(-(W - WA) // (TAIL_CHUNKS_PER_CTA * ctas)))
+    NC = NA + -(-(W - WA) // LB)
+    return dict(LA=LA, NA=NA, WA=WA, LB=LB, NC=NC)
+
+
+def chunk_start(g, c):
+    return c * g["LA"] if c < g["NA"] else g["WA"] + (c - g["NA"]) * g["LB"]
+
+
+def chunk_len(g, c):
+    return g["LA"] if c < g["NA"] else g["LB"]
+
+
+def chunk_of(g, x):
+    return x // g["LA"] if x < g["WA"] else g["NA"] + (x - g["WA"]) // g["LB"]
 
 
 def _check(n_p, n_q, ctas):
@@ -28,24 +48,32 @@ def _check(n_p, n_q, ctas):
     W = npt * nqt
     if W == 0:
         return
-    L, NC = chunk_geo(W, ctas)
-    assert NC <= CHUNKS_PER_CTA * ctas and L > 3
+    g = chunk_geo(W, ctas)
+    NC = g["NC"]
+    assert NC <= (CHUNKS_PER_CTA + TAIL_CHUNKS_PER_CTA) * ctas
+    assert g["LA"] >= MIN_CHUNK and g["LB"] >= MIN_CHUNK and g["LB"] <= g["LA"]
     slots = {}
     covered = [0] * W
     for c in range(NC):  # the CTA that takes a chunk does not change what it writes
+        L = chunk_len(g, c)
         for o in range(L):
-            x = c * L + o
+            x = chunk_start(g, c) + o
             if x >= W:
                 break
+            assert chunk_of(g, x) == c
             covered[x] += 1
             rt, ct = divmod(x, nqt)
             if o == L - 1 or ct + 1 == nqt:  # segment end, as in the kernel
                 key = c + rt
-                assert key not in slots and key < CHUNKS_PER_CTA * ctas + 1 + npt
+                assert key not in slots
+                assert key < (CHUNKS_PER_CTA + TAIL_CHUNKS_PER_CTA) * ctas + 1 + npt
                 slots[key] = (c, rt)
     assert covered == [1] * W
+    # only the last chunk may be cut short by W
+    for c in range(NC - 1):
+        assert chunk_start(g, c) + chunk_len(g, c) == chunk_start(g, c + 1)
     for rt in range(npt):
-        cf, cl = rt * nqt // L, (rt * nqt + nqt - 1) // L
+        cf, cl = chunk_of(g, rt * nqt), chunk_of(g, rt * nqt + nqt - 1)
         assert [slots[c + rt] for c in range(cf, cl + 1)] == [(c, rt) for c in range(cf, cl + 1)]
 
 
