@@ -44,47 +44,53 @@ NormScratch carve(void* base, int64_t n, size_t* total)
     return s;
 }
 
-// Pass 1: |I(q)|, |P_normal| and the P_normal mean (relative to q).
+// Pass 1: |I(q)|, |P_normal| and the P_normal mean (relative to q).  A warp
+// takes kQPerWarp consecutive queries (cell order) and looks their stencil
+// up once per cell.
 __global__ void __launch_bounds__(kThreads) search_count(GridView g, Radii R, NormScratch s)
 {
     const int lane = threadIdx.x & 31;
     const int64_t n_sorted = *g.n_sorted;
-    for (int64_t p = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); p < n_sorted; p += (int64_t)gridDim.x * kWarps) {
-        const float4 q = g.sorted[p];
-        const int qi = __float_as_int(q.w);
-        int start, excl;
-        const int total = stencil(g, q, lane, &start, &excl);
-        int nf = 0, nn = 0;
-        float sx = 0.f, sy = 0.f, sz = 0.f;
-        for (int base = 0; base < total; base += 32) {
-            const int t = base + lane;
-            const int pos = candidate(t, start, excl);
-            bool inF = false, inN = false;
-            float dx = 0.f, dy = 0.f, dz = 0.f;
-            if (t < total) {
-                const float4 a = g.sorted[pos];
-                dx = a.x - q.x;
-                dy = a.y - q.y;
-                dz = a.z - q.z;
-                const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                inF = within(a, q, d2, R.rf2, R.rf2d);
-                inN = inF && within(a, q, d2, R.rn2, R.rn2d);
+    const int64_t warps = (int64_t)gridDim.x * kWarps;
+    for (int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); w * kQPerWarp < n_sorted; w += warps) {
+        StencilCache sc;
+        for (int k = 0; k < kQPerWarp && w * kQPerWarp + k < n_sorted; ++k) {
+            const float4 q = g.sorted[w * kQPerWarp + k];
+            const int qi = __float_as_int(q.w);
+            const int total = sc.get(g, q, lane);
+            const int start = sc.start, excl = sc.excl;
+            int nf = 0, nn = 0;
+            float sx = 0.f, sy = 0.f, sz = 0.f;
+            for (int base = 0; base < total; base += 32) {
+                const int t = base + lane;
+                const int pos = candidate(t, start, excl);
+                bool inF = false, inN = false;
+                float dx = 0.f, dy = 0.f, dz = 0.f;
+                if (t < total) {
+                    const float4 a = g.sorted[pos];
+                    dx = a.x - q.x;
+                    dy = a.y - q.y;
+                    dz = a.z - q.z;
+                    const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    inF = within(a, q, d2, R.rf2, R.rf2d);
+                    inN = inF && within(a, q, d2, R.rn2, R.rn2d);
+                }
+                nf += __popc(__ballot_sync(kFull, inF));
+                nn += __popc(__ballot_sync(kFull, inN));
+                if (inN) {
+                    sx += dx;
+                    sy += dy;
+                    sz += dz;
+                }
             }
-            nf += __popc(__ballot_sync(kFull, inF));
-            nn += __popc(__ballot_sync(kFull, inN));
-            if (inN) {
-                sx += dx;
-                sy += dy;
-                sz += dz;
+            sx = warp_sum(sx);
+            sy = warp_sum(sy);
+            sz = warp_sum(sz);
+            if (lane == 0) {
+                s.cnt[qi] = nf;
+                const float inv = nn > 0 ? 1.0f / (float)nn : 0.0f;
+                s.mean[qi] = make_float4(sx * inv, sy * inv, sz * inv, __int_as_float(nn));
             }
-        }
-        sx = warp_sum(sx);
-        sy = warp_sum(sy);
-        sz = warp_sum(sz);
-        if (lane == 0) {
-            s.cnt[qi] = nf;
-            const float inv = nn > 0 ? 1.0f / (float)nn : 0.0f;
-            s.mean[qi] = make_float4(sx * inv, sy * inv, sz * inv, __int_as_float(nn));
         }
     }
 }
@@ -121,6 +127,7 @@ __global__ void __launch_bounds__(kThreads) search_fill(GridView g, Radii R, Nor
     const int64_t n_sorted = *g.n_sorted;
     // uniform over the block: every thread reaches the barriers
     for (int64_t chunk = blockIdx.x; chunk * kQPerBlock < n_sorted; chunk += gridDim.x) {
+        StencilCache sc;  // the warp's queries are consecutive in cell order
         for (int k = 0; k < kQPerWarp; ++k) {
             const int slot = warp * kQPerWarp + k;
             const int64_t p = chunk * kQPerBlock + slot;
@@ -131,8 +138,8 @@ __global__ void __launch_bounds__(kThreads) search_fill(GridView g, Radii R, Nor
             const float4 q = g.sorted[p];
             const int qi = __float_as_int(q.w);
             const float4 mq = s.mean[qi];
-            int start, excl;
-            const int total = stencil(g, q, lane, &start, &excl);
+            const int total = sc.get(g, q, lane);
+            const int start = sc.start, excl = sc.excl;
             int64_t out = o.offs[qi];
             float s1x = 0.f, s1y = 0.f, s1z = 0.f;
             float sxx = 0.f, sxy = 0.f, sxz = 0.f, syy = 0.f, syz = 0.f, szz = 0.f;
@@ -270,7 +277,7 @@ cudaError_t kmx_normals_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_params
     clear_counts<<<kmx_stride_blocks(n, 256, ctx->sm_count), 256, 0, st>>>(
         s.cnt, reinterpret_cast<float4*>(normal4), flags, g->d_n, n);
     KMX_COUNT_LAUNCH();
-    search_count<<<kmx_stride_blocks(n, kWarps, ctx->sm_count), kThreads, 0, st>>>(gv, R, s);
+    search_count<<<kmx_stride_blocks(n, kQPerBlock, ctx->sm_count), kThreads, 0, st>>>(gv, R, s);
     if ((e = kmx_scan_i32(ctx, s.cnt, n, g->d_n, offs))) return e;
     NormOut o{reinterpret_cast<float4*>(normal4), flags, offs, nbr, nbr_cap, n, needed, prm->tau_num,
               prm->tau_lin, {prm->viewpoint[0], prm->viewpoint[1], prm->viewpoint[2]}};

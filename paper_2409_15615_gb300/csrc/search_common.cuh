@@ -8,6 +8,8 @@
 #include "kmx_internal.cuh"
 #include "grid_common.cuh"
 
+#include <climits>
+
 namespace kmxs {
 
 constexpr unsigned kFull = 0xffffffffu;
@@ -39,14 +41,20 @@ __device__ __forceinline__ bool within(float4 a, float4 q, float d2, float r2, d
     return e < r2d;
 }
 
-// Lane l < 27 gets (start, count) of stencil cell l; returns the candidate
-// total and leaves each lane's exclusive prefix in *excl.
-__device__ __forceinline__ int stencil(const GridView& g, float4 q, int lane, int* start, int* excl)
+// The grid cell of a bucketed point (its coordinates passed the range check
+// when the grid was built).
+__device__ __forceinline__ void cell_of(const GridView& g, float4 q, int* cx, int* cy, int* cz)
 {
-    int cx, cy, cz;
-    kmx_cell_index(q.x, g.inv_cell, &cx);
-    kmx_cell_index(q.y, g.inv_cell, &cy);
-    kmx_cell_index(q.z, g.inv_cell, &cz);
+    kmx_cell_index(q.x, g.inv_cell, cx);
+    kmx_cell_index(q.y, g.inv_cell, cy);
+    kmx_cell_index(q.z, g.inv_cell, cz);
+}
+
+// Lane l < 27 gets (start, count) of cell l of the stencil around cell
+// (cx, cy, cz); returns the candidate total and leaves each lane's exclusive
+// prefix in *excl.  Every query of one cell has the same stencil.
+__device__ __forceinline__ int stencil_at(const GridView& g, int cx, int cy, int cz, int lane, int* start, int* excl)
+{
     int st = 0, ct = 0;
     if (lane < 27) {
         int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
@@ -67,6 +75,32 @@ __device__ __forceinline__ int stencil(const GridView& g, float4 q, int lane, in
     *excl = incl - ct;
     return __shfl_sync(kFull, incl, 31);
 }
+
+__device__ __forceinline__ int stencil(const GridView& g, float4 q, int lane, int* start, int* excl)
+{
+    int cx, cy, cz;
+    cell_of(g, q, &cx, &cy, &cz);
+    return stencil_at(g, cx, cy, cz, lane, start, excl);
+}
+
+// The stencil of the last query a warp searched, reused while the next
+// queries (consecutive in cell order) sit in the same cell.
+struct StencilCache {
+    int cx = INT_MIN, cy = 0, cz = 0, start = 0, excl = 0, total = 0;
+
+    __device__ __forceinline__ int get(const GridView& g, float4 q, int lane)
+    {
+        int x, y, z;
+        cell_of(g, q, &x, &y, &z);
+        if (x != cx || y != cy || z != cz) {
+            total = stencil_at(g, x, y, z, lane, &start, &excl);
+            cx = x;
+            cy = y;
+            cz = z;
+        }
+        return total;
+    }
+};
 
 // Candidate number t -> position in the sorted point array.
 __device__ __forceinline__ int candidate(int t, int start, int excl)
