@@ -105,3 +105,37 @@ def test_match_non_finite_descriptor_is_reported(env):
     corr, n = ctx.match(dp, None, 300, dp, None, 300, mode=kmx.MATCH_FP32_EXACT)
     ctx.sync()
     assert int(n.item()) == 300
+
+
+def test_context_after_a_device_error_gives_a_fresh_contexts_results(env):
+    """After a recorded device error kmx_sync re-zeroes the context's scan
+    status area; a whole pair (voxelise, grid, normals, Faster-PFH, match,
+    every stage with its scans) then gives exactly what a fresh context
+    gives."""
+    torch, kmx, ctx = env
+    from paper_2409_15615_gb300 import pipeline
+    from synth import scene_pair
+
+    src, tgt, _, _, vps, vpt = scene_pair(77, n=6000, clutter=True)
+    prm_s = kmx.params_default(0.1, viewpoint=np.float32(vps).tolist())
+    prm_t = kmx.params_default(0.1, viewpoint=np.float32(vpt).tolist())
+
+    def run(c):
+        st = pipeline.PairState(c, len(src), len(tgt), overlap=False)
+        st.src.raw.copy_(torch.from_numpy(np.ascontiguousarray(src)).cuda())
+        st.tgt.raw.copy_(torch.from_numpy(np.ascontiguousarray(tgt)).cuda())
+        st.run_checked(len(src), len(tgt), prm_s, prm_t, kmx.MATCH_FP32_EXACT)
+        i, j, _, _ = st.correspondences()
+        st.close()
+        return i, j
+
+    fresh = kmx.Context(0)
+    ref = run(fresh)
+    fresh.close()
+    ctx.check_timeout(20000)
+    with pytest.raises(kmx.KmxError) as e:
+        ctx.sync()
+    assert e.value.status == kmx.KMX_ETIMEOUT
+    got = run(ctx)
+    assert len(ref[0]) > 100
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])

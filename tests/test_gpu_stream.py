@@ -19,7 +19,7 @@ def _pairs(k, n=8000):
 
 
 @pytest.mark.parametrize("graph,concurrent,slots", [(True, False, 2), (False, False, 2), (True, True, 2),
-                                                   (True, True, 3), (False, True, 4)])
+                                                   (True, True, 3), (False, True, 4), (True, True, 1)])
 def test_stream_equals_plain_runs(graph, concurrent, slots):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
