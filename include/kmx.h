@@ -122,7 +122,13 @@ kmx_status kmx_params_default(float v, kmx_params* out);
 
 /* Create a context on CUDA device `device` issuing work on `cuda_stream`
  * (a cudaStream_t; NULL = the legacy default stream).  *out is owned by the
- * caller and released with kmx_destroy. */
+ * caller and released with kmx_destroy.
+ * A context owns a scratch area and a small zeroed area for the look-back
+ * words of its prefix scans; a call grows either one (stream-ordered) when
+ * it needs more.  To capture a call sequence into a CUDA graph, run it once
+ * with the same sizes first, so that the captured calls allocate nothing.
+ * Calls on one context must be ordered (one stream, or events between
+ * streams): they share these areas. */
 kmx_status kmx_create(kmx_ctx** out, int device, void* cuda_stream);
 
 /* Release the context and its scratch memory (synchronises its stream). */
