@@ -27,8 +27,10 @@
 //                  its rows).
 //   match_tiles_fp32_bulk
 //                  the (row tile x column tile) grid, flattened row-major, is
-//                  split into equal contiguous ranges, one per CTA, with as
-//                  many CTAs as fit on the GPU at once.  The source tile stays
+//                  cut into chunks of consecutive tile pairs (about 8 per
+//                  resident CTA, smaller ones for the end of the sequence)
+//                  that the CTAs, 1 or 2 per SM (the context's residency),
+//                  take from a counter.  The source tile stays
 //                  in shared memory; target tiles stream through a 3-stage
 //                  ring filled by cp.async.bulk (mbarrier completion).  For a
 //                  tile pair only the dimensions set in either tile's mask are
@@ -36,7 +38,7 @@
 //                  block of distances.  Per row: (best, its column, second
 //                  best), ties to the lower original column; per column: the
 //                  best (distance, original row) packed into 64 bits and folded
-//                  with atomicMin.  When a CTA leaves a row tile (or its range
+//                  with atomicMin.  When a CTA leaves a row tile (or its chunk
 //                  ends) it writes the rows' summaries as one "segment".
 //   merge_segments per source row, the segments of its row tile, then the
 //                  reciprocity test; results land at the original row.
