@@ -426,23 +426,29 @@ kmx_status kmx_gnc(kmx_ctx* ctx, const kmx_corr* d_corr, const int32_t* d_sel, c
  * driver's allocator, a host framework that forbids allocation calls from
  * plug-in code) get the result of kmx_match(..., KMX_MATCH_FP32_EXACT, ...)
  * without a context and without cudaMalloc, cudaFree or any allocating
- * library routine.
+ * library routine.  It runs the dense exact tile kernel (every descriptor
+ * dimension visited; the same distances, ties and emission as kmx_match),
+ * not kmx_match's zero-skipping one, and it does not check the descriptors
+ * for NaN or infinite values (kmx_match reports those as KMX_ERANGE; here the
+ * result is then unspecified).
  *   Arguments are those of kmx_match (same layouts and meaning) plus the
  *   cudaStream_t to run on; work goes to the device current at the call.
  *   Scratch is a fixed device array of about 6 MB inside the library,
  *   reserved on every device that loads the library until the process exits.
  *   np_cap and nq_cap may not exceed KMX_NOALLOC_MAX_ROWS: larger requests
  *   return KMX_EINVAL and launch nothing.
- *   The first call on a device looks the array's address up (once per
- *   device, with that device current); make that first call before any
- *   stream capture.
+ *   The first call on a device (and the first after the device's CUDA context
+ *   changed) looks the array's address up with that device current; make
+ *   that first call before any stream capture.
  *   All calls share the one array: calls whose work overlaps on the GPU (on
  *   different streams, or from several threads) race and corrupt each
  *   other's results; serialise them.
- *   Device-side overflow of `cap` is visible as *d_n_out > cap (the first cap
- *   pairs are written); no other device error can occur on this path.
+ *   Device-side results: *d_n_out = |A| (the first cap pairs are written, so
+ *   *d_n_out > cap signals overflow of `cap`), or *d_n_out = -1 when a
+ *   bounded wait of the prefix scan gave up (KMX_ETIMEOUT of the other entry
+ *   points; d_out is then unspecified).
  * Returns KMX_OK, KMX_EINVAL (bad argument or size beyond the maximum) or
- * KMX_ECUDA (the symbol lookup or a launch failed).
+ * KMX_ECUDA (the context or symbol lookup, or a launch, failed).
  */
 #define KMX_NOALLOC_MAX_ROWS 32768
 kmx_status kmx_match_noalloc(const float* d_desc_p, const int32_t* d_valid_p, int64_t np_cap, const int64_t* d_np,

@@ -121,9 +121,12 @@ kmx_status kmx_create(kmx_ctx** out, int device, void* cuda_stream)
     c->device = device;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    // the error word is cleared on the context's stream, and waited for, so
+    // that no kernel of the context can run before it is zero
     if (cudaMalloc(&c->d_err, sizeof(unsigned int)) != cudaSuccess ||
         cudaMallocHost(&c->h_err, sizeof(unsigned int)) != cudaSuccess ||
-        cudaMemset(c->d_err, 0, sizeof(unsigned int)) != cudaSuccess) {
+        cudaMemsetAsync(c->d_err, 0, sizeof(unsigned int), c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
         if (c->d_err) cudaFree(c->d_err);
         if (c->h_err) cudaFreeHost(c->h_err);
         delete c;
@@ -178,9 +181,15 @@ kmx_status kmx_sync(kmx_ctx* c)
     if (e != cudaSuccess) return cuda_fail(c, e, "kmx_sync");
     const unsigned int bits = *c->h_err;
     if (!bits) return KMX_OK;
-    cudaMemset(c->d_err, 0, sizeof(unsigned int));
-    // a scan that gave up may have left its status words set: start clean
-    if (c->scan_status) cudaMemset(c->scan_status, 0, sizeof(unsigned long long) * (size_t)c->scan_words);
+    // clear on the context's own stream (a non-blocking stream is not ordered
+    // against the legacy default stream) and wait, so that the next call's
+    // kernels start from zeros; a scan that gave up may have left its status
+    // words set
+    e = cudaMemsetAsync(c->d_err, 0, sizeof(unsigned int), c->stream);
+    if (e == cudaSuccess && c->scan_status)
+        e = cudaMemsetAsync(c->scan_status, 0, sizeof(unsigned long long) * (size_t)c->scan_words, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "kmx_sync");
     if (bits & KMX_DERR_RANGE) return fail(c, KMX_ERANGE, "a voxel or cell index does not fit in 21 bits");
     if (bits & KMX_DERR_CAPACITY) return fail(c, KMX_ECAPACITY, "an output buffer is too small");
     if (bits & KMX_DERR_HASHFULL) return fail(c, KMX_ENOMEM, "hash table full");

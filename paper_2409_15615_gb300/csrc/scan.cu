@@ -130,6 +130,9 @@ __global__ void __launch_bounds__(kThreads) scan_onepass(const T* __restrict__ i
             // consumed by the warp before lane 0 got here)
             __threadfence();
             last = atomicAdd(status + 1, 1ull) == (unsigned long long)(tiles - 1);
+            // acquire side: the zero stores below come after every other
+            // CTA's status stores, which preceded their own fenced increments
+            __threadfence();
         }
     }
     __syncthreads();

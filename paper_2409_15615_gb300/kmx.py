@@ -25,6 +25,7 @@ MATCH_FP32_EXACT = 0
 MATCH_BF16_RERANK = 1
 DESC_DIM = 33
 DESC_STRIDE = 36
+KMX_NOALLOC_MAX_ROWS = 32768  # kmx.h: the row limit of kmx_match_noalloc
 
 _STATUS_NAMES = {0: "KMX_OK", 1: "KMX_EINVAL", 2: "KMX_ENOMEM", 3: "KMX_ECUDA", 4: "KMX_ERANGE",
                  5: "KMX_ECAPACITY", 6: "KMX_ETIMEOUT", 7: "KMX_EBUSY"}
