@@ -104,12 +104,14 @@ typedef struct {
 
 typedef enum {
     KMX_MATCH_FP32_EXACT = 0, /* exact FP32 distances on CUDA cores */
-    /* split-BF16 (hi + lo) tensor-core distances on centred descriptors give
-     * top-8 candidates per row; a row whose candidates provably contain its
-     * exact nearest and second-nearest columns (a(8) - a(2) > 2E, E the bound
-     * on the approximate key's error) is re-ranked exactly in FP32, every
-     * other row goes through the exact FP32 tiles.  The result equals
-     * KMX_MATCH_FP32_EXACT's. */
+    /* BF16 tensor-core distances (FP32 accumulation) on descriptors sorted
+     * into similar 128-row tiles and centred per tile pair give, per row, a
+     * candidate list that provably holds every column whose exact distance is
+     * at most the row's second-smallest one (certified lower and upper
+     * bounds); the candidates are re-ranked exactly in FP32, and a row whose
+     * list overflows (256) goes through the exact FP32 tiles.  The result
+     * equals KMX_MATCH_FP32_EXACT's, including KMX_ERANGE for NaN or
+     * infinite values. */
     KMX_MATCH_BF16_RERANK = 1
 } kmx_match_mode;
 
@@ -367,6 +369,17 @@ kmx_status kmx_fpfh_classic(kmx_ctx* ctx, const kmx_grid* grid, const kmx_params
 kmx_status kmx_match(kmx_ctx* ctx, const float* d_desc_p, const int32_t* d_valid_p, int64_t np_cap,
                      const int64_t* d_np, const float* d_desc_q, const int32_t* d_valid_q, int64_t nq_cap,
                      const int64_t* d_nq, int32_t mode, kmx_corr* d_out, int64_t cap, int64_t* d_n_out);
+
+/* Diagnostics of the last kmx_match(..., KMX_MATCH_BF16_RERANK, ...) on this
+ * context (not from the paper): four device int64 values in d_out: the rows
+ * of the source and of the target cloud whose candidate list overflowed and
+ * went through the exact FP32 tiles, and the candidates collected for the
+ * source rows and for the target rows in total.  np_cap, d_np, nq_cap, d_nq
+ * are those of that call, and no other call may have used the context's
+ * scratch since.  KMX_EINVAL if the context's scratch cannot hold a match of
+ * these capacities. */
+kmx_status kmx_match_diag(kmx_ctx* ctx, int64_t np_cap, const int64_t* d_np, int64_t nq_cap, const int64_t* d_nq,
+                          int64_t* d_out);
 
 /*
  * Correspondence pruning of Sec. III-D, the step after matching: the ratio

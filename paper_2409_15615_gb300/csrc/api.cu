@@ -482,6 +482,20 @@ kmx_status kmx_match(kmx_ctx* c, const float* d_desc_p, const int32_t* d_valid_p
                     "kmx_match");
 }
 
+kmx_status kmx_match_diag(kmx_ctx* c, int64_t np_cap, const int64_t* d_np, int64_t nq_cap, const int64_t* d_nq,
+                          int64_t* d_out)
+{
+    if (!c) return KMX_EINVAL;
+    if (np_cap <= 0 || nq_cap <= 0 || np_cap > INT32_MAX - 1 || nq_cap > INT32_MAX - 1 || !d_out)
+        return fail(c, KMX_EINVAL, "kmx_match_diag: bad argument");
+    const size_t extra = kmx_match_tc_extra_bytes(np_cap, nq_cap, c->sm_count);
+    if (kmx::match_common_bytes(np_cap, nq_cap, 1, extra) > c->ws_size)
+        return fail(c, KMX_EINVAL, "kmx_match_diag: no tensor-core match of these capacities on this context");
+    DeviceGuard dg(c->device);
+    kmx::MatchScratch s = kmx::match_common_carve(c->ws, np_cap, nq_cap, 1, extra);
+    return launched(c, kmx_match_tc_stats(c, s.extra, np_cap, d_np, nq_cap, d_nq, d_out), "kmx_match_diag");
+}
+
 }  // extern "C"
 
 // Matching dispatch (scratch is taken from the context here because the size

@@ -85,6 +85,9 @@ cudaError_t match_emit(kmx_ctx* ctx, const MatchScratch& s, int64_t np_cap, cons
 size_t kmx_match_tc_extra_bytes(int64_t np_cap, int64_t nq_cap, int sm_count);
 cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, const int64_t* d_np, const float* dq,
                                 int64_t nq_cap, const int64_t* d_nq, kmx::MatchScratch& s);
+// diagnostics of the last tensor-core match on the scratch `extra` (see kmx_match_diag)
+cudaError_t kmx_match_tc_stats(kmx_ctx* ctx, void* extra, int64_t np_cap, const int64_t* d_np, int64_t nq_cap,
+                               const int64_t* d_nq, int64_t* dst);
 
 // match_fp32_bulk.cu: the exact FP32 path of kmx_match (packs both sides,
 // matches, merges and emits A)

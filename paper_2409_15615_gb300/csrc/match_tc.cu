@@ -1,33 +1,75 @@
 // Mutual nearest-neighbour matching (Sec. III-C) with BF16 tensor-core
-// distances and exact FP32 re-ranking.
+// distances and exact FP32 re-ranking.  The result equals the exact FP32
+// path's (kmx_match, KMX_MATCH_FP32_EXACT) bit for bit.
 //
-//   pack      FP32 descriptor rows -> two BF16 K-major tiles of 128 rows x 48
-//             (33 values, zero padded): x = hi + lo, hi = bf16(x),
-//             lo = bf16(x - hi).  Both are laid out exactly as the UMMA
-//             shared-memory operand (8x16-byte core matrices, no swizzle), so
-//             one tile is one contiguous 24 KB bulk copy; plus ||y||^2.  A
-//             single BF16 product (2^-9 relative) cannot rank near-duplicate
-//             descriptors (plane points), hi.hi + lo.hi + hi.lo (2^-16) can.
-//   tc_topk   one CTA per (128-row tile, chunk of 128-column tiles): the row
-//             tile stays in shared memory, column tiles stream through a
-//             3-stage ring filled by cp.async.bulk (TMA engine, mbarrier
-//             completion); a single thread issues tcgen05.mma (kind::f16,
-//             M=128 N=128 K=16; three K steps x three products) into one of
-//             two TMEM accumulators while the 4 warps read the other one with
-//             tcgen05.ld and keep, per row, the 8 smallest ranking keys
-//             ||y||^2 - 2 x.y (the row's ||x||^2 does not change the order).
-//   rerank    one warp per row: exact FP32 sum_h (x_h - y_h)^2 over the
-//             candidates of every chunk, lowest index on ties; rows of the
-//             source side give (d1, NN, d2), rows of the target side give the
-//             packed (distance, row) best that the reciprocity test reads.
-// The column direction is the same kernel with the roles of the two clouds
-// swapped.  Every wait on an mbarrier is bounded; on timeout the kernel
-// records KMX_DERR_TIMEOUT, drains what it issued and frees its TMEM.
+// Why the operands are centred per tile.  A distance taken as
+// |x|^2 + |y|^2 - 2 x.y loses the bits that d^2 needs when |x| |y| >> d^2;
+// the descriptors of plane points are near-duplicates (d^2 ~ 0.3 against
+// |x - mean|^2 ~ 10^3), so one global centre is not enough.  Rows that are
+// close in descriptor space are therefore put next to each other (a Morton
+// key over four statistics of the histograms, radix-sorted), every 128-row
+// tile gets its own centre c, and each tile pair is computed as
+//     d^2(x, y) = |x - c_C|^2 + |y - c_C|^2 - 2 (x - c_C).(y - c_C)
+// with c_C the centre of the column tile: both factors of the product are
+// small exactly for the pairs whose ranking matters.
+//
+// Stages (both clouds in one launch each where possible):
+//   coords/keys/sort  per row four statistics (mean bin of each third of the
+//             histogram, log2 of the first third's mass), normalised by their
+//             range over both clouds, 7 bits each -> a 28-bit Morton key;
+//             one stable radix sort over both clouds (a side bit on top).
+//   pack      one CTA per 128-row tile: the tile centre, then per row
+//             b = y - c in BF16 in the UMMA operand layout (K-major, 8x16-byte
+//             core matrices, no swizzle) with three extra K slots
+//             [sqrt(c') |b|, hi(|b|^2), lo(|b|^2)], and a header with |b|, the
+//             centre and max |b|^2.  A packed tile is one contiguous bulk copy.
+//   nearest   for each row tile, the column tile whose centre is nearest.
+//   collect   one CTA per (128-row tile, chunk of column tiles): per column
+//             tile the CTA writes its row tile re-centred on the column
+//             tile's centre as the A operand [x - c_C, sqrt(c') |x - c_C|,
+//             -1/2, -1/2] while the previous tile pair's MMA runs, one thread
+//             issues tcgen05.mma (kind::f16, BF16, M = N = 128, three K steps
+//             of 16) into one of two TMEM accumulators, and the 4 warps read
+//             the other accumulator with tcgen05.ld.  The accumulator holds
+//             M = a.b + c' |a| |b| - |b|^2 / 2 (approximately), so
+//             L = |a|^2 - 2 M - e is a certified lower bound of the exact
+//             d^2, and L + 4.1 c' |a| |b| + 2 e an upper bound.  Per row the
+//             thread keeps the two smallest upper bounds U1 <= U2 it has seen
+//             and collects every column with L <= U2 (its column index goes
+//             to the row's candidate list).  Every column whose exact
+//             distance is at most the row's second-smallest exact distance
+//             is collected (L <= d <= d(2) <= U2).  A 32-column slice whose
+//             largest M cannot give L <= U2 costs one three-input max per two
+//             values.  The CTA starts with the nearest column tile, so U2 is
+//             tight from the first tile on (outside its chunk that tile only
+//             tightens the bounds).
+//   rerank    one warp per row: the exact FP32 distance of every collected
+//             column (sum_h (x_h - y_h)^2, one fused multiply-add per term in
+//             h order: the arithmetic of the exact path), lowest index on
+//             ties.  Rows of the source side give (d1, NN, d2); rows of the
+//             target side give the packed (distance, row) best that the
+//             reciprocity test reads.  A row whose list overflowed goes
+//             through the exact FP32 tiles instead.
+// Every wait on an mbarrier is bounded; on timeout the kernel records
+// KMX_DERR_TIMEOUT, drains what it issued and frees its TMEM.
+//
+// The certified bounds.  With a, b the FP32 centred rows and their BF16
+// roundings a', b' (8 significant bits: relative error <= 2^-8 each),
+// |a'.b' - a.b| <= 2^-7 (1 + 2^-9) |a| |b|.  The tensor core's FP32
+// accumulation of the 48 products is taken to lose at most 48 * 2^-22 of
+// the sum of their magnitudes (a reading: the ISA promises FP32
+// accumulation without stating its rounding).  The slot product
+// bf16(sqrt(c')|a|) bf16(sqrt(c')|b|) >= (1 - 2^-8)^2 c' |a| |b| with
+// c' = 0.008 exceeds both terms together; FP32 rounding of |a|^2, |b|^2,
+// the hi/lo split of |b|^2 (2^-16), the accumulation error on the |b|^2
+// slots and the rounding of the final exact distance are covered by
+// e = 6e-5 (|a|^2 + max |b|^2 of the tile).
 #include "kmx_internal.cuh"
 #include "bulk_copy.cuh"
 #include "match_common.cuh"
 
 #include <cuda_bf16.h>
+#include <float.h>
 
 namespace {
 
@@ -38,24 +80,30 @@ using kmx::mbar_init;
 using kmx::mbar_wait;
 using kmx::smem_u32;
 
-constexpr int kTM = 128;                       // rows per tile (UMMA M)
-constexpr int kTN = 128;                       // columns per tile (UMMA N)
-constexpr int kK = 48;                         // 33 descriptor values padded to 3 x 16
-constexpr int kHalfBytes = kTM * kK * 2;       // one BF16 operand tile: 12288
-constexpr int kOperandBytes = 2 * kHalfBytes;  // high part, then low part
-constexpr int kTileBytes = kOperandBytes + kTM * 4;  // operands + 128 squared norms
-constexpr int kCoreStride = 128;               // LBO: next 8-element K chunk
-constexpr int kGroupStride = 6 * 128;          // SBO: next 8-row group
-constexpr int kStages = 3;                     // column-tile ring
-constexpr int kTopK = 8;
-constexpr int kMaxChunks = 4;                  // 4 x 8 candidates = one warp in rerank
+constexpr int kTM = 128;                      // rows per tile (UMMA M)
+constexpr int kTN = 128;                      // columns per tile (UMMA N)
+constexpr int kK = 48;                        // 33 values + 3 slots, padded to 3 x 16
+constexpr int kOpBytes = kTM * kK * 2;        // one BF16 operand tile: 12288
+constexpr int kCoreStride = 128;              // LBO: next 8-element K chunk
+constexpr int kGroupStride = 6 * 128;         // SBO: next 8-row group
+constexpr int kCenterStride = 36;             // floats per stored centre
+// packed column tile: operand, then |b| per row, the centre, max |b|^2
+constexpr int kHdrBeta = kOpBytes;
+constexpr int kHdrCenter = kHdrBeta + kTN * 4;
+constexpr int kHdrBmax = kHdrCenter + kCenterStride * 4;
+constexpr int kColBytes = kHdrBmax + 16;      // 12960, a multiple of 16
+constexpr int kStages = 3;                    // column-tile ring
 constexpr int kThreads = 128;
-constexpr int kTmemCols = 256;                 // two 128-column FP32 accumulators
+constexpr int kTmemCols = 256;                // two 128-column FP32 accumulators
+constexpr int kMaxChunks = 8;
+constexpr int kCandCap = 256;                 // candidate list per row
+constexpr float kC = 0.008f;                  // c' of the bounds
+constexpr float kSqrtC = 0.08944271909999159f;
+constexpr float kUpper = 4.1f * kC;
+constexpr float kEfp = 6e-5f;
+constexpr int kMortonBits = 7;                // per statistic; 4 x 7 = 28 bits
 
-struct __align__(8) Cand {
-    float v;
-    int idx;
-};
+static_assert(kColBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
 
 // ---------------------------------------------------------------------------
 // PTX wrappers (tcgen05; mbarrier and bulk copy in bulk_copy.cuh)
@@ -63,6 +111,8 @@ struct __align__(8) Cand {
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// generic-proxy shared-memory stores -> visible to the tensor core's reads
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols)
 {
@@ -123,131 +173,307 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// ---------------------------------------------------------------------------
-// pack
-// ---------------------------------------------------------------------------
-
-// One thread per row of the padded matrix.  Rows are centred on the common
-// mean of both clouds first (distances do not change; products get smaller).
-// The largest squared norm of the side is folded into *maxnorm (float bits of
-// a non-negative value order like the value).
-__global__ void __launch_bounds__(256) pack_bf16(const float* __restrict__ desc, int64_t n_cap, const int64_t* d_n,
-                                                 int64_t rows_pad, const float* __restrict__ mean,
-                                                 uint8_t* __restrict__ out, unsigned int* __restrict__ maxnorm)
+__device__ __forceinline__ float fmax3(float a, float b, float c)
 {
-    const int64_t r = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    if (r >= rows_pad) return;
-    const int64_t n = kmx_count(d_n, n_cap);
-    float x[kK];
-#pragma unroll
-    for (int h = 0; h < kK; ++h) x[h] = 0.f;
-    if (r < n) {
-        const float4* row = reinterpret_cast<const float4*>(desc + r * KMX_DESC_STRIDE);
-#pragma unroll
-        for (int c = 0; c < KMX_DESC_STRIDE / 4; ++c) {
-            const float4 v = __ldg(row + c);
-            x[4 * c + 0] = v.x;
-            x[4 * c + 1] = v.y;
-            x[4 * c + 2] = v.z;
-            x[4 * c + 3] = v.w;
-        }
-#pragma unroll
-        for (int h = 0; h < KMX_DESC_DIM; ++h) x[h] -= __ldg(mean + h);
-    }
-    uint8_t* tile = out + (r / kTM) * (int64_t)kTileBytes;
-    const int rin = (int)(r % kTM);
-    float nrm = 0.f;
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+}
+
+// Write one 48-value operand row (values v[0..47]) at row r of a tile in the
+// core-matrix layout.
+__device__ __forceinline__ void store_operand_row(uint8_t* tile, int r, const float (&v)[kK])
+{
+    const int base = (r / 8) * kGroupStride + (r % 8) * 16;
 #pragma unroll
     for (int c = 0; c < kK / 8; ++c) {
-        uint32_t hi[4], lo[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            uint32_t wh = 0, wl = 0;
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int h = 8 * c + 2 * e + u;
-                const float f = h < KMX_DESC_DIM ? x[h] : 0.f;
-                // x = hi + lo with both in BF16: the three products
-                // hi.hi + lo.hi + hi.lo recover x.y to ~2^-16 relative
-                const __nv_bfloat16 bh = __float2bfloat16_rn(f);
-                const __nv_bfloat16 bl = __float2bfloat16_rn(f - __bfloat162float(bh));
-                nrm = fmaf(f, f, nrm);
-                wh |= (uint32_t)__bfloat16_as_ushort(bh) << (16 * u);
-                wl |= (uint32_t)__bfloat16_as_ushort(bl) << (16 * u);
-            }
-            hi[e] = wh;
-            lo[e] = wl;
-        }
-        const int off = (rin / 8) * kGroupStride + c * kCoreStride + (rin % 8) * 16;
-        *reinterpret_cast<uint4*>(tile + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<uint4*>(tile + kHalfBytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        uint4 w;
+        w.x = pack_bf16x2(v[8 * c + 0], v[8 * c + 1]);
+        w.y = pack_bf16x2(v[8 * c + 2], v[8 * c + 3]);
+        w.z = pack_bf16x2(v[8 * c + 4], v[8 * c + 5]);
+        w.w = pack_bf16x2(v[8 * c + 6], v[8 * c + 7]);
+        *reinterpret_cast<uint4*>(tile + base + c * kCoreStride) = w;
     }
-    reinterpret_cast<float*>(tile + kOperandBytes)[rin] = r < n ? nrm : INFINITY;
-    if (r < n) atomicMax(maxnorm, __float_as_uint(nrm));
 }
 
 // ---------------------------------------------------------------------------
-// tensor-core top-k
+// locality order
+// ---------------------------------------------------------------------------
+
+// The four statistics of a descriptor row: the mean bin of each third of the
+// histogram (0 for an empty third) and log2 of the first third's mass
+// (at least 0).  All are >= 0, so their float bits order like the values.
+__device__ __forceinline__ void row_stats(const float* __restrict__ row, float (&s)[4])
+{
+    float m0 = 0.f;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        float w = 0.f, m = 0.f;
+#pragma unroll
+        for (int b = 0; b < 11; ++b) {
+            const float h = __ldg(row + 11 * t + b);
+            w += h;
+            m = fmaf((float)b, h, m);
+        }
+        s[t] = w > 0.f ? fmaxf(m / w, 0.f) : 0.f;
+        if (t == 0) m0 = w;
+    }
+    s[3] = log2f(fmaxf(m0, 1.f));
+}
+
+// Per row of both clouds: the statistics, their range (atomic min / max of
+// the float bits) and a non-finite check.  Rows e < np_cap are the source
+// cloud, the others the target cloud.
+__global__ void __launch_bounds__(256) tc_coords(const float* __restrict__ P, int64_t np_cap,
+                                                 const int64_t* d_np, const float* __restrict__ Q, int64_t nq_cap,
+                                                 const int64_t* d_nq, float4* __restrict__ coords,
+                                                 unsigned int* __restrict__ range, unsigned int* err)
+{
+    const int64_t np = kmx_count(d_np, np_cap), nq = kmx_count(d_nq, nq_cap);
+    float lo[4] = {FLT_MAX, FLT_MAX, FLT_MAX, FLT_MAX}, hi[4] = {0.f, 0.f, 0.f, 0.f};
+    bool bad = false;
+    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < np_cap + nq_cap;
+         e += (int64_t)gridDim.x * 256) {
+        const bool side = e >= np_cap;
+        const int64_t r = side ? e - np_cap : e;
+        if (r >= (side ? nq : np)) continue;
+        const float* row = (side ? Q : P) + r * KMX_DESC_STRIDE;
+#pragma unroll
+        for (int h = 0; h < KMX_DESC_DIM; ++h) bad |= !isfinite(__ldg(row + h));
+        float s[4];
+        row_stats(row, s);
+        coords[e] = make_float4(s[0], s[1], s[2], s[3]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            lo[k] = fminf(lo[k], s[k]);
+            hi[k] = fmaxf(hi[k], s[k]);
+        }
+    }
+    if (bad) kmx_raise(err, KMX_DERR_RANGE);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const unsigned l = __reduce_min_sync(0xffffffffu, __float_as_uint(lo[k]));
+        const unsigned h = __reduce_max_sync(0xffffffffu, __float_as_uint(hi[k]));
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(range + k, l);
+            atomicMax(range + 4 + k, h);
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t spread4(uint32_t v)  // 7 bits -> every 4th bit
+{
+    uint32_t r = 0;
+#pragma unroll
+    for (int b = 0; b < kMortonBits; ++b) r |= ((v >> b) & 1u) << (4 * b);
+    return r;
+}
+
+// Sort keys: side bit 29, "past the count" bit 28, 28-bit Morton code.
+__global__ void __launch_bounds__(256) tc_keys(int64_t np_cap, const int64_t* d_np, int64_t nq_cap,
+                                               const int64_t* d_nq, const float4* __restrict__ coords,
+                                               const unsigned int* __restrict__ range, uint32_t* __restrict__ keys,
+                                               int32_t* __restrict__ vals)
+{
+    const int64_t np = kmx_count(d_np, np_cap), nq = kmx_count(d_nq, nq_cap);
+    const float scale = (float)((1 << kMortonBits) - 1);
+    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < np_cap + nq_cap;
+         e += (int64_t)gridDim.x * 256) {
+        const bool side = e >= np_cap;
+        const int64_t r = side ? e - np_cap : e;
+        uint32_t key = (uint32_t)side << 29;
+        if (r < (side ? nq : np)) {
+            const float4 c = coords[e];
+            const float cs[4] = {c.x, c.y, c.z, c.w};
+            uint32_t m = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float lo = __uint_as_float(range[k]), hi = __uint_as_float(range[4 + k]);
+                const float t = hi > lo ? (cs[k] - lo) / (hi - lo) : 0.f;
+                const uint32_t q = (uint32_t)fminf(fmaxf(t * scale + 0.5f, 0.f), scale);
+                m |= spread4(q) << (3 - k);
+            }
+            key |= m;
+        } else {
+            key |= 1u << 28;
+        }
+        keys[e] = key;
+        vals[e] = (int32_t)r;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// pack: one CTA of 128 threads per tile of one cloud
+// ---------------------------------------------------------------------------
+
+// Rows of the tile are sorted positions [128 t, 128 t + 128) of the cloud;
+// perm maps a sorted position to the descriptor row.  Writes the packed
+// column tile and the centre (also to centers[t]).
+__global__ void __launch_bounds__(kTM) tc_pack(const float* __restrict__ desc, const int32_t* __restrict__ perm,
+                                               int64_t n_cap, const int64_t* d_n, uint8_t* __restrict__ out,
+                                               float* __restrict__ centers)
+{
+    __shared__ float rows_s[kTM][KMX_DESC_DIM + 1];
+    __shared__ float cen[kCenterStride];
+    __shared__ unsigned int bmax2;
+    const int64_t n = kmx_count(d_n, n_cap);
+    const int64_t t = blockIdx.x;
+    if (t * kTM >= n && !(t == 0)) return;  // tiles past the count are never read
+    const int tid = threadIdx.x;
+    const int64_t r = t * kTM + tid;
+    const bool valid = r < n;
+    float y[KMX_DESC_DIM];
+    if (valid) {
+        const float* row = desc + (int64_t)perm[r] * KMX_DESC_STRIDE;
+#pragma unroll
+        for (int h = 0; h < KMX_DESC_DIM; ++h) y[h] = __ldg(row + h);
+    } else {
+#pragma unroll
+        for (int h = 0; h < KMX_DESC_DIM; ++h) y[h] = 0.f;
+    }
+#pragma unroll
+    for (int h = 0; h < KMX_DESC_DIM; ++h) rows_s[tid][h] = y[h];
+    if (tid == 0) bmax2 = 0u;
+    __syncthreads();
+    const int cnt = (int)max((int64_t)0, min((int64_t)kTM, n - t * kTM));
+    if (tid < kCenterStride) {
+        float s = 0.f;
+        if (tid < KMX_DESC_DIM)
+            for (int i = 0; i < cnt; ++i) s += rows_s[i][tid];
+        cen[tid] = (tid < KMX_DESC_DIM && cnt > 0) ? s / (float)cnt : 0.f;
+    }
+    __syncthreads();
+    float v[kK];
+    float nb = 0.f;
+#pragma unroll
+    for (int h = 0; h < KMX_DESC_DIM; ++h) {
+        const float b = y[h] - cen[h];
+        v[h] = b;
+        nb = fmaf(b, b, nb);
+    }
+    const float beta = sqrtf(nb);
+#pragma unroll
+    for (int h = KMX_DESC_DIM; h < kK; ++h) v[h] = 0.f;
+    if (valid) {
+        const float hi = __bfloat162float(__float2bfloat16_rn(nb));
+        v[KMX_DESC_DIM] = kSqrtC * beta;
+        v[KMX_DESC_DIM + 1] = hi;
+        v[KMX_DESC_DIM + 2] = nb - hi;
+    } else {
+#pragma unroll
+        for (int h = 0; h < KMX_DESC_DIM; ++h) v[h] = 0.f;
+        v[KMX_DESC_DIM + 1] = INFINITY;  // -1/2 x inf: the padding column never qualifies
+    }
+    uint8_t* tile = out + t * (int64_t)kColBytes;
+    store_operand_row(tile, tid, v);
+    reinterpret_cast<float*>(tile + kHdrBeta)[tid] = valid ? beta : 0.f;
+    if (valid) atomicMax(&bmax2, __float_as_uint(nb));
+    if (tid < kCenterStride) {
+        reinterpret_cast<float*>(tile + kHdrCenter)[tid] = cen[tid];
+        centers[t * kCenterStride + tid] = cen[tid];
+    }
+    __syncthreads();
+    if (tid < 4) reinterpret_cast<float*>(tile + kHdrBmax)[tid] = tid == 0 ? __uint_as_float(bmax2) : 0.f;
+}
+
+// For each row tile of X: the column tile of Y with the nearest centre (ties
+// to the lower tile).  One warp per row tile.
+__global__ void __launch_bounds__(256) tc_nearest(const float* __restrict__ cx, int64_t nx_cap, const int64_t* d_nx,
+                                                  const float* __restrict__ cy, int64_t ny_cap, const int64_t* d_ny,
+                                                  int32_t* __restrict__ nearest)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int64_t ntx = (kmx_count(d_nx, nx_cap) + kTM - 1) / kTM;
+    const int64_t nty = (kmx_count(d_ny, ny_cap) + kTN - 1) / kTN;
+    if (t >= ntx) return;
+    float c[KMX_DESC_DIM];
+#pragma unroll
+    for (int h = 0; h < KMX_DESC_DIM; ++h) c[h] = cx[t * kCenterStride + h];
+    float best = INFINITY;
+    int bi = 0x7fffffff;
+    for (int64_t u = lane; u < nty; u += 32) {
+        float d = 0.f;
+#pragma unroll
+        for (int h = 0; h < KMX_DESC_DIM; ++h) {
+            const float e = c[h] - cy[u * kCenterStride + h];
+            d = fmaf(e, e, d);
+        }
+        if (d < best) {
+            best = d;
+            bi = (int)u;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob < best || (ob == best && oi < bi)) {
+            best = ob;
+            bi = oi;
+        }
+    }
+    if (lane == 0) nearest[t] = bi == 0x7fffffff ? 0 : bi;
+}
+
+// ---------------------------------------------------------------------------
+// tensor-core candidate collection
 // ---------------------------------------------------------------------------
 
 struct TcShared {
-    uint8_t a[kOperandBytes];
-    uint8_t b[kStages][kOperandBytes];
-    float nrm[2][kTN];
-    uint64_t bar_a, bar_b[kStages], bar_mma[2];
+    uint8_t a[2][kOpBytes];
+    uint8_t b[kStages][kColBytes];
+    uint64_t bar_b[kStages], bar_mma[2];
     uint32_t tmem;
-    int failed;
 };
 
-__device__ __forceinline__ void topk_insert(float* tv, int* ti, float v, int j)
-{
-    tv[kTopK - 1] = v;
-    ti[kTopK - 1] = j;
-#pragma unroll
-    for (int p = kTopK - 1; p > 0; --p) {
-        if (tv[p] < tv[p - 1]) {
-            const float fv = tv[p];
-            tv[p] = tv[p - 1];
-            tv[p - 1] = fv;
-            const int fi = ti[p];
-            ti[p] = ti[p - 1];
-            ti[p - 1] = fi;
-        }
-    }
-}
-
 // The grid is sized from the capacities; the (row tile, column chunk) split
-// of the actual counts is decided here (kmx::work_chunks) and published in
-// *chunks_out for the re-ranking kernel.
-__global__ void __launch_bounds__(kThreads, 1) tc_topk(const uint8_t* __restrict__ packA, int64_t rows_cap,
-                                                      const int64_t* d_rows, const uint8_t* __restrict__ packB,
-                                                      int64_t cols_cap, const int64_t* d_cols, int target_ctas,
-                                                      Cand* __restrict__ part, int* __restrict__ chunks_out,
-                                                      unsigned int* err)
+// of the actual counts is decided here (kmx::work_chunks).
+__global__ void __launch_bounds__(kThreads, 1) tc_collect(const float* __restrict__ X,
+                                                         const int32_t* __restrict__ permX, int64_t nx_cap,
+                                                         const int64_t* d_nx, const uint8_t* __restrict__ packY,
+                                                         int64_t ny_cap, const int64_t* d_ny,
+                                                         const int32_t* __restrict__ nearest, int target_ctas,
+                                                         int32_t* __restrict__ cand, int32_t* __restrict__ cnt,
+                                                         unsigned int* err)
 {
     extern __shared__ uint8_t smem_raw[];
     TcShared& S = *reinterpret_cast<TcShared*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int64_t rows = kmx_count(d_rows, rows_cap), cols = kmx_count(d_cols, cols_cap);
+    const int64_t rows = kmx_count(d_nx, nx_cap), cols = kmx_count(d_ny, ny_cap);
     const int64_t n_rt = (rows + kTM - 1) / kTM;
     const int64_t n_ct = (cols + kTN - 1) / kTN;
     const int chunks = kmx::work_chunks(n_rt, n_ct, target_ctas, kMaxChunks);
-    if (blockIdx.x == 0 && tid == 0) *chunks_out = chunks;
     if ((int64_t)blockIdx.x >= n_rt * chunks) return;
     const int chunk = (int)(blockIdx.x % chunks);
-    const int64_t row0 = (int64_t)(blockIdx.x / chunks) * kTM;
+    const int64_t rt = blockIdx.x / chunks;
     const int64_t tiles_per_chunk = (n_ct + chunks - 1) / chunks;
     const int64_t t0 = chunk * tiles_per_chunk;
     const int T = (int)max((int64_t)0, min(n_ct, t0 + tiles_per_chunk) - t0);
+    if (T == 0) return;
+    // the sequence of column tiles: the nearest tile first, then the chunk
+    // (without the nearest tile when it lies inside the chunk)
+    const int64_t cs = nearest[rt];
+    const bool cs_in = cs >= t0 && cs < t0 + T;
+    const int nseq = T + (cs_in ? 0 : 1);
+    auto tile_of = [&](int s) -> int64_t {
+        if (s == 0) return cs;
+        const int64_t r = t0 + s - 1;
+        return (cs_in && r >= cs) ? r + 1 : r;
+    };
     const uint32_t idesc = idesc_bf16(kTM, kTN);
 
     if (tid == 0) {
-        mbar_init(&S.bar_a, 1);
         for (int s = 0; s < kStages; ++s) mbar_init(&S.bar_b[s], 1);
         mbar_init(&S.bar_mma[0], 1);
         mbar_init(&S.bar_mma[1], 1);
         mbar_fence_init();
-        S.failed = 0;
     }
     if (warp == 0) tmem_alloc(&S.tmem, kTmemCols);
     tc_fence_before();
@@ -255,116 +481,134 @@ __global__ void __launch_bounds__(kThreads, 1) tc_topk(const uint8_t* __restrict
     tc_fence_after();
     const uint32_t tmem = S.tmem;
 
-    float tv[kTopK];
-    int ti[kTopK];
+    const int64_t row = rt * kTM + tid;
+    const bool row_valid = row < rows;
+    float x[KMX_DESC_DIM];
+    if (row_valid) {
+        const float* xr = X + (int64_t)permX[row] * KMX_DESC_STRIDE;
 #pragma unroll
-    for (int k = 0; k < kTopK; ++k) {
-        tv[k] = INFINITY;
-        ti[k] = -1;
+        for (int h = 0; h < KMX_DESC_DIM; ++h) x[h] = __ldg(xr + h);
+    } else {
+#pragma unroll
+        for (int h = 0; h < KMX_DESC_DIM; ++h) x[h] = 0.f;
     }
-    int issued_b = 0;  // column tiles whose copy thread 0 has issued
-    if (tid == 0 && T > 0) {
-        mbar_expect_tx(&S.bar_a, kOperandBytes);
-        bulk_g2s(S.a, packA + (row0 / kTM) * (int64_t)kTileBytes, kOperandBytes, &S.bar_a);
-        for (; issued_b < T && issued_b < kStages; ++issued_b) {
-            mbar_expect_tx(&S.bar_b[issued_b], kOperandBytes);
-            bulk_g2s(S.b[issued_b], packB + (t0 + issued_b) * (int64_t)kTileBytes, kOperandBytes,
-                     &S.bar_b[issued_b]);
+
+    int issued_b = 0, issued_mma = 0;
+    if (tid == 0) {
+        for (; issued_b < nseq && issued_b < kStages; ++issued_b) {
+            mbar_expect_tx(&S.bar_b[issued_b], kColBytes);
+            bulk_g2s(S.b[issued_b], packY + tile_of(issued_b) * (int64_t)kColBytes, kColBytes, &S.bar_b[issued_b]);
         }
     }
-    const uint32_t a_base = smem_u32(S.a);
-    // thread 0: tile t into accumulator t & 1 -- per K step of 16, the three
-    // products hi.hi + lo.hi + hi.lo of the split operands
-    auto issue = [&](int t) {
-        const uint32_t b_base = smem_u32(S.b[t % kStages]);
-        const uint32_t d = tmem + (uint32_t)((t & 1) * kTN);
+    bool fail = false, failed = false;
+    float U1 = FLT_MAX, U2 = FLT_MAX;
+    float rb_cur = 0.f, al_cur = 0.f, ef_cur = 0.f;  // tile s: |a|^2 - e, |a|, e
+    float rb_prev = 0.f, al_prev = 0.f, ef_prev = 0.f;
+
+    for (int s = 0; s <= nseq; ++s) {
+        rb_prev = rb_cur;
+        al_prev = al_cur;
+        ef_prev = ef_cur;
+        if (s < nseq) {
+            // ---- A operand of tile pair s: the row re-centred on the column tile's centre
+            if (!mbar_wait(&S.bar_b[s % kStages], (s / kStages) & 1)) fail = true;
+            const uint8_t* bt = S.b[s % kStages];
+            const float* cen = reinterpret_cast<const float*>(bt + kHdrCenter);
+            const float bmax2 = reinterpret_cast<const float*>(bt + kHdrBmax)[0];
+            float v[kK];
+            float r2 = 0.f;
 #pragma unroll
-        for (int k = 0; k < kK / 16; ++k) {
-            const uint32_t ko = k * 2 * kCoreStride;
-            const uint64_t ah = smem_desc(a_base + ko, kCoreStride, kGroupStride);
-            const uint64_t al = smem_desc(a_base + kHalfBytes + ko, kCoreStride, kGroupStride);
-            const uint64_t bh = smem_desc(b_base + ko, kCoreStride, kGroupStride);
-            const uint64_t bl = smem_desc(b_base + kHalfBytes + ko, kCoreStride, kGroupStride);
-            umma_bf16(d, ah, bh, idesc, k > 0);
-            umma_bf16(d, al, bh, idesc, 1);
-            umma_bf16(d, ah, bl, idesc, 1);
-        }
-        umma_commit(&S.bar_mma[t & 1]);
-    };
-    if (tid == 0 && T > 0) {
-        bool ok = mbar_wait(&S.bar_a, 0) && mbar_wait(&S.bar_b[0], 0);
-        if (ok) {
+            for (int h = 0; h < KMX_DESC_DIM; ++h) {
+                const float a = x[h] - cen[h];
+                v[h] = a;
+                r2 = fmaf(a, a, r2);
+            }
+            const float al = sqrtf(r2);
+            v[KMX_DESC_DIM] = kSqrtC * al;
+            v[KMX_DESC_DIM + 1] = -0.5f;
+            v[KMX_DESC_DIM + 2] = -0.5f;
+#pragma unroll
+            for (int h = KMX_DESC_DIM + 3; h < kK; ++h) v[h] = 0.f;
+            store_operand_row(S.a[s & 1], tid, v);
+            ef_cur = kEfp * (r2 + bmax2);
+            rb_cur = r2 - ef_cur;
+            al_cur = al;
+            fence_proxy_async();
+            tc_fence_before();
+            failed = __syncthreads_or(fail) != 0;
             tc_fence_after();
-            issue(0);
-        } else {
-            S.failed = 1;
-        }
-    }
-    __syncthreads();
-    int issued_mma = (T > 0 && !S.failed) ? 1 : 0;
-    for (int t = 0; t < T && !S.failed; ++t) {
-        const int s = t & 1;
-        // column norms of tile t (plain loads; visible after the barrier below)
-        S.nrm[s][tid] = reinterpret_cast<const float*>(packB + (t0 + t) * (int64_t)kTileBytes + kOperandBytes)[tid];
-        if (tid == 0 && t + 1 < T) {
-            if (mbar_wait(&S.bar_b[(t + 1) % kStages], ((t + 1) / kStages) & 1)) {
-                tc_fence_after();
-                issue(t + 1);
+            if (failed) break;
+            if (tid == 0) {
+                const uint32_t a_base = smem_u32(S.a[s & 1]);
+                const uint32_t b_base = smem_u32(S.b[s % kStages]);
+                const uint32_t d = tmem + (uint32_t)((s & 1) * kTN);
+#pragma unroll
+                for (int k = 0; k < kK / 16; ++k) {
+                    const uint32_t ko = k * 2 * kCoreStride;
+                    umma_bf16(d, smem_desc(a_base + ko, kCoreStride, kGroupStride),
+                              smem_desc(b_base + ko, kCoreStride, kGroupStride), idesc, k > 0);
+                }
+                umma_commit(&S.bar_mma[s & 1]);
                 ++issued_mma;
-            } else {
-                S.failed = 1;
             }
         }
-        if (!mbar_wait(&S.bar_mma[s], (t >> 1) & 1)) S.failed = 1;
-        tc_fence_after();
-        if (tid == 0 && t + kStages < T) {  // MMA t is done with its stage
-            const int st = t % kStages;
-            mbar_expect_tx(&S.bar_b[st], kOperandBytes);
-            bulk_g2s(S.b[st], packB + (t0 + t + kStages) * (int64_t)kTileBytes, kOperandBytes, &S.bar_b[st]);
-            ++issued_b;
-        }
-        __syncthreads();
-        if (S.failed) break;
-        const int64_t col0 = (t0 + t) * kTN;
-        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * kTN);
-        // Fast path: 32 keys and their minimum without a branch; only when
-        // the minimum beats the current 8th key are the keys inserted one by
-        // one (rare once the list has filled).
+        if (s >= 1) {
+            // ---- epilogue of tile pair p = s - 1
+            const int p = s - 1;
+            if (!mbar_wait(&S.bar_mma[p & 1], (p >> 1) & 1)) fail = true;
+            tc_fence_after();
+            const bool collect = p > 0 || cs_in;
+            const int64_t col0 = tile_of(p) * kTN;
+            const float* beta = reinterpret_cast<const float*>(S.b[p % kStages] + kHdrBeta);
+            const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((p & 1) * kTN);
 #pragma unroll 1
-        for (int c0 = 0; c0 < kTN; c0 += 32) {
-            float v[32];
-            tmem_ld32(lane_addr + c0, v);
+            for (int c0 = 0; c0 < kTN; c0 += 32) {
+                float v[32];
+                tmem_ld32(lane_addr + c0, v);
+                float m[11];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = fmaf(-2.0f, v[j], S.nrm[s][c0 + j]);
-            float m[16];
+                for (int j = 0; j < 10; ++j) m[j] = fmax3(v[3 * j], v[3 * j + 1], v[3 * j + 2]);
+                m[10] = fmaxf(v[30], v[31]);
+                const float mx = fmax3(fmax3(fmax3(m[0], m[1], m[2]), fmax3(m[3], m[4], m[5]), fmax3(m[6], m[7], m[8])),
+                                       m[9], m[10]);
+                if (row_valid && fmaf(-2.f, mx, rb_prev) <= U2) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) m[j] = fminf(v[j], v[j + 16]);
-#pragma unroll
-            for (int w = 8; w >= 1; w >>= 1)
-#pragma unroll
-                for (int j = 0; j < w; ++j) m[j] = fminf(m[j], m[j + w]);
-            if (m[0] < tv[kTopK - 1]) {
-#pragma unroll 1
-                for (int j = 0; j < 32; ++j) {
-                    float vj = v[0];
-#pragma unroll
-                    for (int k = 1; k < 32; ++k) vj = (j == k) ? v[k] : vj;  // register select, no local memory
-                    if (vj < tv[kTopK - 1]) topk_insert(tv, ti, vj, (int)(col0 + c0 + j));
+                    for (int j = 0; j < 32; ++j) {
+                        const float L = fmaf(-2.f, v[j], rb_prev);
+                        if (L <= U2) {
+                            if (collect) {
+                                const int pos = atomicAdd(cnt + row, 1);
+                                if (pos < kCandCap) cand[row * kCandCap + pos] = (int32_t)(col0 + c0 + j);
+                            }
+                            const float U = fmaf(kUpper * al_prev, beta[c0 + j], L + 2.f * ef_prev);
+                            if (U < U1) {
+                                U2 = U1;
+                                U1 = U;
+                            } else if (U < U2) {
+                                U2 = U;
+                            }
+                        }
+                    }
                 }
             }
+            tc_fence_before();
+            failed = __syncthreads_or(fail) != 0;
+            tc_fence_after();
+            if (failed) break;
+            if (tid == 0 && p + kStages < nseq) {  // MMA p and its epilogue are done with the stage
+                const int st = p % kStages;
+                mbar_expect_tx(&S.bar_b[st], kColBytes);
+                bulk_g2s(S.b[st], packY + tile_of(p + kStages) * (int64_t)kColBytes, kColBytes, &S.bar_b[st]);
+                ++issued_b;
+            }
         }
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
     }
-    if (S.failed) {
+    if (failed) {
         // drain: every issued copy and MMA must land before the memory goes
-        // away.  Each barrier has at most one phase outstanding (a stage is
-        // re-armed only after its previous copy was consumed), so waiting for
-        // the last phase issued on each barrier suffices.
+        // away.  Each barrier has at most one phase outstanding, so waiting
+        // for the last phase issued on each barrier suffices.
         if (tid == 0) {
             kmx_raise(err, KMX_DERR_TIMEOUT);
-            mbar_wait(&S.bar_a, 0);
             for (int st = 0; st < kStages; ++st) {
                 const int last = issued_b - 1 - ((issued_b - 1 - st) % kStages + kStages) % kStages;
                 if (last >= 0 && last % kStages == st) mbar_wait(&S.bar_b[st], (last / kStages) & 1);
@@ -374,14 +618,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_topk(const uint8_t* __restrict
                 if (last >= 0 && (last & 1) == k) mbar_wait(&S.bar_mma[k], (last >> 1) & 1);
             }
         }
-        __syncthreads();
-    } else {
-        const int64_t row = row0 + tid;
-        if (row < rows) {
-            Cand* out = part + ((int64_t)chunk * rows_cap + row) * kTopK;
-#pragma unroll
-            for (int k = 0; k < kTopK; ++k) out[k] = Cand{tv[k], ti[k]};
-        }
     }
     tc_fence_before();
     __syncthreads();
@@ -390,113 +626,39 @@ __global__ void __launch_bounds__(kThreads, 1) tc_topk(const uint8_t* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// common mean of both descriptor sets (deterministic: fixed partition, fixed
-// summation order)
+// exact FP32 re-ranking of the collected columns
 // ---------------------------------------------------------------------------
 
-constexpr int kSumBlocks = 64;
-
-// Block b sums, per descriptor value, rows [b*R, (b+1)*R) of P followed by Q.
-__global__ void __launch_bounds__(64) col_partial(const float* __restrict__ P, int64_t np_cap, const int64_t* d_np,
-                                                  const float* __restrict__ Q, int64_t nq_cap, const int64_t* d_nq,
-                                                  double* __restrict__ partial)
-{
-    const int h = threadIdx.x;
-    if (h >= KMX_DESC_DIM) return;
-    const int64_t np = kmx_count(d_np, np_cap), nq = kmx_count(d_nq, nq_cap), n = np + nq;
-    const int64_t R = (n + kSumBlocks - 1) / kSumBlocks;
-    const int64_t lo = (int64_t)blockIdx.x * R, hi = min(n, lo + R);
-    double s = 0.0;
-    for (int64_t r = lo; r < hi; ++r) {
-        const float v = r < np ? __ldg(P + r * KMX_DESC_STRIDE + h) : __ldg(Q + (r - np) * KMX_DESC_STRIDE + h);
-        s += (double)v;
-    }
-    partial[blockIdx.x * KMX_DESC_DIM + h] = s;
-}
-
-__global__ void col_mean(const double* __restrict__ partial, int64_t np_cap, const int64_t* d_np, int64_t nq_cap,
-                         const int64_t* d_nq, float* __restrict__ mean, unsigned int* __restrict__ maxnorm)
-{
-    const int h = threadIdx.x;
-    const int64_t n = kmx_count(d_np, np_cap) + kmx_count(d_nq, nq_cap);
-    if (h < KMX_DESC_DIM) {
-        double s = 0.0;
-        for (int b = 0; b < kSumBlocks; ++b) s += partial[b * KMX_DESC_DIM + h];
-        mean[h] = n > 0 ? (float)(s / (double)n) : 0.f;
-    } else if (h < KMX_DESC_STRIDE) {
-        mean[h] = 0.f;
-    }
-    if (h < 2) maxnorm[h] = 0u;
-}
-
-// ---------------------------------------------------------------------------
-// certified exact FP32 re-ranking
-// ---------------------------------------------------------------------------
-
-// Bound on |approximate key - exact key| for one row (keys ||y||^2 - 2 x.y of
-// the centred descriptors): the split operands represent x, y to 2^-18
-// relative per element and the FP32 accumulation of 144 products adds at
-// most ~2^-16 of sum |x_h y_h|, so 2 * 2^-14 * |x| * max|y| covers the
-// product term with margin; 2^-18 * max|y|^2 covers the FP32 norms and the
-// final fused multiply-add.
-__device__ __forceinline__ float key_error_bound(float x_norm2, float ymax_norm2)
-{
-    return 2.0f * (1.0f / 16384.0f) * sqrtf(x_norm2) * sqrtf(ymax_norm2) + (1.0f / 262144.0f) * ymax_norm2;
-}
-
-// One warp per row of X.  Lane c holds candidate c of the chunk lists
-// (chunks x 8 <= 32).  With a(k) the k-th smallest approximate key over the
-// candidates, a(8) - a(2) > 2E proves that the exact nearest and second-
-// nearest columns are among the candidates (each key is within E of its
-// exact value); the row is then re-ranked exactly: sum_h (x_h - y_h)^2 in
-// FP32 with fmaf in h order, the arithmetic of the exact path, lowest index
-// on ties.  Otherwise the row is flagged for the exact fallback.
-__global__ void __launch_bounds__(256) rerank(const float* __restrict__ X, int64_t rows_cap, const int64_t* d_rows,
-                                              const float* __restrict__ Y, const Cand* __restrict__ part,
-                                              const int* __restrict__ d_chunks, const float* __restrict__ mean,
-                                              const unsigned int* __restrict__ ymax_bits,
-                                              kmx::RowBest* __restrict__ rows_out,
-                                              unsigned long long* __restrict__ cols_best,
-                                              int32_t* __restrict__ fallback, int* __restrict__ final_chunks)
+// One warp per sorted row position.  Rows whose list overflowed are flagged
+// for the exact fallback.  rows_out (source side) gets (d1, NN, d2) at the
+// original row; cols_best (target side) the packed (d1, NN).
+__global__ void __launch_bounds__(256) tc_rerank(const float* __restrict__ X, const int32_t* __restrict__ permX,
+                                                 int64_t nx_cap, const int64_t* d_nx, const float* __restrict__ Y,
+                                                 const int32_t* __restrict__ permY, int64_t ny_cap,
+                                                 const int64_t* d_ny, const int32_t* __restrict__ cand,
+                                                 const int32_t* __restrict__ cnt,
+                                                 kmx::RowBest* __restrict__ rows_out,
+                                                 unsigned long long* __restrict__ cols_best,
+                                                 int32_t* __restrict__ fallback, int* __restrict__ final_chunks)
 {
     const int lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (final_chunks && i == 0 && lane == 0) *final_chunks = 1;  // rows_out holds whole-row summaries
-    if (i >= kmx_count(d_rows, rows_cap)) return;
-    const int chunks = *d_chunks;
-    int j = -1;
-    float a = INFINITY;
-    if (lane < chunks * kTopK) {
-        const Cand c = part[((int64_t)(lane / kTopK) * rows_cap + i) * kTopK + lane % kTopK];
-        j = c.idx;
-        if (j >= 0) a = c.v;
-    }
-    // ranks of the approximate keys (ties by lane), a(2) and a(8)
-    int rank = 0, valid = 0;
-#pragma unroll
-    for (int o = 0; o < 32; ++o) {
-        const float ao = __shfl_sync(0xffffffffu, a, o);
-        const int jo = __shfl_sync(0xffffffffu, j, o);
-        valid += jo >= 0;
-        rank += (jo >= 0) && (ao < a || (ao == a && o < lane));
-    }
-    const float a2 = __shfl_sync(0xffffffffu, a, __ffs(__ballot_sync(0xffffffffu, j >= 0 && rank == 1)) - 1 & 31);
-    const float a8 = __shfl_sync(0xffffffffu, a, __ffs(__ballot_sync(0xffffffffu, j >= 0 && rank == 7)) - 1 & 31);
-    const float* x = X + i * KMX_DESC_STRIDE;
-    float xn2 = 0.f;
-#pragma unroll
-    for (int h = 0; h < KMX_DESC_DIM; ++h) {
-        const float e = __ldg(x + h) - __ldg(mean + h);
-        xn2 = fmaf(e, e, xn2);
-    }
-    const float E = key_error_bound(xn2, __uint_as_float(*ymax_bits));
-    const bool certified = valid < kTopK || (a8 - a2 > 2.0f * E);
-    if (!certified) {
-        if (lane == 0) fallback[i] = 1;
+    if (i >= kmx_count(d_nx, nx_cap)) return;
+    const int orig = permX[i];
+    const int c = cnt[i];
+    if (c > kCandCap) {
+        if (lane == 0) fallback[orig] = 1;
         return;
     }
-    float d = INFINITY;
-    if (j >= 0) {
+    const float* x = X + (int64_t)orig * KMX_DESC_STRIDE;
+    const int64_t ny = kmx_count(d_ny, ny_cap);
+    float b1 = INFINITY, b2 = INFINITY;
+    int j1 = 0x7fffffff;
+    for (int q = lane; q < c; q += 32) {
+        const int pos = cand[i * kCandCap + q];
+        if (pos < 0 || pos >= ny) continue;  // padding columns are never collected
+        const int j = permY[pos];
         const float* y = Y + (int64_t)j * KMX_DESC_STRIDE;
         float acc = 0.f;
 #pragma unroll
@@ -504,11 +666,8 @@ __global__ void __launch_bounds__(256) rerank(const float* __restrict__ X, int64
             const float e = __ldg(x + h) - __ldg(y + h);
             acc = fmaf(e, e, acc);
         }
-        d = acc;
+        kmx::row_update(b1, j1, b2, acc, j);
     }
-    float b1 = d;
-    int j1 = j >= 0 ? j : 0x7fffffff;
-    float b2 = INFINITY;
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) {
         const float od1 = __shfl_xor_sync(0xffffffffu, b1, o);
@@ -517,8 +676,8 @@ __global__ void __launch_bounds__(256) rerank(const float* __restrict__ X, int64
         kmx::row_merge(b1, j1, b2, od1, oj, od2);
     }
     if (lane != 0) return;
-    if (rows_out) rows_out[i] = kmx::RowBest{b1, j1, b2};
-    if (cols_best && j1 != 0x7fffffff) cols_best[i] = kmx::pack_dist_index(b1, (uint32_t)j1);
+    if (rows_out) rows_out[orig] = kmx::RowBest{b1, j1, b2};
+    if (cols_best && j1 != 0x7fffffff) cols_best[orig] = kmx::pack_dist_index(b1, (uint32_t)j1);
 }
 
 // Compact the flagged rows into a list (ascending) and publish its length.
@@ -534,7 +693,7 @@ __global__ void __launch_bounds__(256) compact_flags(int64_t n_cap, const int64_
 }
 
 // Merge the exact fallback partials of each listed row and store them where
-// the certified rows went.
+// the re-ranked rows went.
 __global__ void __launch_bounds__(256) fallback_merge(const kmx::RowBest* __restrict__ part,
                                                       const int* __restrict__ d_chunks, int64_t list_cap,
                                                       const int32_t* __restrict__ list,
@@ -557,18 +716,23 @@ __global__ void __launch_bounds__(256) fallback_merge(const kmx::RowBest* __rest
 
 size_t tc_smem_bytes()
 {
-    // ~100 KB: two CTAs per SM, i.e. two 256-column TMEM allocations
-    size_t need = sizeof(TcShared) + 1024;
+    // at least 96 KB: at most two CTAs per SM, i.e. two 256-column TMEM
+    // allocations (a third CTA would wait in tcgen05.alloc)
+    const size_t need = sizeof(TcShared) + 1024;
     return need < 96 * 1024 ? 96 * 1024 : need;
 }
 
 struct TcBuffers {
+    float4* coords;         // [np_cap + nq_cap]
+    unsigned int* range;    // [8]: min bits of the 4 statistics, then max bits
+    uint32_t *keys, *keys_tmp;
+    int32_t *vals, *vals_tmp;  // sorted: [0, np) source rows, [np_cap, np_cap + nq) target rows
+    void* sort_scratch;
     uint8_t *packP, *packQ;
-    Cand *candP, *candQ;
-    double* partial;
-    float* mean;
-    unsigned int* maxnorm;  // [0] = P side, [1] = Q side
-    int* chunks;            // [0] candP, [1] candQ, [2] fallback P, [3] fallback Q
+    float *cenP, *cenQ;
+    int32_t *nearP, *nearQ;
+    int32_t *candP, *candQ, *cntP, *cntQ;
+    int* chunks;            // [2] fallback P, [3] fallback Q
     int32_t *flagP, *flagQ, *listP, *listQ;
     int64_t *posP, *posQ, *nlist;  // nlist[0] P, [1] Q
     kmx::RowBest *fbP, *fbQ;
@@ -578,15 +742,26 @@ TcBuffers tc_carve(void* base, int64_t np_cap, int64_t nq_cap, size_t* total)
 {
     TcBuffers b{};
     kmx_arena a{static_cast<char*>(base), 0};
+    const int64_t n2 = np_cap + nq_cap;
     const int64_t tp = (np_cap + kTM - 1) / kTM, tq = (nq_cap + kTM - 1) / kTM;
     const int fc = kmx_match_fp32_max_chunks();
-    b.packP = (uint8_t*)a.take((size_t)tp * kTileBytes);
-    b.packQ = (uint8_t*)a.take((size_t)tq * kTileBytes);
-    b.candP = (Cand*)a.take(sizeof(Cand) * kTopK * (size_t)kMaxChunks * (np_cap + 1));
-    b.candQ = (Cand*)a.take(sizeof(Cand) * kTopK * (size_t)kMaxChunks * (nq_cap + 1));
-    b.partial = (double*)a.take(sizeof(double) * kSumBlocks * KMX_DESC_DIM);
-    b.mean = (float*)a.take(sizeof(float) * KMX_DESC_STRIDE);
-    b.maxnorm = (unsigned int*)a.take(sizeof(unsigned int) * 2);
+    b.coords = (float4*)a.take(sizeof(float4) * (size_t)n2);
+    b.range = (unsigned int*)a.take(sizeof(unsigned int) * 8);
+    b.keys = (uint32_t*)a.take(sizeof(uint32_t) * (size_t)n2);
+    b.keys_tmp = (uint32_t*)a.take(sizeof(uint32_t) * (size_t)n2);
+    b.vals = (int32_t*)a.take(sizeof(int32_t) * (size_t)n2);
+    b.vals_tmp = (int32_t*)a.take(sizeof(int32_t) * (size_t)n2);
+    b.sort_scratch = a.take(kmx_sort_scratch_bytes(n2));
+    b.packP = (uint8_t*)a.take((size_t)tp * kColBytes);
+    b.packQ = (uint8_t*)a.take((size_t)tq * kColBytes);
+    b.cenP = (float*)a.take(sizeof(float) * kCenterStride * (size_t)tp);
+    b.cenQ = (float*)a.take(sizeof(float) * kCenterStride * (size_t)tq);
+    b.nearP = (int32_t*)a.take(sizeof(int32_t) * (size_t)tp);
+    b.nearQ = (int32_t*)a.take(sizeof(int32_t) * (size_t)tq);
+    b.candP = (int32_t*)a.take(sizeof(int32_t) * kCandCap * (size_t)np_cap);
+    b.candQ = (int32_t*)a.take(sizeof(int32_t) * kCandCap * (size_t)nq_cap);
+    b.cntP = (int32_t*)a.take(sizeof(int32_t) * (size_t)(np_cap + nq_cap));
+    b.cntQ = b.cntP + np_cap;
     b.chunks = (int*)a.take(sizeof(int) * 4);
     b.flagP = (int32_t*)a.take(sizeof(int32_t) * (np_cap + 1));
     b.flagQ = (int32_t*)a.take(sizeof(int32_t) * (nq_cap + 1));
@@ -616,39 +791,53 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
     cudaStream_t st = ctx->stream;
     size_t total = 0;
     TcBuffers b = tc_carve(s.extra, np_cap, nq_cap, &total);
+    const int64_t n2 = np_cap + nq_cap;
     const int64_t tp = (np_cap + kTM - 1) / kTM, tq = (nq_cap + kTM - 1) / kTM;
     const size_t smem = tc_smem_bytes();
     cudaError_t e = kmx_once_per_device(kmx_attr_tc_topk, [smem] {
-        return cudaFuncSetAttribute(tc_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return cudaFuncSetAttribute(tc_collect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     });
     if (e) return e;
     if ((e = cudaMemsetAsync(b.flagP, 0, sizeof(int32_t) * (np_cap + 1), st))) return e;
     if ((e = cudaMemsetAsync(b.flagQ, 0, sizeof(int32_t) * (nq_cap + 1), st))) return e;
-    const int target = 2 * ctx->sm_count;
-    // common mean, then split-BF16 packs of the centred rows
+    if ((e = cudaMemsetAsync(b.cntP, 0, sizeof(int32_t) * (size_t)n2, st))) return e;
+    if ((e = cudaMemsetAsync(b.range, 0xFF, sizeof(unsigned int) * 4, st))) return e;
+    if ((e = cudaMemsetAsync(b.range + 4, 0, sizeof(unsigned int) * 4, st))) return e;
+    // locality order of both clouds
+    const unsigned gb = kmx_stride_blocks(n2, 256, ctx->sm_count);
     KMX_COUNT_LAUNCH();
-    col_partial<<<kSumBlocks, 64, 0, st>>>(dp, np_cap, d_np, dq, nq_cap, d_nq, b.partial);
+    tc_coords<<<gb, 256, 0, st>>>(dp, np_cap, d_np, dq, nq_cap, d_nq, b.coords, b.range, ctx->d_err);
     KMX_COUNT_LAUNCH();
-    col_mean<<<1, 64, 0, st>>>(b.partial, np_cap, d_np, nq_cap, d_nq, b.mean, b.maxnorm);
+    tc_keys<<<gb, 256, 0, st>>>(np_cap, d_np, nq_cap, d_nq, b.coords, b.range, b.keys, b.vals);
+    if ((e = cudaGetLastError())) return e;
+    if ((e = kmx_sort_u32(ctx, b.keys, b.vals, b.keys_tmp, b.vals_tmp, n2, 32, b.sort_scratch))) return e;
+    const int32_t* permP = b.vals;
+    const int32_t* permQ = b.vals + np_cap;
+    // packed tiles and centres
     KMX_COUNT_LAUNCH();
-    pack_bf16<<<kmx_blocks(tp * kTM, 256), 256, 0, st>>>(dp, np_cap, d_np, tp * kTM, b.mean, b.packP, b.maxnorm);
+    tc_pack<<<(unsigned)tp, kTM, 0, st>>>(dp, permP, np_cap, d_np, b.packP, b.cenP);
     KMX_COUNT_LAUNCH();
-    pack_bf16<<<kmx_blocks(tq * kTM, 256), 256, 0, st>>>(dq, nq_cap, d_nq, tq * kTM, b.mean, b.packQ,
-                                                        b.maxnorm + 1);
+    tc_pack<<<(unsigned)tq, kTM, 0, st>>>(dq, permQ, nq_cap, d_nq, b.packQ, b.cenQ);
+    KMX_COUNT_LAUNCH();
+    tc_nearest<<<kmx_blocks(tp, 8), 256, 0, st>>>(b.cenP, np_cap, d_np, b.cenQ, nq_cap, d_nq, b.nearP);
+    KMX_COUNT_LAUNCH();
+    tc_nearest<<<kmx_blocks(tq, 8), 256, 0, st>>>(b.cenQ, nq_cap, d_nq, b.cenP, np_cap, d_np, b.nearQ);
     // candidates both ways
+    const int target = 2 * ctx->sm_count;
     KMX_COUNT_LAUNCH();
-    tc_topk<<<(unsigned)(tp * kMaxChunks), kThreads, smem, st>>>(b.packP, np_cap, d_np, b.packQ, nq_cap, d_nq, target,
-                                                                 b.candP, b.chunks + 0, ctx->d_err);
+    tc_collect<<<(unsigned)(tp * kMaxChunks), kThreads, smem, st>>>(dp, permP, np_cap, d_np, b.packQ, nq_cap, d_nq,
+                                                                    b.nearP, target, b.candP, b.cntP, ctx->d_err);
     KMX_COUNT_LAUNCH();
-    tc_topk<<<(unsigned)(tq * kMaxChunks), kThreads, smem, st>>>(b.packQ, nq_cap, d_nq, b.packP, np_cap, d_np, target,
-                                                                 b.candQ, b.chunks + 1, ctx->d_err);
-    // certified exact re-ranking; uncertified rows are flagged
+    tc_collect<<<(unsigned)(tq * kMaxChunks), kThreads, smem, st>>>(dq, permQ, nq_cap, d_nq, b.packP, np_cap, d_np,
+                                                                    b.nearQ, target, b.candQ, b.cntQ, ctx->d_err);
+    // exact re-ranking; overflowed rows are flagged
     KMX_COUNT_LAUNCH();
-    rerank<<<kmx_blocks(np_cap, 8), 256, 0, st>>>(dp, np_cap, d_np, dq, b.candP, b.chunks + 0, b.mean, b.maxnorm + 1,
-                                                  s.part, nullptr, b.flagP, s.chunks);
+    tc_rerank<<<kmx_blocks(np_cap, 8), 256, 0, st>>>(dp, permP, np_cap, d_np, dq, permQ, nq_cap, d_nq, b.candP,
+                                                     b.cntP, s.part, nullptr, b.flagP, s.chunks);
     KMX_COUNT_LAUNCH();
-    rerank<<<kmx_blocks(nq_cap, 8), 256, 0, st>>>(dq, nq_cap, d_nq, dp, b.candQ, b.chunks + 1, b.mean, b.maxnorm,
-                                                  nullptr, s.colbest, b.flagQ, nullptr);
+    tc_rerank<<<kmx_blocks(nq_cap, 8), 256, 0, st>>>(dq, permQ, nq_cap, d_nq, dp, permP, np_cap, d_np, b.candQ,
+                                                     b.cntQ, nullptr, s.colbest, b.flagQ, nullptr);
+    if ((e = cudaGetLastError())) return e;
     // exact fallback for the flagged rows of each side
     if ((e = kmx_scan_i32(ctx, b.flagP, np_cap, d_np, b.posP))) return e;
     KMX_COUNT_LAUNCH();
@@ -671,12 +860,40 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
     return cudaGetLastError();
 }
 
-// Rows that needed the exact fallback in the last BF16 match on this scratch
-// (diagnostics): copies nlist[0..1] to the caller's device buffer.
-cudaError_t kmx_match_tc_fallback_counts(kmx_ctx* ctx, const kmx::MatchScratch& s, int64_t np_cap, int64_t nq_cap,
-                                         int64_t* dst)
+// Diagnostics of the last tensor-core match on this scratch: rows that went
+// through the exact fallback (source, target) and candidates collected
+// (source, target), as four int64 values in the caller's device buffer.
+__global__ void tc_stats(const int64_t* __restrict__ nlist, const int32_t* __restrict__ cntP, int64_t np_cap,
+                         const int64_t* d_np, const int32_t* __restrict__ cntQ, int64_t nq_cap, const int64_t* d_nq,
+                         int64_t* __restrict__ out)
+{
+    __shared__ unsigned long long sp, sq;
+    if (threadIdx.x == 0) {
+        sp = 0;
+        sq = 0;
+    }
+    __syncthreads();
+    const int64_t np = kmx_count(d_np, np_cap), nq = kmx_count(d_nq, nq_cap);
+    unsigned long long a = 0, b = 0;
+    for (int64_t i = threadIdx.x; i < np; i += blockDim.x) a += (unsigned long long)min(cntP[i], kCandCap);
+    for (int64_t i = threadIdx.x; i < nq; i += blockDim.x) b += (unsigned long long)min(cntQ[i], kCandCap);
+    atomicAdd(&sp, a);
+    atomicAdd(&sq, b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        out[0] = nlist[0];
+        out[1] = nlist[1];
+        out[2] = (int64_t)sp;
+        out[3] = (int64_t)sq;
+    }
+}
+
+cudaError_t kmx_match_tc_stats(kmx_ctx* ctx, void* extra, int64_t np_cap, const int64_t* d_np, int64_t nq_cap,
+                               const int64_t* d_nq, int64_t* dst)
 {
     size_t total = 0;
-    TcBuffers b = tc_carve(s.extra, np_cap, nq_cap, &total);
-    return cudaMemcpyAsync(dst, b.nlist, 2 * sizeof(int64_t), cudaMemcpyDeviceToDevice, ctx->stream);
+    TcBuffers b = tc_carve(extra, np_cap, nq_cap, &total);
+    KMX_COUNT_LAUNCH();
+    tc_stats<<<1, 256, 0, ctx->stream>>>(b.nlist, b.cntP, np_cap, d_np, b.cntQ, nq_cap, d_nq, dst);
+    return cudaGetLastError();
 }

@@ -1,0 +1,140 @@
+// Stable least-significant-digit radix sort of (uint32 key, int32 value)
+// pairs, 8 bits per pass.  The tensor-core matcher uses it to put descriptor
+// rows in the order of a locality key, so that 128-row tiles hold similar
+// descriptors.
+//
+// One pass over digit position p:
+//   count    block b counts the digits of its 2048 elements; counts are laid
+//            out digit-major (counts[d * blocks + b]) so that their
+//            exclusive scan is, for every (digit, block), the first output
+//            position of that block's elements with that digit;
+//   scan     kmx_scan_i32 over the 256 * blocks counts;
+//   scatter  block b writes element e with digit d to
+//            scan[d * blocks + b] + (elements of the block before e with
+//            digit d).  Elements are taken in index order (item k of thread
+//            t is element 256 k + t), warps resolve equal digits with
+//            __match_any_sync, and the per-digit prefixes over warps and
+//            items are kept in shared memory, so the pass is stable.
+#include "kmx_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = 8;
+constexpr int kPerBlock = kThreads * kItems;
+constexpr int kDigits = 256;
+constexpr int kWarps = kThreads / 32;
+
+__global__ void __launch_bounds__(kThreads) radix_count(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                                                        int32_t* __restrict__ counts, int blocks)
+{
+    __shared__ int hist[kDigits];
+    hist[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kPerBlock;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        const int64_t e = base + k * kThreads + threadIdx.x;
+        if (e < n) atomicAdd(&hist[(keys[e] >> shift) & 0xFFu], 1);
+    }
+    __syncthreads();
+    counts[(int64_t)threadIdx.x * blocks + blockIdx.x] = hist[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kThreads) radix_scatter(const uint32_t* __restrict__ keys,
+                                                          const int32_t* __restrict__ vals, int64_t n, int shift,
+                                                          const int64_t* __restrict__ offs, int blocks,
+                                                          uint32_t* __restrict__ keys_out,
+                                                          int32_t* __restrict__ vals_out)
+{
+    __shared__ int wcount[kWarps][kDigits];  // this item's count per warp and digit, then its warp prefix
+    __shared__ int running[kDigits];         // elements of earlier items, per digit
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    running[tid] = 0;
+    const int64_t base = (int64_t)blockIdx.x * kPerBlock;
+    const int64_t first = offs[(int64_t)tid * blocks + blockIdx.x];  // thread tid holds digit tid's start
+    __shared__ int64_t start[kDigits];
+    start[tid] = first;
+    for (int k = 0; k < kItems; ++k) {
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) wcount[w][tid] = 0;
+        __syncthreads();
+        const int64_t e = base + k * kThreads + tid;
+        const bool valid = e < n;
+        const uint32_t key = valid ? keys[e] : 0u;
+        const int d = (int)((key >> shift) & 0xFFu);
+        const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+        int rank = 0;
+        if (valid) {
+            const unsigned peers = __match_any_sync(vmask, d);
+            rank = __popc(peers & lt);
+            if (rank == 0) wcount[warp][d] = __popc(peers);
+        }
+        __syncthreads();
+        {  // thread tid: exclusive prefix over warps of digit tid
+            int acc = running[tid];
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                const int c = wcount[w][tid];
+                wcount[w][tid] = acc;
+                acc += c;
+            }
+            running[tid] = acc;
+        }
+        __syncthreads();
+        if (valid) {
+            const int64_t pos = start[d] + wcount[warp][d] + rank;
+            keys_out[pos] = key;
+            vals_out[pos] = vals[e];
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+int kmx_sort_blocks(int64_t n) { return (int)((n + kPerBlock - 1) / kPerBlock); }
+
+size_t kmx_sort_scratch_bytes(int64_t n)
+{
+    const int64_t b = kmx_sort_blocks(n) > 0 ? kmx_sort_blocks(n) : 1;
+    kmx_arena a{nullptr, 0};
+    a.take(sizeof(int32_t) * (size_t)(kDigits * b + 1));
+    a.take(sizeof(int64_t) * (size_t)(kDigits * b + 1));
+    return kmx_align_up(a.used, 256);
+}
+
+cudaError_t kmx_sort_u32(kmx_ctx* ctx, uint32_t* keys, int32_t* vals, uint32_t* keys_tmp, int32_t* vals_tmp,
+                         int64_t n, int bits, void* scratch)
+{
+    if (n <= 0) return cudaSuccess;
+    const int blocks = kmx_sort_blocks(n);
+    kmx_arena a{static_cast<char*>(scratch), 0};
+    int32_t* counts = (int32_t*)a.take(sizeof(int32_t) * (size_t)(kDigits * blocks + 1));
+    int64_t* offs = (int64_t*)a.take(sizeof(int64_t) * (size_t)(kDigits * blocks + 1));
+    const int64_t m = (int64_t)kDigits * blocks;
+    uint32_t *ki = keys, *ko = keys_tmp;
+    int32_t *vi = vals, *vo = vals_tmp;
+    cudaError_t e;
+    for (int shift = 0; shift < bits; shift += 8) {
+        KMX_COUNT_LAUNCH();
+        radix_count<<<blocks, kThreads, 0, ctx->stream>>>(ki, n, shift, counts, blocks);
+        if ((e = cudaGetLastError())) return e;
+        if ((e = kmx_scan_i32(ctx, counts, m, nullptr, offs))) return e;
+        KMX_COUNT_LAUNCH();
+        radix_scatter<<<blocks, kThreads, 0, ctx->stream>>>(ki, vi, n, shift, offs, blocks, ko, vo);
+        if ((e = cudaGetLastError())) return e;
+        uint32_t* tk = ki;
+        ki = ko;
+        ko = tk;
+        int32_t* tv = vi;
+        vi = vo;
+        vo = tv;
+    }
+    if (ki != keys) {  // an odd number of passes: the result is in the temporaries
+        if ((e = cudaMemcpyAsync(keys, ki, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream))) return e;
+        if ((e = cudaMemcpyAsync(vals, vi, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream))) return e;
+    }
+    return cudaSuccess;
+}

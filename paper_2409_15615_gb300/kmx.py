@@ -93,6 +93,7 @@ def library():
         "kmx_ground_bins": (C.c_int32, [C.POINTER(GroundParams)]),
         "kmx_suppress_ground": (C.c_int, [vp, vp, i64, i32, C.POINTER(GroundParams), vp, vp, vp, vp]),
         "kmx_match": (C.c_int, [vp, vp, vp, i64, vp, vp, vp, i64, vp, i32, vp, i64, vp]),
+        "kmx_match_diag": (C.c_int, [vp, i64, vp, i64, vp, vp]),
         "kmx_prune": (C.c_int, [vp, vp, i64, vp, vp, vp, i32, C.c_double, vp, vp, vp, vp, vp, vp]),
         "kmx_gnc": (C.c_int, [vp, vp, vp, vp, vp, i64, vp, vp, C.c_double, i32, C.c_double, C.c_double, vp, vp,
                               vp, vp]),
@@ -338,6 +339,14 @@ class Context:
                                        _ptr(n_out)), "kmx_match")
         return out, n_out
 
+    def match_diag(self, np_cap, nq_cap, d_np=None, d_nq=None):
+        """kmx_match_diag after a KMX_MATCH_BF16_RERANK match of these
+        capacities: int64 tensor [4] (fallback rows source / target,
+        candidates collected source / target)."""
+        out = torch.zeros(4, dtype=torch.int64, device=self.device)
+        self._check(self.lib.kmx_match_diag(self.h, int(np_cap), _ptr(d_np), int(nq_cap), _ptr(d_nq), _ptr(out)),
+                    "kmx_match_diag")
+        return out
 
     def prune(self, corr, corr_cap, src4, tgt4, beta, n_tau=3000, d_n_corr=None, out=None):
         """kmx_prune (Sec. III-D): ratio filter, pairwise-invariant graph, max
