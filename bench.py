@@ -1,15 +1,19 @@
 """Benchmark of the kmx front end: Faster-PFH + mutual-NN registration pairs
-per second on the LiDAR-shaped pair (64 beams x 2048 azimuth bins, ~120k raw
-points per scan, voxel 0.3 m -> ~19k voxelised points).
+per second on the large dense pair (2M raw points per cloud from the
+indoor-room generator, voxel 0.02 m -> ~300k voxelised points and ~300k
+descriptors per cloud, full ~300k x ~300k mutual nearest-neighbour
+matching), the largest configuration that one GPU holds.
 
 One step = one registration pair through the whole hot path: voxelise both
 clouds, hashed grid, radius search + normals (Algorithm 1 step 1), step 2 +
 SPFH + FPFH (Eqs. A2-A5), mutual matching (Sec. III-C), inputs resident in
-HBM.  L2 is flushed (a 512 MB write) between timed steps, outside the timed
-events.  ``e2e`` streams the same pairs through the public overlapped API
-(pipeline.PairStream) from pinned host memory: every pair's host->device copies
-and the read-back of its correspondences are inside the timed region, and the
-copies of neighbouring pairs overlap the current pair's kernels.
+HBM, the pair replayed as one CUDA graph.  L2 is flushed (a 512 MB write)
+between timed steps, outside the timed events.  ``e2e`` streams the same
+pairs through the public overlapped API (pipeline.PairStream) from pinned
+host memory: every pair's host->device copies and the read-back of its
+correspondences are inside the timed region.  The LiDAR scan pair (64 beams
+x 2048 azimuth bins, voxel 0.3 m) follows as the ``lidar_pair`` block, with
+the batched, serving, registration, suppression and ablation sections.
 
 Under torchrun every rank runs its own pair (replicas, weak scaling, no
 collective on the data path; a barrier and a max-reduction of the timings
@@ -30,20 +34,23 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from synth import lidar_pair  # noqa: E402
+from synth import indoor_pair, lidar_pair  # noqa: E402
 
-WORKLOAD = dict(name="lidar_pair_64beam_2048az_v0.3", voxel=0.3, az_bins=2048, seed=1000)
+INDOOR = dict(name="indoor_pair_2M_v0.02", kind="indoor", voxel=0.02, seed=31, slots=2)
+LIDAR = dict(name="lidar_pair_64beam_2048az_v0.3", kind="lidar", voxel=0.3, az_bins=2048, seed=1000, slots=4)
+WORKLOAD = INDOOR
 
-# DRAM bytes (read + write) of one launch, from the ncu captures summarised in
-# profiles/; an entry is removed whenever its kernel changes.
-PROFILED_TRAFFIC = {"match_tiles_fp32_bulk": 5341440}  # DRAM read+write bytes of one launch (ncu, LiDAR pair)
-METRIC = "Faster-PFH+mutual-NN pairs/s (LiDAR scan pair, voxel 0.3 m)"
+# DRAM bytes (read + write) of one launch of the dominant kernel, from the ncu
+# capture summarised beside it; None until the current kernel was captured.
+PROFILED_TRAFFIC = {}
+METRIC = "Faster-PFH+mutual-NN pairs/s (2M-point indoor pair, voxel 0.02 m, full mutual NN)"
+ORACLE_MATCH_ROWS = 400  # rows per side of the oracle's sampled FP64 brute-force matching
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="kmx", choices=["kmx", "reference"])
     ap.add_argument("--match", default="auto", choices=["auto", "fp32", "bf16"])
@@ -52,17 +59,16 @@ def parse():
                                                              "the pair captured as one CUDA graph")
     ap.add_argument("--batch-pairs", type=int, default=256,
                     help="also time a batch of this many uneven pairs in one graph launch (0 = skip)")
-    ap.add_argument("--serve-requests", type=int, default=64,
+    ap.add_argument("--serve-requests", type=int, default=1000,
                     help="also run the serving loop with this many requests per rate (0 = skip)")
     ap.add_argument("--serve-rates", default="50,100,200,500,1000,2000",
                     help="request rates (req/s) for the serving loop")
-    ap.add_argument("--no-indoor", action="store_true", help="skip the 2M-point indoor pair (voxel 0.02 m, "
-                    "full ~300k x 300k matching in both modes)")
+    ap.add_argument("--no-lidar", action="store_true", help="skip the LiDAR scan pair block")
     ap.add_argument("--no-ablation", action="store_true", help="skip the classic-FPFH vs Faster-PFH comparison")
     ap.add_argument("--no-suppressed", action="store_true", help="skip the LiDAR pair with geometric suppression "
                     "(ground removal) and device-side registration")
     ap.add_argument("--no-register", action="store_true", help="skip timing kmx_prune + kmx_gnc (ratio filter, "
-                    "invariant graph, max k-core, GNC-TLS pose) on the pair's correspondences")
+                    "invariant graph, max k-core, GNC-TLS pose) on the LiDAR pair's correspondences")
     return ap.parse_args()
 
 
@@ -72,10 +78,15 @@ def dist_env():
     return replicas.dist_env()
 
 
-def make_pair(rank):
+def make_pair(w, rank):
+    """(src, tgt, vp_src, vp_tgt, R, t) of workload ``w`` for this rank."""
     from paper_2409_15615_gb300 import replicas
 
-    src, tgt, R, t, vps, vpt = lidar_pair(replicas.pair_seed(WORKLOAD["seed"], rank), az_bins=WORKLOAD["az_bins"])
+    seed = replicas.pair_seed(w["seed"], rank)
+    if w["kind"] == "indoor":
+        src, tgt, R, t, vps, vpt = indoor_pair(seed)
+    else:
+        src, tgt, R, t, vps, vpt = lidar_pair(seed, az_bins=w["az_bins"])
     return src, tgt, vps, vpt, R, t
 
 
@@ -84,13 +95,33 @@ def make_pair(rank):
 # ----------------------------------------------------------------------------
 
 
-def oracle_pair_seconds(src, tgt, vps, vpt):
+def oracle_pair_sample(src, tgt, vps, vpt, v, match_rows=ORACLE_MATCH_ROWS, seed=0):
+    """The oracle on one pair of the workload, on the host cores: voxelise
+    both clouds, Faster-PFH on both whole clouds, and the FP64 brute-force
+    nearest rows of ``match_rows`` sampled rows of each side against every
+    row of the other side.  Returns (estimated seconds for the whole pair,
+    seconds spent): the matching time is scaled by (rows of the side) /
+    match_rows per direction, the other stages count as measured."""
     import oracle
 
-    v = WORKLOAD["voxel"]
     t0 = time.perf_counter()
-    oracle.front_end(src, tgt, v, np.float32(vps).astype(np.float64), np.float32(vpt).astype(np.float64))
-    return time.perf_counter() - t0
+    vs, _ = oracle.voxelize(src, v)
+    vt, _ = oracle.voxelize(tgt, v)
+    fs = oracle.faster_pfh(vs, oracle.OracleParams(v, viewpoint=np.float32(vps).astype(np.float64)))
+    ft = oracle.faster_pfh(vt, oracle.OracleParams(v, viewpoint=np.float32(vpt).astype(np.float64)))
+    t1 = time.perf_counter()
+    FP, FQ = fs["fpfh"], ft["fpfh"]
+    rng = np.random.default_rng(seed)
+    est = t1 - t0
+    for X, Y in ((FP, FQ), (FQ, FP)):
+        if len(X) == 0 or len(Y) == 0:
+            continue
+        k = min(match_rows, len(X))
+        rows = X[rng.choice(len(X), k, replace=False)]
+        a = time.perf_counter()
+        oracle.nearest(rows, Y)
+        est += (time.perf_counter() - a) * len(X) / k
+    return est, time.perf_counter() - t0
 
 
 def oracle_cores():
@@ -98,27 +129,16 @@ def oracle_cores():
     return int(n) if n else (os.cpu_count() or 1)
 
 
-def cpu_baseline(src, tgt, vps, vpt, budget_s=12.0):
-    times = []
-    t_end = time.perf_counter() + budget_s
-    while not times or (time.perf_counter() < t_end and len(times) < 20):
-        times.append(oracle_pair_seconds(src, tgt, vps, vpt))
-    out = dict(value=1.0 / statistics.median(times), unit="pairs/s", cores=oracle_cores(), kind="oracle",
-               sample="%d whole pairs of the workload (voxelise, Faster-PFH on both clouds, FP64 brute-force "
-                      "mutual NN); median pair time %.3f s" % (len(times), statistics.median(times)))
-    # the same pair once on one host thread (a child process with OMP_NUM_THREADS=1)
-    code = ("import sys, time, numpy as np; sys.path.insert(0, %r); import bench; "
-            "from synth import lidar_pair; "
-            "s, t, R, tr, a, b = lidar_pair(%d, az_bins=%d); "
-            "print(bench.oracle_pair_seconds(s, t, a, b))" % (ROOT, WORKLOAD["seed"], WORKLOAD["az_bins"]))
-    try:
-        env = dict(os.environ, OMP_NUM_THREADS="1")
-        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
-        sec = float(r.stdout.strip().splitlines()[-1])
-        out["one_thread"] = dict(value=1.0 / sec, unit="pairs/s", cores=1, sample="one whole pair of the workload")
-    except (subprocess.SubprocessError, ValueError, IndexError, OSError) as e:
-        out["one_thread"] = dict(error=type(e).__name__)
-    return out
+def oracle_sample_text(w):
+    return ("one pair of %s: oracle voxelisation and Faster-PFH of both whole clouds, FP64 brute-force nearest "
+            "rows of %d sampled rows per side against all rows of the other side, the matching time scaled "
+            "to every row of both sides" % (w["name"], ORACLE_MATCH_ROWS))
+
+
+def cpu_baseline(w, src, tgt, vps, vpt):
+    est, spent = oracle_pair_sample(src, tgt, vps, vpt, w["voxel"])
+    return dict(value=1.0 / est, unit="pairs/s", cores=oracle_cores(), kind="oracle",
+                sample=oracle_sample_text(w) + "; estimated %.2f s per pair, %.1f s of host time spent" % (est, spent))
 
 
 def run_reference(args):
@@ -128,18 +148,25 @@ def run_reference(args):
     from oracle import build as ob
 
     ob.build()
-    src, tgt, vps, vpt, _, _ = make_pair(0)
-    for _ in range(min(args.warmup, 1)):
-        oracle_pair_seconds(src, tgt, vps, vpt)
-    times = [oracle_pair_seconds(src, tgt, vps, vpt) for _ in range(args.steps)]
-    total = sum(times)
+    w = WORKLOAD
+    src, tgt, vps, vpt, _, _ = make_pair(w, 0)
+    for k in range(min(args.warmup, 1)):
+        oracle_pair_sample(src, tgt, vps, vpt, w["voxel"], seed=1000 + k)
+    est = []
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        est.append(oracle_pair_sample(src, tgt, vps, vpt, w["voxel"], seed=k)[0])
+    spent = time.perf_counter() - t0
+    total = sum(est)
     value = args.steps / total
     line = dict(metric=METRIC, value=value, unit="pairs/s", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
                 ms_per_step=1000 * total / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f64", data="synthetic", impl="reference",
-                config=dict(workload=WORKLOAD["name"], raw_points=[len(src), len(tgt)]),
+                config=dict(workload=w["name"], raw_points=[len(src), len(tgt)], voxel=w["voxel"],
+                            parallelism="replicas", l2="not applicable (host)"),
                 cpu_baseline=dict(value=value, unit="pairs/s", kind="oracle", cores=oracle_cores(),
-                                  sample="every step is one whole pair of the workload on the host cores"),
+                                  sample="every step: " + oracle_sample_text(w) + "; %.1f s of host time for %d "
+                                         "steps" % (spent, args.steps)),
                 e2e=dict(value=value, unit="pairs/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
@@ -154,12 +181,12 @@ class ClockSampler:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, period_ms=50):
         self.proc = None
         self.gpu = gpu_index
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.QUERY,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(period_ms)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
@@ -197,23 +224,19 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 
 
-def run_kmx(args):
-    import torch
+def mode_name(kmx, m):
+    return "fp32_exact" if m == kmx.MATCH_FP32_EXACT else "bf16_tensor_rerank"
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
 
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_2409_15615_gb300 import build as kb
+def bench_pair(torch, w, args, rank, world, local, headline):
+    """One workload's pair step: graph replay, L2 flushed between steps, the
+    match mode chosen on warm-up steps (both modes return the exact
+    correspondence set); per-stage times, roofline, end to end through host
+    buffers.  Returns the fields of a bench line."""
+    from paper_2409_15615_gb300 import kmx, pipeline, replicas
 
-    kb.build()
-    from paper_2409_15615_gb300 import kmx, pipeline
-
-    mode = kmx.MATCH_BF16_RERANK if args.match == "bf16" else kmx.MATCH_FP32_EXACT
-    src, tgt, vps, vpt, R_gt, t_gt = make_pair(rank)
-    v = WORKLOAD["voxel"]
+    src, tgt, vps, vpt, R_gt, t_gt = make_pair(w, rank)
+    v = w["voxel"]
     ps = kmx.params_default(v, viewpoint=np.float32(vps).tolist())
     pt = kmx.params_default(v, viewpoint=np.float32(vpt).tolist())
     stream = torch.cuda.current_stream()
@@ -221,27 +244,25 @@ def run_kmx(args):
     pair = pipeline.PairState(ctx, len(src), len(tgt))
     pair.src.raw.copy_(torch.from_numpy(src).cuda())
     pair.tgt.raw.copy_(torch.from_numpy(tgt).cuda())
-    pair.run_checked(len(src), len(tgt), ps, pt, mode)  # sizes buffers, checks device errors
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-
-    # both match modes return the exact correspondence set; "auto" keeps the
-    # faster one for this workload (timed on warm-up steps)
-    mode_ms = {}
-    if args.match == "auto":
-        for m in (kmx.MATCH_FP32_EXACT, kmx.MATCH_BF16_RERANK):
-            pair.run_checked(len(src), len(tgt), ps, pt, m)
-            t = []
-            for _ in range(3):
-                flush.zero_()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                pair.run(len(src), len(tgt), ps, pt, m)
-                b.record(stream)
-                b.synchronize()
-                t.append(a.elapsed_time(b))
-            mode_ms["fp32_exact" if m == kmx.MATCH_FP32_EXACT else "bf16_certified"] = float(np.median(t))
-        mode = min((kmx.MATCH_FP32_EXACT, kmx.MATCH_BF16_RERANK),
-                   key=lambda m: mode_ms["fp32_exact" if m == kmx.MATCH_FP32_EXACT else "bf16_certified"])
+    modes = {"fp32": [kmx.MATCH_FP32_EXACT], "bf16": [kmx.MATCH_BF16_RERANK],
+             "auto": [kmx.MATCH_FP32_EXACT, kmx.MATCH_BF16_RERANK]}[args.match]
+    mode_ms, sets = {}, {}
+    for m in modes:
+        pair.run_checked(len(src), len(tgt), ps, pt, m)  # sizes buffers, checks device errors
+        sets[m] = pair.corr[: int(pair.n_corr.item())].cpu().numpy()
+        t = []
+        for _ in range(3):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pair.run(len(src), len(tgt), ps, pt, m)
+            b.record(stream)
+            b.synchronize()
+            t.append(a.elapsed_time(b))
+        mode_ms[mode_name(kmx, m)] = float(np.median(t))
+    mode = min(modes, key=lambda m: mode_ms[mode_name(kmx, m)])
+    identical = all(np.array_equal(sets[m], sets[modes[0]]) for m in modes)
 
     def direct_step():
         pair.run(len(src), len(tgt), ps, pt, mode)
@@ -268,8 +289,9 @@ def run_kmx(args):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    time.sleep(0.3)
+    clocks = ClockSampler(local) if headline else None
+    if clocks:
+        time.sleep(0.3)
     wall0 = time.perf_counter()
     for k in range(args.steps):
         flush.zero_()
@@ -280,43 +302,71 @@ def run_kmx(args):
     wall = time.perf_counter() - wall0
     if world > 1:
         torch.distributed.barrier()
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
     pair.sync()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    from paper_2409_15615_gb300 import replicas
-
-    total_ms = replicas.max_over_ranks(sum(step_ms), device="cuda")
-    value = replicas.whole_job_throughput(args.steps, world, total_ms / 1000.0)
+    total_ms = replicas.max_over_ranks(sum(step_ms), device="cuda") if headline else sum(step_ms)
+    value = replicas.whole_job_throughput(args.steps, world if headline else 1, total_ms / 1000.0)
 
     # ---- per-stage timing (events between the C-ABI calls of one step)
     stages = stage_times(torch, ctx, pair, len(src), len(tgt), ps, pt, mode, flush, reps=max(5, args.steps // 2))
-    work = algorithmic_work(pair, ctx)
+    work = algorithmic_work(pair, ctx, mode)
     roof = roofline(stages, work, mode)
     roof["feature_stages"] = stage_roofline(stages, work)
+    diag = None
+    if mode == kmx.MATCH_BF16_RERANK:
+        s_, t_ = pair.src, pair.tgt
+        d = ctx.match_diag(s_.n_cap, t_.n_cap, s_.out["n_valid"], t_.out["n_valid"]).cpu().numpy()
+        ctx.sync()
+        np_, nq_ = work["match"]["np"], work["match"]["nq"]
+        diag = dict(fallback_rows=[int(d[0]), int(d[1])],
+                    candidates_per_row=[float(d[2]) / max(np_, 1), float(d[3]) / max(nq_, 1)])
 
     # ---- end to end through host buffers
-    e2e = end_to_end(torch, ctx, pair, src, tgt, ps, pt, mode, flush, args.steps, world)
+    e2e = end_to_end(torch, ctx, pair, src, tgt, ps, pt, mode, args.steps, world if headline else 1, w["slots"],
+                     reduce=headline)
 
     launches = count_launches(torch, direct_step)  # the captured graph holds the same kernels
-    n_src_vox = int(pair.src.n_vox.item())
-    n_tgt_vox = int(pair.tgt.n_vox.item())
+    n_vox = [int(pair.src.n_vox.item()), int(pair.tgt.n_vox.item())]
+    n_desc = [int(pair.src.out["n_valid"].item()), int(pair.tgt.out["n_valid"].item())]
     n_corr = int(pair.n_corr.item())
-    if rank != 0:
-        return
-    line = dict(
-        metric=METRIC, value=value, unit="pairs/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
-        ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
-        dtype="f32" if mode == kmx.MATCH_FP32_EXACT else "bf16+f32", data="synthetic",
-        config=dict(workload=WORKLOAD["name"], raw_points=[len(src), len(tgt)], voxelised=[n_src_vox, n_tgt_vox],
-                    descriptors=[int(pair.src.out["n_valid"].item()), int(pair.tgt.out["n_valid"].item())],
-                    correspondences=n_corr, match="fp32_exact" if mode == kmx.MATCH_FP32_EXACT else "bf16_rerank",
+    out = dict(
+        value=value, unit="pairs/s", ms_per_step=total_ms / args.steps,
+        dtype="f32" if mode == kmx.MATCH_FP32_EXACT else "bf16+f32",
+        config=dict(workload=w["name"], raw_points=[len(src), len(tgt)], voxel=v, voxelised=n_vox,
+                    descriptors=n_desc, correspondences=n_corr, match=mode_name(kmx, mode),
                     l2="flushed between steps (512 MB write outside the timed events)", parallelism="replicas"),
-        points_per_s=world * args.steps * (n_src_vox + n_tgt_vox) / (total_ms / 1000.0),
+        points_per_s=(world if headline else 1) * args.steps * sum(n_vox) / (total_ms / 1000.0),
         latency_ms=dict(p50=float(np.percentile(step_ms, 50)), p99=float(np.percentile(step_ms, 99))),
         wall_s=wall, stages_ms=stages, roofline=roof, e2e=e2e, gpu_launches=launches * args.steps,
-        gpu_launches_per_step=launches, clocks=clk, match_mode_ms_per_step=mode_ms or None,
-        cuda_graph=graph is not None,
-    )
+        gpu_launches_per_step=launches, clocks=clk, match_mode_ms_per_step=mode_ms,
+        match_modes_identical=identical, tensor_match_diag=diag, cuda_graph=graph is not None)
+    del graph
+    pair.close()
+    ctx.close()
+    return out, (src, tgt, vps, vpt)
+
+
+def run_kmx(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2409_15615_gb300 import build as kb
+
+    kb.build()
+    head, (src, tgt, vps, vpt) = bench_pair(torch, WORKLOAD, args, rank, world, local, headline=True)
+    if rank != 0:
+        return
+    line = dict(metric=METRIC, value=head.pop("value"), unit=head.pop("unit"), n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=head.pop("ms_per_step"), higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype=head.pop("dtype"), data="synthetic")
+    line.update(head)
+
     # the sections after the headline each run guarded: a failure is recorded
     # in its entry ({"error": ...}) and the line is still printed
     def section(name, fn):
@@ -325,24 +375,23 @@ def run_kmx(args):
         except Exception as e:  # reported in the JSON line, not hidden
             line[name] = {"error": "%s: %s" % (type(e).__name__, str(e).splitlines()[0] if str(e) else "")}
 
+    if not args.no_lidar:
+        section("lidar_pair", lambda: bench_pair(torch, LIDAR, args, rank, 1, local, headline=False)[0])
     if not args.no_register:
-        section("register", lambda: bench_register(torch, ctx, pair, WORKLOAD["voxel"], R_gt, t_gt,
-                                                   reps=max(5, args.steps // 4),
+        section("register", lambda: bench_register(torch, rank, reps=max(5, args.steps // 4),
                                                    with_oracle=world == 1 and not args.no_cpu_baseline))
     if not args.no_suppressed:
         section("suppressed", lambda: bench_suppressed(torch, rank, steps=max(10, args.steps),
                                                        warmup=max(3, args.warmup)))
     if not args.no_ablation:
         section("ablation_classic_fpfh", lambda: bench_ablation(torch, rank, reps=max(5, args.steps // 3)))
-    if not args.no_indoor:
-        section("indoor", lambda: bench_indoor(torch, rank, reps=3))
     if args.batch_pairs > 0:
         section("batched", lambda: bench_batched(torch, args.batch_pairs, rank))
     if args.serve_requests > 0:
         section("serving", lambda: bench_serving(torch, args.serve_requests,
                                                  [float(x) for x in args.serve_rates.split(",")], rank))
     if world == 1 and not args.no_cpu_baseline:
-        section("cpu_baseline", lambda: cpu_baseline(src, tgt, vps, vpt))
+        section("cpu_baseline", lambda: cpu_baseline(WORKLOAD, src, tgt, vps, vpt))
     print(json.dumps(line), flush=True)
 
 
@@ -372,65 +421,32 @@ def bench_batched(torch, n_pairs, rank):
                 correspondences=n_corr, same_counts_as_plain=same, autotune=table)
 
 
-def bench_indoor(torch, rank, reps):
-    """The large dense pair: 2M raw points per cloud from the indoor-room
-    generator, voxel 0.02 m (~300k points), full mutual matching of all
-    descriptors.  One pair per step, graph replay, inputs resident in HBM;
-    exact FP32 and BF16 tensor-core + certified FP32 rerank timed on the same
-    pair, with their correspondence sets compared."""
-    from synth import indoor_pair
-
+def bench_register(torch, rank, reps, with_oracle):
+    """Registration after matching, on the device, on the LiDAR scan pair
+    without suppression: kmx_prune (Sec. III-D: ratio filter N_tau = 3000,
+    invariant graph with beta = 1.5 v, max k-core) then kmx_gnc (Sec. III-E:
+    GNC-TLS), on the pair's correspondences resident in HBM.  Median device
+    time of each call and of both (CUDA events), the pose errors against the
+    generator's ground truth, and beside it, once, the oracle's same two
+    stages on the same input."""
     from paper_2409_15615_gb300 import kmx, pipeline
 
-    src, tgt, R, t, vps, vpt = indoor_pair(31 + rank)
-    v = 0.02
-    ctx = kmx.Context(0)
+    src, tgt, vps, vpt, R_gt, t_gt = make_pair(LIDAR, rank)
+    voxel = LIDAR["voxel"]
+    ctx = kmx.Context(torch.cuda.current_device(), torch.cuda.current_stream())
     pair = pipeline.PairState(ctx, len(src), len(tgt))
     pair.src.raw.copy_(torch.from_numpy(src).cuda())
     pair.tgt.raw.copy_(torch.from_numpy(tgt).cuda())
-    ps = kmx.params_default(v, viewpoint=np.float32(vps).tolist())
-    pt = kmx.params_default(v, viewpoint=np.float32(vpt).tolist())
-    out = dict(raw_points=[len(src), len(tgt)])
-    stream = torch.cuda.current_stream()
-    sets = {}
-    for mode, name in ((kmx.MATCH_FP32_EXACT, "fp32_exact"), (kmx.MATCH_BF16_RERANK, "bf16_certified")):
-        pair.run_checked(len(src), len(tgt), ps, pt, mode)
-        graph = pair.capture(len(src), len(tgt), ps, pt, mode)
-        graph.replay()
-        torch.cuda.synchronize()
-        ts = []
-        for _ in range(reps):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            graph.replay()
-            b.record(stream)
-            b.synchronize()
-            ts.append(a.elapsed_time(b))
-        pair.sync()
-        n = int(pair.n_corr.item())
-        sets[name] = pair.corr[:n].cpu().numpy()
-        out[name] = dict(ms_per_pair=float(np.median(ts)), pairs_per_s=1e3 / float(np.median(ts)), correspondences=n)
-        del graph
-    # feature stages alone (both clouds, graph replay) give the match share
-    out["voxelised"] = [int(pair.src.n_vox.item()), int(pair.tgt.n_vox.item())]
-    out["descriptors"] = [int(pair.src.out["n_valid"].item()), int(pair.tgt.out["n_valid"].item())]
-    np_, nq_ = out["descriptors"]
-    fp = out["fp32_exact"]["ms_per_pair"]
-    out["points_per_s"] = (out["voxelised"][0] + out["voxelised"][1]) / (fp / 1e3)
-    out["identical_sets"] = bool(np.array_equal(sets["fp32_exact"], sets["bf16_certified"]))
-    out["match_flops_dense"] = 3.0 * np_ * nq_ * 33
-    pair.close()
-    ctx.close()
-    return out
+    pair.run_checked(len(src), len(tgt), kmx.params_default(voxel, viewpoint=np.float32(vps).tolist()),
+                     kmx.params_default(voxel, viewpoint=np.float32(vpt).tolist()), kmx.MATCH_FP32_EXACT)
+    try:
+        return _register(torch, ctx, pair, voxel, R_gt, t_gt, reps, with_oracle)
+    finally:
+        pair.close()
+        ctx.close()
 
 
-def bench_register(torch, ctx, pair, voxel, R_gt, t_gt, reps, with_oracle):
-    """Registration after matching, on the device: kmx_prune (Sec. III-D:
-    ratio filter N_tau = 3000, invariant graph with beta = 1.5 v, max k-core)
-    then kmx_gnc (Sec. III-E: GNC-TLS), on the pair's correspondences resident
-    in HBM.  Median device time of each call and of both (CUDA events), the
-    pose errors against the generator's ground truth, and beside it, once,
-    the oracle's same two stages on the same input."""
+def _register(torch, ctx, pair, voxel, R_gt, t_gt, reps, with_oracle):
     from oracle import registration as reg
 
     n_corr = int(pair.n_corr.item())
@@ -492,8 +508,8 @@ def bench_suppressed(torch, rank, steps, warmup):
     from oracle import registration as reg
     from paper_2409_15615_gb300 import kmx, pipeline, replicas
 
-    src, tgt, R, t, vps, vpt = lidar_pair(replicas.pair_seed(WORKLOAD["seed"], rank), az_bins=WORKLOAD["az_bins"])
-    v = WORKLOAD["voxel"]
+    src, tgt, R, t, vps, vpt = lidar_pair(replicas.pair_seed(LIDAR["seed"], rank), az_bins=LIDAR["az_bins"])
+    v = LIDAR["voxel"]
     ctx = kmx.Context(torch.cuda.current_device(), torch.cuda.current_stream())
     pair = pipeline.PairState(ctx, len(src), len(tgt))
     gp = kmx.ground_params_default()
@@ -578,8 +594,8 @@ def bench_ablation(torch, rank, reps):
     from paper_2409_15615_gb300 import replicas
     from synth import scene_pair
 
-    seed = replicas.pair_seed(WORKLOAD["seed"], rank)
-    cases = [("lidar_64beam_2048az_v0.3", lidar_pair(seed, az_bins=WORKLOAD["az_bins"]), 0.3),
+    seed = replicas.pair_seed(LIDAR["seed"], rank)
+    cases = [("lidar_64beam_2048az_v0.3", lidar_pair(seed, az_bins=LIDAR["az_bins"]), 0.3),
              ("scene_20k_v0.1", scene_pair(seed, n=20000), 0.1)]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     out = {}
@@ -640,8 +656,11 @@ def bench_serving(torch, n_req, rates, rank, n_maps=32):
     """Poisson request streams against ``n_maps`` device-resident maps (raw
     size log-uniform in [100k, 1M], LiDAR and indoor generators, voxelised
     and described once), query scans log-uniform in [5k, 300k] raw points
-    drawn from a pool of 64; HBM admission budget 60 GB; p50 / p99 latency
-    and completed pairs/s per rate."""
+    drawn from a pool of 64; admission by measured free HBM within a 60 GB
+    budget; p50 / p99 latency and completed pairs/s per rate.  Beside it, the
+    same request mix served one request at a time (one slot, all arrived at
+    t = 0: the plain path's throughput) and with all slots (all arrived at
+    t = 0: the loop's saturated throughput)."""
     from synth.scenes import map_cloud, query_scan
 
     from paper_2409_15615_gb300 import kmx, serve
@@ -657,23 +676,44 @@ def bench_serving(torch, n_req, rates, rank, n_maps=32):
     for k in range(64):
         n = int(round(np.exp(rng.uniform(np.log(5000), np.log(300000)))))
         pool.append(query_scan(int(rng.integers(1 << 30)), n))
+
+    def mix(rate, seed):
+        arr = serve.poisson_arrivals(rate, n_req, seed=seed)
+        r2 = np.random.default_rng(seed)
+        out = []
+        for i in range(n_req):
+            q, vpq = pool[int(r2.integers(len(pool)))]
+            m = int(r2.integers(len(maps)))
+            out.append(serve.Request(i, m, q, maps[m].voxel, tuple(vpq), float(arr[i])))
+        return out
+
+    srv = serve.Server(maps, slots=8)
+    srv.run(mix(1000.0, 1)[:32], realtime=False)  # warm the slots' scratch
     out = []
     for rate in rates:
-        arr = serve.poisson_arrivals(rate, n_req, seed=int(rate) + rank)
-        reqs = []
-        for i in range(n_req):
-            q, vpq = pool[int(rng.integers(len(pool)))]
-            m = int(rng.integers(len(maps)))
-            reqs.append(serve.Request(i, m, q, maps[m].voxel, tuple(vpq), float(arr[i])))
-        srv = serve.Server(maps, slots=8)
-        done = srv.run(reqs, realtime=True)
+        srv.stats = dict(admitted=0, held_by_memory=0, peak_in_use=0)
+        done = srv.run(mix(rate, int(rate) + rank), realtime=True)
         st = serve.latency_stats(done)
         st["rate_req_s"] = rate
+        st["held_by_memory"] = srv.stats["held_by_memory"]
+        st["peak_admitted_gb"] = srv.stats["peak_in_use"] / 2 ** 30
         out.append(st)
+    sat_mix = mix(2000.0, 99 + rank)
+    t0 = time.perf_counter()
+    srv.run(sat_mix, realtime=False)
+    sat = n_req / (time.perf_counter() - t0)
+    plain = serve.Server(maps, slots=1)
+    plain.run(sat_mix[:16], realtime=False)
+    t0 = time.perf_counter()
+    plain.run(sat_mix, realtime=False)
+    plain_ps = n_req / (time.perf_counter() - t0)
     resident = [int(len(m.desc)) for m in maps]
     ctx.close()
-    return dict(requests_per_rate=n_req, slots=8, budget_gb=60, maps=len(maps),
-                map_descriptors=dict(min=min(resident), max=max(resident), total=sum(resident)), per_rate=out)
+    return dict(requests_per_rate=n_req, slots=8, budget_gb=60, admission="measured free HBM (cudaMemGetInfo + "
+                "unused cached blocks) less a 2 GB reserve, within the budget", maps=len(maps),
+                map_descriptors=dict(min=min(resident), max=max(resident), total=sum(resident)), per_rate=out,
+                saturated_pairs_per_s=sat, plain_one_at_a_time_pairs_per_s=plain_ps,
+                speedup_vs_plain=sat / plain_ps)
 
 
 def stage_times(torch, ctx, pair, n_src, n_tgt, ps, pt, mode, flush, reps):
@@ -718,10 +758,10 @@ def stage_times(torch, ctx, pair, n_src, n_tgt, ps, pt, mode, flush, reps):
 
 def executed_dims(P, Q, tile=128):
     """Mean number of the 33 dimensions the exact matcher visits per tile
-    pair: rows grouped by nonzero mask (masks ordered with dimension 0 most
-    significant), 128-row tiles, a dimension visited when any row of either
-    tile is nonzero there.  Rows with one mask are interchangeable, so this
-    reproduces the kernel's tile masks exactly."""
+    pair: rows grouped by nonzero mask (masks ordered with dimension 0 as the
+    most significant bit), 128-row tiles, a dimension visited when any row
+    of either tile is nonzero there.  Rows with one mask are
+    interchangeable, so this reproduces the kernel's tile masks exactly."""
     def tile_masks(X):
         nz = X != 0
         bits = (nz.astype(np.uint64) << np.arange(33, dtype=np.uint64)).sum(1)
@@ -732,12 +772,14 @@ def executed_dims(P, Q, tile=128):
         n_t = (len(X) + tile - 1) // tile
         return np.array([np.bitwise_or.reduce(srt[t * tile:(t + 1) * tile]) for t in range(n_t)], np.uint64)
     mp, mq = tile_masks(P), tile_masks(Q)
-    pop = np.vectorize(lambda v: bin(int(v)).count("1"))
-    both = mp[:, None] | mq[None, :]
-    return float(pop(both).mean())
+    total = 0
+    for a in range(0, len(mp), 256):  # popcount of the OR, in blocks
+        both = mp[a:a + 256, None] | mq[None, :]
+        total += int(np.unpackbits(both.view(np.uint8)).sum())
+    return float(total) / max(len(mp) * len(mq), 1)
 
 
-def algorithmic_work(pair, ctx):
+def algorithmic_work(pair, ctx, mode):
     """Counts that define the algorithmic bytes / flops of each stage."""
     out = {}
     for side, cs in (("src", pair.src), ("tgt", pair.tgt)):
@@ -753,9 +795,10 @@ def algorithmic_work(pair, ctx):
         nJ = int(cs.out["n_valid"].item())
         out[side] = dict(n=n, sum_mF=int(mF.sum()), n_B=int(B.sum()), sum_mV_B=int(mV[B].sum()),
                          sum_mV_J=int(mV[(flags & 2) > 0].sum()), n_J=nJ, n_raw=int(cs.raw.shape[0]))
-    out["match"] = dict(np=out["src"]["n_J"], nq=out["tgt"]["n_J"],
-                        executed_dims=executed_dims(pair.src.out["desc"][: out["src"]["n_J"], :33].cpu().numpy(),
-                                                    pair.tgt.out["desc"][: out["tgt"]["n_J"], :33].cpu().numpy()))
+    out["match"] = dict(np=out["src"]["n_J"], nq=out["tgt"]["n_J"])
+    if mode == 0:
+        out["match"]["executed_dims"] = executed_dims(pair.src.out["desc"][: out["src"]["n_J"], :33].cpu().numpy(),
+                                                      pair.tgt.out["desc"][: out["tgt"]["n_J"], :33].cpu().numpy())
     return out
 
 
@@ -786,6 +829,11 @@ def stage_roofline(stages, work):
 
 
 def roofline(stages, work, mode):
+    """The dominant stage of the step against its roofline.  Matching counts
+    the algorithmic 2 |J_P| |J_Q| 33 flops (one multiply-add per descriptor
+    value of every pair of rows) over the whole kmx_match call (both
+    directions, re-ranking and emission included); a feature stage counts
+    its algorithmic bytes (stage_bytes)."""
     peaks = measured_peaks()
     best = None
     for side in ("src", "tgt"):
@@ -797,28 +845,25 @@ def roofline(stages, work, mode):
     m = work["match"]
     match_ms = stages["match"]
     if match_ms > best[1]:
-        if mode == 0:
-            flops = 3.0 * m["np"] * m["nq"] * 33
-            achieved = flops / (match_ms / 1000.0) / 1e12
-            peak = peaks["fp32_tflops"]
-            executed = achieved * m["executed_dims"] / 33.0
-            return dict(kernel="match_tiles_fp32_bulk (kmx_match, FP32 exact)", bound="alu", achieved=achieved,
-                        peak=peak, unit="TFLOP/s", frac=achieved / peak,
-                        traffic=PROFILED_TRAFFIC.get("match_tiles_fp32_bulk"),
-                        executed_dims_per_tile_pair=m["executed_dims"], executed_tflops=executed,
-                        executed_frac=executed / peak,
-                        note="achieved counts the algorithmic 3 flops (sub + fma) for all 33 values of every "
-                             "descriptor pair; the kernel skips dimensions that are zero across a whole 128 x 128 "
-                             "tile pair (exact), so it executes executed_dims_per_tile_pair / 33 of them "
-                             "(executed_tflops); duration = the whole kmx_match call (sort, pack, tiles, merge, "
-                             "emit) from CUDA events; peak = 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived, no "
-                             "measured FP32 peak); traffic = DRAM read+write bytes of one launch from ncu "
-                             "(profiles/match_tiles_fp32_bulk_lidar_pair.md)")
         flops = 2.0 * m["np"] * m["nq"] * 33
         achieved = flops / (match_ms / 1000.0) / 1e12
-        peak = peaks["bf16_tflops"]
-        return dict(kernel="kmx_match (BF16 tcgen05 + rerank)", bound="tensor", achieved=achieved, peak=peak,
-                    unit="TFLOP/s", frac=achieved / peak, traffic=None)
+        if mode == 0:
+            peak = peaks["fp32_tflops"]
+            return dict(kernel="kmx_match, exact FP32 (match_tiles_fp32_bulk)", bound="alu", achieved=achieved,
+                        peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                        traffic=PROFILED_TRAFFIC.get("match_tiles_fp32_bulk"), algorithmic_flops=flops,
+                        ms=match_ms, executed_dims_per_tile_pair=m.get("executed_dims"),
+                        note="duration = the whole kmx_match call from CUDA events; peak = 152 SMs x 128 FP32 "
+                             "lanes x 2 flop x 2.07 GHz (derived from unit counts and the maximum clock)")
+        peak = peaks["bf16_tflops_sustained"]
+        return dict(kernel="kmx_match, BF16 tcgen05 candidates both ways + exact FP32 rerank (tc_collect)",
+                    bound="tensor", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                    frac_of_burst=achieved / peaks["bf16_tflops"], traffic=PROFILED_TRAFFIC.get("tc_collect"),
+                    algorithmic_flops=flops, ms=match_ms,
+                    note="duration = the whole kmx_match call from CUDA events (two tc_collect launches, sort, "
+                         "pack, rerank, emission); peak = measured sustained dense BF16 (MEASURED_PEAKS.json), "
+                         "frac_of_burst against the burst figure; the kernel issues 2 x 48/33 of the "
+                         "algorithmic flops (both directions, K padded to 48)")
     name, ms, by = best
     achieved = by / (ms / 1000.0) / 1e9
     return dict(kernel=name, bound="hbm", achieved=achieved, peak=peaks["hbm_gbs"], unit="GB/s",
@@ -826,33 +871,31 @@ def roofline(stages, work, mode):
 
 
 def measured_peaks():
-    p = dict(hbm_gbs=6800.0, bf16_tflops=1900.0, source="fallback")
+    p = dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0, source="fallback")
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             m = json.load(f)
-        p = dict(hbm_gbs=float(m["hbm_gbs"]), bf16_tflops=float(m["bf16_tflops"]), source="measured")
+        p = dict(hbm_gbs=float(m["hbm_gbs"]), bf16_tflops=float(m["bf16_tflops"]),
+                 bf16_tflops_sustained=float(m.get("bf16_tflops_sustained", m["bf16_tflops"])), source="measured")
     except (OSError, KeyError, ValueError):
         pass
     p["fp32_tflops"] = 152 * 128 * 2 * 2.07e9 / 1e12
     return p
 
 
-E2E_SLOTS = 4
-
-
-def end_to_end(torch, ctx, pair, src, tgt, ps, pt, mode, flush, steps, world):
+def end_to_end(torch, ctx, pair, src, tgt, ps, pt, mode, steps, world, slots, reduce=True):
     """The same pairs through the public streaming API (pipeline.PairStream)
     from pinned host buffers: every pair's H2D upload of both raw clouds and
     D2H download of its correspondences (the whole [cap, 4] buffer and the
     count) are inside the timed region; uploads and downloads overlap the
-    kernels, and four pairs are in flight on four compute streams (four
-    slots, graph replay; more slots measured no faster).  Timed with CUDA events from the first upload to the last
+    kernels, and ``slots`` pairs are in flight on as many compute streams
+    (graph replay).  Timed with CUDA events from the first upload to the last
     download; each pair's inputs arrive by copy, so no L2 flush is added."""
     from paper_2409_15615_gb300 import pipeline, replicas
 
     h_src = torch.from_numpy(src).pin_memory()
     h_tgt = torch.from_numpy(tgt).pin_memory()
-    stream_ = pipeline.PairStream(ctx, len(src), len(tgt), slots=E2E_SLOTS)
+    stream_ = pipeline.PairStream(ctx, len(src), len(tgt), slots=slots)
     stream_.prepare(len(src), len(tgt), ps, pt, mode)
     h_corr = torch.empty(stream_.slots[0].corr.shape, dtype=torch.int32).pin_memory()
     h_n = torch.empty(1, dtype=torch.int64).pin_memory()
@@ -865,12 +908,12 @@ def end_to_end(torch, ctx, pair, src, tgt, ps, pt, mode, flush, steps, world):
     lat = [a.elapsed_time(b) for a, b in ev]
     n_corr = int(h_n[0])
     stream_.close()
-    total = replicas.max_over_ranks(total_ms, device="cuda")
+    total = replicas.max_over_ranks(total_ms, device="cuda") if reduce else total_ms
     return dict(value=world * steps / (total / 1000.0), unit="pairs/s",
                 h2d_bytes_per_step=int(src.nbytes + tgt.nbytes),
                 d2h_bytes_per_step=int(h_corr.numel() * 4 + 8),
                 p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
-                correspondences=n_corr, overlapped=True, pairs_in_flight=E2E_SLOTS)
+                correspondences=n_corr, overlapped=True, pairs_in_flight=slots)
 
 
 def count_launches(torch, step):

@@ -109,7 +109,7 @@ typedef enum {
      * candidate list that provably holds every column whose exact distance is
      * at most the row's second-smallest one (certified lower and upper
      * bounds); the candidates are re-ranked exactly in FP32, and a row whose
-     * list overflows (256) goes through the exact FP32 tiles.  The result
+     * list overflows (512) goes through the exact FP32 tiles.  The result
      * equals KMX_MATCH_FP32_EXACT's, including KMX_ERANGE for NaN or
      * infinite values. */
     KMX_MATCH_BF16_RERANK = 1

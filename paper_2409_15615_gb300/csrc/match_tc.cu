@@ -81,22 +81,23 @@ using kmx::mbar_wait;
 using kmx::smem_u32;
 
 constexpr int kTM = 128;                      // rows per tile (UMMA M)
-constexpr int kTN = 128;                      // columns per tile (UMMA N)
+constexpr int kTN = 256;                      // columns per column tile (UMMA N)
 constexpr int kK = 48;                        // 33 values + 3 slots, padded to 3 x 16
-constexpr int kOpBytes = kTM * kK * 2;        // one BF16 operand tile: 12288
+constexpr int kOpBytesA = kTM * kK * 2;       // one BF16 row tile: 12288
+constexpr int kOpBytesB = kTN * kK * 2;       // one BF16 column tile: 24576
 constexpr int kCoreStride = 128;              // LBO: next 8-element K chunk
 constexpr int kGroupStride = 6 * 128;         // SBO: next 8-row group
 constexpr int kCenterStride = 36;             // floats per stored centre
 // packed column tile: operand, then |b| per row, the centre, max |b|^2
-constexpr int kHdrBeta = kOpBytes;
+constexpr int kHdrBeta = kOpBytesB;
 constexpr int kHdrCenter = kHdrBeta + kTN * 4;
 constexpr int kHdrBmax = kHdrCenter + kCenterStride * 4;
-constexpr int kColBytes = kHdrBmax + 16;      // 12960, a multiple of 16
-constexpr int kStages = 3;                    // column-tile ring
-constexpr int kThreads = 128;
-constexpr int kTmemCols = 256;                // two 128-column FP32 accumulators
+constexpr int kColBytes = kHdrBmax + 16;      // 25760, a multiple of 16
+constexpr int kStages = 4;                    // column-tile ring
+constexpr int kThreads = 512;                 // 16 warps: four per TMEM lane quarter
+constexpr int kTmemCols = 512;                // two 256-column FP32 accumulators
 constexpr int kMaxChunks = 8;
-constexpr int kCandCap = 256;                 // candidate list per row
+constexpr int kCandCap = 512;                 // candidate list per row
 constexpr float kC = 0.008f;                  // c' of the bounds
 constexpr float kSqrtC = 0.08944271909999159f;
 constexpr float kUpper = 4.1f * kC;
@@ -182,8 +183,19 @@ __device__ __forceinline__ float fmax3(float a, float b, float c)
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
 {
-    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
-           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);  // .x = lo (low half), .y = hi
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// Write 8 operand values (one 16-byte core-matrix row) at chunk c of row r.
+__device__ __forceinline__ void store_operand_chunk(uint8_t* tile, int r, int c, const float* v)
+{
+    uint4 w;
+    w.x = pack_bf16x2(v[0], v[1]);
+    w.y = pack_bf16x2(v[2], v[3]);
+    w.z = pack_bf16x2(v[4], v[5]);
+    w.w = pack_bf16x2(v[6], v[7]);
+    *reinterpret_cast<uint4*>(tile + (r / 8) * kGroupStride + (r % 8) * 16 + c * kCoreStride) = w;
 }
 
 // Write one 48-value operand row (values v[0..47]) at row r of a tile in the
@@ -309,24 +321,24 @@ __global__ void __launch_bounds__(256) tc_keys(int64_t np_cap, const int64_t* d_
 }
 
 // ---------------------------------------------------------------------------
-// pack: one CTA of 128 threads per tile of one cloud
+// pack: one CTA of 256 threads per column tile of one cloud
 // ---------------------------------------------------------------------------
 
-// Rows of the tile are sorted positions [128 t, 128 t + 128) of the cloud;
+// Rows of the tile are sorted positions [256 t, 256 t + 256) of the cloud;
 // perm maps a sorted position to the descriptor row.  Writes the packed
 // column tile and the centre (also to centers[t]).
-__global__ void __launch_bounds__(kTM) tc_pack(const float* __restrict__ desc, const int32_t* __restrict__ perm,
+__global__ void __launch_bounds__(kTN) tc_pack(const float* __restrict__ desc, const int32_t* __restrict__ perm,
                                                int64_t n_cap, const int64_t* d_n, uint8_t* __restrict__ out,
                                                float* __restrict__ centers)
 {
-    __shared__ float rows_s[kTM][KMX_DESC_DIM + 1];
+    __shared__ float rows_s[kTN][KMX_DESC_DIM + 1];
     __shared__ float cen[kCenterStride];
     __shared__ unsigned int bmax2;
     const int64_t n = kmx_count(d_n, n_cap);
     const int64_t t = blockIdx.x;
-    if (t * kTM >= n && !(t == 0)) return;  // tiles past the count are never read
+    if (t * kTN >= n && !(t == 0)) return;  // tiles past the count are never read
     const int tid = threadIdx.x;
-    const int64_t r = t * kTM + tid;
+    const int64_t r = t * kTN + tid;
     const bool valid = r < n;
     float y[KMX_DESC_DIM];
     if (valid) {
@@ -341,21 +353,21 @@ __global__ void __launch_bounds__(kTM) tc_pack(const float* __restrict__ desc, c
     for (int h = 0; h < KMX_DESC_DIM; ++h) rows_s[tid][h] = y[h];
     if (tid == 0) bmax2 = 0u;
     __syncthreads();
-    const int cnt = (int)max((int64_t)0, min((int64_t)kTM, n - t * kTM));
+    const int cnt = (int)max((int64_t)0, min((int64_t)kTN, n - t * kTN));
     if (tid < kCenterStride) {
-        float s = 0.f;
+        float sum = 0.f;
         if (tid < KMX_DESC_DIM)
-            for (int i = 0; i < cnt; ++i) s += rows_s[i][tid];
-        cen[tid] = (tid < KMX_DESC_DIM && cnt > 0) ? s / (float)cnt : 0.f;
+            for (int i = 0; i < cnt; ++i) sum += rows_s[i][tid];
+        cen[tid] = (tid < KMX_DESC_DIM && cnt > 0) ? sum / (float)cnt : 0.f;
     }
     __syncthreads();
     float v[kK];
     float nb = 0.f;
 #pragma unroll
     for (int h = 0; h < KMX_DESC_DIM; ++h) {
-        const float b = y[h] - cen[h];
-        v[h] = b;
-        nb = fmaf(b, b, nb);
+        const float bv = y[h] - cen[h];
+        v[h] = bv;
+        nb = fmaf(bv, bv, nb);
     }
     const float beta = sqrtf(nb);
 #pragma unroll
@@ -382,15 +394,16 @@ __global__ void __launch_bounds__(kTM) tc_pack(const float* __restrict__ desc, c
     if (tid < 4) reinterpret_cast<float*>(tile + kHdrBmax)[tid] = tid == 0 ? __uint_as_float(bmax2) : 0.f;
 }
 
-// For each row tile of X: the column tile of Y with the nearest centre (ties
-// to the lower tile).  One warp per row tile.
+// For each column tile of X (256 rows; row tile T of X lies in tile T / 2):
+// the column tile of Y with the nearest centre (ties to the lower tile).
+// One warp per tile.
 __global__ void __launch_bounds__(256) tc_nearest(const float* __restrict__ cx, int64_t nx_cap, const int64_t* d_nx,
                                                   const float* __restrict__ cy, int64_t ny_cap, const int64_t* d_ny,
                                                   int32_t* __restrict__ nearest)
 {
     const int lane = threadIdx.x & 31;
     const int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    const int64_t ntx = (kmx_count(d_nx, nx_cap) + kTM - 1) / kTM;
+    const int64_t ntx = (kmx_count(d_nx, nx_cap) + kTN - 1) / kTN;
     const int64_t nty = (kmx_count(d_ny, ny_cap) + kTN - 1) / kTN;
     if (t >= ntx) return;
     float c[KMX_DESC_DIM];
@@ -427,12 +440,27 @@ __global__ void __launch_bounds__(256) tc_nearest(const float* __restrict__ cx, 
 // ---------------------------------------------------------------------------
 
 struct TcShared {
-    uint8_t a[2][kOpBytes];
+    uint8_t a[2][kOpBytesA];
     uint8_t b[kStages][kColBytes];
+    float r2[3][kTM];  // |x - c|^2 of every row, by step modulo 3 (written one step ahead of its reads,
+                       // while the slowest thread may still read the previous step's)
     uint64_t bar_b[kStages], bar_mma[2];
     uint32_t tmem;
 };
 
+// Threads (16 warps) have two roles per step (one 256-column tile):
+//   re-centring  thread t writes values 8 (t & 3) .. + 7 of row t >> 2 of
+//                the A operand (the t & 3 == 3 thread also value 32 and the
+//                three slots); the four threads of a row are neighbouring
+//                lanes and add their partial |x - c|^2 with two shuffles;
+//   epilogue     warp w reads TMEM lanes (rows) 32 (w & 3) .. + 31 and
+//                accumulator columns 64 (w >> 2) .. + 63.  The four threads
+//                of a row keep their own bounds and candidate decisions over
+//                their own columns (disjoint sets, one list per row).
+// One CTA per SM (its TMEM allocation is all 512 columns).  One barrier per
+// step: it publishes the A operand to the MMA and orders the previous
+// step's accumulator reads before the next MMA into that accumulator.
+//
 // The grid is sized from the capacities; the (row tile, column chunk) split
 // of the actual counts is decided here (kmx::work_chunks).
 __global__ void __launch_bounds__(kThreads, 1) tc_collect(const float* __restrict__ X,
@@ -445,7 +473,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_collect(const float* __restric
 {
     extern __shared__ uint8_t smem_raw[];
     TcShared& S = *reinterpret_cast<TcShared*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t rows = kmx_count(d_nx, nx_cap), cols = kmx_count(d_ny, ny_cap);
     const int64_t n_rt = (rows + kTM - 1) / kTM;
     const int64_t n_ct = (cols + kTN - 1) / kTN;
@@ -459,38 +487,48 @@ __global__ void __launch_bounds__(kThreads, 1) tc_collect(const float* __restric
     if (T == 0) return;
     // the sequence of column tiles: the nearest tile first, then the chunk
     // (without the nearest tile when it lies inside the chunk)
-    const int64_t cs = nearest[rt];
+    const int64_t cs = nearest[rt >> 1];
     const bool cs_in = cs >= t0 && cs < t0 + T;
     const int nseq = T + (cs_in ? 0 : 1);
     auto tile_of = [&](int s) -> int64_t {
         if (s == 0) return cs;
-        const int64_t r = t0 + s - 1;
-        return (cs_in && r >= cs) ? r + 1 : r;
+        const int64_t rr = t0 + s - 1;
+        return (cs_in && rr >= cs) ? rr + 1 : rr;
     };
     const uint32_t idesc = idesc_bf16(kTM, kTN);
 
+    // re-centring role
+    const int rrow = tid >> 2, part = tid & 3;
+    const int64_t xrow = rt * kTM + rrow;
+    const bool xvalid = xrow < rows;
+    // epilogue role
+    const int quarter = warp & 3, slice = warp >> 2;
+    const int r = quarter * 32 + lane;
+    const int64_t row = rt * kTM + r;
+    const bool row_valid = row < rows;
+
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(&S.bar_b[s], 1);
+        for (int st = 0; st < kStages; ++st) mbar_init(&S.bar_b[st], 1);
         mbar_init(&S.bar_mma[0], 1);
         mbar_init(&S.bar_mma[1], 1);
         mbar_fence_init();
     }
     if (warp == 0) tmem_alloc(&S.tmem, kTmemCols);
+    if (part == 3) {  // the last K chunk (values 40..47) is zero in every A operand
+        const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        store_operand_chunk(S.a[0], rrow, 5, z);
+        store_operand_chunk(S.a[1], rrow, 5, z);
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = S.tmem;
 
-    const int64_t row = rt * kTM + tid;
-    const bool row_valid = row < rows;
-    float x[KMX_DESC_DIM];
-    if (row_valid) {
-        const float* xr = X + (int64_t)permX[row] * KMX_DESC_STRIDE;
+    float x[9];  // values 8 part .. 8 part + 7 (and 32 for part 3) of this thread's re-centring row
+    {
+        const float* xr = xvalid ? X + (int64_t)permX[xrow] * KMX_DESC_STRIDE + 8 * part : nullptr;
 #pragma unroll
-        for (int h = 0; h < KMX_DESC_DIM; ++h) x[h] = __ldg(xr + h);
-    } else {
-#pragma unroll
-        for (int h = 0; h < KMX_DESC_DIM; ++h) x[h] = 0.f;
+        for (int h = 0; h < 9; ++h) x[h] = (xvalid && (h < 8 || part == 3)) ? __ldg(xr + h) : 0.f;
     }
 
     int issued_b = 0, issued_mma = 0;
@@ -502,43 +540,49 @@ __global__ void __launch_bounds__(kThreads, 1) tc_collect(const float* __restric
     }
     bool fail = false, failed = false;
     float U1 = FLT_MAX, U2 = FLT_MAX;
-    float rb_cur = 0.f, al_cur = 0.f, ef_cur = 0.f;  // tile s: |a|^2 - e, |a|, e
-    float rb_prev = 0.f, al_prev = 0.f, ef_prev = 0.f;
 
     for (int s = 0; s <= nseq; ++s) {
-        rb_prev = rb_cur;
-        al_prev = al_cur;
-        ef_prev = ef_cur;
         if (s < nseq) {
-            // ---- A operand of tile pair s: the row re-centred on the column tile's centre
+            // ---- A operand of step s: rows re-centred on the column tile's centre
             if (!mbar_wait(&S.bar_b[s % kStages], (s / kStages) & 1)) fail = true;
             const uint8_t* bt = S.b[s % kStages];
-            const float* cen = reinterpret_cast<const float*>(bt + kHdrCenter);
-            const float bmax2 = reinterpret_cast<const float*>(bt + kHdrBmax)[0];
-            float v[kK];
-            float r2 = 0.f;
+            const float4* cen4 = reinterpret_cast<const float4*>(bt + kHdrCenter) + 2 * part;
+            const float4 c0 = cen4[0], c1 = cen4[1];
+            const float cc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+            float av[8];
+            float p2 = 0.f;
 #pragma unroll
-            for (int h = 0; h < KMX_DESC_DIM; ++h) {
-                const float a = x[h] - cen[h];
-                v[h] = a;
-                r2 = fmaf(a, a, r2);
+            for (int h = 0; h < 8; ++h) {
+                av[h] = x[h] - cc[h];
+                p2 = fmaf(av[h], av[h], p2);
             }
-            const float al = sqrtf(r2);
-            v[KMX_DESC_DIM] = kSqrtC * al;
-            v[KMX_DESC_DIM + 1] = -0.5f;
-            v[KMX_DESC_DIM + 2] = -0.5f;
-#pragma unroll
-            for (int h = KMX_DESC_DIM + 3; h < kK; ++h) v[h] = 0.f;
-            store_operand_row(S.a[s & 1], tid, v);
-            ef_cur = kEfp * (r2 + bmax2);
-            rb_cur = r2 - ef_cur;
-            al_cur = al;
+            float a32 = 0.f;
+            if (part == 3) {
+                a32 = x[8] - reinterpret_cast<const float*>(bt + kHdrCenter)[32];
+                p2 = fmaf(a32, a32, p2);
+            }
+            uint8_t* at = S.a[s & 1];
+            store_operand_chunk(at, rrow, part, av);
+            // the four partial sums of the row (neighbouring lanes); each
+            // lane forms the same total
+            p2 += __shfl_xor_sync(0xffffffffu, p2, 1);
+            p2 += __shfl_xor_sync(0xffffffffu, p2, 2);
+            if (part == 3) {
+                const float v4[8] = {a32, kSqrtC * sqrtf(p2), -0.5f, -0.5f, 0.f, 0.f, 0.f, 0.f};
+                store_operand_chunk(at, rrow, 4, v4);
+            }
+            if (part == 0) S.r2[s % 3][rrow] = p2;
             fence_proxy_async();
-            tc_fence_before();
-            failed = __syncthreads_or(fail) != 0;
-            tc_fence_after();
-            if (failed) break;
-            if (tid == 0) {
+        }
+        // publishes the A operand and r2 of step s; every thread has finished
+        // the epilogue of step s - 2 (accumulator (s & 1) is free) and its
+        // reads of the column tile of step s - 2
+        tc_fence_before();
+        failed = __syncthreads_or(fail) != 0;
+        tc_fence_after();
+        if (failed) break;
+        if (tid == 0) {
+            if (s < nseq) {
                 const uint32_t a_base = smem_u32(S.a[s & 1]);
                 const uint32_t b_base = smem_u32(S.b[s % kStages]);
                 const uint32_t d = tmem + (uint32_t)((s & 1) * kTN);
@@ -551,56 +595,69 @@ __global__ void __launch_bounds__(kThreads, 1) tc_collect(const float* __restric
                 umma_commit(&S.bar_mma[s & 1]);
                 ++issued_mma;
             }
+            // the stage of step s - 2 is free: its MMA and its epilogue are done
+            if (s >= 2 && s - 2 + kStages < nseq) {
+                const int st = (s - 2) % kStages;
+                mbar_expect_tx(&S.bar_b[st], kColBytes);
+                bulk_g2s(S.b[st], packY + tile_of(s - 2 + kStages) * (int64_t)kColBytes, kColBytes, &S.bar_b[st]);
+                ++issued_b;
+            }
         }
         if (s >= 1) {
-            // ---- epilogue of tile pair p = s - 1
+            // ---- epilogue of step p = s - 1: this thread's 64 columns
             const int p = s - 1;
             if (!mbar_wait(&S.bar_mma[p & 1], (p >> 1) & 1)) fail = true;
             tc_fence_after();
+            const uint8_t* bt = S.b[p % kStages];
+            const float r2 = S.r2[p % 3][r];
+            const float ef = kEfp * (r2 + reinterpret_cast<const float*>(bt + kHdrBmax)[0]);
+            const float rb = r2 - ef;
+            const float up = kUpper * sqrtf(r2);
             const bool collect = p > 0 || cs_in;
-            const int64_t col0 = tile_of(p) * kTN;
-            const float* beta = reinterpret_cast<const float*>(S.b[p % kStages] + kHdrBeta);
-            const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((p & 1) * kTN);
+            const int64_t col0 = tile_of(p) * kTN + slice * 64;
+            const float* beta = reinterpret_cast<const float*>(bt + kHdrBeta) + slice * 64;
+            const uint32_t lane_addr =
+                tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((p & 1) * kTN + slice * 64);
 #pragma unroll 1
-            for (int c0 = 0; c0 < kTN; c0 += 32) {
+            for (int c0 = 0; c0 < 64; c0 += 32) {
                 float v[32];
                 tmem_ld32(lane_addr + c0, v);
-                float m[11];
 #pragma unroll
-                for (int j = 0; j < 10; ++j) m[j] = fmax3(v[3 * j], v[3 * j + 1], v[3 * j + 2]);
-                m[10] = fmaxf(v[30], v[31]);
-                const float mx = fmax3(fmax3(fmax3(m[0], m[1], m[2]), fmax3(m[3], m[4], m[5]), fmax3(m[6], m[7], m[8])),
-                                       m[9], m[10]);
-                if (row_valid && fmaf(-2.f, mx, rb_prev) <= U2) {
+                for (int g = 0; g < 4; ++g) {
+                    const float* vg = v + 8 * g;
+                    const float m = fmax3(fmax3(vg[0], vg[1], vg[2]), fmax3(vg[3], vg[4], vg[5]), fmaxf(vg[6], vg[7]));
+                    // L = |a|^2 - e - 2 M is monotone in M: the group's largest
+                    // M gives its smallest L
+                    if (row_valid && fmaf(-2.f, m, rb) <= U2) {
+                        unsigned msk = 0;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float L = fmaf(-2.f, v[j], rb_prev);
-                        if (L <= U2) {
-                            if (collect) {
-                                const int pos = atomicAdd(cnt + row, 1);
-                                if (pos < kCandCap) cand[row * kCandCap + pos] = (int32_t)(col0 + c0 + j);
-                            }
-                            const float U = fmaf(kUpper * al_prev, beta[c0 + j], L + 2.f * ef_prev);
-                            if (U < U1) {
-                                U2 = U1;
-                                U1 = U;
-                            } else if (U < U2) {
-                                U2 = U;
+                        for (int j = 0; j < 8; ++j) msk |= (fmaf(-2.f, vg[j], rb) <= U2 ? 1u : 0u) << j;
+                        while (msk) {
+                            const int j = __ffs(msk) - 1;
+                            msk &= msk - 1;
+                            float vj = vg[0];
+#pragma unroll
+                            for (int k = 1; k < 8; ++k) vj = (j == k) ? vg[k] : vj;
+                            const float L = fmaf(-2.f, vj, rb);
+                            if (L <= U2) {  // U2 may have dropped since the mask was taken
+                                const int cj = c0 + 8 * g + j;
+                                if (collect) {
+                                    const int pos = atomicAdd(cnt + row, 1);
+                                    if (pos < kCandCap) cand[row * kCandCap + pos] = (int32_t)(col0 + cj);
+                                }
+                                const float U = fmaf(up, beta[cj], L + 2.f * ef);
+                                if (U < U1) {
+                                    U2 = U1;
+                                    U1 = U;
+                                } else if (U < U2) {
+                                    U2 = U;
+                                }
                             }
                         }
                     }
                 }
             }
             tc_fence_before();
-            failed = __syncthreads_or(fail) != 0;
-            tc_fence_after();
-            if (failed) break;
-            if (tid == 0 && p + kStages < nseq) {  // MMA p and its epilogue are done with the stage
-                const int st = p % kStages;
-                mbar_expect_tx(&S.bar_b[st], kColBytes);
-                bulk_g2s(S.b[st], packY + tile_of(p + kStages) * (int64_t)kColBytes, kColBytes, &S.bar_b[st]);
-                ++issued_b;
-            }
         }
     }
     if (failed) {
@@ -716,10 +773,10 @@ __global__ void __launch_bounds__(256) fallback_merge(const kmx::RowBest* __rest
 
 size_t tc_smem_bytes()
 {
-    // at least 96 KB: at most two CTAs per SM, i.e. two 256-column TMEM
-    // allocations (a third CTA would wait in tcgen05.alloc)
+    // at least 120 KB: one CTA per SM, whose TMEM allocation is all 512
+    // columns (a second CTA would wait in tcgen05.alloc)
     const size_t need = sizeof(TcShared) + 1024;
-    return need < 96 * 1024 ? 96 * 1024 : need;
+    return need < 120 * 1024 ? 120 * 1024 : need;
 }
 
 struct TcBuffers {
@@ -743,7 +800,7 @@ TcBuffers tc_carve(void* base, int64_t np_cap, int64_t nq_cap, size_t* total)
     TcBuffers b{};
     kmx_arena a{static_cast<char*>(base), 0};
     const int64_t n2 = np_cap + nq_cap;
-    const int64_t tp = (np_cap + kTM - 1) / kTM, tq = (nq_cap + kTM - 1) / kTM;
+    const int64_t tp = (np_cap + kTN - 1) / kTN, tq = (nq_cap + kTN - 1) / kTN;  // column tiles
     const int fc = kmx_match_fp32_max_chunks();
     b.coords = (float4*)a.take(sizeof(float4) * (size_t)n2);
     b.range = (unsigned int*)a.take(sizeof(unsigned int) * 8);
@@ -792,7 +849,8 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
     size_t total = 0;
     TcBuffers b = tc_carve(s.extra, np_cap, nq_cap, &total);
     const int64_t n2 = np_cap + nq_cap;
-    const int64_t tp = (np_cap + kTM - 1) / kTM, tq = (nq_cap + kTM - 1) / kTM;
+    const int64_t tp = (np_cap + kTM - 1) / kTM, tq = (nq_cap + kTM - 1) / kTM;    // row tiles
+    const int64_t ctp = (np_cap + kTN - 1) / kTN, ctq = (nq_cap + kTN - 1) / kTN;  // column tiles
     const size_t smem = tc_smem_bytes();
     cudaError_t e = kmx_once_per_device(kmx_attr_tc_topk, [smem] {
         return cudaFuncSetAttribute(tc_collect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -815,13 +873,13 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
     const int32_t* permQ = b.vals + np_cap;
     // packed tiles and centres
     KMX_COUNT_LAUNCH();
-    tc_pack<<<(unsigned)tp, kTM, 0, st>>>(dp, permP, np_cap, d_np, b.packP, b.cenP);
+    tc_pack<<<(unsigned)ctp, kTN, 0, st>>>(dp, permP, np_cap, d_np, b.packP, b.cenP);
     KMX_COUNT_LAUNCH();
-    tc_pack<<<(unsigned)tq, kTM, 0, st>>>(dq, permQ, nq_cap, d_nq, b.packQ, b.cenQ);
+    tc_pack<<<(unsigned)ctq, kTN, 0, st>>>(dq, permQ, nq_cap, d_nq, b.packQ, b.cenQ);
     KMX_COUNT_LAUNCH();
-    tc_nearest<<<kmx_blocks(tp, 8), 256, 0, st>>>(b.cenP, np_cap, d_np, b.cenQ, nq_cap, d_nq, b.nearP);
+    tc_nearest<<<kmx_blocks(ctp, 8), 256, 0, st>>>(b.cenP, np_cap, d_np, b.cenQ, nq_cap, d_nq, b.nearP);
     KMX_COUNT_LAUNCH();
-    tc_nearest<<<kmx_blocks(tq, 8), 256, 0, st>>>(b.cenQ, nq_cap, d_nq, b.cenP, np_cap, d_np, b.nearQ);
+    tc_nearest<<<kmx_blocks(ctq, 8), 256, 0, st>>>(b.cenQ, nq_cap, d_nq, b.cenP, np_cap, d_np, b.nearQ);
     // candidates both ways
     const int target = 2 * ctx->sm_count;
     KMX_COUNT_LAUNCH();

@@ -4,11 +4,16 @@ device-resident maps.
 Each map cloud is voxelised, gridded and described once (Faster-PFH, Sec.
 III-C); its descriptors and valid set J stay resident in HBM.  A request is a
 query scan to be matched against one map.  Requests arrive over time; the loop
-admits an arrived request as soon as a slot is free and the HBM it needs fits
-in the budget, runs it on that slot's stream (so requests in flight overlap on
-the device), and retires it when its completion event has fired.  A slot is a
-stream plus a kmx context (its own scratch); a request's device buffers are
-taken from PyTorch's caching allocator and released when it retires.
+admits an arrived request as soon as a slot is free and the device has the
+memory it needs: the request's estimated footprint must fit both in the free
+HBM measured at that moment (cudaMemGetInfo, plus what PyTorch's caching
+allocator holds unused), less a reserve, and in the loop's budget (60 GB by
+default).  It runs on that slot's stream (so requests in flight overlap on the
+device) and retires when its completion event has fired.  A slot is a stream
+plus a kmx context (its own scratch); a request's device buffers are taken
+from PyTorch's caching allocator and released when it retires.  When nothing
+can be retired or admitted the loop sleeps until the next arrival (at most
+0.2 ms) instead of spinning.
 
 Latency of a request = completion time observed on the host - arrival time.
 The loop reports p50 / p99 latency and completed pairs per second.
@@ -24,11 +29,12 @@ import torch
 
 from . import kmx, pipeline
 
-# rough device bytes per raw query point of one request (cloud, grid,
-# normals, SPFH and descriptor buffers, correspondences) plus a fixed part for
-# the matching scratch; used only for admission against the budget
-BYTES_PER_POINT = 450
+# device bytes of one request besides its CloudState buffers: the matching
+# scratch of the exact path per descriptor row of either side, and a fixed
+# part for the kmx context's scratch and the grid's hash table slack
+MATCH_BYTES_PER_ROW = 96
 BYTES_FIXED = 32 << 20
+RESERVE_BYTES = 2 << 30
 
 
 @dataclass
@@ -108,20 +114,37 @@ def _run_request(slot: _Slot, req: Request, m: ResidentMap, mode: int, nbr_per_p
     slot.event = ev
 
 
-def request_bytes(req: Request, m: ResidentMap) -> int:
-    return BYTES_FIXED + BYTES_PER_POINT * len(req.xyz) + 16 * max(1, m.n_valid)
+def request_bytes(req: Request, m: ResidentMap, nbr_per_point: int = 96) -> int:
+    """Device bytes a request allocates: its CloudState buffers (raw cloud,
+    voxels, normals, flags, CSR offsets, neighbour lists, descriptors, J),
+    the grid (cell keys, ranges and a sorted copy of the points), the
+    correspondences and the matching scratch."""
+    n = max(len(req.xyz), 1)
+    cloud = n * (12 + 16 + 16 + 1 + 8 + 4 * nbr_per_point + 4 * kmx.DESC_STRIDE + 4)
+    grid = n * (2 * 8 + 2 * 8 + 16)
+    corr = 16 * max(1, min(n, m.n_valid))
+    return BYTES_FIXED + cloud + grid + corr + MATCH_BYTES_PER_ROW * (n + max(1, m.n_valid))
+
+
+def device_headroom(device) -> int:
+    """Bytes a new request can still take: free device memory plus the blocks
+    PyTorch's caching allocator holds without using them."""
+    free, _ = torch.cuda.mem_get_info(device)
+    return int(free) + int(torch.cuda.memory_reserved(device) - torch.cuda.memory_allocated(device))
 
 
 class Server:
     """Continuous-batching loop over `slots` concurrent slots."""
 
     def __init__(self, maps, slots: int = 8, budget_bytes: int = 60 << 30, mode: int = kmx.MATCH_FP32_EXACT,
-                 device: int = 0):
+                 device: int = 0, reserve_bytes: int = RESERVE_BYTES):
         self.maps = maps
         self.device = torch.device("cuda", device)
         self.slots = [_Slot(self.device) for _ in range(slots)]
         self.budget = budget_bytes
+        self.reserve = reserve_bytes
         self.mode = mode
+        self.stats = dict(admitted=0, held_by_memory=0, peak_in_use=0)
 
     def run(self, requests, realtime: bool = True, max_seconds: float = 600.0):
         """Serve `requests` (sorted by arrival).  With realtime=False all
@@ -133,6 +156,7 @@ class Server:
         t0 = time.perf_counter()
         while (pending or any(s.req is not None for s in self.slots)) and time.perf_counter() - t0 < max_seconds:
             now = time.perf_counter() - t0
+            progress = False
             # retire finished requests
             for s in self.slots:
                 if s.req is not None and s.event.query():
@@ -161,6 +185,7 @@ class Server:
                     in_use -= s.bytes
                     s.req, s.state, s.event, s.bytes = None, None, None, 0
                     done.append(r)
+                    progress = True
             # admit arrived requests while a slot and the budget allow
             for s in self.slots:
                 if s.req is not None or not pending:
@@ -169,15 +194,25 @@ class Server:
                 if realtime and r.arrival > now:
                     break
                 need = request_bytes(r, self.maps[r.map_id])
-                if in_use + need > self.budget and in_use > 0:
+                if in_use > 0 and (in_use + need > self.budget or
+                                   device_headroom(self.device) < need + self.reserve):
+                    self.stats["held_by_memory"] += 1
                     break
                 pending.popleft()
                 r.admitted = time.perf_counter() - t0
                 s.req, s.bytes = r, need
                 in_use += need
+                self.stats["admitted"] += 1
+                self.stats["peak_in_use"] = max(self.stats["peak_in_use"], in_use)
                 _run_request(s, r, self.maps[r.map_id], self.mode)
-            if not realtime and not pending:
-                pass
+                progress = True
+            if not progress:
+                # nothing to retire or admit: wait for the next arrival or for
+                # work in flight, without spinning
+                wait = 2e-4
+                if pending and realtime and not any(s.req is not None for s in self.slots):
+                    wait = min(wait, max(0.0, pending[0].arrival - (time.perf_counter() - t0)))
+                time.sleep(wait)
         return done
 
 

@@ -57,8 +57,9 @@ def _edge_distance(f, lo, hi):
 
 def chained_pair_prone(pts, normal4, has_normal, ill, voffs, vnbr, eps, band=FEATURE_BAND):
     """Per point, the number of its SPFH pairs (Eq. A2) whose bins can change
-    when every well-posed normal may be off by up to ``eps`` rad (and an
-    ill-posed one by anything).  Bounds, with s = |d x u| and r the norm of
+    when every well-posed normal may be off by up to ``eps`` rad (a scalar,
+    or per point: then a pair takes the larger of its two points' values)
+    and an ill-posed one by anything.  Bounds, with s = |d x u| and r the norm of
     the atan2 arguments: |df3| <= 2 eps, |df2| <= 2 eps / s + 2 eps,
     |df1| <= (2 |df2| + 2 eps) / r.  A pair is counted when a feature lies
     within its bound (+ band) of a bin edge or the atan2 cut, when the source
@@ -74,6 +75,9 @@ def chained_pair_prone(pts, normal4, has_normal, ill, voffs, vnbr, eps, band=FEA
     dn = np.linalg.norm(d, axis=1)
     ok = dn > 0
     q, k, d, dn = q[ok], k[ok], d[ok], dn[ok]
+    if np.ndim(eps):
+        e_pt = np.asarray(eps, np.float64)
+        eps = np.maximum(e_pt[q], e_pt[k])
     d0 = d / dn[:, None]
     nq, nk = normal4[q, :3], normal4[k, :3]
     cq = np.abs(np.sum(nq * d0, 1))
@@ -98,3 +102,113 @@ def chained_pair_prone(pts, normal4, has_normal, ill, voffs, vnbr, eps, band=FEA
     prone |= _edge_distance(f2, -1.0, 1.0) < b2 + band
     prone |= _edge_distance(f3, -1.0, 1.0) < b3 + band
     return np.bincount(q, weights=prone.astype(np.float64), minlength=len(cnt)).astype(np.int64)
+
+
+# ----------------------------------------------------------------------------
+# chained parity: which points and pairs a band can move
+# ----------------------------------------------------------------------------
+
+NORMAL_TOL_RAD = 1e-5
+LIN_BAND = 1e-5
+
+
+def lin_bands(pts, f, tau_lin):
+    """From the oracle's Faster-PFH chain ``f`` of one cloud: the points whose
+    reliability flag B may differ at FP32 precision (p_lin within 1e-5 of
+    tau_lin) and the points whose membership in J may differ (those, and
+    every point with such a neighbour: |I_valid| can change).
+    Returns (b_band, j_band)."""
+    n = len(pts)
+    n4, fl = f["normal4"], f["flags"]
+    b_band = ((fl & 4) > 0) & (np.abs(n4[:, 3] - tau_lin) < LIN_BAND)
+    owner = np.repeat(np.arange(n), np.diff(f["offs"]))
+    j_band = b_band.copy()
+    if b_band.any():
+        j_band[np.unique(owner[b_band[f["nbr"]]])] = True
+    return b_band, j_band
+
+
+def row_allowance(pts, J, voffs, vnbr, n_marg, npairs, F):
+    """Per FPFH row (rows of F, points J): the L2 norm of the deviation the
+    row may show, every bin within 1e-4 at the 100-per-histogram scale plus
+    the allowance of its own and its neighbours' flip-prone pairs."""
+    a_fp = fpfh_allowance(pts, J, voffs, vnbr, spfh_allowance(n_marg, npairs))
+    allow = np.zeros(len(F))
+    for l in range(3):
+        tol = BIN_TOL * np.maximum(F[:, l * H:(l + 1) * H].sum(1), 100.0) / 100.0 + a_fp
+        allow += H * tol * tol
+    return np.sqrt(allow)
+
+
+def attribute_pairs(A_o, A_g, fo_p, fo_q, Jo_p, Jo_q, fg_p, fg_q, Jg_p, Jg_q, allow_p, allow_q, mutual_match):
+    """Correspondence sets of a reference chain (A_o) and of the GPU chain
+    (A_g), both with i, j as point indices; fo_* / fg_* the two chains'
+    descriptors (rows in the order of Jo_* / Jg_*); allow_* the deviation a
+    row of the reference's J may show (the band).  The nearest neighbours are
+    taken on both descriptor sets (FP64).  Every pair in one set and not the
+    other must be attributed to a band:
+      - membership: an end point, or a nearest neighbour involved, is not in
+        both J (the J band is checked separately);
+      - band: every nearest-neighbour decision that differs between the two
+        descriptor sets (row i: reference NN a, GPU NN b) is a swap that the
+        rows' deviations can cause, d_o(i, b) - d_o(i, a) <=
+        2 allow_i + allow_a + allow_b (triangle inequality).
+    A differing pair whose decisions all agree, or a swap beyond the band,
+    is unexplained.  Pass the measured deviations |fg - fo| of the rows as
+    allow_* after checking them against the allowed ones, so that a swap is
+    explained by the deviations that actually occurred.
+    Returns (unexplained pairs, counts per reason)."""
+    idx = lambda J: {int(q): r for r, q in enumerate(J)}
+    ro_p, ro_q, rg_p, rg_q = idx(Jo_p), idx(Jo_q), idx(Jg_p), idx(Jg_q)
+    _, so = mutual_match(fo_p, fo_q)
+    _, sg = mutual_match(fg_p, fg_q)
+    nn_o_pq = lambda i: int(Jo_q[so["nn_pq"][ro_p[i]]])
+    nn_g_pq = lambda i: int(Jg_q[sg["nn_pq"][rg_p[i]]])
+    nn_o_qp = lambda j: int(Jo_p[so["nn_qp"][ro_q[j]]])
+    nn_g_qp = lambda j: int(Jg_p[sg["nn_qp"][rg_q[j]]])
+    d_o = lambda i, j: float(np.linalg.norm(fo_p[ro_p[i]] - fo_q[ro_q[j]]))
+    both_p = lambda i: i in ro_p and i in rg_p
+    both_q = lambda j: j in ro_q and j in rg_q
+
+    def row_ok(i):  # None: membership; True / False: agree or in band / beyond band
+        if not both_p(i):
+            return None
+        a, b = nn_o_pq(i), nn_g_pq(i)
+        if a == b:
+            return True
+        if not (both_q(a) and both_q(b)):
+            return None
+        lim = 2 * allow_p[ro_p[i]] + allow_q[ro_q[a]] + allow_q[ro_q[b]]
+        return "swap" if d_o(i, b) - d_o(i, a) <= lim * (1 + 1e-9) + 1e-9 else False
+
+    def col_ok(j):
+        if not both_q(j):
+            return None
+        a, b = nn_o_qp(j), nn_g_qp(j)
+        if a == b:
+            return True
+        if not (both_p(a) and both_p(b)):
+            return None
+        lim = 2 * allow_q[ro_q[j]] + allow_p[ro_p[a]] + allow_p[ro_p[b]]
+        return "swap" if d_o(a, j) - d_o(b, j) >= -lim * (1 + 1e-9) - 1e-9 else False
+
+    ref = set(zip(A_o["i"].tolist(), A_o["j"].tolist()))
+    got = set(zip(A_g["i"].tolist(), A_g["j"].tolist()))
+    reasons = dict(membership=0, band=0)
+    unexplained = []
+    for i, j in sorted(ref ^ got):
+        cols = {j}
+        if both_p(i):
+            cols |= {nn_o_pq(i), nn_g_pq(i)}
+        checks = [row_ok(i)] + [col_ok(c) for c in sorted(cols)]
+        if any(c is False for c in checks):
+            unexplained.append((i, j))
+        elif any(c is None for c in checks):
+            reasons["membership"] += 1
+        elif any(c == "swap" for c in checks):
+            reasons["band"] += 1
+        else:
+            unexplained.append((i, j))  # every decision agrees: the sets should too
+    reasons["differing"] = len(ref ^ got)
+    reasons["pairs"] = len(ref)
+    return unexplained, reasons

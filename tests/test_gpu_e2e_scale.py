@@ -8,6 +8,8 @@
   ~300k voxels): voxelisation is checked bit-exactly in full; descriptors and
   matches on sampled rows, against the oracle run on the whole cloud.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -66,6 +68,54 @@ def test_registration_success_parity(env, orc):
 
 
 @pytest.mark.slow
+def test_registration_success_parity_1000(env, orc):
+    """Sec. IV-A success (rotation < 5 deg, translation < 2 m) of the oracle's
+    ratio filter, k-core and GNC-TLS (Secs. III-D, III-E) on the GPU's
+    correspondences, against the oracle's whole chain, over 1000 seeded pairs
+    (clutter scenes of 2k-6k points, overlap and noise varied so that a share
+    of the pairs fails): the success rates must differ by at most 0.5
+    percentage points.  The oracle runs in a pool of spawned processes while
+    the GPU computes."""
+    import multiprocessing as mp
+
+    import e2e_workers as w
+
+    torch, kmx, ctx = env
+    from paper_2409_15615_gb300 import pipeline
+
+    seeds = list(range(20000, 21000))
+    pool = mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1), initializer=w.init_worker)
+    try:
+        ref = {s: pool.apply_async(w.oracle_chain, (s,)) for s in seeds}
+        pair = pipeline.PairState(ctx, 6000, 6000)
+        gpu = {}
+        for s in seeds:
+            src, tgt, R, t, vps, vpt = w.make_pair(s)
+            pair.src.raw[: len(src)].copy_(torch.from_numpy(src).cuda())
+            pair.tgt.raw[: len(tgt)].copy_(torch.from_numpy(tgt).cuda())
+            ps = kmx.params_default(0.1, viewpoint=np.float32(vps).tolist())
+            pt = kmx.params_default(0.1, viewpoint=np.float32(vpt).tolist())
+            pair.run_checked(len(src), len(tgt), ps, pt, kmx.MATCH_FP32_EXACT)
+            gi, gj, gd1, gd2 = pair.correspondences()
+            vs = pair.src.vox4[: int(pair.src.n_vox.item())].cpu().numpy()
+            vt = pair.tgt.vox4[: int(pair.tgt.n_vox.item())].cpu().numpy()
+            gpu[s] = pool.apply_async(w.oracle_register, (s, gi, gj, gd1, gd2, vs, vt))
+        pair.close()
+        ok_o = {s: ref[s].get()[0] for s in seeds}
+        ok_g = {s: gpu[s].get() for s in seeds}
+    finally:
+        pool.close()
+        pool.join()
+    rate_o = np.mean([ok_o[s] for s in seeds])
+    rate_g = np.mean([ok_g[s] for s in seeds])
+    disagree = [s for s in seeds if ok_o[s] != ok_g[s]]
+    print("success: oracle chain %.3f, GPU correspondences %.3f, %d pairs disagree %s" % (
+        rate_o, rate_g, len(disagree), disagree[:20]))
+    assert 0.3 < rate_o < 0.98, "the mix must contain both successes and failures (%.3f)" % rate_o
+    assert abs(rate_o - rate_g) <= 0.005, (rate_o, rate_g, disagree)
+
+
+@pytest.mark.slow
 def test_indoor_2m_pair_sampled(env, orc):
     torch, kmx, ctx = env
     src, tgt, R, t, vps, vpt = indoor_pair(31)
@@ -91,10 +141,13 @@ def test_indoor_2m_pair_sampled(env, orc):
     g_offs = lst["offs"][: ns + 1].cpu().numpy()
     assert np.array_equal(g_offs, fs["offs"])
     del lst
-    # J: equal up to points whose reliability sits on the tau_lin band
+    # J: equal outside the points whose reliability (or a neighbour's) sits
+    # on the tau_lin band
+    from parity_helpers import lin_bands
+
     g_J = pair.src.out["valid"][: int(pair.src.out["n_valid"].item())].cpu().numpy()
     diff = np.setxor1d(g_J, fs["J"])
-    assert len(diff) <= max(3, len(fs["J"]) // 2000)
+    assert lin_bands(vs, fs, 0.99)[1][diff].all(), "J differs outside the tau_lin band"
     # sampled FPFH rows (those whose neighbourhood has no J/B difference),
     # each within tolerance plus the exact allowance of its flip-prone pairs
     from parity_helpers import fpfh_allowance, hist_violation, spfh_allowance
@@ -115,24 +168,29 @@ def test_indoor_2m_pair_sampled(env, orc):
     got = g_desc[torch.as_tensor([row_of[int(fs["J"][r])] for r in sel], device="cuda"), :33].cpu().numpy()
     v = hist_violation(got.astype(np.float64), fs["fpfh"][sel], a_fp[sel])
     assert v.max() <= 1.0, "FPFH off by %.3g x tolerance" % v.max()
-    # sampled matches: exact nearest target row of sampled source rows, and
-    # their reciprocity, against the GPU's correspondence set
-    if len(diff) == 0:
-        gi, gj, _, _ = pair.correspondences()
-        got = dict(zip(gi.tolist(), gj.tolist()))
-        rows = rng.choice(len(fs["J"]), 300, replace=False)
-        nn, d1, d2 = orc.nearest(fs["fpfh"][rows], ft["fpfh"])
-        back, e1, e2 = orc.nearest(ft["fpfh"][nn], fs["fpfh"])
-        # rows whose descriptors carry a bin flip (chained FP32 vs FP64) may
-        # legitimately differ; they are rare, so require 97 % agreement
-        agree = checked_m = 0
-        for k, r in enumerate(rows):
-            if (d2[k] - d1[k]) / max(d2[k], 1e-300) < 1e-3 or (e2[k] - e1[k]) / max(e2[k], 1e-300) < 1e-3:
-                continue
-            q = int(fs["J"][r])
-            mutual = back[k] == r
-            ok = got.get(q) == int(ft["J"][nn[k]]) if mutual else q not in got
-            agree += ok
-            checked_m += 1
-        assert checked_m > 150 and agree >= 0.97 * checked_m
+    # sampled matches on the GPU's own descriptors: for sampled source rows,
+    # the nearest target row and its nearest source row (FP64) decide the
+    # mutual pair; the GPU's correspondence set must agree on every sampled
+    # row outside the 1e-3 top-2 gap band (the whole chain's differences from
+    # the oracle's are attributed to descriptor bands in test_chained_pair)
+    gi, gj, _, _ = pair.correspondences()
+    got = dict(zip(gi.tolist(), gj.tolist()))
+    nJs, nJt = int(pair.src.out["n_valid"].item()), int(pair.tgt.out["n_valid"].item())
+    GP = pair.src.out["desc"][:nJs, :33].cpu().numpy().astype(np.float64)
+    GQ = pair.tgt.out["desc"][:nJt, :33].cpu().numpy().astype(np.float64)
+    gJt = pair.tgt.out["valid"][:nJt].cpu().numpy()
+    rows = rng.choice(nJs, 300, replace=False)
+    nn, d1, d2 = orc.nearest(GP[rows], GQ)
+    back, e1, e2 = orc.nearest(GQ[nn], GP)
+    checked_m = 0
+    for k, r in enumerate(rows):
+        if (d2[k] - d1[k]) / max(d2[k], 1e-300) < 1e-3 or (e2[k] - e1[k]) / max(e2[k], 1e-300) < 1e-3:
+            continue
+        q = int(g_J[r])
+        if back[k] == r:
+            assert got.get(q) == int(gJt[nn[k]]), "row %d: mutual pair missing or wrong" % q
+        else:
+            assert q not in got, "row %d: pair emitted without reciprocity" % q
+        checked_m += 1
+    assert checked_m > 150
     pair.close()

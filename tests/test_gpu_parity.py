@@ -476,19 +476,34 @@ def test_match_empty(torch_cuda, ctx):
 # ----------------------------------------------------------------------------
 
 
-@pytest.mark.parametrize("case", ["scene", "lidar"])
+@pytest.mark.parametrize("case", ["scene", "lidar", "scene_v005"])
 def test_chained_pair(torch_cuda, ctx, orc, case):
+    """The whole chain against the oracle.  Voxels bit-exact; J equal outside
+    the points whose reliability (or a neighbour's) sits on the tau_lin band.
+    The GPU's correspondences are then compared with the oracle's matching of
+    the oracle's own FP64 step 2, SPFH and FPFH computed from the GPU's step-1
+    outputs (normals and flags; neighbour lists are bit-exact): they must be
+    equal except pairs attributed to a propagated band (a nearest-neighbour
+    swap that the FP32 rounding of the descriptors, including pair features
+    within 2e-6 of a decision edge, can cause: parity_helpers.attribute_pairs).
+    The difference between that and the oracle's whole chain stems from the
+    normals alone, which the normals tests hold to 1e-5 rad outside the
+    ill-posed bands; its size is reported in the assertion messages."""
     from paper_2409_15615_gb300 import kmx, pipeline
+    from parity_helpers import attribute_pairs, lin_bands, row_allowance
 
     torch = torch_cuda
     if case == "scene":
         src, tgt, R, t, vps, vpt = scene_pair(8)
         v = 0.1
+    elif case == "scene_v005":
+        src, tgt, R, t, vps, vpt = scene_pair(18, n=60000)
+        v = 0.05
     else:
         src, tgt, R, t, vps, vpt = lidar_pair(8)
         v = 0.3
-    A, fs, ft, vs, vt = orc.front_end(src, tgt, v, np.float32(vps).astype(np.float64),
-                                      np.float32(vpt).astype(np.float64))
+    vp_s, vp_t = np.float32(vps).astype(np.float64), np.float32(vpt).astype(np.float64)
+    A, fs, ft, vs, vt = orc.front_end(src, tgt, v, vp_s, vp_t)
     ps, _ = params_for(kmx, orc, v, vps)
     pt, _ = params_for(kmx, orc, v, vpt)
     pair = pipeline.PairState(ctx, len(src), len(tgt))
@@ -497,18 +512,42 @@ def test_chained_pair(torch_cuda, ctx, orc, case):
     pair.run_checked(len(src), len(tgt), ps, pt, kmx.MATCH_FP32_EXACT)
     assert int(pair.src.n_vox.item()) == len(vs) and int(pair.tgt.n_vox.item()) == len(vt)
     assert np.array_equal(pair.src.vox4[: len(vs)].cpu().numpy().view(np.uint32), vs.view(np.uint32))
-    # J: equal up to points whose B flag sits on the tau_lin band
-    for cs, fo in ((pair.src, fs), (pair.tgt, ft)):
+    assert np.array_equal(pair.tgt.vox4[: len(vt)].cpu().numpy().view(np.uint32), vt.view(np.uint32))
+    hyb = []
+    for cs, fo, pts in ((pair.src, fs, vs), (pair.tgt, ft, vt)):
+        n = len(pts)
+        _, j_band = lin_bands(pts, fo, 0.99)
         nJ = int(cs.out["n_valid"].item())
         gJ = cs.out["valid"][:nJ].cpu().numpy()
         diff = np.setxor1d(gJ, fo["J"])
-        assert len(diff) <= max(2, len(fo["J"]) // 1000), "J differs in %d points" % len(diff)
+        assert j_band[diff].all(), "J differs outside the tau_lin band at %s" % diff[~j_band[diff]][:10]
+        # the oracle's step 2 and descriptors on the GPU's step-1 outputs
+        n4g = cs.bufs["normal4"][:n].cpu().numpy().astype(np.float64)
+        flg = cs.bufs["flags"][:n].cpu().numpy()
+        voffs, vnbr, J, fl2 = orc.valid_filter(fo["offs"], fo["nbr"], flg & 5, 3)
+        assert np.array_equal(J, gJ)
+        sp, npairs, _, n_marg = orc.spfh(pts, n4g, fl2, voffs, vnbr, H, with_margin=True, band=FEATURE_BAND)
+        F = orc.fpfh(pts, J, voffs, vnbr, sp)
+        hyb.append((J, F, row_allowance(pts, J, voffs, vnbr, n_marg, npairs, F),
+                    cs.out["desc"][:nJ, :33].cpu().numpy().astype(np.float64)))
     gi, gj, gd1, gd2 = pair.correspondences()
-    ref = set(zip(A["i"].tolist(), A["j"].tolist()))
-    got = set(zip(gi.tolist(), gj.tolist()))
-    agree = len(ref & got) / max(len(ref), 1)
     pair.close()
-    assert agree > 0.97, "only %.3f of the oracle's correspondences reproduced" % agree
+    G = np.zeros(len(gi), dtype=A.dtype)
+    G["i"], G["j"] = gi, gj
+    (Jp, Fp, ap, gp), (Jq, Fq, aq, gq) = hyb
+    # every row's measured deviation lies within its band; the swaps are then
+    # attributed to the deviations that occurred
+    dp = np.linalg.norm(gp - Fp, axis=1)
+    dq = np.linalg.norm(gq - Fq, axis=1)
+    assert np.all(dp <= ap) and np.all(dq <= aq), "a descriptor row deviates beyond its band"
+    H_, _ = orc.mutual_match(Fp, Fq)
+    Hp = H_.copy()
+    Hp["i"], Hp["j"] = Jp[H_["i"]], Jq[H_["j"]]
+    bad, why = attribute_pairs(Hp, G, Fp, Fq, Jp, Jq, gp, gq, Jp, Jq, dp, dq, orc.mutual_match)
+    whole = len(set(zip(A["i"].tolist(), A["j"].tolist())) ^ set(zip(Hp["i"].tolist(), Hp["j"].tolist())))
+    assert not bad, "pairs differ without a band: %s (%s; the normals move %d of %d pairs)" % (
+        bad[:5], why, whole, len(A))
+    assert why["pairs"] > 100, (why, whole)
 
 
 # ----------------------------------------------------------------------------
@@ -572,13 +611,13 @@ def test_match_bf16_equals_exact_fp32(torch_cuda, ctx, orc):
 
 
 def test_match_bf16_duplicates_overflow_to_exact(torch_cuda, ctx):
-    """300 copies of one descriptor tie at distance 0 for every row near them:
-    those rows' candidate lists overflow (256) and go through the exact FP32
+    """600 copies of one descriptor tie at distance 0 for every row near them:
+    those rows' candidate lists overflow (512) and go through the exact FP32
     tiles; ties resolve to the lowest index exactly as in the exact path."""
     rng = np.random.default_rng(21)
     FP = rng.gamma(0.5, 20.0, (900, 33)).astype(np.float32)
     FQ = rng.gamma(0.5, 20.0, (1100, 33)).astype(np.float32)
-    FQ[100:400] = FP[5]
+    FQ[100:700] = FP[5]
     FP[600:650] = FP[5]
     n = _same_as_exact(torch_cuda, ctx, FP, FQ)
     assert n > 0
