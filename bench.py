@@ -397,28 +397,30 @@ def run_kmx(args):
 
 def bench_batched(torch, n_pairs, rank):
     """Uneven pairs (raw size log-uniform in [5k, 300k], scene and LiDAR
-    generators, voxel in {0.05, 0.1, 0.3}) in one graph launch, lanes and
-    match mode autotuned, against the same pairs run one at a time."""
+    generators, voxel in {0.05, 0.1, 0.3}) in one graph launch, with lanes,
+    the exact matcher's chunk size and the tensor-core size bucket picked by
+    the autotuner, against the plain path: the same pairs one at a time, each
+    as its own captured graph of the one-pair step, replayed in sequence."""
     from synth import batch_pairs
 
     from paper_2409_15615_gb300 import batch
 
     specs = [batch.PairSpec(p["src"], p["tgt"], p["voxel"], tuple(p["vp_src"]), tuple(p["vp_tgt"]))
              for p in batch_pairs(7000 + rank, n_pairs=n_pairs)]
-    runner, table = batch.autotune(specs, lane_options=(1, 4, 8, 16))
+    runner, table = batch.autotune(specs)
     best = min(table, key=lambda r: r["batch_s"])
     sec = batch.time_batch(runner, reps=5, graph=True)
-    # the plain path: the same pairs one at a time, direct launches, one stream
-    plain = batch.BatchRunner(specs, lanes=1, mode=best["mode"]).prepare()
-    plain_sec = batch.time_batch(plain, reps=3, graph=False)
-    n_corr = int(runner.n_corr.sum().item())
-    same = bool(torch.equal(runner.n_corr, plain.n_corr))
+    plain_sec, plain_counts = batch.time_plain(specs, reps=3, tc_min=best["tc_min"])
+    counts = runner.n_corr.cpu().numpy()
+    n_corr = int(counts.sum())
+    same = bool(np.array_equal(counts, plain_counts))
     runner.close()
-    plain.close()
-    return dict(pairs=n_pairs, lanes=best["lanes"], mode="fp32_exact" if best["mode"] == 0 else "bf16_certified",
-                batch_ms=sec * 1e3, pairs_per_s=n_pairs / sec, plain_pairs_per_s=n_pairs / plain_sec,
-                speedup_vs_plain=plain_sec / sec, raw_points=int(sum(len(s.src) + len(s.tgt) for s in specs)),
-                correspondences=n_corr, same_counts_as_plain=same, autotune=table)
+    return dict(pairs=n_pairs, lanes=best["lanes"], chunks_per_cta=best["chunks"] or 8, tc_min=best["tc_min"],
+                tc_pairs=best["tc_pairs"], batch_ms=sec * 1e3, pairs_per_s=n_pairs / sec,
+                plain_pairs_per_s=n_pairs / plain_sec, speedup_vs_plain=plain_sec / sec,
+                raw_points=int(sum(len(s.src) + len(s.tgt) for s in specs)), correspondences=n_corr,
+                same_counts_as_plain=same, autotune=table,
+                plain="each pair as its own captured graph of the one-pair step (two streams), one after the other")
 
 
 def bench_register(torch, rank, reps, with_oracle):

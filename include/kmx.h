@@ -149,6 +149,16 @@ kmx_status kmx_set_stream(kmx_ctx* ctx, void* cuda_stream);
  * scheduling choice.  Returns KMX_EINVAL for other values. */
 kmx_status kmx_set_match_residency(kmx_ctx* ctx, int ctas_per_sm);
 
+/* Work-item size of the exact FP32 matcher (KMX_MATCH_FP32_EXACT): its tile
+ * kernel cuts the (row tile x column tile) sequence into about
+ * chunks_per_cta chunks per resident CTA, which the CTAs take from a device
+ * counter (smaller ones at the end of the sequence); 1..32, 0 restores the
+ * default 8.  Larger values balance uneven tile pairs better, smaller ones
+ * keep a source tile longer in shared memory.  The results do not depend on
+ * it.  Not from the paper: a scheduling parameter (the batch autotuner
+ * searches it).  Returns KMX_EINVAL for other values. */
+kmx_status kmx_set_match_chunks(kmx_ctx* ctx, int chunks_per_cta);
+
 /* Make sure the context scratch holds at least `bytes` bytes. */
 kmx_status kmx_reserve(kmx_ctx* ctx, int64_t bytes);
 

@@ -164,6 +164,13 @@ kmx_status kmx_set_match_residency(kmx_ctx* c, int ctas_per_sm)
     return KMX_OK;
 }
 
+kmx_status kmx_set_match_chunks(kmx_ctx* c, int chunks_per_cta)
+{
+    if (!c || chunks_per_cta < 0 || chunks_per_cta > 32) return KMX_EINVAL;
+    c->match_chunks_per_cta = chunks_per_cta;
+    return KMX_OK;
+}
+
 kmx_status kmx_reserve(kmx_ctx* c, int64_t bytes)
 {
     if (!c || bytes < 0) return KMX_EINVAL;

@@ -30,6 +30,7 @@ struct kmx_ctx {
     unsigned int* h_err;   // pinned host mirror for kmx_sync
     int sm_count;
     int match_ctas_per_sm;  // exact matcher residency, 0 = default
+    int match_chunks_per_cta;  // exact matcher work items per resident CTA, 0 = default
     unsigned long long* scan_status;  // zeroed look-back area of the scans (scan.cu)
     int64_t scan_words;
     char msg[256];

@@ -66,7 +66,8 @@ constexpr uint32_t kPBytes = kDim * kTile * sizeof(float2);  // 33792
 constexpr uint32_t kQBytes = kDim * kTile * sizeof(float);   // 16896
 constexpr uint32_t kPermBytes = kTile * sizeof(int32_t);     // 512
 constexpr int kCtasPerSm = 2;
-constexpr int kChunksPerCta = 8;      // chunks of the tile sequence per resident CTA (load balance)
+constexpr int kChunksPerCta = 8;      // default chunks of the tile sequence per resident CTA (load balance)
+constexpr int kMaxChunksPerCta = 32;  // the largest setting (kmx_set_match_chunks)
 constexpr int kTailChunksPerCta = 4;  // smaller chunks per CTA for the end of the sequence
 constexpr int kMinChunk = 4;       // tile pairs per chunk at least (more than kStages - 1)
 
@@ -313,9 +314,9 @@ __device__ __forceinline__ void row_step(unsigned long long& k1, float& b2, floa
 
 constexpr unsigned long long kNoBest = (0x7f800000ull << 32) | 0x7fffffffull;  // (+inf, no column)
 
-__device__ __forceinline__ ChunkGeo chunk_geo(int64_t W, int ctas)
+__device__ __forceinline__ ChunkGeo chunk_geo(int64_t W, int ctas, int chunks_per_cta)
 {
-    const int64_t per = (int64_t)kChunksPerCta * ctas;
+    const int64_t per = (int64_t)chunks_per_cta * ctas;
     int64_t LA = (W + per - 1) / per;
     if (LA < kMinChunk) LA = kMinChunk;
     const int64_t tail = W < ctas * LA ? W : ctas * LA;
@@ -384,7 +385,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
                           const unsigned long long* __restrict__ pmask, int64_t np_cap, const int64_t* d_np,
                           const float* __restrict__ qn, const int32_t* __restrict__ qperm,
                           const unsigned long long* __restrict__ qmask, int64_t nq_cap, const int64_t* d_nq,
-                          int ctas, int32_t* __restrict__ counter, kmx::RowBest* __restrict__ seg,
+                          int ctas, int chunks_per_cta, int32_t* __restrict__ counter,
+                          kmx::RowBest* __restrict__ seg,
                           unsigned long long* __restrict__ colbest, unsigned int* __restrict__ err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -405,7 +407,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
         mbar_fence_init();
         S.failed = 0;
         S.end_item = INT_MAX;
-        S.cg = chunk_geo(W, ctas);
+        S.cg = chunk_geo(W, ctas, chunks_per_cta);
     }
     __syncthreads();
     int issued = 0;  // meaningful in thread 0: local items whose copies were issued
@@ -612,7 +614,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
 // ties by original column), then the reciprocity test; results go to the
 // original row.
 __global__ void __launch_bounds__(256) merge_segments(const kmx::RowBest* __restrict__ seg,
-                                                      const int32_t* __restrict__ pperm, int ctas, int64_t np_cap,
+                                                      const int32_t* __restrict__ pperm, int ctas,
+                                                      int chunks_per_cta, int64_t np_cap,
                                                       const int64_t* d_np, int64_t nq_cap, const int64_t* d_nq,
                                                       const unsigned long long* __restrict__ colbest,
                                                       kmx::RowBest* __restrict__ merged, int32_t* __restrict__ mflag)
@@ -624,7 +627,7 @@ __global__ void __launch_bounds__(256) merge_segments(const kmx::RowBest* __rest
     for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < np; i += (int64_t)gridDim.x * 256) {
         kmx::RowBest r{INFINITY, 0x7fffffff, INFINITY};
         if (W > 0) {
-            const ChunkGeo cg = chunk_geo(W, ctas);
+            const ChunkGeo cg = chunk_geo(W, ctas, chunks_per_cta);
             const int64_t rt = i / kTile;
             const int64_t cf = chunk_of(cg, rt * nqt), cl = chunk_of(cg, rt * nqt + nqt - 1);
             r = seg[(cf + rt) * kTile + (i % kTile)];
@@ -679,7 +682,7 @@ BulkScratch carve(void* base, int64_t np_cap, int64_t nq_cap, int max_ctas, size
     s.sort.distinct = static_cast<int32_t*>(a.take(sizeof(int32_t) * T));
     s.seg = static_cast<kmx::RowBest*>(
         a.take(sizeof(kmx::RowBest) * kTile *
-               (size_t)((kChunksPerCta + kTailChunksPerCta) * max_ctas + 1 + tiles_of(np_cap))));
+               (size_t)((kMaxChunksPerCta + kTailChunksPerCta) * max_ctas + 1 + tiles_of(np_cap))));
     *total = kmx_align_up(a.used, 256);
     return s;
 }
@@ -726,6 +729,7 @@ cudaError_t kmx_match_fp32_bulk_launch(kmx_ctx* ctx, const float* dp, const int3
         return e;
     const int want = ctx->match_ctas_per_sm > 0 ? ctx->match_ctas_per_sm : kCtasPerSm;
     const int ctas = max(1, min(per_sm, min(want, kCtasPerSm))) * ctx->sm_count;
+    const int cpc = ctx->match_chunks_per_cta > 0 ? min(ctx->match_chunks_per_cta, kMaxChunksPerCta) : kChunksPerCta;
     const unsigned small_grid = 4u * (unsigned)ctx->sm_count;  // grid-stride over the actual rows
     if ((e = cudaMemsetAsync(b.sort.keys, 0xFF, sizeof(unsigned long long) * b.sort.T, st))) return e;
     if ((e = cudaMemsetAsync(b.sort.count, 0, sizeof(int32_t) * (2 * (size_t)b.sort.T + 2), st))) return e;
@@ -738,11 +742,11 @@ cudaError_t kmx_match_fp32_bulk_launch(kmx_ctx* ctx, const float* dp, const int3
     KMX_COUNT_LAUNCH();
     match_tiles_fp32_bulk<<<ctas, kThreads, sizeof(BulkShared), st>>>(
         static_cast<const float2*>(b.sort.packed[0]), b.sort.perm[0], b.sort.mask[0], np_cap, d_np,
-        static_cast<const float*>(b.sort.packed[1]), b.sort.perm[1], b.sort.mask[1], nq_cap, d_nq, ctas,
+        static_cast<const float*>(b.sort.packed[1]), b.sort.perm[1], b.sort.mask[1], nq_cap, d_nq, ctas, cpc,
         b.chunk_counter, b.seg, s.colbest, ctx->d_err);
     KMX_COUNT_LAUNCH();
     merge_segments<<<kmx_stride_blocks(np_cap, 256, ctx->sm_count), 256, 0, st>>>(
-        b.seg, b.sort.perm[0], ctas, np_cap, d_np, nq_cap, d_nq, s.colbest, s.merged, s.mflag);
+        b.seg, b.sort.perm[0], ctas, cpc, np_cap, d_np, nq_cap, d_nq, s.colbest, s.merged, s.mflag);
     if ((e = cudaGetLastError())) return e;
     return kmx::match_emit(ctx, s, np_cap, d_np, vp, vq, out, cap, n_out);
 }

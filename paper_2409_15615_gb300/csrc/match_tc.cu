@@ -81,21 +81,23 @@ using kmx::mbar_wait;
 using kmx::smem_u32;
 
 constexpr int kTM = 128;                      // rows per tile (UMMA M)
-constexpr int kTN = 256;                      // columns per column tile (UMMA N)
+constexpr int kTN = 128;                      // columns per column tile (UMMA N)
 constexpr int kK = 48;                        // 33 values + 3 slots, padded to 3 x 16
 constexpr int kOpBytesA = kTM * kK * 2;       // one BF16 row tile: 12288
-constexpr int kOpBytesB = kTN * kK * 2;       // one BF16 column tile: 24576
+constexpr int kOpBytesB = kTN * kK * 2;       // one BF16 column tile: 12288
 constexpr int kCoreStride = 128;              // LBO: next 8-element K chunk
 constexpr int kGroupStride = 6 * 128;         // SBO: next 8-row group
 constexpr int kCenterStride = 36;             // floats per stored centre
-// packed column tile: operand, then |b| per row, the centre, max |b|^2
+// packed column tile: operand, then |b| per row, the centre, max |b|^2, and
+// the largest |b| of every group of 8 rows
 constexpr int kHdrBeta = kOpBytesB;
 constexpr int kHdrCenter = kHdrBeta + kTN * 4;
 constexpr int kHdrBmax = kHdrCenter + kCenterStride * 4;
-constexpr int kColBytes = kHdrBmax + 16;      // 25760, a multiple of 16
+constexpr int kHdrGBeta = kHdrBmax + 16;
+constexpr int kColBytes = kHdrGBeta + (kTN / 8) * 4;  // 13024, a multiple of 16
 constexpr int kStages = 4;                    // column-tile ring
-constexpr int kThreads = 512;                 // 16 warps: four per TMEM lane quarter
-constexpr int kTmemCols = 512;                // two 256-column FP32 accumulators
+constexpr int kThreads = 256;                 // 8 warps: two per TMEM lane quarter
+constexpr int kTmemCols = 256;                // two 128-column FP32 accumulators
 constexpr int kMaxChunks = 8;
 constexpr int kCandCap = 512;                 // candidate list per row
 constexpr float kC = 0.008f;                  // c' of the bounds
@@ -157,27 +159,39 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar)
                  : "memory");
 }
 
-// 32 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
+// 64 consecutive FP32 columns of this thread's TMEM lane: two loads in
+// flight, one wait.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float* v)
 {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
+    uint32_t r[64];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t* q = r + 32 * h;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+            : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7]),
+              "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]), "=r"(q[14]), "=r"(q[15]),
+              "=r"(q[16]), "=r"(q[17]), "=r"(q[18]), "=r"(q[19]), "=r"(q[20]), "=r"(q[21]), "=r"(q[22]), "=r"(q[23]),
+              "=r"(q[24]), "=r"(q[25]), "=r"(q[26]), "=r"(q[27]), "=r"(q[28]), "=r"(q[29]), "=r"(q[30]), "=r"(q[31])
+            : "r"(taddr + 32 * h));
+    }
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ float fmax3(float a, float b, float c)
 {
     float d;
     asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+__device__ __forceinline__ float fmin3(float a, float b, float c)
+{
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
     return d;
 }
 
@@ -321,10 +335,10 @@ __global__ void __launch_bounds__(256) tc_keys(int64_t np_cap, const int64_t* d_
 }
 
 // ---------------------------------------------------------------------------
-// pack: one CTA of 256 threads per column tile of one cloud
+// pack: one CTA of 128 threads per column tile of one cloud
 // ---------------------------------------------------------------------------
 
-// Rows of the tile are sorted positions [256 t, 256 t + 256) of the cloud;
+// Rows of the tile are sorted positions [128 t, 128 t + 128) of the cloud;
 // perm maps a sorted position to the descriptor row.  Writes the packed
 // column tile and the centre (also to centers[t]).
 __global__ void __launch_bounds__(kTN) tc_pack(const float* __restrict__ desc, const int32_t* __restrict__ perm,
@@ -392,11 +406,15 @@ __global__ void __launch_bounds__(kTN) tc_pack(const float* __restrict__ desc, c
     }
     __syncthreads();
     if (tid < 4) reinterpret_cast<float*>(tile + kHdrBmax)[tid] = tid == 0 ? __uint_as_float(bmax2) : 0.f;
+    // the largest |b| of each group of 8 rows (lanes 8k .. 8k + 7 of a warp)
+    float gb = valid ? beta : 0.f;
+#pragma unroll
+    for (int o = 4; o >= 1; o >>= 1) gb = fmaxf(gb, __shfl_xor_sync(0xffffffffu, gb, o));
+    if ((tid & 7) == 0) reinterpret_cast<float*>(tile + kHdrGBeta)[tid >> 3] = gb;
 }
 
-// For each column tile of X (256 rows; row tile T of X lies in tile T / 2):
-// the column tile of Y with the nearest centre (ties to the lower tile).
-// One warp per tile.
+// For each tile of X (its row tiles are its column tiles): the column tile
+// of Y with the nearest centre (ties to the lower tile).  One warp per tile.
 __global__ void __launch_bounds__(256) tc_nearest(const float* __restrict__ cx, int64_t nx_cap, const int64_t* d_nx,
                                                   const float* __restrict__ cy, int64_t ny_cap, const int64_t* d_ny,
                                                   int32_t* __restrict__ nearest)
@@ -442,28 +460,33 @@ __global__ void __launch_bounds__(256) tc_nearest(const float* __restrict__ cx, 
 struct TcShared {
     uint8_t a[2][kOpBytesA];
     uint8_t b[kStages][kColBytes];
-    float r2[3][kTM];  // |x - c|^2 of every row, by step modulo 3 (written one step ahead of its reads,
-                       // while the slowest thread may still read the previous step's)
+    // per row and step (modulo 3: written one step ahead of its reads, while
+    // the slowest thread may still read the previous step's): |a|^2 - e,
+    // the factor c' |a| of the upper bounds, 2 e, and the second-smallest
+    // upper bound over the row's two column slices as of three steps earlier
+    float4 rowc[3][kTM];
+    float2 ul[3][kTM][2];  // (U1, U2) of the two column slices of every row, by step modulo 3
     uint64_t bar_b[kStages], bar_mma[2];
     uint32_t tmem;
 };
 
-// Threads (16 warps) have two roles per step (one 256-column tile):
-//   re-centring  thread t writes values 8 (t & 3) .. + 7 of row t >> 2 of
-//                the A operand (the t & 3 == 3 thread also value 32 and the
-//                three slots); the four threads of a row are neighbouring
-//                lanes and add their partial |x - c|^2 with two shuffles;
+// Threads (8 warps) have two roles per step (one 128-column tile):
+//   re-centring  thread t writes values 16 (t & 1) .. of row t >> 1 of the A
+//                operand (the t & 1 == 1 thread values 16 .. 32 and the three
+//                slots); the two threads of a row are neighbouring lanes and
+//                add their partial |x - c|^2 with one shuffle;
 //   epilogue     warp w reads TMEM lanes (rows) 32 (w & 3) .. + 31 and
-//                accumulator columns 64 (w >> 2) .. + 63.  The four threads
-//                of a row keep their own bounds and candidate decisions over
+//                accumulator columns 64 (w >> 2) .. + 63.  The two threads of
+//                a row keep their own bounds and candidate decisions over
 //                their own columns (disjoint sets, one list per row).
-// One CTA per SM (its TMEM allocation is all 512 columns).  One barrier per
+// Two CTAs per SM (each holds half of the TMEM), so that one CTA's
+// re-centring and barrier overlap the other's epilogue.  One barrier per
 // step: it publishes the A operand to the MMA and orders the previous
 // step's accumulator reads before the next MMA into that accumulator.
 //
 // The grid is sized from the capacities; the (row tile, column chunk) split
 // of the actual counts is decided here (kmx::work_chunks).
-__global__ void __launch_bounds__(kThreads, 1) tc_collect(const float* __restrict__ X,
+__global__ void __launch_bounds__(kThreads, 2) tc_collect(const float* __restrict__ X,
                                                          const int32_t* __restrict__ permX, int64_t nx_cap,
                                                          const int64_t* d_nx, const uint8_t* __restrict__ packY,
                                                          int64_t ny_cap, const int64_t* d_ny,
@@ -487,7 +510,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_collect(const float* __restric
     if (T == 0) return;
     // the sequence of column tiles: the nearest tile first, then the chunk
     // (without the nearest tile when it lies inside the chunk)
-    const int64_t cs = nearest[rt >> 1];
+    const int64_t cs = nearest[rt];
     const bool cs_in = cs >= t0 && cs < t0 + T;
     const int nseq = T + (cs_in ? 0 : 1);
     auto tile_of = [&](int s) -> int64_t {
@@ -498,7 +521,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_collect(const float* __restric
     const uint32_t idesc = idesc_bf16(kTM, kTN);
 
     // re-centring role
-    const int rrow = tid >> 2, part = tid & 3;
+    const int rrow = tid >> 1, part = tid & 1;
     const int64_t xrow = rt * kTM + rrow;
     const bool xvalid = xrow < rows;
     // epilogue role
@@ -514,7 +537,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_collect(const float* __restric
         mbar_fence_init();
     }
     if (warp == 0) tmem_alloc(&S.tmem, kTmemCols);
-    if (part == 3) {  // the last K chunk (values 40..47) is zero in every A operand
+    if (part == 1) {  // the last K chunk (values 40..47) is zero in every A operand
         const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         store_operand_chunk(S.a[0], rrow, 5, z);
         store_operand_chunk(S.a[1], rrow, 5, z);
@@ -524,11 +547,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_collect(const float* __restric
     tc_fence_after();
     const uint32_t tmem = S.tmem;
 
-    float x[9];  // values 8 part .. 8 part + 7 (and 32 for part 3) of this thread's re-centring row
+    float x[17];  // values 16 part .. 16 part + 15 (and 32 for part 1) of this thread's re-centring row
     {
-        const float* xr = xvalid ? X + (int64_t)permX[xrow] * KMX_DESC_STRIDE + 8 * part : nullptr;
+        const float* xr = xvalid ? X + (int64_t)permX[xrow] * KMX_DESC_STRIDE + 16 * part : nullptr;
 #pragma unroll
-        for (int h = 0; h < 9; ++h) x[h] = (xvalid && (h < 8 || part == 3)) ? __ldg(xr + h) : 0.f;
+        for (int h = 0; h < 17; ++h) x[h] = (xvalid && (h < 16 || part == 1)) ? __ldg(xr + h) : 0.f;
     }
 
     int issued_b = 0, issued_mma = 0;
@@ -539,39 +562,59 @@ __global__ void __launch_bounds__(kThreads, 1) tc_collect(const float* __restric
         }
     }
     bool fail = false, failed = false;
-    float U1 = FLT_MAX, U2 = FLT_MAX;
+    // upper bounds of the columns this thread has seen (own slice only), and
+    // the second-smallest upper bound over all four slices of the row as of
+    // the last barrier
+    float U1 = FLT_MAX, U2 = FLT_MAX, Ush = FLT_MAX;
 
     for (int s = 0; s <= nseq; ++s) {
         if (s < nseq) {
             // ---- A operand of step s: rows re-centred on the column tile's centre
             if (!mbar_wait(&S.bar_b[s % kStages], (s / kStages) & 1)) fail = true;
             const uint8_t* bt = S.b[s % kStages];
-            const float4* cen4 = reinterpret_cast<const float4*>(bt + kHdrCenter) + 2 * part;
-            const float4 c0 = cen4[0], c1 = cen4[1];
-            const float cc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-            float av[8];
+            const float4* cen4 = reinterpret_cast<const float4*>(bt + kHdrCenter) + 4 * part;
+            float av[16];
             float p2 = 0.f;
 #pragma unroll
-            for (int h = 0; h < 8; ++h) {
-                av[h] = x[h] - cc[h];
-                p2 = fmaf(av[h], av[h], p2);
+            for (int c = 0; c < 4; ++c) {
+                const float4 cv = cen4[c];
+                av[4 * c + 0] = x[4 * c + 0] - cv.x;
+                av[4 * c + 1] = x[4 * c + 1] - cv.y;
+                av[4 * c + 2] = x[4 * c + 2] - cv.z;
+                av[4 * c + 3] = x[4 * c + 3] - cv.w;
             }
+#pragma unroll
+            for (int h = 0; h < 16; ++h) p2 = fmaf(av[h], av[h], p2);
             float a32 = 0.f;
-            if (part == 3) {
-                a32 = x[8] - reinterpret_cast<const float*>(bt + kHdrCenter)[32];
+            if (part == 1) {
+                a32 = x[16] - reinterpret_cast<const float*>(bt + kHdrCenter)[32];
                 p2 = fmaf(a32, a32, p2);
             }
             uint8_t* at = S.a[s & 1];
-            store_operand_chunk(at, rrow, part, av);
-            // the four partial sums of the row (neighbouring lanes); each
-            // lane forms the same total
+            store_operand_chunk(at, rrow, 2 * part, av);
+            store_operand_chunk(at, rrow, 2 * part + 1, av + 8);
+            // the two partial sums of the row (neighbouring lanes); both lanes
+            // form the same total
             p2 += __shfl_xor_sync(0xffffffffu, p2, 1);
-            p2 += __shfl_xor_sync(0xffffffffu, p2, 2);
-            if (part == 3) {
+            if (part == 1) {
                 const float v4[8] = {a32, kSqrtC * sqrtf(p2), -0.5f, -0.5f, 0.f, 0.f, 0.f, 0.f};
                 store_operand_chunk(at, rrow, 4, v4);
             }
-            if (part == 0) S.r2[s % 3][rrow] = p2;
+            if (part == 0) {
+                const float bmax2 = reinterpret_cast<const float*>(bt + kHdrBmax)[0];
+                const float ef = kEfp * (p2 + bmax2);
+                float ush = FLT_MAX;
+                if (s >= 3) {
+                    // the row's two slices as of step s - 3 (written in the
+                    // epilogue of iteration s - 2, published by the barrier of
+                    // step s - 1): their upper bounds come from disjoint
+                    // columns, so the second smallest of the eight is the
+                    // second smallest over all columns they saw
+                    const float2 a0 = S.ul[s % 3][rrow][0], a1 = S.ul[s % 3][rrow][1];
+                    ush = fminf(fmaxf(a0.x, a1.x), a0.x <= a1.x ? a0.y : a1.y);
+                }
+                S.rowc[s % 3][rrow] = make_float4(p2 - ef, kUpper * sqrtf(p2), 2.f * ef, ush);
+            }
             fence_proxy_async();
         }
         // publishes the A operand and r2 of step s; every thread has finished
@@ -609,54 +652,73 @@ __global__ void __launch_bounds__(kThreads, 1) tc_collect(const float* __restric
             if (!mbar_wait(&S.bar_mma[p & 1], (p >> 1) & 1)) fail = true;
             tc_fence_after();
             const uint8_t* bt = S.b[p % kStages];
-            const float r2 = S.r2[p % 3][r];
-            const float ef = kEfp * (r2 + reinterpret_cast<const float*>(bt + kHdrBmax)[0]);
-            const float rb = r2 - ef;
-            const float up = kUpper * sqrtf(r2);
+            const float4 rc = S.rowc[p % 3][r];
+            const float rb = rc.x, ua = rc.y, ue = rc.z;
+            Ush = fminf(Ush, rc.w);
+            const float* gbeta = reinterpret_cast<const float*>(bt + kHdrGBeta) + slice * 8;
             const bool collect = p > 0 || cs_in;
             const int64_t col0 = tile_of(p) * kTN + slice * 64;
-            const float* beta = reinterpret_cast<const float*>(bt + kHdrBeta) + slice * 64;
             const uint32_t lane_addr =
                 tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((p & 1) * kTN + slice * 64);
-#pragma unroll 1
-            for (int c0 = 0; c0 < 64; c0 += 32) {
-                float v[32];
-                tmem_ld32(lane_addr + c0, v);
+            float v[64];
+            tmem_ld64(lane_addr, v);
+            // the eight groups' smallest lower bounds, independent of each
+            // other; one branch for all of them in the common case
+            float Lm[8];
 #pragma unroll
-                for (int g = 0; g < 4; ++g) {
+            for (int g = 0; g < 8; ++g) {
+                const float* vg = v + 8 * g;
+                const float m = fmax3(fmax3(vg[0], vg[1], vg[2]), fmax3(vg[3], vg[4], vg[5]), fmaxf(vg[6], vg[7]));
+                // L = |a|^2 - e - 2 M is monotone in M: the group's largest M
+                // gives its smallest L
+                Lm[g] = fmaf(-2.f, m, rb);
+            }
+            const float lmin = fmin3(fmin3(Lm[0], Lm[1], Lm[2]), fmin3(Lm[3], Lm[4], Lm[5]), fminf(Lm[6], Lm[7]));
+            if (row_valid && lmin <= fminf(U2, Ush)) {
+#pragma unroll
+                for (int g = 0; g < 8; ++g) {
                     const float* vg = v + 8 * g;
-                    const float m = fmax3(fmax3(vg[0], vg[1], vg[2]), fmax3(vg[3], vg[4], vg[5]), fmaxf(vg[6], vg[7]));
-                    // L = |a|^2 - e - 2 M is monotone in M: the group's largest
-                    // M gives its smallest L
-                    if (row_valid && fmaf(-2.f, m, rb) <= U2) {
-                        unsigned msk = 0;
+                    const float Lmin = Lm[g];
+                    if (Lmin <= fminf(U2, Ush)) {
+                        // the group's two best columns (largest M first): upper
+                        // bounds for them
+                        float h0 = fmaxf(vg[0], vg[1]), l0 = fminf(vg[0], vg[1]);
+                        float h1 = fmaxf(vg[2], vg[3]), l1 = fminf(vg[2], vg[3]);
+                        float h2 = fmaxf(vg[4], vg[5]), l2 = fminf(vg[4], vg[5]);
+                        float h3 = fmaxf(vg[6], vg[7]), l3 = fminf(vg[6], vg[7]);
+                        l0 = fmaxf(fminf(h0, h1), fmaxf(l0, l1));
+                        h0 = fmaxf(h0, h1);
+                        l2 = fmaxf(fminf(h2, h3), fmaxf(l2, l3));
+                        h2 = fmaxf(h2, h3);
+                        const float m2 = fmaxf(fminf(h0, h2), fmaxf(l0, l2));
+                        const float uadd = fmaf(ua, gbeta[g], ue);
+                        const float Ua = Lmin + uadd, Ub = fmaf(-2.f, m2, rb) + uadd;
+                        if (Ua < U1) {
+                            U2 = fminf(U1, Ub);
+                            U1 = Ua;
+                        } else if (Ua < U2) {
+                            U2 = Ua;
+                        }
+                        if (collect) {
+                            const float thr = fminf(U2, Ush);
+                            unsigned msk = 0;
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) msk |= (fmaf(-2.f, vg[j], rb) <= U2 ? 1u : 0u) << j;
-                        while (msk) {
-                            const int j = __ffs(msk) - 1;
-                            msk &= msk - 1;
-                            float vj = vg[0];
-#pragma unroll
-                            for (int k = 1; k < 8; ++k) vj = (j == k) ? vg[k] : vj;
-                            const float L = fmaf(-2.f, vj, rb);
-                            if (L <= U2) {  // U2 may have dropped since the mask was taken
-                                const int cj = c0 + 8 * g + j;
-                                if (collect) {
-                                    const int pos = atomicAdd(cnt + row, 1);
-                                    if (pos < kCandCap) cand[row * kCandCap + pos] = (int32_t)(col0 + cj);
-                                }
-                                const float U = fmaf(up, beta[cj], L + 2.f * ef);
-                                if (U < U1) {
-                                    U2 = U1;
-                                    U1 = U;
-                                } else if (U < U2) {
-                                    U2 = U;
+                            for (int j = 0; j < 8; ++j) msk |= (fmaf(-2.f, vg[j], rb) <= thr ? 1u : 0u) << j;
+                            const int k = __popc(msk);
+                            if (k) {
+                                int pos = atomicAdd(cnt + row, k);
+                                while (msk) {
+                                    const int j = __ffs(msk) - 1;
+                                    msk &= msk - 1;
+                                    if (pos < kCandCap) cand[row * kCandCap + pos] = (int32_t)(col0 + 8 * g + j);
+                                    ++pos;
                                 }
                             }
                         }
                     }
                 }
             }
+            S.ul[p % 3][r][slice] = make_float2(U1, U2);
             tc_fence_before();
         }
     }
@@ -773,10 +835,10 @@ __global__ void __launch_bounds__(256) fallback_merge(const kmx::RowBest* __rest
 
 size_t tc_smem_bytes()
 {
-    // at least 120 KB: one CTA per SM, whose TMEM allocation is all 512
-    // columns (a second CTA would wait in tcgen05.alloc)
+    // at least 96 KB: at most two CTAs per SM, i.e. two 256-column TMEM
+    // allocations (a third CTA would wait in tcgen05.alloc)
     const size_t need = sizeof(TcShared) + 1024;
-    return need < 120 * 1024 ? 120 * 1024 : need;
+    return need < 96 * 1024 ? 96 * 1024 : need;
 }
 
 struct TcBuffers {
@@ -850,7 +912,7 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
     TcBuffers b = tc_carve(s.extra, np_cap, nq_cap, &total);
     const int64_t n2 = np_cap + nq_cap;
     const int64_t tp = (np_cap + kTM - 1) / kTM, tq = (nq_cap + kTM - 1) / kTM;    // row tiles
-    const int64_t ctp = (np_cap + kTN - 1) / kTN, ctq = (nq_cap + kTN - 1) / kTN;  // column tiles
+    const int64_t ctp = (np_cap + kTN - 1) / kTN, ctq = (nq_cap + kTN - 1) / kTN;  // column tiles (the same)
     const size_t smem = tc_smem_bytes();
     cudaError_t e = kmx_once_per_device(kmx_attr_tc_topk, [smem] {
         return cudaFuncSetAttribute(tc_collect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -16,8 +16,9 @@
 // the other two from a quadratic in FP64; the normal is the best-conditioned
 // cross product of two rows of A - l3 I in FP64 (search_common.cuh).  GB300 issues FP64
 // at a small fraction of the FP32 rate and a warp instruction costs the same
-// with 1 or 32 active lanes, so each block first gathers the covariances of
-// its 32 queries in shared memory and then solves them one per lane.
+// with 1 or 32 active lanes, so the search warps store each query's moments
+// and a separate pass solves them one query per thread (every lane busy, no
+// warp of the search waiting for a solve).
 #include "search_common.cuh"
 
 using namespace kmxs;
@@ -32,6 +33,7 @@ constexpr int kQPerBlock = kWarps * kQPerWarp;  // = 32, one per lane of the sol
 struct NormScratch {
     int32_t* cnt;    // [n+1] |I(q)|
     float4* mean;    // [n] P_normal mean minus the query point; w = |P_normal| (int bits)
+    float4* mom;     // [n][3] centred moments s1x s1y s1z sxx | sxy sxz syy syz | szz - - -
 };
 
 NormScratch carve(void* base, int64_t n, size_t* total)
@@ -40,6 +42,7 @@ NormScratch carve(void* base, int64_t n, size_t* total)
     kmx_arena a{static_cast<char*>(base), 0};
     s.cnt = (int32_t*)a.take(sizeof(int32_t) * (n + 1));
     s.mean = (float4*)a.take(sizeof(float4) * (n + 1));
+    s.mom = (float4*)a.take(sizeof(float4) * 3 * (n + 1));
     *total = kmx_align_up(a.used, 256);
     return s;
 }
@@ -109,14 +112,11 @@ struct NormOut {
 };
 
 // Pass 2: CSR lists and centred second moments over P_normal (a warp per
-// query, kQPerWarp queries per warp), then the FP64 eigen-solve, orientation
-// and linearity test with one query per lane of warp 0.
+// query, kQPerWarp consecutive queries per warp); the moments go to scratch
+// for solve_normals.
 __global__ void __launch_bounds__(kThreads) search_fill(GridView g, Radii R, NormScratch s, NormOut o,
                                                         unsigned int* err)
 {
-    __shared__ float sm_mom[9][kQPerBlock];  // s1x s1y s1z sxx sxy sxz syy syz szz
-    __shared__ float sm_q[3][kQPerBlock];
-    __shared__ int sm_qi[kQPerBlock], sm_nN[kQPerBlock];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t total_list = o.offs[o.n_cap];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -125,16 +125,12 @@ __global__ void __launch_bounds__(kThreads) search_fill(GridView g, Radii R, Nor
     }
     const bool write = o.nbr && total_list <= o.nbr_cap;
     const int64_t n_sorted = *g.n_sorted;
-    // uniform over the block: every thread reaches the barriers
     for (int64_t chunk = blockIdx.x; chunk * kQPerBlock < n_sorted; chunk += gridDim.x) {
         StencilCache sc;  // the warp's queries are consecutive in cell order
         for (int k = 0; k < kQPerWarp; ++k) {
             const int slot = warp * kQPerWarp + k;
             const int64_t p = chunk * kQPerBlock + slot;
-            if (p >= n_sorted) {
-                if (lane == 0) sm_qi[slot] = -1;
-                continue;
-            }
+            if (p >= n_sorted) break;
             const float4 q = g.sorted[p];
             const int qi = __float_as_int(q.w);
             const float4 mq = s.mean[qi];
@@ -185,43 +181,38 @@ __global__ void __launch_bounds__(kThreads) search_fill(GridView g, Radii R, Nor
             syz = warp_sum(syz);
             szz = warp_sum(szz);
             if (lane == 0) {
-                sm_mom[0][slot] = s1x;
-                sm_mom[1][slot] = s1y;
-                sm_mom[2][slot] = s1z;
-                sm_mom[3][slot] = sxx;
-                sm_mom[4][slot] = sxy;
-                sm_mom[5][slot] = sxz;
-                sm_mom[6][slot] = syy;
-                sm_mom[7][slot] = syz;
-                sm_mom[8][slot] = szz;
-                sm_q[0][slot] = q.x;
-                sm_q[1][slot] = q.y;
-                sm_q[2][slot] = q.z;
-                sm_qi[slot] = qi;
-                sm_nN[slot] = __float_as_int(mq.w);
+                float4* m = s.mom + 3 * (int64_t)qi;
+                m[0] = make_float4(s1x, s1y, s1z, sxx);
+                m[1] = make_float4(sxy, sxz, syy, syz);
+                m[2] = make_float4(szz, 0.f, 0.f, 0.f);
             }
         }
-        __syncthreads();
-        if (warp == 0 && sm_qi[lane] >= 0) {
-            const int qi = sm_qi[lane];
-            const int nN = sm_nN[lane];
-            const int mF = (int)(o.offs[qi + 1] - o.offs[qi]);
-            uint8_t flag = 0;
-            float4 nout = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (mF >= o.tau_num && nN >= o.tau_num) {
-                float mom[9];
-#pragma unroll
-                for (int i = 0; i < 9; ++i) mom[i] = sm_mom[i][lane];
-                double plin;
-                flag |= 4;
-                if (normal_from_moments(mom, nN, sm_q[0][lane], sm_q[1][lane], sm_q[2][lane], o.vp, &nout, &plin) &&
-                    plin < (double)o.tau_lin)
-                    flag |= 1;
-            }
-            o.normal4[qi] = nout;
-            o.flags[qi] = flag;
+    }
+}
+
+// Pass 3: per bucketed point (one per thread), the FP64 eigen-solve of its
+// moments, orientation toward the viewpoint and the linearity test.
+__global__ void __launch_bounds__(kThreads) solve_normals(GridView g, NormScratch s, NormOut o)
+{
+    const int64_t n_sorted = *g.n_sorted;
+    for (int64_t p = (int64_t)blockIdx.x * kThreads + threadIdx.x; p < n_sorted; p += (int64_t)gridDim.x * kThreads) {
+        const float4 q = g.sorted[p];
+        const int qi = __float_as_int(q.w);
+        const int nN = __float_as_int(s.mean[qi].w);
+        const int mF = (int)(o.offs[qi + 1] - o.offs[qi]);
+        uint8_t flag = 0;
+        float4 nout = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (mF >= o.tau_num && nN >= o.tau_num) {
+            const float4* m = s.mom + 3 * (int64_t)qi;
+            const float4 m0 = m[0], m1 = m[1], m2 = m[2];
+            float mom[9] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w, m2.x};
+            double plin;
+            flag |= 4;
+            if (normal_from_moments(mom, nN, q.x, q.y, q.z, o.vp, &nout, &plin) && plin < (double)o.tau_lin)
+                flag |= 1;
         }
-        __syncthreads();  // the shared moments are rewritten by the next chunk
+        o.normal4[qi] = nout;
+        o.flags[qi] = flag;
     }
 }
 
@@ -283,6 +274,8 @@ cudaError_t kmx_normals_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_params
               prm->tau_lin, {prm->viewpoint[0], prm->viewpoint[1], prm->viewpoint[2]}};
     KMX_COUNT_LAUNCH();
     search_fill<<<kmx_stride_blocks(n, kQPerBlock, ctx->sm_count), kThreads, 0, st>>>(gv, R, s, o, ctx->d_err);
+    KMX_COUNT_LAUNCH();
+    solve_normals<<<kmx_stride_blocks(n, kThreads, ctx->sm_count), kThreads, 0, st>>>(gv, s, o);
     if (nbr) {
         KMX_COUNT_LAUNCH();
         empty_lists_on_overflow<<<kmx_stride_blocks(n + 1, 256, ctx->sm_count), 256, 0, st>>>(offs, n, needed,

@@ -77,6 +77,7 @@ def library():
         "kmx_set_stream": (C.c_int, [vp, vp]),
         "kmx_reserve": (C.c_int, [vp, i64]),
         "kmx_set_match_residency": (C.c_int, [vp, i32]),
+        "kmx_set_match_chunks": (C.c_int, [vp, i32]),
         "kmx_sync": (C.c_int, [vp]),
         "kmx_last_error": (C.c_char_p, [vp]),
         "kmx_launch_count": (C.c_int64, []),
@@ -198,6 +199,11 @@ class Context:
         """CTAs per SM of the exact matcher's tile kernel (1 or 2, 0 = default
         2): 1 leaves half of every SM to kernels on other streams."""
         self._check(self.lib.kmx_set_match_residency(self.h, int(ctas_per_sm)), "kmx_set_match_residency")
+
+    def set_match_chunks(self, chunks_per_cta: int):
+        """Work items per resident CTA of the exact matcher (1..32, 0 =
+        default 8); results do not depend on it."""
+        self._check(self.lib.kmx_set_match_chunks(self.h, int(chunks_per_cta)), "kmx_set_match_chunks")
 
     def reserve(self, nbytes: int):
         self._check(self.lib.kmx_reserve(self.h, int(nbytes)), "kmx_reserve")

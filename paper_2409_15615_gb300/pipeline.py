@@ -124,11 +124,12 @@ class PairState:
                        n_out=self.n_corr if n_out is None else n_out)
         return self
 
-    def capture(self, n_src: int, n_tgt: int, p_src: kmx.Params, p_tgt: kmx.Params, mode: int):
+    def capture(self, n_src: int, n_tgt: int, p_src: kmx.Params, p_tgt: kmx.Params, mode: int, **io):
         """Record one pair as a CUDA graph.  Buffers, grids and the context
         scratch must already have their final sizes (call run_checked
         first), so the recorded sequence allocates nothing.  Replaying the
-        graph reruns the pair on whatever is in self.src.raw / self.tgt.raw."""
+        graph reruns the pair on whatever is in self.src.raw / self.tgt.raw
+        (or the raw_src / raw_tgt / corr_out / n_out given, as for run())."""
         ctx = self.ctx
         cap_stream = torch.cuda.Stream(device=ctx.device)
         old = ctx.stream
@@ -137,16 +138,16 @@ class PairState:
         graph = torch.cuda.CUDAGraph()
         try:
             with torch.cuda.graph(graph, stream=cap_stream):
-                self.run(n_src, n_tgt, p_src, p_tgt, mode)
+                self.run(n_src, n_tgt, p_src, p_tgt, mode, **io)
         finally:
             ctx.set_stream(old)
         return graph
 
-    def run_checked(self, n_src, n_tgt, p_src, p_tgt, mode):
+    def run_checked(self, n_src, n_tgt, p_src, p_tgt, mode, **io):
         """run() then synchronise; grows the neighbour lists and reruns once
         if they did not fit."""
         for attempt in range(2):
-            self.run(n_src, n_tgt, p_src, p_tgt, mode)
+            self.run(n_src, n_tgt, p_src, p_tgt, mode, **io)
             try:
                 self.sync()
                 return self

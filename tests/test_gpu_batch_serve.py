@@ -48,14 +48,19 @@ def _specs():
     return specs
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_batch_graph_equals_single_pairs(torch_cuda, mode):
+@pytest.mark.parametrize("mode,chunks,tc_min", [(0, 0, None), (1, 0, None), (0, 4, 5e7), (0, 16, 1.5e8)])
+def test_batch_graph_equals_single_pairs(torch_cuda, mode, chunks, tc_min):
+    """Every configuration the autotuner can pick (lanes, the exact matcher's
+    chunk size, the size bucket that goes to the tensor-core matcher) gives
+    the one-pair-at-a-time correspondences, replay after replay."""
     torch = torch_cuda
     from paper_2409_15615_gb300.batch import BatchRunner
 
     specs = _specs()
     ref = [_single(torch, sp, mode) for sp in specs]
-    r = BatchRunner(specs, lanes=3, mode=mode).prepare()
+    r = BatchRunner(specs, lanes=3, mode=mode, chunks=chunks, tc_min=tc_min).prepare()
+    if tc_min is not None:
+        assert 0 < sum(m != 0 for m in r.modes) < len(specs)
     r.capture()
     for rep in range(2):  # the graph replays to the same result
         r.corr.fill_(-1)
@@ -99,6 +104,13 @@ def test_serving_alone_equals_in_the_mix(torch_cuda):
         assert np.array_equal(r.corr, alone[r.rid]), "request %d differs in the mix" % r.rid
     st = latency_stats(mix)
     assert st["n"] == len(reqs) and st["p99_ms"] >= st["p50_ms"] > 0
+    # admission by free HBM: a reserve larger than the device holds still
+    # admits one request at a time, and every request completes
+    huge = Server(maps, slots=4, reserve_bytes=1 << 50)
+    done = huge.run([Request(r.rid, r.map_id, r.xyz, r.voxel, r.viewpoint, 0.0) for r in reqs[:4]], realtime=False)
+    assert len(done) == 4 and huge.stats["held_by_memory"] > 0
+    for r in done:
+        assert np.array_equal(r.corr, alone[r.rid])
     # admission by budget: with room for one request at a time they still all complete
     tight = Server(maps, slots=4, budget_bytes=1).run(
         [Request(r.rid, r.map_id, r.xyz, r.voxel, r.viewpoint, 0.0) for r in reqs[:4]], realtime=False)
