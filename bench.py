@@ -319,8 +319,11 @@ def bench_pair(torch, w, args, rank, world, local, headline):
         d = ctx.match_diag(s_.n_cap, t_.n_cap, s_.out["n_valid"], t_.out["n_valid"]).cpu().numpy()
         ctx.sync()
         np_, nq_ = work["match"]["np"], work["match"]["nq"]
+        tiles_p, tiles_q = -(-np_ // 128), -(-nq_ // 128)
         diag = dict(fallback_rows=[int(d[0]), int(d[1])],
-                    candidates_per_row=[float(d[2]) / max(np_, 1), float(d[3]) / max(nq_, 1)])
+                    candidates_per_row=[float(d[2]) / max(np_, 1), float(d[3]) / max(nq_, 1)],
+                    tensor_tile_pairs=[int(d[4]), int(d[5])],
+                    tensor_tile_pair_fraction=float(d[4] + d[5]) / max(2 * tiles_p * tiles_q, 1))
 
     # ---- end to end through host buffers
     e2e = end_to_end(torch, ctx, pair, src, tgt, ps, pt, mode, args.steps, world if headline else 1, w["slots"],

@@ -105,10 +105,13 @@ typedef struct {
 typedef enum {
     KMX_MATCH_FP32_EXACT = 0, /* exact FP32 distances on CUDA cores */
     /* BF16 tensor-core distances (FP32 accumulation) on descriptors sorted
-     * into similar 128-row tiles and centred per tile pair give, per row, a
-     * candidate list that provably holds every column whose exact distance is
-     * at most the row's second-smallest one (certified lower and upper
-     * bounds); the candidates are re-ranked exactly in FP32, and a row whose
+     * into similar 128-row tiles (the leaves of a principal-direction tree)
+     * and centred per tile pair give, per row, a candidate list that provably
+     * holds every column whose exact distance is at most the row's
+     * second-smallest one (certified lower and upper bounds); tile pairs
+     * that the triangle inequality rules out (centre distance minus tile
+     * radius beyond a row's bound) are not computed; the candidates are
+     * re-ranked exactly in FP32, and a row whose
      * list overflows (512) goes through the exact FP32 tiles.  The result
      * equals KMX_MATCH_FP32_EXACT's, including KMX_ERANGE for NaN or
      * infinite values. */
@@ -381,10 +384,12 @@ kmx_status kmx_match(kmx_ctx* ctx, const float* d_desc_p, const int32_t* d_valid
                      const int64_t* d_nq, int32_t mode, kmx_corr* d_out, int64_t cap, int64_t* d_n_out);
 
 /* Diagnostics of the last kmx_match(..., KMX_MATCH_BF16_RERANK, ...) on this
- * context (not from the paper): four device int64 values in d_out: the rows
+ * context (not from the paper): six device int64 values in d_out: the rows
  * of the source and of the target cloud whose candidate list overflowed and
- * went through the exact FP32 tiles, and the candidates collected for the
- * source rows and for the target rows in total.  np_cap, d_np, nq_cap, d_nq
+ * went through the exact FP32 tiles, the candidates collected for the source
+ * rows and for the target rows in total, and the 128 x 128 tile pairs whose
+ * distances went through the tensor cores with source rows and with target
+ * rows (the tiles that the triangle-inequality test could not rule out).  np_cap, d_np, nq_cap, d_nq
  * are those of that call, and no other call may have used the context's
  * scratch since.  KMX_EINVAL if the context's scratch cannot hold a match of
  * these capacities. */

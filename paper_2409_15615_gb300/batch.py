@@ -266,6 +266,7 @@ def time_plain(pairs, reps: int = 3, device: int = 0, mode: int = kmx.MATCH_FP32
     for i, p in enumerate(pairs):
         src_arena[src_off[i]:src_off[i + 1]].copy_(torch.from_numpy(p.src))
         tgt_arena[tgt_off[i]:tgt_off[i + 1]].copy_(torch.from_numpy(p.tgt))
+    calls = []
     for i, p in enumerate(pairs):
         m = mode if tc_min is None else (kmx.MATCH_BF16_RERANK if len(p.src) * len(p.tgt) >= tc_min
                                          else kmx.MATCH_FP32_EXACT)
@@ -273,8 +274,15 @@ def time_plain(pairs, reps: int = 3, device: int = 0, mode: int = kmx.MATCH_FP32
         pt = kmx.params_default(p.voxel, viewpoint=np.float32(p.vp_tgt).tolist())
         args = dict(raw_src=src_arena[src_off[i]:src_off[i + 1]], raw_tgt=tgt_arena[tgt_off[i]:tgt_off[i + 1]],
                     corr_out=corr[out_off[i]:out_off[i + 1]], n_out=n_corr[i:i + 1])
-        st.run_checked(len(p.src), len(p.tgt), ps, pt, m, **args)  # sizes every buffer for this pair
-        graphs.append(st.capture(len(p.src), len(p.tgt), ps, pt, m, **args))
+        calls.append((len(p.src), len(p.tgt), ps, pt, m, args))
+    # every pair once first: the state's buffers and the context's scratch
+    # reach their final sizes before any graph records their addresses (a
+    # buffer grown after a capture would leave that graph pointing at freed
+    # memory)
+    for ns, nt, ps, pt, m, args in calls:
+        st.run_checked(ns, nt, ps, pt, m, **args)
+    for ns, nt, ps, pt, m, args in calls:
+        graphs.append(st.capture(ns, nt, ps, pt, m, **args))
     s = torch.cuda.current_stream(dev)
     t = []
     for _ in range(reps):

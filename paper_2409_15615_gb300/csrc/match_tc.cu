@@ -14,35 +14,48 @@
 // small exactly for the pairs whose ranking matters.
 //
 // Stages (both clouds in one launch each where possible):
-//   coords/keys/sort  per row four statistics (mean bin of each third of the
-//             histogram, log2 of the first third's mass), normalised by their
-//             range over both clouds, 7 bits each -> a 28-bit Morton key;
-//             one stable radix sort over both clouds (a side bit on top).
+//   order     a principal-direction tree over the rows of each cloud: a
+//             node's rows are split at a whole number of 128-row tiles
+//             (left: ceil(len / 256) * 128 rows) by their projection on the
+//             node's principal direction (power iteration on up to 512
+//             sampled rows), level by level with one stable radix sort per
+//             level keyed by (side, node, quantised projection).  Its leaves
+//             are the 128-row tiles, and they are tight: the rows of a tile
+//             are similar descriptors.
 //   pack      one CTA per 128-row tile: the tile centre, then per row
 //             b = y - c in BF16 in the UMMA operand layout (K-major, 8x16-byte
 //             core matrices, no swizzle) with three extra K slots
 //             [sqrt(c') |b|, hi(|b|^2), lo(|b|^2)], and a header with |b|, the
 //             centre and max |b|^2.  A packed tile is one contiguous bulk copy.
-//   nearest   for each row tile, the column tile whose centre is nearest.
-//   collect   one CTA per (128-row tile, chunk of column tiles): per column
-//             tile the CTA writes its row tile re-centred on the column
-//             tile's centre as the A operand [x - c_C, sqrt(c') |x - c_C|,
-//             -1/2, -1/2] while the previous tile pair's MMA runs, one thread
-//             issues tcgen05.mma (kind::f16, BF16, M = N = 128, three K steps
-//             of 16) into one of two TMEM accumulators, and the 4 warps read
-//             the other accumulator with tcgen05.ld.  The accumulator holds
-//             M = a.b + c' |a| |b| - |b|^2 / 2 (approximately), so
-//             L = |a|^2 - 2 M - e is a certified lower bound of the exact
-//             d^2, and L + 4.1 c' |a| |b| + 2 e an upper bound.  Per row the
-//             thread keeps the two smallest upper bounds U1 <= U2 it has seen
-//             and collects every column with L <= U2 (its column index goes
-//             to the row's candidate list).  Every column whose exact
-//             distance is at most the row's second-smallest exact distance
-//             is collected (L <= d <= d(2) <= U2).  A 32-column slice whose
-//             largest M cannot give L <= U2 costs one three-input max per two
-//             values.  The CTA starts with the nearest column tile, so U2 is
-//             tight from the first tile on (outside its chunk that tile only
-//             tightens the bounds).
+//   plan      one CTA per row tile: the column tile with the nearest centre
+//             is compared exactly (FP32, the exact path's arithmetic); its
+//             columns up to each row's second-smallest distance d2 are the
+//             row's first candidates and d2 its first upper bound U.  A
+//             column tile with centre c and radius r = max |y - c| can only
+//             hold a column within U of row x if |x - c| - r <= sqrt(U)
+//             (triangle inequality; tested first for the whole row tile with
+//             its own centre and radius, then row by row, with margins for
+//             FP32 rounding).  The tiles that pass form the row tile's list,
+//             cut into work items of 32 tiles.
+//   collect   persistent CTAs, each taking every gridDim-th work item: per
+//             column tile of the item the CTA writes its row tile re-centred
+//             on the column tile's centre as the A operand
+//             [x - c_C, sqrt(c') |x - c_C|, -1/2, -1/2] while earlier tiles'
+//             products run, one thread issues tcgen05.mma (kind::f16, BF16,
+//             M = N = 128, three K steps of 16) into one of four TMEM
+//             accumulators, and eight warps read them with tcgen05.ld.  The
+//             accumulator holds M = a.b + c' |a| |b| - |b|^2 / 2
+//             (approximately), so L = |a|^2 - 2 M - e is a certified lower
+//             bound of the exact d^2, and L + 4.1 c' |a| |b| + 2 e an upper
+//             bound.  Per row the thread keeps the two smallest upper bounds
+//             U1 <= U2 (starting from the row's bound U) and collects every
+//             column with L <= U2 (its column index goes to the row's
+//             candidate list).  Every column whose exact distance is at most
+//             the row's second-smallest exact distance is collected
+//             (L <= d <= d(2) <= U2).  A 32-column slice whose largest M
+//             cannot give L <= U2 costs one three-input max per two values.
+//             At the end of an item the row's U is lowered to what the item
+//             found (atomic minimum), for the items that start later.
 //   rerank    one warp per row: the exact FP32 distance of every collected
 //             column (sum_h (x_h - y_h)^2, one fused multiply-add per term in
 //             h order: the arithmetic of the exact path), lowest index on
@@ -96,15 +109,18 @@ constexpr int kHdrBmax = kHdrCenter + kCenterStride * 4;
 constexpr int kHdrGBeta = kHdrBmax + 16;
 constexpr int kColBytes = kHdrGBeta + (kTN / 8) * 4;  // 13024, a multiple of 16
 constexpr int kStages = 4;                    // column-tile ring
-constexpr int kThreads = 256;                 // 8 warps: two per TMEM lane quarter
-constexpr int kTmemCols = 256;                // two 128-column FP32 accumulators
-constexpr int kMaxChunks = 8;
+constexpr int kThreads = 512;                 // 16 warps (roles in tc_collect)
+constexpr int kTmemCols = 512;                // four 128-column FP32 accumulators
 constexpr int kCandCap = 512;                 // candidate list per row
+constexpr int kItemTiles = 32;                // column tiles per work item
 constexpr float kC = 0.008f;                  // c' of the bounds
 constexpr float kSqrtC = 0.08944271909999159f;
 constexpr float kUpper = 4.1f * kC;
 constexpr float kEfp = 6e-5f;
-constexpr int kMortonBits = 7;                // per statistic; 4 x 7 = 28 bits
+// margins of the tile test: computed distances and radii are within 3e-5
+// relative of the exact ones (33 FP32 terms), squares within 1e-4
+constexpr float kTolR = 3e-5f;
+constexpr float kTolD = 1e-4f;
 
 static_assert(kColBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
 
@@ -201,17 +217,6 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
     return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// Write 8 operand values (one 16-byte core-matrix row) at chunk c of row r.
-__device__ __forceinline__ void store_operand_chunk(uint8_t* tile, int r, int c, const float* v)
-{
-    uint4 w;
-    w.x = pack_bf16x2(v[0], v[1]);
-    w.y = pack_bf16x2(v[2], v[3]);
-    w.z = pack_bf16x2(v[4], v[5]);
-    w.w = pack_bf16x2(v[6], v[7]);
-    *reinterpret_cast<uint4*>(tile + (r / 8) * kGroupStride + (r % 8) * 16 + c * kCoreStride) = w;
-}
-
 // Write one 48-value operand row (values v[0..47]) at row r of a tile in the
 // core-matrix layout.
 __device__ __forceinline__ void store_operand_row(uint8_t* tile, int r, const float (&v)[kK])
@@ -229,108 +234,275 @@ __device__ __forceinline__ void store_operand_row(uint8_t* tile, int r, const fl
 }
 
 // ---------------------------------------------------------------------------
-// locality order
+// locality order: a principal-direction tree
 // ---------------------------------------------------------------------------
 
-// The four statistics of a descriptor row: the mean bin of each third of the
-// histogram (0 for an empty third) and log2 of the first third's mass
-// (at least 0).  All are >= 0, so their float bits order like the values.
-__device__ __forceinline__ void row_stats(const float* __restrict__ row, float (&s)[4])
+constexpr int kTreeSample = 512;  // rows sampled per node for its direction
+constexpr int kTreeIters = 6;     // power iterations
+constexpr int kTreeThreads = 256;
+constexpr int kColSplit = 7;      // partial sums per column in the sample reductions (7 x 33 <= 256)
+constexpr int kDirStride = 68;    // floats per node: centre (33), direction (33), projection range (2)
+constexpr size_t kTreeSmem = sizeof(float) * kTreeSample * KMX_DESC_DIM;
+
+// Rows of the left child of a node of `len` rows: a whole number of tiles,
+// ceil(len / 256) * 128; a node of at most 128 rows is a leaf (its left
+// child is itself, its right child empty).
+__host__ __device__ __forceinline__ int64_t tree_left(int64_t len)
 {
-    float m0 = 0.f;
-#pragma unroll
-    for (int t = 0; t < 3; ++t) {
-        float w = 0.f, m = 0.f;
-#pragma unroll
-        for (int b = 0; b < 11; ++b) {
-            const float h = __ldg(row + 11 * t + b);
-            w += h;
-            m = fmaf((float)b, h, m);
-        }
-        s[t] = w > 0.f ? fmaxf(m / w, 0.f) : 0.f;
-        if (t == 0) m0 = w;
-    }
-    s[3] = log2f(fmaxf(m0, 1.f));
+    return len > kTM ? (len + 2 * kTM - 1) / (2 * kTM) * kTM : len;
 }
 
-// Per row of both clouds: the statistics, their range (atomic min / max of
-// the float bits) and a non-finite check.  Rows e < np_cap are the source
-// cloud, the others the target cloud.
-__global__ void __launch_bounds__(256) tc_coords(const float* __restrict__ P, int64_t np_cap,
-                                                 const int64_t* d_np, const float* __restrict__ Q, int64_t nq_cap,
-                                                 const int64_t* d_nq, float4* __restrict__ coords,
-                                                 unsigned int* __restrict__ range, unsigned int* err)
+// Levels until every node is a leaf.
+int tree_levels(int64_t n)
 {
-    const int64_t np = kmx_count(d_np, np_cap), nq = kmx_count(d_nq, nq_cap);
-    float lo[4] = {FLT_MAX, FLT_MAX, FLT_MAX, FLT_MAX}, hi[4] = {0.f, 0.f, 0.f, 0.f};
-    bool bad = false;
-    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < np_cap + nq_cap;
-         e += (int64_t)gridDim.x * 256) {
-        const bool side = e >= np_cap;
-        const int64_t r = side ? e - np_cap : e;
-        if (r >= (side ? nq : np)) continue;
-        const float* row = (side ? Q : P) + r * KMX_DESC_STRIDE;
-#pragma unroll
-        for (int h = 0; h < KMX_DESC_DIM; ++h) bad |= !isfinite(__ldg(row + h));
-        float s[4];
-        row_stats(row, s);
-        coords[e] = make_float4(s[0], s[1], s[2], s[3]);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            lo[k] = fminf(lo[k], s[k]);
-            hi[k] = fmaxf(hi[k], s[k]);
-        }
-    }
-    if (bad) kmx_raise(err, KMX_DERR_RANGE);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const unsigned l = __reduce_min_sync(0xffffffffu, __float_as_uint(lo[k]));
-        const unsigned h = __reduce_max_sync(0xffffffffu, __float_as_uint(hi[k]));
-        if ((threadIdx.x & 31) == 0) {
-            atomicMin(range + k, l);
-            atomicMax(range + 4 + k, h);
-        }
-    }
+    const int64_t tiles = (n + kTM - 1) / kTM;
+    int l = 0;
+    while ((int64_t{1} << l) < tiles) ++l;
+    return l;
 }
 
-__device__ __forceinline__ uint32_t spread4(uint32_t v)  // 7 bits -> every 4th bit
+// (start, len) of node k of level l over a side of n rows.
+__device__ __forceinline__ void tree_node(int64_t n, int l, int64_t k, int64_t& start, int64_t& len)
 {
-    uint32_t r = 0;
-#pragma unroll
-    for (int b = 0; b < kMortonBits; ++b) r |= ((v >> b) & 1u) << (4 * b);
-    return r;
-}
-
-// Sort keys: side bit 29, "past the count" bit 28, 28-bit Morton code.
-__global__ void __launch_bounds__(256) tc_keys(int64_t np_cap, const int64_t* d_np, int64_t nq_cap,
-                                               const int64_t* d_nq, const float4* __restrict__ coords,
-                                               const unsigned int* __restrict__ range, uint32_t* __restrict__ keys,
-                                               int32_t* __restrict__ vals)
-{
-    const int64_t np = kmx_count(d_np, np_cap), nq = kmx_count(d_nq, nq_cap);
-    const float scale = (float)((1 << kMortonBits) - 1);
-    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < np_cap + nq_cap;
-         e += (int64_t)gridDim.x * 256) {
-        const bool side = e >= np_cap;
-        const int64_t r = side ? e - np_cap : e;
-        uint32_t key = (uint32_t)side << 29;
-        if (r < (side ? nq : np)) {
-            const float4 c = coords[e];
-            const float cs[4] = {c.x, c.y, c.z, c.w};
-            uint32_t m = 0;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float lo = __uint_as_float(range[k]), hi = __uint_as_float(range[4 + k]);
-                const float t = hi > lo ? (cs[k] - lo) / (hi - lo) : 0.f;
-                const uint32_t q = (uint32_t)fminf(fmaxf(t * scale + 0.5f, 0.f), scale);
-                m |= spread4(q) << (3 - k);
-            }
-            key |= m;
+    start = 0;
+    len = n;
+    for (int b = l - 1; b >= 0; --b) {
+        const int64_t h = tree_left(len);
+        if ((k >> b) & 1) {
+            start += h;
+            len -= h;
         } else {
-            key |= 1u << 28;
+            len = h;
         }
-        keys[e] = key;
-        vals[e] = (int32_t)r;
+    }
+}
+
+// The level-l node holding sorted position pos (< n), with its (start, len).
+__device__ __forceinline__ int64_t tree_node_of(int64_t n, int l, int64_t pos, int64_t& start, int64_t& len)
+{
+    start = 0;
+    len = n;
+    int64_t k = 0;
+    for (int b = 0; b < l; ++b) {
+        const int64_t h = tree_left(len);
+        if (pos - start >= h) {
+            k = 2 * k + 1;
+            start += h;
+            len -= h;
+        } else {
+            k = 2 * k;
+            len = h;
+        }
+    }
+    return k;
+}
+
+// Sorted positions of both clouds start as the identity: entries e < np_cap
+// are the source cloud, the others the target cloud.
+__global__ void __launch_bounds__(256) tree_init(int64_t np_cap, int64_t n2, int32_t* __restrict__ vals)
+{
+    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < n2; e += (int64_t)gridDim.x * 256)
+        vals[e] = (int32_t)(e < np_cap ? e : e - np_cap);
+}
+
+// One CTA per (node of this level, side): the node's centre and principal
+// direction from up to kTreeSample of its rows (evenly spaced in its current
+// order), and the range of their projections.  Leaves do nothing.
+__global__ void __launch_bounds__(kTreeThreads) tree_dir(const float* __restrict__ P, int64_t np_cap,
+                                                         const int64_t* d_np, const float* __restrict__ Q,
+                                                         int64_t nq_cap, const int64_t* d_nq,
+                                                         const int32_t* __restrict__ vals, int level,
+                                                         float* __restrict__ dirs)
+{
+    extern __shared__ float tree_smem[];
+    float(*xs)[KMX_DESC_DIM] = reinterpret_cast<float(*)[KMX_DESC_DIM]>(tree_smem);
+    __shared__ float part[kColSplit][KMX_DESC_DIM];
+    __shared__ float cvec[KMX_DESC_DIM], vvec[KMX_DESC_DIM], uvec[KMX_DESC_DIM];
+    __shared__ float w[kTreeSample];
+    __shared__ float redf[2][kTreeThreads / 32];
+    __shared__ int redi[kTreeThreads / 32];
+    __shared__ float s_scale;
+    __shared__ int s_far;
+    const int side = blockIdx.y;
+    const int64_t k = blockIdx.x;
+    const int64_t n = side ? kmx_count(d_nq, nq_cap) : kmx_count(d_np, np_cap);
+    int64_t start, len;
+    tree_node(n, level, k, start, len);
+    if (len <= kTM) return;
+    const float* X = side ? Q : P;
+    const int32_t* perm = vals + (side ? np_cap : 0);
+    const int m = (int)min(len, (int64_t)kTreeSample);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int idx = tid; idx < m * KMX_DESC_DIM; idx += kTreeThreads) {
+        const int i = idx / KMX_DESC_DIM, h = idx - i * KMX_DESC_DIM;
+        const int64_t pos = start + (int64_t)i * len / m;
+        xs[i][h] = __ldg(X + (int64_t)perm[pos] * KMX_DESC_STRIDE + h);
+    }
+    __syncthreads();
+    // centre
+    const int cpart = tid / KMX_DESC_DIM, ch = tid - cpart * KMX_DESC_DIM;
+    if (cpart < kColSplit) {
+        float acc = 0.f;
+        for (int i = cpart; i < m; i += kColSplit) acc += xs[i][ch];
+        part[cpart][ch] = acc;
+    }
+    __syncthreads();
+    if (tid < KMX_DESC_DIM) {
+        float acc = 0.f;
+#pragma unroll
+        for (int c = 0; c < kColSplit; ++c) acc += part[c][tid];
+        cvec[tid] = acc / (float)m;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < m * KMX_DESC_DIM; idx += kTreeThreads) {
+        const int i = idx / KMX_DESC_DIM, h = idx - i * KMX_DESC_DIM;
+        xs[i][h] -= cvec[h];
+    }
+    __syncthreads();
+    // start from the sampled row farthest from the centre (lowest index on ties)
+    {
+        float best = -1.f;
+        int bi = 0;
+        for (int i = tid; i < m; i += kTreeThreads) {
+            float acc = 0.f;
+#pragma unroll
+            for (int h = 0; h < KMX_DESC_DIM; ++h) acc = fmaf(xs[i][h], xs[i][h], acc);
+            if (acc > best) {
+                best = acc;
+                bi = i;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            redf[0][warp] = best;
+            redi[warp] = bi;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            float b = redf[0][0];
+            int i0 = redi[0];
+            for (int q = 1; q < kTreeThreads / 32; ++q)
+                if (redf[0][q] > b || (redf[0][q] == b && redi[q] < i0)) {
+                    b = redf[0][q];
+                    i0 = redi[q];
+                }
+            s_far = i0;
+        }
+        __syncthreads();
+        if (tid < KMX_DESC_DIM) uvec[tid] = xs[s_far][tid];
+    }
+    // power iterations v <- S^T S v / |S^T S v| on the centred sample S
+    for (int it = 0; it <= kTreeIters; ++it) {
+        __syncthreads();
+        if (tid == 0) {
+            float nn = 0.f;
+            for (int h = 0; h < KMX_DESC_DIM; ++h) nn = fmaf(uvec[h], uvec[h], nn);
+            s_scale = nn > 0.f ? rsqrtf(nn) : 0.f;
+        }
+        __syncthreads();
+        if (tid < KMX_DESC_DIM) vvec[tid] = s_scale > 0.f ? uvec[tid] * s_scale : (tid == 0 ? 1.f : 0.f);
+        __syncthreads();
+        if (it == kTreeIters) break;
+        for (int i = tid; i < m; i += kTreeThreads) {
+            float acc = 0.f;
+#pragma unroll
+            for (int h = 0; h < KMX_DESC_DIM; ++h) acc = fmaf(xs[i][h], vvec[h], acc);
+            w[i] = acc;
+        }
+        __syncthreads();
+        if (cpart < kColSplit) {
+            float acc = 0.f;
+            for (int i = cpart; i < m; i += kColSplit) acc = fmaf(w[i], xs[i][ch], acc);
+            part[cpart][ch] = acc;
+        }
+        __syncthreads();
+        if (tid < KMX_DESC_DIM) {
+            float acc = 0.f;
+#pragma unroll
+            for (int c = 0; c < kColSplit; ++c) acc += part[c][tid];
+            uvec[tid] = acc;
+        }
+    }
+    // range of the sample's projections
+    float lo = INFINITY, hi = -INFINITY;
+    for (int i = tid; i < m; i += kTreeThreads) {
+        float acc = 0.f;
+#pragma unroll
+        for (int h = 0; h < KMX_DESC_DIM; ++h) acc = fmaf(xs[i][h], vvec[h], acc);
+        lo = fminf(lo, acc);
+        hi = fmaxf(hi, acc);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+        redf[0][warp] = lo;
+        redf[1][warp] = hi;
+    }
+    __syncthreads();
+    float* d = dirs + (((int64_t)side << level) + k) * kDirStride;
+    if (tid < KMX_DESC_DIM) {
+        d[tid] = cvec[tid];
+        d[KMX_DESC_DIM + tid] = vvec[tid];
+    }
+    if (tid == 0) {
+        for (int q = 1; q < kTreeThreads / 32; ++q) {
+            lo = fminf(lo, redf[0][q]);
+            hi = fmaxf(hi, redf[1][q]);
+        }
+        d[2 * KMX_DESC_DIM] = fminf(lo, redf[0][0]);
+        d[2 * KMX_DESC_DIM + 1] = fmaxf(hi, redf[1][0]);
+    }
+}
+
+// Sort key of every sorted position for this level: side (top bit), node
+// index (level bits), then the row's projection on its node's direction,
+// quantised over the sample's range (0 in a leaf).  Positions past a side's
+// count get the side's largest key, so they stay behind its rows.
+__global__ void __launch_bounds__(256) tree_key(const float* __restrict__ P, int64_t np_cap, const int64_t* d_np,
+                                                const float* __restrict__ Q, int64_t nq_cap, const int64_t* d_nq,
+                                                const int32_t* __restrict__ vals, int level, int key_bits,
+                                                const float* __restrict__ dirs, uint32_t* __restrict__ keys)
+{
+    const int64_t np = kmx_count(d_np, np_cap), nq = kmx_count(d_nq, nq_cap);
+    const int pbits = key_bits - 1 - level;
+    const int qbits = pbits < 22 ? pbits : 22;
+    const float qmax = (float)((1u << qbits) - 1u);
+    const uint32_t side_max = (1u << (key_bits - 1)) - 1u;
+    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < np_cap + nq_cap; e += (int64_t)gridDim.x * 256) {
+        const int side = e >= np_cap;
+        const int64_t pos = side ? e - np_cap : e;
+        const int64_t n = side ? nq : np;
+        uint32_t key;
+        if (pos >= n) {
+            key = side_max;
+        } else {
+            int64_t start, len;
+            const int64_t k = tree_node_of(n, level, pos, start, len);
+            uint32_t q = 0;
+            if (len > kTM) {
+                const float* d = dirs + (((int64_t)side << level) + k) * kDirStride;
+                const float* x = (side ? Q : P) + (int64_t)vals[e] * KMX_DESC_STRIDE;
+                float p = 0.f;
+#pragma unroll
+                for (int h = 0; h < KMX_DESC_DIM; ++h) p = fmaf(__ldg(x + h) - d[h], d[KMX_DESC_DIM + h], p);
+                const float lo = d[2 * KMX_DESC_DIM], hi = d[2 * KMX_DESC_DIM + 1];
+                const float t = hi > lo ? (p - lo) / (hi - lo) * qmax : 0.f;
+                q = (uint32_t)fminf(fmaxf(t, 0.f), qmax) << (pbits - qbits);
+            }
+            key = ((uint32_t)k << pbits) | q;
+        }
+        keys[e] = ((uint32_t)side << (key_bits - 1)) | key;
     }
 }
 
@@ -340,10 +512,12 @@ __global__ void __launch_bounds__(256) tc_keys(int64_t np_cap, const int64_t* d_
 
 // Rows of the tile are sorted positions [128 t, 128 t + 128) of the cloud;
 // perm maps a sorted position to the descriptor row.  Writes the packed
-// column tile and the centre (also to centers[t]).
+// column tile, and to centers[t] the centre (33 values) and the largest
+// |y - c|^2 of the tile (at 33).  A non-finite descriptor value raises
+// KMX_DERR_RANGE.
 __global__ void __launch_bounds__(kTN) tc_pack(const float* __restrict__ desc, const int32_t* __restrict__ perm,
                                                int64_t n_cap, const int64_t* d_n, uint8_t* __restrict__ out,
-                                               float* __restrict__ centers)
+                                               float* __restrict__ centers, unsigned int* err)
 {
     __shared__ float rows_s[kTN][KMX_DESC_DIM + 1];
     __shared__ float cen[kCenterStride];
@@ -359,6 +533,10 @@ __global__ void __launch_bounds__(kTN) tc_pack(const float* __restrict__ desc, c
         const float* row = desc + (int64_t)perm[r] * KMX_DESC_STRIDE;
 #pragma unroll
         for (int h = 0; h < KMX_DESC_DIM; ++h) y[h] = __ldg(row + h);
+        bool bad = false;
+#pragma unroll
+        for (int h = 0; h < KMX_DESC_DIM; ++h) bad |= !isfinite(y[h]);
+        if (bad) kmx_raise(err, KMX_DERR_RANGE);
     } else {
 #pragma unroll
         for (int h = 0; h < KMX_DESC_DIM; ++h) y[h] = 0.f;
@@ -406,6 +584,7 @@ __global__ void __launch_bounds__(kTN) tc_pack(const float* __restrict__ desc, c
     }
     __syncthreads();
     if (tid < 4) reinterpret_cast<float*>(tile + kHdrBmax)[tid] = tid == 0 ? __uint_as_float(bmax2) : 0.f;
+    if (tid == 0) centers[t * kCenterStride + KMX_DESC_DIM] = __uint_as_float(bmax2);
     // the largest |b| of each group of 8 rows (lanes 8k .. 8k + 7 of a warp)
     float gb = valid ? beta : 0.f;
 #pragma unroll
@@ -413,300 +592,545 @@ __global__ void __launch_bounds__(kTN) tc_pack(const float* __restrict__ desc, c
     if ((tid & 7) == 0) reinterpret_cast<float*>(tile + kHdrGBeta)[tid >> 3] = gb;
 }
 
-// For each tile of X (its row tiles are its column tiles): the column tile
-// of Y with the nearest centre (ties to the lower tile).  One warp per tile.
-__global__ void __launch_bounds__(256) tc_nearest(const float* __restrict__ cx, int64_t nx_cap, const int64_t* d_nx,
-                                                  const float* __restrict__ cy, int64_t ny_cap, const int64_t* d_ny,
-                                                  int32_t* __restrict__ nearest)
+// ---------------------------------------------------------------------------
+// plan: first candidates, first bounds and the column tiles each row tile needs
+// ---------------------------------------------------------------------------
+
+// False only when no column of a tile with centre distance `dist` and radius
+// `rad` can lie within squared distance u2: for every column y,
+// |x - y| >= |x - c| - |y - c| >= dist - rad (margins for FP32 rounding).
+__device__ __forceinline__ bool tile_may_hold(float dist, float rad, float u2)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    const int64_t ntx = (kmx_count(d_nx, nx_cap) + kTN - 1) / kTN;
-    const int64_t nty = (kmx_count(d_ny, ny_cap) + kTN - 1) / kTN;
-    if (t >= ntx) return;
-    float c[KMX_DESC_DIM];
+    const float g = dist * (1.f - kTolR) - rad * (1.f + kTolR);
+    return !(g > 0.f && g * g * (1.f - kTolD) > u2);
+}
+
+// One CTA of 128 threads (thread = row) per row tile rt of X, with cenX and
+// cenY the centres and squared radii of both clouds' tiles (tc_pack).
+//   1. the column tile cs with the centre nearest to the row tile's centre
+//      (lowest index on ties);
+//   2. each row's exact FP32 distances to the columns of cs (the exact
+//      path's arithmetic): its second-smallest d2 over distinct columns is
+//      an upper bound of the row's d(2); the columns with distance <= d2 are
+//      its first candidates (cnt[row] = their number) and ub[row] = d2;
+//   3. every other column tile that tile_may_hold for some row of the tile
+//      (first for the whole tile: centre distance minus both radii against
+//      the largest d2, then row by row), in increasing order, into
+//      need[rt * need_stride ...]; nneed[rt] = their number, and the list is
+//      cut into items (rt, first) of kItemTiles tiles appended to `items`.
+__global__ void __launch_bounds__(kTM) tc_plan(const float* __restrict__ X, const int32_t* __restrict__ permX,
+                                               int64_t nx_cap, const int64_t* d_nx, const float* __restrict__ cenX,
+                                               const float* __restrict__ Y, const int32_t* __restrict__ permY,
+                                               int64_t ny_cap, const int64_t* d_ny, const float* __restrict__ cenY,
+                                               int32_t* __restrict__ cand, int32_t* __restrict__ cnt,
+                                               float* __restrict__ ub, int32_t* __restrict__ need,
+                                               int64_t need_stride, int32_t* __restrict__ nneed,
+                                               int2* __restrict__ items, int* __restrict__ n_items)
+{
+    __shared__ float ys[kTN][KMX_DESC_DIM];
+    __shared__ float sc[kTN][kCenterStride];  // surviving tiles: centre, radius at [33]
+    __shared__ int32_t sid[kTN];
+    __shared__ float cR[KMX_DESC_DIM];
+    __shared__ unsigned needbits[kTN / 32];
+    __shared__ int wcnt[kTN / 32];
+    __shared__ float redf[kTN / 32];
+    __shared__ int redi[kTN / 32];
+    __shared__ int s_cs, s_total;
+    __shared__ float s_maxu;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t rows = kmx_count(d_nx, nx_cap), cols = kmx_count(d_ny, ny_cap);
+    const int64_t rt = blockIdx.x;
+    if (rt * kTM >= rows || cols <= 0) return;
+    const int64_t n_ct = (cols + kTN - 1) / kTN;
+    const int64_t xrow = rt * kTM + tid;
+    const bool valid = xrow < rows;
+    float x[KMX_DESC_DIM];
+    {
+        const float* xr = valid ? X + (int64_t)permX[xrow] * KMX_DESC_STRIDE : nullptr;
 #pragma unroll
-    for (int h = 0; h < KMX_DESC_DIM; ++h) c[h] = cx[t * kCenterStride + h];
-    float best = INFINITY;
-    int bi = 0x7fffffff;
-    for (int64_t u = lane; u < nty; u += 32) {
-        float d = 0.f;
+        for (int h = 0; h < KMX_DESC_DIM; ++h) x[h] = valid ? __ldg(xr + h) : 0.f;
+    }
+    if (tid < KMX_DESC_DIM) cR[tid] = cenX[rt * kCenterStride + tid];
+    const float rR = sqrtf(cenX[rt * kCenterStride + KMX_DESC_DIM]);
+    __syncthreads();
+    // 1. nearest column tile
+    {
+        float best = INFINITY;
+        int bi = 0x7fffffff;
+        for (int64_t u = tid; u < n_ct; u += kTM) {
+            const float* c = cenY + u * kCenterStride;
+            float d = 0.f;
 #pragma unroll
-        for (int h = 0; h < KMX_DESC_DIM; ++h) {
-            const float e = c[h] - cy[u * kCenterStride + h];
-            d = fmaf(e, e, d);
+            for (int h = 0; h < KMX_DESC_DIM; ++h) {
+                const float e = cR[h] - __ldg(c + h);
+                d = fmaf(e, e, d);
+            }
+            if (d < best) {
+                best = d;
+                bi = (int)u;
+            }
         }
-        if (d < best) {
-            best = d;
-            bi = (int)u;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob < best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            redf[warp] = best;
+            redi[warp] = bi;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            float b = redf[0];
+            int i0 = redi[0];
+            for (int q = 1; q < kTN / 32; ++q)
+                if (redf[q] < b || (redf[q] == b && redi[q] < i0)) {
+                    b = redf[q];
+                    i0 = redi[q];
+                }
+            s_cs = i0 == 0x7fffffff ? 0 : i0;
+            s_total = 0;
+        }
+        __syncthreads();
+    }
+    const int64_t cs = s_cs;
+    {
+        const int64_t yp = cs * kTN + tid;
+        const bool yv = yp < cols;
+        const float* yr = yv ? Y + (int64_t)permY[yp] * KMX_DESC_STRIDE : nullptr;
+#pragma unroll
+        for (int h = 0; h < KMX_DESC_DIM; ++h) ys[tid][h] = yv ? __ldg(yr + h) : 0.f;
+    }
+    __syncthreads();
+    // 2. exact distances to the nearest tile
+    const int ncol = (int)min((int64_t)kTN, cols - cs * kTN);
+    float d2 = INFINITY;
+    if (valid) {
+        float d1 = INFINITY;
+        for (int j = 0; j < ncol; ++j) {
+            float acc = 0.f;
+#pragma unroll
+            for (int h = 0; h < KMX_DESC_DIM; ++h) {
+                const float e = x[h] - ys[j][h];
+                acc = fmaf(e, e, acc);
+            }
+            if (acc < d1) {
+                d2 = d1;
+                d1 = acc;
+            } else if (acc < d2) {
+                d2 = acc;
+            }
+        }
+        int k = 0;
+        for (int j = 0; j < ncol; ++j) {
+            float acc = 0.f;
+#pragma unroll
+            for (int h = 0; h < KMX_DESC_DIM; ++h) {
+                const float e = x[h] - ys[j][h];
+                acc = fmaf(e, e, acc);
+            }
+            if (acc <= d2) cand[xrow * kCandCap + k++] = (int32_t)(cs * kTN + j);
+        }
+        cnt[xrow] = k;
+        ub[xrow] = d2;
+    }
+    {
+        float mu = valid ? d2 : 0.f;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) mu = fmaxf(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+        if (lane == 0) redf[warp] = mu;
+        __syncthreads();
+        if (tid == 0) s_maxu = fmaxf(fmaxf(redf[0], redf[1]), fmaxf(redf[2], redf[3]));
+        __syncthreads();
+    }
+    const float maxu = s_maxu;
+    // 3. the other column tiles, 128 at a time
+    for (int64_t base = 0; base < n_ct; base += kTN) {
+        const int64_t u = base + tid;
+        bool surv = false;
+        float ru = 0.f;
+        if (u < n_ct && u != cs) {
+            const float* c = cenY + u * kCenterStride;
+            float d = 0.f;
+#pragma unroll
+            for (int h = 0; h < KMX_DESC_DIM; ++h) {
+                const float e = cR[h] - __ldg(c + h);
+                d = fmaf(e, e, d);
+            }
+            ru = sqrtf(__ldg(c + KMX_DESC_DIM));
+            surv = tile_may_hold(sqrtf(d), rR + ru, maxu);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, surv);
+        if (lane == 0) wcnt[warp] = __popc(bal);
+        if (tid < kTN / 32) needbits[tid] = 0u;
+        __syncthreads();
+        int off = 0;
+        for (int q = 0; q < warp; ++q) off += wcnt[q];
+        const int nsurv = wcnt[0] + wcnt[1] + wcnt[2] + wcnt[3];
+        if (surv) {
+            const int idx = off + __popc(bal & ((1u << lane) - 1u));
+            sid[idx] = (int32_t)u;
+            const float* c = cenY + u * kCenterStride;
+#pragma unroll
+            for (int h = 0; h < KMX_DESC_DIM; ++h) sc[idx][h] = __ldg(c + h);
+            sc[idx][KMX_DESC_DIM] = ru;
+        }
+        __syncthreads();
+        for (int q = 0; q < nsurv; ++q) {
+            bool nd = false;
+            if (valid) {
+                float d = 0.f;
+#pragma unroll
+                for (int h = 0; h < KMX_DESC_DIM; ++h) {
+                    const float e = x[h] - sc[q][h];
+                    d = fmaf(e, e, d);
+                }
+                nd = tile_may_hold(sqrtf(d), sc[q][KMX_DESC_DIM], d2);
+            }
+            const unsigned b = __ballot_sync(0xffffffffu, nd);
+            if (lane == 0 && b) atomicOr(&needbits[q >> 5], 1u << (q & 31));
+        }
+        __syncthreads();
+        if (tid < nsurv) {
+            const unsigned word = needbits[tid >> 5];
+            if ((word >> (tid & 31)) & 1u) {
+                int rank = __popc(word & ((1u << (tid & 31)) - 1u));
+                for (int q = 0; q < (tid >> 5); ++q) rank += __popc(needbits[q]);
+                need[rt * need_stride + s_total + rank] = sid[tid];
+            }
+        }
+        __syncthreads();
+        if (tid == 0)
+            s_total += __popc(needbits[0]) + __popc(needbits[1]) + __popc(needbits[2]) + __popc(needbits[3]);
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const int total = s_total;
+        nneed[rt] = total;
+        const int nit = (total + kItemTiles - 1) / kItemTiles;
+        if (nit > 0) {
+            const int b = atomicAdd(n_items, nit);
+            for (int i = 0; i < nit; ++i) items[b + i] = make_int2((int)rt, i * kItemTiles);
         }
     }
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob < best || (ob == best && oi < bi)) {
-            best = ob;
-            bi = oi;
-        }
-    }
-    if (lane == 0) nearest[t] = bi == 0x7fffffff ? 0 : bi;
 }
 
 // ---------------------------------------------------------------------------
 // tensor-core candidate collection
 // ---------------------------------------------------------------------------
 
+constexpr int kAStages = 3;   // re-centred row tiles in flight
+constexpr int kAccBufs = 4;   // TMEM accumulators (4 x 128 columns: the whole TMEM)
+
 struct TcShared {
-    uint8_t a[2][kOpBytesA];
+    uint8_t a[kAStages][kOpBytesA];
     uint8_t b[kStages][kColBytes];
-    // per row and step (modulo 3: written one step ahead of its reads, while
-    // the slowest thread may still read the previous step's): |a|^2 - e,
-    // the factor c' |a| of the upper bounds, 2 e, and the second-smallest
-    // upper bound over the row's two column slices as of three steps earlier
-    float4 rowc[3][kTM];
-    float2 ul[3][kTM][2];  // (U1, U2) of the two column slices of every row, by step modulo 3
-    uint64_t bar_b[kStages], bar_mma[2];
+    // per row and A stage: |a|^2 - e, the factor c' |a| of the upper bounds, 2 e
+    float4 rowc[kAStages][kTM];
+    float gb[kAStages][kTN / 8];  // the column tile's largest |b| per group of 8
+    float2 ul[kTM][2];            // latest (U1, U2) of the two column slices of every row
+    uint64_t full_b[kStages], empty_b[kStages];
+    uint64_t full_a[kAStages], empty_a[kAStages];
+    uint64_t acc_full[kAccBufs], acc_empty[kAccBufs];
     uint32_t tmem;
+    int failed;
 };
 
-// Threads (8 warps) have two roles per step (one 128-column tile):
-//   re-centring  thread t writes values 16 (t & 1) .. of row t >> 1 of the A
-//                operand (the t & 1 == 1 thread values 16 .. 32 and the three
-//                slots); the two threads of a row are neighbouring lanes and
-//                add their partial |x - c|^2 with one shuffle;
-//   epilogue     warp w reads TMEM lanes (rows) 32 (w & 3) .. + 31 and
-//                accumulator columns 64 (w >> 2) .. + 63.  The two threads of
-//                a row keep their own bounds and candidate decisions over
-//                their own columns (disjoint sets, one list per row).
-// Two CTAs per SM (each holds half of the TMEM), so that one CTA's
-// re-centring and barrier overlap the other's epilogue.  One barrier per
-// step: it publishes the A operand to the MMA and orders the previous
-// step's accumulator reads before the next MMA into that accumulator.
-//
-// The grid is sized from the capacities; the (row tile, column chunk) split
-// of the actual counts is decided here (kmx::work_chunks).
-__global__ void __launch_bounds__(kThreads, 2) tc_collect(const float* __restrict__ X,
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Epilogue warps only (warps 8..15).
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+// Persistent CTAs; CTA b takes the work items b, b + gridDim.x, ... (an item
+// is up to kItemTiles column tiles of one row tile's list).  Warp roles (16
+// warps), each running its own loop over the CTA's sequence of column tiles
+// and handing tiles on through mbarriers, so that copying, re-centring,
+// tensor-core products and the epilogue of different tiles overlap:
+//   warp 1 (lane 0)   producer: bulk-copies column tiles into a 4-stage ring;
+//   warps 4..7        re-centring: thread = row; the row re-centred on the
+//                     column tile's centre as the A operand (3-stage ring),
+//                     and the row's constants of the bounds;
+//   warp 0 (lane 0)   issues tcgen05.mma (M = N = 128, three K steps) into one
+//                     of four TMEM accumulators and commits to the barriers
+//                     that free the accumulator's reader, the A stage and the
+//                     B stage;
+//   warps 8..15       epilogue: warp w reads TMEM lanes 32 (w & 3) .. + 31,
+//                     columns 64 ((w - 8) >> 2) .. + 63 of the accumulator.
+// The two epilogue threads of a row keep their own upper bounds over their
+// own columns and publish them after every tile; each combines its own with
+// the other's latest published pair (their column sets are disjoint, so any
+// snapshot is a valid bound).  Both start an item from the row's bound U
+// counted as two columns at U (the two best columns of the plan's tile,
+// which no item holds); at an item boundary the epilogue warps meet on a
+// named barrier, so that no thread reads a bound of the previous item's row.
+__global__ void __launch_bounds__(kThreads, 1) tc_collect(const float* __restrict__ X,
                                                          const int32_t* __restrict__ permX, int64_t nx_cap,
                                                          const int64_t* d_nx, const uint8_t* __restrict__ packY,
-                                                         int64_t ny_cap, const int64_t* d_ny,
-                                                         const int32_t* __restrict__ nearest, int target_ctas,
-                                                         int32_t* __restrict__ cand, int32_t* __restrict__ cnt,
-                                                         unsigned int* err)
+                                                         const int32_t* __restrict__ need, int64_t need_stride,
+                                                         const int32_t* __restrict__ nneed,
+                                                         const int2* __restrict__ items, const int* __restrict__ n_items,
+                                                         float* __restrict__ ub, int32_t* __restrict__ cand,
+                                                         int32_t* __restrict__ cnt, unsigned int* err)
 {
     extern __shared__ uint8_t smem_raw[];
     TcShared& S = *reinterpret_cast<TcShared*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t rows = kmx_count(d_nx, nx_cap), cols = kmx_count(d_ny, ny_cap);
-    const int64_t n_rt = (rows + kTM - 1) / kTM;
-    const int64_t n_ct = (cols + kTN - 1) / kTN;
-    const int chunks = kmx::work_chunks(n_rt, n_ct, target_ctas, kMaxChunks);
-    if ((int64_t)blockIdx.x >= n_rt * chunks) return;
-    const int chunk = (int)(blockIdx.x % chunks);
-    const int64_t rt = blockIdx.x / chunks;
-    const int64_t tiles_per_chunk = (n_ct + chunks - 1) / chunks;
-    const int64_t t0 = chunk * tiles_per_chunk;
-    const int T = (int)max((int64_t)0, min(n_ct, t0 + tiles_per_chunk) - t0);
-    if (T == 0) return;
-    // the sequence of column tiles: the nearest tile first, then the chunk
-    // (without the nearest tile when it lies inside the chunk)
-    const int64_t cs = nearest[rt];
-    const bool cs_in = cs >= t0 && cs < t0 + T;
-    const int nseq = T + (cs_in ? 0 : 1);
-    auto tile_of = [&](int s) -> int64_t {
-        if (s == 0) return cs;
-        const int64_t rr = t0 + s - 1;
-        return (cs_in && rr >= cs) ? rr + 1 : rr;
+    const int64_t rows = kmx_count(d_nx, nx_cap);
+    const int nit = *n_items;
+    if ((int)blockIdx.x >= nit) return;
+    const int stride = (int)gridDim.x;
+    auto item_tiles = [&](int it, const int32_t*& tl, int64_t& rt) -> int {
+        const int2 item = items[it];
+        rt = item.x;
+        tl = need + (int64_t)item.x * need_stride + item.y;
+        return min(kItemTiles, nneed[item.x] - item.y);
     };
-    const uint32_t idesc = idesc_bf16(kTM, kTN);
-
-    // re-centring role
-    const int rrow = tid >> 1, part = tid & 1;
-    const int64_t xrow = rt * kTM + rrow;
-    const bool xvalid = xrow < rows;
-    // epilogue role
-    const int quarter = warp & 3, slice = warp >> 2;
-    const int r = quarter * 32 + lane;
-    const int64_t row = rt * kTM + r;
-    const bool row_valid = row < rows;
 
     if (tid == 0) {
-        for (int st = 0; st < kStages; ++st) mbar_init(&S.bar_b[st], 1);
-        mbar_init(&S.bar_mma[0], 1);
-        mbar_init(&S.bar_mma[1], 1);
+        for (int st = 0; st < kStages; ++st) {
+            mbar_init(&S.full_b[st], 1);
+            mbar_init(&S.empty_b[st], 1 + 4);      // MMA commit + the 4 re-centring warps
+        }
+        for (int st = 0; st < kAStages; ++st) {
+            mbar_init(&S.full_a[st], 4);           // re-centring warps
+            mbar_init(&S.empty_a[st], 1 + 8);      // MMA commit + the 8 epilogue warps
+        }
+        for (int k = 0; k < kAccBufs; ++k) {
+            mbar_init(&S.acc_full[k], 1);          // MMA commit
+            mbar_init(&S.acc_empty[k], 8);         // epilogue warps
+        }
         mbar_fence_init();
+        S.failed = 0;
     }
     if (warp == 0) tmem_alloc(&S.tmem, kTmemCols);
-    if (part == 1) {  // the last K chunk (values 40..47) is zero in every A operand
-        const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        store_operand_chunk(S.a[0], rrow, 5, z);
-        store_operand_chunk(S.a[1], rrow, 5, z);
-    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = S.tmem;
-
-    float x[17];  // values 16 part .. 16 part + 15 (and 32 for part 1) of this thread's re-centring row
-    {
-        const float* xr = xvalid ? X + (int64_t)permX[xrow] * KMX_DESC_STRIDE + 16 * part : nullptr;
-#pragma unroll
-        for (int h = 0; h < 17; ++h) x[h] = (xvalid && (h < 16 || part == 1)) ? __ldg(xr + h) : 0.f;
-    }
-
+    volatile int* failed = &S.failed;
     int issued_b = 0, issued_mma = 0;
-    if (tid == 0) {
-        for (; issued_b < nseq && issued_b < kStages; ++issued_b) {
-            mbar_expect_tx(&S.bar_b[issued_b], kColBytes);
-            bulk_g2s(S.b[issued_b], packY + tile_of(issued_b) * (int64_t)kColBytes, kColBytes, &S.bar_b[issued_b]);
-        }
-    }
-    bool fail = false, failed = false;
-    // upper bounds of the columns this thread has seen (own slice only), and
-    // the second-smallest upper bound over all four slices of the row as of
-    // the last barrier
-    float U1 = FLT_MAX, U2 = FLT_MAX, Ush = FLT_MAX;
 
-    for (int s = 0; s <= nseq; ++s) {
-        if (s < nseq) {
-            // ---- A operand of step s: rows re-centred on the column tile's centre
-            if (!mbar_wait(&S.bar_b[s % kStages], (s / kStages) & 1)) fail = true;
-            const uint8_t* bt = S.b[s % kStages];
-            const float4* cen4 = reinterpret_cast<const float4*>(bt + kHdrCenter) + 4 * part;
-            float av[16];
-            float p2 = 0.f;
+    if (warp == 1) {
+        // ---- producer
+        if (lane == 0) {
+            int t = 0;
+            for (int it = blockIdx.x; it < nit && !*failed; it += stride) {
+                const int32_t* tl;
+                int64_t rt;
+                const int nt = item_tiles(it, tl, rt);
+                for (int k = 0; k < nt; ++k, ++t) {
+                    const int st = t % kStages;
+                    if (t >= kStages && !mbar_wait(&S.empty_b[st], ((t / kStages) - 1) & 1)) {
+                        *failed = 1;
+                        break;
+                    }
+                    mbar_expect_tx(&S.full_b[st], kColBytes);
+                    bulk_g2s(S.b[st], packY + (int64_t)tl[k] * kColBytes, kColBytes, &S.full_b[st]);
+                    issued_b = t + 1;
+                }
+            }
+        }
+    } else if (warp == 0) {
+        // ---- tensor-core products
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(kTM, kTN);
+            int t = 0;
+            for (int it = blockIdx.x; it < nit && !*failed; it += stride) {
+                const int32_t* tl;
+                int64_t rt;
+                const int nt = item_tiles(it, tl, rt);
+                for (int k = 0; k < nt; ++k, ++t) {
+                    const int st = t % kStages, sa = t % kAStages, ab = t % kAccBufs;
+                    bool ok = mbar_wait(&S.full_b[st], (t / kStages) & 1) &&
+                              mbar_wait(&S.full_a[sa], (t / kAStages) & 1);
+                    if (ok && t >= kAccBufs) ok = mbar_wait(&S.acc_empty[ab], ((t / kAccBufs) - 1) & 1);
+                    if (!ok) {
+                        *failed = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a_base = smem_u32(S.a[sa]);
+                    const uint32_t b_base = smem_u32(S.b[st]);
+                    const uint32_t d = tmem + (uint32_t)(ab * kTN);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const float4 cv = cen4[c];
-                av[4 * c + 0] = x[4 * c + 0] - cv.x;
-                av[4 * c + 1] = x[4 * c + 1] - cv.y;
-                av[4 * c + 2] = x[4 * c + 2] - cv.z;
-                av[4 * c + 3] = x[4 * c + 3] - cv.w;
+                    for (int kk = 0; kk < kK / 16; ++kk) {
+                        const uint32_t ko = kk * 2 * kCoreStride;
+                        umma_bf16(d, smem_desc(a_base + ko, kCoreStride, kGroupStride),
+                                  smem_desc(b_base + ko, kCoreStride, kGroupStride), idesc, kk > 0);
+                    }
+                    umma_commit(&S.acc_full[ab]);
+                    umma_commit(&S.empty_a[sa]);
+                    umma_commit(&S.empty_b[st]);
+                    issued_mma = t + 1;
+                }
             }
+        }
+    } else if (warp >= 4 && warp < 8) {
+        // ---- re-centring: thread = row
+        const int rrow = tid - 128;
+        int64_t cur = -1;
+        float x[KMX_DESC_DIM];
+        int t = 0;
+        bool dead = false;
+        for (int it = blockIdx.x; it < nit && !dead; it += stride) {
+            const int32_t* tl;
+            int64_t rt;
+            const int nt = item_tiles(it, tl, rt);
+            if (rt != cur) {
+                cur = rt;
+                const int64_t xrow = rt * kTM + rrow;
+                const bool xvalid = xrow < rows;
+                const float* xr = xvalid ? X + (int64_t)permX[xrow] * KMX_DESC_STRIDE : nullptr;
 #pragma unroll
-            for (int h = 0; h < 16; ++h) p2 = fmaf(av[h], av[h], p2);
-            float a32 = 0.f;
-            if (part == 1) {
-                a32 = x[16] - reinterpret_cast<const float*>(bt + kHdrCenter)[32];
-                p2 = fmaf(a32, a32, p2);
+                for (int h = 0; h < KMX_DESC_DIM; ++h) x[h] = xvalid ? __ldg(xr + h) : 0.f;
             }
-            uint8_t* at = S.a[s & 1];
-            store_operand_chunk(at, rrow, 2 * part, av);
-            store_operand_chunk(at, rrow, 2 * part + 1, av + 8);
-            // the two partial sums of the row (neighbouring lanes); both lanes
-            // form the same total
-            p2 += __shfl_xor_sync(0xffffffffu, p2, 1);
-            if (part == 1) {
-                const float v4[8] = {a32, kSqrtC * sqrtf(p2), -0.5f, -0.5f, 0.f, 0.f, 0.f, 0.f};
-                store_operand_chunk(at, rrow, 4, v4);
-            }
-            if (part == 0) {
+            for (int k = 0; k < nt; ++k, ++t) {
+                const int st = t % kStages, sa = t % kAStages;
+                bool ok = !*failed;
+                if (ok && t >= kAStages) ok = mbar_wait(&S.empty_a[sa], ((t / kAStages) - 1) & 1);
+                if (ok) ok = mbar_wait(&S.full_b[st], (t / kStages) & 1);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    if (lane == 0) *failed = 1;
+                    dead = true;
+                    break;
+                }
+                const uint8_t* bt = S.b[st];
+                const float4* cen4 = reinterpret_cast<const float4*>(bt + kHdrCenter);
+                float v[kK];
+                float p2 = 0.f;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const float4 cv = cen4[c];
+                    v[4 * c + 0] = x[4 * c + 0] - cv.x;
+                    v[4 * c + 1] = x[4 * c + 1] - cv.y;
+                    v[4 * c + 2] = x[4 * c + 2] - cv.z;
+                    v[4 * c + 3] = x[4 * c + 3] - cv.w;
+                }
+                v[32] = x[32] - reinterpret_cast<const float*>(bt + kHdrCenter)[32];
+#pragma unroll
+                for (int h = 0; h < KMX_DESC_DIM; ++h) p2 = fmaf(v[h], v[h], p2);
+                const float al = sqrtf(p2);
+                v[KMX_DESC_DIM] = kSqrtC * al;
+                v[KMX_DESC_DIM + 1] = -0.5f;
+                v[KMX_DESC_DIM + 2] = -0.5f;
+#pragma unroll
+                for (int h = KMX_DESC_DIM + 3; h < kK; ++h) v[h] = 0.f;
+                store_operand_row(S.a[sa], rrow, v);
                 const float bmax2 = reinterpret_cast<const float*>(bt + kHdrBmax)[0];
                 const float ef = kEfp * (p2 + bmax2);
-                float ush = FLT_MAX;
-                if (s >= 3) {
-                    // the row's two slices as of step s - 3 (written in the
-                    // epilogue of iteration s - 2, published by the barrier of
-                    // step s - 1): their upper bounds come from disjoint
-                    // columns, so the second smallest of the eight is the
-                    // second smallest over all columns they saw
-                    const float2 a0 = S.ul[s % 3][rrow][0], a1 = S.ul[s % 3][rrow][1];
-                    ush = fminf(fmaxf(a0.x, a1.x), a0.x <= a1.x ? a0.y : a1.y);
+                S.rowc[sa][rrow] = make_float4(p2 - ef, kUpper * al, 2.f * ef, 0.f);
+                if (rrow < kTN / 8) S.gb[sa][rrow] = reinterpret_cast<const float*>(bt + kHdrGBeta)[rrow];
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&S.empty_b[st]);  // done with the column tile's header
+                    mbar_arrive(&S.full_a[sa]);
                 }
-                S.rowc[s % 3][rrow] = make_float4(p2 - ef, kUpper * sqrtf(p2), 2.f * ef, ush);
-            }
-            fence_proxy_async();
-        }
-        // publishes the A operand and r2 of step s; every thread has finished
-        // the epilogue of step s - 2 (accumulator (s & 1) is free) and its
-        // reads of the column tile of step s - 2
-        tc_fence_before();
-        failed = __syncthreads_or(fail) != 0;
-        tc_fence_after();
-        if (failed) break;
-        if (tid == 0) {
-            if (s < nseq) {
-                const uint32_t a_base = smem_u32(S.a[s & 1]);
-                const uint32_t b_base = smem_u32(S.b[s % kStages]);
-                const uint32_t d = tmem + (uint32_t)((s & 1) * kTN);
-#pragma unroll
-                for (int k = 0; k < kK / 16; ++k) {
-                    const uint32_t ko = k * 2 * kCoreStride;
-                    umma_bf16(d, smem_desc(a_base + ko, kCoreStride, kGroupStride),
-                              smem_desc(b_base + ko, kCoreStride, kGroupStride), idesc, k > 0);
-                }
-                umma_commit(&S.bar_mma[s & 1]);
-                ++issued_mma;
-            }
-            // the stage of step s - 2 is free: its MMA and its epilogue are done
-            if (s >= 2 && s - 2 + kStages < nseq) {
-                const int st = (s - 2) % kStages;
-                mbar_expect_tx(&S.bar_b[st], kColBytes);
-                bulk_g2s(S.b[st], packY + tile_of(s - 2 + kStages) * (int64_t)kColBytes, kColBytes, &S.bar_b[st]);
-                ++issued_b;
             }
         }
-        if (s >= 1) {
-            // ---- epilogue of step p = s - 1: this thread's 64 columns
-            const int p = s - 1;
-            if (!mbar_wait(&S.bar_mma[p & 1], (p >> 1) & 1)) fail = true;
-            tc_fence_after();
-            const uint8_t* bt = S.b[p % kStages];
-            const float4 rc = S.rowc[p % 3][r];
-            const float rb = rc.x, ua = rc.y, ue = rc.z;
-            Ush = fminf(Ush, rc.w);
-            const float* gbeta = reinterpret_cast<const float*>(bt + kHdrGBeta) + slice * 8;
-            const bool collect = p > 0 || cs_in;
-            const int64_t col0 = tile_of(p) * kTN + slice * 64;
-            const uint32_t lane_addr =
-                tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((p & 1) * kTN + slice * 64);
-            float v[64];
-            tmem_ld64(lane_addr, v);
-            // the eight groups' smallest lower bounds, independent of each
-            // other; one branch for all of them in the common case
-            float Lm[8];
-#pragma unroll
-            for (int g = 0; g < 8; ++g) {
-                const float* vg = v + 8 * g;
-                const float m = fmax3(fmax3(vg[0], vg[1], vg[2]), fmax3(vg[3], vg[4], vg[5]), fmaxf(vg[6], vg[7]));
-                // L = |a|^2 - e - 2 M is monotone in M: the group's largest M
-                // gives its smallest L
-                Lm[g] = fmaf(-2.f, m, rb);
-            }
-            const float lmin = fmin3(fmin3(Lm[0], Lm[1], Lm[2]), fmin3(Lm[3], Lm[4], Lm[5]), fminf(Lm[6], Lm[7]));
-            if (row_valid && lmin <= fminf(U2, Ush)) {
+    } else if (warp >= 8) {
+        // ---- epilogue
+        const int quarter = warp & 3, slice = (warp - 8) >> 2;
+        const int r = quarter * 32 + lane;
+        int t = 0;
+        bool dead = false;
+        // every epilogue warp runs every item (after a failure without
+        // waiting or working), so that all meet on each named barrier
+        for (int it = blockIdx.x; it < nit; it += stride) {
+            const int32_t* tl;
+            int64_t rt;
+            const int nt = item_tiles(it, tl, rt);
+            const int64_t row = rt * kTM + r;
+            const bool row_valid = row < rows;
+            float U1 = row_valid ? __ldcg(ub + row) : FLT_MAX, U2 = U1;
+            epi_sync();  // the previous item's bounds are no longer read
+            *reinterpret_cast<volatile unsigned long long*>(&S.ul[r][slice]) =
+                (unsigned long long)__float_as_uint(U1) | ((unsigned long long)__float_as_uint(U2) << 32);
+            epi_sync();
+            for (int k = 0; k < nt; ++k, ++t) {
+                const int sa = t % kAStages, ab = t % kAccBufs;
+                if (dead) continue;
+                bool ok = !*failed;
+                if (ok) ok = mbar_wait(&S.acc_full[ab], (t / kAccBufs) & 1);
+                // the A stage (row constants) cannot be refilled before this
+                // warp's arrival on empty_a, so its phase t / kAStages is the
+                // current one: the wait only acquires the re-centring writes
+                if (ok) ok = mbar_wait(&S.full_a[sa], (t / kAStages) & 1);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    if (lane == 0) *failed = 1;
+                    dead = true;
+                    continue;
+                }
+                tc_fence_after();
+                const float4 rc = S.rowc[sa][r];
+                const float rb = rc.x, ua = rc.y, ue = rc.z;
+                // one 64-bit load: the pair is never seen half written
+                const unsigned long long ou = *reinterpret_cast<volatile unsigned long long*>(&S.ul[r][slice ^ 1]);
+                const float2 other =
+                    make_float2(__uint_as_float((uint32_t)ou), __uint_as_float((uint32_t)(ou >> 32)));
+                const float* gbeta = S.gb[sa] + slice * 8;
+                const int64_t col0 = (int64_t)tl[k] * kTN + slice * 64;
+                float v[64];
+                tmem_ld64(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * kTN + slice * 64), v);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&S.acc_empty[ab]);  // the accumulator is read
+                }
+                // the second-smallest upper bound over both slices' columns
+                const float Ush = fminf(fmaxf(U1, other.x), U1 <= other.x ? U2 : other.y);
+                float Lm[8];
 #pragma unroll
                 for (int g = 0; g < 8; ++g) {
                     const float* vg = v + 8 * g;
-                    const float Lmin = Lm[g];
-                    if (Lmin <= fminf(U2, Ush)) {
-                        // the group's two best columns (largest M first): upper
-                        // bounds for them
-                        float h0 = fmaxf(vg[0], vg[1]), l0 = fminf(vg[0], vg[1]);
-                        float h1 = fmaxf(vg[2], vg[3]), l1 = fminf(vg[2], vg[3]);
-                        float h2 = fmaxf(vg[4], vg[5]), l2 = fminf(vg[4], vg[5]);
-                        float h3 = fmaxf(vg[6], vg[7]), l3 = fminf(vg[6], vg[7]);
-                        l0 = fmaxf(fminf(h0, h1), fmaxf(l0, l1));
-                        h0 = fmaxf(h0, h1);
-                        l2 = fmaxf(fminf(h2, h3), fmaxf(l2, l3));
-                        h2 = fmaxf(h2, h3);
-                        const float m2 = fmaxf(fminf(h0, h2), fmaxf(l0, l2));
-                        const float uadd = fmaf(ua, gbeta[g], ue);
-                        const float Ua = Lmin + uadd, Ub = fmaf(-2.f, m2, rb) + uadd;
-                        if (Ua < U1) {
-                            U2 = fminf(U1, Ub);
-                            U1 = Ua;
-                        } else if (Ua < U2) {
-                            U2 = Ua;
-                        }
-                        if (collect) {
+                    const float m =
+                        fmax3(fmax3(vg[0], vg[1], vg[2]), fmax3(vg[3], vg[4], vg[5]), fmaxf(vg[6], vg[7]));
+                    // L = |a|^2 - e - 2 M is monotone in M: the group's largest M
+                    // gives its smallest L
+                    Lm[g] = fmaf(-2.f, m, rb);
+                }
+                const float lmin =
+                    fmin3(fmin3(Lm[0], Lm[1], Lm[2]), fmin3(Lm[3], Lm[4], Lm[5]), fminf(Lm[6], Lm[7]));
+                if (row_valid && lmin <= fminf(U2, Ush)) {
+#pragma unroll
+                    for (int g = 0; g < 8; ++g) {
+                        const float* vg = v + 8 * g;
+                        const float Lmin = Lm[g];
+                        if (Lmin <= fminf(U2, Ush)) {
+                            // the group's two best columns (largest M first):
+                            // upper bounds for them
+                            float h0 = fmaxf(vg[0], vg[1]), l0 = fminf(vg[0], vg[1]);
+                            float h1 = fmaxf(vg[2], vg[3]), l1 = fminf(vg[2], vg[3]);
+                            float h2 = fmaxf(vg[4], vg[5]), l2 = fminf(vg[4], vg[5]);
+                            float h3 = fmaxf(vg[6], vg[7]), l3 = fminf(vg[6], vg[7]);
+                            l0 = fmaxf(fminf(h0, h1), fmaxf(l0, l1));
+                            h0 = fmaxf(h0, h1);
+                            l2 = fmaxf(fminf(h2, h3), fmaxf(l2, l3));
+                            h2 = fmaxf(h2, h3);
+                            const float m2 = fmaxf(fminf(h0, h2), fmaxf(l0, l2));
+                            const float uadd = fmaf(ua, gbeta[g], ue);
+                            const float Ua = Lmin + uadd, Ub = fmaf(-2.f, m2, rb) + uadd;
+                            if (Ua < U1) {
+                                U2 = fminf(U1, Ub);
+                                U1 = Ua;
+                            } else if (Ua < U2) {
+                                U2 = Ua;
+                            }
                             const float thr = fminf(U2, Ush);
                             unsigned msk = 0;
 #pragma unroll
                             for (int j = 0; j < 8; ++j) msk |= (fmaf(-2.f, vg[j], rb) <= thr ? 1u : 0u) << j;
-                            const int k = __popc(msk);
-                            if (k) {
-                                int pos = atomicAdd(cnt + row, k);
+                            const int nc = __popc(msk);
+                            if (nc) {
+                                int pos = atomicAdd(cnt + row, nc);
                                 while (msk) {
                                     const int j = __ffs(msk) - 1;
                                     msk &= msk - 1;
@@ -717,24 +1141,36 @@ __global__ void __launch_bounds__(kThreads, 2) tc_collect(const float* __restric
                         }
                     }
                 }
+                *reinterpret_cast<volatile unsigned long long*>(&S.ul[r][slice]) =
+                    (unsigned long long)__float_as_uint(U1) | ((unsigned long long)__float_as_uint(U2) << 32);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&S.empty_a[sa]);  // the row constants are read
             }
-            S.ul[p % 3][r][slice] = make_float2(U1, U2);
-            tc_fence_before();
+            if (!dead && row_valid) {
+                // lower the row's bound for the items that start later (bounds
+                // are >= 0, so their bits order like integers)
+                const unsigned long long ou = *reinterpret_cast<volatile unsigned long long*>(&S.ul[r][slice ^ 1]);
+                const float ox = __uint_as_float((uint32_t)ou), oy = __uint_as_float((uint32_t)(ou >> 32));
+                const float Uf = fminf(U2, fminf(fmaxf(U1, ox), U1 <= ox ? U2 : oy));
+                if (Uf >= 0.f) atomicMin(reinterpret_cast<int*>(ub + row), __float_as_int(Uf));
+            }
         }
     }
-    if (failed) {
+    __syncthreads();
+    if (*failed) {
         // drain: every issued copy and MMA must land before the memory goes
-        // away.  Each barrier has at most one phase outstanding, so waiting
-        // for the last phase issued on each barrier suffices.
-        if (tid == 0) {
-            kmx_raise(err, KMX_DERR_TIMEOUT);
+        // away (each waits for the last phase its barrier has outstanding)
+        if (tid == 32) {
             for (int st = 0; st < kStages; ++st) {
                 const int last = issued_b - 1 - ((issued_b - 1 - st) % kStages + kStages) % kStages;
-                if (last >= 0 && last % kStages == st) mbar_wait(&S.bar_b[st], (last / kStages) & 1);
+                if (last >= 0 && last % kStages == st) mbar_wait(&S.full_b[st], (last / kStages) & 1);
             }
-            for (int k = 0; k < 2; ++k) {
-                const int last = issued_mma - 1 - ((issued_mma - 1 - k) % 2 + 2) % 2;
-                if (last >= 0 && (last & 1) == k) mbar_wait(&S.bar_mma[k], (last >> 1) & 1);
+        }
+        if (tid == 0) {
+            kmx_raise(err, KMX_DERR_TIMEOUT);
+            for (int k = 0; k < kAccBufs; ++k) {
+                const int last = issued_mma - 1 - ((issued_mma - 1 - k) % kAccBufs + kAccBufs) % kAccBufs;
+                if (last >= 0 && last % kAccBufs == k) mbar_wait(&S.acc_full[k], (last / kAccBufs) & 1);
             }
         }
     }
@@ -835,48 +1271,63 @@ __global__ void __launch_bounds__(256) fallback_merge(const kmx::RowBest* __rest
 
 size_t tc_smem_bytes()
 {
-    // at least 96 KB: at most two CTAs per SM, i.e. two 256-column TMEM
-    // allocations (a third CTA would wait in tcgen05.alloc)
+    // at least 120 KB: one CTA per SM, whose TMEM allocation is all 512
+    // columns (a second CTA would wait in tcgen05.alloc)
     const size_t need = sizeof(TcShared) + 1024;
-    return need < 96 * 1024 ? 96 * 1024 : need;
+    return need < 120 * 1024 ? 120 * 1024 : need;
 }
 
 struct TcBuffers {
-    float4* coords;         // [np_cap + nq_cap]
-    unsigned int* range;    // [8]: min bits of the 4 statistics, then max bits
     uint32_t *keys, *keys_tmp;
     int32_t *vals, *vals_tmp;  // sorted: [0, np) source rows, [np_cap, np_cap + nq) target rows
     void* sort_scratch;
+    float* dirs;               // [2 << (levels - 1)][kDirStride]
     uint8_t *packP, *packQ;
     float *cenP, *cenQ;
-    int32_t *nearP, *nearQ;
+    float *ubP, *ubQ;
+    int32_t *needP, *needQ, *nneedP, *nneedQ;
+    int2 *itemsP, *itemsQ;
+    int* nitems;               // [0] source rows, [1] target rows
     int32_t *candP, *candQ, *cntP, *cntQ;
-    int* chunks;            // [2] fallback P, [3] fallback Q
+    int* chunks;               // [2] fallback P, [3] fallback Q
     int32_t *flagP, *flagQ, *listP, *listQ;
     int64_t *posP, *posQ, *nlist;  // nlist[0] P, [1] Q
     kmx::RowBest *fbP, *fbQ;
 };
+
+int tc_levels(int64_t np_cap, int64_t nq_cap)
+{
+    const int lp = tree_levels(np_cap), lq = tree_levels(nq_cap);
+    return lp > lq ? lp : lq;
+}
 
 TcBuffers tc_carve(void* base, int64_t np_cap, int64_t nq_cap, size_t* total)
 {
     TcBuffers b{};
     kmx_arena a{static_cast<char*>(base), 0};
     const int64_t n2 = np_cap + nq_cap;
-    const int64_t tp = (np_cap + kTN - 1) / kTN, tq = (nq_cap + kTN - 1) / kTN;  // column tiles
+    const int64_t tp = (np_cap + kTN - 1) / kTN, tq = (nq_cap + kTN - 1) / kTN;  // tiles of either cloud
+    const int levels = tc_levels(np_cap, nq_cap);
     const int fc = kmx_match_fp32_max_chunks();
-    b.coords = (float4*)a.take(sizeof(float4) * (size_t)n2);
-    b.range = (unsigned int*)a.take(sizeof(unsigned int) * 8);
     b.keys = (uint32_t*)a.take(sizeof(uint32_t) * (size_t)n2);
     b.keys_tmp = (uint32_t*)a.take(sizeof(uint32_t) * (size_t)n2);
     b.vals = (int32_t*)a.take(sizeof(int32_t) * (size_t)n2);
     b.vals_tmp = (int32_t*)a.take(sizeof(int32_t) * (size_t)n2);
     b.sort_scratch = a.take(kmx_sort_scratch_bytes(n2));
+    b.dirs = (float*)a.take(sizeof(float) * kDirStride * ((size_t)2 << (levels > 0 ? levels - 1 : 0)));
     b.packP = (uint8_t*)a.take((size_t)tp * kColBytes);
     b.packQ = (uint8_t*)a.take((size_t)tq * kColBytes);
     b.cenP = (float*)a.take(sizeof(float) * kCenterStride * (size_t)tp);
     b.cenQ = (float*)a.take(sizeof(float) * kCenterStride * (size_t)tq);
-    b.nearP = (int32_t*)a.take(sizeof(int32_t) * (size_t)tp);
-    b.nearQ = (int32_t*)a.take(sizeof(int32_t) * (size_t)tq);
+    b.ubP = (float*)a.take(sizeof(float) * (size_t)np_cap);
+    b.ubQ = (float*)a.take(sizeof(float) * (size_t)nq_cap);
+    b.needP = (int32_t*)a.take(sizeof(int32_t) * (size_t)tp * (size_t)tq);
+    b.needQ = (int32_t*)a.take(sizeof(int32_t) * (size_t)tq * (size_t)tp);
+    b.nneedP = (int32_t*)a.take(sizeof(int32_t) * (size_t)tp);
+    b.nneedQ = (int32_t*)a.take(sizeof(int32_t) * (size_t)tq);
+    b.itemsP = (int2*)a.take(sizeof(int2) * (size_t)tp * (size_t)((tq + kItemTiles - 1) / kItemTiles));
+    b.itemsQ = (int2*)a.take(sizeof(int2) * (size_t)tq * (size_t)((tp + kItemTiles - 1) / kItemTiles));
+    b.nitems = (int*)a.take(sizeof(int) * 2);
     b.candP = (int32_t*)a.take(sizeof(int32_t) * kCandCap * (size_t)np_cap);
     b.candQ = (int32_t*)a.take(sizeof(int32_t) * kCandCap * (size_t)nq_cap);
     b.cntP = (int32_t*)a.take(sizeof(int32_t) * (size_t)(np_cap + nq_cap));
@@ -911,45 +1362,56 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
     size_t total = 0;
     TcBuffers b = tc_carve(s.extra, np_cap, nq_cap, &total);
     const int64_t n2 = np_cap + nq_cap;
-    const int64_t tp = (np_cap + kTM - 1) / kTM, tq = (nq_cap + kTM - 1) / kTM;    // row tiles
-    const int64_t ctp = (np_cap + kTN - 1) / kTN, ctq = (nq_cap + kTN - 1) / kTN;  // column tiles (the same)
+    const int64_t tp = (np_cap + kTN - 1) / kTN, tq = (nq_cap + kTN - 1) / kTN;
+    const int levels = tc_levels(np_cap, nq_cap);
+    const int key_bits = levels <= 14 ? 24 : 32;
+    if (levels > 30) return cudaErrorInvalidValue;
     const size_t smem = tc_smem_bytes();
     cudaError_t e = kmx_once_per_device(kmx_attr_tc_topk, [smem] {
-        return cudaFuncSetAttribute(tc_collect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t r = cudaFuncSetAttribute(tc_collect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (r) return r;
+        return cudaFuncSetAttribute(tree_dir, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTreeSmem);
     });
     if (e) return e;
     if ((e = cudaMemsetAsync(b.flagP, 0, sizeof(int32_t) * (np_cap + 1), st))) return e;
     if ((e = cudaMemsetAsync(b.flagQ, 0, sizeof(int32_t) * (nq_cap + 1), st))) return e;
     if ((e = cudaMemsetAsync(b.cntP, 0, sizeof(int32_t) * (size_t)n2, st))) return e;
-    if ((e = cudaMemsetAsync(b.range, 0xFF, sizeof(unsigned int) * 4, st))) return e;
-    if ((e = cudaMemsetAsync(b.range + 4, 0, sizeof(unsigned int) * 4, st))) return e;
-    // locality order of both clouds
+    if ((e = cudaMemsetAsync(b.nitems, 0, sizeof(int) * 2, st))) return e;
+    // locality order of both clouds: one tree level per sort
     const unsigned gb = kmx_stride_blocks(n2, 256, ctx->sm_count);
     KMX_COUNT_LAUNCH();
-    tc_coords<<<gb, 256, 0, st>>>(dp, np_cap, d_np, dq, nq_cap, d_nq, b.coords, b.range, ctx->d_err);
-    KMX_COUNT_LAUNCH();
-    tc_keys<<<gb, 256, 0, st>>>(np_cap, d_np, nq_cap, d_nq, b.coords, b.range, b.keys, b.vals);
-    if ((e = cudaGetLastError())) return e;
-    if ((e = kmx_sort_u32(ctx, b.keys, b.vals, b.keys_tmp, b.vals_tmp, n2, 32, b.sort_scratch))) return e;
+    tree_init<<<gb, 256, 0, st>>>(np_cap, n2, b.vals);
+    for (int l = 0; l < levels; ++l) {
+        KMX_COUNT_LAUNCH();
+        tree_dir<<<dim3(1u << l, 2), kTreeThreads, kTreeSmem, st>>>(dp, np_cap, d_np, dq, nq_cap, d_nq, b.vals, l,
+                                                                     b.dirs);
+        KMX_COUNT_LAUNCH();
+        tree_key<<<gb, 256, 0, st>>>(dp, np_cap, d_np, dq, nq_cap, d_nq, b.vals, l, key_bits, b.dirs, b.keys);
+        if ((e = cudaGetLastError())) return e;
+        if ((e = kmx_sort_u32(ctx, b.keys, b.vals, b.keys_tmp, b.vals_tmp, n2, key_bits, b.sort_scratch))) return e;
+    }
     const int32_t* permP = b.vals;
     const int32_t* permQ = b.vals + np_cap;
-    // packed tiles and centres
+    // packed tiles, centres and radii
     KMX_COUNT_LAUNCH();
-    tc_pack<<<(unsigned)ctp, kTN, 0, st>>>(dp, permP, np_cap, d_np, b.packP, b.cenP);
+    tc_pack<<<(unsigned)tp, kTN, 0, st>>>(dp, permP, np_cap, d_np, b.packP, b.cenP, ctx->d_err);
     KMX_COUNT_LAUNCH();
-    tc_pack<<<(unsigned)ctq, kTN, 0, st>>>(dq, permQ, nq_cap, d_nq, b.packQ, b.cenQ);
+    tc_pack<<<(unsigned)tq, kTN, 0, st>>>(dq, permQ, nq_cap, d_nq, b.packQ, b.cenQ, ctx->d_err);
+    // first candidates, bounds and tile lists both ways
     KMX_COUNT_LAUNCH();
-    tc_nearest<<<kmx_blocks(ctp, 8), 256, 0, st>>>(b.cenP, np_cap, d_np, b.cenQ, nq_cap, d_nq, b.nearP);
+    tc_plan<<<(unsigned)tp, kTM, 0, st>>>(dp, permP, np_cap, d_np, b.cenP, dq, permQ, nq_cap, d_nq, b.cenQ, b.candP,
+                                          b.cntP, b.ubP, b.needP, tq, b.nneedP, b.itemsP, b.nitems + 0);
     KMX_COUNT_LAUNCH();
-    tc_nearest<<<kmx_blocks(ctq, 8), 256, 0, st>>>(b.cenQ, nq_cap, d_nq, b.cenP, np_cap, d_np, b.nearQ);
-    // candidates both ways
-    const int target = 2 * ctx->sm_count;
+    tc_plan<<<(unsigned)tq, kTM, 0, st>>>(dq, permQ, nq_cap, d_nq, b.cenQ, dp, permP, np_cap, d_np, b.cenP, b.candQ,
+                                          b.cntQ, b.ubQ, b.needQ, tp, b.nneedQ, b.itemsQ, b.nitems + 1);
+    // tensor-core candidates both ways: one persistent CTA per SM
+    const unsigned grid = (unsigned)(ctx->sm_count > 0 ? ctx->sm_count : 1);
     KMX_COUNT_LAUNCH();
-    tc_collect<<<(unsigned)(tp * kMaxChunks), kThreads, smem, st>>>(dp, permP, np_cap, d_np, b.packQ, nq_cap, d_nq,
-                                                                    b.nearP, target, b.candP, b.cntP, ctx->d_err);
+    tc_collect<<<grid, kThreads, smem, st>>>(dp, permP, np_cap, d_np, b.packQ, b.needP, tq, b.nneedP, b.itemsP,
+                                             b.nitems + 0, b.ubP, b.candP, b.cntP, ctx->d_err);
     KMX_COUNT_LAUNCH();
-    tc_collect<<<(unsigned)(tq * kMaxChunks), kThreads, smem, st>>>(dq, permQ, nq_cap, d_nq, b.packP, np_cap, d_np,
-                                                                    b.nearQ, target, b.candQ, b.cntQ, ctx->d_err);
+    tc_collect<<<grid, kThreads, smem, st>>>(dq, permQ, nq_cap, d_nq, b.packP, b.needQ, tp, b.nneedQ, b.itemsQ,
+                                             b.nitems + 1, b.ubQ, b.candQ, b.cntQ, ctx->d_err);
     // exact re-ranking; overflowed rows are flagged
     KMX_COUNT_LAUNCH();
     tc_rerank<<<kmx_blocks(np_cap, 8), 256, 0, st>>>(dp, permP, np_cap, d_np, dq, permQ, nq_cap, d_nq, b.candP,
@@ -981,30 +1443,43 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
 }
 
 // Diagnostics of the last tensor-core match on this scratch: rows that went
-// through the exact fallback (source, target) and candidates collected
-// (source, target), as four int64 values in the caller's device buffer.
+// through the exact fallback (source, target), candidates collected
+// (source, target) and tile pairs computed on the tensor cores (source row
+// tiles, target row tiles), as six int64 values in the caller's device
+// buffer.
 __global__ void tc_stats(const int64_t* __restrict__ nlist, const int32_t* __restrict__ cntP, int64_t np_cap,
                          const int64_t* d_np, const int32_t* __restrict__ cntQ, int64_t nq_cap, const int64_t* d_nq,
+                         const int32_t* __restrict__ nneedP, const int32_t* __restrict__ nneedQ,
                          int64_t* __restrict__ out)
 {
-    __shared__ unsigned long long sp, sq;
+    __shared__ unsigned long long sp, sq, tp, tq;
     if (threadIdx.x == 0) {
         sp = 0;
         sq = 0;
+        tp = 0;
+        tq = 0;
     }
     __syncthreads();
     const int64_t np = kmx_count(d_np, np_cap), nq = kmx_count(d_nq, nq_cap);
-    unsigned long long a = 0, b = 0;
+    unsigned long long a = 0, b = 0, c = 0, d = 0;
     for (int64_t i = threadIdx.x; i < np; i += blockDim.x) a += (unsigned long long)min(cntP[i], kCandCap);
     for (int64_t i = threadIdx.x; i < nq; i += blockDim.x) b += (unsigned long long)min(cntQ[i], kCandCap);
+    if (nq > 0)
+        for (int64_t i = threadIdx.x; i < (np + kTM - 1) / kTM; i += blockDim.x) c += (unsigned long long)nneedP[i];
+    if (np > 0)
+        for (int64_t i = threadIdx.x; i < (nq + kTM - 1) / kTM; i += blockDim.x) d += (unsigned long long)nneedQ[i];
     atomicAdd(&sp, a);
     atomicAdd(&sq, b);
+    atomicAdd(&tp, c);
+    atomicAdd(&tq, d);
     __syncthreads();
     if (threadIdx.x == 0) {
         out[0] = nlist[0];
         out[1] = nlist[1];
         out[2] = (int64_t)sp;
         out[3] = (int64_t)sq;
+        out[4] = (int64_t)tp;
+        out[5] = (int64_t)tq;
     }
 }
 
@@ -1014,6 +1489,7 @@ cudaError_t kmx_match_tc_stats(kmx_ctx* ctx, void* extra, int64_t np_cap, const 
     size_t total = 0;
     TcBuffers b = tc_carve(extra, np_cap, nq_cap, &total);
     KMX_COUNT_LAUNCH();
-    tc_stats<<<1, 256, 0, ctx->stream>>>(b.nlist, b.cntP, np_cap, d_np, b.cntQ, nq_cap, d_nq, dst);
+    tc_stats<<<1, 256, 0, ctx->stream>>>(b.nlist, b.cntP, np_cap, d_np, b.cntQ, nq_cap, d_nq, b.nneedP, b.nneedQ,
+                                         dst);
     return cudaGetLastError();
 }

@@ -347,9 +347,10 @@ class Context:
 
     def match_diag(self, np_cap, nq_cap, d_np=None, d_nq=None):
         """kmx_match_diag after a KMX_MATCH_BF16_RERANK match of these
-        capacities: int64 tensor [4] (fallback rows source / target,
-        candidates collected source / target)."""
-        out = torch.zeros(4, dtype=torch.int64, device=self.device)
+        capacities: int64 tensor [6] (fallback rows source / target,
+        candidates collected source / target, tensor-core tile pairs with
+        source / target rows)."""
+        out = torch.zeros(6, dtype=torch.int64, device=self.device)
         self._check(self.lib.kmx_match_diag(self.h, int(np_cap), _ptr(d_np), int(nq_cap), _ptr(d_nq), _ptr(out)),
                     "kmx_match_diag")
         return out

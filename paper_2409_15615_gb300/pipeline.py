@@ -129,7 +129,11 @@ class PairState:
         scratch must already have their final sizes (call run_checked
         first), so the recorded sequence allocates nothing.  Replaying the
         graph reruns the pair on whatever is in self.src.raw / self.tgt.raw
-        (or the raw_src / raw_tgt / corr_out / n_out given, as for run())."""
+        (or the raw_src / raw_tgt / corr_out / n_out given, as for run()).
+        A graph records buffer addresses: a later run that grows the
+        neighbour lists or the contexts' scratch frees buffers that earlier
+        graphs still point at, so size the state for every pair it will
+        replay before capturing any of them."""
         ctx = self.ctx
         cap_stream = torch.cuda.Stream(device=ctx.device)
         old = ctx.stream

@@ -610,6 +610,31 @@ def test_match_bf16_equals_exact_fp32(torch_cuda, ctx, orc):
     assert diag[2] >= 2 * len(FP) - 2 and diag[3] >= 2 * len(FQ) - 2
 
 
+@pytest.mark.parametrize("clustered", [True, False])
+def test_match_bf16_many_items(torch_cuda, ctx, clustered):
+    """Sizes with several work items per row tile and several items per
+    persistent CTA (row tiles change between a CTA's items): byte equality
+    with the exact path.  On clustered descriptors (mixtures of tight
+    clusters, like the near-duplicate rows of planes) the triangle-inequality
+    test leaves only a part of the tile pairs to the tensor cores; on
+    unstructured ones it may keep nearly all."""
+    rng = np.random.default_rng(77 + clustered)
+    if clustered:
+        cen = rng.gamma(0.5, 20.0, (60, 33))
+        FP = (cen[rng.integers(0, 60, 20000)] + rng.normal(0, 0.6, (20000, 33))).astype(np.float32)
+        FQ = (cen[rng.integers(0, 60, 12000)] + rng.normal(0, 0.6, (12000, 33))).astype(np.float32)
+    else:
+        FP = rng.gamma(0.5, 20.0, (20000, 33)).astype(np.float32)
+        FQ = rng.gamma(0.5, 20.0, (12000, 33)).astype(np.float32)
+    n = _same_as_exact(torch_cuda, ctx, FP, FQ)
+    assert n > 0
+    d = ctx.match_diag(len(FP), len(FQ)).cpu().numpy()
+    all_pairs = -(-len(FP) // 128) * -(-len(FQ) // 128)
+    assert 0 < d[4] <= all_pairs and 0 < d[5] <= all_pairs
+    if clustered:
+        assert d[4] + d[5] < all_pairs, "pruning left %s of %d tile pairs" % (d[4:], 2 * all_pairs)
+
+
 def test_match_bf16_duplicates_overflow_to_exact(torch_cuda, ctx):
     """600 copies of one descriptor tie at distance 0 for every row near them:
     those rows' candidate lists overflow (512) and go through the exact FP32
