@@ -100,7 +100,9 @@ cudaError_t kmx_match_fp32_bulk_launch(kmx_ctx* ctx, const float* dp, const int3
 // match_fp32.cu
 int kmx_match_fp32_max_chunks();
 // exact FP32 row summaries for the descriptor rows listed in rows[0..*d_nlist)
-// (list positions index `part`, [max_chunks][list_cap]); no column bests
+// (chunk c of list position r at part[c * list length + r]; part holds
+// kmx_match_fp32_max_chunks() * (list_cap + 1) entries and the chunk count,
+// at most 512, is published in *chunks_out); no column bests
 cudaError_t kmx_match_fp32_rows_launch(kmx_ctx* ctx, const float* dp, const int32_t* rows, int64_t list_cap,
                                        const int64_t* d_nlist, const float* dq, int64_t nq_cap, const int64_t* d_nq,
                                        kmx::RowBest* part, int* chunks_out);

@@ -68,11 +68,21 @@ __device__ __forceinline__ void store_tile(float (*sm)[kTile], const float4 (&re
     }
 }
 
+// Column chunks per row tile of a whole-cloud call; the count used is decided
+// on the device (kmx::work_chunks) and published in MatchScratch::chunks.
+constexpr int kMaxChunksFp32 = 8;
+// Column chunks per row tile of a row-list call (a few fallback rows spread
+// over the whole GPU), bounded on the device by the room of the partial
+// buffer: kMaxChunksFp32 * (list_cap + 1) entries.
+constexpr int kMaxChunksRows = 512;
+
 // The grid is sized from the capacities; the split of the actual work (row
 // tiles x column chunks) is computed here from the device-side counts, so a
 // call sized for 121k rows that finds 12k descriptors still spreads them over
 // the whole GPU.  With a row list the rows are list positions (np = list
-// length) and colbest may be null (no column bests).
+// length), colbest may be null (no column bests), and the partials of chunk c
+// are part[c * np ...] (packed by the actual list length, so that a short
+// list can use many chunks).
 __global__ void __launch_bounds__(kThreads) match_tiles_fp32(const float* __restrict__ dp,
                                                              const int32_t* __restrict__ rows_list, int64_t np_cap,
                                                              const int64_t* d_np, const float* __restrict__ dq,
@@ -86,7 +96,13 @@ __global__ void __launch_bounds__(kThreads) match_tiles_fp32(const float* __rest
     const int64_t np = kmx_count(d_np, np_cap), nq = kmx_count(d_nq, nq_cap);
     const int64_t npt = (np + kTile - 1) / kTile;
     const int64_t nqt = (nq + kTile - 1) / kTile;
-    const int chunks = kmx::work_chunks(npt, nqt, target_ctas, max_chunks);
+    const int64_t stride = rows_list ? np : np_cap;  // partials of one chunk
+    int maxc = max_chunks;
+    if (rows_list) {
+        const int64_t room = (int64_t)kMaxChunksFp32 * (np_cap + 1) / (np > 0 ? np : 1);
+        if (room < maxc) maxc = (int)room;
+    }
+    const int chunks = kmx::work_chunks(npt, nqt, target_ctas, maxc);
     if (blockIdx.x == 0 && threadIdx.x == 0) *chunks_out = chunks;
     if ((int64_t)blockIdx.x >= npt * chunks) return;
     const int chunk = (int)(blockIdx.x % chunks);
@@ -204,13 +220,10 @@ __global__ void __launch_bounds__(kThreads) match_tiles_fp32(const float* __rest
             kmx::row_merge(d1, jj, d2, od1, oj, od2);
         }
         const int64_t row = row0 + ty * 8 + i;
-        if (tx == 0 && row < np) part[(int64_t)chunk * np_cap + row] = kmx::RowBest{d1, jj, d2};
+        if (tx == 0 && row < np) part[(int64_t)chunk * stride + row] = kmx::RowBest{d1, jj, d2};
     }
 }
 
-// Up to this many column chunks per row tile; the count used is decided on
-// the device (kmx::work_chunks) and published in MatchScratch::chunks.
-constexpr int kMaxChunksFp32 = 8;
 
 // Opt in to >48 KB of dynamic shared memory once per device (the first call
 // happens before any capture of a pair into a CUDA graph).
@@ -250,11 +263,13 @@ cudaError_t kmx_match_fp32_rows_launch(kmx_ctx* ctx, const float* dp, const int3
 {
     cudaError_t e = set_smem_attr();
     if (e) return e;
+    // row tiles x chunks <= row tiles + target for the split work_chunks picks
     const int64_t npt = (list_cap + kTile - 1) / kTile;
-    const int64_t blocks = (npt > 0 ? npt : 1) * kMaxChunksFp32;
+    const int target = 4 * ctx->sm_count;
+    const int64_t blocks = (npt > 0 ? npt : 1) + target;
     KMX_COUNT_LAUNCH();
     match_tiles_fp32<<<(unsigned)blocks, kThreads, sizeof(FpShared), ctx->stream>>>(
-        dp, rows, list_cap, d_nlist, dq, nq_cap, d_nq, 4 * ctx->sm_count, kMaxChunksFp32, part, nullptr, chunks_out);
+        dp, rows, list_cap, d_nlist, dq, nq_cap, d_nq, target, kMaxChunksRows, part, nullptr, chunks_out);
     return cudaGetLastError();
 }
 

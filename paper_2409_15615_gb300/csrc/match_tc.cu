@@ -18,10 +18,12 @@
 //             node's rows are split at a whole number of 128-row tiles
 //             (left: ceil(len / 256) * 128 rows) by their projection on the
 //             node's principal direction (power iteration on up to 512
-//             sampled rows), level by level with one stable radix sort per
-//             level keyed by (side, node, quantised projection).  Its leaves
-//             are the 128-row tiles, and they are tight: the rows of a tile
-//             are similar descriptors.
+//             sampled rows).  The upper levels run level by level with one
+//             stable radix sort per level keyed by (side, node, quantised
+//             projection); below nodes of 16 tiles one CTA per node finishes
+//             its subtree in shared memory (bitonic sorts).  The leaves are
+//             the 128-row tiles, and they are tight: the rows of a tile are
+//             similar descriptors.
 //   pack      one CTA per 128-row tile: the tile centre, then per row
 //             b = y - c in BF16 in the UMMA operand layout (K-major, 8x16-byte
 //             core matrices, no swizzle) with three extra K slots
@@ -43,7 +45,8 @@
 //             [x - c_C, sqrt(c') |x - c_C|, -1/2, -1/2] while earlier tiles'
 //             products run, one thread issues tcgen05.mma (kind::f16, BF16,
 //             M = N = 128, three K steps of 16) into one of four TMEM
-//             accumulators, and eight warps read them with tcgen05.ld.  The
+//             accumulators, and two warpgroups of four warps read them
+//             with tcgen05.ld (alternate tiles, two tiles in flight).  The
 //             accumulator holds M = a.b + c' |a| |b| - |b|^2 / 2
 //             (approximately), so L = |a|^2 - 2 M - e is a certified lower
 //             bound of the exact d^2, and L + 4.1 c' |a| |b| + 2 e an upper
@@ -52,8 +55,8 @@
 //             column with L <= U2 (its column index goes to the row's
 //             candidate list).  Every column whose exact distance is at most
 //             the row's second-smallest exact distance is collected
-//             (L <= d <= d(2) <= U2).  A 32-column slice whose largest M
-//             cannot give L <= U2 costs one three-input max per two values.
+//             (L <= d <= d(2) <= U2).  A group of 8 columns whose largest
+//             M cannot give L <= U2 costs three max operations and an FMA.
 //             At the end of an item the row's U is lowered to what the item
 //             found (atomic minimum), for the items that start later.
 //   rerank    one warp per row: the exact FP32 distance of every collected
@@ -108,11 +111,13 @@ constexpr int kHdrCenter = kHdrBeta + kTN * 4;
 constexpr int kHdrBmax = kHdrCenter + kCenterStride * 4;
 constexpr int kHdrGBeta = kHdrBmax + 16;
 constexpr int kColBytes = kHdrGBeta + (kTN / 8) * 4;  // 13024, a multiple of 16
-constexpr int kStages = 4;                    // column-tile ring
+constexpr int kStages = 6;                    // column-tile ring
 constexpr int kThreads = 512;                 // 16 warps (roles in tc_collect)
 constexpr int kTmemCols = 512;                // four 128-column FP32 accumulators
 constexpr int kCandCap = 512;                 // candidate list per row
 constexpr int kItemTiles = 32;                // column tiles per work item
+constexpr int kPlanRec = 32;                  // columns of the nearest tile recorded per row in the plan
+constexpr int kCandBuf = 16;                  // candidates buffered per row and epilogue warpgroup in the collect kernel
 constexpr float kC = 0.008f;                  // c' of the bounds
 constexpr float kSqrtC = 0.08944271909999159f;
 constexpr float kUpper = 4.1f * kC;
@@ -121,6 +126,9 @@ constexpr float kEfp = 6e-5f;
 // relative of the exact ones (33 FP32 terms), squares within 1e-4
 constexpr float kTolR = 3e-5f;
 constexpr float kTolD = 1e-4f;
+// bound on the rounding error of |x|^2 + |c|^2 - 2 x.c in FP32, relative to
+// (|x| + |c|)^2: 40 u with u = 2^-24, rounded up
+constexpr float kDotErr = 3e-6f;
 
 static_assert(kColBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
 
@@ -238,11 +246,14 @@ __device__ __forceinline__ void store_operand_row(uint8_t* tile, int r, const fl
 // ---------------------------------------------------------------------------
 
 constexpr int kTreeSample = 512;  // rows sampled per node for its direction
-constexpr int kTreeIters = 6;     // power iterations
+constexpr int kTreeIters = 4;     // power iterations
 constexpr int kTreeThreads = 256;
 constexpr int kColSplit = 7;      // partial sums per column in the sample reductions (7 x 33 <= 256)
 constexpr int kDirStride = 68;    // floats per node: centre (33), direction (33), projection range (2)
 constexpr size_t kTreeSmem = sizeof(float) * kTreeSample * KMX_DESC_DIM;
+constexpr int kFinishLevels = 4;                         // levels below a node of 16 tiles
+constexpr int kFinishRows = kTM << kFinishLevels;        // 2048
+constexpr size_t kFinishSmem = kTreeSmem + sizeof(int32_t) * 3 * kFinishRows;
 
 // Rows of the left child of a node of `len` rows: a whole number of tiles,
 // ceil(len / 256) * 128; a node of at most 128 rows is a leaf (its left
@@ -297,66 +308,74 @@ __device__ __forceinline__ int64_t tree_node_of(int64_t n, int l, int64_t pos, i
     return k;
 }
 
-// Sorted positions of both clouds start as the identity: entries e < np_cap
-// are the source cloud, the others the target cloud.
-__global__ void __launch_bounds__(256) tree_init(int64_t np_cap, int64_t n2, int32_t* __restrict__ vals)
+// The tree works on both clouds' rows packed together: entry e < np is
+// source row e, entry np + i target row i (np, nq the device counts).  They
+// start as the identity, and *n2 = np + nq.
+__global__ void __launch_bounds__(256) tree_init(int64_t np_cap, const int64_t* d_np, int64_t nq_cap,
+                                                 const int64_t* d_nq, int32_t* __restrict__ vals,
+                                                 int64_t* __restrict__ n2)
 {
-    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < n2; e += (int64_t)gridDim.x * 256)
-        vals[e] = (int32_t)(e < np_cap ? e : e - np_cap);
+    const int64_t np = kmx_count(d_np, np_cap), nq = kmx_count(d_nq, nq_cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *n2 = np + nq;
+    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < np + nq; e += (int64_t)gridDim.x * 256)
+        vals[e] = (int32_t)(e < np ? e : e - np);
 }
 
-// One CTA per (node of this level, side): the node's centre and principal
-// direction from up to kTreeSample of its rows (evenly spaced in its current
-// order), and the range of their projections.  Leaves do nothing.
-__global__ void __launch_bounds__(kTreeThreads) tree_dir(const float* __restrict__ P, int64_t np_cap,
-                                                         const int64_t* d_np, const float* __restrict__ Q,
-                                                         int64_t nq_cap, const int64_t* d_nq,
-                                                         const int32_t* __restrict__ vals, int level,
-                                                         float* __restrict__ dirs)
+// The sorted rows into the layout the later stages read: source rows at
+// [0, np), target rows at [np_cap, np_cap + nq).
+__global__ void __launch_bounds__(256) tree_out(int64_t np_cap, const int64_t* d_np, int64_t nq_cap,
+                                                const int64_t* d_nq, const int32_t* __restrict__ vals,
+                                                int32_t* __restrict__ perm)
 {
-    extern __shared__ float tree_smem[];
-    float(*xs)[KMX_DESC_DIM] = reinterpret_cast<float(*)[KMX_DESC_DIM]>(tree_smem);
-    __shared__ float part[kColSplit][KMX_DESC_DIM];
-    __shared__ float cvec[KMX_DESC_DIM], vvec[KMX_DESC_DIM], uvec[KMX_DESC_DIM];
-    __shared__ float w[kTreeSample];
-    __shared__ float redf[2][kTreeThreads / 32];
-    __shared__ int redi[kTreeThreads / 32];
-    __shared__ float s_scale;
-    __shared__ int s_far;
-    const int side = blockIdx.y;
-    const int64_t k = blockIdx.x;
-    const int64_t n = side ? kmx_count(d_nq, nq_cap) : kmx_count(d_np, np_cap);
-    int64_t start, len;
-    tree_node(n, level, k, start, len);
-    if (len <= kTM) return;
-    const float* X = side ? Q : P;
-    const int32_t* perm = vals + (side ? np_cap : 0);
+    const int64_t np = kmx_count(d_np, np_cap), nq = kmx_count(d_nq, nq_cap);
+    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < np + nq; e += (int64_t)gridDim.x * 256)
+        perm[e < np ? e : np_cap + (e - np)] = vals[e];
+}
+
+// Shared memory of one node's direction (besides the sampled rows).
+struct DirSmem {
+    float part[kColSplit][KMX_DESC_DIM];
+    float cvec[KMX_DESC_DIM], vvec[KMX_DESC_DIM], uvec[KMX_DESC_DIM];
+    float w[kTreeSample];
+    float redf[2][kTreeThreads / 32];
+    int redi[kTreeThreads / 32];
+    float scale;
+    int far;
+};
+
+// Centre (D.cvec) and principal direction (D.vvec) of a node of `len` rows
+// whose rows are X[perm[0 .. len)], from up to kTreeSample of them (evenly
+// spaced in the current order) held centred in xs; lo / hi (thread 0) get
+// the range of the sample's projections.  Every thread of the CTA calls it.
+__device__ void node_direction(const float* __restrict__ X, const int32_t* perm, int64_t len,
+                               float (*xs)[KMX_DESC_DIM], DirSmem& D, float& lo, float& hi)
+{
     const int m = (int)min(len, (int64_t)kTreeSample);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cpart = tid / KMX_DESC_DIM, ch = tid - cpart * KMX_DESC_DIM;
+    __syncthreads();  // the caller's earlier use of xs and D is over
     for (int idx = tid; idx < m * KMX_DESC_DIM; idx += kTreeThreads) {
         const int i = idx / KMX_DESC_DIM, h = idx - i * KMX_DESC_DIM;
-        const int64_t pos = start + (int64_t)i * len / m;
-        xs[i][h] = __ldg(X + (int64_t)perm[pos] * KMX_DESC_STRIDE + h);
+        xs[i][h] = __ldg(X + (int64_t)perm[(int64_t)i * len / m] * KMX_DESC_STRIDE + h);
     }
     __syncthreads();
     // centre
-    const int cpart = tid / KMX_DESC_DIM, ch = tid - cpart * KMX_DESC_DIM;
     if (cpart < kColSplit) {
         float acc = 0.f;
         for (int i = cpart; i < m; i += kColSplit) acc += xs[i][ch];
-        part[cpart][ch] = acc;
+        D.part[cpart][ch] = acc;
     }
     __syncthreads();
     if (tid < KMX_DESC_DIM) {
         float acc = 0.f;
 #pragma unroll
-        for (int c = 0; c < kColSplit; ++c) acc += part[c][tid];
-        cvec[tid] = acc / (float)m;
+        for (int c = 0; c < kColSplit; ++c) acc += D.part[c][tid];
+        D.cvec[tid] = acc / (float)m;
     }
     __syncthreads();
     for (int idx = tid; idx < m * KMX_DESC_DIM; idx += kTreeThreads) {
         const int i = idx / KMX_DESC_DIM, h = idx - i * KMX_DESC_DIM;
-        xs[i][h] -= cvec[h];
+        xs[i][h] -= D.cvec[h];
     }
     __syncthreads();
     // start from the sampled row farthest from the centre (lowest index on ties)
@@ -382,61 +401,62 @@ __global__ void __launch_bounds__(kTreeThreads) tree_dir(const float* __restrict
             }
         }
         if (lane == 0) {
-            redf[0][warp] = best;
-            redi[warp] = bi;
+            D.redf[0][warp] = best;
+            D.redi[warp] = bi;
         }
         __syncthreads();
         if (tid == 0) {
-            float b = redf[0][0];
-            int i0 = redi[0];
+            float b = D.redf[0][0];
+            int i0 = D.redi[0];
             for (int q = 1; q < kTreeThreads / 32; ++q)
-                if (redf[0][q] > b || (redf[0][q] == b && redi[q] < i0)) {
-                    b = redf[0][q];
-                    i0 = redi[q];
+                if (D.redf[0][q] > b || (D.redf[0][q] == b && D.redi[q] < i0)) {
+                    b = D.redf[0][q];
+                    i0 = D.redi[q];
                 }
-            s_far = i0;
+            D.far = i0;
         }
         __syncthreads();
-        if (tid < KMX_DESC_DIM) uvec[tid] = xs[s_far][tid];
+        if (tid < KMX_DESC_DIM) D.uvec[tid] = xs[D.far][tid];
     }
     // power iterations v <- S^T S v / |S^T S v| on the centred sample S
     for (int it = 0; it <= kTreeIters; ++it) {
         __syncthreads();
         if (tid == 0) {
             float nn = 0.f;
-            for (int h = 0; h < KMX_DESC_DIM; ++h) nn = fmaf(uvec[h], uvec[h], nn);
-            s_scale = nn > 0.f ? rsqrtf(nn) : 0.f;
+            for (int h = 0; h < KMX_DESC_DIM; ++h) nn = fmaf(D.uvec[h], D.uvec[h], nn);
+            D.scale = nn > 0.f ? rsqrtf(nn) : 0.f;
         }
         __syncthreads();
-        if (tid < KMX_DESC_DIM) vvec[tid] = s_scale > 0.f ? uvec[tid] * s_scale : (tid == 0 ? 1.f : 0.f);
+        if (tid < KMX_DESC_DIM) D.vvec[tid] = D.scale > 0.f ? D.uvec[tid] * D.scale : (tid == 0 ? 1.f : 0.f);
         __syncthreads();
         if (it == kTreeIters) break;
         for (int i = tid; i < m; i += kTreeThreads) {
             float acc = 0.f;
 #pragma unroll
-            for (int h = 0; h < KMX_DESC_DIM; ++h) acc = fmaf(xs[i][h], vvec[h], acc);
-            w[i] = acc;
+            for (int h = 0; h < KMX_DESC_DIM; ++h) acc = fmaf(xs[i][h], D.vvec[h], acc);
+            D.w[i] = acc;
         }
         __syncthreads();
         if (cpart < kColSplit) {
             float acc = 0.f;
-            for (int i = cpart; i < m; i += kColSplit) acc = fmaf(w[i], xs[i][ch], acc);
-            part[cpart][ch] = acc;
+            for (int i = cpart; i < m; i += kColSplit) acc = fmaf(D.w[i], xs[i][ch], acc);
+            D.part[cpart][ch] = acc;
         }
         __syncthreads();
         if (tid < KMX_DESC_DIM) {
             float acc = 0.f;
 #pragma unroll
-            for (int c = 0; c < kColSplit; ++c) acc += part[c][tid];
-            uvec[tid] = acc;
+            for (int c = 0; c < kColSplit; ++c) acc += D.part[c][tid];
+            D.uvec[tid] = acc;
         }
     }
     // range of the sample's projections
-    float lo = INFINITY, hi = -INFINITY;
+    lo = INFINITY;
+    hi = -INFINITY;
     for (int i = tid; i < m; i += kTreeThreads) {
         float acc = 0.f;
 #pragma unroll
-        for (int h = 0; h < KMX_DESC_DIM; ++h) acc = fmaf(xs[i][h], vvec[h], acc);
+        for (int h = 0; h < KMX_DESC_DIM; ++h) acc = fmaf(xs[i][h], D.vvec[h], acc);
         lo = fminf(lo, acc);
         hi = fmaxf(hi, acc);
     }
@@ -446,29 +466,138 @@ __global__ void __launch_bounds__(kTreeThreads) tree_dir(const float* __restrict
         hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     }
     if (lane == 0) {
-        redf[0][warp] = lo;
-        redf[1][warp] = hi;
+        D.redf[0][warp] = lo;
+        D.redf[1][warp] = hi;
     }
     __syncthreads();
+    if (tid == 0)
+        for (int q = 1; q < kTreeThreads / 32; ++q) {
+            lo = fminf(lo, D.redf[0][q]);
+            hi = fmaxf(hi, D.redf[1][q]);
+        }
+}
+
+// One CTA per (node of this level, side): the node's centre and principal
+// direction and the range of its sample's projections.  Leaves do nothing.
+__global__ void __launch_bounds__(kTreeThreads) tree_dir(const float* __restrict__ P, int64_t np_cap,
+                                                         const int64_t* d_np, const float* __restrict__ Q,
+                                                         int64_t nq_cap, const int64_t* d_nq,
+                                                         const int32_t* __restrict__ vals, int level,
+                                                         float* __restrict__ dirs)
+{
+    extern __shared__ float tree_smem[];
+    float(*xs)[KMX_DESC_DIM] = reinterpret_cast<float(*)[KMX_DESC_DIM]>(tree_smem);
+    __shared__ DirSmem D;
+    const int side = blockIdx.y;
+    const int64_t k = blockIdx.x;
+    const int64_t n = side ? kmx_count(d_nq, nq_cap) : kmx_count(d_np, np_cap);
+    int64_t start, len;
+    tree_node(n, level, k, start, len);
+    if (len <= kTM) return;
+    float lo, hi;
+    node_direction(side ? Q : P, vals + (side ? kmx_count(d_np, np_cap) : 0) + start, len, xs, D, lo, hi);
     float* d = dirs + (((int64_t)side << level) + k) * kDirStride;
+    const int tid = threadIdx.x;
     if (tid < KMX_DESC_DIM) {
-        d[tid] = cvec[tid];
-        d[KMX_DESC_DIM + tid] = vvec[tid];
+        d[tid] = D.cvec[tid];
+        d[KMX_DESC_DIM + tid] = D.vvec[tid];
     }
     if (tid == 0) {
-        for (int q = 1; q < kTreeThreads / 32; ++q) {
-            lo = fminf(lo, redf[0][q]);
-            hi = fmaxf(hi, redf[1][q]);
-        }
-        d[2 * KMX_DESC_DIM] = fminf(lo, redf[0][0]);
-        d[2 * KMX_DESC_DIM + 1] = fmaxf(hi, redf[1][0]);
+        d[2 * KMX_DESC_DIM] = lo;
+        d[2 * KMX_DESC_DIM + 1] = hi;
     }
 }
 
-// Sort key of every sorted position for this level: side (top bit), node
-// index (level bits), then the row's projection on its node's direction,
-// quantised over the sample's range (0 in a leaf).  Positions past a side's
-// count get the side's largest key, so they stay behind its rows.
+// The last levels of the tree, below `level0` (whose nodes hold at most
+// kFinishRows rows): one CTA per (level-0 node, side) splits its subtree
+// level by level in shared memory.  Per node: its direction, the projections
+// of all its rows, a bitonic sort by (projection, position), and the rows
+// in that order; the next level splits the node where tree_left says.
+__global__ void __launch_bounds__(kTreeThreads) tree_finish(const float* __restrict__ P, int64_t np_cap,
+                                                            const int64_t* d_np, const float* __restrict__ Q,
+                                                            int64_t nq_cap, const int64_t* d_nq,
+                                                            int32_t* __restrict__ vals, int level0, int levels)
+{
+    extern __shared__ float tree_smem[];
+    float(*xs)[KMX_DESC_DIM] = reinterpret_cast<float(*)[KMX_DESC_DIM]>(tree_smem);
+    int32_t* perm = reinterpret_cast<int32_t*>(tree_smem + kTreeSample * KMX_DESC_DIM);  // [kFinishRows]
+    float* pk = reinterpret_cast<float*>(perm + kFinishRows);                             // [kFinishRows]
+    int32_t* pi = reinterpret_cast<int32_t*>(pk + kFinishRows);                           // [kFinishRows]
+    __shared__ DirSmem D;
+    const int side = blockIdx.y;
+    const int tid = threadIdx.x;
+    const int64_t n = side ? kmx_count(d_nq, nq_cap) : kmx_count(d_np, np_cap);
+    int64_t start, len;
+    tree_node(n, level0, blockIdx.x, start, len);
+    if (len <= kTM) return;
+    const float* X = side ? Q : P;
+    int32_t* gv = vals + (side ? kmx_count(d_np, np_cap) : 0) + start;
+    for (int i = tid; i < len; i += kTreeThreads) perm[i] = gv[i];
+    for (int l = level0; l < levels; ++l) {
+        const int sub = l - level0;
+        for (int c = 0; c < (1 << sub); ++c) {
+            // the sub-node's range within the CTA's rows
+            int64_t cs = 0, cl = len;
+            for (int b = sub - 1; b >= 0; --b) {
+                const int64_t h = tree_left(cl);
+                if ((c >> b) & 1) {
+                    cs += h;
+                    cl -= h;
+                } else {
+                    cl = h;
+                }
+            }
+            if (cl <= kTM) continue;
+            float lo, hi;
+            node_direction(X, perm + cs, cl, xs, D, lo, hi);
+            int np2 = 1;
+            while (np2 < cl) np2 <<= 1;
+            for (int i = tid; i < np2; i += kTreeThreads) {
+                float p = INFINITY;
+                if (i < cl) {
+                    const float* x = X + (int64_t)perm[cs + i] * KMX_DESC_STRIDE;
+                    p = 0.f;
+#pragma unroll
+                    for (int h = 0; h < KMX_DESC_DIM; ++h) p = fmaf(__ldg(x + h) - D.cvec[h], D.vvec[h], p);
+                    if (!(p <= INFINITY)) p = INFINITY;  // NaN: a total order for the network
+                }
+                pk[i] = p;
+                pi[i] = i;
+            }
+            __syncthreads();
+            for (int kk = 2; kk <= np2; kk <<= 1) {
+                for (int j = kk >> 1; j > 0; j >>= 1) {
+                    for (int i = tid; i < np2; i += kTreeThreads) {
+                        const int o = i ^ j;
+                        if (o > i) {
+                            const float a = pk[i], b = pk[o];
+                            const int ia = pi[i], ib = pi[o];
+                            const bool gt = a > b || (!(a < b) && ia > ib);
+                            if (gt == ((i & kk) == 0)) {
+                                pk[i] = b;
+                                pk[o] = a;
+                                pi[i] = ib;
+                                pi[o] = ia;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            // the rows in sorted order (pk is free now)
+            int32_t* tmp = reinterpret_cast<int32_t*>(pk);
+            for (int i = tid; i < cl; i += kTreeThreads) tmp[i] = perm[cs + min(pi[i], (int)cl - 1)];
+            __syncthreads();
+            for (int i = tid; i < cl; i += kTreeThreads) perm[cs + i] = tmp[i];
+            __syncthreads();
+        }
+    }
+    for (int i = tid; i < len; i += kTreeThreads) gv[i] = perm[i];
+}
+
+// Sort key of every packed entry for this level: side (top bit), node index
+// (level bits), then the row's projection on its node's direction,
+// quantised over the sample's range (0 in a leaf).
 __global__ void __launch_bounds__(256) tree_key(const float* __restrict__ P, int64_t np_cap, const int64_t* d_np,
                                                 const float* __restrict__ Q, int64_t nq_cap, const int64_t* d_nq,
                                                 const int32_t* __restrict__ vals, int level, int key_bits,
@@ -478,31 +607,23 @@ __global__ void __launch_bounds__(256) tree_key(const float* __restrict__ P, int
     const int pbits = key_bits - 1 - level;
     const int qbits = pbits < 22 ? pbits : 22;
     const float qmax = (float)((1u << qbits) - 1u);
-    const uint32_t side_max = (1u << (key_bits - 1)) - 1u;
-    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < np_cap + nq_cap; e += (int64_t)gridDim.x * 256) {
-        const int side = e >= np_cap;
-        const int64_t pos = side ? e - np_cap : e;
-        const int64_t n = side ? nq : np;
-        uint32_t key;
-        if (pos >= n) {
-            key = side_max;
-        } else {
-            int64_t start, len;
-            const int64_t k = tree_node_of(n, level, pos, start, len);
-            uint32_t q = 0;
-            if (len > kTM) {
-                const float* d = dirs + (((int64_t)side << level) + k) * kDirStride;
-                const float* x = (side ? Q : P) + (int64_t)vals[e] * KMX_DESC_STRIDE;
-                float p = 0.f;
+    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < np + nq; e += (int64_t)gridDim.x * 256) {
+        const int side = e >= np;
+        const int64_t pos = side ? e - np : e;
+        int64_t start, len;
+        const int64_t k = tree_node_of(side ? nq : np, level, pos, start, len);
+        uint32_t q = 0;
+        if (len > kTM) {
+            const float* d = dirs + (((int64_t)side << level) + k) * kDirStride;
+            const float* x = (side ? Q : P) + (int64_t)vals[e] * KMX_DESC_STRIDE;
+            float p = 0.f;
 #pragma unroll
-                for (int h = 0; h < KMX_DESC_DIM; ++h) p = fmaf(__ldg(x + h) - d[h], d[KMX_DESC_DIM + h], p);
-                const float lo = d[2 * KMX_DESC_DIM], hi = d[2 * KMX_DESC_DIM + 1];
-                const float t = hi > lo ? (p - lo) / (hi - lo) * qmax : 0.f;
-                q = (uint32_t)fminf(fmaxf(t, 0.f), qmax) << (pbits - qbits);
-            }
-            key = ((uint32_t)k << pbits) | q;
+            for (int h = 0; h < KMX_DESC_DIM; ++h) p = fmaf(__ldg(x + h) - d[h], d[KMX_DESC_DIM + h], p);
+            const float lo = d[2 * KMX_DESC_DIM], hi = d[2 * KMX_DESC_DIM + 1];
+            const float t = hi > lo ? (p - lo) / (hi - lo) * qmax : 0.f;
+            q = (uint32_t)fminf(fmaxf(t, 0.f), qmax) << (pbits - qbits);
         }
-        keys[e] = ((uint32_t)side << (key_bits - 1)) | key;
+        keys[e] = ((uint32_t)side << (key_bits - 1)) | ((uint32_t)k << pbits) | q;
     }
 }
 
@@ -596,6 +717,28 @@ __global__ void __launch_bounds__(kTN) tc_pack(const float* __restrict__ desc, c
 // plan: first candidates, first bounds and the column tiles each row tile needs
 // ---------------------------------------------------------------------------
 
+// Squared distance between the shared-memory centre cR (33 values) and the
+// centre of tile u (a 36-float row of centres, 16-byte aligned).
+__device__ __forceinline__ float centre_dist2(const float* __restrict__ cR, const float* __restrict__ c)
+{
+    const float4* c4 = reinterpret_cast<const float4*>(c);
+    float d = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const float4 v = __ldg(c4 + q);
+        float e = cR[4 * q] - v.x;
+        d = fmaf(e, e, d);
+        e = cR[4 * q + 1] - v.y;
+        d = fmaf(e, e, d);
+        e = cR[4 * q + 2] - v.z;
+        d = fmaf(e, e, d);
+        e = cR[4 * q + 3] - v.w;
+        d = fmaf(e, e, d);
+    }
+    const float e = cR[32] - __ldg(c + 32);
+    return fmaf(e, e, d);
+}
+
 // False only when no column of a tile with centre distance `dist` and radius
 // `rad` can lie within squared distance u2: for every column y,
 // |x - y| >= |x - c| - |y - c| >= dist - rad (margins for FP32 rounding).
@@ -611,8 +754,8 @@ __device__ __forceinline__ bool tile_may_hold(float dist, float rad, float u2)
 //      (lowest index on ties);
 //   2. each row's exact FP32 distances to the columns of cs (the exact
 //      path's arithmetic): its second-smallest d2 over distinct columns is
-//      an upper bound of the row's d(2); the columns with distance <= d2 are
-//      its first candidates (cnt[row] = their number) and ub[row] = d2;
+//      an upper bound of the row's d(2); the columns with distance <= d2
+//      are its first candidates (cnt[row] = their number), and ub[row] = d2;
 //   3. every other column tile that tile_may_hold for some row of the tile
 //      (first for the whole tile: centre distance minus both radii against
 //      the largest d2, then row by row), in increasing order, into
@@ -627,9 +770,10 @@ __global__ void __launch_bounds__(kTM) tc_plan(const float* __restrict__ X, cons
                                                int64_t need_stride, int32_t* __restrict__ nneed,
                                                int2* __restrict__ items, int* __restrict__ n_items)
 {
-    __shared__ float ys[kTN][KMX_DESC_DIM];
-    __shared__ float sc[kTN][kCenterStride];  // surviving tiles: centre, radius at [33]
+    __shared__ __align__(16) float ys[kTN][kCenterStride];  // the nearest tile's rows, zero-padded to 36
+    __shared__ __align__(16) float sc[kTN][kCenterStride];  // surviving tiles: centre, radius at [33]
     __shared__ int32_t sid[kTN];
+    __shared__ uint8_t rec[kPlanRec][kTM];  // per row: columns recorded in the first pass
     __shared__ float cR[KMX_DESC_DIM];
     __shared__ unsigned needbits[kTN / 32];
     __shared__ int wcnt[kTN / 32];
@@ -659,13 +803,7 @@ __global__ void __launch_bounds__(kTM) tc_plan(const float* __restrict__ X, cons
         float best = INFINITY;
         int bi = 0x7fffffff;
         for (int64_t u = tid; u < n_ct; u += kTM) {
-            const float* c = cenY + u * kCenterStride;
-            float d = 0.f;
-#pragma unroll
-            for (int h = 0; h < KMX_DESC_DIM; ++h) {
-                const float e = cR[h] - __ldg(c + h);
-                d = fmaf(e, e, d);
-            }
+            const float d = centre_dist2(cR, cenY + u * kCenterStride);
             if (d < best) {
                 best = d;
                 bi = (int)u;
@@ -704,37 +842,61 @@ __global__ void __launch_bounds__(kTM) tc_plan(const float* __restrict__ X, cons
         const bool yv = yp < cols;
         const float* yr = yv ? Y + (int64_t)permY[yp] * KMX_DESC_STRIDE : nullptr;
 #pragma unroll
-        for (int h = 0; h < KMX_DESC_DIM; ++h) ys[tid][h] = yv ? __ldg(yr + h) : 0.f;
+        for (int h = 0; h < kCenterStride; ++h) ys[tid][h] = (yv && h < KMX_DESC_DIM) ? __ldg(yr + h) : 0.f;
     }
     __syncthreads();
-    // 2. exact distances to the nearest tile
+    // 2. exact distances to the nearest tile.  One pass finds d1 <= d2 and
+    // records the columns whose distance was at most the running second-
+    // smallest (a superset of those with distance <= d2: the running value
+    // never falls below the final one); only the recorded columns are
+    // compared again (with the same arithmetic, so the same values) and those
+    // within d2 become candidates.  More than kPlanRec records: a second
+    // pass over the whole tile.
     const int ncol = (int)min((int64_t)kTN, cols - cs * kTN);
     float d2 = INFINITY;
     if (valid) {
-        float d1 = INFINITY;
-        for (int j = 0; j < ncol; ++j) {
+        auto dist = [&](int j) -> float {
+            const float4* y4 = reinterpret_cast<const float4*>(ys[j]);
             float acc = 0.f;
 #pragma unroll
-            for (int h = 0; h < KMX_DESC_DIM; ++h) {
-                const float e = x[h] - ys[j][h];
+            for (int c = 0; c < 8; ++c) {
+                const float4 yv4 = y4[c];
+                float e = x[4 * c] - yv4.x;
+                acc = fmaf(e, e, acc);
+                e = x[4 * c + 1] - yv4.y;
+                acc = fmaf(e, e, acc);
+                e = x[4 * c + 2] - yv4.z;
+                acc = fmaf(e, e, acc);
+                e = x[4 * c + 3] - yv4.w;
                 acc = fmaf(e, e, acc);
             }
+            const float e = x[32] - ys[j][32];
+            return fmaf(e, e, acc);
+        };
+        float d1 = INFINITY;
+        int nrec = 0;
+        for (int j = 0; j < ncol; ++j) {
+            const float acc = dist(j);
             if (acc < d1) {
                 d2 = d1;
                 d1 = acc;
             } else if (acc < d2) {
                 d2 = acc;
             }
+            if (acc <= d2) {
+                if (nrec < kPlanRec) rec[nrec][tid] = (uint8_t)j;
+                ++nrec;
+            }
         }
         int k = 0;
-        for (int j = 0; j < ncol; ++j) {
-            float acc = 0.f;
-#pragma unroll
-            for (int h = 0; h < KMX_DESC_DIM; ++h) {
-                const float e = x[h] - ys[j][h];
-                acc = fmaf(e, e, acc);
+        if (nrec <= kPlanRec) {
+            for (int i = 0; i < nrec; ++i) {
+                const int j = rec[i][tid];
+                if (dist(j) <= d2) cand[xrow * kCandCap + k++] = (int32_t)(cs * kTN + j);
             }
-            if (acc <= d2) cand[xrow * kCandCap + k++] = (int32_t)(cs * kTN + j);
+        } else {
+            for (int j = 0; j < ncol; ++j)
+                if (dist(j) <= d2) cand[xrow * kCandCap + k++] = (int32_t)(cs * kTN + j);
         }
         cnt[xrow] = k;
         ub[xrow] = d2;
@@ -749,6 +911,10 @@ __global__ void __launch_bounds__(kTM) tc_plan(const float* __restrict__ X, cons
         __syncthreads();
     }
     const float maxu = s_maxu;
+    float xx = 0.f;
+#pragma unroll
+    for (int h = 0; h < KMX_DESC_DIM; ++h) xx = fmaf(x[h], x[h], xx);
+    const float xn = sqrtf(xx);
     // 3. the other column tiles, 128 at a time
     for (int64_t base = 0; base < n_ct; base += kTN) {
         const int64_t u = base + tid;
@@ -756,12 +922,7 @@ __global__ void __launch_bounds__(kTM) tc_plan(const float* __restrict__ X, cons
         float ru = 0.f;
         if (u < n_ct && u != cs) {
             const float* c = cenY + u * kCenterStride;
-            float d = 0.f;
-#pragma unroll
-            for (int h = 0; h < KMX_DESC_DIM; ++h) {
-                const float e = cR[h] - __ldg(c + h);
-                d = fmaf(e, e, d);
-            }
+            const float d = centre_dist2(cR, c);
             ru = sqrtf(__ldg(c + KMX_DESC_DIM));
             surv = tile_may_hold(sqrtf(d), rR + ru, maxu);
         }
@@ -775,22 +936,46 @@ __global__ void __launch_bounds__(kTM) tc_plan(const float* __restrict__ X, cons
         if (surv) {
             const int idx = off + __popc(bal & ((1u << lane) - 1u));
             sid[idx] = (int32_t)u;
-            const float* c = cenY + u * kCenterStride;
+            const float4* c4 = reinterpret_cast<const float4*>(cenY + u * kCenterStride);
+            float4* s4 = reinterpret_cast<float4*>(sc[idx]);
+            float cc = 0.f;
 #pragma unroll
-            for (int h = 0; h < KMX_DESC_DIM; ++h) sc[idx][h] = __ldg(c + h);
-            sc[idx][KMX_DESC_DIM] = ru;
+            for (int q = 0; q < 9; ++q) {
+                const float4 v = __ldg(c4 + q);
+                s4[q] = v;
+                if (q < 8) {
+                    cc = fmaf(v.x, v.x, cc);
+                    cc = fmaf(v.y, v.y, cc);
+                    cc = fmaf(v.z, v.z, cc);
+                    cc = fmaf(v.w, v.w, cc);
+                } else {
+                    cc = fmaf(v.x, v.x, cc);
+                }
+            }
+            sc[idx][KMX_DESC_DIM] = ru;            // radius
+            sc[idx][KMX_DESC_DIM + 1] = cc;        // |c|^2
+            sc[idx][KMX_DESC_DIM + 2] = sqrtf(cc); // |c|
         }
         __syncthreads();
         for (int q = 0; q < nsurv; ++q) {
             bool nd = false;
             if (valid) {
-                float d = 0.f;
+                // |x - c|^2 = |x|^2 + |c|^2 - 2 x.c with paired FMAs; its
+                // error is below 40 u (|x| + |c|)^2 (u = 2^-24), taken off
+                // before the test
+                const float4* c4 = reinterpret_cast<const float4*>(sc[q]);
+                float2 dot = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int h = 0; h < KMX_DESC_DIM; ++h) {
-                    const float e = x[h] - sc[q][h];
-                    d = fmaf(e, e, d);
+                for (int c = 0; c < 8; ++c) {
+                    const float4 cv = c4[c];
+                    dot = __ffma2_rn(make_float2(x[4 * c], x[4 * c + 1]), make_float2(cv.x, cv.y), dot);
+                    dot = __ffma2_rn(make_float2(x[4 * c + 2], x[4 * c + 3]), make_float2(cv.z, cv.w), dot);
                 }
-                nd = tile_may_hold(sqrtf(d), sc[q][KMX_DESC_DIM], d2);
+                const float4 tail = c4[8];  // [32], radius, |c|^2, |c|
+                const float xc = fmaf(x[32], tail.x, dot.x + dot.y);
+                const float s = xn + tail.w;
+                const float dd = fmaf(-2.f, xc, xx + tail.z) - kDotErr * s * s;
+                nd = tile_may_hold(sqrtf(fmaxf(dd, 0.f)), tail.y, d2);
             }
             const unsigned b = __ballot_sync(0xffffffffu, nd);
             if (lane == 0 && b) atomicOr(&needbits[q >> 5], 1u << (q & 31));
@@ -824,8 +1009,12 @@ __global__ void __launch_bounds__(kTM) tc_plan(const float* __restrict__ X, cons
 // tensor-core candidate collection
 // ---------------------------------------------------------------------------
 
-constexpr int kAStages = 3;   // re-centred row tiles in flight
+constexpr int kAStages = 6;   // re-centred row tiles in flight
 constexpr int kAccBufs = 4;   // TMEM accumulators (4 x 128 columns: the whole TMEM)
+// Tile t goes to epilogue warpgroup t % 2; with even ring sizes every phase
+// of a barrier of the A ring or of the accumulators gets its arrivals from
+// the same warpgroup.
+static_assert(kAStages % 2 == 0 && kAccBufs % 2 == 0, "rings alternate between the two epilogue warpgroups");
 
 struct TcShared {
     uint8_t a[kAStages][kOpBytesA];
@@ -833,7 +1022,10 @@ struct TcShared {
     // per row and A stage: |a|^2 - e, the factor c' |a| of the upper bounds, 2 e
     float4 rowc[kAStages][kTM];
     float gb[kAStages][kTN / 8];  // the column tile's largest |b| per group of 8
-    float2 ul[kTM][2];            // latest (U1, U2) of the two column slices of every row
+    float2 ul[kTM][2];            // latest (U1, U2) of every row from each epilogue warpgroup
+    // candidates of the current item per (warpgroup, row), appended to the row's
+    // global list when full and at the item's end (stride 17: no bank conflicts)
+    int32_t cbuf[2][kTM][kCandBuf + 1];
     uint64_t full_b[kStages], empty_b[kStages];
     uint64_t full_a[kAStages], empty_a[kAStages];
     uint64_t acc_full[kAccBufs], acc_empty[kAccBufs];
@@ -862,12 +1054,14 @@ __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" :::
 //                     of four TMEM accumulators and commits to the barriers
 //                     that free the accumulator's reader, the A stage and the
 //                     B stage;
-//   warps 8..15       epilogue: warp w reads TMEM lanes 32 (w & 3) .. + 31,
-//                     columns 64 ((w - 8) >> 2) .. + 63 of the accumulator.
-// The two epilogue threads of a row keep their own upper bounds over their
-// own columns and publish them after every tile; each combines its own with
-// the other's latest published pair (their column sets are disjoint, so any
-// snapshot is a valid bound).  Both start an item from the row's bound U
+//   warps 8..15       epilogue, two warpgroups: warps 8..11 take the tiles
+//                     t with t % 2 == 0, warps 12..15 the others; warp w reads
+//                     TMEM lanes 32 (w & 3) .. + 31, all 128 columns of the
+//                     tile's accumulator in two halves of 64.
+// The two epilogue threads of a row (one per warpgroup) keep their own upper
+// bounds over their own tiles' columns and publish them after every tile;
+// each combines its own with the other's latest published pair (their column
+// sets are disjoint, so any snapshot is a valid bound).  Both start an item from the row's bound U
 // counted as two columns at U (the two best columns of the plan's tile,
 // which no item holds); at an item boundary the epilogue warps meet on a
 // named barrier, so that no thread reads a bound of the previous item's row.
@@ -901,11 +1095,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_collect(const float* __restric
         }
         for (int st = 0; st < kAStages; ++st) {
             mbar_init(&S.full_a[st], 4);           // re-centring warps
-            mbar_init(&S.empty_a[st], 1 + 8);      // MMA commit + the 8 epilogue warps
+            mbar_init(&S.empty_a[st], 1 + 4);      // MMA commit + the 4 warps of the tile's epilogue warpgroup
         }
         for (int k = 0; k < kAccBufs; ++k) {
             mbar_init(&S.acc_full[k], 1);          // MMA commit
-            mbar_init(&S.acc_empty[k], 8);         // epilogue warps
+            mbar_init(&S.acc_empty[k], 4);         // the 4 warps of the tile's epilogue warpgroup
         }
         mbar_fence_init();
         S.failed = 0;
@@ -1005,18 +1199,24 @@ __global__ void __launch_bounds__(kThreads, 1) tc_collect(const float* __restric
                 const uint8_t* bt = S.b[st];
                 const float4* cen4 = reinterpret_cast<const float4*>(bt + kHdrCenter);
                 float v[kK];
-                float p2 = 0.f;
+                // paired FP32 operations (the same per-lane rounding); |a|^2
+                // as two interleaved partial sums
+                float2 q2 = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     const float4 cv = cen4[c];
-                    v[4 * c + 0] = x[4 * c + 0] - cv.x;
-                    v[4 * c + 1] = x[4 * c + 1] - cv.y;
-                    v[4 * c + 2] = x[4 * c + 2] - cv.z;
-                    v[4 * c + 3] = x[4 * c + 3] - cv.w;
+                    // x + (-c) is exactly x - c
+                    const float2 d0 = __fadd2_rn(make_float2(x[4 * c + 0], x[4 * c + 1]), make_float2(-cv.x, -cv.y));
+                    const float2 d1 = __fadd2_rn(make_float2(x[4 * c + 2], x[4 * c + 3]), make_float2(-cv.z, -cv.w));
+                    v[4 * c + 0] = d0.x;
+                    v[4 * c + 1] = d0.y;
+                    v[4 * c + 2] = d1.x;
+                    v[4 * c + 3] = d1.y;
+                    q2 = __ffma2_rn(d0, d0, q2);
+                    q2 = __ffma2_rn(d1, d1, q2);
                 }
                 v[32] = x[32] - reinterpret_cast<const float*>(bt + kHdrCenter)[32];
-#pragma unroll
-                for (int h = 0; h < KMX_DESC_DIM; ++h) p2 = fmaf(v[h], v[h], p2);
+                const float p2 = fmaf(v[32], v[32], q2.x + q2.y);
                 const float al = sqrtf(p2);
                 v[KMX_DESC_DIM] = kSqrtC * al;
                 v[KMX_DESC_DIM + 1] = -0.5f;
@@ -1038,8 +1238,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_collect(const float* __restric
         }
     } else if (warp >= 8) {
         // ---- epilogue
-        const int quarter = warp & 3, slice = (warp - 8) >> 2;
+        const int quarter = warp & 3, wg = (warp - 8) >> 2;  // warpgroup wg takes the tiles t with t % 2 == wg
         const int r = quarter * 32 + lane;
+        int32_t* cbuf = S.cbuf[wg][r];
+        int nbuf = 0;
+        // one atomic per flush reserves the places in the row's global list
+        auto flush_cands = [&](int64_t row, int nb) {
+            const int pos = atomicAdd(cnt + row, nb);
+            for (int i = 0; i < nb; ++i)
+                if (pos + i < kCandCap) cand[row * kCandCap + pos + i] = cbuf[i];
+        };
         int t = 0;
         bool dead = false;
         // every epilogue warp runs every item (after a failure without
@@ -1052,17 +1260,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_collect(const float* __restric
             const bool row_valid = row < rows;
             float U1 = row_valid ? __ldcg(ub + row) : FLT_MAX, U2 = U1;
             epi_sync();  // the previous item's bounds are no longer read
-            *reinterpret_cast<volatile unsigned long long*>(&S.ul[r][slice]) =
+            *reinterpret_cast<volatile unsigned long long*>(&S.ul[r][wg]) =
                 (unsigned long long)__float_as_uint(U1) | ((unsigned long long)__float_as_uint(U2) << 32);
             epi_sync();
             for (int k = 0; k < nt; ++k, ++t) {
+                if ((t & 1) != wg) continue;  // the other warpgroup's tile
                 const int sa = t % kAStages, ab = t % kAccBufs;
                 if (dead) continue;
                 bool ok = !*failed;
                 if (ok) ok = mbar_wait(&S.acc_full[ab], (t / kAccBufs) & 1);
                 // the A stage (row constants) cannot be refilled before this
-                // warp's arrival on empty_a, so its phase t / kAStages is the
-                // current one: the wait only acquires the re-centring writes
+                // warpgroup's arrival on empty_a, so its phase t / kAStages is
+                // the current one: the wait only acquires the re-centring writes
                 if (ok) ok = mbar_wait(&S.full_a[sa], (t / kAStages) & 1);
                 if (!__all_sync(0xffffffffu, ok)) {
                     if (lane == 0) *failed = 1;
@@ -1073,83 +1282,88 @@ __global__ void __launch_bounds__(kThreads, 1) tc_collect(const float* __restric
                 const float4 rc = S.rowc[sa][r];
                 const float rb = rc.x, ua = rc.y, ue = rc.z;
                 // one 64-bit load: the pair is never seen half written
-                const unsigned long long ou = *reinterpret_cast<volatile unsigned long long*>(&S.ul[r][slice ^ 1]);
+                const unsigned long long ou = *reinterpret_cast<volatile unsigned long long*>(&S.ul[r][wg ^ 1]);
                 const float2 other =
                     make_float2(__uint_as_float((uint32_t)ou), __uint_as_float((uint32_t)(ou >> 32)));
-                const float* gbeta = S.gb[sa] + slice * 8;
-                const int64_t col0 = (int64_t)tl[k] * kTN + slice * 64;
-                float v[64];
-                tmem_ld64(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * kTN + slice * 64), v);
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) {
-                    mbar_arrive(&S.acc_empty[ab]);  // the accumulator is read
-                }
-                // the second-smallest upper bound over both slices' columns
-                const float Ush = fminf(fmaxf(U1, other.x), U1 <= other.x ? U2 : other.y);
-                float Lm[8];
-#pragma unroll
-                for (int g = 0; g < 8; ++g) {
-                    const float* vg = v + 8 * g;
-                    const float m =
-                        fmax3(fmax3(vg[0], vg[1], vg[2]), fmax3(vg[3], vg[4], vg[5]), fmaxf(vg[6], vg[7]));
-                    // L = |a|^2 - e - 2 M is monotone in M: the group's largest M
-                    // gives its smallest L
-                    Lm[g] = fmaf(-2.f, m, rb);
-                }
-                const float lmin =
-                    fmin3(fmin3(Lm[0], Lm[1], Lm[2]), fmin3(Lm[3], Lm[4], Lm[5]), fminf(Lm[6], Lm[7]));
-                if (row_valid && lmin <= fminf(U2, Ush)) {
+                const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * kTN);
+#pragma unroll 1
+                for (int h = 0; h < 2; ++h) {  // the two 64-column halves of the tile
+                    float v[64];
+                    tmem_ld64(tbase + (uint32_t)(h * 64), v);
+                    if (h == 1) {
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&S.acc_empty[ab]);  // the accumulator is read
+                    }
+                    const float* gbeta = S.gb[sa] + h * 8;
+                    const int64_t col0 = (int64_t)tl[k] * kTN + h * 64;
+                    // the second-smallest upper bound over both warpgroups' columns
+                    const float Ush = fminf(fmaxf(U1, other.x), U1 <= other.x ? U2 : other.y);
+                    float Lm[8];
 #pragma unroll
                     for (int g = 0; g < 8; ++g) {
                         const float* vg = v + 8 * g;
-                        const float Lmin = Lm[g];
-                        if (Lmin <= fminf(U2, Ush)) {
-                            // the group's two best columns (largest M first):
-                            // upper bounds for them
-                            float h0 = fmaxf(vg[0], vg[1]), l0 = fminf(vg[0], vg[1]);
-                            float h1 = fmaxf(vg[2], vg[3]), l1 = fminf(vg[2], vg[3]);
-                            float h2 = fmaxf(vg[4], vg[5]), l2 = fminf(vg[4], vg[5]);
-                            float h3 = fmaxf(vg[6], vg[7]), l3 = fminf(vg[6], vg[7]);
-                            l0 = fmaxf(fminf(h0, h1), fmaxf(l0, l1));
-                            h0 = fmaxf(h0, h1);
-                            l2 = fmaxf(fminf(h2, h3), fmaxf(l2, l3));
-                            h2 = fmaxf(h2, h3);
-                            const float m2 = fmaxf(fminf(h0, h2), fmaxf(l0, l2));
-                            const float uadd = fmaf(ua, gbeta[g], ue);
-                            const float Ua = Lmin + uadd, Ub = fmaf(-2.f, m2, rb) + uadd;
-                            if (Ua < U1) {
-                                U2 = fminf(U1, Ub);
-                                U1 = Ua;
-                            } else if (Ua < U2) {
-                                U2 = Ua;
-                            }
-                            const float thr = fminf(U2, Ush);
-                            unsigned msk = 0;
+                        const float m =
+                            fmax3(fmax3(vg[0], vg[1], vg[2]), fmax3(vg[3], vg[4], vg[5]), fmaxf(vg[6], vg[7]));
+                        // L = |a|^2 - e - 2 M is monotone in M: the group's
+                        // largest M gives its smallest L
+                        Lm[g] = fmaf(-2.f, m, rb);
+                    }
+                    const float lmin =
+                        fmin3(fmin3(Lm[0], Lm[1], Lm[2]), fmin3(Lm[3], Lm[4], Lm[5]), fminf(Lm[6], Lm[7]));
+                    if (row_valid && lmin <= fminf(U2, Ush)) {
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) msk |= (fmaf(-2.f, vg[j], rb) <= thr ? 1u : 0u) << j;
-                            const int nc = __popc(msk);
-                            if (nc) {
-                                int pos = atomicAdd(cnt + row, nc);
+                        for (int g = 0; g < 8; ++g) {
+                            const float* vg = v + 8 * g;
+                            const float Lmin = Lm[g];
+                            if (Lmin <= fminf(U2, Ush)) {
+                                // the group's two best columns (largest M
+                                // first): upper bounds for them
+                                float h0 = fmaxf(vg[0], vg[1]), l0 = fminf(vg[0], vg[1]);
+                                float h1 = fmaxf(vg[2], vg[3]), l1 = fminf(vg[2], vg[3]);
+                                float h2 = fmaxf(vg[4], vg[5]), l2 = fminf(vg[4], vg[5]);
+                                float h3 = fmaxf(vg[6], vg[7]), l3 = fminf(vg[6], vg[7]);
+                                l0 = fmaxf(fminf(h0, h1), fmaxf(l0, l1));
+                                h0 = fmaxf(h0, h1);
+                                l2 = fmaxf(fminf(h2, h3), fmaxf(l2, l3));
+                                h2 = fmaxf(h2, h3);
+                                const float m2 = fmaxf(fminf(h0, h2), fmaxf(l0, l2));
+                                const float uadd = fmaf(ua, gbeta[g], ue);
+                                const float Ua = Lmin + uadd, Ub = fmaf(-2.f, m2, rb) + uadd;
+                                if (Ua < U1) {
+                                    U2 = fminf(U1, Ub);
+                                    U1 = Ua;
+                                } else if (Ua < U2) {
+                                    U2 = Ua;
+                                }
+                                const float thr = fminf(U2, Ush);
+                                unsigned msk = 0;
+#pragma unroll
+                                for (int j = 0; j < 8; ++j) msk |= (fmaf(-2.f, vg[j], rb) <= thr ? 1u : 0u) << j;
                                 while (msk) {
                                     const int j = __ffs(msk) - 1;
                                     msk &= msk - 1;
-                                    if (pos < kCandCap) cand[row * kCandCap + pos] = (int32_t)(col0 + 8 * g + j);
-                                    ++pos;
+                                    if (nbuf == kCandBuf) {
+                                        flush_cands(row, nbuf);
+                                        nbuf = 0;
+                                    }
+                                    cbuf[nbuf++] = (int32_t)(col0 + 8 * g + j);
                                 }
                             }
                         }
                     }
                 }
-                *reinterpret_cast<volatile unsigned long long*>(&S.ul[r][slice]) =
+                *reinterpret_cast<volatile unsigned long long*>(&S.ul[r][wg]) =
                     (unsigned long long)__float_as_uint(U1) | ((unsigned long long)__float_as_uint(U2) << 32);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&S.empty_a[sa]);  // the row constants are read
             }
+            if (!dead && nbuf > 0) flush_cands(row, nbuf);
+            nbuf = 0;
             if (!dead && row_valid) {
                 // lower the row's bound for the items that start later (bounds
                 // are >= 0, so their bits order like integers)
-                const unsigned long long ou = *reinterpret_cast<volatile unsigned long long*>(&S.ul[r][slice ^ 1]);
+                const unsigned long long ou = *reinterpret_cast<volatile unsigned long long*>(&S.ul[r][wg ^ 1]);
                 const float ox = __uint_as_float((uint32_t)ou), oy = __uint_as_float((uint32_t)(ou >> 32));
                 const float Uf = fminf(U2, fminf(fmaxf(U1, ox), U1 <= ox ? U2 : oy));
                 if (Uf >= 0.f) atomicMin(reinterpret_cast<int*>(ub + row), __float_as_int(Uf));
@@ -1247,8 +1461,8 @@ __global__ void __launch_bounds__(256) compact_flags(int64_t n_cap, const int64_
     if (flags[i]) list[pos[i]] = (int32_t)i;
 }
 
-// Merge the exact fallback partials of each listed row and store them where
-// the re-ranked rows went.
+// Merge the exact fallback partials of each listed row (chunk c's partials
+// at part[c * list length ...]) and store them where the re-ranked rows went.
 __global__ void __launch_bounds__(256) fallback_merge(const kmx::RowBest* __restrict__ part,
                                                       const int* __restrict__ d_chunks, int64_t list_cap,
                                                       const int32_t* __restrict__ list,
@@ -1257,11 +1471,12 @@ __global__ void __launch_bounds__(256) fallback_merge(const kmx::RowBest* __rest
                                                       unsigned long long* __restrict__ cols_best)
 {
     const int64_t r = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    if (r >= min(*n_list, list_cap)) return;
+    const int64_t n = min(*n_list, list_cap);
+    if (r >= n) return;
     kmx::RowBest b = part[r];
     const int chunks = *d_chunks;
     for (int c = 1; c < chunks; ++c) {
-        const kmx::RowBest o = part[(int64_t)c * list_cap + r];
+        const kmx::RowBest o = part[(int64_t)c * n + r];
         kmx::row_merge(b.d1, b.j1, b.d2, o.d1, o.j1, o.d2);
     }
     const int i = list[r];
@@ -1279,7 +1494,9 @@ size_t tc_smem_bytes()
 
 struct TcBuffers {
     uint32_t *keys, *keys_tmp;
-    int32_t *vals, *vals_tmp;  // sorted: [0, np) source rows, [np_cap, np_cap + nq) target rows
+    int32_t *vals, *vals_tmp;  // the tree's packed entries (source rows, then target rows)
+    int32_t* perm;             // sorted: [0, np) source rows, [np_cap, np_cap + nq) target rows
+    int64_t* n2;               // np + nq on the device
     void* sort_scratch;
     float* dirs;               // [2 << (levels - 1)][kDirStride]
     uint8_t *packP, *packQ;
@@ -1313,6 +1530,8 @@ TcBuffers tc_carve(void* base, int64_t np_cap, int64_t nq_cap, size_t* total)
     b.keys_tmp = (uint32_t*)a.take(sizeof(uint32_t) * (size_t)n2);
     b.vals = (int32_t*)a.take(sizeof(int32_t) * (size_t)n2);
     b.vals_tmp = (int32_t*)a.take(sizeof(int32_t) * (size_t)n2);
+    b.perm = (int32_t*)a.take(sizeof(int32_t) * (size_t)n2);
+    b.n2 = (int64_t*)a.take(sizeof(int64_t));
     b.sort_scratch = a.take(kmx_sort_scratch_bytes(n2));
     b.dirs = (float*)a.take(sizeof(float) * kDirStride * ((size_t)2 << (levels > 0 ? levels - 1 : 0)));
     b.packP = (uint8_t*)a.take((size_t)tp * kColBytes);
@@ -1370,7 +1589,9 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
     cudaError_t e = kmx_once_per_device(kmx_attr_tc_topk, [smem] {
         cudaError_t r = cudaFuncSetAttribute(tc_collect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (r) return r;
-        return cudaFuncSetAttribute(tree_dir, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTreeSmem);
+        r = cudaFuncSetAttribute(tree_dir, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTreeSmem);
+        if (r) return r;
+        return cudaFuncSetAttribute(tree_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFinishSmem);
     });
     if (e) return e;
     if ((e = cudaMemsetAsync(b.flagP, 0, sizeof(int32_t) * (np_cap + 1), st))) return e;
@@ -1380,18 +1601,28 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
     // locality order of both clouds: one tree level per sort
     const unsigned gb = kmx_stride_blocks(n2, 256, ctx->sm_count);
     KMX_COUNT_LAUNCH();
-    tree_init<<<gb, 256, 0, st>>>(np_cap, n2, b.vals);
-    for (int l = 0; l < levels; ++l) {
+    tree_init<<<gb, 256, 0, st>>>(np_cap, d_np, nq_cap, d_nq, b.vals, b.n2);
+    const int level0 = levels > kFinishLevels ? levels - kFinishLevels : 0;
+    for (int l = 0; l < level0; ++l) {
         KMX_COUNT_LAUNCH();
         tree_dir<<<dim3(1u << l, 2), kTreeThreads, kTreeSmem, st>>>(dp, np_cap, d_np, dq, nq_cap, d_nq, b.vals, l,
                                                                      b.dirs);
         KMX_COUNT_LAUNCH();
         tree_key<<<gb, 256, 0, st>>>(dp, np_cap, d_np, dq, nq_cap, d_nq, b.vals, l, key_bits, b.dirs, b.keys);
         if ((e = cudaGetLastError())) return e;
-        if ((e = kmx_sort_u32(ctx, b.keys, b.vals, b.keys_tmp, b.vals_tmp, n2, key_bits, b.sort_scratch))) return e;
+        if ((e = kmx_sort_u32(ctx, b.keys, b.vals, b.keys_tmp, b.vals_tmp, n2, b.n2, key_bits, b.sort_scratch)))
+            return e;
     }
-    const int32_t* permP = b.vals;
-    const int32_t* permQ = b.vals + np_cap;
+    if (levels > 0) {  // the subtrees of at most 16 tiles, one CTA each
+        KMX_COUNT_LAUNCH();
+        tree_finish<<<dim3(1u << level0, 2), kTreeThreads, kFinishSmem, st>>>(dp, np_cap, d_np, dq, nq_cap, d_nq,
+                                                                             b.vals, level0, levels);
+        if ((e = cudaGetLastError())) return e;
+    }
+    KMX_COUNT_LAUNCH();
+    tree_out<<<gb, 256, 0, st>>>(np_cap, d_np, nq_cap, d_nq, b.vals, b.perm);
+    const int32_t* permP = b.perm;
+    const int32_t* permQ = b.perm + np_cap;
     // packed tiles, centres and radii
     KMX_COUNT_LAUNCH();
     tc_pack<<<(unsigned)tp, kTN, 0, st>>>(dp, permP, np_cap, d_np, b.packP, b.cenP, ctx->d_err);

@@ -25,10 +25,12 @@ constexpr int kPerBlock = kThreads * kItems;
 constexpr int kDigits = 256;
 constexpr int kWarps = kThreads / 32;
 
-__global__ void __launch_bounds__(kThreads) radix_count(const uint32_t* __restrict__ keys, int64_t n, int shift,
-                                                        int32_t* __restrict__ counts, int blocks)
+__global__ void __launch_bounds__(kThreads) radix_count(const uint32_t* __restrict__ keys, int64_t n_cap,
+                                                        const int64_t* d_n, int shift, int32_t* __restrict__ counts,
+                                                        int blocks)
 {
     __shared__ int hist[kDigits];
+    const int64_t n = kmx_count(d_n, n_cap);
     hist[threadIdx.x] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kPerBlock;
@@ -42,11 +44,14 @@ __global__ void __launch_bounds__(kThreads) radix_count(const uint32_t* __restri
 }
 
 __global__ void __launch_bounds__(kThreads) radix_scatter(const uint32_t* __restrict__ keys,
-                                                          const int32_t* __restrict__ vals, int64_t n, int shift,
+                                                          const int32_t* __restrict__ vals, int64_t n_cap,
+                                                          const int64_t* d_n, int shift,
                                                           const int64_t* __restrict__ offs, int blocks,
                                                           uint32_t* __restrict__ keys_out,
                                                           int32_t* __restrict__ vals_out)
 {
+    const int64_t n = kmx_count(d_n, n_cap);
+    if ((int64_t)blockIdx.x * kPerBlock >= n) return;  // no element here (block-uniform)
     __shared__ int wcount[kWarps][kDigits];  // this item's count per warp and digit, then its warp prefix
     __shared__ int running[kDigits];         // elements of earlier items, per digit
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -92,6 +97,18 @@ __global__ void __launch_bounds__(kThreads) radix_scatter(const uint32_t* __rest
     }
 }
 
+// The result back into the callers' arrays after an odd number of passes.
+__global__ void __launch_bounds__(256) radix_copy(const uint32_t* __restrict__ ks, const int32_t* __restrict__ vs,
+                                                  int64_t n_cap, const int64_t* d_n, uint32_t* __restrict__ kd,
+                                                  int32_t* __restrict__ vd)
+{
+    const int64_t n = kmx_count(d_n, n_cap);
+    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < n; e += (int64_t)gridDim.x * 256) {
+        kd[e] = ks[e];
+        vd[e] = vs[e];
+    }
+}
+
 }  // namespace
 
 int kmx_sort_blocks(int64_t n) { return (int)((n + kPerBlock - 1) / kPerBlock); }
@@ -106,7 +123,7 @@ size_t kmx_sort_scratch_bytes(int64_t n)
 }
 
 cudaError_t kmx_sort_u32(kmx_ctx* ctx, uint32_t* keys, int32_t* vals, uint32_t* keys_tmp, int32_t* vals_tmp,
-                         int64_t n, int bits, void* scratch)
+                         int64_t n, const int64_t* d_n, int bits, void* scratch)
 {
     if (n <= 0) return cudaSuccess;
     const int blocks = kmx_sort_blocks(n);
@@ -119,11 +136,11 @@ cudaError_t kmx_sort_u32(kmx_ctx* ctx, uint32_t* keys, int32_t* vals, uint32_t* 
     cudaError_t e;
     for (int shift = 0; shift < bits; shift += 8) {
         KMX_COUNT_LAUNCH();
-        radix_count<<<blocks, kThreads, 0, ctx->stream>>>(ki, n, shift, counts, blocks);
+        radix_count<<<blocks, kThreads, 0, ctx->stream>>>(ki, n, d_n, shift, counts, blocks);
         if ((e = cudaGetLastError())) return e;
         if ((e = kmx_scan_i32(ctx, counts, m, nullptr, offs))) return e;
         KMX_COUNT_LAUNCH();
-        radix_scatter<<<blocks, kThreads, 0, ctx->stream>>>(ki, vi, n, shift, offs, blocks, ko, vo);
+        radix_scatter<<<blocks, kThreads, 0, ctx->stream>>>(ki, vi, n, d_n, shift, offs, blocks, ko, vo);
         if ((e = cudaGetLastError())) return e;
         uint32_t* tk = ki;
         ki = ko;
@@ -133,8 +150,9 @@ cudaError_t kmx_sort_u32(kmx_ctx* ctx, uint32_t* keys, int32_t* vals, uint32_t* 
         vo = tv;
     }
     if (ki != keys) {  // an odd number of passes: the result is in the temporaries
-        if ((e = cudaMemcpyAsync(keys, ki, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream))) return e;
-        if ((e = cudaMemcpyAsync(vals, vi, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream))) return e;
+        KMX_COUNT_LAUNCH();
+        radix_copy<<<kmx_stride_blocks(n, 256, ctx->sm_count), 256, 0, ctx->stream>>>(ki, vi, n, d_n, keys, vals);
+        if ((e = cudaGetLastError())) return e;
     }
     return cudaSuccess;
 }

@@ -650,6 +650,20 @@ def test_match_bf16_duplicates_overflow_to_exact(torch_cuda, ctx):
     assert diag[0] >= 51, "the 51 rows equal to the duplicated descriptor overflow: %s" % diag
 
 
+def test_match_bf16_one_overflow_row_many_columns(torch_cuda, ctx):
+    """One source row ties with 700 target rows: its list overflows and the
+    exact fallback spreads that single row over hundreds of column chunks
+    (partials packed by the list length); the result is byte-identical."""
+    rng = np.random.default_rng(23)
+    FP = rng.gamma(0.5, 20.0, (2000, 33)).astype(np.float32)
+    FQ = rng.gamma(0.5, 20.0, (40000, 33)).astype(np.float32)
+    FQ[1000:1700] = FP[7]
+    n = _same_as_exact(torch_cuda, ctx, FP, FQ)
+    assert n > 0
+    diag = ctx.match_diag(len(FP), len(FQ)).cpu().numpy()
+    assert diag[0] >= 1, "row 7 overflows: %s" % diag
+
+
 def test_match_bf16_nonfinite_is_range_error(torch_cuda, ctx):
     from paper_2409_15615_gb300 import kmx
 
