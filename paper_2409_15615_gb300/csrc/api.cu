@@ -334,6 +334,7 @@ kmx_status kmx_build_grid(kmx_ctx* c, const float* d_xyz4, int64_t n_cap, const 
     g->keys = (unsigned long long*)a.take(sizeof(unsigned long long) * T);
     g->cells = (int2*)a.take(sizeof(int2) * T);
     g->sorted = (float4*)a.take(sizeof(float4) * (n_cap + 1));
+    g->sslot = (int32_t*)a.take(sizeof(int32_t) * (n_cap + 1));
     g->d_n_own = (int64_t*)a.take(sizeof(int64_t));
     g->d_n_sorted = (int64_t*)a.take(sizeof(int64_t));
     kmx_status s = ensure_ws(c, kmx_grid_scratch_bytes(n_cap, T));

@@ -83,12 +83,15 @@ __global__ void __launch_bounds__(kThreads) spfh_kernel(int64_t n_cap, const int
             bool ok = false, valid = false;
             if (t < e) {
                 const int k = nbr[t];
-                // bit0 is never written here, so a byte another warp is
-                // updating still shows the same B
+                // the point and normal are loaded with the flag (one round
+                // trip instead of two); bit0 is never written here, so a byte
+                // another warp is updating still shows the same B
+                const float4 pk = __ldg(&pts[k]);
+                const float4 nk = __ldg(&normal4[k]);
                 valid = (flags[k] & 1) != 0;
                 if (k != q && valid) {
                     float f[3];
-                    ok = pair_features(pq, nq, __ldg(&pts[k]), __ldg(&normal4[k]), f);
+                    ok = pair_features(pq, nq, pk, nk, f);
                     if (ok) {
                         atomicAdd(&hist[warp][feature_bin(f[0], -PI, PI)], 1);
                         atomicAdd(&hist[warp][kH + feature_bin(f[1], -1.f, 1.f)], 1);
@@ -162,8 +165,8 @@ __global__ void __launch_bounds__(kThreads) fpfh_kernel(int64_t n_cap, const int
             for (int i = 0; i < cnt; ++i) {
                 const float* r = spfh + (int64_t)sk[warp][i] * kStride;
                 const float we = sw[warp][i];
-                kahan_add(acc, comp, __ldg(&r[lane]) * we);
-                if (lane == 0) kahan_add(acc32, comp32, __ldg(&r[32]) * we);
+                kahan_add_prod(acc, comp, __ldg(&r[lane]), we);
+                if (lane == 0) kahan_add_prod(acc32, comp32, __ldg(&r[32]), we);
             }
             __syncwarp();
         }

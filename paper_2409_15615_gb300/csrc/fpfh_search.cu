@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kThreads) walk_normals(GridView g, Radii R, fl
             }
             const float4 q = g.sorted[p];
             int start, excl;
-            const int total = stencil(g, q, lane, &start, &excl);
+            const int total = stencil(g, p, lane, &start, &excl);
             // sweep 1: |I|, |P_normal| and the mean offset from q
             int nf = 0, nn = 0;
             float sx = 0.f, sy = 0.f, sz = 0.f;
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(kThreads) valid_walk(GridView g, Radii R, int 
         const uint8_t fq = flags[qi];
         if (!(fq & 1)) continue;
         int start, excl;
-        const int total = stencil(g, q, lane, &start, &excl);
+        const int total = stencil(g, p, lane, &start, &excl);
         int mv = 0;
         for (int base = 0; base < total; base += 32) {
             const int t = base + lane;
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(kThreads) spfh_walk(GridView g, Radii R, const
         __syncwarp();
         const float4 nq = normal4[qi];
         int start, excl;
-        const int total = stencil(g, q, lane, &start, &excl);
+        const int total = stencil(g, p, lane, &start, &excl);
         int pairs = 0;
         for (int base = 0; base < total; base += 32) {
             const int t = base + lane;
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kThreads) fpfh_walk(GridView g, Radii R, const
         const int qi = __float_as_int(q.w);
         if (!(flags[qi] & 2)) continue;
         int start, excl;
-        const int total = stencil(g, q, lane, &start, &excl);
+        const int total = stencil(g, p, lane, &start, &excl);
         float acc = 0.f, comp = 0.f, acc32 = 0.f, comp32 = 0.f;
         int m = 0;
         for (int base = 0; base < total; base += 32) {
@@ -334,8 +334,8 @@ __global__ void __launch_bounds__(kThreads) fpfh_walk(GridView g, Radii R, const
             for (int i = 0; i < cnt; ++i) {
                 const float* r = spfh + (int64_t)sk[warp][i] * kStride;
                 const float we = sw[warp][i];
-                kahan_add(acc, comp, __ldg(&r[lane]) * we);
-                if (lane == 0) kahan_add(acc32, comp32, __ldg(&r[32]) * we);
+                kahan_add_prod(acc, comp, __ldg(&r[lane]), we);
+                if (lane == 0) kahan_add_prod(acc32, comp32, __ldg(&r[32]), we);
             }
             __syncwarp();
         }
@@ -364,7 +364,7 @@ cudaError_t kmx_fpfh_search_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_pa
     size_t total = 0;
     ClassicScratch s = carve(scratch, g->n_cap, spfh == nullptr, &total);
     float* sp = spfh ? spfh : s.spfh;
-    GridView gv{g->sorted, g->cells, g->keys, g->table_size, g->inv_cell, g->d_n_sorted};
+    GridView gv{g->sorted, g->cells, g->keys, g->table_size, g->inv_cell, g->d_n_sorted, g->sslot};
     Radii R;
     R.rf2 = prm->r_fpfh * prm->r_fpfh;
     R.rn2 = prm->r_normal * prm->r_normal;

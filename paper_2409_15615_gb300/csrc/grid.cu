@@ -80,7 +80,8 @@ __global__ void __launch_bounds__(kThreads) grid_scatter(int64_t n_cap, const in
 // indices there) places it, so each cell holds its points in ascending index
 // order, with the index in w.
 __global__ void __launch_bounds__(kThreads) grid_fill(const float4* __restrict__ pts, int64_t n_cap,
-                                                      const int64_t* d_n, GridScratch s, float4* __restrict__ sorted)
+                                                      const int64_t* d_n, GridScratch s, float4* __restrict__ sorted,
+                                                      int32_t* __restrict__ sslot)
 {
     const int64_t n = kmx_count(d_n, n_cap);
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
@@ -93,6 +94,7 @@ __global__ void __launch_bounds__(kThreads) grid_fill(const float4* __restrict__
         for (int f = 0; f < L; ++f) rank += (seg[f] < (int32_t)i);
         const float4 p = pts[i];
         sorted[b + rank] = make_float4(p.x, p.y, p.z, __int_as_float((int32_t)i));
+        sslot[b + rank] = slot;
     }
 }
 
@@ -107,6 +109,7 @@ size_t kmx_grid_bytes(int64_t n_cap, uint32_t* table_size)
     a.take(sizeof(unsigned long long) * T);
     a.take(sizeof(int2) * T);
     a.take(sizeof(float4) * (n_cap + 1));
+    a.take(sizeof(int32_t) * (n_cap + 1));  // cell slot per sorted point
     a.take(sizeof(int64_t));  // grid-owned count
     a.take(sizeof(int64_t));  // bucketed count
     return kmx_align_up(a.used, 256);
@@ -138,6 +141,6 @@ cudaError_t kmx_grid_build_launch(kmx_ctx* ctx, kmx_grid* g, void* scratch)
     KMX_COUNT_LAUNCH();
     grid_scatter<<<nb, kThreads, 0, st>>>(g->n_cap, g->d_n, s);
     KMX_COUNT_LAUNCH();
-    grid_fill<<<nb, kThreads, 0, st>>>(g->pts, g->n_cap, g->d_n, s, g->sorted);
+    grid_fill<<<nb, kThreads, 0, st>>>(g->pts, g->n_cap, g->d_n, s, g->sorted, g->sslot);
     return cudaGetLastError();
 }

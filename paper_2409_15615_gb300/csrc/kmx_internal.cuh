@@ -49,6 +49,7 @@ struct kmx_grid {
     unsigned long long* keys;  // [table_size] packed cell keys, ~0 = empty
     int2* cells;            // [table_size] (start, count) in sorted order
     float4* sorted;         // [n_cap] points in cell order, w = original index (int bits)
+    int32_t* sslot;         // [n_cap] hash slot of each sorted point's cell
     const float4* pts;      // caller's points in original order
     int64_t* d_n_own;       // grid-owned count when the caller passed none
     void* mem;

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kThreads) search_count(GridView g, Radii R, No
         for (int k = 0; k < kQPerWarp && w * kQPerWarp + k < n_sorted; ++k) {
             const float4 q = g.sorted[w * kQPerWarp + k];
             const int qi = __float_as_int(q.w);
-            const int total = sc.get(g, q, lane);
+            const int total = sc.get(g, w * kQPerWarp + k, lane);
             const int start = sc.start, excl = sc.excl;
             int nf = 0, nn = 0;
             float sx = 0.f, sy = 0.f, sz = 0.f;
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kThreads) search_fill(GridView g, Radii R, Nor
             const float4 q = g.sorted[p];
             const int qi = __float_as_int(q.w);
             const float4 mq = s.mean[qi];
-            const int total = sc.get(g, q, lane);
+            const int total = sc.get(g, p, lane);
             const int start = sc.start, excl = sc.excl;
             int64_t out = o.offs[qi];
             float s1x = 0.f, s1y = 0.f, s1z = 0.f;
@@ -256,7 +256,7 @@ cudaError_t kmx_normals_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_params
     cudaStream_t st = ctx->stream;
     size_t total = 0;
     NormScratch s = carve(scratch, g->n_cap, &total);
-    GridView gv{g->sorted, g->cells, g->keys, g->table_size, g->inv_cell, g->d_n_sorted};
+    GridView gv{g->sorted, g->cells, g->keys, g->table_size, g->inv_cell, g->d_n_sorted, g->sslot};
     Radii R;
     R.rf2 = prm->r_fpfh * prm->r_fpfh;
     R.rn2 = prm->r_normal * prm->r_normal;

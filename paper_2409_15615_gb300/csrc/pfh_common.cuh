@@ -76,4 +76,15 @@ __device__ __forceinline__ void kahan_add(float& sum, float& comp, float term)
     sum = t;
 }
 
+// Compensated sum of the term a * b, its product fused with the subtraction
+// of the compensation (one rounding), so that every kernel that adds the
+// same terms in the same order gets the same bits.
+__device__ __forceinline__ void kahan_add_prod(float& sum, float& comp, float a, float b)
+{
+    const float y = fmaf(a, b, -comp);
+    const float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
 }  // namespace kmxp

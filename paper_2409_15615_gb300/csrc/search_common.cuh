@@ -21,6 +21,7 @@ struct GridView {
     uint32_t T;
     double inv_cell;
     const int64_t* n_sorted;
+    const int32_t* __restrict__ sslot;  // hash slot of each sorted point's cell
 };
 
 struct Radii {
@@ -41,13 +42,18 @@ __device__ __forceinline__ bool within(float4 a, float4 q, float d2, float r2, d
     return e < r2d;
 }
 
-// The grid cell of a bucketed point (its coordinates passed the range check
-// when the grid was built).
-__device__ __forceinline__ void cell_of(const GridView& g, float4 q, int* cx, int* cy, int* cz)
+// The packed cell key of the point at sorted position p: the grid build
+// computed it (FP64 floor of x / cell) and kept its hash slot.
+__device__ __forceinline__ unsigned long long cell_key_at(const GridView& g, int64_t p)
 {
-    kmx_cell_index(q.x, g.inv_cell, cx);
-    kmx_cell_index(q.y, g.inv_cell, cy);
-    kmx_cell_index(q.z, g.inv_cell, cz);
+    return __ldg(g.keys + __ldg(g.sslot + p));
+}
+
+__device__ __forceinline__ void unpack_cell(unsigned long long key, int* cx, int* cy, int* cz)
+{
+    *cx = (int)((key >> 42) & 0x1FFFFFull) - KMX_KEY_BIAS;
+    *cy = (int)((key >> 21) & 0x1FFFFFull) - KMX_KEY_BIAS;
+    *cz = (int)(key & 0x1FFFFFull) - KMX_KEY_BIAS;
 }
 
 // Lane l < 27 gets (start, count) of cell l of the stencil around cell
@@ -76,27 +82,28 @@ __device__ __forceinline__ int stencil_at(const GridView& g, int cx, int cy, int
     return __shfl_sync(kFull, incl, 31);
 }
 
-__device__ __forceinline__ int stencil(const GridView& g, float4 q, int lane, int* start, int* excl)
+// The stencil of the query at sorted position p.
+__device__ __forceinline__ int stencil(const GridView& g, int64_t p, int lane, int* start, int* excl)
 {
     int cx, cy, cz;
-    cell_of(g, q, &cx, &cy, &cz);
+    unpack_cell(cell_key_at(g, p), &cx, &cy, &cz);
     return stencil_at(g, cx, cy, cz, lane, start, excl);
 }
 
 // The stencil of the last query a warp searched, reused while the next
 // queries (consecutive in cell order) sit in the same cell.
 struct StencilCache {
-    int cx = INT_MIN, cy = 0, cz = 0, start = 0, excl = 0, total = 0;
+    unsigned long long key = KMX_EMPTY_KEY;
+    int start = 0, excl = 0, total = 0;
 
-    __device__ __forceinline__ int get(const GridView& g, float4 q, int lane)
+    __device__ __forceinline__ int get(const GridView& g, int64_t p, int lane)
     {
-        int x, y, z;
-        cell_of(g, q, &x, &y, &z);
-        if (x != cx || y != cy || z != cz) {
+        const unsigned long long k = cell_key_at(g, p);
+        if (k != key) {
+            int x, y, z;
+            unpack_cell(k, &x, &y, &z);
             total = stencil_at(g, x, y, z, lane, &start, &excl);
-            cx = x;
-            cy = y;
-            cz = z;
+            key = k;
         }
         return total;
     }

@@ -236,10 +236,20 @@ class PairStream:
         self.graphs = [None] * slots
         self.k = 0
 
-    def prepare(self, n_src, n_tgt, p_src, p_tgt, mode, graph: bool = True):
+    def prepare(self, n_src, n_tgt, p_src, p_tgt, mode, graph: bool = True, sample=None):
         """Size every buffer (a checked run per slot) and, with ``graph``,
-        record each slot's pair as a CUDA graph for these sizes."""
+        record each slot's pair as a CUDA graph for these sizes.  ``sample``
+        = (src, tgt) host or device clouds of these sizes, representative of
+        the stream: each slot sizes its neighbour lists and scratch on them
+        (without one the checked runs see whatever the raw buffers hold, and
+        the lists keep their default capacity)."""
         for i, s in enumerate(self.slots):
+            if sample is not None:
+                s.src.raw[:n_src].copy_(torch.as_tensor(sample[0]))
+                s.tgt.raw[:n_tgt].copy_(torch.as_tensor(sample[1]))
+            else:
+                s.src.raw[:n_src].zero_()
+                s.tgt.raw[:n_tgt].zero_()
             s.run_checked(n_src, n_tgt, p_src, p_tgt, mode)
             self.graphs[i] = s.capture(n_src, n_tgt, p_src, p_tgt, mode) if graph else None
         torch.cuda.synchronize(self.ctx.device)

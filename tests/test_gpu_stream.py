@@ -43,7 +43,7 @@ def test_stream_equals_plain_runs(graph, concurrent, slots):
         ref.append(set(zip(i.tolist(), j.tolist())))
     plain.close()
     st = pipeline.PairStream(ctx, n, n, concurrent=concurrent, slots=slots)
-    st.prepare(n, n, prm, prm, kmx.MATCH_FP32_EXACT, graph=graph)
+    st.prepare(n, n, prm, prm, kmx.MATCH_FP32_EXACT, graph=graph, sample=(pairs[0][0], pairs[0][1]))
     hosts = [(torch.from_numpy(s).pin_memory(), torch.from_numpy(t).pin_memory()) for s, t, _, _ in pairs]
     outs = [(torch.empty(st.slots[0].corr.shape, dtype=torch.int32).pin_memory(),
              torch.empty(1, dtype=torch.int64).pin_memory()) for _ in range(8)]
