@@ -182,6 +182,9 @@ inline cudaError_t kmx_once_per_device(int bit, F fn)
 // grown here when needed (so a first call of a size must not be inside a
 // graph capture).  A look-back wait that runs out raises KMX_DERR_TIMEOUT.
 cudaError_t kmx_scan_i32(kmx_ctx* ctx, const int32_t* in, int64_t n, const int64_t* d_n, int64_t* out);
+// The same, but only out[0 .. min(*d_n, n)] are written (the tiles past the
+// count do no work).
+cudaError_t kmx_scan_i32_live(kmx_ctx* ctx, const int32_t* in, int64_t n, const int64_t* d_n, int64_t* out);
 // Status words a scan of n values uses.
 int64_t kmx_scan_words(int64_t n);
 // Make the context's zeroed status area hold at least `words` words.

@@ -245,8 +245,8 @@ __device__ __forceinline__ void store_operand_row(uint8_t* tile, int r, const fl
 // locality order: a principal-direction tree
 // ---------------------------------------------------------------------------
 
-constexpr int kTreeSample = 512;  // rows sampled per node for its direction
-constexpr int kTreeIters = 4;     // power iterations
+constexpr int kTreeSample = 256;  // rows sampled per node for its direction
+constexpr int kTreeIters = 2;     // power iterations
 constexpr int kTreeThreads = 256;
 constexpr int kColSplit = 7;      // partial sums per column in the sample reductions (7 x 33 <= 256)
 constexpr int kDirStride = 68;    // floats per node: centre (33), direction (33), projection range (2)
@@ -957,28 +957,42 @@ __global__ void __launch_bounds__(kTM) tc_plan(const float* __restrict__ X, cons
             sc[idx][KMX_DESC_DIM + 2] = sqrtf(cc); // |c|
         }
         __syncthreads();
-        for (int q = 0; q < nsurv; ++q) {
-            bool nd = false;
+        // two surviving tiles per step (independent chains)
+        for (int q = 0; q < nsurv; q += 2) {
+            const int q1 = min(q + 1, nsurv - 1);
+            bool nd0 = false, nd1 = false;
             if (valid) {
                 // |x - c|^2 = |x|^2 + |c|^2 - 2 x.c with paired FMAs; its
                 // error is below 40 u (|x| + |c|)^2 (u = 2^-24), taken off
                 // before the test
-                const float4* c4 = reinterpret_cast<const float4*>(sc[q]);
-                float2 dot = make_float2(0.f, 0.f);
+                const float4* ca = reinterpret_cast<const float4*>(sc[q]);
+                const float4* cb = reinterpret_cast<const float4*>(sc[q1]);
+                float2 da = make_float2(0.f, 0.f), db = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    const float4 cv = c4[c];
-                    dot = __ffma2_rn(make_float2(x[4 * c], x[4 * c + 1]), make_float2(cv.x, cv.y), dot);
-                    dot = __ffma2_rn(make_float2(x[4 * c + 2], x[4 * c + 3]), make_float2(cv.z, cv.w), dot);
+                    const float4 va = ca[c], vb = cb[c];
+                    const float2 x0 = make_float2(x[4 * c], x[4 * c + 1]);
+                    const float2 x1 = make_float2(x[4 * c + 2], x[4 * c + 3]);
+                    da = __ffma2_rn(x0, make_float2(va.x, va.y), da);
+                    db = __ffma2_rn(x0, make_float2(vb.x, vb.y), db);
+                    da = __ffma2_rn(x1, make_float2(va.z, va.w), da);
+                    db = __ffma2_rn(x1, make_float2(vb.z, vb.w), db);
                 }
-                const float4 tail = c4[8];  // [32], radius, |c|^2, |c|
-                const float xc = fmaf(x[32], tail.x, dot.x + dot.y);
-                const float s = xn + tail.w;
-                const float dd = fmaf(-2.f, xc, xx + tail.z) - kDotErr * s * s;
-                nd = tile_may_hold(sqrtf(fmaxf(dd, 0.f)), tail.y, d2);
+                const float4 ta = ca[8], tb = cb[8];  // [32], radius, |c|^2, |c|
+                const float xca = fmaf(x[32], ta.x, da.x + da.y);
+                const float xcb = fmaf(x[32], tb.x, db.x + db.y);
+                const float sa_ = xn + ta.w, sb_ = xn + tb.w;
+                const float dda = fmaf(-2.f, xca, xx + ta.z) - kDotErr * sa_ * sa_;
+                const float ddb = fmaf(-2.f, xcb, xx + tb.z) - kDotErr * sb_ * sb_;
+                nd0 = tile_may_hold(sqrtf(fmaxf(dda, 0.f)), ta.y, d2);
+                nd1 = q + 1 < nsurv && tile_may_hold(sqrtf(fmaxf(ddb, 0.f)), tb.y, d2);
             }
-            const unsigned b = __ballot_sync(0xffffffffu, nd);
-            if (lane == 0 && b) atomicOr(&needbits[q >> 5], 1u << (q & 31));
+            const unsigned b0 = __ballot_sync(0xffffffffu, nd0);
+            const unsigned b1 = __ballot_sync(0xffffffffu, nd1);
+            if (lane == 0) {
+                if (b0) atomicOr(&needbits[q >> 5], 1u << (q & 31));
+                if (b1) atomicOr(&needbits[(q + 1) >> 5], 1u << ((q + 1) & 31));
+            }
         }
         __syncthreads();
         if (tid < nsurv) {

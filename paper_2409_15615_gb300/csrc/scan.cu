@@ -42,13 +42,14 @@ __device__ __forceinline__ void store_status(unsigned long long* p, unsigned lon
 // status[0] is the tile counter, status[1] the count of finished CTAs,
 // status[2 + t] the status word of tile t; all zero before the launch and
 // zeroed again by the last CTA.  Entries at i >= count read as 0; out[i] is
-// written for i < len.
+// written for i < len, or with live_only for i <= count only (the tiles that
+// start past the count just count themselves finished).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) scan_onepass(const T* __restrict__ in, int64_t len, int64_t count_cap,
                                                          const int64_t* __restrict__ d_count,
                                                          int64_t* __restrict__ out,
                                                          unsigned long long* __restrict__ status, int64_t tiles,
-                                                         unsigned int* __restrict__ err)
+                                                         unsigned int* __restrict__ err, bool live_only)
 {
     __shared__ int64_t wsum[kThreads / 32];
     __shared__ int64_t tile_prefix;
@@ -62,6 +63,17 @@ __global__ void __launch_bounds__(kThreads) scan_onepass(const T* __restrict__ i
         return;
     }
     const int64_t count = d_count ? min(*d_count, count_cap) : count_cap;
+    if (live_only && tile * kTile > count) {  // block-uniform: no output of this tile is wanted
+        if (threadIdx.x == 0) {
+            __threadfence();
+            last = atomicAdd(status + 1, 1ull) == (unsigned long long)(tiles - 1);
+            __threadfence();
+        }
+        __syncthreads();
+        if (last)
+            for (int64_t i = threadIdx.x; i < tiles + 2; i += kThreads) store_status(&status[i], 0ull);
+        return;
+    }
     const int64_t base = tile * kTile + (int64_t)threadIdx.x * kItems;
     int64_t v[kItems];
     int64_t s = 0;
@@ -176,7 +188,8 @@ cudaError_t kmx_scan_reserve(kmx_ctx* ctx, int64_t words)
     return cudaSuccess;
 }
 
-cudaError_t kmx_scan_i32(kmx_ctx* ctx, const int32_t* in, int64_t n, const int64_t* d_n, int64_t* out)
+static cudaError_t scan_launch(kmx_ctx* ctx, const int32_t* in, int64_t n, const int64_t* d_n, int64_t* out,
+                               bool live_only)
 {
     const int64_t len = n + 1;
     const int64_t tiles = tiles_for(len);
@@ -184,6 +197,16 @@ cudaError_t kmx_scan_i32(kmx_ctx* ctx, const int32_t* in, int64_t n, const int64
     if (e) return e;
     KMX_COUNT_LAUNCH();
     scan_onepass<int32_t><<<(unsigned)tiles, kThreads, 0, ctx->stream>>>(in, len, n, d_n, out, ctx->scan_status,
-                                                                          tiles, ctx->d_err);
+                                                                          tiles, ctx->d_err, live_only);
     return cudaGetLastError();
+}
+
+cudaError_t kmx_scan_i32(kmx_ctx* ctx, const int32_t* in, int64_t n, const int64_t* d_n, int64_t* out)
+{
+    return scan_launch(ctx, in, n, d_n, out, false);
+}
+
+cudaError_t kmx_scan_i32_live(kmx_ctx* ctx, const int32_t* in, int64_t n, const int64_t* d_n, int64_t* out)
+{
+    return scan_launch(ctx, in, n, d_n, out, true);
 }

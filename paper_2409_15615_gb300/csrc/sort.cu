@@ -5,9 +5,10 @@
 //
 // One pass over digit position p:
 //   count    block b counts the digits of its 2048 elements; counts are laid
-//            out digit-major (counts[d * blocks + b]) so that their
-//            exclusive scan is, for every (digit, block), the first output
-//            position of that block's elements with that digit;
+//            out digit-major (counts[d * blocks + b], blocks = the blocks
+//            below the element count, which may be a device value) so that
+//            their exclusive scan is, for every (digit, block), the first
+//            output position of that block's elements with that digit;
 //   scan     kmx_scan_i32 over the 256 * blocks counts;
 //   scatter  block b writes element e with digit d to
 //            scan[d * blocks + b] + (elements of the block before e with
@@ -25,12 +26,23 @@ constexpr int kPerBlock = kThreads * kItems;
 constexpr int kDigits = 256;
 constexpr int kWarps = kThreads / 32;
 
+// Blocks that hold elements below the count: the digit-major counts use
+// this stride, so that their scan covers no empty block.
+__device__ __forceinline__ int live_blocks(int64_t n)
+{
+    const int64_t b = (n + kPerBlock - 1) / kPerBlock;
+    return (int)(b > 0 ? b : 1);
+}
+
 __global__ void __launch_bounds__(kThreads) radix_count(const uint32_t* __restrict__ keys, int64_t n_cap,
                                                         const int64_t* d_n, int shift, int32_t* __restrict__ counts,
-                                                        int blocks)
+                                                        int64_t* __restrict__ n_counts)
 {
     __shared__ int hist[kDigits];
     const int64_t n = kmx_count(d_n, n_cap);
+    const int blocks = live_blocks(n);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *n_counts = (int64_t)kDigits * blocks;
+    if ((int)blockIdx.x >= blocks) return;  // block-uniform
     hist[threadIdx.x] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kPerBlock;
@@ -46,12 +58,13 @@ __global__ void __launch_bounds__(kThreads) radix_count(const uint32_t* __restri
 __global__ void __launch_bounds__(kThreads) radix_scatter(const uint32_t* __restrict__ keys,
                                                           const int32_t* __restrict__ vals, int64_t n_cap,
                                                           const int64_t* d_n, int shift,
-                                                          const int64_t* __restrict__ offs, int blocks,
+                                                          const int64_t* __restrict__ offs,
                                                           uint32_t* __restrict__ keys_out,
                                                           int32_t* __restrict__ vals_out)
 {
     const int64_t n = kmx_count(d_n, n_cap);
     if ((int64_t)blockIdx.x * kPerBlock >= n) return;  // no element here (block-uniform)
+    const int blocks = live_blocks(n);
     __shared__ int wcount[kWarps][kDigits];  // this item's count per warp and digit, then its warp prefix
     __shared__ int running[kDigits];         // elements of earlier items, per digit
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -119,6 +132,7 @@ size_t kmx_sort_scratch_bytes(int64_t n)
     kmx_arena a{nullptr, 0};
     a.take(sizeof(int32_t) * (size_t)(kDigits * b + 1));
     a.take(sizeof(int64_t) * (size_t)(kDigits * b + 1));
+    a.take(sizeof(int64_t));
     return kmx_align_up(a.used, 256);
 }
 
@@ -130,17 +144,18 @@ cudaError_t kmx_sort_u32(kmx_ctx* ctx, uint32_t* keys, int32_t* vals, uint32_t* 
     kmx_arena a{static_cast<char*>(scratch), 0};
     int32_t* counts = (int32_t*)a.take(sizeof(int32_t) * (size_t)(kDigits * blocks + 1));
     int64_t* offs = (int64_t*)a.take(sizeof(int64_t) * (size_t)(kDigits * blocks + 1));
+    int64_t* n_counts = (int64_t*)a.take(sizeof(int64_t));  // counts actually laid out (256 x live blocks)
     const int64_t m = (int64_t)kDigits * blocks;
     uint32_t *ki = keys, *ko = keys_tmp;
     int32_t *vi = vals, *vo = vals_tmp;
     cudaError_t e;
     for (int shift = 0; shift < bits; shift += 8) {
         KMX_COUNT_LAUNCH();
-        radix_count<<<blocks, kThreads, 0, ctx->stream>>>(ki, n, d_n, shift, counts, blocks);
+        radix_count<<<blocks, kThreads, 0, ctx->stream>>>(ki, n, d_n, shift, counts, n_counts);
         if ((e = cudaGetLastError())) return e;
-        if ((e = kmx_scan_i32(ctx, counts, m, nullptr, offs))) return e;
+        if ((e = kmx_scan_i32_live(ctx, counts, m, n_counts, offs))) return e;
         KMX_COUNT_LAUNCH();
-        radix_scatter<<<blocks, kThreads, 0, ctx->stream>>>(ki, vi, n, d_n, shift, offs, blocks, ko, vo);
+        radix_scatter<<<blocks, kThreads, 0, ctx->stream>>>(ki, vi, n, d_n, shift, offs, ko, vo);
         if ((e = cudaGetLastError())) return e;
         uint32_t* tk = ki;
         ki = ko;
