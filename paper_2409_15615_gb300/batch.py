@@ -201,7 +201,7 @@ def time_batch(runner: BatchRunner, reps: int = 3, graph: bool = True) -> float:
 
 
 def autotune(pairs, device: int = 0, lane_options=(4, 8, 16), chunk_options=(4, 8, 16),
-             tc_options=(None, 4e10, 1.6e11), log=None):
+             tc_options=(None, 1e10, 4e10, 1.6e11), log=None):
     """Pick (lanes, chunks per CTA, size bucket boundary of the tensor-core
     matcher) by timing the graph-captured batch: a coordinate search (lanes
     with the defaults, then the chunk size, then the boundary).  Every

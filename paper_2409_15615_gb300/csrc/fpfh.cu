@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(kThreads) scatter_valid(int64_t n_cap, const i
         if (jflag[q]) valid[jpos[q]] = (int32_t)q;
 }
 
-__global__ void __launch_bounds__(kThreads) spfh_kernel(int64_t n_cap, const int64_t* d_n,
+__global__ void __launch_bounds__(kThreads, 5) spfh_kernel(int64_t n_cap, const int64_t* d_n,
                                                         const float4* __restrict__ pts,
                                                         const float4* __restrict__ normal4, uint8_t* flags,
                                                         const int64_t* __restrict__ offs,
