@@ -115,6 +115,11 @@ __global__ void __launch_bounds__(kThreads, 5) spfh_kernel(int64_t n_cap, const 
     }
 }
 
+// Four rows per warp: the 8 lanes of group g = lane / 8 take row j of J; lane
+// s = lane % 8 owns bins 4 s .. 4 s + 3 (s = 0 also bin 32) and loads them as
+// one float4 of each neighbour's SPFH row, so the four groups keep four rows
+// in flight per step.  Every bin adds its neighbours' values in list order
+// with the compensated product-sum the list-free path uses (the same bits).
 __global__ void __launch_bounds__(kThreads) fpfh_kernel(int64_t n_cap, const int32_t* __restrict__ valid,
                                                         const int64_t* __restrict__ n_valid,
                                                         const float4* __restrict__ pts,
@@ -123,21 +128,32 @@ __global__ void __launch_bounds__(kThreads) fpfh_kernel(int64_t n_cap, const int
                                                         const int32_t* __restrict__ nbr,
                                                         const float* __restrict__ spfh, float* __restrict__ desc)
 {
-    // per warp, the valid neighbours of one 32-entry chunk of the list, in
-    // list order: their index and weight 1 / w_k
-    __shared__ int32_t sk[kWarps][32];
-    __shared__ float sw[kWarps][32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // per group, the valid neighbours of one 8-entry chunk of its row's list,
+    // in list order: their index and weight 1 / w_k
+    __shared__ int32_t sk[kWarps][4][8];
+    __shared__ float sw[kWarps][4][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 3, s = lane & 7;
     const int64_t nv = min(*n_valid, n_cap);
-    for (int64_t j = (int64_t)blockIdx.x * kWarps + warp; j < nv; j += (int64_t)gridDim.x * kWarps) {
-        const int q = valid[j];
-        const float4 pq = pts[q];
-        float acc = 0.f, comp = 0.f, acc32 = 0.f, comp32 = 0.f;
+    const int64_t warps = (int64_t)gridDim.x * kWarps;
+    for (int64_t w4 = (int64_t)blockIdx.x * kWarps + warp; w4 * 4 < nv; w4 += warps) {
+        const int64_t j = w4 * 4 + g;
+        const bool active = j < nv;
+        int q = -1;
+        float4 pq = make_float4(0.f, 0.f, 0.f, 0.f);
+        int64_t b = 0, e = 0;
+        if (active) {
+            q = valid[j];
+            pq = pts[q];
+            b = offs[q];
+            e = offs[q + 1];
+        }
+        float acc[4] = {0.f, 0.f, 0.f, 0.f}, comp[4] = {0.f, 0.f, 0.f, 0.f};
+        float acc32 = 0.f, comp32 = 0.f;
         int m = 0;
-        const int64_t b = offs[q], e = offs[q + 1];
-        for (int64_t t = b + lane; t - lane < e; t += 32) {
+        for (int64_t c = 0; __any_sync(kFull, b + c < e); c += 8) {
+            const int64_t t = b + c + s;
             int k = -1;
-            float w = 0.f;
+            float wt = 0.f;
             if (t < e) {
                 const int kk = nbr[t];
                 if (kk != q && (__ldg(&flags[kk]) & 1)) {
@@ -146,35 +162,45 @@ __global__ void __launch_bounds__(kThreads) fpfh_kernel(int64_t n_cap, const int
                     const float d2 = dot3(dx, dy, dz, dx, dy, dz);
                     if (d2 > 0.f) {
                         k = kk;
-                        w = 1.0f / sqrtf(d2);
+                        wt = 1.0f / sqrtf(d2);
                     }
                 }
             }
-            const unsigned bal = __ballot_sync(kFull, k >= 0);
-            const int cnt = __popc(bal);
+            const unsigned gb = (__ballot_sync(kFull, k >= 0) >> (8 * g)) & 0xFFu;
+            const int cnt = __popc(gb);
             if (k >= 0) {
-                const int slot = __popc(bal & ((1u << lane) - 1u));
-                sk[warp][slot] = k;
-                sw[warp][slot] = w;
+                const int slot = __popc(gb & ((1u << s) - 1u));
+                sk[warp][g][slot] = k;
+                sw[warp][g][slot] = wt;
             }
             __syncwarp();
             m += cnt;
-            // lanes are the bins; the rows of the chunk's neighbours are added
-            // in list order, four loads in flight
+            const int steps = __reduce_max_sync(kFull, (unsigned)cnt);
 #pragma unroll 4
-            for (int i = 0; i < cnt; ++i) {
-                const float* r = spfh + (int64_t)sk[warp][i] * kStride;
-                const float we = sw[warp][i];
-                kahan_add_prod(acc, comp, __ldg(&r[lane]), we);
-                if (lane == 0) kahan_add_prod(acc32, comp32, __ldg(&r[32]), we);
+            for (int i = 0; i < steps; ++i) {
+                if (i < cnt) {
+                    const float* r = spfh + (int64_t)sk[warp][g][i] * kStride;
+                    const float we = sw[warp][g][i];
+                    const float4 v = __ldg(reinterpret_cast<const float4*>(r) + s);
+                    kahan_add_prod(acc[0], comp[0], v.x, we);
+                    kahan_add_prod(acc[1], comp[1], v.y, we);
+                    kahan_add_prod(acc[2], comp[2], v.z, we);
+                    kahan_add_prod(acc[3], comp[3], v.w, we);
+                    if (s == 0) kahan_add_prod(acc32, comp32, __ldg(&r[32]), we);
+                }
             }
             __syncwarp();
         }
-        const float* rq = spfh + (int64_t)q * kStride;
-        const float invm = m > 0 ? 1.0f / (float)m : 0.f;
-        float* out = desc + j * kStride;
-        out[lane] = rq[lane] + acc * invm;
-        if (lane < kStride - 32) out[32 + lane] = lane == 0 ? rq[32] + acc32 * invm : 0.f;
+        if (active) {
+            const float* rq = spfh + (int64_t)q * kStride;
+            const float invm = m > 0 ? 1.0f / (float)m : 0.f;
+            float* out = desc + j * kStride;
+            const float4 rv = reinterpret_cast<const float4*>(rq)[s];
+            reinterpret_cast<float4*>(out)[s] = make_float4(fmaf(acc[0], invm, rv.x), fmaf(acc[1], invm, rv.y),
+                                                            fmaf(acc[2], invm, rv.z), fmaf(acc[3], invm, rv.w));
+            if (s == 0)
+                reinterpret_cast<float4*>(out)[8] = make_float4(fmaf(acc32, invm, rq[32]), 0.f, 0.f, 0.f);
+        }
     }
 }
 

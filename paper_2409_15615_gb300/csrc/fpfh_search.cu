@@ -342,8 +342,8 @@ __global__ void __launch_bounds__(kThreads) fpfh_walk(GridView g, Radii R, const
         const float* rq = spfh + (int64_t)qi * kStride;
         const float invm = m > 0 ? 1.0f / (float)m : 0.f;
         float* out = desc + jpos[qi] * kStride;
-        out[lane] = rq[lane] + acc * invm;
-        if (lane < kStride - 32) out[32 + lane] = lane == 0 ? rq[32] + acc32 * invm : 0.f;
+        out[lane] = fmaf(acc, invm, rq[lane]);
+        if (lane < kStride - 32) out[32 + lane] = lane == 0 ? fmaf(acc32, invm, rq[32]) : 0.f;
     }
 }
 

@@ -761,14 +761,14 @@ __device__ __forceinline__ bool tile_may_hold(float dist, float rad, float u2)
 //      the largest d2, then row by row), in increasing order, into
 //      need[rt * need_stride ...]; nneed[rt] = their number, and the list is
 //      cut into items (rt, first) of kItemTiles tiles appended to `items`.
-__global__ void __launch_bounds__(kTM) tc_plan(const float* __restrict__ X, const int32_t* __restrict__ permX,
-                                               int64_t nx_cap, const int64_t* d_nx, const float* __restrict__ cenX,
-                                               const float* __restrict__ Y, const int32_t* __restrict__ permY,
-                                               int64_t ny_cap, const int64_t* d_ny, const float* __restrict__ cenY,
-                                               int32_t* __restrict__ cand, int32_t* __restrict__ cnt,
-                                               float* __restrict__ ub, int32_t* __restrict__ need,
-                                               int64_t need_stride, int32_t* __restrict__ nneed,
-                                               int2* __restrict__ items, int* __restrict__ n_items)
+__device__ __forceinline__ void plan_tile(const float* __restrict__ X, const int32_t* __restrict__ permX,
+                                          int64_t nx_cap, const int64_t* d_nx, const float* __restrict__ cenX,
+                                          const float* __restrict__ Y, const int32_t* __restrict__ permY,
+                                          int64_t ny_cap, const int64_t* d_ny, const float* __restrict__ cenY,
+                                          int32_t* __restrict__ cand, int32_t* __restrict__ cnt,
+                                          float* __restrict__ ub, int32_t* __restrict__ need, int64_t need_stride,
+                                          int32_t* __restrict__ nneed, int2* __restrict__ items,
+                                          int* __restrict__ n_items, const int64_t rt)
 {
     __shared__ __align__(16) float ys[kTN][kCenterStride];  // the nearest tile's rows, zero-padded to 36
     __shared__ __align__(16) float sc[kTN][kCenterStride];  // surviving tiles: centre, radius at [33]
@@ -784,7 +784,6 @@ __global__ void __launch_bounds__(kTM) tc_plan(const float* __restrict__ X, cons
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t rows = kmx_count(d_nx, nx_cap), cols = kmx_count(d_ny, ny_cap);
-    const int64_t rt = blockIdx.x;
     if (rt * kTM >= rows || cols <= 0) return;
     const int64_t n_ct = (cols + kTN - 1) / kTN;
     const int64_t xrow = rt * kTM + tid;
@@ -1017,6 +1016,39 @@ __global__ void __launch_bounds__(kTM) tc_plan(const float* __restrict__ X, cons
             for (int i = 0; i < nit; ++i) items[b + i] = make_int2((int)rt, i * kItemTiles);
         }
     }
+}
+
+// One direction of the plan (rows X against column tiles of Y).
+struct PlanDir {
+    const float* X;
+    const int32_t* permX;
+    int64_t nx_cap;
+    const int64_t* d_nx;
+    const float* cenX;
+    const float* Y;
+    const int32_t* permY;
+    int64_t ny_cap;
+    const int64_t* d_ny;
+    const float* cenY;
+    int32_t* cand;
+    int32_t* cnt;
+    float* ub;
+    int32_t* need;
+    int64_t need_stride;
+    int32_t* nneed;
+    int2* items;
+    int* n_items;
+};
+
+// Both directions in one launch: blocks [0, split) take the row tiles of the
+// first direction, the others those of the second (one tail instead of two).
+__global__ void __launch_bounds__(kTM) tc_plan(PlanDir a, PlanDir b, int64_t split)
+{
+    const bool second = (int64_t)blockIdx.x >= split;
+    const PlanDir d = second ? b : a;
+    plan_tile(d.X, d.permX, d.nx_cap, d.d_nx, d.cenX, d.Y, d.permY, d.ny_cap, d.d_ny, d.cenY, d.cand, d.cnt, d.ub,
+              d.need, d.need_stride, d.nneed, d.items, d.n_items,
+              second ? (int64_t)blockIdx.x - split : (int64_t)blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1412,9 +1444,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_collect(const float* __restric
 // exact FP32 re-ranking of the collected columns
 // ---------------------------------------------------------------------------
 
-// One warp per sorted row position.  Rows whose list overflowed are flagged
-// for the exact fallback.  rows_out (source side) gets (d1, NN, d2) at the
-// original row; cols_best (target side) the packed (d1, NN).
+// Four sorted row positions per warp, eight lanes each (lane s takes
+// candidates s, s + 8, ...).  Rows whose list overflowed are flagged for the
+// exact fallback.  rows_out (source side) gets (d1, NN, d2) at the original
+// row; cols_best (target side) the packed (d1, NN).
 __global__ void __launch_bounds__(256) tc_rerank(const float* __restrict__ X, const int32_t* __restrict__ permX,
                                                  int64_t nx_cap, const int64_t* d_nx, const float* __restrict__ Y,
                                                  const int32_t* __restrict__ permY, int64_t ny_cap,
@@ -1424,41 +1457,65 @@ __global__ void __launch_bounds__(256) tc_rerank(const float* __restrict__ X, co
                                                  unsigned long long* __restrict__ cols_best,
                                                  int32_t* __restrict__ fallback, int* __restrict__ final_chunks)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31, s = lane & 7;
+    const int64_t i = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 4 + (lane >> 3);
     if (final_chunks && i == 0 && lane == 0) *final_chunks = 1;  // rows_out holds whole-row summaries
-    if (i >= kmx_count(d_nx, nx_cap)) return;
-    const int orig = permX[i];
-    const int c = cnt[i];
-    if (c > kCandCap) {
-        if (lane == 0) fallback[orig] = 1;
-        return;
-    }
-    const float* x = X + (int64_t)orig * KMX_DESC_STRIDE;
-    const int64_t ny = kmx_count(d_ny, ny_cap);
+    const int64_t nx = kmx_count(d_nx, nx_cap), ny = kmx_count(d_ny, ny_cap);
+    const bool active = i < nx;
+    const int orig = active ? permX[i] : 0;
+    const int c = active ? cnt[i] : 0;
     float b1 = INFINITY, b2 = INFINITY;
     int j1 = 0x7fffffff;
-    for (int q = lane; q < c; q += 32) {
-        const int pos = cand[i * kCandCap + q];
-        if (pos < 0 || pos >= ny) continue;  // padding columns are never collected
-        const int j = permY[pos];
-        const float* y = Y + (int64_t)j * KMX_DESC_STRIDE;
-        float acc = 0.f;
+    if (c <= kCandCap && c > s) {
+        // the row once, then every candidate with the exact path's arithmetic
+        // (one fused multiply-add per term in h order)
+        float x[KMX_DESC_DIM];
+        const float4* x4 = reinterpret_cast<const float4*>(X + (int64_t)orig * KMX_DESC_STRIDE);
 #pragma unroll
-        for (int h = 0; h < KMX_DESC_DIM; ++h) {
-            const float e = __ldg(x + h) - __ldg(y + h);
-            acc = fmaf(e, e, acc);
+        for (int q4 = 0; q4 < 8; ++q4) {
+            const float4 v = __ldg(x4 + q4);
+            x[4 * q4] = v.x;
+            x[4 * q4 + 1] = v.y;
+            x[4 * q4 + 2] = v.z;
+            x[4 * q4 + 3] = v.w;
         }
-        kmx::row_update(b1, j1, b2, acc, j);
+        x[32] = __ldg(X + (int64_t)orig * KMX_DESC_STRIDE + 32);
+        for (int q = s; q < c; q += 8) {
+            const int pos = cand[i * kCandCap + q];
+            if (pos < 0 || pos >= ny) continue;  // padding columns are never collected
+            const int j = permY[pos];
+            const float* y = Y + (int64_t)j * KMX_DESC_STRIDE;
+            const float4* y4 = reinterpret_cast<const float4*>(y);
+            float acc = 0.f;
+#pragma unroll
+            for (int q4 = 0; q4 < 8; ++q4) {
+                const float4 v = __ldg(y4 + q4);
+                float e = x[4 * q4] - v.x;
+                acc = fmaf(e, e, acc);
+                e = x[4 * q4 + 1] - v.y;
+                acc = fmaf(e, e, acc);
+                e = x[4 * q4 + 2] - v.z;
+                acc = fmaf(e, e, acc);
+                e = x[4 * q4 + 3] - v.w;
+                acc = fmaf(e, e, acc);
+            }
+            const float e = x[32] - __ldg(y + 32);
+            acc = fmaf(e, e, acc);
+            kmx::row_update(b1, j1, b2, acc, j);
+        }
     }
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
+    for (int o = 4; o >= 1; o >>= 1) {  // within the row's eight lanes
         const float od1 = __shfl_xor_sync(0xffffffffu, b1, o);
         const int oj = __shfl_xor_sync(0xffffffffu, j1, o);
         const float od2 = __shfl_xor_sync(0xffffffffu, b2, o);
         kmx::row_merge(b1, j1, b2, od1, oj, od2);
     }
-    if (lane != 0) return;
+    if (s != 0 || !active) return;
+    if (c > kCandCap) {
+        fallback[orig] = 1;
+        return;
+    }
     if (rows_out) rows_out[orig] = kmx::RowBest{b1, j1, b2};
     if (cols_best && j1 != 0x7fffffff) cols_best[orig] = kmx::pack_dist_index(b1, (uint32_t)j1);
 }
@@ -1622,9 +1679,12 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
         tree_dir<<<dim3(1u << l, 2), kTreeThreads, kTreeSmem, st>>>(dp, np_cap, d_np, dq, nq_cap, d_nq, b.vals, l,
                                                                      b.dirs);
         KMX_COUNT_LAUNCH();
-        tree_key<<<gb, 256, 0, st>>>(dp, np_cap, d_np, dq, nq_cap, d_nq, b.vals, l, key_bits, b.dirs, b.keys);
+        // 16-bit keys (two radix passes) while they leave at least 9 bits of
+        // projection (levels 0..6), wider keys below
+        const int kb = l <= 6 ? 16 : key_bits;
+        tree_key<<<gb, 256, 0, st>>>(dp, np_cap, d_np, dq, nq_cap, d_nq, b.vals, l, kb, b.dirs, b.keys);
         if ((e = cudaGetLastError())) return e;
-        if ((e = kmx_sort_u32(ctx, b.keys, b.vals, b.keys_tmp, b.vals_tmp, n2, b.n2, key_bits, b.sort_scratch)))
+        if ((e = kmx_sort_u32(ctx, b.keys, b.vals, b.keys_tmp, b.vals_tmp, n2, b.n2, kb, b.sort_scratch)))
             return e;
     }
     if (levels > 0) {  // the subtrees of at most 16 tiles, one CTA each
@@ -1643,12 +1703,12 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
     KMX_COUNT_LAUNCH();
     tc_pack<<<(unsigned)tq, kTN, 0, st>>>(dq, permQ, nq_cap, d_nq, b.packQ, b.cenQ, ctx->d_err);
     // first candidates, bounds and tile lists both ways
+    const PlanDir planP{dp, permP, np_cap, d_np, b.cenP, dq, permQ, nq_cap, d_nq, b.cenQ, b.candP,
+                        b.cntP, b.ubP, b.needP, tq, b.nneedP, b.itemsP, b.nitems + 0};
+    const PlanDir planQ{dq, permQ, nq_cap, d_nq, b.cenQ, dp, permP, np_cap, d_np, b.cenP, b.candQ,
+                        b.cntQ, b.ubQ, b.needQ, tp, b.nneedQ, b.itemsQ, b.nitems + 1};
     KMX_COUNT_LAUNCH();
-    tc_plan<<<(unsigned)tp, kTM, 0, st>>>(dp, permP, np_cap, d_np, b.cenP, dq, permQ, nq_cap, d_nq, b.cenQ, b.candP,
-                                          b.cntP, b.ubP, b.needP, tq, b.nneedP, b.itemsP, b.nitems + 0);
-    KMX_COUNT_LAUNCH();
-    tc_plan<<<(unsigned)tq, kTM, 0, st>>>(dq, permQ, nq_cap, d_nq, b.cenQ, dp, permP, np_cap, d_np, b.cenP, b.candQ,
-                                          b.cntQ, b.ubQ, b.needQ, tp, b.nneedQ, b.itemsQ, b.nitems + 1);
+    tc_plan<<<(unsigned)(tp + tq), kTM, 0, st>>>(planP, planQ, tp);
     // tensor-core candidates both ways: one persistent CTA per SM
     const unsigned grid = (unsigned)(ctx->sm_count > 0 ? ctx->sm_count : 1);
     KMX_COUNT_LAUNCH();
@@ -1659,10 +1719,10 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
                                              b.nitems + 1, b.ubQ, b.candQ, b.cntQ, ctx->d_err);
     // exact re-ranking; overflowed rows are flagged
     KMX_COUNT_LAUNCH();
-    tc_rerank<<<kmx_blocks(np_cap, 8), 256, 0, st>>>(dp, permP, np_cap, d_np, dq, permQ, nq_cap, d_nq, b.candP,
+    tc_rerank<<<kmx_blocks(np_cap, 32), 256, 0, st>>>(dp, permP, np_cap, d_np, dq, permQ, nq_cap, d_nq, b.candP,
                                                      b.cntP, s.part, nullptr, b.flagP, s.chunks);
     KMX_COUNT_LAUNCH();
-    tc_rerank<<<kmx_blocks(nq_cap, 8), 256, 0, st>>>(dq, permQ, nq_cap, d_nq, dp, permP, np_cap, d_np, b.candQ,
+    tc_rerank<<<kmx_blocks(nq_cap, 32), 256, 0, st>>>(dq, permQ, nq_cap, d_nq, dp, permP, np_cap, d_np, b.candQ,
                                                      b.cntQ, nullptr, s.colbest, b.flagQ, nullptr);
     if ((e = cudaGetLastError())) return e;
     // exact fallback for the flagged rows of each side
