@@ -17,7 +17,7 @@
 //   order     a principal-direction tree over the rows of each cloud: a
 //             node's rows are split at a whole number of 128-row tiles
 //             (left: ceil(len / 256) * 128 rows) by their projection on the
-//             node's principal direction (power iteration on up to 512
+//             node's principal direction (power iteration on up to 256
 //             sampled rows).  The upper levels run level by level with one
 //             stable radix sort per level keyed by (side, node, quantised
 //             projection); below nodes of 16 tiles one CTA per node finishes

@@ -109,6 +109,79 @@ struct StencilCache {
     }
 };
 
+// One thread per query: calls f(a) for every bucketed point a of the 27-cell
+// stencil around sorted position p, in the order of the stored neighbour
+// lists (cells dx fastest, then dy, then dz; points of a cell in sorted
+// order).
+template <typename F>
+__device__ __forceinline__ void for_each_candidate(const GridView& g, int64_t p, F&& f)
+{
+    int cx, cy, cz;
+    unpack_cell(cell_key_at(g, p), &cx, &cy, &cz);
+    for (int c = 0; c < 27; ++c) {
+        const int dx = c % 3 - 1, dy = (c / 3) % 3 - 1, dz = c / 9 - 1;
+        const int slot = kmx_hash_find(g.keys, g.T, kmx_pack_key(cx + dx, cy + dy, cz + dz));
+        if (slot < 0) continue;
+        const int2 cell = __ldg(g.cells + slot);
+        for (int i = 0; i < cell.y; ++i) f(__ldg(g.sorted + cell.x + i));
+    }
+}
+
+// Sweep 1 of a query at q, one thread: |I| (r_FPFH), |P_normal| (r_normal)
+// and the sum of the P_normal offsets from q, in list order.
+struct Sweep1 {
+    int nf = 0, nn = 0;
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+};
+
+__device__ __forceinline__ Sweep1 sweep1(const GridView& g, const Radii& R, int64_t p, float4 q)
+{
+    Sweep1 r;
+    for_each_candidate(g, p, [&](float4 a) {
+        const float dx = a.x - q.x, dy = a.y - q.y, dz = a.z - q.z;
+        const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        if (within(a, q, d2, R.rf2, R.rf2d)) {
+            ++r.nf;
+            if (within(a, q, d2, R.rn2, R.rn2d)) {
+                ++r.nn;
+                r.sx += dx;
+                r.sy += dy;
+                r.sz += dz;
+            }
+        }
+    });
+    return r;
+}
+
+// Moments of the P_normal offsets centred on their mean (mx, my, mz), one
+// thread, in list order: s1 (3), then xx xy xz yy yz zz.  With nbr, the
+// r_FPFH neighbours' indices are written from nbr[0] on.
+__device__ __forceinline__ void sweep2(const GridView& g, const Radii& R, int64_t p, float4 q, float mx, float my,
+                                       float mz, float (&mom)[9], int32_t* nbr)
+{
+#pragma unroll
+    for (int i = 0; i < 9; ++i) mom[i] = 0.f;
+    int64_t out = 0;
+    for_each_candidate(g, p, [&](float4 a) {
+        const float dx = a.x - q.x, dy = a.y - q.y, dz = a.z - q.z;
+        const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        if (!within(a, q, d2, R.rf2, R.rf2d)) return;
+        if (nbr) nbr[out++] = __float_as_int(a.w);
+        if (within(a, q, d2, R.rn2, R.rn2d)) {
+            const float ex = dx - mx, ey = dy - my, ez = dz - mz;
+            mom[0] += ex;
+            mom[1] += ey;
+            mom[2] += ez;
+            mom[3] = fmaf(ex, ex, mom[3]);
+            mom[4] = fmaf(ex, ey, mom[4]);
+            mom[5] = fmaf(ex, ez, mom[5]);
+            mom[6] = fmaf(ey, ey, mom[6]);
+            mom[7] = fmaf(ey, ez, mom[7]);
+            mom[8] = fmaf(ez, ez, mom[8]);
+        }
+    });
+}
+
 // Candidate number t -> position in the sorted point array.
 __device__ __forceinline__ int candidate(int t, int start, int excl)
 {
