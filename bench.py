@@ -42,7 +42,7 @@ WORKLOAD = INDOOR
 
 # DRAM bytes (read + write) of one launch of the dominant kernel, from the ncu
 # capture summarised beside it; None until the current kernel was captured.
-PROFILED_TRAFFIC = {}
+PROFILED_TRAFFIC = {"tc_collect": 98.6e6}  # bytes per launch on the 2M-point indoor pair (ncu, 1-pass capture)
 METRIC = "Faster-PFH+mutual-NN pairs/s (2M-point indoor pair, voxel 0.02 m, full mutual NN)"
 ORACLE_MATCH_ROWS = 400  # rows per side of the oracle's sampled FP64 brute-force matching
 
