@@ -69,6 +69,9 @@ def parse():
                     "(ground removal) and device-side registration")
     ap.add_argument("--no-register", action="store_true", help="skip timing kmx_prune + kmx_gnc (ratio filter, "
                     "invariant graph, max k-core, GNC-TLS pose) on the LiDAR pair's correspondences")
+    ap.add_argument("--workload", default="indoor", choices=["indoor", "lidar"],
+                    help="the pair timed as the headline: the 2M-point indoor pair (default) or the LiDAR pair "
+                         "(for profiling captures of the LiDAR-sized kernels, never a bench line)")
     ap.add_argument("--indoor-points", type=int, default=0,
                     help="raw points per cloud of the indoor pair (default: the 2M-point workload); a smaller "
                          "pair of the same generator for profiling captures, never a bench line")
@@ -369,8 +372,8 @@ def run_kmx(args):
     from paper_2409_15615_gb300 import build as kb
 
     kb.build()
-    work = WORKLOAD
-    if args.indoor_points:
+    work = LIDAR if args.workload == "lidar" else WORKLOAD
+    if args.indoor_points and args.workload == "indoor":
         # a smaller pair of the same generator, for profiling captures only
         work = dict(WORKLOAD, name="indoor_pair_%dk_v0.02" % (args.indoor_points // 1000),
                     points=args.indoor_points)
