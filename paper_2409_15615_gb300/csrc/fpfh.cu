@@ -6,8 +6,8 @@
 //                (Eq. A4); in the same pass |I_valid(q)| = |{ i in M[q] : B[i] }|
 //                and so q in J iff B[q] and |I_valid(q)| >= tau_num
 //   scan/scatter J in ascending point order
-//   fpfh_kernel  FPFH(q) = SPFH(q) + (1/m) sum_k SPFH(k) / w_k (Eq. A5), one
-//                warp per row, lane l owning bin l, compensated summation
+//   fpfh_kernel  FPFH(q) = SPFH(q) + (1/m) sum_k SPFH(k) / w_k (Eq. A5), four
+//                rows per warp, a lane owning four bins, compensated summation
 //
 // I_valid is never materialised: the SPFH and FPFH kernels walk M[q] and
 // skip entries without B (one byte gathered per neighbour).
