@@ -335,6 +335,13 @@ def bench_pair(torch, w, args, rank, world, local, headline):
             roof["executed_tensor_flops"] = ex
             roof["executed_tflops"] = ex / (roof["ms"] / 1000.0) / 1e12
 
+    precision = None
+    if headline:
+        try:
+            precision = precision_vs_fp64(pair)
+        except Exception as exc:  # a report, never a reason to lose the line
+            precision = dict(error="%s: %s" % (type(exc).__name__, exc))
+
     # ---- end to end through host buffers
     e2e = end_to_end(torch, ctx, pair, src, tgt, ps, pt, mode, args.steps, world if headline else 1, w["slots"],
                      reduce=headline)
@@ -353,7 +360,8 @@ def bench_pair(torch, w, args, rank, world, local, headline):
         latency_ms=dict(p50=float(np.percentile(step_ms, 50)), p99=float(np.percentile(step_ms, 99))),
         wall_s=wall, stages_ms=stages, roofline=roof, e2e=e2e, gpu_launches=launches * args.steps,
         gpu_launches_per_step=launches, clocks=clk, match_mode_ms_per_step=mode_ms,
-        match_modes_identical=identical, tensor_match_diag=diag, cuda_graph=graph is not None)
+        match_modes_identical=identical, tensor_match_diag=diag, precision_vs_fp64=precision,
+        cuda_graph=graph is not None)
     del graph
     pair.close()
     ctx.close()
@@ -935,6 +943,50 @@ def end_to_end(torch, ctx, pair, src, tgt, ps, pt, mode, steps, world, slots, re
                 d2h_bytes_per_step=int(h_corr.numel() * 4 + 8),
                 p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
                 correspondences=n_corr, overlapped=True, pairs_in_flight=slots)
+
+
+def precision_vs_fp64(pair, rows=200, seed=0):
+    """Per-result error of the step's correspondences against FP64, on the
+    GPU's own descriptors: for sampled correspondences (i, j), the distances
+    d1 = |x_i - y_j|^2 and d2 (second-nearest row of the target) recomputed in
+    FP64 by brute force over every target row, their relative errors, and
+    whether the FP64 nearest row is j (rows whose FP64 top-2 gap is below
+    1e-3 relative are counted apart: there the nearest row may differ)."""
+    gi, gj, gd1, gd2 = pair.correspondences()
+    if len(gi) == 0:
+        return None
+    s_, t_ = pair.src, pair.tgt
+    nJs, nJt = int(s_.out["n_valid"].item()), int(t_.out["n_valid"].item())
+    JP = s_.out["valid"][:nJs].cpu().numpy()
+    JQ = t_.out["valid"][:nJt].cpu().numpy()
+    P = s_.out["desc"][:nJs, :33].cpu().numpy().astype(np.float64)
+    Q = t_.out["desc"][:nJt, :33].cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(len(gi), min(rows, len(gi)), replace=False)
+    rp = np.searchsorted(JP, gi[pick])
+    rq = np.searchsorted(JQ, gj[pick])
+    q2 = (Q * Q).sum(1)
+    e1, e2, same, ties = [], [], 0, 0
+    for k0 in range(0, len(pick), 50):
+        X = P[rp[k0:k0 + 50]]
+        d = np.maximum((X * X).sum(1)[:, None] + q2[None, :] - 2.0 * X @ Q.T, 0.0)
+        part = np.partition(d, 1, axis=1)
+        nn = d.argmin(1)
+        for r in range(len(X)):
+            k = k0 + r
+            exact1 = float(((P[rp[k]] - Q[rq[k]]) ** 2).sum())  # d1 of the returned pair, direct form
+            b1, b2 = float(part[r, 0]), float(part[r, 1])
+            e1.append(abs(float(gd1[pick[k]]) - exact1) / max(exact1, 1e-30))
+            e2.append(abs(float(gd2[pick[k]]) - b2) / max(b2, 1e-30))
+            if (b2 - b1) / max(b2, 1e-300) < 1e-3:
+                ties += 1
+            elif nn[r] == rq[k]:
+                same += 1
+    e1, e2 = np.array(e1), np.array(e2)
+    checked = len(pick) - ties
+    return dict(rows=int(len(pick)), nn_equal_fp64=same / max(checked, 1), top2_gap_below_1e3=ties,
+                d1_rel_err_max=float(e1.max()), d1_rel_err_median=float(np.median(e1)),
+                d2_rel_err_max=float(e2.max()), d2_rel_err_median=float(np.median(e2)))
 
 
 def count_launches(torch, step):
