@@ -947,11 +947,12 @@ def end_to_end(torch, ctx, pair, src, tgt, ps, pt, mode, steps, world, slots, re
 
 def precision_vs_fp64(pair, rows=200, seed=0):
     """Per-result error of the step's correspondences against FP64, on the
-    GPU's own descriptors: for sampled correspondences (i, j), the distances
-    d1 = |x_i - y_j|^2 and d2 (second-nearest row of the target) recomputed in
-    FP64 by brute force over every target row, their relative errors, and
-    whether the FP64 nearest row is j (rows whose FP64 top-2 gap is below
-    1e-3 relative are counted apart: there the nearest row may differ)."""
+    GPU's own descriptors: for sampled correspondences (i, j), the descriptor
+    distances d1 = |x_i - y_j| and d2 (second-nearest row of the target; both
+    Euclidean, as kmx_corr holds them) recomputed in FP64 by brute force over
+    every target row, their relative errors, and whether the FP64 nearest row
+    is j (rows whose FP64 top-2 squared distances are within 1e-3 relative are
+    counted apart: there the nearest row may differ)."""
     gi, gj, gd1, gd2 = pair.correspondences()
     if len(gi) == 0:
         return None
@@ -974,10 +975,11 @@ def precision_vs_fp64(pair, rows=200, seed=0):
         nn = d.argmin(1)
         for r in range(len(X)):
             k = k0 + r
-            exact1 = float(((P[rp[k]] - Q[rq[k]]) ** 2).sum())  # d1 of the returned pair, direct form
+            exact1 = float(np.sqrt(((P[rp[k]] - Q[rq[k]]) ** 2).sum()))  # d1 of the returned pair, direct form
             b1, b2 = float(part[r, 0]), float(part[r, 1])
+            exact2 = float(np.sqrt(b2))
             e1.append(abs(float(gd1[pick[k]]) - exact1) / max(exact1, 1e-30))
-            e2.append(abs(float(gd2[pick[k]]) - b2) / max(b2, 1e-30))
+            e2.append(abs(float(gd2[pick[k]]) - exact2) / max(exact2, 1e-30))
             if (b2 - b1) / max(b2, 1e-300) < 1e-3:
                 ties += 1
             elif nn[r] == rq[k]:

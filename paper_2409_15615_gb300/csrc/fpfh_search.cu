@@ -15,9 +15,10 @@
 //                          tau_num and tau_lin (step 1)
 //   valid_walk             |I_valid(q)| over the neighbours with B; J (step 2)
 //   spfh_walk, fpfh_walk   over B neighbours, for B points / for J
-// The normals take one thread per query, the other stages one warp per
-// query; queries run in the grid's cell order so that neighbouring threads
-// and warps walk the same cells.  The neighbours a stage visits come
+// The normals take one thread per query on a large cloud and one warp per
+// query on a small one, by the same rule as kmx_normals (kThreadQueryMin);
+// the other stages take one warp per query.  Queries run in the grid's cell
+// order so that neighbouring threads and warps walk the same cells.  The neighbours a stage visits come
 // in the same order as in the stored lists of kmx_normals, so every sum is
 // formed in the same order and the list-free Faster-PFH reproduces the
 // list-based one bit for bit.
@@ -31,6 +32,8 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+constexpr int kQPerWarp = 4;
+constexpr int kQPerBlock = kWarps * kQPerWarp;  // = 32, one per lane of the solving warp
 constexpr int kMinNormal = 3;                   // classic: PCA of fewer points fixes no plane
 
 struct ClassicScratch {
@@ -59,30 +62,157 @@ __global__ void __launch_bounds__(kThreads) walk_normals(GridView g, Radii R, fl
                                                          int tau_num, float tau_lin, float4* __restrict__ normal4,
                                                          uint8_t* __restrict__ flags, int32_t* __restrict__ jflag)
 {
-    // one thread per query: the two sweeps of kmx_normals (the same order,
-    // so the same bits), then the FP64 solve of its moments
+    __shared__ float sm_mom[9][kQPerBlock];
+    __shared__ float sm_q[3][kQPerBlock];
+    __shared__ int sm_qi[kQPerBlock], sm_nN[kQPerBlock];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t n_sorted = *g.n_sorted;
     const float vp[3] = {vp0, vp1, vp2};
-    for (int64_t p = (int64_t)blockIdx.x * kThreads + threadIdx.x; p < n_sorted; p += (int64_t)gridDim.x * kThreads) {
-        const float4 q = g.sorted[p];
-        const int qi = __float_as_int(q.w);
-        const Sweep1 r = sweep1(g, R, p, q);
-        const bool pca = kClassic ? r.nn >= kMinNormal : (r.nf >= tau_num && r.nn >= tau_num);
-        uint8_t flag = 0;
-        float4 nout = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (pca) {
-            const float inv = r.nn > 0 ? 1.0f / (float)r.nn : 0.0f;
-            float mom[9];
-            sweep2(g, R, p, q, r.sx * inv, r.sy * inv, r.sz * inv, mom, nullptr);
-            double plin;
-            flag |= 4;
-            const bool has = normal_from_moments(mom, r.nn, q.x, q.y, q.z, vp, &nout, &plin);
-            if (kClassic && has) flag |= 3;
-            if (!kClassic && has && plin < (double)tau_lin) flag |= 1;
+    if (n_sorted >= kThreadQueryMin) {
+        // one thread per query: the two sweeps of kmx_normals (the same
+        // order, so the same bits), then the FP64 solve of its moments
+        for (int64_t p = (int64_t)blockIdx.x * kThreads + threadIdx.x; p < n_sorted; p += (int64_t)gridDim.x * kThreads) {
+            const float4 q = g.sorted[p];
+            const int qi = __float_as_int(q.w);
+            const Sweep1 r = sweep1(g, R, p, q);
+            const bool pca = kClassic ? r.nn >= kMinNormal : (r.nf >= tau_num && r.nn >= tau_num);
+            uint8_t flag = 0;
+            float4 nout = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (pca) {
+                const float inv = r.nn > 0 ? 1.0f / (float)r.nn : 0.0f;
+                float mom[9];
+                sweep2(g, R, p, q, r.sx * inv, r.sy * inv, r.sz * inv, mom, nullptr);
+                double plin;
+                flag |= 4;
+                const bool has = normal_from_moments(mom, r.nn, q.x, q.y, q.z, vp, &nout, &plin);
+                if (kClassic && has) flag |= 3;
+                if (!kClassic && has && plin < (double)tau_lin) flag |= 1;
+            }
+            normal4[qi] = nout;
+            flags[qi] = flag;
+            if (kClassic) jflag[qi] = flag & 1;
         }
-        normal4[qi] = nout;
-        flags[qi] = flag;
-        if (kClassic) jflag[qi] = flag & 1;
+        return;
+    }
+    // one warp per query (the same layout as kmx_normals on a small cloud);
+    // the block's 32 queries are solved by warp 0, one per lane
+    // uniform over the block: every thread reaches the barriers
+    for (int64_t chunk = blockIdx.x; chunk * kQPerBlock < n_sorted; chunk += gridDim.x) {
+        for (int k = 0; k < kQPerWarp; ++k) {
+            const int slot = warp * kQPerWarp + k;
+            const int64_t p = chunk * kQPerBlock + slot;
+            if (p >= n_sorted) {
+                if (lane == 0) sm_qi[slot] = -1;
+                continue;
+            }
+            const float4 q = g.sorted[p];
+            int start, excl;
+            const int total = stencil(g, p, lane, &start, &excl);
+            // sweep 1: |I|, |P_normal| and the mean offset from q
+            int nf = 0, nn = 0;
+            float sx = 0.f, sy = 0.f, sz = 0.f;
+            for (int base = 0; base < total; base += 32) {
+                const int t = base + lane;
+                const int pos = candidate(t, start, excl);
+                bool inF = false, inN = false;
+                float dx = 0.f, dy = 0.f, dz = 0.f;
+                if (t < total) {
+                    const float4 a = g.sorted[pos];
+                    dx = a.x - q.x;
+                    dy = a.y - q.y;
+                    dz = a.z - q.z;
+                    const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    inF = within(a, q, d2, R.rf2, R.rf2d);
+                    inN = inF && within(a, q, d2, R.rn2, R.rn2d);
+                }
+                nf += __popc(__ballot_sync(kFull, inF));
+                nn += __popc(__ballot_sync(kFull, inN));
+                if (inN) {
+                    sx += dx;
+                    sy += dy;
+                    sz += dz;
+                }
+            }
+            sx = warp_sum(sx);
+            sy = warp_sum(sy);
+            sz = warp_sum(sz);
+            const float inv = nn > 0 ? 1.0f / (float)nn : 0.0f;
+            const float mx = sx * inv, my = sy * inv, mz = sz * inv;
+            // sweep 2: moments of the offsets centred on that mean
+            float s1x = 0.f, s1y = 0.f, s1z = 0.f;
+            float sxx = 0.f, sxy = 0.f, sxz = 0.f, syy = 0.f, syz = 0.f, szz = 0.f;
+            const bool pca = kClassic ? nn >= kMinNormal : (nf >= tau_num && nn >= tau_num);
+            if (pca) {
+                for (int base = 0; base < total; base += 32) {
+                    const int t = base + lane;
+                    const int pos = candidate(t, start, excl);
+                    if (t < total) {
+                        const float4 a = g.sorted[pos];
+                        const float dx = a.x - q.x, dy = a.y - q.y, dz = a.z - q.z;
+                        const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                        if (within(a, q, d2, R.rf2, R.rf2d) && within(a, q, d2, R.rn2, R.rn2d)) {
+                            const float ex = dx - mx, ey = dy - my, ez = dz - mz;
+                            s1x += ex;
+                            s1y += ey;
+                            s1z += ez;
+                            sxx = fmaf(ex, ex, sxx);
+                            sxy = fmaf(ex, ey, sxy);
+                            sxz = fmaf(ex, ez, sxz);
+                            syy = fmaf(ey, ey, syy);
+                            syz = fmaf(ey, ez, syz);
+                            szz = fmaf(ez, ez, szz);
+                        }
+                    }
+                }
+            }
+            s1x = warp_sum(s1x);
+            s1y = warp_sum(s1y);
+            s1z = warp_sum(s1z);
+            sxx = warp_sum(sxx);
+            sxy = warp_sum(sxy);
+            sxz = warp_sum(sxz);
+            syy = warp_sum(syy);
+            syz = warp_sum(syz);
+            szz = warp_sum(szz);
+            if (lane == 0) {
+                sm_mom[0][slot] = s1x;
+                sm_mom[1][slot] = s1y;
+                sm_mom[2][slot] = s1z;
+                sm_mom[3][slot] = sxx;
+                sm_mom[4][slot] = sxy;
+                sm_mom[5][slot] = sxz;
+                sm_mom[6][slot] = syy;
+                sm_mom[7][slot] = syz;
+                sm_mom[8][slot] = szz;
+                sm_q[0][slot] = q.x;
+                sm_q[1][slot] = q.y;
+                sm_q[2][slot] = q.z;
+                sm_qi[slot] = __float_as_int(q.w);
+                sm_nN[slot] = pca ? nn : -1;
+            }
+        }
+        __syncthreads();
+        if (warp == 0 && sm_qi[lane] >= 0) {
+            const int qi = sm_qi[lane];
+            const int nN = sm_nN[lane];
+            uint8_t flag = 0;
+            float4 nout = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (nN >= 0) {
+                float mom[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) mom[i] = sm_mom[i][lane];
+                double plin;
+                flag |= 4;
+                const bool has = normal_from_moments(mom, nN, sm_q[0][lane], sm_q[1][lane], sm_q[2][lane], vp, &nout,
+                                                     &plin);
+                if (kClassic && has) flag |= 3;
+                if (!kClassic && has && plin < (double)tau_lin) flag |= 1;
+            }
+            normal4[qi] = nout;
+            flags[qi] = flag;
+            if (kClassic) jflag[qi] = flag & 1;
+        }
+        __syncthreads();  // the shared moments are rewritten by the next chunk
     }
 }
 
@@ -277,7 +407,7 @@ cudaError_t kmx_fpfh_search_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_pa
     if ((e = cudaMemsetAsync(normal4, 0, sizeof(float4) * n, st))) return e;
     if ((e = cudaMemsetAsync(flags, 0, n, st))) return e;
     if ((e = cudaMemsetAsync(s.jflag, 0, sizeof(int32_t) * (n + 1), st))) return e;
-    const unsigned nbn = kmx_stride_blocks(n, kThreads, ctx->sm_count);
+    const unsigned nbn = kmx_stride_blocks(n, kQPerBlock, ctx->sm_count);
     const unsigned nbw = kmx_stride_blocks(n, kWarps, ctx->sm_count);
     const float4* n4 = reinterpret_cast<const float4*>(normal4);
     KMX_COUNT_LAUNCH();

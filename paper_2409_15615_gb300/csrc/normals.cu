@@ -2,11 +2,17 @@
 // r_FPFH (Eq. A1), the r_normal subsample P_normal, PCA normal and linearity,
 // and the reliability flag B.
 //
-// One thread per query, queries taken in cell order so that neighbouring
-// threads walk the same cells (their candidate loads coincide or share cache
-// lines).  A thread walks its 27-cell stencil in the order of the stored
-// lists and sums in that order (no shuffles, no cross-lane reductions).  Two
-// passes: the first counts |I| and accumulates the P_normal mean; after a
+// Queries are taken in cell order so that neighbouring threads or warps walk
+// the same cells (their candidate loads coincide or share cache lines).  The
+// kernels pick one of two layouts from the device point count, the same way in
+// every launch (kThreadQueryMin, search_common.cuh):
+//  - large clouds: one thread per query.  The thread walks its 27-cell stencil
+//    in the order of the stored lists and sums in that order.
+//  - small clouds (too few queries to fill the GPU one per thread): one warp
+//    per query.  The 27 stencil cells are looked up by 27 lanes at once, their
+//    candidate ranges are flattened into one index space, and all 32 lanes
+//    test candidates.
+// Two passes: the first counts |I| and accumulates the P_normal mean; after a
 // prefix sum of the counts the second writes the CSR lists and accumulates
 // the covariance centred on that mean.
 //
@@ -25,6 +31,9 @@ using namespace kmxs;
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kQPerWarp = 4;                    // queries per warp in the warp-per-query fill pass
+constexpr int kQPerBlock = kWarps * kQPerWarp;  // = 32, queries per block per step in that mode
 
 struct NormScratch {
     int32_t* cnt;    // [n+1] |I(q)|
@@ -43,11 +52,58 @@ NormScratch carve(void* base, int64_t n, size_t* total)
     return s;
 }
 
-// Pass 1: |I(q)|, |P_normal| and the P_normal mean (relative to q); one
-// thread per query (sorted position), its stencil walked in list order.
+// Pass 1: |I(q)|, |P_normal| and the P_normal mean (relative to q), per
+// sorted position.
 __global__ void __launch_bounds__(kThreads) search_count(GridView g, Radii R, NormScratch s)
 {
+    const int lane = threadIdx.x & 31;
     const int64_t n_sorted = *g.n_sorted;
+    if (n_sorted < kThreadQueryMin) {  // one warp per query
+        const int64_t warps = (int64_t)gridDim.x * kWarps;
+        for (int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); w * kQPerWarp < n_sorted; w += warps) {
+            StencilCache sc;
+            for (int k = 0; k < kQPerWarp && w * kQPerWarp + k < n_sorted; ++k) {
+                const float4 q = g.sorted[w * kQPerWarp + k];
+                const int qi = __float_as_int(q.w);
+                const int total = sc.get(g, w * kQPerWarp + k, lane);
+                const int start = sc.start, excl = sc.excl;
+                int nf = 0, nn = 0;
+                float sx = 0.f, sy = 0.f, sz = 0.f;
+                for (int base = 0; base < total; base += 32) {
+                    const int t = base + lane;
+                    const int pos = candidate(t, start, excl);
+                    bool inF = false, inN = false;
+                    float dx = 0.f, dy = 0.f, dz = 0.f;
+                    if (t < total) {
+                        const float4 a = g.sorted[pos];
+                        dx = a.x - q.x;
+                        dy = a.y - q.y;
+                        dz = a.z - q.z;
+                        const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                        inF = within(a, q, d2, R.rf2, R.rf2d);
+                        inN = inF && within(a, q, d2, R.rn2, R.rn2d);
+                    }
+                    nf += __popc(__ballot_sync(kFull, inF));
+                    nn += __popc(__ballot_sync(kFull, inN));
+                    if (inN) {
+                        sx += dx;
+                        sy += dy;
+                        sz += dz;
+                    }
+                }
+                sx = warp_sum(sx);
+                sy = warp_sum(sy);
+                sz = warp_sum(sz);
+                if (lane == 0) {
+                    s.cnt[qi] = nf;
+                    const float inv = nn > 0 ? 1.0f / (float)nn : 0.0f;
+                    s.mean[qi] = make_float4(sx * inv, sy * inv, sz * inv, __int_as_float(nn));
+                }
+            }
+        }
+        return;
+    }
+    // one thread per query
     for (int64_t p = (int64_t)blockIdx.x * kThreads + threadIdx.x; p < n_sorted; p += (int64_t)gridDim.x * kThreads) {
         const float4 q = g.sorted[p];
         const int qi = __float_as_int(q.w);
@@ -71,11 +127,12 @@ struct NormOut {
     float vp[3];
 };
 
-// Pass 2: CSR lists and centred second moments over P_normal, one thread
-// per query; the moments go to scratch for solve_normals.
+// Pass 2: CSR lists and centred second moments over P_normal per sorted
+// position; the moments go to scratch for solve_normals.
 __global__ void __launch_bounds__(kThreads) search_fill(GridView g, Radii R, NormScratch s, NormOut o,
                                                         unsigned int* err)
 {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t total_list = o.offs[o.n_cap];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *o.needed = total_list;
@@ -83,6 +140,73 @@ __global__ void __launch_bounds__(kThreads) search_fill(GridView g, Radii R, Nor
     }
     const bool write = o.nbr && total_list <= o.nbr_cap;
     const int64_t n_sorted = *g.n_sorted;
+    if (n_sorted < kThreadQueryMin) {  // one warp per query
+        for (int64_t chunk = blockIdx.x; chunk * kQPerBlock < n_sorted; chunk += gridDim.x) {
+            StencilCache sc;  // the warp's queries are consecutive in cell order
+            for (int k = 0; k < kQPerWarp; ++k) {
+                const int slot = warp * kQPerWarp + k;
+                const int64_t p = chunk * kQPerBlock + slot;
+                if (p >= n_sorted) break;
+                const float4 q = g.sorted[p];
+                const int qi = __float_as_int(q.w);
+                const float4 mq = s.mean[qi];
+                const int total = sc.get(g, p, lane);
+                const int start = sc.start, excl = sc.excl;
+                int64_t out = o.offs[qi];
+                float s1x = 0.f, s1y = 0.f, s1z = 0.f;
+                float sxx = 0.f, sxy = 0.f, sxz = 0.f, syy = 0.f, syz = 0.f, szz = 0.f;
+                for (int base = 0; base < total; base += 32) {
+                    const int t = base + lane;
+                    const int pos = candidate(t, start, excl);
+                    bool inF = false, inN = false;
+                    float dx = 0.f, dy = 0.f, dz = 0.f;
+                    int idx = 0;
+                    if (t < total) {
+                        const float4 a = g.sorted[pos];
+                        idx = __float_as_int(a.w);
+                        dx = a.x - q.x;
+                        dy = a.y - q.y;
+                        dz = a.z - q.z;
+                        const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                        inF = within(a, q, d2, R.rf2, R.rf2d);
+                        inN = inF && within(a, q, d2, R.rn2, R.rn2d);
+                    }
+                    const unsigned bal = __ballot_sync(kFull, inF);
+                    if (inF && write) o.nbr[out + __popc(bal & ((1u << lane) - 1u))] = idx;
+                    out += __popc(bal);
+                    if (inN) {
+                        const float ex = dx - mq.x, ey = dy - mq.y, ez = dz - mq.z;
+                        s1x += ex;
+                        s1y += ey;
+                        s1z += ez;
+                        sxx = fmaf(ex, ex, sxx);
+                        sxy = fmaf(ex, ey, sxy);
+                        sxz = fmaf(ex, ez, sxz);
+                        syy = fmaf(ey, ey, syy);
+                        syz = fmaf(ey, ez, syz);
+                        szz = fmaf(ez, ez, szz);
+                    }
+                }
+                s1x = warp_sum(s1x);
+                s1y = warp_sum(s1y);
+                s1z = warp_sum(s1z);
+                sxx = warp_sum(sxx);
+                sxy = warp_sum(sxy);
+                sxz = warp_sum(sxz);
+                syy = warp_sum(syy);
+                syz = warp_sum(syz);
+                szz = warp_sum(szz);
+                if (lane == 0) {
+                    float4* m = s.mom + 3 * (int64_t)qi;
+                    m[0] = make_float4(s1x, s1y, s1z, sxx);
+                    m[1] = make_float4(sxy, sxz, syy, syz);
+                    m[2] = make_float4(szz, 0.f, 0.f, 0.f);
+                }
+            }
+        }
+        return;
+    }
+    // one thread per query
     for (int64_t p = (int64_t)blockIdx.x * kThreads + threadIdx.x; p < n_sorted; p += (int64_t)gridDim.x * kThreads) {
         const float4 q = g.sorted[p];
         const int qi = __float_as_int(q.w);
@@ -174,12 +298,12 @@ cudaError_t kmx_normals_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_params
     clear_counts<<<kmx_stride_blocks(n, 256, ctx->sm_count), 256, 0, st>>>(
         s.cnt, reinterpret_cast<float4*>(normal4), flags, g->d_n, n);
     KMX_COUNT_LAUNCH();
-    search_count<<<kmx_stride_blocks(n, kThreads, ctx->sm_count), kThreads, 0, st>>>(gv, R, s);
+    search_count<<<kmx_stride_blocks(n, kQPerBlock, ctx->sm_count), kThreads, 0, st>>>(gv, R, s);
     if ((e = kmx_scan_i32(ctx, s.cnt, n, g->d_n, offs))) return e;
     NormOut o{reinterpret_cast<float4*>(normal4), flags, offs, nbr, nbr_cap, n, needed, prm->tau_num,
               prm->tau_lin, {prm->viewpoint[0], prm->viewpoint[1], prm->viewpoint[2]}};
     KMX_COUNT_LAUNCH();
-    search_fill<<<kmx_stride_blocks(n, kThreads, ctx->sm_count), kThreads, 0, st>>>(gv, R, s, o, ctx->d_err);
+    search_fill<<<kmx_stride_blocks(n, kQPerBlock, ctx->sm_count), kThreads, 0, st>>>(gv, R, s, o, ctx->d_err);
     KMX_COUNT_LAUNCH();
     solve_normals<<<kmx_stride_blocks(n, kThreads, ctx->sm_count), kThreads, 0, st>>>(gv, s, o);
     if (nbr) {

@@ -109,6 +109,12 @@ struct StencilCache {
     }
 };
 
+// Device point count from which the radius searches (normals, the list-free
+// FPFH path) give each query one thread; below it one warp takes a query, so
+// that a small cloud still fills the GPU.  Every search kernel applies the
+// same rule, which keeps the list and list-free paths bit-identical.
+constexpr int64_t kThreadQueryMin = 65536;
+
 // One thread per query: calls f(a) for every bucketed point a of the 27-cell
 // stencil around sorted position p, in the order of the stored neighbour
 // lists (cells dx fastest, then dy, then dz; points of a cell in sorted

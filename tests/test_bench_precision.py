@@ -1,7 +1,8 @@
 """The bench's per-result FP64 check (`bench.precision_vs_fp64`) on a CPU
 stand-in of a pair: correspondences built from the exact FP64 nearest rows
-must report full agreement and FP32-level relative errors, and a planted wrong
-partner must lower the agreement."""
+must report full agreement and FP32-level relative errors; a planted wrong
+partner must lower the agreement, and squared distances in place of the
+Euclidean ones kmx_corr holds must show as large relative errors."""
 import types
 
 import numpy as np
@@ -32,8 +33,8 @@ def _case(seed=3, n=300, m=400):
     nn = D.argmin(1)
     srt = np.sort(D, axis=1)
     gi, gj = JP, JQ[nn]
-    d1 = srt[:, 0].astype(np.float32)
-    d2 = srt[:, 1].astype(np.float32)
+    d1 = np.sqrt(srt[:, 0]).astype(np.float32)  # kmx_corr holds Euclidean distances
+    d2 = np.sqrt(srt[:, 1]).astype(np.float32)
     return P, Q, JP, JQ, gi, gj, d1, d2, nn
 
 
@@ -55,3 +56,12 @@ def test_planted_wrong_partner_is_seen():
     r = bench.precision_vs_fp64(_fake_pair(P, Q, JP, JQ, gi, gj, d1, d2), rows=300)
     assert r["nn_equal_fp64"] < 0.6
     assert r["d1_rel_err_max"] > 1e-3  # the stated d1 no longer matches the returned pair
+
+
+def test_squared_distances_are_seen():
+    import bench
+
+    P, Q, JP, JQ, gi, gj, d1, d2, _ = _case()
+    r = bench.precision_vs_fp64(_fake_pair(P, Q, JP, JQ, gi, gj, d1 * d1, d2 * d2), rows=120)
+    assert r["nn_equal_fp64"] == 1.0
+    assert r["d1_rel_err_median"] > 1.0 and r["d2_rel_err_median"] > 1.0
