@@ -89,11 +89,12 @@ __global__ void __launch_bounds__(kThreads) match_tiles_fp32(const float* __rest
                                                              int64_t nq_cap, const int64_t* d_nq, int target_ctas,
                                                              int max_chunks, kmx::RowBest* __restrict__ part,
                                                              unsigned long long* __restrict__ colbest,
-                                                             int* __restrict__ chunks_out)
+                                                             int* __restrict__ chunks_out, int64_t rows_min)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FpShared& S = *reinterpret_cast<FpShared*>(smem_raw);
     const int64_t np = kmx_count(d_np, np_cap), nq = kmx_count(d_nq, nq_cap);
+    if (rows_list && np <= rows_min) return;  // a short list: rows_stream takes it
     const int64_t npt = (np + kTile - 1) / kTile;
     const int64_t nqt = (nq + kTile - 1) / kTile;
     const int64_t stride = rows_list ? np : np_cap;  // partials of one chunk
@@ -225,6 +226,85 @@ __global__ void __launch_bounds__(kThreads) match_tiles_fp32(const float* __rest
 }
 
 
+// A short row list (at most kStreamRows rows; the tensor-core matcher's
+// fallback usually lists a handful): one item per (list row, column chunk),
+// each a CTA pass over the chunk's columns.  The arithmetic is the tiled
+// kernel's (x - y, then one fused multiply-add per dimension in dimension
+// order), so the summaries are the same bits; the partials go to
+// part[c * n + r] as the tiled kernel leaves them.  The tiled kernel spends a
+// whole 128-row tile on each of these rows.
+constexpr int kStreamRows = 64;
+constexpr int kStreamChunks = 128;
+constexpr int kStreamThreads = 256;
+static_assert(kDim == 33 && kStride == 36, "rows_stream unrolls 8 float4 and one scalar per row");
+
+__global__ void __launch_bounds__(kStreamThreads) rows_stream(const float* __restrict__ dp,
+                                                              const int32_t* __restrict__ rows, int64_t list_cap,
+                                                              const int64_t* d_nlist, const float* __restrict__ dq,
+                                                              int64_t nq_cap, const int64_t* d_nq, int64_t part_cap,
+                                                              kmx::RowBest* __restrict__ part,
+                                                              int* __restrict__ chunks_out)
+{
+    __shared__ kmx::RowBest red[kStreamThreads / 32];
+    const int64_t n = kmx_count(d_nlist, list_cap);
+    if (n > kStreamRows) return;  // the tiled kernel takes it
+    const int64_t nq = kmx_count(d_nq, nq_cap);
+    const int64_t room = part_cap / (n > 0 ? n : 1);
+    const int chunks = (int)(room < kStreamChunks ? (room > 1 ? room : 1) : kStreamChunks);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *chunks_out = chunks;
+    const int64_t per = (nq + chunks - 1) / chunks;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // uniform over the block: every thread reaches the barriers
+    for (int64_t item = blockIdx.x; item < n * chunks; item += gridDim.x) {
+        const int64_t r = item / chunks;
+        const int c = (int)(item % chunks);
+        const float* x = dp + (int64_t)rows[r] * kStride;
+        float xr[kDim];
+#pragma unroll
+        for (int k = 0; k < kDim; ++k) xr[k] = __ldg(x + k);
+        float b1 = INFINITY, b2 = INFINITY;
+        int j1 = 0x7fffffff;
+        const int64_t c0 = (int64_t)c * per;
+        const int64_t c1 = c0 + per < nq ? c0 + per : nq;
+        for (int64_t j = c0 + threadIdx.x; j < c1; j += kStreamThreads) {
+            const float* y = dq + j * kStride;
+            const float4* y4 = reinterpret_cast<const float4*>(y);
+            float acc = 0.f;
+#pragma unroll
+            for (int q4 = 0; q4 < 8; ++q4) {
+                const float4 v = __ldg(y4 + q4);
+                float e = __fsub_rn(xr[4 * q4], v.x);
+                acc = __fmaf_rn(e, e, acc);
+                e = __fsub_rn(xr[4 * q4 + 1], v.y);
+                acc = __fmaf_rn(e, e, acc);
+                e = __fsub_rn(xr[4 * q4 + 2], v.z);
+                acc = __fmaf_rn(e, e, acc);
+                e = __fsub_rn(xr[4 * q4 + 3], v.w);
+                acc = __fmaf_rn(e, e, acc);
+            }
+            const float e = __fsub_rn(xr[32], __ldg(y + 32));
+            acc = __fmaf_rn(e, e, acc);
+            kmx::row_update(b1, j1, b2, acc, (int)j);
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            const float od1 = __shfl_xor_sync(0xffffffffu, b1, o);
+            const int oj = __shfl_xor_sync(0xffffffffu, j1, o);
+            const float od2 = __shfl_xor_sync(0xffffffffu, b2, o);
+            kmx::row_merge(b1, j1, b2, od1, oj, od2);
+        }
+        if (lane == 0) red[warp] = kmx::RowBest{b1, j1, b2};
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            kmx::RowBest b = red[0];
+            for (int w = 1; w < kStreamThreads / 32; ++w)
+                kmx::row_merge(b.d1, b.j1, b.d2, red[w].d1, red[w].j1, red[w].d2);
+            part[(int64_t)c * n + r] = b;
+        }
+        __syncthreads();  // red is rewritten by the next item
+    }
+}
+
 // Opt in to >48 KB of dynamic shared memory once per device (the first call
 // happens before any capture of a pair into a CUDA graph).
 cudaError_t set_smem_attr()
@@ -253,7 +333,7 @@ cudaError_t kmx_match_fp32_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap,
     const int64_t blocks = (npt > 0 ? npt : 1) * max_chunks;
     KMX_COUNT_LAUNCH();
     match_tiles_fp32<<<(unsigned)blocks, kThreads, sizeof(FpShared), ctx->stream>>>(
-        dp, nullptr, np_cap, d_np, dq, nq_cap, d_nq, 4 * ctx->sm_count, max_chunks, s.part, s.colbest, s.chunks);
+        dp, nullptr, np_cap, d_np, dq, nq_cap, d_nq, 4 * ctx->sm_count, max_chunks, s.part, s.colbest, s.chunks, 0);
     return cudaGetLastError();
 }
 
@@ -263,13 +343,20 @@ cudaError_t kmx_match_fp32_rows_launch(kmx_ctx* ctx, const float* dp, const int3
 {
     cudaError_t e = set_smem_attr();
     if (e) return e;
+    // both kernels read the list length on the device; exactly one of them
+    // works (and publishes the chunk count): rows_stream up to kStreamRows
+    // rows, the tiled kernel above
+    KMX_COUNT_LAUNCH();
+    rows_stream<<<(unsigned)(2 * (ctx->sm_count > 0 ? ctx->sm_count : 1)), kStreamThreads, 0, ctx->stream>>>(
+        dp, rows, list_cap, d_nlist, dq, nq_cap, d_nq, (int64_t)kMaxChunksFp32 * (list_cap + 1), part, chunks_out);
     // row tiles x chunks <= row tiles + target for the split work_chunks picks
     const int64_t npt = (list_cap + kTile - 1) / kTile;
     const int target = 4 * ctx->sm_count;
     const int64_t blocks = (npt > 0 ? npt : 1) + target;
     KMX_COUNT_LAUNCH();
     match_tiles_fp32<<<(unsigned)blocks, kThreads, sizeof(FpShared), ctx->stream>>>(
-        dp, rows, list_cap, d_nlist, dq, nq_cap, d_nq, target, kMaxChunksRows, part, nullptr, chunks_out);
+        dp, rows, list_cap, d_nlist, dq, nq_cap, d_nq, target, kMaxChunksRows, part, nullptr, chunks_out,
+        kStreamRows);
     return cudaGetLastError();
 }
 

@@ -332,6 +332,25 @@ __global__ void __launch_bounds__(256) tree_out(int64_t np_cap, const int64_t* d
         perm[e < np ? e : np_cap + (e - np)] = vals[e];
 }
 
+// (x - c) . v over the 33 values of descriptor row x (16-byte aligned, read
+// as eight float4 and one float).
+__device__ __forceinline__ float project(const float* __restrict__ x, const float* c, const float* v)
+{
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    float4 r[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) r[q] = __ldg(x4 + q);
+    float p = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        p = fmaf(r[q].x - c[4 * q], v[4 * q], p);
+        p = fmaf(r[q].y - c[4 * q + 1], v[4 * q + 1], p);
+        p = fmaf(r[q].z - c[4 * q + 2], v[4 * q + 2], p);
+        p = fmaf(r[q].w - c[4 * q + 3], v[4 * q + 3], p);
+    }
+    return fmaf(__ldg(x + 32) - c[32], v[32], p);
+}
+
 // Shared memory of one node's direction (besides the sampled rows).
 struct DirSmem {
     float part[kColSplit][KMX_DESC_DIM];
@@ -354,9 +373,23 @@ __device__ void node_direction(const float* __restrict__ X, const int32_t* perm,
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int cpart = tid / KMX_DESC_DIM, ch = tid - cpart * KMX_DESC_DIM;
     __syncthreads();  // the caller's earlier use of xs and D is over
-    for (int idx = tid; idx < m * KMX_DESC_DIM; idx += kTreeThreads) {
-        const int i = idx / KMX_DESC_DIM, h = idx - i * KMX_DESC_DIM;
-        xs[i][h] = __ldg(X + (int64_t)perm[(int64_t)i * len / m] * KMX_DESC_STRIDE + h);
+    // one sampled row per thread: its index, then the row as nine
+    // independent loads (all in flight at once)
+    for (int i = tid; i < m; i += kTreeThreads) {
+        const float* x = X + (int64_t)perm[(int64_t)i * len / m] * KMX_DESC_STRIDE;
+        const float4* x4 = reinterpret_cast<const float4*>(x);
+        float4 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = __ldg(x4 + q);
+        const float last = __ldg(x + 32);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            xs[i][4 * q] = v[q].x;
+            xs[i][4 * q + 1] = v[q].y;
+            xs[i][4 * q + 2] = v[q].z;
+            xs[i][4 * q + 3] = v[q].w;
+        }
+        xs[i][32] = last;
     }
     __syncthreads();
     // centre
@@ -555,10 +588,7 @@ __global__ void __launch_bounds__(kTreeThreads) tree_finish(const float* __restr
             for (int i = tid; i < np2; i += kTreeThreads) {
                 float p = INFINITY;
                 if (i < cl) {
-                    const float* x = X + (int64_t)perm[cs + i] * KMX_DESC_STRIDE;
-                    p = 0.f;
-#pragma unroll
-                    for (int h = 0; h < KMX_DESC_DIM; ++h) p = fmaf(__ldg(x + h) - D.cvec[h], D.vvec[h], p);
+                    p = project(X + (int64_t)perm[cs + i] * KMX_DESC_STRIDE, D.cvec, D.vvec);
                     if (!(p <= INFINITY)) p = INFINITY;  // NaN: a total order for the network
                 }
                 pk[i] = p;
@@ -616,9 +646,7 @@ __global__ void __launch_bounds__(256) tree_key(const float* __restrict__ P, int
         if (len > kTM) {
             const float* d = dirs + (((int64_t)side << level) + k) * kDirStride;
             const float* x = (side ? Q : P) + (int64_t)vals[e] * KMX_DESC_STRIDE;
-            float p = 0.f;
-#pragma unroll
-            for (int h = 0; h < KMX_DESC_DIM; ++h) p = fmaf(__ldg(x + h) - d[h], d[KMX_DESC_DIM + h], p);
+            const float p = project(x, d, d + KMX_DESC_DIM);
             const float lo = d[2 * KMX_DESC_DIM], hi = d[2 * KMX_DESC_DIM + 1];
             const float t = hi > lo ? (p - lo) / (hi - lo) * qmax : 0.f;
             q = (uint32_t)fminf(fmaxf(t, 0.f), qmax) << (pbits - qbits);
@@ -1445,9 +1473,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_collect(const float* __restric
 // ---------------------------------------------------------------------------
 
 // Four sorted row positions per warp, eight lanes each (lane s takes
-// candidates s, s + 8, ...).  Rows whose list overflowed are flagged for the
-// exact fallback.  rows_out (source side) gets (d1, NN, d2) at the original
-// row; cols_best (target side) the packed (d1, NN).
+// candidates s, s + 8, ...).  Rows whose list overflowed are appended to the
+// exact fallback's list (in any order: each row's summary is its own).
+// rows_out (source side) gets (d1, NN, d2) at the original row; cols_best
+// (target side) the packed (d1, NN).
 __global__ void __launch_bounds__(256) tc_rerank(const float* __restrict__ X, const int32_t* __restrict__ permX,
                                                  int64_t nx_cap, const int64_t* d_nx, const float* __restrict__ Y,
                                                  const int32_t* __restrict__ permY, int64_t ny_cap,
@@ -1455,7 +1484,8 @@ __global__ void __launch_bounds__(256) tc_rerank(const float* __restrict__ X, co
                                                  const int32_t* __restrict__ cnt,
                                                  kmx::RowBest* __restrict__ rows_out,
                                                  unsigned long long* __restrict__ cols_best,
-                                                 int32_t* __restrict__ fallback, int* __restrict__ final_chunks)
+                                                 int32_t* __restrict__ fb_list, int64_t* __restrict__ fb_n,
+                                                 int* __restrict__ final_chunks)
 {
     const int lane = threadIdx.x & 31, s = lane & 7;
     const int64_t i = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 4 + (lane >> 3);
@@ -1513,27 +1543,17 @@ __global__ void __launch_bounds__(256) tc_rerank(const float* __restrict__ X, co
     }
     if (s != 0 || !active) return;
     if (c > kCandCap) {
-        fallback[orig] = 1;
+        fb_list[atomicAdd(reinterpret_cast<unsigned long long*>(fb_n), 1ull)] = orig;  // at most nx entries
         return;
     }
     if (rows_out) rows_out[orig] = kmx::RowBest{b1, j1, b2};
     if (cols_best && j1 != 0x7fffffff) cols_best[orig] = kmx::pack_dist_index(b1, (uint32_t)j1);
 }
 
-// Compact the flagged rows into a list (ascending) and publish its length.
-__global__ void __launch_bounds__(256) compact_flags(int64_t n_cap, const int64_t* d_n,
-                                                     const int32_t* __restrict__ flags,
-                                                     const int64_t* __restrict__ pos, int32_t* __restrict__ list,
-                                                     int64_t* __restrict__ n_list)
-{
-    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    if (i == 0) *n_list = pos[n_cap];
-    if (i >= kmx_count(d_n, n_cap)) return;
-    if (flags[i]) list[pos[i]] = (int32_t)i;
-}
-
 // Merge the exact fallback partials of each listed row (chunk c's partials
 // at part[c * list length ...]) and store them where the re-ranked rows went.
+// One warp per row: lane l merges chunks l, l + 32, ..., then the lanes
+// merge (the summary of a union does not depend on the merge order).
 __global__ void __launch_bounds__(256) fallback_merge(const kmx::RowBest* __restrict__ part,
                                                       const int* __restrict__ d_chunks, int64_t list_cap,
                                                       const int32_t* __restrict__ list,
@@ -1541,18 +1561,29 @@ __global__ void __launch_bounds__(256) fallback_merge(const kmx::RowBest* __rest
                                                       kmx::RowBest* __restrict__ rows_out,
                                                       unsigned long long* __restrict__ cols_best)
 {
-    const int64_t r = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const int lane = threadIdx.x & 31;
     const int64_t n = min(*n_list, list_cap);
-    if (r >= n) return;
-    kmx::RowBest b = part[r];
     const int chunks = *d_chunks;
-    for (int c = 1; c < chunks; ++c) {
-        const kmx::RowBest o = part[(int64_t)c * n + r];
-        kmx::row_merge(b.d1, b.j1, b.d2, o.d1, o.j1, o.d2);
+    const int64_t warps = (int64_t)gridDim.x * 8;
+    for (int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); r < n; r += warps) {
+        float d1 = INFINITY, d2 = INFINITY;
+        int j1 = 0x7fffffff;
+        for (int c = lane; c < chunks; c += 32) {
+            const kmx::RowBest o = part[(int64_t)c * n + r];
+            kmx::row_merge(d1, j1, d2, o.d1, o.j1, o.d2);
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            const float od1 = __shfl_xor_sync(0xffffffffu, d1, o);
+            const int oj = __shfl_xor_sync(0xffffffffu, j1, o);
+            const float od2 = __shfl_xor_sync(0xffffffffu, d2, o);
+            kmx::row_merge(d1, j1, d2, od1, oj, od2);
+        }
+        if (lane != 0) continue;
+        const int i = list[r];
+        if (rows_out) rows_out[i] = kmx::RowBest{d1, j1, d2};
+        if (cols_best && j1 != 0x7fffffff) cols_best[i] = kmx::pack_dist_index(d1, (uint32_t)j1);
     }
-    const int i = list[r];
-    if (rows_out) rows_out[i] = b;
-    if (cols_best && b.j1 != 0x7fffffff) cols_best[i] = kmx::pack_dist_index(b.d1, (uint32_t)b.j1);
 }
 
 size_t tc_smem_bytes()
@@ -1578,8 +1609,8 @@ struct TcBuffers {
     int* nitems;               // [0] source rows, [1] target rows
     int32_t *candP, *candQ, *cntP, *cntQ;
     int* chunks;               // [2] fallback P, [3] fallback Q
-    int32_t *flagP, *flagQ, *listP, *listQ;
-    int64_t *posP, *posQ, *nlist;  // nlist[0] P, [1] Q
+    int32_t *listP, *listQ;    // fallback rows (original indices)
+    int64_t* nlist;            // their counts: [0] P, [1] Q
     kmx::RowBest *fbP, *fbQ;
 };
 
@@ -1623,12 +1654,8 @@ TcBuffers tc_carve(void* base, int64_t np_cap, int64_t nq_cap, size_t* total)
     b.cntP = (int32_t*)a.take(sizeof(int32_t) * (size_t)(np_cap + nq_cap));
     b.cntQ = b.cntP + np_cap;
     b.chunks = (int*)a.take(sizeof(int) * 4);
-    b.flagP = (int32_t*)a.take(sizeof(int32_t) * (np_cap + 1));
-    b.flagQ = (int32_t*)a.take(sizeof(int32_t) * (nq_cap + 1));
     b.listP = (int32_t*)a.take(sizeof(int32_t) * (np_cap + 1));
     b.listQ = (int32_t*)a.take(sizeof(int32_t) * (nq_cap + 1));
-    b.posP = (int64_t*)a.take(sizeof(int64_t) * (np_cap + 1));
-    b.posQ = (int64_t*)a.take(sizeof(int64_t) * (nq_cap + 1));
     b.nlist = (int64_t*)a.take(sizeof(int64_t) * 2);
     b.fbP = (kmx::RowBest*)a.take(sizeof(kmx::RowBest) * (size_t)fc * (np_cap + 1));
     b.fbQ = (kmx::RowBest*)a.take(sizeof(kmx::RowBest) * (size_t)fc * (nq_cap + 1));
@@ -1665,8 +1692,7 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
         return cudaFuncSetAttribute(tree_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFinishSmem);
     });
     if (e) return e;
-    if ((e = cudaMemsetAsync(b.flagP, 0, sizeof(int32_t) * (np_cap + 1), st))) return e;
-    if ((e = cudaMemsetAsync(b.flagQ, 0, sizeof(int32_t) * (nq_cap + 1), st))) return e;
+    if ((e = cudaMemsetAsync(b.nlist, 0, sizeof(int64_t) * 2, st))) return e;
     if ((e = cudaMemsetAsync(b.cntP, 0, sizeof(int32_t) * (size_t)n2, st))) return e;
     if ((e = cudaMemsetAsync(b.nitems, 0, sizeof(int) * 2, st))) return e;
     // locality order of both clouds: one tree level per sort
@@ -1720,18 +1746,12 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
     // exact re-ranking; overflowed rows are flagged
     KMX_COUNT_LAUNCH();
     tc_rerank<<<kmx_blocks(np_cap, 32), 256, 0, st>>>(dp, permP, np_cap, d_np, dq, permQ, nq_cap, d_nq, b.candP,
-                                                     b.cntP, s.part, nullptr, b.flagP, s.chunks);
+                                                     b.cntP, s.part, nullptr, b.listP, b.nlist + 0, s.chunks);
     KMX_COUNT_LAUNCH();
     tc_rerank<<<kmx_blocks(nq_cap, 32), 256, 0, st>>>(dq, permQ, nq_cap, d_nq, dp, permP, np_cap, d_np, b.candQ,
-                                                     b.cntQ, nullptr, s.colbest, b.flagQ, nullptr);
+                                                     b.cntQ, nullptr, s.colbest, b.listQ, b.nlist + 1, nullptr);
     if ((e = cudaGetLastError())) return e;
     // exact fallback for the flagged rows of each side
-    if ((e = kmx_scan_i32(ctx, b.flagP, np_cap, d_np, b.posP))) return e;
-    KMX_COUNT_LAUNCH();
-    compact_flags<<<kmx_blocks(np_cap, 256), 256, 0, st>>>(np_cap, d_np, b.flagP, b.posP, b.listP, b.nlist + 0);
-    if ((e = kmx_scan_i32(ctx, b.flagQ, nq_cap, d_nq, b.posQ))) return e;
-    KMX_COUNT_LAUNCH();
-    compact_flags<<<kmx_blocks(nq_cap, 256), 256, 0, st>>>(nq_cap, d_nq, b.flagQ, b.posQ, b.listQ, b.nlist + 1);
     if ((e = kmx_match_fp32_rows_launch(ctx, dp, b.listP, np_cap, b.nlist + 0, dq, nq_cap, d_nq, b.fbP,
                                         b.chunks + 2)))
         return e;
@@ -1739,11 +1759,12 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
                                         b.chunks + 3)))
         return e;
     KMX_COUNT_LAUNCH();
-    fallback_merge<<<kmx_blocks(np_cap, 256), 256, 0, st>>>(b.fbP, b.chunks + 2, np_cap, b.listP, b.nlist + 0, s.part,
-                                                            nullptr);
+    fallback_merge<<<kmx_stride_blocks(np_cap, 8, ctx->sm_count), 256, 0, st>>>(b.fbP, b.chunks + 2, np_cap,
+                                                                                b.listP, b.nlist + 0, s.part, nullptr);
     KMX_COUNT_LAUNCH();
-    fallback_merge<<<kmx_blocks(nq_cap, 256), 256, 0, st>>>(b.fbQ, b.chunks + 3, nq_cap, b.listQ, b.nlist + 1,
-                                                            nullptr, s.colbest);
+    fallback_merge<<<kmx_stride_blocks(nq_cap, 8, ctx->sm_count), 256, 0, st>>>(b.fbQ, b.chunks + 3, nq_cap,
+                                                                                b.listQ, b.nlist + 1, nullptr,
+                                                                                s.colbest);
     return cudaGetLastError();
 }
 

@@ -650,6 +650,23 @@ def test_match_bf16_duplicates_overflow_to_exact(torch_cuda, ctx):
     assert diag[0] >= 51, "the 51 rows equal to the duplicated descriptor overflow: %s" % diag
 
 
+@pytest.mark.parametrize("overflow_rows", [64, 65, 201])
+def test_match_bf16_overflow_row_counts(torch_cuda, ctx, overflow_rows):
+    """overflow_rows source rows equal one descriptor that 600 target rows
+    copy: all of them overflow.  Up to 64 listed rows the fallback streams
+    each row over column chunks, above that it runs the tiled kernel; both
+    sides of the switch give the exact path's bytes."""
+    rng = np.random.default_rng(29)
+    FP = rng.gamma(0.5, 20.0, (900, 33)).astype(np.float32)
+    FQ = rng.gamma(0.5, 20.0, (3000, 33)).astype(np.float32)
+    FQ[100:700] = FP[5]
+    FP[600:600 + overflow_rows - 1] = FP[5]
+    n = _same_as_exact(torch_cuda, ctx, FP, FQ)
+    assert n > 0
+    diag = ctx.match_diag(len(FP), len(FQ)).cpu().numpy()
+    assert diag[0] >= overflow_rows, "overflowed rows: %s" % diag
+
+
 def test_match_bf16_one_overflow_row_many_columns(torch_cuda, ctx):
     """One source row ties with 700 target rows: its list overflows and the
     exact fallback spreads that single row over hundreds of column chunks
