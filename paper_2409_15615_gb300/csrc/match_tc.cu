@@ -248,9 +248,13 @@ __device__ __forceinline__ void store_operand_row(uint8_t* tile, int r, const fl
 constexpr int kTreeSample = 256;  // rows sampled per node for its direction
 constexpr int kTreeIters = 2;     // power iterations
 constexpr int kTreeThreads = 256;
-constexpr int kColSplit = 7;      // partial sums per column in the sample reductions (7 x 33 <= 256)
 constexpr int kDirStride = 68;    // floats per node: centre (33), direction (33), projection range (2)
 constexpr size_t kTreeSmem = sizeof(float) * kTreeSample * KMX_DESC_DIM;
+// Rows of a node tree_local splits in one CTA.  Its gathers of the node's
+// descriptor rows run on one SM, so a larger node is faster on the global
+// kernels, which spread a level over the whole GPU (on the 2M-point indoor
+// pair, 16384 beat 8192, 4096 and 65536).
+constexpr int kLocalRows = 16384;
 constexpr int kFinishLevels = 4;                         // levels below a node of 16 tiles
 constexpr int kFinishRows = kTM << kFinishLevels;        // 2048
 constexpr size_t kFinishSmem = kTreeSmem + sizeof(int32_t) * 3 * kFinishRows;
@@ -308,6 +312,14 @@ __device__ __forceinline__ int64_t tree_node_of(int64_t n, int l, int64_t pos, i
     return k;
 }
 
+// Largest node of level l over a side of n rows (the leftmost: a left
+// child is never smaller than its sibling).
+__host__ __device__ __forceinline__ int64_t level_max(int64_t n, int l)
+{
+    for (int b = 0; b < l; ++b) n = tree_left(n);
+    return n;
+}
+
 // The tree works on both clouds' rows packed together: entry e < np is
 // source row e, entry np + i target row i (np, nq the device counts).  They
 // start as the identity, and *n2 = np + nq.
@@ -351,13 +363,23 @@ __device__ __forceinline__ float project(const float* __restrict__ x, const floa
     return fmaf(__ldg(x + 32) - c[32], v[32], p);
 }
 
-// Shared memory of one node's direction (besides the sampled rows).
+// Partial sums per column in the sample reductions of a CTA of NT threads
+// (7 x 33 <= 256, 31 x 33 <= 1024).
+template <int NT>
+__host__ __device__ constexpr int col_split()
+{
+    return NT / KMX_DESC_DIM;
+}
+
+// Shared memory of one node's direction (besides the sampled rows), for a
+// CTA of NT threads.
+template <int NT>
 struct DirSmem {
-    float part[kColSplit][KMX_DESC_DIM];
+    float part[col_split<NT>()][KMX_DESC_DIM];
     float cvec[KMX_DESC_DIM], vvec[KMX_DESC_DIM], uvec[KMX_DESC_DIM];
     float w[kTreeSample];
-    float redf[2][kTreeThreads / 32];
-    int redi[kTreeThreads / 32];
+    float redf[2][NT / 32];
+    int redi[NT / 32];
     float scale;
     int far;
 };
@@ -365,17 +387,20 @@ struct DirSmem {
 // Centre (D.cvec) and principal direction (D.vvec) of a node of `len` rows
 // whose rows are X[perm[0 .. len)], from up to kTreeSample of them (evenly
 // spaced in the current order) held centred in xs; lo / hi (thread 0) get
-// the range of the sample's projections.  Every thread of the CTA calls it.
+// the range of the sample's projections.  Every thread of the CTA (NT
+// threads) calls it.
+template <int NT>
 __device__ void node_direction(const float* __restrict__ X, const int32_t* perm, int64_t len,
-                               float (*xs)[KMX_DESC_DIM], DirSmem& D, float& lo, float& hi)
+                               float (*xs)[KMX_DESC_DIM], DirSmem<NT>& D, float& lo, float& hi)
 {
+    constexpr int kColSplit = col_split<NT>();
     const int m = (int)min(len, (int64_t)kTreeSample);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int cpart = tid / KMX_DESC_DIM, ch = tid - cpart * KMX_DESC_DIM;
     __syncthreads();  // the caller's earlier use of xs and D is over
     // one sampled row per thread: its index, then the row as nine
     // independent loads (all in flight at once)
-    for (int i = tid; i < m; i += kTreeThreads) {
+    for (int i = tid; i < m; i += NT) {
         const float* x = X + (int64_t)perm[(int64_t)i * len / m] * KMX_DESC_STRIDE;
         const float4* x4 = reinterpret_cast<const float4*>(x);
         float4 v[8];
@@ -406,7 +431,7 @@ __device__ void node_direction(const float* __restrict__ X, const int32_t* perm,
         D.cvec[tid] = acc / (float)m;
     }
     __syncthreads();
-    for (int idx = tid; idx < m * KMX_DESC_DIM; idx += kTreeThreads) {
+    for (int idx = tid; idx < m * KMX_DESC_DIM; idx += NT) {
         const int i = idx / KMX_DESC_DIM, h = idx - i * KMX_DESC_DIM;
         xs[i][h] -= D.cvec[h];
     }
@@ -415,7 +440,7 @@ __device__ void node_direction(const float* __restrict__ X, const int32_t* perm,
     {
         float best = -1.f;
         int bi = 0;
-        for (int i = tid; i < m; i += kTreeThreads) {
+        for (int i = tid; i < m; i += NT) {
             float acc = 0.f;
 #pragma unroll
             for (int h = 0; h < KMX_DESC_DIM; ++h) acc = fmaf(xs[i][h], xs[i][h], acc);
@@ -441,7 +466,7 @@ __device__ void node_direction(const float* __restrict__ X, const int32_t* perm,
         if (tid == 0) {
             float b = D.redf[0][0];
             int i0 = D.redi[0];
-            for (int q = 1; q < kTreeThreads / 32; ++q)
+            for (int q = 1; q < NT / 32; ++q)
                 if (D.redf[0][q] > b || (D.redf[0][q] == b && D.redi[q] < i0)) {
                     b = D.redf[0][q];
                     i0 = D.redi[q];
@@ -463,7 +488,7 @@ __device__ void node_direction(const float* __restrict__ X, const int32_t* perm,
         if (tid < KMX_DESC_DIM) D.vvec[tid] = D.scale > 0.f ? D.uvec[tid] * D.scale : (tid == 0 ? 1.f : 0.f);
         __syncthreads();
         if (it == kTreeIters) break;
-        for (int i = tid; i < m; i += kTreeThreads) {
+        for (int i = tid; i < m; i += NT) {
             float acc = 0.f;
 #pragma unroll
             for (int h = 0; h < KMX_DESC_DIM; ++h) acc = fmaf(xs[i][h], D.vvec[h], acc);
@@ -486,7 +511,7 @@ __device__ void node_direction(const float* __restrict__ X, const int32_t* perm,
     // range of the sample's projections
     lo = INFINITY;
     hi = -INFINITY;
-    for (int i = tid; i < m; i += kTreeThreads) {
+    for (int i = tid; i < m; i += NT) {
         float acc = 0.f;
 #pragma unroll
         for (int h = 0; h < KMX_DESC_DIM; ++h) acc = fmaf(xs[i][h], D.vvec[h], acc);
@@ -504,7 +529,7 @@ __device__ void node_direction(const float* __restrict__ X, const int32_t* perm,
     }
     __syncthreads();
     if (tid == 0)
-        for (int q = 1; q < kTreeThreads / 32; ++q) {
+        for (int q = 1; q < NT / 32; ++q) {
             lo = fminf(lo, D.redf[0][q]);
             hi = fmaxf(hi, D.redf[1][q]);
         }
@@ -520,10 +545,12 @@ __global__ void __launch_bounds__(kTreeThreads) tree_dir(const float* __restrict
 {
     extern __shared__ float tree_smem[];
     float(*xs)[KMX_DESC_DIM] = reinterpret_cast<float(*)[KMX_DESC_DIM]>(tree_smem);
-    __shared__ DirSmem D;
+    __shared__ DirSmem<kTreeThreads> D;
     const int side = blockIdx.y;
     const int64_t k = blockIdx.x;
-    const int64_t n = side ? kmx_count(d_nq, nq_cap) : kmx_count(d_np, np_cap);
+    const int64_t np = kmx_count(d_np, np_cap), nq = kmx_count(d_nq, nq_cap);
+    if (level_max(np > nq ? np : nq, level) <= kLocalRows) return;  // tree_local takes this level
+    const int64_t n = side ? nq : np;
     int64_t start, len;
     tree_node(n, level, k, start, len);
     if (len <= kTM) return;
@@ -545,27 +572,34 @@ __global__ void __launch_bounds__(kTreeThreads) tree_dir(const float* __restrict
 // kFinishRows rows): one CTA per (level-0 node, side) splits its subtree
 // level by level in shared memory.  Per node: its direction, the projections
 // of all its rows, a bitonic sort by (projection, position), and the rows
-// in that order; the next level splits the node where tree_left says.
+// in that order; the next level splits the node where tree_left says.  The
+// entries are read from src and written to vals (src may be vals).
 __global__ void __launch_bounds__(kTreeThreads) tree_finish(const float* __restrict__ P, int64_t np_cap,
                                                             const int64_t* d_np, const float* __restrict__ Q,
                                                             int64_t nq_cap, const int64_t* d_nq,
-                                                            int32_t* __restrict__ vals, int level0, int levels)
+                                                            const int32_t* src, int32_t* vals, int level0,
+                                                            int levels)
 {
     extern __shared__ float tree_smem[];
     float(*xs)[KMX_DESC_DIM] = reinterpret_cast<float(*)[KMX_DESC_DIM]>(tree_smem);
     int32_t* perm = reinterpret_cast<int32_t*>(tree_smem + kTreeSample * KMX_DESC_DIM);  // [kFinishRows]
     float* pk = reinterpret_cast<float*>(perm + kFinishRows);                             // [kFinishRows]
     int32_t* pi = reinterpret_cast<int32_t*>(pk + kFinishRows);                           // [kFinishRows]
-    __shared__ DirSmem D;
+    __shared__ DirSmem<kTreeThreads> D;
     const int side = blockIdx.y;
     const int tid = threadIdx.x;
     const int64_t n = side ? kmx_count(d_nq, nq_cap) : kmx_count(d_np, np_cap);
     int64_t start, len;
     tree_node(n, level0, blockIdx.x, start, len);
-    if (len <= kTM) return;
     const float* X = side ? Q : P;
+    const int32_t* gs = src + (side ? kmx_count(d_np, np_cap) : 0) + start;
     int32_t* gv = vals + (side ? kmx_count(d_np, np_cap) : 0) + start;
-    for (int i = tid; i < len; i += kTreeThreads) perm[i] = gv[i];
+    if (len <= kTM) {  // a leaf: only the copy from src, if src is another array
+        if (gs != gv)
+            for (int i = tid; i < len; i += kTreeThreads) gv[i] = gs[i];
+        return;
+    }
+    for (int i = tid; i < len; i += kTreeThreads) perm[i] = gs[i];
     for (int l = level0; l < levels; ++l) {
         const int sub = l - level0;
         for (int c = 0; c < (1 << sub); ++c) {
@@ -625,15 +659,204 @@ __global__ void __launch_bounds__(kTreeThreads) tree_finish(const float* __restr
     for (int i = tid; i < len; i += kTreeThreads) gv[i] = perm[i];
 }
 
+// One tree level for nodes that fit in shared memory (at most kLocalRows
+// rows), one CTA of NT threads per (node, side), in one launch instead of
+// the direction, key and radix-sort launches of a global level.  The split
+// is the global levels' split: the first tree_left(len) rows in the order of
+// (16-bit key, position), the key being the projection on the node's
+// direction quantised over the sample's range.  That set is found without a
+// sort: two 256-bin histograms give the key T of the split row and how many
+// rows with key T go left; then a stable partition writes the left rows,
+// then the right rows, each in their current order, from src to dst.  Leaves
+// are copied, and so is every node of a level that the global kernels
+// ordered (some node of the level larger than kLocalRows on the device).
+constexpr size_t kLocalSmemBase = kTreeSmem;  // the sampled rows; the 16-bit keys follow
+constexpr int kLocalWideCtas = 304;           // from this many CTAs per level, CTAs of 256 threads (4 per SM)
+
+size_t local_smem_bytes(int64_t max_rows)
+{
+    return kLocalSmemBase + sizeof(uint16_t) * (size_t)((max_rows + 7) / 8 * 8);
+}
+
+// Smallest bin b with before + (hist[0] + ... + hist[b]) >= target, and the
+// count before it (bins in order), by warp 0 of the CTA; the result in
+// *bin / *below.
+__device__ __forceinline__ void select_bin(const int* hist, int before, int target, int* bin, int* below)
+{
+    const int lane = threadIdx.x & 31;
+    int c[8], sum = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        c[q] = hist[lane * 8 + q];
+        sum += c[q];
+    }
+    int incl = sum;  // inclusive prefix over lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    int run = before + incl - sum;
+    int found = -1, fb = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        if (found < 0 && run + c[q] >= target) {
+            found = lane * 8 + q;
+            fb = run;
+        }
+        run += c[q];
+    }
+    const unsigned hit = __ballot_sync(0xffffffffu, found >= 0);
+    const int src = hit ? __ffs(hit) - 1 : 31;
+    found = __shfl_sync(0xffffffffu, found, src);
+    fb = __shfl_sync(0xffffffffu, fb, src);
+    if (lane == 0) {
+        *bin = found < 0 ? 255 : found;
+        *below = fb;
+    }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) tree_local(const float* __restrict__ P, int64_t np_cap,
+                                                           const int64_t* d_np, const float* __restrict__ Q,
+                                                           int64_t nq_cap, const int64_t* d_nq,
+                                                           const int32_t* __restrict__ src,
+                                                           int32_t* __restrict__ dst, int level, unsigned int* err)
+{
+    constexpr int kWarpsL = NT / 32;
+    extern __shared__ float tree_smem[];
+    float(*xs)[KMX_DESC_DIM] = reinterpret_cast<float(*)[KMX_DESC_DIM]>(tree_smem);
+    uint16_t* key = reinterpret_cast<uint16_t*>(tree_smem + kTreeSample * KMX_DESC_DIM);
+    __shared__ DirSmem<NT> D;
+    __shared__ int hist[256];
+    __shared__ int wsum[kWarpsL];
+    __shared__ int sel[4];   // B1, below B1, T, rows of key T that go left
+    __shared__ float range[2];
+    const int side = blockIdx.y;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t np = kmx_count(d_np, np_cap), nq = kmx_count(d_nq, nq_cap);
+    const int64_t n = side ? nq : np;
+    int64_t start, len64;
+    tree_node(n, level, blockIdx.x, start, len64);
+    const int32_t* gs = src + (side ? np : 0) + start;
+    int32_t* gd = dst + (side ? np : 0) + start;
+    const bool ordered = level_max(np > nq ? np : nq, level) > kLocalRows;  // by the global kernels
+    if (len64 <= kTM || ordered || len64 > kLocalRows) {
+        if (!ordered && len64 > kLocalRows && tid == 0) kmx_raise(err, KMX_DERR_CAPACITY);  // cannot occur
+        for (int64_t i = tid; i < len64; i += NT) gd[i] = gs[i];
+        return;
+    }
+    const int len = (int)len64;
+    const int h = (int)tree_left(len64);  // 0 < h < len
+    const float* X = side ? Q : P;
+    float lo, hi;
+    node_direction(X, gs, len64, xs, D, lo, hi);
+    if (tid == 0) {
+        range[0] = lo;
+        range[1] = hi;
+    }
+    if (tid < 256) hist[tid] = 0;
+    __syncthreads();
+    lo = range[0];
+    hi = range[1];
+    const float qs = hi > lo ? 65535.f / (hi - lo) : 0.f;
+    // keys and the histogram of their high bytes
+    // (one shared atomic per distinct bin and warp: keys cluster, and equal
+    // bins within a warp would otherwise serialise)
+    for (int base = 0; base < len; base += NT) {
+        const int i = base + tid;
+        int bin = -1;
+        if (i < len) {
+            const float p = project(X + (int64_t)gs[i] * KMX_DESC_STRIDE, D.cvec, D.vvec);
+            const float t = fminf(fmaxf((p - lo) * qs, 0.f), 65535.f);  // NaN -> 0
+            const uint16_t k = (uint16_t)t;
+            key[i] = k;
+            bin = k >> 8;
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, bin);
+        if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
+    }
+    __syncthreads();
+    if (warp == 0) select_bin(hist, 0, h, &sel[0], &sel[1]);
+    __syncthreads();
+    const int b1 = sel[0], below1 = sel[1];
+    if (tid < 256) hist[tid] = 0;
+    __syncthreads();
+    for (int base = 0; base < len; base += NT) {
+        const int i = base + tid;
+        int bin = -1;
+        if (i < len) {
+            const uint16_t k = key[i];
+            if ((k >> 8) == b1) bin = k & 0xff;
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, bin);
+        if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int b2, below2;
+        select_bin(hist, below1, h, &b2, &below2);
+        if (lane == 0) {
+            sel[2] = (b1 << 8) | b2;
+            sel[3] = h - below2;
+        }
+    }
+    __syncthreads();
+    const int T = sel[2], need = sel[3];
+    // stable partition in rounds of NT rows: per round, the
+    // counts of key < T (low half of a word) and key == T (high half) before
+    // each row
+    int run_l = 0, run_e = 0;  // over earlier rounds (uniform)
+    for (int base = 0; base < len; base += NT) {
+        const int i = base + tid;
+        const bool valid = i < len;
+        const int k = valid ? (int)key[i] : 0x10000;
+        const bool isl = valid && k < T, ise = valid && k == T;
+        const unsigned bl = __ballot_sync(0xffffffffu, isl), be = __ballot_sync(0xffffffffu, ise);
+        const unsigned lt = (1u << lane) - 1u;
+        if (lane == 0) wsum[warp] = __popc(bl) | (__popc(be) << 16);
+        __syncthreads();
+        int pre = 0, tot = 0;
+#pragma unroll 8
+        for (int w = 0; w < kWarpsL; ++w) {
+            const int v = wsum[w];
+            pre += w < warp ? v : 0;
+            tot += v;
+        }
+        const int nl = run_l + (pre & 0xffff) + __popc(bl & lt);  // key < T before row i
+        const int ne = run_e + (pre >> 16) + __popc(be & lt);     // key == T before row i
+        if (valid) {
+            const int left_before = nl + min(ne, need);
+            const bool left = isl || (ise && ne < need);
+            const int pos = left ? left_before : h + (i - left_before);
+            if (pos < len) {  // always (the counts add up to h left rows); checked, not assumed
+                gd[pos] = gs[i];
+            } else {
+                kmx_raise(err, KMX_DERR_CAPACITY);
+            }
+        }
+        run_l += tot & 0xffff;
+        run_e += tot >> 16;
+        __syncthreads();  // wsum is rewritten by the next round
+    }
+}
+
 // Sort key of every packed entry for this level: side (top bit), node index
 // (level bits), then the row's projection on its node's direction,
-// quantised over the sample's range (0 in a leaf).
+// quantised over the sample's range (0 in a leaf).  *n_sort gets the count
+// the radix sort takes (0 when tree_local takes the level).
 __global__ void __launch_bounds__(256) tree_key(const float* __restrict__ P, int64_t np_cap, const int64_t* d_np,
                                                 const float* __restrict__ Q, int64_t nq_cap, const int64_t* d_nq,
                                                 const int32_t* __restrict__ vals, int level, int key_bits,
-                                                const float* __restrict__ dirs, uint32_t* __restrict__ keys)
+                                                const float* __restrict__ dirs, uint32_t* __restrict__ keys,
+                                                int64_t* __restrict__ n_sort)
 {
     const int64_t np = kmx_count(d_np, np_cap), nq = kmx_count(d_nq, nq_cap);
+    // the entries this level's radix sort orders: all of them, or none when
+    // every node fits tree_local
+    const bool global = level_max(np > nq ? np : nq, level) > kLocalRows;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *n_sort = global ? np + nq : 0;
+    if (!global) return;
     const int pbits = key_bits - 1 - level;
     const int qbits = pbits < 22 ? pbits : 22;
     const float qmax = (float)((1u << qbits) - 1u);
@@ -1599,6 +1822,7 @@ struct TcBuffers {
     int32_t *vals, *vals_tmp;  // the tree's packed entries (source rows, then target rows)
     int32_t* perm;             // sorted: [0, np) source rows, [np_cap, np_cap + nq) target rows
     int64_t* n2;               // np + nq on the device
+    int64_t* nsort;            // the entries a global level's radix sort takes (np + nq or 0)
     void* sort_scratch;
     float* dirs;               // [2 << (levels - 1)][kDirStride]
     uint8_t *packP, *packQ;
@@ -1634,6 +1858,7 @@ TcBuffers tc_carve(void* base, int64_t np_cap, int64_t nq_cap, size_t* total)
     b.vals_tmp = (int32_t*)a.take(sizeof(int32_t) * (size_t)n2);
     b.perm = (int32_t*)a.take(sizeof(int32_t) * (size_t)n2);
     b.n2 = (int64_t*)a.take(sizeof(int64_t));
+    b.nsort = (int64_t*)a.take(sizeof(int64_t));
     b.sort_scratch = a.take(kmx_sort_scratch_bytes(n2));
     b.dirs = (float*)a.take(sizeof(float) * kDirStride * ((size_t)2 << (levels > 0 ? levels - 1 : 0)));
     b.packP = (uint8_t*)a.take((size_t)tp * kColBytes);
@@ -1689,6 +1914,12 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
         if (r) return r;
         r = cudaFuncSetAttribute(tree_dir, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTreeSmem);
         if (r) return r;
+        r = cudaFuncSetAttribute(tree_local<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)local_smem_bytes(kLocalRows));
+        if (r) return r;
+        r = cudaFuncSetAttribute(tree_local<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)local_smem_bytes(kLocalRows));
+        if (r) return r;
         return cudaFuncSetAttribute(tree_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFinishSmem);
     });
     if (e) return e;
@@ -1700,23 +1931,43 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
     KMX_COUNT_LAUNCH();
     tree_init<<<gb, 256, 0, st>>>(np_cap, d_np, nq_cap, d_nq, b.vals, b.n2);
     const int level0 = levels > kFinishLevels ? levels - kFinishLevels : 0;
-    for (int l = 0; l < level0; ++l) {
+    // Levels whose nodes can exceed kLocalRows at the capacities run the
+    // global kernels (direction, keys, radix sort), which do nothing on the
+    // device once every node fits; tree_local then splits the level (or,
+    // after the global kernels, copies it).  The entries alternate between
+    // vals and vals_tmp.
+    int64_t node_max = np_cap > nq_cap ? np_cap : nq_cap;  // largest node of level l at any device count
+    int32_t* cur = b.vals;                                  // the entries as the last level left them
+    for (int l = 0; l < level0; ++l, node_max = tree_left(node_max)) {
+        int32_t* next = cur == b.vals ? b.vals_tmp : b.vals;
+        if (node_max > kLocalRows) {
+            KMX_COUNT_LAUNCH();
+            tree_dir<<<dim3(1u << l, 2), kTreeThreads, kTreeSmem, st>>>(dp, np_cap, d_np, dq, nq_cap, d_nq, cur, l,
+                                                                         b.dirs);
+            KMX_COUNT_LAUNCH();
+            // 16-bit keys (two radix passes) while they leave at least 9 bits
+            // of projection (levels 0..6), wider keys below
+            const int kb = l <= 6 ? 16 : key_bits;
+            tree_key<<<gb, 256, 0, st>>>(dp, np_cap, d_np, dq, nq_cap, d_nq, cur, l, kb, b.dirs, b.keys, b.nsort);
+            if ((e = cudaGetLastError())) return e;
+            if ((e = kmx_sort_u32(ctx, b.keys, cur, b.keys_tmp, next, n2, b.nsort, kb, b.sort_scratch))) return e;
+        }
+        const int64_t rows = node_max < kLocalRows ? node_max : kLocalRows;
         KMX_COUNT_LAUNCH();
-        tree_dir<<<dim3(1u << l, 2), kTreeThreads, kTreeSmem, st>>>(dp, np_cap, d_np, dq, nq_cap, d_nq, b.vals, l,
-                                                                     b.dirs);
-        KMX_COUNT_LAUNCH();
-        // 16-bit keys (two radix passes) while they leave at least 9 bits of
-        // projection (levels 0..6), wider keys below
-        const int kb = l <= 6 ? 16 : key_bits;
-        tree_key<<<gb, 256, 0, st>>>(dp, np_cap, d_np, dq, nq_cap, d_nq, b.vals, l, kb, b.dirs, b.keys);
+        if ((int64_t{2} << l) >= kLocalWideCtas) {
+            tree_local<256><<<dim3(1u << l, 2), 256, local_smem_bytes(rows), st>>>(dp, np_cap, d_np, dq, nq_cap,
+                                                                                  d_nq, cur, next, l, ctx->d_err);
+        } else {
+            tree_local<1024><<<dim3(1u << l, 2), 1024, local_smem_bytes(rows), st>>>(dp, np_cap, d_np, dq, nq_cap,
+                                                                                    d_nq, cur, next, l, ctx->d_err);
+        }
         if ((e = cudaGetLastError())) return e;
-        if ((e = kmx_sort_u32(ctx, b.keys, b.vals, b.keys_tmp, b.vals_tmp, n2, b.n2, kb, b.sort_scratch)))
-            return e;
+        cur = next;
     }
     if (levels > 0) {  // the subtrees of at most 16 tiles, one CTA each
         KMX_COUNT_LAUNCH();
         tree_finish<<<dim3(1u << level0, 2), kTreeThreads, kFinishSmem, st>>>(dp, np_cap, d_np, dq, nq_cap, d_nq,
-                                                                             b.vals, level0, levels);
+                                                                             cur, b.vals, level0, levels);
         if ((e = cudaGetLastError())) return e;
     }
     KMX_COUNT_LAUNCH();

@@ -46,10 +46,15 @@ __global__ void __launch_bounds__(kThreads) radix_count(const uint32_t* __restri
     hist[threadIdx.x] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kPerBlock;
+    // one shared atomic per distinct digit and warp: the digits of a block
+    // often coincide (sorted prefixes), and equal addresses serialise
+    const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
         const int64_t e = base + k * kThreads + threadIdx.x;
-        if (e < n) atomicAdd(&hist[(keys[e] >> shift) & 0xFFu], 1);
+        const int d = e < n ? (int)((keys[e] >> shift) & 0xFFu) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (d >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[d], __popc(peers));
     }
     __syncthreads();
     counts[(int64_t)threadIdx.x * blocks + blockIdx.x] = hist[threadIdx.x];
