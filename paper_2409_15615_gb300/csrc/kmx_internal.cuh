@@ -193,12 +193,14 @@ cudaError_t kmx_scan_reserve(kmx_ctx* ctx, int64_t words);
 // sort.cu: stable LSD radix sort of the first min(*d_n, n) (key, value)
 // pairs (all n when d_n is null) by the low `bits` bits of the key (8 per
 // pass, rounded up), on the context stream; the result is in (keys, vals),
-// and entries past the count are left alone.  scratch:
+// or, with vals_out, the values are in vals_out (distinct from vals and
+// vals_tmp; vals is then left unchanged and the keys end in either keys
+// array).  Entries past the count are left alone.  scratch:
 // kmx_sort_scratch_bytes(n).  Its scans use the context's look-back area
 // (grown on first use of a size).
 size_t kmx_sort_scratch_bytes(int64_t n);
 cudaError_t kmx_sort_u32(kmx_ctx* ctx, uint32_t* keys, int32_t* vals, uint32_t* keys_tmp, int32_t* vals_tmp,
-                         int64_t n, const int64_t* d_n, int bits, void* scratch);
+                         int64_t n, const int64_t* d_n, int bits, void* scratch, int32_t* vals_out = nullptr);
 
 // voxel.cu
 size_t kmx_voxelize_scratch_bytes(int64_t n_raw);

@@ -257,7 +257,10 @@ constexpr size_t kTreeSmem = sizeof(float) * kTreeSample * KMX_DESC_DIM;
 constexpr int kLocalRows = 16384;
 constexpr int kFinishLevels = 4;                         // levels below a node of 16 tiles
 constexpr int kFinishRows = kTM << kFinishLevels;        // 2048
-constexpr size_t kFinishSmem = kTreeSmem + sizeof(int32_t) * 3 * kFinishRows;
+constexpr int kFinishSample = 128;                       // rows sampled per node below level0 (at most 2048 rows)
+// sampled rows, entries, partition buffer, 16-bit keys
+constexpr size_t kFinishSmem = sizeof(float) * kFinishSample * KMX_DESC_DIM + sizeof(int32_t) * 2 * kFinishRows +
+                               sizeof(uint16_t) * kFinishRows;
 
 // Rows of the left child of a node of `len` rows: a whole number of tiles,
 // ceil(len / 256) * 128; a node of at most 128 rows is a leaf (its left
@@ -372,12 +375,12 @@ __host__ __device__ constexpr int col_split()
 }
 
 // Shared memory of one node's direction (besides the sampled rows), for a
-// CTA of NT threads.
-template <int NT>
+// CTA of NT threads sampling up to S rows.
+template <int NT, int S = kTreeSample>
 struct DirSmem {
     float part[col_split<NT>()][KMX_DESC_DIM];
     float cvec[KMX_DESC_DIM], vvec[KMX_DESC_DIM], uvec[KMX_DESC_DIM];
-    float w[kTreeSample];
+    float w[S];
     float redf[2][NT / 32];
     int redi[NT / 32];
     float scale;
@@ -385,16 +388,15 @@ struct DirSmem {
 };
 
 // Centre (D.cvec) and principal direction (D.vvec) of a node of `len` rows
-// whose rows are X[perm[0 .. len)], from up to kTreeSample of them (evenly
-// spaced in the current order) held centred in xs; lo / hi (thread 0) get
-// the range of the sample's projections.  Every thread of the CTA (NT
-// threads) calls it.
-template <int NT>
+// whose rows are X[perm[0 .. len)], from up to S of them (evenly spaced in
+// the current order) held centred in xs; lo / hi (thread 0) get the range of
+// the sample's projections.  Every thread of the CTA (NT threads) calls it.
+template <int NT, int S>
 __device__ void node_direction(const float* __restrict__ X, const int32_t* perm, int64_t len,
-                               float (*xs)[KMX_DESC_DIM], DirSmem<NT>& D, float& lo, float& hi)
+                               float (*xs)[KMX_DESC_DIM], DirSmem<NT, S>& D, float& lo, float& hi)
 {
     constexpr int kColSplit = col_split<NT>();
-    const int m = (int)min(len, (int64_t)kTreeSample);
+    const int m = (int)min(len, (int64_t)S);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int cpart = tid / KMX_DESC_DIM, ch = tid - cpart * KMX_DESC_DIM;
     __syncthreads();  // the caller's earlier use of xs and D is over
@@ -479,10 +481,13 @@ __device__ void node_direction(const float* __restrict__ X, const int32_t* perm,
     // power iterations v <- S^T S v / |S^T S v| on the centred sample S
     for (int it = 0; it <= kTreeIters; ++it) {
         __syncthreads();
-        if (tid == 0) {
-            float nn = 0.f;
-            for (int h = 0; h < KMX_DESC_DIM; ++h) nn = fmaf(D.uvec[h], D.uvec[h], nn);
-            D.scale = nn > 0.f ? rsqrtf(nn) : 0.f;
+        if (warp == 0) {  // |u|^2 across the warp (lane 0 adds the 33rd value)
+            const float a = D.uvec[lane];
+            float nn = a * a;
+            if (lane == 0) nn = fmaf(D.uvec[32], D.uvec[32], nn);
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+            if (lane == 0) D.scale = nn > 0.f ? rsqrtf(nn) : 0.f;
         }
         __syncthreads();
         if (tid < KMX_DESC_DIM) D.vvec[tid] = D.scale > 0.f ? D.uvec[tid] * D.scale : (tid == 0 ? 1.f : 0.f);
@@ -568,97 +573,6 @@ __global__ void __launch_bounds__(kTreeThreads) tree_dir(const float* __restrict
     }
 }
 
-// The last levels of the tree, below `level0` (whose nodes hold at most
-// kFinishRows rows): one CTA per (level-0 node, side) splits its subtree
-// level by level in shared memory.  Per node: its direction, the projections
-// of all its rows, a bitonic sort by (projection, position), and the rows
-// in that order; the next level splits the node where tree_left says.  The
-// entries are read from src and written to vals (src may be vals).
-__global__ void __launch_bounds__(kTreeThreads) tree_finish(const float* __restrict__ P, int64_t np_cap,
-                                                            const int64_t* d_np, const float* __restrict__ Q,
-                                                            int64_t nq_cap, const int64_t* d_nq,
-                                                            const int32_t* src, int32_t* vals, int level0,
-                                                            int levels)
-{
-    extern __shared__ float tree_smem[];
-    float(*xs)[KMX_DESC_DIM] = reinterpret_cast<float(*)[KMX_DESC_DIM]>(tree_smem);
-    int32_t* perm = reinterpret_cast<int32_t*>(tree_smem + kTreeSample * KMX_DESC_DIM);  // [kFinishRows]
-    float* pk = reinterpret_cast<float*>(perm + kFinishRows);                             // [kFinishRows]
-    int32_t* pi = reinterpret_cast<int32_t*>(pk + kFinishRows);                           // [kFinishRows]
-    __shared__ DirSmem<kTreeThreads> D;
-    const int side = blockIdx.y;
-    const int tid = threadIdx.x;
-    const int64_t n = side ? kmx_count(d_nq, nq_cap) : kmx_count(d_np, np_cap);
-    int64_t start, len;
-    tree_node(n, level0, blockIdx.x, start, len);
-    const float* X = side ? Q : P;
-    const int32_t* gs = src + (side ? kmx_count(d_np, np_cap) : 0) + start;
-    int32_t* gv = vals + (side ? kmx_count(d_np, np_cap) : 0) + start;
-    if (len <= kTM) {  // a leaf: only the copy from src, if src is another array
-        if (gs != gv)
-            for (int i = tid; i < len; i += kTreeThreads) gv[i] = gs[i];
-        return;
-    }
-    for (int i = tid; i < len; i += kTreeThreads) perm[i] = gs[i];
-    for (int l = level0; l < levels; ++l) {
-        const int sub = l - level0;
-        for (int c = 0; c < (1 << sub); ++c) {
-            // the sub-node's range within the CTA's rows
-            int64_t cs = 0, cl = len;
-            for (int b = sub - 1; b >= 0; --b) {
-                const int64_t h = tree_left(cl);
-                if ((c >> b) & 1) {
-                    cs += h;
-                    cl -= h;
-                } else {
-                    cl = h;
-                }
-            }
-            if (cl <= kTM) continue;
-            float lo, hi;
-            node_direction(X, perm + cs, cl, xs, D, lo, hi);
-            int np2 = 1;
-            while (np2 < cl) np2 <<= 1;
-            for (int i = tid; i < np2; i += kTreeThreads) {
-                float p = INFINITY;
-                if (i < cl) {
-                    p = project(X + (int64_t)perm[cs + i] * KMX_DESC_STRIDE, D.cvec, D.vvec);
-                    if (!(p <= INFINITY)) p = INFINITY;  // NaN: a total order for the network
-                }
-                pk[i] = p;
-                pi[i] = i;
-            }
-            __syncthreads();
-            for (int kk = 2; kk <= np2; kk <<= 1) {
-                for (int j = kk >> 1; j > 0; j >>= 1) {
-                    for (int i = tid; i < np2; i += kTreeThreads) {
-                        const int o = i ^ j;
-                        if (o > i) {
-                            const float a = pk[i], b = pk[o];
-                            const int ia = pi[i], ib = pi[o];
-                            const bool gt = a > b || (!(a < b) && ia > ib);
-                            if (gt == ((i & kk) == 0)) {
-                                pk[i] = b;
-                                pk[o] = a;
-                                pi[i] = ib;
-                                pi[o] = ia;
-                            }
-                        }
-                    }
-                    __syncthreads();
-                }
-            }
-            // the rows in sorted order (pk is free now)
-            int32_t* tmp = reinterpret_cast<int32_t*>(pk);
-            for (int i = tid; i < cl; i += kTreeThreads) tmp[i] = perm[cs + min(pi[i], (int)cl - 1)];
-            __syncthreads();
-            for (int i = tid; i < cl; i += kTreeThreads) perm[cs + i] = tmp[i];
-            __syncthreads();
-        }
-    }
-    for (int i = tid; i < len; i += kTreeThreads) gv[i] = perm[i];
-}
-
 // One tree level for nodes that fit in shared memory (at most kLocalRows
 // rows), one CTA of NT threads per (node, side), in one launch instead of
 // the direction, key and radix-sort launches of a global level.  The split
@@ -668,8 +582,9 @@ __global__ void __launch_bounds__(kTreeThreads) tree_finish(const float* __restr
 // sort: two 256-bin histograms give the key T of the split row and how many
 // rows with key T go left; then a stable partition writes the left rows,
 // then the right rows, each in their current order, from src to dst.  Leaves
-// are copied, and so is every node of a level that the global kernels
-// ordered (some node of the level larger than kLocalRows on the device).
+// are copied.  A level that the global kernels ordered (some node of the
+// level larger than kLocalRows on the device) is left alone: their radix
+// sort wrote dst.
 constexpr size_t kLocalSmemBase = kTreeSmem;  // the sampled rows; the 16-bit keys follow
 constexpr int kLocalWideCtas = 304;           // from this many CTAs per level, CTAs of 256 threads (4 per SM)
 
@@ -716,6 +631,97 @@ __device__ __forceinline__ void select_bin(const int* hist, int before, int targ
     }
 }
 
+// Rows [0, len) of a node with 16-bit keys key[0 .. len) (written before
+// the call): the first h rows in the order of (key, position) go left.  Two
+// 256-bin histograms give the key T of the split row and how many rows with
+// key T go left; then a stable partition calls put(pos, get(i)) for every
+// row i, left rows at positions 0 .. h - 1 and right rows at h .. len - 1,
+// each in their current order (get(i) is issued before the round's barrier,
+// so that a global load overlaps it).  All NT (>= 256) threads call it;
+// hist[256], sel[4] and wsum[NT / 32] are shared scratch.  Ends after a
+// barrier.
+template <int NT, typename Get, typename Put>
+__device__ void split_at(const uint16_t* key, int len, int h, int* hist, int* sel, int* wsum, unsigned int* err,
+                         Get get, Put put)
+{
+    static_assert(NT >= 256, "one thread per bin clears the histograms");
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __syncthreads();  // the keys are written
+    if (tid < 256) hist[tid] = 0;
+    __syncthreads();
+    // one shared atomic per distinct bin and warp: keys cluster, and equal
+    // bins within a warp would otherwise serialise
+    for (int base = 0; base < len; base += NT) {
+        const int i = base + tid;
+        const int bin = i < len ? (int)(key[i] >> 8) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, bin);
+        if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
+    }
+    __syncthreads();
+    if (warp == 0) select_bin(hist, 0, h, &sel[0], &sel[1]);
+    __syncthreads();
+    const int b1 = sel[0], below1 = sel[1];
+    if (tid < 256) hist[tid] = 0;
+    __syncthreads();
+    for (int base = 0; base < len; base += NT) {
+        const int i = base + tid;
+        int bin = -1;
+        if (i < len) {
+            const int k = key[i];
+            if ((k >> 8) == b1) bin = k & 0xff;
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, bin);
+        if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int b2, below2;
+        select_bin(hist, below1, h, &b2, &below2);
+        if (lane == 0) {
+            sel[2] = (b1 << 8) | b2;
+            sel[3] = h - below2;
+        }
+    }
+    __syncthreads();
+    const int T = sel[2], need = sel[3];
+    // stable partition in rounds of NT rows: per round, the counts of
+    // key < T (low half of a word) and key == T (high half) before each row
+    int run_l = 0, run_e = 0;  // over earlier rounds (uniform)
+    for (int base = 0; base < len; base += NT) {
+        const int i = base + tid;
+        const bool valid = i < len;
+        const int32_t v = valid ? get(i) : 0;
+        const int k = valid ? (int)key[i] : 0x10000;
+        const bool isl = valid && k < T, ise = valid && k == T;
+        const unsigned bl = __ballot_sync(0xffffffffu, isl), be = __ballot_sync(0xffffffffu, ise);
+        const unsigned lt = (1u << lane) - 1u;
+        if (lane == 0) wsum[warp] = __popc(bl) | (__popc(be) << 16);
+        __syncthreads();
+        int pre = 0, tot = 0;
+#pragma unroll 8
+        for (int w = 0; w < NT / 32; ++w) {
+            const int v = wsum[w];
+            pre += w < warp ? v : 0;
+            tot += v;
+        }
+        const int nl = run_l + (pre & 0xffff) + __popc(bl & lt);  // key < T before row i
+        const int ne = run_e + (pre >> 16) + __popc(be & lt);     // key == T before row i
+        if (valid) {
+            const int left_before = nl + min(ne, need);
+            const bool left = isl || (ise && ne < need);
+            const int pos = left ? left_before : h + (i - left_before);
+            if (pos < len) {  // always (the counts add up to h left rows); checked, not assumed
+                put(pos, v);
+            } else {
+                kmx_raise(err, KMX_DERR_CAPACITY);
+            }
+        }
+        run_l += tot & 0xffff;
+        run_e += tot >> 16;
+        __syncthreads();  // wsum is rewritten by the next round
+    }
+}
+
 template <int NT>
 __global__ void __launch_bounds__(NT, 1024 / NT) tree_local(const float* __restrict__ P, int64_t np_cap,
                                                            const int64_t* d_np, const float* __restrict__ Q,
@@ -733,16 +739,17 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tree_local(const float* __restr
     __shared__ int sel[4];   // B1, below B1, T, rows of key T that go left
     __shared__ float range[2];
     const int side = blockIdx.y;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const int64_t np = kmx_count(d_np, np_cap), nq = kmx_count(d_nq, nq_cap);
     const int64_t n = side ? nq : np;
     int64_t start, len64;
     tree_node(n, level, blockIdx.x, start, len64);
     const int32_t* gs = src + (side ? np : 0) + start;
     int32_t* gd = dst + (side ? np : 0) + start;
-    const bool ordered = level_max(np > nq ? np : nq, level) > kLocalRows;  // by the global kernels
-    if (len64 <= kTM || ordered || len64 > kLocalRows) {
-        if (!ordered && len64 > kLocalRows && tid == 0) kmx_raise(err, KMX_DERR_CAPACITY);  // cannot occur
+    // a level the global kernels ordered (their sort wrote dst) needs nothing
+    if (level_max(np > nq ? np : nq, level) > kLocalRows) return;
+    if (len64 <= kTM || len64 > kLocalRows) {  // a leaf (a larger node cannot occur): only the copy
+        if (len64 > kLocalRows && tid == 0) kmx_raise(err, KMX_DERR_CAPACITY);
         for (int64_t i = tid; i < len64; i += NT) gd[i] = gs[i];
         return;
     }
@@ -755,90 +762,96 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tree_local(const float* __restr
         range[0] = lo;
         range[1] = hi;
     }
-    if (tid < 256) hist[tid] = 0;
     __syncthreads();
     lo = range[0];
     hi = range[1];
     const float qs = hi > lo ? 65535.f / (hi - lo) : 0.f;
-    // keys and the histogram of their high bytes
-    // (one shared atomic per distinct bin and warp: keys cluster, and equal
-    // bins within a warp would otherwise serialise)
-    for (int base = 0; base < len; base += NT) {
-        const int i = base + tid;
-        int bin = -1;
-        if (i < len) {
-            const float p = project(X + (int64_t)gs[i] * KMX_DESC_STRIDE, D.cvec, D.vvec);
-            const float t = fminf(fmaxf((p - lo) * qs, 0.f), 65535.f);  // NaN -> 0
-            const uint16_t k = (uint16_t)t;
-            key[i] = k;
-            bin = k >> 8;
-        }
-        const unsigned peers = __match_any_sync(0xffffffffu, bin);
-        if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
+    int32_t g = tid < len ? gs[tid] : 0;
+    for (int i = tid; i < len; i += NT) {
+        const int32_t gn = i + NT < len ? gs[i + NT] : 0;  // the next row's index, loaded during this row
+        const float p = project(X + (int64_t)g * KMX_DESC_STRIDE, D.cvec, D.vvec);
+        key[i] = (uint16_t)fminf(fmaxf((p - lo) * qs, 0.f), 65535.f);  // NaN -> 0
+        g = gn;
     }
-    __syncthreads();
-    if (warp == 0) select_bin(hist, 0, h, &sel[0], &sel[1]);
-    __syncthreads();
-    const int b1 = sel[0], below1 = sel[1];
-    if (tid < 256) hist[tid] = 0;
-    __syncthreads();
-    for (int base = 0; base < len; base += NT) {
-        const int i = base + tid;
-        int bin = -1;
-        if (i < len) {
-            const uint16_t k = key[i];
-            if ((k >> 8) == b1) bin = k & 0xff;
-        }
-        const unsigned peers = __match_any_sync(0xffffffffu, bin);
-        if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
+    split_at<NT>(key, len, h, hist, sel, wsum, err, [&](int i) { return gs[i]; },
+                 [&](int pos, int32_t v) { gd[pos] = v; });
+}
+
+// The last levels of the tree, below `level0` (whose nodes hold at most
+// kFinishRows rows): one CTA per (level-0 node, side) splits its subtree
+// level by level in shared memory.  Per node: its direction (from up to
+// kFinishSample rows), 16-bit keys of all its rows and split_at, as
+// tree_local does; the next level splits each half again.  The entries are
+// read from src and written to vals (src may be vals).
+__global__ void __launch_bounds__(kTreeThreads) tree_finish(const float* __restrict__ P, int64_t np_cap,
+                                                            const int64_t* d_np, const float* __restrict__ Q,
+                                                            int64_t nq_cap, const int64_t* d_nq,
+                                                            const int32_t* src, int32_t* vals, int level0,
+                                                            int levels, unsigned int* err)
+{
+    extern __shared__ float tree_smem[];
+    float(*xs)[KMX_DESC_DIM] = reinterpret_cast<float(*)[KMX_DESC_DIM]>(tree_smem);
+    int32_t* perm = reinterpret_cast<int32_t*>(tree_smem + kFinishSample * KMX_DESC_DIM);  // [kFinishRows]
+    int32_t* tmp = perm + kFinishRows;                                                    // [kFinishRows]
+    uint16_t* key = reinterpret_cast<uint16_t*>(tmp + kFinishRows);                       // [kFinishRows]
+    __shared__ DirSmem<kTreeThreads, kFinishSample> D;
+    __shared__ int hist[256];
+    __shared__ int wsum[kTreeThreads / 32];
+    __shared__ int sel[4];
+    __shared__ float range[2];
+    const int side = blockIdx.y;
+    const int tid = threadIdx.x;
+    const int64_t np = kmx_count(d_np, np_cap);
+    const int64_t n = side ? kmx_count(d_nq, nq_cap) : np;
+    int64_t start, len;
+    tree_node(n, level0, blockIdx.x, start, len);
+    const float* X = side ? Q : P;
+    const int32_t* gs = src + (side ? np : 0) + start;
+    int32_t* gv = vals + (side ? np : 0) + start;
+    if (len <= kTM || len > kFinishRows) {  // a leaf (a larger node cannot occur): only the copy
+        if (len > kFinishRows && tid == 0) kmx_raise(err, KMX_DERR_CAPACITY);
+        if (gs != gv)
+            for (int64_t i = tid; i < len; i += kTreeThreads) gv[i] = gs[i];
+        return;
     }
-    __syncthreads();
-    if (warp == 0) {
-        int b2, below2;
-        select_bin(hist, below1, h, &b2, &below2);
-        if (lane == 0) {
-            sel[2] = (b1 << 8) | b2;
-            sel[3] = h - below2;
-        }
-    }
-    __syncthreads();
-    const int T = sel[2], need = sel[3];
-    // stable partition in rounds of NT rows: per round, the
-    // counts of key < T (low half of a word) and key == T (high half) before
-    // each row
-    int run_l = 0, run_e = 0;  // over earlier rounds (uniform)
-    for (int base = 0; base < len; base += NT) {
-        const int i = base + tid;
-        const bool valid = i < len;
-        const int k = valid ? (int)key[i] : 0x10000;
-        const bool isl = valid && k < T, ise = valid && k == T;
-        const unsigned bl = __ballot_sync(0xffffffffu, isl), be = __ballot_sync(0xffffffffu, ise);
-        const unsigned lt = (1u << lane) - 1u;
-        if (lane == 0) wsum[warp] = __popc(bl) | (__popc(be) << 16);
-        __syncthreads();
-        int pre = 0, tot = 0;
-#pragma unroll 8
-        for (int w = 0; w < kWarpsL; ++w) {
-            const int v = wsum[w];
-            pre += w < warp ? v : 0;
-            tot += v;
-        }
-        const int nl = run_l + (pre & 0xffff) + __popc(bl & lt);  // key < T before row i
-        const int ne = run_e + (pre >> 16) + __popc(be & lt);     // key == T before row i
-        if (valid) {
-            const int left_before = nl + min(ne, need);
-            const bool left = isl || (ise && ne < need);
-            const int pos = left ? left_before : h + (i - left_before);
-            if (pos < len) {  // always (the counts add up to h left rows); checked, not assumed
-                gd[pos] = gs[i];
-            } else {
-                kmx_raise(err, KMX_DERR_CAPACITY);
+    for (int i = tid; i < len; i += kTreeThreads) perm[i] = gs[i];
+    for (int l = level0; l < levels; ++l) {
+        const int sub = l - level0;
+        for (int c = 0; c < (1 << sub); ++c) {
+            // the sub-node's range within the CTA's rows
+            int64_t cs = 0, cl = len;
+            for (int b = sub - 1; b >= 0; --b) {
+                const int64_t h = tree_left(cl);
+                if ((c >> b) & 1) {
+                    cs += h;
+                    cl -= h;
+                } else {
+                    cl = h;
+                }
             }
+            if (cl <= kTM) continue;
+            float lo, hi;
+            node_direction(X, perm + cs, cl, xs, D, lo, hi);
+            if (tid == 0) {
+                range[0] = lo;
+                range[1] = hi;
+            }
+            __syncthreads();
+            lo = range[0];
+            hi = range[1];
+            const float qs = hi > lo ? 65535.f / (hi - lo) : 0.f;
+            for (int i = tid; i < cl; i += kTreeThreads) {
+                const float p = project(X + (int64_t)perm[cs + i] * KMX_DESC_STRIDE, D.cvec, D.vvec);
+                key[i] = (uint16_t)fminf(fmaxf((p - lo) * qs, 0.f), 65535.f);  // NaN -> 0
+            }
+            split_at<kTreeThreads>(key, (int)cl, (int)tree_left(cl), hist, sel, wsum, err,
+                                   [&](int i) { return perm[cs + i]; }, [&](int pos, int32_t v) { tmp[pos] = v; });
+            for (int i = tid; i < cl; i += kTreeThreads) perm[cs + i] = tmp[i];
+            // (the next node_direction starts with a barrier)
         }
-        run_l += tot & 0xffff;
-        run_e += tot >> 16;
-        __syncthreads();  // wsum is rewritten by the next round
     }
+    __syncthreads();
+    for (int i = tid; i < len; i += kTreeThreads) gv[i] = perm[i];
 }
 
 // Sort key of every packed entry for this level: side (top bit), node index
@@ -968,26 +981,25 @@ __global__ void __launch_bounds__(kTN) tc_pack(const float* __restrict__ desc, c
 // plan: first candidates, first bounds and the column tiles each row tile needs
 // ---------------------------------------------------------------------------
 
-// Squared distance between the shared-memory centre cR (33 values) and the
-// centre of tile u (a 36-float row of centres, 16-byte aligned).
+// Squared distance between a row tile's centre cR (shared, 16-byte aligned,
+// 33 values) and the centre of tile u (a 36-float row of centres, 16-byte
+// aligned): two interleaved chains of paired FP32 terms, then their sum.  It
+// only decides which tiles are tested, within the tile test's margins.
 __device__ __forceinline__ float centre_dist2(const float* __restrict__ cR, const float* __restrict__ c)
 {
     const float4* c4 = reinterpret_cast<const float4*>(c);
-    float d = 0.f;
+    const float4* r4 = reinterpret_cast<const float4*>(cR);
+    float2 d = make_float2(0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        const float4 v = __ldg(c4 + q);
-        float e = cR[4 * q] - v.x;
-        d = fmaf(e, e, d);
-        e = cR[4 * q + 1] - v.y;
-        d = fmaf(e, e, d);
-        e = cR[4 * q + 2] - v.z;
-        d = fmaf(e, e, d);
-        e = cR[4 * q + 3] - v.w;
-        d = fmaf(e, e, d);
+        const float4 v = __ldg(c4 + q), r = r4[q];
+        float2 e = __fadd2_rn(make_float2(r.x, r.y), make_float2(-v.x, -v.y));
+        d = __ffma2_rn(e, e, d);
+        e = __fadd2_rn(make_float2(r.z, r.w), make_float2(-v.z, -v.w));
+        d = __ffma2_rn(e, e, d);
     }
     const float e = cR[32] - __ldg(c + 32);
-    return fmaf(e, e, d);
+    return fmaf(e, e, d.x + d.y);
 }
 
 // False only when no column of a tile with centre distance `dist` and radius
@@ -1021,11 +1033,11 @@ __device__ __forceinline__ void plan_tile(const float* __restrict__ X, const int
                                           int32_t* __restrict__ nneed, int2* __restrict__ items,
                                           int* __restrict__ n_items, const int64_t rt)
 {
-    __shared__ __align__(16) float ys[kTN][kCenterStride];  // the nearest tile's rows, zero-padded to 36
+    __shared__ __align__(16) float ys[kTN][kCenterStride];  // the nearest tile's rows negated, zero-padded to 36
     __shared__ __align__(16) float sc[kTN][kCenterStride];  // surviving tiles: centre, radius at [33]
     __shared__ int32_t sid[kTN];
     __shared__ uint8_t rec[kPlanRec][kTM];  // per row: columns recorded in the first pass
-    __shared__ float cR[KMX_DESC_DIM];
+    __shared__ __align__(16) float cR[kCenterStride];
     __shared__ unsigned needbits[kTN / 32];
     __shared__ int wcnt[kTN / 32];
     __shared__ float redf[kTN / 32];
@@ -1092,7 +1104,7 @@ __device__ __forceinline__ void plan_tile(const float* __restrict__ X, const int
         const bool yv = yp < cols;
         const float* yr = yv ? Y + (int64_t)permY[yp] * KMX_DESC_STRIDE : nullptr;
 #pragma unroll
-        for (int h = 0; h < kCenterStride; ++h) ys[tid][h] = (yv && h < KMX_DESC_DIM) ? __ldg(yr + h) : 0.f;
+        for (int h = 0; h < kCenterStride; ++h) ys[tid][h] = (yv && h < KMX_DESC_DIM) ? -__ldg(yr + h) : 0.f;
     }
     __syncthreads();
     // 2. exact distances to the nearest tile.  One pass finds d1 <= d2 and
@@ -1105,28 +1117,50 @@ __device__ __forceinline__ void plan_tile(const float* __restrict__ X, const int
     const int ncol = (int)min((int64_t)kTN, cols - cs * kTN);
     float d2 = INFINITY;
     if (valid) {
+        // the exact path's arithmetic: x + (-y) per dimension, one fused
+        // multiply-add per term in dimension order
         auto dist = [&](int j) -> float {
             const float4* y4 = reinterpret_cast<const float4*>(ys[j]);
             float acc = 0.f;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const float4 yv4 = y4[c];
-                float e = x[4 * c] - yv4.x;
+                float e = __fadd_rn(x[4 * c], yv4.x);
                 acc = fmaf(e, e, acc);
-                e = x[4 * c + 1] - yv4.y;
+                e = __fadd_rn(x[4 * c + 1], yv4.y);
                 acc = fmaf(e, e, acc);
-                e = x[4 * c + 2] - yv4.z;
+                e = __fadd_rn(x[4 * c + 2], yv4.z);
                 acc = fmaf(e, e, acc);
-                e = x[4 * c + 3] - yv4.w;
+                e = __fadd_rn(x[4 * c + 3], yv4.w);
                 acc = fmaf(e, e, acc);
             }
-            const float e = x[32] - ys[j][32];
+            const float e = __fadd_rn(x[32], ys[j][32]);
             return fmaf(e, e, acc);
+        };
+        // the same for columns j and j + 1 at once, one in each half of the
+        // paired FP32 instructions (each half the arithmetic above)
+        auto dist_pair = [&](int j) -> float2 {
+            const float4* ya = reinterpret_cast<const float4*>(ys[j]);
+            const float4* yb = reinterpret_cast<const float4*>(ys[j + 1]);
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float4 va = ya[c], vb = yb[c];
+                float2 e = __fadd2_rn(make_float2(x[4 * c], x[4 * c]), make_float2(va.x, vb.x));
+                acc = __ffma2_rn(e, e, acc);
+                e = __fadd2_rn(make_float2(x[4 * c + 1], x[4 * c + 1]), make_float2(va.y, vb.y));
+                acc = __ffma2_rn(e, e, acc);
+                e = __fadd2_rn(make_float2(x[4 * c + 2], x[4 * c + 2]), make_float2(va.z, vb.z));
+                acc = __ffma2_rn(e, e, acc);
+                e = __fadd2_rn(make_float2(x[4 * c + 3], x[4 * c + 3]), make_float2(va.w, vb.w));
+                acc = __ffma2_rn(e, e, acc);
+            }
+            const float2 e = __fadd2_rn(make_float2(x[32], x[32]), make_float2(ys[j][32], ys[j + 1][32]));
+            return __ffma2_rn(e, e, acc);
         };
         float d1 = INFINITY;
         int nrec = 0;
-        for (int j = 0; j < ncol; ++j) {
-            const float acc = dist(j);
+        auto take = [&](float acc, int j) {
             if (acc < d1) {
                 d2 = d1;
                 d1 = acc;
@@ -1137,7 +1171,14 @@ __device__ __forceinline__ void plan_tile(const float* __restrict__ X, const int
                 if (nrec < kPlanRec) rec[nrec][tid] = (uint8_t)j;
                 ++nrec;
             }
+        };
+        int j = 0;
+        for (; j + 1 < ncol; j += 2) {
+            const float2 acc = dist_pair(j);
+            take(acc.x, j);
+            take(acc.y, j + 1);
         }
+        if (j < ncol) take(dist(j), j);
         int k = 0;
         if (nrec <= kPlanRec) {
             for (int i = 0; i < nrec; ++i) {
@@ -1819,7 +1860,8 @@ size_t tc_smem_bytes()
 
 struct TcBuffers {
     uint32_t *keys, *keys_tmp;
-    int32_t *vals, *vals_tmp;  // the tree's packed entries (source rows, then target rows)
+    int32_t *vals, *vals_tmp;  // the tree's packed entries (source rows, then target rows), level to level
+    int32_t* vals_sort;        // the radix sort's temporary values
     int32_t* perm;             // sorted: [0, np) source rows, [np_cap, np_cap + nq) target rows
     int64_t* n2;               // np + nq on the device
     int64_t* nsort;            // the entries a global level's radix sort takes (np + nq or 0)
@@ -1856,6 +1898,7 @@ TcBuffers tc_carve(void* base, int64_t np_cap, int64_t nq_cap, size_t* total)
     b.keys_tmp = (uint32_t*)a.take(sizeof(uint32_t) * (size_t)n2);
     b.vals = (int32_t*)a.take(sizeof(int32_t) * (size_t)n2);
     b.vals_tmp = (int32_t*)a.take(sizeof(int32_t) * (size_t)n2);
+    b.vals_sort = (int32_t*)a.take(sizeof(int32_t) * (size_t)n2);
     b.perm = (int32_t*)a.take(sizeof(int32_t) * (size_t)n2);
     b.n2 = (int64_t*)a.take(sizeof(int64_t));
     b.nsort = (int64_t*)a.take(sizeof(int64_t));
@@ -1934,8 +1977,9 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
     // Levels whose nodes can exceed kLocalRows at the capacities run the
     // global kernels (direction, keys, radix sort), which do nothing on the
     // device once every node fits; tree_local then splits the level (or,
-    // after the global kernels, copies it).  The entries alternate between
-    // vals and vals_tmp.
+    // after the global kernels, does nothing).  The entries alternate
+    // between vals and vals_tmp: the sort and tree_local read one and write
+    // the other.
     int64_t node_max = np_cap > nq_cap ? np_cap : nq_cap;  // largest node of level l at any device count
     int32_t* cur = b.vals;                                  // the entries as the last level left them
     for (int l = 0; l < level0; ++l, node_max = tree_left(node_max)) {
@@ -1950,7 +1994,9 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
             const int kb = l <= 6 ? 16 : key_bits;
             tree_key<<<gb, 256, 0, st>>>(dp, np_cap, d_np, dq, nq_cap, d_nq, cur, l, kb, b.dirs, b.keys, b.nsort);
             if ((e = cudaGetLastError())) return e;
-            if ((e = kmx_sort_u32(ctx, b.keys, cur, b.keys_tmp, next, n2, b.nsort, kb, b.sort_scratch))) return e;
+            if ((e = kmx_sort_u32(ctx, b.keys, cur, b.keys_tmp, b.vals_sort, n2, b.nsort, kb, b.sort_scratch,
+                                  next)))
+                return e;
         }
         const int64_t rows = node_max < kLocalRows ? node_max : kLocalRows;
         KMX_COUNT_LAUNCH();
@@ -1967,7 +2013,8 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
     if (levels > 0) {  // the subtrees of at most 16 tiles, one CTA each
         KMX_COUNT_LAUNCH();
         tree_finish<<<dim3(1u << level0, 2), kTreeThreads, kFinishSmem, st>>>(dp, np_cap, d_np, dq, nq_cap, d_nq,
-                                                                             cur, b.vals, level0, levels);
+                                                                             cur, b.vals, level0, levels,
+                                                                             ctx->d_err);
         if ((e = cudaGetLastError())) return e;
     }
     KMX_COUNT_LAUNCH();

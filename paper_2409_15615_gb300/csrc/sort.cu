@@ -142,7 +142,7 @@ size_t kmx_sort_scratch_bytes(int64_t n)
 }
 
 cudaError_t kmx_sort_u32(kmx_ctx* ctx, uint32_t* keys, int32_t* vals, uint32_t* keys_tmp, int32_t* vals_tmp,
-                         int64_t n, const int64_t* d_n, int bits, void* scratch)
+                         int64_t n, const int64_t* d_n, int bits, void* scratch, int32_t* vals_out)
 {
     if (n <= 0) return cudaSuccess;
     const int blocks = kmx_sort_blocks(n);
@@ -151,10 +151,15 @@ cudaError_t kmx_sort_u32(kmx_ctx* ctx, uint32_t* keys, int32_t* vals, uint32_t* 
     int64_t* offs = (int64_t*)a.take(sizeof(int64_t) * (size_t)(kDigits * blocks + 1));
     int64_t* n_counts = (int64_t*)a.take(sizeof(int64_t));  // counts actually laid out (256 x live blocks)
     const int64_t m = (int64_t)kDigits * blocks;
+    const int passes = (bits + 7) / 8;
     uint32_t *ki = keys, *ko = keys_tmp;
-    int32_t *vi = vals, *vo = vals_tmp;
+    int32_t* vi = vals;
     cudaError_t e;
-    for (int shift = 0; shift < bits; shift += 8) {
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        // values: with vals_out the passes alternate so that the last one
+        // writes vals_out; otherwise between vals and vals_tmp
+        int32_t* vo = vals_out ? (((passes - 1 - p) & 1) ? vals_tmp : vals_out) : (vi == vals ? vals_tmp : vals);
         KMX_COUNT_LAUNCH();
         radix_count<<<blocks, kThreads, 0, ctx->stream>>>(ki, n, d_n, shift, counts, n_counts);
         if ((e = cudaGetLastError())) return e;
@@ -165,11 +170,9 @@ cudaError_t kmx_sort_u32(kmx_ctx* ctx, uint32_t* keys, int32_t* vals, uint32_t* 
         uint32_t* tk = ki;
         ki = ko;
         ko = tk;
-        int32_t* tv = vi;
         vi = vo;
-        vo = tv;
     }
-    if (ki != keys) {  // an odd number of passes: the result is in the temporaries
+    if (!vals_out && vi != vals) {  // an odd number of passes: the result is in the temporaries
         KMX_COUNT_LAUNCH();
         radix_copy<<<kmx_stride_blocks(n, 256, ctx->sm_count), 256, 0, ctx->stream>>>(ki, vi, n, d_n, keys, vals);
         if ((e = cudaGetLastError())) return e;
