@@ -76,10 +76,11 @@ constexpr int kMaxChunksFp32 = 8;
 // buffer: kMaxChunksFp32 * (list_cap + 1) entries.
 constexpr int kMaxChunksRows = 512;
 
-// The grid is sized from the capacities; the split of the actual work (row
-// tiles x column chunks) is computed here from the device-side counts, so a
-// call sized for 121k rows that finds 12k descriptors still spreads them over
-// the whole GPU.  With a row list the rows are list positions (np = list
+// The split of the actual work into (row tile, column chunk) blocks is
+// computed here from the device-side counts, so a call sized for 121k rows
+// that finds 12k descriptors still spreads them over the whole GPU; each CTA
+// loops over blocks, so the grid may be smaller than the work (the row-list
+// launch takes one CTA per SM).  With a row list the rows are list positions (np = list
 // length), colbest may be null (no column bests), and the partials of chunk c
 // are part[c * np ...] (packed by the actual list length, so that a short
 // list can use many chunks).
@@ -105,123 +106,127 @@ __global__ void __launch_bounds__(kThreads) match_tiles_fp32(const float* __rest
     }
     const int chunks = kmx::work_chunks(npt, nqt, target_ctas, maxc);
     if (blockIdx.x == 0 && threadIdx.x == 0) *chunks_out = chunks;
-    if ((int64_t)blockIdx.x >= npt * chunks) return;
-    const int chunk = (int)(blockIdx.x % chunks);
-    const int64_t row0 = (int64_t)(blockIdx.x / chunks) * kTile;
-    const int64_t tiles_per_chunk = (nqt + chunks - 1) / chunks;
-    const int64_t qt0 = chunk * tiles_per_chunk;
-    const int T = (int)max((int64_t)0, min(nqt, qt0 + tiles_per_chunk) - qt0);
-    const int tx = threadIdx.x & 15;                                   // column group
-    const int ty = (threadIdx.x >> 5) * 2 + ((threadIdx.x >> 4) & 1);  // row group
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // (row tile, chunk) blocks, blk = row tile * chunks + chunk; a CTA takes
+    // blocks blockIdx.x, blockIdx.x + gridDim.x, ...
+    for (int64_t blk = blockIdx.x; blk < npt * chunks; blk += gridDim.x) {
+        const int chunk = (int)(blk % chunks);
+        const int64_t row0 = (blk / chunks) * kTile;
+        const int64_t tiles_per_chunk = (nqt + chunks - 1) / chunks;
+        const int64_t qt0 = chunk * tiles_per_chunk;
+        const int T = (int)max((int64_t)0, min(nqt, qt0 + tiles_per_chunk) - qt0);
+        const int tx = threadIdx.x & 15;                                   // column group
+        const int ty = (threadIdx.x >> 5) * 2 + ((threadIdx.x >> 4) & 1);  // row group
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    float4 reg[kLoads];
-    fetch_tile(reg, dp, rows_list, row0, np);
-    store_tile(S.P, reg, 1.0f);
-    if (T > 0) {
-        fetch_tile(reg, dq, nullptr, qt0 * kTile, nq);
-        store_tile(S.Qn[0], reg, -1.0f);
-    }
-    __syncthreads();
+        float4 reg[kLoads];
+        fetch_tile(reg, dp, rows_list, row0, np);
+        store_tile(S.P, reg, 1.0f);
+        if (T > 0) {
+            fetch_tile(reg, dq, nullptr, qt0 * kTile, nq);
+            store_tile(S.Qn[0], reg, -1.0f);
+        }
+        __syncthreads();
 
-    float b1[8], b2[8];
-    int j1[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        b1[i] = INFINITY;
-        b2[i] = INFINITY;
-        j1[i] = 0x7fffffff;
-    }
-    for (int t = 0; t < T; ++t) {
-        const int buf = t & 1;
-        const int64_t col0 = (qt0 + t) * kTile;
-        if (t + 1 < T) fetch_tile(reg, dq, nullptr, col0 + kTile, nq);  // in flight during the math
-        float2 acc[8][4];
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int jp = 0; jp < 4; ++jp) acc[i][jp] = make_float2(0.f, 0.f);
-#pragma unroll 3
-        for (int k = 0; k < kDim; ++k) {
-            const float4 a0 = *reinterpret_cast<const float4*>(&S.P[k][ty * 8]);
-            const float4 a1 = *reinterpret_cast<const float4*>(&S.P[k][ty * 8 + 4]);
-            const float4 c0 = *reinterpret_cast<const float4*>(&S.Qn[buf][k][tx * 8]);
-            const float4 c1 = *reinterpret_cast<const float4*>(&S.Qn[buf][k][tx * 8 + 4]);
-            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float2 nc[4] = {make_float2(c0.x, c0.y), make_float2(c0.z, c0.w), make_float2(c1.x, c1.y),
-                                  make_float2(c1.z, c1.w)};
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float2 ai = make_float2(a[i], a[i]);
-#pragma unroll
-                for (int jp = 0; jp < 4; ++jp) {
-                    const float2 d = __fadd2_rn(ai, nc[jp]);
-                    acc[i][jp] = __ffma2_rn(d, d, acc[i][jp]);
-                }
-            }
+        float b1[8], b2[8];
+        int j1[8];
+    #pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            b1[i] = INFINITY;
+            b2[i] = INFINITY;
+            j1[i] = 0x7fffffff;
         }
-        // row bests (this thread's columns visited in ascending order)
-#pragma unroll
-        for (int jp = 0; jp < 4; ++jp) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int64_t col = col0 + tx * 8 + 2 * jp + h;
-                if (col < nq) {
-#pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        kmx::row_update(b1[i], j1[i], b2[i], h ? acc[i][jp].y : acc[i][jp].x, (int)col);
-                }
-            }
-        }
-        // column bests: this thread's 8 rows, then the partner half-warp, then
-        // the 8 warps through shared memory, then one atomicMin per column
-        if (colbest) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                unsigned long long best = ~0ull;
-#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int buf = t & 1;
+            const int64_t col0 = (qt0 + t) * kTile;
+            if (t + 1 < T) fetch_tile(reg, dq, nullptr, col0 + kTile, nq);  // in flight during the math
+            float2 acc[8][4];
+    #pragma unroll
+            for (int i = 0; i < 8; ++i)
+    #pragma unroll
+                for (int jp = 0; jp < 4; ++jp) acc[i][jp] = make_float2(0.f, 0.f);
+    #pragma unroll 3
+            for (int k = 0; k < kDim; ++k) {
+                const float4 a0 = *reinterpret_cast<const float4*>(&S.P[k][ty * 8]);
+                const float4 a1 = *reinterpret_cast<const float4*>(&S.P[k][ty * 8 + 4]);
+                const float4 c0 = *reinterpret_cast<const float4*>(&S.Qn[buf][k][tx * 8]);
+                const float4 c1 = *reinterpret_cast<const float4*>(&S.Qn[buf][k][tx * 8 + 4]);
+                const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float2 nc[4] = {make_float2(c0.x, c0.y), make_float2(c0.z, c0.w), make_float2(c1.x, c1.y),
+                                      make_float2(c1.z, c1.w)};
+    #pragma unroll
                 for (int i = 0; i < 8; ++i) {
-                    const int64_t row = row0 + ty * 8 + i;
-                    if (row < np) {
-                        const float dij = (j & 1) ? acc[i][j >> 1].y : acc[i][j >> 1].x;
-                        const unsigned long long key = kmx::pack_dist_index(dij, (uint32_t)row);
-                        best = key < best ? key : best;
+                    const float2 ai = make_float2(a[i], a[i]);
+    #pragma unroll
+                    for (int jp = 0; jp < 4; ++jp) {
+                        const float2 d = __fadd2_rn(ai, nc[jp]);
+                        acc[i][jp] = __ffma2_rn(d, d, acc[i][jp]);
                     }
                 }
-                const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, 16);
-                best = other < best ? other : best;
-                if (lane < 16) S.colred[warp][tx * 8 + j] = best;
             }
-            __syncthreads();
-            if (threadIdx.x < kTile) {
-                unsigned long long best = S.colred[0][threadIdx.x];
-#pragma unroll
-                for (int w = 1; w < kThreads / 32; ++w) {
-                    const unsigned long long o = S.colred[w][threadIdx.x];
-                    best = o < best ? o : best;
+            // row bests (this thread's columns visited in ascending order)
+    #pragma unroll
+            for (int jp = 0; jp < 4; ++jp) {
+    #pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t col = col0 + tx * 8 + 2 * jp + h;
+                    if (col < nq) {
+    #pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            kmx::row_update(b1[i], j1[i], b2[i], h ? acc[i][jp].y : acc[i][jp].x, (int)col);
+                    }
                 }
-                const int64_t col = col0 + threadIdx.x;
-                if (col < nq && best != ~0ull) atomicMin(&colbest[col], best);
             }
+            // column bests: this thread's 8 rows, then the partner half-warp, then
+            // the 8 warps through shared memory, then one atomicMin per column
+            if (colbest) {
+    #pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    unsigned long long best = ~0ull;
+    #pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int64_t row = row0 + ty * 8 + i;
+                        if (row < np) {
+                            const float dij = (j & 1) ? acc[i][j >> 1].y : acc[i][j >> 1].x;
+                            const unsigned long long key = kmx::pack_dist_index(dij, (uint32_t)row);
+                            best = key < best ? key : best;
+                        }
+                    }
+                    const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, 16);
+                    best = other < best ? other : best;
+                    if (lane < 16) S.colred[warp][tx * 8 + j] = best;
+                }
+                __syncthreads();
+                if (threadIdx.x < kTile) {
+                    unsigned long long best = S.colred[0][threadIdx.x];
+    #pragma unroll
+                    for (int w = 1; w < kThreads / 32; ++w) {
+                        const unsigned long long o = S.colred[w][threadIdx.x];
+                        best = o < best ? o : best;
+                    }
+                    const int64_t col = col0 + threadIdx.x;
+                    if (col < nq && best != ~0ull) atomicMin(&colbest[col], best);
+                }
+            }
+            if (t + 1 < T) store_tile(S.Qn[buf ^ 1], reg, -1.0f);
+            __syncthreads();
         }
-        if (t + 1 < T) store_tile(S.Qn[buf ^ 1], reg, -1.0f);
-        __syncthreads();
-    }
-    // merge the 16 column groups of each row (lanes sharing ty sit in one
-    // half-warp: xor offsets 1..8)
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        float d1 = b1[i], d2 = b2[i];
-        int jj = j1[i];
-#pragma unroll
-        for (int o = 1; o < 16; o <<= 1) {
-            const float od1 = __shfl_xor_sync(0xffffffffu, d1, o);
-            const float od2 = __shfl_xor_sync(0xffffffffu, d2, o);
-            const int oj = __shfl_xor_sync(0xffffffffu, jj, o);
-            kmx::row_merge(d1, jj, d2, od1, oj, od2);
+        // merge the 16 column groups of each row (lanes sharing ty sit in one
+        // half-warp: xor offsets 1..8)
+    #pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            float d1 = b1[i], d2 = b2[i];
+            int jj = j1[i];
+    #pragma unroll
+            for (int o = 1; o < 16; o <<= 1) {
+                const float od1 = __shfl_xor_sync(0xffffffffu, d1, o);
+                const float od2 = __shfl_xor_sync(0xffffffffu, d2, o);
+                const int oj = __shfl_xor_sync(0xffffffffu, jj, o);
+                kmx::row_merge(d1, jj, d2, od1, oj, od2);
+            }
+            const int64_t row = row0 + ty * 8 + i;
+            if (tx == 0 && row < np) part[(int64_t)chunk * stride + row] = kmx::RowBest{d1, jj, d2};
         }
-        const int64_t row = row0 + ty * 8 + i;
-        if (tx == 0 && row < np) part[(int64_t)chunk * stride + row] = kmx::RowBest{d1, jj, d2};
+        __syncthreads();  // shared tiles are rewritten by the next block
     }
 }
 
@@ -349,10 +354,11 @@ cudaError_t kmx_match_fp32_rows_launch(kmx_ctx* ctx, const float* dp, const int3
     KMX_COUNT_LAUNCH();
     rows_stream<<<(unsigned)(2 * (ctx->sm_count > 0 ? ctx->sm_count : 1)), kStreamThreads, 0, ctx->stream>>>(
         dp, rows, list_cap, d_nlist, dq, nq_cap, d_nq, (int64_t)kMaxChunksFp32 * (list_cap + 1), part, chunks_out);
-    // row tiles x chunks <= row tiles + target for the split work_chunks picks
-    const int64_t npt = (list_cap + kTile - 1) / kTile;
+    // one CTA per SM (the kernel's registers allow one), looping over the
+    // (row tile, chunk) blocks: the list is usually short, and then every
+    // CTA of a grid sized for list_cap would only check the count and exit
     const int target = 4 * ctx->sm_count;
-    const int64_t blocks = (npt > 0 ? npt : 1) + target;
+    const int64_t blocks = ctx->sm_count > 0 ? ctx->sm_count : 1;
     KMX_COUNT_LAUNCH();
     match_tiles_fp32<<<(unsigned)blocks, kThreads, sizeof(FpShared), ctx->stream>>>(
         dp, rows, list_cap, d_nlist, dq, nq_cap, d_nq, target, kMaxChunksRows, part, nullptr, chunks_out,

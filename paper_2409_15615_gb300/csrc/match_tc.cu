@@ -257,7 +257,7 @@ constexpr size_t kTreeSmem = sizeof(float) * kTreeSample * KMX_DESC_DIM;
 constexpr int kLocalRows = 16384;
 constexpr int kFinishLevels = 4;                         // levels below a node of 16 tiles
 constexpr int kFinishRows = kTM << kFinishLevels;        // 2048
-constexpr int kFinishSample = 128;                       // rows sampled per node below level0 (at most 2048 rows)
+constexpr int kFinishSample = 256;                       // rows sampled per node below level0 (at most 2048 rows)
 // sampled rows, entries, partition buffer, 16-bit keys
 constexpr size_t kFinishSmem = sizeof(float) * kFinishSample * KMX_DESC_DIM + sizeof(int32_t) * 2 * kFinishRows +
                                sizeof(uint16_t) * kFinishRows;
