@@ -1033,8 +1033,11 @@ __device__ __forceinline__ void plan_tile(const float* __restrict__ X, const int
                                           int32_t* __restrict__ nneed, int2* __restrict__ items,
                                           int* __restrict__ n_items, const int64_t rt)
 {
-    __shared__ __align__(16) float ys[kTN][kCenterStride];  // the nearest tile's rows negated, zero-padded to 36
-    __shared__ __align__(16) float sc[kTN][kCenterStride];  // surviving tiles: centre, radius at [33]
+    // the nearest tile's rows (negated, zero-padded to 36) in the exact pass,
+    // then the surviving tiles (centre, radius at [33]) in the tile lists
+    __shared__ __align__(16) float ysc[kTN][kCenterStride];
+    float(*ys)[kCenterStride] = ysc;
+    float(*sc)[kCenterStride] = ysc;
     __shared__ int32_t sid[kTN];
     __shared__ uint8_t rec[kPlanRec][kTM];  // per row: columns recorded in the first pass
     __shared__ __align__(16) float cR[kCenterStride];
