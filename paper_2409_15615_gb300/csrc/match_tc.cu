@@ -908,73 +908,77 @@ __global__ void __launch_bounds__(kTN) tc_pack(const float* __restrict__ desc, c
     __shared__ float cen[kCenterStride];
     __shared__ unsigned int bmax2;
     const int64_t n = kmx_count(d_n, n_cap);
-    const int64_t t = blockIdx.x;
-    if (t * kTN >= n && !(t == 0)) return;  // tiles past the count are never read
     const int tid = threadIdx.x;
-    const int64_t r = t * kTN + tid;
-    const bool valid = r < n;
-    float y[KMX_DESC_DIM];
-    if (valid) {
-        const float* row = desc + (int64_t)perm[r] * KMX_DESC_STRIDE;
-#pragma unroll
-        for (int h = 0; h < KMX_DESC_DIM; ++h) y[h] = __ldg(row + h);
-        bool bad = false;
-#pragma unroll
-        for (int h = 0; h < KMX_DESC_DIM; ++h) bad |= !isfinite(y[h]);
-        if (bad) kmx_raise(err, KMX_DERR_RANGE);
-    } else {
-#pragma unroll
-        for (int h = 0; h < KMX_DESC_DIM; ++h) y[h] = 0.f;
+    // the tiles below the count (tile 0 always), blockIdx.x, blockIdx.x +
+    // gridDim.x, ...; tiles past the count are never read
+    const int64_t tiles = n > 0 ? (n + kTN - 1) / kTN : 1;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int64_t r = t * kTN + tid;
+        const bool valid = r < n;
+        float y[KMX_DESC_DIM];
+        if (valid) {
+            const float* row = desc + (int64_t)perm[r] * KMX_DESC_STRIDE;
+    #pragma unroll
+            for (int h = 0; h < KMX_DESC_DIM; ++h) y[h] = __ldg(row + h);
+            bool bad = false;
+    #pragma unroll
+            for (int h = 0; h < KMX_DESC_DIM; ++h) bad |= !isfinite(y[h]);
+            if (bad) kmx_raise(err, KMX_DERR_RANGE);
+        } else {
+    #pragma unroll
+            for (int h = 0; h < KMX_DESC_DIM; ++h) y[h] = 0.f;
+        }
+    #pragma unroll
+        for (int h = 0; h < KMX_DESC_DIM; ++h) rows_s[tid][h] = y[h];
+        if (tid == 0) bmax2 = 0u;
+        __syncthreads();
+        const int cnt = (int)max((int64_t)0, min((int64_t)kTN, n - t * kTN));
+        if (tid < kCenterStride) {
+            float sum = 0.f;
+            if (tid < KMX_DESC_DIM)
+                for (int i = 0; i < cnt; ++i) sum += rows_s[i][tid];
+            cen[tid] = (tid < KMX_DESC_DIM && cnt > 0) ? sum / (float)cnt : 0.f;
+        }
+        __syncthreads();
+        float v[kK];
+        float nb = 0.f;
+    #pragma unroll
+        for (int h = 0; h < KMX_DESC_DIM; ++h) {
+            const float bv = y[h] - cen[h];
+            v[h] = bv;
+            nb = fmaf(bv, bv, nb);
+        }
+        const float beta = sqrtf(nb);
+    #pragma unroll
+        for (int h = KMX_DESC_DIM; h < kK; ++h) v[h] = 0.f;
+        if (valid) {
+            const float hi = __bfloat162float(__float2bfloat16_rn(nb));
+            v[KMX_DESC_DIM] = kSqrtC * beta;
+            v[KMX_DESC_DIM + 1] = hi;
+            v[KMX_DESC_DIM + 2] = nb - hi;
+        } else {
+    #pragma unroll
+            for (int h = 0; h < KMX_DESC_DIM; ++h) v[h] = 0.f;
+            v[KMX_DESC_DIM + 1] = INFINITY;  // -1/2 x inf: the padding column never qualifies
+        }
+        uint8_t* tile = out + t * (int64_t)kColBytes;
+        store_operand_row(tile, tid, v);
+        reinterpret_cast<float*>(tile + kHdrBeta)[tid] = valid ? beta : 0.f;
+        if (valid) atomicMax(&bmax2, __float_as_uint(nb));
+        if (tid < kCenterStride) {
+            reinterpret_cast<float*>(tile + kHdrCenter)[tid] = cen[tid];
+            centers[t * kCenterStride + tid] = cen[tid];
+        }
+        __syncthreads();
+        if (tid < 4) reinterpret_cast<float*>(tile + kHdrBmax)[tid] = tid == 0 ? __uint_as_float(bmax2) : 0.f;
+        if (tid == 0) centers[t * kCenterStride + KMX_DESC_DIM] = __uint_as_float(bmax2);
+        // the largest |b| of each group of 8 rows (lanes 8k .. 8k + 7 of a warp)
+        float gb = valid ? beta : 0.f;
+    #pragma unroll
+        for (int o = 4; o >= 1; o >>= 1) gb = fmaxf(gb, __shfl_xor_sync(0xffffffffu, gb, o));
+        if ((tid & 7) == 0) reinterpret_cast<float*>(tile + kHdrGBeta)[tid >> 3] = gb;
+        __syncthreads();  // the shared rows, centre and maximum are rewritten by the next tile
     }
-#pragma unroll
-    for (int h = 0; h < KMX_DESC_DIM; ++h) rows_s[tid][h] = y[h];
-    if (tid == 0) bmax2 = 0u;
-    __syncthreads();
-    const int cnt = (int)max((int64_t)0, min((int64_t)kTN, n - t * kTN));
-    if (tid < kCenterStride) {
-        float sum = 0.f;
-        if (tid < KMX_DESC_DIM)
-            for (int i = 0; i < cnt; ++i) sum += rows_s[i][tid];
-        cen[tid] = (tid < KMX_DESC_DIM && cnt > 0) ? sum / (float)cnt : 0.f;
-    }
-    __syncthreads();
-    float v[kK];
-    float nb = 0.f;
-#pragma unroll
-    for (int h = 0; h < KMX_DESC_DIM; ++h) {
-        const float bv = y[h] - cen[h];
-        v[h] = bv;
-        nb = fmaf(bv, bv, nb);
-    }
-    const float beta = sqrtf(nb);
-#pragma unroll
-    for (int h = KMX_DESC_DIM; h < kK; ++h) v[h] = 0.f;
-    if (valid) {
-        const float hi = __bfloat162float(__float2bfloat16_rn(nb));
-        v[KMX_DESC_DIM] = kSqrtC * beta;
-        v[KMX_DESC_DIM + 1] = hi;
-        v[KMX_DESC_DIM + 2] = nb - hi;
-    } else {
-#pragma unroll
-        for (int h = 0; h < KMX_DESC_DIM; ++h) v[h] = 0.f;
-        v[KMX_DESC_DIM + 1] = INFINITY;  // -1/2 x inf: the padding column never qualifies
-    }
-    uint8_t* tile = out + t * (int64_t)kColBytes;
-    store_operand_row(tile, tid, v);
-    reinterpret_cast<float*>(tile + kHdrBeta)[tid] = valid ? beta : 0.f;
-    if (valid) atomicMax(&bmax2, __float_as_uint(nb));
-    if (tid < kCenterStride) {
-        reinterpret_cast<float*>(tile + kHdrCenter)[tid] = cen[tid];
-        centers[t * kCenterStride + tid] = cen[tid];
-    }
-    __syncthreads();
-    if (tid < 4) reinterpret_cast<float*>(tile + kHdrBmax)[tid] = tid == 0 ? __uint_as_float(bmax2) : 0.f;
-    if (tid == 0) centers[t * kCenterStride + KMX_DESC_DIM] = __uint_as_float(bmax2);
-    // the largest |b| of each group of 8 rows (lanes 8k .. 8k + 7 of a warp)
-    float gb = valid ? beta : 0.f;
-#pragma unroll
-    for (int o = 4; o >= 1; o >>= 1) gb = fmaxf(gb, __shfl_xor_sync(0xffffffffu, gb, o));
-    if ((tid & 7) == 0) reinterpret_cast<float*>(tile + kHdrGBeta)[tid >> 3] = gb;
 }
 
 // ---------------------------------------------------------------------------
@@ -1335,15 +1339,26 @@ struct PlanDir {
     int* n_items;
 };
 
-// Both directions in one launch: blocks [0, split) take the row tiles of the
-// first direction, the others those of the second (one tail instead of two).
-__global__ void __launch_bounds__(kTM) tc_plan(PlanDir a, PlanDir b, int64_t split)
+// Both directions in one launch (one tail instead of two): CTAs take row
+// tiles from a counter (*next, zeroed before the launch), first those of
+// direction a, then those of b, up to the device counts.
+__global__ void __launch_bounds__(kTM) tc_plan(PlanDir a, PlanDir b, int* __restrict__ next)
 {
-    const bool second = (int64_t)blockIdx.x >= split;
-    const PlanDir d = second ? b : a;
-    plan_tile(d.X, d.permX, d.nx_cap, d.d_nx, d.cenX, d.Y, d.permY, d.ny_cap, d.d_ny, d.cenY, d.cand, d.cnt, d.ub,
-              d.need, d.need_stride, d.nneed, d.items, d.n_items,
-              second ? (int64_t)blockIdx.x - split : (int64_t)blockIdx.x);
+    __shared__ int s_k;
+    const int64_t ta = (kmx_count(a.d_nx, a.nx_cap) + kTM - 1) / kTM;
+    const int64_t tb = (kmx_count(b.d_nx, b.nx_cap) + kTM - 1) / kTM;
+    for (;;) {
+        if (threadIdx.x == 0) s_k = atomicAdd(next, 1);
+        __syncthreads();
+        const int64_t k = s_k;
+        __syncthreads();  // s_k is read before thread 0 takes the next tile
+        if (k >= ta + tb) break;
+        const bool second = k >= ta;
+        const PlanDir d = second ? b : a;
+        plan_tile(d.X, d.permX, d.nx_cap, d.d_nx, d.cenX, d.Y, d.permY, d.ny_cap, d.d_ny, d.cenY, d.cand, d.cnt, d.ub,
+                  d.need, d.need_stride, d.nneed, d.items, d.n_items, second ? k - ta : k);
+        __syncthreads();  // the next tile rewrites the shared arrays
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1755,66 +1770,71 @@ __global__ void __launch_bounds__(256) tc_rerank(const float* __restrict__ X, co
                                                  int* __restrict__ final_chunks)
 {
     const int lane = threadIdx.x & 31, s = lane & 7;
-    const int64_t i = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 4 + (lane >> 3);
-    if (final_chunks && i == 0 && lane == 0) *final_chunks = 1;  // rows_out holds whole-row summaries
+    if (final_chunks && blockIdx.x == 0 && threadIdx.x == 0) *final_chunks = 1;  // rows_out holds whole-row summaries
     const int64_t nx = kmx_count(d_nx, nx_cap), ny = kmx_count(d_ny, ny_cap);
-    const bool active = i < nx;
-    const int orig = active ? permX[i] : 0;
-    const int c = active ? cnt[i] : 0;
-    float b1 = INFINITY, b2 = INFINITY;
-    int j1 = 0x7fffffff;
-    if (c <= kCandCap && c > s) {
-        // the row once, then every candidate with the exact path's arithmetic
-        // (one fused multiply-add per term in h order)
-        float x[KMX_DESC_DIM];
-        const float4* x4 = reinterpret_cast<const float4*>(X + (int64_t)orig * KMX_DESC_STRIDE);
-#pragma unroll
-        for (int q4 = 0; q4 < 8; ++q4) {
-            const float4 v = __ldg(x4 + q4);
-            x[4 * q4] = v.x;
-            x[4 * q4 + 1] = v.y;
-            x[4 * q4 + 2] = v.z;
-            x[4 * q4 + 3] = v.w;
-        }
-        x[32] = __ldg(X + (int64_t)orig * KMX_DESC_STRIDE + 32);
-        for (int q = s; q < c; q += 8) {
-            const int pos = cand[i * kCandCap + q];
-            if (pos < 0 || pos >= ny) continue;  // padding columns are never collected
-            const int j = permY[pos];
-            const float* y = Y + (int64_t)j * KMX_DESC_STRIDE;
-            const float4* y4 = reinterpret_cast<const float4*>(y);
-            float acc = 0.f;
-#pragma unroll
+    // groups of four rows per warp, strided over the grid (the loop is
+    // uniform over the warp: its shuffles need every lane)
+    for (int64_t base = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 4; base < nx;
+         base += (int64_t)gridDim.x * 32) {
+        const int64_t i = base + (lane >> 3);
+        const bool active = i < nx;
+        const int orig = active ? permX[i] : 0;
+        const int c = active ? cnt[i] : 0;
+        float b1 = INFINITY, b2 = INFINITY;
+        int j1 = 0x7fffffff;
+        if (c <= kCandCap && c > s) {
+            // the row once, then every candidate with the exact path's arithmetic
+            // (one fused multiply-add per term in h order)
+            float x[KMX_DESC_DIM];
+            const float4* x4 = reinterpret_cast<const float4*>(X + (int64_t)orig * KMX_DESC_STRIDE);
+    #pragma unroll
             for (int q4 = 0; q4 < 8; ++q4) {
-                const float4 v = __ldg(y4 + q4);
-                float e = x[4 * q4] - v.x;
-                acc = fmaf(e, e, acc);
-                e = x[4 * q4 + 1] - v.y;
-                acc = fmaf(e, e, acc);
-                e = x[4 * q4 + 2] - v.z;
-                acc = fmaf(e, e, acc);
-                e = x[4 * q4 + 3] - v.w;
-                acc = fmaf(e, e, acc);
+                const float4 v = __ldg(x4 + q4);
+                x[4 * q4] = v.x;
+                x[4 * q4 + 1] = v.y;
+                x[4 * q4 + 2] = v.z;
+                x[4 * q4 + 3] = v.w;
             }
-            const float e = x[32] - __ldg(y + 32);
-            acc = fmaf(e, e, acc);
-            kmx::row_update(b1, j1, b2, acc, j);
+            x[32] = __ldg(X + (int64_t)orig * KMX_DESC_STRIDE + 32);
+            for (int q = s; q < c; q += 8) {
+                const int pos = cand[i * kCandCap + q];
+                if (pos < 0 || pos >= ny) continue;  // padding columns are never collected
+                const int j = permY[pos];
+                const float* y = Y + (int64_t)j * KMX_DESC_STRIDE;
+                const float4* y4 = reinterpret_cast<const float4*>(y);
+                float acc = 0.f;
+    #pragma unroll
+                for (int q4 = 0; q4 < 8; ++q4) {
+                    const float4 v = __ldg(y4 + q4);
+                    float e = x[4 * q4] - v.x;
+                    acc = fmaf(e, e, acc);
+                    e = x[4 * q4 + 1] - v.y;
+                    acc = fmaf(e, e, acc);
+                    e = x[4 * q4 + 2] - v.z;
+                    acc = fmaf(e, e, acc);
+                    e = x[4 * q4 + 3] - v.w;
+                    acc = fmaf(e, e, acc);
+                }
+                const float e = x[32] - __ldg(y + 32);
+                acc = fmaf(e, e, acc);
+                kmx::row_update(b1, j1, b2, acc, j);
+            }
         }
+    #pragma unroll
+        for (int o = 4; o >= 1; o >>= 1) {  // within the row's eight lanes
+            const float od1 = __shfl_xor_sync(0xffffffffu, b1, o);
+            const int oj = __shfl_xor_sync(0xffffffffu, j1, o);
+            const float od2 = __shfl_xor_sync(0xffffffffu, b2, o);
+            kmx::row_merge(b1, j1, b2, od1, oj, od2);
+        }
+        if (s != 0 || !active) continue;
+        if (c > kCandCap) {
+            fb_list[atomicAdd(reinterpret_cast<unsigned long long*>(fb_n), 1ull)] = orig;  // at most nx entries
+            continue;
+        }
+        if (rows_out) rows_out[orig] = kmx::RowBest{b1, j1, b2};
+        if (cols_best && j1 != 0x7fffffff) cols_best[orig] = kmx::pack_dist_index(b1, (uint32_t)j1);
     }
-#pragma unroll
-    for (int o = 4; o >= 1; o >>= 1) {  // within the row's eight lanes
-        const float od1 = __shfl_xor_sync(0xffffffffu, b1, o);
-        const int oj = __shfl_xor_sync(0xffffffffu, j1, o);
-        const float od2 = __shfl_xor_sync(0xffffffffu, b2, o);
-        kmx::row_merge(b1, j1, b2, od1, oj, od2);
-    }
-    if (s != 0 || !active) return;
-    if (c > kCandCap) {
-        fb_list[atomicAdd(reinterpret_cast<unsigned long long*>(fb_n), 1ull)] = orig;  // at most nx entries
-        return;
-    }
-    if (rows_out) rows_out[orig] = kmx::RowBest{b1, j1, b2};
-    if (cols_best && j1 != 0x7fffffff) cols_best[orig] = kmx::pack_dist_index(b1, (uint32_t)j1);
 }
 
 // Merge the exact fallback partials of each listed row (chunk c's partials
@@ -1875,7 +1895,7 @@ struct TcBuffers {
     float *ubP, *ubQ;
     int32_t *needP, *needQ, *nneedP, *nneedQ;
     int2 *itemsP, *itemsQ;
-    int* nitems;               // [0] source rows, [1] target rows
+    int* nitems;               // [0] source rows, [1] target rows, [2] the plan's tile counter
     int32_t *candP, *candQ, *cntP, *cntQ;
     int* chunks;               // [2] fallback P, [3] fallback Q
     int32_t *listP, *listQ;    // fallback rows (original indices)
@@ -1919,7 +1939,7 @@ TcBuffers tc_carve(void* base, int64_t np_cap, int64_t nq_cap, size_t* total)
     b.nneedQ = (int32_t*)a.take(sizeof(int32_t) * (size_t)tq);
     b.itemsP = (int2*)a.take(sizeof(int2) * (size_t)tp * (size_t)((tq + kItemTiles - 1) / kItemTiles));
     b.itemsQ = (int2*)a.take(sizeof(int2) * (size_t)tq * (size_t)((tp + kItemTiles - 1) / kItemTiles));
-    b.nitems = (int*)a.take(sizeof(int) * 2);
+    b.nitems = (int*)a.take(sizeof(int) * 4);
     b.candP = (int32_t*)a.take(sizeof(int32_t) * kCandCap * (size_t)np_cap);
     b.candQ = (int32_t*)a.take(sizeof(int32_t) * kCandCap * (size_t)nq_cap);
     b.cntP = (int32_t*)a.take(sizeof(int32_t) * (size_t)(np_cap + nq_cap));
@@ -1971,7 +1991,7 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
     if (e) return e;
     if ((e = cudaMemsetAsync(b.nlist, 0, sizeof(int64_t) * 2, st))) return e;
     if ((e = cudaMemsetAsync(b.cntP, 0, sizeof(int32_t) * (size_t)n2, st))) return e;
-    if ((e = cudaMemsetAsync(b.nitems, 0, sizeof(int) * 2, st))) return e;
+    if ((e = cudaMemsetAsync(b.nitems, 0, sizeof(int) * 3, st))) return e;
     // locality order of both clouds: one tree level per sort
     const unsigned gb = kmx_stride_blocks(n2, 256, ctx->sm_count);
     KMX_COUNT_LAUNCH();
@@ -2026,16 +2046,19 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
     const int32_t* permQ = b.perm + np_cap;
     // packed tiles, centres and radii
     KMX_COUNT_LAUNCH();
-    tc_pack<<<(unsigned)tp, kTN, 0, st>>>(dp, permP, np_cap, d_np, b.packP, b.cenP, ctx->d_err);
+    tc_pack<<<kmx_stride_blocks(tp, 1, ctx->sm_count, 16), kTN, 0, st>>>(dp, permP, np_cap, d_np, b.packP, b.cenP,
+                                                                        ctx->d_err);
     KMX_COUNT_LAUNCH();
-    tc_pack<<<(unsigned)tq, kTN, 0, st>>>(dq, permQ, nq_cap, d_nq, b.packQ, b.cenQ, ctx->d_err);
+    tc_pack<<<kmx_stride_blocks(tq, 1, ctx->sm_count, 16), kTN, 0, st>>>(dq, permQ, nq_cap, d_nq, b.packQ, b.cenQ,
+                                                                        ctx->d_err);
     // first candidates, bounds and tile lists both ways
     const PlanDir planP{dp, permP, np_cap, d_np, b.cenP, dq, permQ, nq_cap, d_nq, b.cenQ, b.candP,
                         b.cntP, b.ubP, b.needP, tq, b.nneedP, b.itemsP, b.nitems + 0};
     const PlanDir planQ{dq, permQ, nq_cap, d_nq, b.cenQ, dp, permP, np_cap, d_np, b.cenP, b.candQ,
                         b.cntQ, b.ubQ, b.needQ, tp, b.nneedQ, b.itemsQ, b.nitems + 1};
     KMX_COUNT_LAUNCH();
-    tc_plan<<<(unsigned)(tp + tq), kTM, 0, st>>>(planP, planQ, tp);
+    // about five CTAs per SM fit (registers); more would only wait for the counter
+    tc_plan<<<kmx_stride_blocks(tp + tq, 1, ctx->sm_count, 5), kTM, 0, st>>>(planP, planQ, b.nitems + 2);
     // tensor-core candidates both ways: one persistent CTA per SM
     const unsigned grid = (unsigned)(ctx->sm_count > 0 ? ctx->sm_count : 1);
     KMX_COUNT_LAUNCH();
@@ -2046,11 +2069,13 @@ cudaError_t kmx_match_tc_launch(kmx_ctx* ctx, const float* dp, int64_t np_cap, c
                                              b.nitems + 1, b.ubQ, b.candQ, b.cntQ, ctx->d_err);
     // exact re-ranking; overflowed rows are flagged
     KMX_COUNT_LAUNCH();
-    tc_rerank<<<kmx_blocks(np_cap, 32), 256, 0, st>>>(dp, permP, np_cap, d_np, dq, permQ, nq_cap, d_nq, b.candP,
-                                                     b.cntP, s.part, nullptr, b.listP, b.nlist + 0, s.chunks);
+    tc_rerank<<<kmx_stride_blocks(np_cap, 32, ctx->sm_count), 256, 0, st>>>(
+        dp, permP, np_cap, d_np, dq, permQ, nq_cap, d_nq, b.candP, b.cntP, s.part, nullptr, b.listP, b.nlist + 0,
+        s.chunks);
     KMX_COUNT_LAUNCH();
-    tc_rerank<<<kmx_blocks(nq_cap, 32), 256, 0, st>>>(dq, permQ, nq_cap, d_nq, dp, permP, np_cap, d_np, b.candQ,
-                                                     b.cntQ, nullptr, s.colbest, b.listQ, b.nlist + 1, nullptr);
+    tc_rerank<<<kmx_stride_blocks(nq_cap, 32, ctx->sm_count), 256, 0, st>>>(
+        dq, permQ, nq_cap, d_nq, dp, permP, np_cap, d_np, b.candQ, b.cntQ, nullptr, s.colbest, b.listQ, b.nlist + 1,
+        nullptr);
     if ((e = cudaGetLastError())) return e;
     // exact fallback for the flagged rows of each side
     if ((e = kmx_match_fp32_rows_launch(ctx, dp, b.listP, np_cap, b.nlist + 0, dq, nq_cap, d_nq, b.fbP,
