@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(kThreads) scatter_valid(int64_t n_cap, const i
         if (jflag[q]) valid[jpos[q]] = (int32_t)q;
 }
 
-__global__ void __launch_bounds__(kThreads, 5) spfh_kernel(int64_t n_cap, const int64_t* d_n,
+__global__ void __launch_bounds__(kThreads, 4) spfh_kernel(int64_t n_cap, const int64_t* d_n,
                                                         const float4* __restrict__ pts,
                                                         const float4* __restrict__ normal4, uint8_t* flags,
                                                         const int64_t* __restrict__ offs,
@@ -79,28 +79,45 @@ __global__ void __launch_bounds__(kThreads, 5) spfh_kernel(int64_t n_cap, const 
         const float PI = 3.14159265358979f;
         const int64_t b = offs[q], e = offs[q + 1];
         int pairs = 0, mv = 0;
-        for (int64_t t = b + lane; t - lane < e; t += 32) {
-            bool ok = false, valid = false;
-            if (t < e) {
-                const int k = nbr[t];
-                // the point and normal are loaded with the flag (one round
-                // trip instead of two); bit0 is never written here, so a byte
-                // another warp is updating still shows the same B
-                const float4 pk = __ldg(&pts[k]);
-                const float4 nk = __ldg(&normal4[k]);
-                valid = (flags[k] & 1) != 0;
-                if (k != q && valid) {
-                    float f[3];
-                    ok = pair_features(pq, nq, pk, nk, f);
-                    if (ok) {
-                        atomicAdd(&hist[warp][feature_bin(f[0], -PI, PI)], 1);
-                        atomicAdd(&hist[warp][kH + feature_bin(f[1], -1.f, 1.f)], 1);
-                        atomicAdd(&hist[warp][2 * kH + feature_bin(f[2], -1.f, 1.f)], 1);
-                    }
+        // two list entries per lane and step: both indices, then both
+        // neighbours' point, normal and flag, are requested before any use
+        for (int64_t t0 = b; t0 < e; t0 += 64) {
+            const int64_t ta = t0 + lane, tb = ta + 32;
+            const bool ha = ta < e, hb = tb < e;
+            const int ka = ha ? nbr[ta] : 0;
+            const int kb = hb ? nbr[tb] : 0;
+            float4 pa = pq, na = nq, pb = pq, nb = nq;
+            bool va = false, vb = false;
+            if (ha) {
+                pa = __ldg(&pts[ka]);
+                na = __ldg(&normal4[ka]);
+                va = (flags[ka] & 1) != 0;
+            }
+            if (hb) {
+                pb = __ldg(&pts[kb]);
+                nb = __ldg(&normal4[kb]);
+                vb = (flags[kb] & 1) != 0;
+            }
+            bool oka = false, okb = false;
+            float f[3];
+            if (ha && ka != q && va) {
+                oka = pair_features(pq, nq, pa, na, f);
+                if (oka) {
+                    atomicAdd(&hist[warp][feature_bin(f[0], -PI, PI)], 1);
+                    atomicAdd(&hist[warp][kH + feature_bin(f[1], -1.f, 1.f)], 1);
+                    atomicAdd(&hist[warp][2 * kH + feature_bin(f[2], -1.f, 1.f)], 1);
                 }
             }
-            pairs += __popc(__ballot_sync(kFull, ok));
-            mv += __popc(__ballot_sync(kFull, valid));
+            if (hb && kb != q && vb) {
+                okb = pair_features(pq, nq, pb, nb, f);
+                if (okb) {
+                    atomicAdd(&hist[warp][feature_bin(f[0], -PI, PI)], 1);
+                    atomicAdd(&hist[warp][kH + feature_bin(f[1], -1.f, 1.f)], 1);
+                    atomicAdd(&hist[warp][2 * kH + feature_bin(f[2], -1.f, 1.f)], 1);
+                }
+            }
+            pairs += __popc(__ballot_sync(kFull, oka)) + __popc(__ballot_sync(kFull, okb));
+            mv += __popc(__ballot_sync(kFull, va)) + __popc(__ballot_sync(kFull, vb));
         }
         if (lane == 0) {
             const bool inJ = mv >= tau_num;  // q itself is in M[q] with B
@@ -223,17 +240,21 @@ cudaError_t kmx_fasterpfh_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_para
     float* sp = spfh ? spfh : s.spfh;
     const int64_t n = g->n_cap;
     cudaError_t e = cudaSuccess;
+    // one wave each: both kernels are latency-bound gathers whose queries cost
+    // about the same, so every resident block takes an equal share
+    unsigned nbs = 0, nbf = 0;
+    if ((e = kmx_wave_blocks(spfh_kernel, kThreads, 0, n, kWarps, ctx->sm_count, &nbs))) return e;
+    if ((e = kmx_wave_blocks(fpfh_kernel, kThreads, 0, n, 4 * kWarps, ctx->sm_count, &nbf))) return e;
     // spfh_kernel writes the J flag of every point below the count; the scan
     // reads no other entry
-    const unsigned nbw = kmx_stride_blocks(n, kWarps, ctx->sm_count);
     KMX_COUNT_LAUNCH();
-    spfh_kernel<<<nbw, kThreads, 0, st>>>(n, g->d_n, g->pts, reinterpret_cast<const float4*>(normal4), flags,
+    spfh_kernel<<<nbs, kThreads, 0, st>>>(n, g->d_n, g->pts, reinterpret_cast<const float4*>(normal4), flags,
                                           offs, nbr, prm->tau_num, sp, s.jflag);
     if ((e = kmx_scan_i32(ctx, s.jflag, n, g->d_n, s.jpos))) return e;
     KMX_COUNT_LAUNCH();
     scatter_valid<<<kmx_stride_blocks(n, kThreads, ctx->sm_count), kThreads, 0, st>>>(n, g->d_n, s.jflag, s.jpos,
                                                                                        valid, n_valid);
     KMX_COUNT_LAUNCH();
-    fpfh_kernel<<<nbw, kThreads, 0, st>>>(n, valid, n_valid, g->pts, flags, offs, nbr, sp, desc);
+    fpfh_kernel<<<nbf, kThreads, 0, st>>>(n, valid, n_valid, g->pts, flags, offs, nbr, sp, desc);
     return cudaGetLastError();
 }

@@ -144,6 +144,22 @@ static inline unsigned int kmx_stride_blocks(int64_t cap_items, int items_per_bl
     return b < lim ? b : lim;
 }
 
+// Blocks for a grid-stride kernel, capped at one wave: the blocks of `kernel`
+// (at `threads` threads, `smem` dynamic shared bytes) that fit on every SM at
+// once, as its registers and shared memory allow.  Every block then starts at
+// launch and takes an equal share of the items; a grid above one wave would
+// leave its last blocks to run alone on a partly empty GPU.
+template <typename Kernel>
+static inline cudaError_t kmx_wave_blocks(Kernel kernel, int threads, size_t smem, int64_t cap_items,
+                                          int items_per_block, int sm_count, unsigned int* blocks)
+{
+    int per_sm = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    if (e) return e;
+    *blocks = kmx_stride_blocks(cap_items, items_per_block, sm_count, per_sm > 0 ? per_sm : 1);
+    return cudaSuccess;
+}
+
 // Bump allocator over the context scratch.  With base == nullptr it only
 // measures (every pointer it returns is null and `used` is the total).
 struct kmx_arena {
