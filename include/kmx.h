@@ -308,6 +308,10 @@ kmx_status kmx_normals(kmx_ctx* ctx, const kmx_grid* grid, const kmx_params* par
  *   with w_k = |a_k - a_q| over the m neighbours k != q.
  *   d_normal4, d_nbr_offs, d_nbr  as written by kmx_normals (or any input of
  *              the same layout).
+ *   nbr_cap    entries of d_nbr (as passed to kmx_normals); list entries at
+ *              or past it are not read.  The context scratch holds one
+ *              8-byte entry per list entry (each point's FPFH neighbours
+ *              and weights, written by the SPFH pass for the FPFH pass).
  *   d_flags    [n] uint8 in/out: bit0 (B) is read; bit1 is set for q in J.
  *   d_desc     [n_cap][36] float32: row j holds FPFH(J[j]) for j < |J|
  *              (33 values + 3 zeros); other rows are not written.
@@ -317,8 +321,8 @@ kmx_status kmx_normals(kmx_ctx* ctx, const kmx_grid* grid, const kmx_params* par
  *              for points without B); NULL keeps it in scratch.
  */
 kmx_status kmx_fasterpfh(kmx_ctx* ctx, const kmx_grid* grid, const kmx_params* params, const float* d_normal4,
-                         uint8_t* d_flags, const int64_t* d_nbr_offs, const int32_t* d_nbr, float* d_desc,
-                         int32_t* d_valid, int64_t* d_n_valid, float* d_spfh);
+                         uint8_t* d_flags, const int64_t* d_nbr_offs, const int32_t* d_nbr, int64_t nbr_cap,
+                         float* d_desc, int32_t* d_valid, int64_t* d_n_valid, float* d_spfh);
 
 /*
  * Algorithm 1 (steps 1 and 2) and the descriptors of Eqs. A2-A5 in one call,

@@ -385,20 +385,20 @@ kmx_status kmx_normals(kmx_ctx* c, const kmx_grid* g, const kmx_params* p, float
 }
 
 kmx_status kmx_fasterpfh(kmx_ctx* c, const kmx_grid* g, const kmx_params* p, const float* d_normal4,
-                         uint8_t* d_flags, const int64_t* d_nbr_offs, const int32_t* d_nbr, float* d_desc,
-                         int32_t* d_valid, int64_t* d_n_valid, float* d_spfh)
+                         uint8_t* d_flags, const int64_t* d_nbr_offs, const int32_t* d_nbr, int64_t nbr_cap,
+                         float* d_desc, int32_t* d_valid, int64_t* d_n_valid, float* d_spfh)
 {
     if (!c) return KMX_EINVAL;
     kmx_status s = check_params(c, g, p, "kmx_fasterpfh");
     if (s) return s;
-    if (!d_normal4 || !aligned16(d_normal4) || !d_flags || !d_nbr_offs || !d_nbr || !d_desc || !aligned16(d_desc) ||
-        !d_valid || !d_n_valid || (d_spfh && !aligned16(d_spfh)))
+    if (!d_normal4 || !aligned16(d_normal4) || !d_flags || !d_nbr_offs || !d_nbr || nbr_cap < 0 || !d_desc ||
+        !aligned16(d_desc) || !d_valid || !d_n_valid || (d_spfh && !aligned16(d_spfh)))
         return fail(c, KMX_EINVAL, "kmx_fasterpfh: bad argument");
     DeviceGuard dg(c->device);
-    s = ensure_ws(c, kmx_fasterpfh_scratch_bytes(g->n_cap, d_spfh == nullptr));
+    s = ensure_ws(c, kmx_fasterpfh_scratch_bytes(g->n_cap, d_spfh == nullptr, nbr_cap));
     if (s) return s;
     return launched(c,
-                    kmx_fasterpfh_launch(c, g, p, d_normal4, d_flags, d_nbr_offs, d_nbr, d_desc, d_valid,
+                    kmx_fasterpfh_launch(c, g, p, d_normal4, d_flags, d_nbr_offs, d_nbr, nbr_cap, d_desc, d_valid,
                                          d_n_valid, d_spfh, c->ws),
                     "kmx_fasterpfh");
 }

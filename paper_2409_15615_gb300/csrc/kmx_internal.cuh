@@ -236,10 +236,10 @@ cudaError_t kmx_normals_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_params
                                void* scratch);
 
 // fpfh.cu
-size_t kmx_fasterpfh_scratch_bytes(int64_t n_cap, bool need_spfh);
+size_t kmx_fasterpfh_scratch_bytes(int64_t n_cap, bool need_spfh, int64_t nbr_cap);
 cudaError_t kmx_fasterpfh_launch(kmx_ctx* ctx, const kmx_grid* g, const kmx_params* p, const float* normal4,
-                                 uint8_t* flags, const int64_t* offs, const int32_t* nbr, float* desc,
-                                 int32_t* valid, int64_t* n_valid, float* spfh, void* scratch);
+                                 uint8_t* flags, const int64_t* offs, const int32_t* nbr, int64_t nbr_cap,
+                                 float* desc, int32_t* valid, int64_t* n_valid, float* spfh, void* scratch);
 
 // ground.cu: geometric suppression; kmx_ground_bins_of is -1 for invalid
 // parameters

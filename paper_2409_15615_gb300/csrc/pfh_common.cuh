@@ -87,4 +87,19 @@ __device__ __forceinline__ void kahan_add_prod(float& sum, float& comp, float a,
     sum = t;
 }
 
+// kahan_add_prod on two independent sums at once, in paired FP32
+// instructions; ncomp holds the negated compensation.  Each component takes
+// exactly kahan_add_prod's roundings: fma(a, b, -c), then s + y, then
+// -((t - s) - y) computed as y + (s - t) (round-to-nearest is symmetric under
+// negation, and s - t is the fma of t, -1 and s).  The paired form issues half
+// the instructions for the same bits.
+__device__ __forceinline__ void kahan_add_prod2(float2& sum, float2& ncomp, float2 a, float2 b)
+{
+    const float2 y = __ffma2_rn(a, b, ncomp);
+    const float2 t = __fadd2_rn(sum, y);
+    const float2 e = __ffma2_rn(t, make_float2(-1.f, -1.f), sum);
+    ncomp = __fadd2_rn(y, e);
+    sum = t;
+}
+
 }  // namespace kmxp

@@ -86,7 +86,7 @@ def library():
         "kmx_build_grid": (C.c_int, [vp, vp, i64, vp, f32, C.POINTER(vp)]),
         "kmx_grid_free": (None, [vp]),
         "kmx_normals": (C.c_int, [vp, vp, C.POINTER(Params), vp, vp, vp, vp, i64, vp]),
-        "kmx_fasterpfh": (C.c_int, [vp, vp, C.POINTER(Params), vp, vp, vp, vp, vp, vp, vp, vp]),
+        "kmx_fasterpfh": (C.c_int, [vp, vp, C.POINTER(Params), vp, vp, vp, vp, i64, vp, vp, vp, vp]),
         "kmx_fpfh_classic": (C.c_int, [vp, vp, C.POINTER(Params), vp, vp, vp, vp, vp, vp]),
         "kmx_features": (C.c_int, [vp, vp, C.POINTER(Params), vp, vp, vp, vp, vp, vp]),
         "kmx_voxelize_count": (C.c_int, [vp, vp, i64, vp, i32, f32, vp, i64, vp, vp]),
@@ -302,8 +302,8 @@ class Context:
         if want_spfh:
             spfh = o.get("spfh", torch.empty((max(n, 1), DESC_STRIDE), dtype=torch.float32, device=self.device))
         self._check(self.lib.kmx_fasterpfh(self.h, grid.handle, C.byref(params), _ptr(normal4), _ptr(flags),
-                                           _ptr(offs), _ptr(nbr), _ptr(desc), _ptr(valid), _ptr(n_valid),
-                                           _ptr(spfh)), "kmx_fasterpfh")
+                                           _ptr(offs), _ptr(nbr), int(nbr.numel()), _ptr(desc), _ptr(valid),
+                                           _ptr(n_valid), _ptr(spfh)), "kmx_fasterpfh")
         return dict(desc=desc, valid=valid, n_valid=n_valid, spfh=spfh)
 
     def _search_descriptors(self, fn, grid, params, want_spfh, out):

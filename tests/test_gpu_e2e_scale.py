@@ -7,13 +7,15 @@
 * The large dense indoor pair (2M raw points per cloud, voxel 0.02 m,
   ~300k voxels): voxelisation is checked bit-exactly in full; descriptors and
   matches on sampled rows, against the oracle run on the whole cloud.
+* The same checks on the batched workload's largest members (300k raw points,
+  voxel 0.05 m, scene and LiDAR generators) matched on the tensor cores.
 """
 import os
 
 import numpy as np
 import pytest
 
-from synth import indoor_pair, scene_pair
+from synth import indoor_pair, lidar_pair, scene_pair
 
 pytestmark = pytest.mark.gpu
 
@@ -115,24 +117,21 @@ def test_registration_success_parity_1000(env, orc):
     assert abs(rate_o - rate_g) <= 0.005, (rate_o, rate_g, disagree)
 
 
-@pytest.mark.slow
-def test_indoor_2m_pair_sampled(env, orc):
-    torch, kmx, ctx = env
-    src, tgt, R, t, vps, vpt = indoor_pair(31)
-    v = 0.02
-    pair = _gpu_pair(torch, kmx, ctx, src, tgt, v, vps, vpt, kmx.MATCH_FP32_EXACT)
+def _check_sampled(torch, kmx, ctx, orc, pair, src, tgt, v, vps, min_vox):
+    """Voxels bit-exact in full; neighbour counts exact; J equal outside the
+    tau_lin band; 2000 sampled FPFH rows within their allowance; 300 sampled
+    source rows' mutual pairs equal to the FP64 nearest rows of the GPU's
+    own descriptors outside the 1e-3 gap band."""
     # voxelisation: bit-exact, whole clouds
     vs, _ = orc.voxelize(src, v)
     vt, _ = orc.voxelize(tgt, v)
     ns, nt = int(pair.src.n_vox.item()), int(pair.tgt.n_vox.item())
-    assert (ns, nt) == (len(vs), len(vt)) and ns > 200000
+    assert (ns, nt) == (len(vs), len(vt)) and ns > min_vox
     assert np.array_equal(pair.src.vox4[:ns].cpu().numpy().view(np.uint32), vs.view(np.uint32))
     assert np.array_equal(pair.tgt.vox4[:nt].cpu().numpy().view(np.uint32), vt.view(np.uint32))
-    # the oracle's chain on both whole clouds
+    # the oracle's chain on the whole source cloud
     ps = orc.OracleParams(v, viewpoint=np.float32(vps).astype(np.float64))
-    pt = orc.OracleParams(v, viewpoint=np.float32(vpt).astype(np.float64))
     fs = orc.faster_pfh(vs, ps)
-    ft = orc.faster_pfh(vt, pt)
     # neighbour counts are exact integers (the pair ran list-free; the list
     # call on the same grid gives the counts)
     prm = kmx.params_default(v, viewpoint=np.float32(vps).tolist())
@@ -194,3 +193,29 @@ def test_indoor_2m_pair_sampled(env, orc):
         checked_m += 1
     assert checked_m > 150
     pair.close()
+
+
+@pytest.mark.slow
+def test_indoor_2m_pair_sampled(env, orc):
+    torch, kmx, ctx = env
+    src, tgt, R, t, vps, vpt = indoor_pair(31)
+    v = 0.02
+    pair = _gpu_pair(torch, kmx, ctx, src, tgt, v, vps, vpt, kmx.MATCH_FP32_EXACT)
+    _check_sampled(torch, kmx, ctx, orc, pair, src, tgt, v, vps, 200000)
+
+
+@pytest.mark.parametrize("gen", ["scene", "lidar"])
+def test_batch_extremes_sampled(env, orc, gen):
+    """The largest members of the batched workload: 300k raw points per cloud
+    from either generator at the smallest voxel (0.05 m), about 85k-180k
+    descriptors per side, matched on the tensor cores (BF16 candidates, exact
+    FP32 rerank) as the batch matches its large pairs."""
+    torch, kmx, ctx = env
+    if gen == "scene":
+        src, tgt, R, t, vps, vpt = scene_pair(28, n=300000)
+    else:
+        src, tgt, R, t, vps, vpt = lidar_pair(28, az_bins=int(round(300000 / 64 / 0.92)))
+    assert len(src) > 290000
+    v = 0.05
+    pair = _gpu_pair(torch, kmx, ctx, src, tgt, v, vps, vpt, kmx.MATCH_BF16_RERANK)
+    _check_sampled(torch, kmx, ctx, orc, pair, src, tgt, v, vps, 100000)
