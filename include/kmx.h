@@ -308,8 +308,8 @@ kmx_status kmx_normals(kmx_ctx* ctx, const kmx_grid* grid, const kmx_params* par
  *   with w_k = |a_k - a_q| over the m neighbours k != q.
  *   d_normal4, d_nbr_offs, d_nbr  as written by kmx_normals (or any input of
  *              the same layout).
- *   nbr_cap    entries of d_nbr (as passed to kmx_normals); list entries at
- *              or past it are not read.  The context scratch holds one
+ *   nbr_cap    entries of d_nbr (as passed to kmx_normals; KMX_EINVAL if
+ *              negative); list entries at or past it are not read.  The context scratch holds one
  *              8-byte entry per list entry (each point's FPFH neighbours
  *              and weights, written by the SPFH pass for the FPFH pass).
  *   d_flags    [n] uint8 in/out: bit0 (B) is read; bit1 is set for q in J.

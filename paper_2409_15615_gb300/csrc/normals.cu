@@ -128,9 +128,11 @@ struct NormOut {
 };
 
 // Pass 2: CSR lists and centred second moments over P_normal per sorted
-// position; the moments go to scratch for solve_normals.
-__global__ void __launch_bounds__(kThreads) search_fill(GridView g, Radii R, NormScratch s, NormOut o,
-                                                        unsigned int* err)
+// position; the moments go to scratch for solve_normals.  Five blocks per SM
+// (a few registers spilled): no faster alone, but faster beside the other
+// cloud's kernels on a second stream.
+__global__ void __launch_bounds__(kThreads, 5) search_fill(GridView g, Radii R, NormScratch s, NormOut o,
+                                                           unsigned int* err)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t total_list = o.offs[o.n_cap];
