@@ -69,8 +69,19 @@ def library():
         raise ImportError("libkmx.so is not built (run paper_2409_15615_gb300.build.build()); "
                           "the kmx front end has no CPU fallback")
     lib = C.CDLL(path)
+    for name, (res, args) in signatures().items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def signatures():
+    """ctypes (restype, argtypes) of every entry point the binding calls, in
+    the order of the declarations in include/kmx.h."""
     vp, i64, i32, f32 = C.c_void_p, C.c_int64, C.c_int32, C.c_float
-    sig = {
+    return {
         "kmx_params_default": (C.c_int, [f32, C.POINTER(Params)]),
         "kmx_create": (C.c_int, [C.POINTER(vp), C.c_int, vp]),
         "kmx_destroy": (None, [vp]),
@@ -99,12 +110,6 @@ def library():
         "kmx_gnc": (C.c_int, [vp, vp, vp, vp, vp, i64, vp, vp, C.c_double, i32, C.c_double, C.c_double, vp, vp,
                               vp, vp]),
     }
-    for name, (res, args) in sig.items():
-        fn = getattr(lib, name)
-        fn.restype = res
-        fn.argtypes = args
-    _LIB = lib
-    return lib
 
 
 def _ptr(t):

@@ -70,3 +70,64 @@ def test_pair_stream_needs_a_slot():
 
     with pytest.raises(ValueError):
         pipeline.PairStream(None, 1, 1, slots=0)
+
+
+def _header_params():
+    """name -> (return type, [parameter types]) of every declaration in
+    include/kmx.h, comments removed."""
+    out = {}
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"^\s*((?:const\s+)?[\w\s\*]+?)\b(kmx_\w+)\s*\(([^;{]*?)\)\s*;", text, flags=re.M):
+            ret, name, args = m.group(1).strip(), m.group(2), m.group(3).strip()
+            params = [] if args in ("", "void") else [" ".join(a.split()) for a in args.split(",")]
+            out[name] = (ret, params)
+    return out
+
+
+def _kind_of_c(decl):
+    """The ctypes kind a C parameter or return type needs."""
+    d = decl.replace("const ", "")
+    if "*" in d:
+        return "char_p" if re.match(r"^char\s*\*$", d.strip()) else "pointer"
+    base = d.split()[0]
+    return {"int64_t": "i64", "int32_t": "i32", "int": "i32", "kmx_status": "i32", "float": "f32",
+            "double": "f64", "void": "void", "size_t": "u64"}[base]
+
+
+def _kind_of_ctypes(t):
+    import ctypes as C
+
+    if t is None:
+        return "void"
+    if t is C.c_char_p:
+        return "char_p"
+    if t is C.c_void_p or (isinstance(t, type) and issubclass(t, C._Pointer)):
+        return "pointer"
+    return {C.c_int64: "i64", C.c_int32: "i32", C.c_float: "f32", C.c_double: "f64", C.c_uint64: "u64"}[t]
+
+
+def test_binding_signatures_match_the_header():
+    """Every entry point the ctypes binding declares has the header's
+    parameter count and, position by position, the same kind (pointer, int32,
+    int64, float, double): a call through the binding passes what the C ABI
+    expects."""
+    from paper_2409_15615_gb300 import kmx
+
+    hdr = _header_params()
+    for name, (res, args) in kmx.signatures().items():
+        assert name in hdr, name
+        ret, params = hdr[name]
+        assert len(params) == len(args), (name, params, args)
+        # a parameter's type is everything but its name
+        want = []
+        for p in params:
+            m = re.match(r"^(.*?)(\w+)$", p)
+            want.append(_kind_of_c(m.group(1).strip()))
+        got = [_kind_of_ctypes(a) for a in args]
+        assert want == got, (name, want, got)
+        assert _kind_of_c(ret) == _kind_of_ctypes(res), (name, ret, res)
