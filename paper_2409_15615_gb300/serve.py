@@ -34,6 +34,11 @@ from . import kmx, pipeline
 # part for the kmx context's scratch and the grid's hash table slack
 MATCH_BYTES_PER_ROW = 96
 BYTES_FIXED = 32 << 20
+# the Faster-PFH call's context scratch: per point the J flag and position, an
+# SPFH row and the FPFH neighbour count; per neighbour-list entry 8 bytes (the
+# FPFH neighbours with their weights)
+FEATURE_BYTES_PER_POINT = 4 + 8 + 4 * kmx.DESC_STRIDE + 4
+FEATURE_BYTES_PER_ENTRY = 8
 RESERVE_BYTES = 2 << 30
 
 
@@ -117,10 +122,11 @@ def _run_request(slot: _Slot, req: Request, m: ResidentMap, mode: int, nbr_per_p
 def request_bytes(req: Request, m: ResidentMap, nbr_per_point: int = 96) -> int:
     """Device bytes a request allocates: its CloudState buffers (raw cloud,
     voxels, normals, flags, CSR offsets, neighbour lists, descriptors, J),
-    the grid (cell keys, ranges and a sorted copy of the points), the
-    correspondences and the matching scratch."""
+    the Faster-PFH scratch, the grid (cell keys, ranges and a sorted copy of
+    the points), the correspondences and the matching scratch."""
     n = max(len(req.xyz), 1)
     cloud = n * (12 + 16 + 16 + 1 + 8 + 4 * nbr_per_point + 4 * kmx.DESC_STRIDE + 4)
+    cloud += n * (FEATURE_BYTES_PER_POINT + FEATURE_BYTES_PER_ENTRY * nbr_per_point)
     grid = n * (2 * 8 + 2 * 8 + 16)
     corr = 16 * max(1, min(n, m.n_valid))
     return BYTES_FIXED + cloud + grid + corr + MATCH_BYTES_PER_ROW * (n + max(1, m.n_valid))
