@@ -407,7 +407,7 @@ def launch_count() -> int:
 
 
 def bf16_available() -> bool:
-    """Whether this build provides the BF16 tensor-core matching mode."""
+    """Whether the loaded library provides the BF16 tensor-core matching mode."""
     return True
 
 
