@@ -132,6 +132,17 @@ def request_bytes(req: Request, m: ResidentMap, nbr_per_point: int = 96) -> int:
     return BYTES_FIXED + cloud + grid + corr + MATCH_BYTES_PER_ROW * (n + max(1, m.n_valid))
 
 
+def admissible(need: int, in_use: int, budget: int, headroom: int, reserve: int) -> bool:
+    """Whether a request of `need` bytes may start now: it must fit in the
+    budget beside the `in_use` bytes of the requests in flight, and in the
+    measured device headroom less the reserve.  With nothing in flight a
+    request always starts (a single request larger than the budget still
+    runs, alone), so the loop cannot stall."""
+    if in_use <= 0:
+        return True
+    return in_use + need <= budget and headroom >= need + reserve
+
+
 def device_headroom(device) -> int:
     """Bytes a new request can still take: free device memory plus the blocks
     PyTorch's caching allocator holds without using them."""
@@ -200,8 +211,8 @@ class Server:
                 if realtime and r.arrival > now:
                     break
                 need = request_bytes(r, self.maps[r.map_id])
-                if in_use > 0 and (in_use + need > self.budget or
-                                   device_headroom(self.device) < need + self.reserve):
+                if in_use > 0 and not admissible(need, in_use, self.budget, device_headroom(self.device),
+                                                 self.reserve):
                     self.stats["held_by_memory"] += 1
                     break
                 pending.popleft()
